@@ -1,0 +1,409 @@
+"""NysADMM oracle -- TEST INFRASTRUCTURE ONLY.
+
+A plain, slow, FP64 NumPy restatement of the method of "NysADMM: faster
+composite convex optimization via low-rank approximation" (Zhao, Frangella,
+Udell, ICML 2022).  Only the tests, the smoke check and the benchmark's CPU
+baseline leg may import this module; the product path never does.  It shares
+no code with the CUDA library: its one shared dependency is the seeded input
+generator module, which holds no arithmetic of the method.
+
+Each function names the passage of the paper it restates.  NumPy / SciPy
+library routines (matmul, QR, Cholesky, SVD, triangular solve) serve as single
+steps; nothing is blocked, fused or reordered beyond the paper's algorithms.
+
+Readings where the paper is silent or ambiguous (all listed in the design doc):
+  * shift nu = shift_scale * eps(||Y||_2); eps(t) is the spacing of the working
+    precision at t (MATLAB eps); default shift_scale = sqrt(d) (the adaptive
+    algorithm's form, App. B), used for the fixed-rank sketch as well.
+  * Cholesky failure: nu is multiplied by 10, up to 3 retries.
+  * PCG stopping: 'rel' (||w|| <= tol*||r||), 'abs' (||w|| <= tol, Alg.
+    Nystrom PCG as printed), or a fixed iteration count.
+  * ADMM starts from x = z = u = 0; PCG is warm-started at the previous x.
+  * Adaptive rank: stop at the first rank whose empirical condition number
+    (lam_s + rho)/rho <= Tol; otherwise double, and when doubling would pass
+    s_max, extend to s_max once and stop.
+
+Functions with no independent pin: none (every function here is pinned by a
+test in tests/test_oracle_pins.py against closed forms, library solvers,
+brute force or the paper's lemmas).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg as sla
+
+
+class NotSPDError(RuntimeError):
+    pass
+
+
+class BreakdownError(RuntimeError):
+    pass
+
+
+# ---------------------------------------------------------------------------
+# Scalars
+# ---------------------------------------------------------------------------
+
+def eps_of(t: float, mantissa_bits: int = 52) -> float:
+    """Spacing of the working precision at |t| (MATLAB eps(t)), used for the
+    shift of Alg. Randomized Nystrom Approximation (App. B).
+
+    For t = f * 2^e with 0.5 <= f < 1 this is 2^(e - 1 - mantissa_bits).
+    mantissa_bits = 52 for FP64, 23 for FP32."""
+    t = abs(float(t))
+    if t == 0.0:
+        return 2.0 ** (-1074) if mantissa_bits == 52 else 2.0 ** (-149)
+    _, e = math.frexp(t)
+    return 2.0 ** (e - 1 - mantissa_bits)
+
+
+def soft_threshold(v: np.ndarray, kappa: float) -> np.ndarray:
+    """z-update of ADMM for h = gamma*||.||_1 (Sec. 2.1): sign(v) max(|v|-kappa, 0)."""
+    return np.sign(v) * np.maximum(np.abs(v) - kappa, 0.0)
+
+
+# ---------------------------------------------------------------------------
+# Randomized Nystrom approximation (App. B, Alg. Randomized Nystrom Approximation)
+# ---------------------------------------------------------------------------
+
+def thin_qr(Omega: np.ndarray) -> np.ndarray:
+    """qr(Omega, 0): orthonormal basis of range(Omega) (Householder, LAPACK)."""
+    Q, _ = np.linalg.qr(Omega, mode="reduced")
+    return Q
+
+
+def nystrom_from_sketch(Y: np.ndarray, Omega: np.ndarray, shift_scale: float = 1.0,
+                        mantissa_bits: int = 52, max_retries: int = 3):
+    """Steps after Y = H Omega of the randomized Nystrom approximation:
+
+        nu   = shift_scale * eps(||Y||_2)
+        Y_nu = Y + nu * Omega
+        C    = chol(Omega^T Y_nu)        (upper, C^T C = Omega^T Y_nu)
+        B    = Y_nu / C                  (B C = Y_nu)
+        [U, Sigma] = svd(B, 0)
+        Lam  = max(0, Sigma^2 - nu)
+
+    Returns (U, lam, nu) with lam sorted in descending order.
+    """
+    sigma_max = np.linalg.norm(Y, 2)
+    nu = shift_scale * eps_of(sigma_max, mantissa_bits)
+    for _ in range(max_retries + 1):
+        Ynu = Y + nu * Omega
+        M = Omega.T @ Ynu
+        M = 0.5 * (M + M.T)
+        try:
+            C = np.linalg.cholesky(M).T          # upper triangular, C^T C = M
+        except np.linalg.LinAlgError:
+            nu *= 10.0
+            continue
+        if not np.all(np.isfinite(C)):
+            nu *= 10.0
+            continue
+        # B C = Y_nu  <=>  C^T B^T = Y_nu^T
+        B = sla.solve_triangular(C, Ynu.T, trans="T", lower=False).T
+        U, S, _ = np.linalg.svd(B, full_matrices=False)
+        lam = np.maximum(0.0, S * S - nu)
+        return U, lam, nu
+    raise NotSPDError("Omega^T Y_nu is not numerically SPD after shift retries")
+
+
+def nystrom(H_apply, Omega: np.ndarray, shift_scale: float = 1.0, mantissa_bits: int = 52):
+    """Alg. Randomized Nystrom Approximation: H_apply(X) returns H X.
+
+    Omega is the Gaussian test matrix (d x s); it is orthonormalised here."""
+    Q = thin_qr(Omega)
+    Y = H_apply(Q)
+    U, lam, nu = nystrom_from_sketch(Y, Q, shift_scale, mantissa_bits)
+    return U, lam, nu, Q, Y
+
+
+def nystrom_definition(H: np.ndarray, Omega: np.ndarray) -> np.ndarray:
+    """Eq. (Nystrom approximation): H<Omega> = (H Omega)(Omega^T H Omega)^+ (H Omega)^T."""
+    HO = H @ Omega
+    return HO @ np.linalg.pinv(Omega.T @ HO) @ HO.T
+
+
+# ---------------------------------------------------------------------------
+# Nystrom preconditioner (Sec. 2.2, Eq. Nystrom preconditioner)
+# ---------------------------------------------------------------------------
+
+def precond_apply(U: np.ndarray, lam: np.ndarray, rho: float, v: np.ndarray) -> np.ndarray:
+    """P^{-1} v = (lam_s + rho) U (Lam + rho I)^{-1} U^T v + (I - U U^T) v."""
+    lam_s = lam[-1]
+    Utv = U.T @ v
+    return (lam_s + rho) * (U @ (Utv / (lam + rho)))[..., ] + v - U @ Utv
+
+
+def precond_dense(U: np.ndarray, lam: np.ndarray, rho: float):
+    """Dense P and P^{-1} exactly as printed in Eq. (Nystrom preconditioner)."""
+    d = U.shape[0]
+    lam_s = lam[-1]
+    I = np.eye(d)
+    P = (U * (lam + rho)) @ U.T / (lam_s + rho) + (I - U @ U.T)
+    Pinv = (lam_s + rho) * (U / (lam + rho)) @ U.T + (I - U @ U.T)
+    return P, Pinv
+
+
+def empirical_condition_number(lam: np.ndarray, rho: float) -> float:
+    """Eq. (empirical condition number): (lam_s + rho) / rho."""
+    return (lam[-1] + rho) / rho
+
+
+def effective_dimension(H: np.ndarray, rho: float) -> float:
+    """Eq. (effective dimension): tr(H (H + rho I)^{-1})."""
+    ev = np.linalg.eigvalsh(H)
+    ev = np.maximum(ev, 0.0)
+    return float(np.sum(ev / (ev + rho)))
+
+
+# ---------------------------------------------------------------------------
+# Nystrom PCG (App. B, Alg. Nystrom PCG)
+# ---------------------------------------------------------------------------
+
+def pcg(H_apply, rho: float, U, lam, r: np.ndarray, x0: np.ndarray, tol: float,
+        tol_mode: str = "rel", maxit: int | None = None, fixed_iters: int | None = None):
+    """Solve (H + rho I) x = r by PCG with the Nystrom preconditioner.
+
+    U = None (or an empty basis) gives plain CG (P = I).
+    Stopping test at the top of the loop, as printed: ||w||_2 > eps.
+      tol_mode 'rel': eps = tol * ||r||;  'abs': eps = tol.
+    fixed_iters: run exactly this many iterations (no stopping test).
+    Returns (x, iterations, ||w||)."""
+    d = r.shape[0]
+    if maxit is None:
+        maxit = min(d, 1000)
+
+    def Pinv(v):
+        if U is None or U.shape[1] == 0:
+            return v.copy()
+        return precond_apply(U, lam, rho, v)
+
+    def Hrho(v):
+        return H_apply(v) + rho * v
+
+    x = x0.astype(np.float64).copy()
+    w = r - Hrho(x)
+    y = Pinv(w)
+    p = y.copy()
+    thresh = tol * np.linalg.norm(r) if tol_mode == "rel" else tol
+    it = 0
+    while True:
+        if fixed_iters is not None:
+            if it >= fixed_iters:
+                break
+        else:
+            if not (np.linalg.norm(w) > thresh) or it >= maxit:
+                break
+        v = Hrho(p)
+        pv = p @ v
+        if not (pv > 0.0) or not np.isfinite(pv):
+            raise BreakdownError("p^T (H + rho I) p <= 0")
+        alpha = (w @ y) / pv
+        x = x + alpha * p
+        w_new = w - alpha * v
+        y_new = Pinv(w_new)
+        beta = (w_new @ y_new) / (w @ y)
+        p = y_new + beta * p
+        w, y = w_new, y_new
+        it += 1
+    return x, it, float(np.linalg.norm(w))
+
+
+# ---------------------------------------------------------------------------
+# Lasso (Eq. 2) by NysADMM (Alg. NysADMM with Eq. ADMMSubProb, H^l = I, g = 0)
+# ---------------------------------------------------------------------------
+
+def lasso_objective(A, b, gamma, x) -> float:
+    """Eq. (2): 1/2 ||A x - b||^2 + gamma ||x||_1."""
+    res = A @ x - b
+    return 0.5 * float(res @ res) + gamma * float(np.sum(np.abs(x)))
+
+
+def lasso_kkt_eta(A, b, gamma, x) -> float:
+    """Eq. (31): ||x - prox_{gamma||.||_1}(x - A^T(Ax - b))|| / (1 + ||x|| + ||Ax - b||)."""
+    res = A @ x - b
+    g = A.T @ res
+    num = np.linalg.norm(x - soft_threshold(x - g, gamma))
+    return float(num / (1.0 + np.linalg.norm(x) + np.linalg.norm(res)))
+
+
+def lasso_dual_gap(A, b, gamma, x) -> float:
+    """Primal minus dual objective at the dual-feasible point obtained by
+    scaling the residual theta = (b - A x) * min(1, gamma / ||A^T (b - A x)||_inf).
+    Dual of Eq. (2): max 1/2||b||^2 - 1/2||b - theta||^2 s.t. ||A^T theta||_inf <= gamma."""
+    theta = b - A @ x
+    s = np.max(np.abs(A.T @ theta))
+    if s > gamma:
+        theta = theta * (gamma / s)
+    dual = 0.5 * float(b @ b) - 0.5 * float((b - theta) @ (b - theta))
+    return lasso_objective(A, b, gamma, x) - dual
+
+
+def lasso_nysadmm(A: np.ndarray, b: np.ndarray, gamma: float, rho: float, Omega: np.ndarray,
+                  admm_iters: int, pcg_tol: float = 1e-8, pcg_tol_mode: str = "rel",
+                  shift_scale: float | None = None, pcg_fixed=None, pcg_maxit=None,
+                  eps_abs: float | None = None, eps_rel: float | None = None,
+                  precond=None):
+    """Alg. NysADMM for the lasso.
+
+    Sketch once (App. B) with H = A^T A, then for k = 0, 1, ...:
+        r^k     = rho z - rho u + A^T b            (Eq. ADMMSubProb with l = 1/2||.-b||^2)
+        x^{k+1} = PCG solve of (A^T A + rho I) x = r^k, warm-started at x^k
+        z^{k+1} = S_{gamma/rho}(x^{k+1} + u^k)
+        u^{k+1} = u^k + x^{k+1} - z^{k+1}
+        r_p     = ||x^{k+1} - z^{k+1}||,  r_d = rho ||z^k - z^{k+1}||   (Sec. 2.1)
+    pcg_fixed: None, an int, or a per-iteration sequence of PCG iteration counts.
+    Stops after admm_iters, or earlier when eps_abs/eps_rel are given and the
+    residual test of Sec. 2.1 holds.
+    Returns dict with x, z, u, U, lam, nu, and per-iteration traces."""
+    n, d = A.shape
+    if shift_scale is None:
+        shift_scale = math.sqrt(d)
+    H_apply = lambda X: A.T @ (A @ X)
+    if precond is None:
+        U, lam, nu, Q, _ = nystrom(H_apply, Omega, shift_scale)
+    else:
+        U, lam, nu = precond
+    x = np.zeros(d)
+    z = np.zeros(d)
+    u = np.zeros(d)
+    q = A.T @ b
+    trace = {"pcg_iters": [], "r_p": [], "r_d": [], "z": []}
+    for k in range(admm_iters):
+        r = rho * z - rho * u + q
+        fixed = None
+        if pcg_fixed is not None:
+            fixed = pcg_fixed if isinstance(pcg_fixed, int) else int(pcg_fixed[k])
+        x, it, _ = pcg(H_apply, rho, U, lam, r, x, pcg_tol, pcg_tol_mode,
+                       maxit=pcg_maxit, fixed_iters=fixed)
+        z_old = z
+        z = soft_threshold(x + u, gamma / rho)
+        u = u + x - z
+        r_p = float(np.linalg.norm(x - z))
+        r_d = float(rho * np.linalg.norm(z_old - z))
+        trace["pcg_iters"].append(it)
+        trace["r_p"].append(r_p)
+        trace["r_d"].append(r_d)
+        trace["z"].append(z.copy())
+        if eps_abs is not None and eps_rel is not None:
+            if (r_p <= eps_abs + eps_rel * max(np.linalg.norm(x), np.linalg.norm(z)) and
+                    r_d <= eps_abs + eps_rel * np.linalg.norm(rho * u)):
+                break
+    return {"x": x, "z": z, "u": u, "U": U, "lam": lam, "nu": nu, "trace": trace}
+
+
+# ---------------------------------------------------------------------------
+# Adaptive sketch size (App. C, Alg. AdaptiveRandNysAppx)
+# ---------------------------------------------------------------------------
+
+def adaptive_nystrom(H_apply, Omega_pool: np.ndarray, s0: int, s_max: int, rho: float,
+                     tol: float, shift_scale: float | None = None, mantissa_bits: int = 52):
+    """Alg. AdaptiveRandNysAppx.  Gaussian blocks are consecutive column slices
+    of Omega_pool (d x s_max), each orthonormalised on its own; the sketch of
+    earlier blocks is reused.  Returns (U, lam, nu, ranks_tried)."""
+    d = Omega_pool.shape[0]
+    if shift_scale is None:
+        shift_scale = math.sqrt(d)
+    Om = np.zeros((d, 0))
+    Y = np.zeros((d, 0))
+    m = s0
+    used = 0
+    ranks = []
+    while True:
+        Om0 = thin_qr(Omega_pool[:, used:used + m])
+        used += m
+        Y0 = H_apply(Om0)
+        Om = np.hstack([Om, Om0])
+        Y = np.hstack([Y, Y0])
+        U, lam, nu = nystrom_from_sketch(Y, Om, shift_scale, mantissa_bits)
+        ranks.append(Om.shape[1])
+        if empirical_condition_number(lam, rho) <= tol:
+            break
+        m = s0
+        s0 = 2 * s0
+        if s0 > s_max:
+            s0 = s0 - m
+            m = s_max - s0
+            if m > 0:
+                Om0 = thin_qr(Omega_pool[:, used:used + m])
+                used += m
+                Y0 = H_apply(Om0)
+                Om = np.hstack([Om, Om0])
+                Y = np.hstack([Y, Y0])
+                U, lam, nu = nystrom_from_sketch(Y, Om, shift_scale, mantissa_bits)
+                ranks.append(Om.shape[1])
+            break
+    return U, lam, nu, ranks
+
+
+# ---------------------------------------------------------------------------
+# l1-regularised logistic regression (Sec. 3.2, Eq. 9)
+# ---------------------------------------------------------------------------
+
+def logistic_objective(A, b_pm, gamma, x) -> float:
+    """Eq. (9) with labels mapped to {0,1} by b01 = (1 + b)/2:
+    -sum_i (b01_i t_i - log(1 + exp(t_i))) + gamma ||x||_1,  t = A x."""
+    b01 = 0.5 * (1.0 + b_pm)
+    t = A @ x
+    softplus = np.maximum(t, 0.0) + np.log1p(np.exp(-np.abs(t)))
+    return float(np.sum(softplus - b01 * t) + gamma * np.sum(np.abs(x)))
+
+
+def logistic_weights(t: np.ndarray, b01: np.ndarray):
+    """Sec. 3.2: w_i = 1/(2 + e^{-t_i} + e^{t_i}),
+    q_i = t_i + (b01_i - 1/(1 + e^{-t_i})) / w_i."""
+    with np.errstate(over="ignore"):
+        w = 1.0 / (2.0 + np.exp(-t) + np.exp(t))
+        sig = 1.0 / (1.0 + np.exp(-t))
+    q = t + (b01 - sig) / w
+    if not np.all(np.isfinite(q)):
+        raise FloatingPointError("logistic weight underflow (|A x| too large for this form)")
+    return w, q
+
+
+def logistic_nysadmm(A, b_pm, gamma, rho, Omega_pool, admm_iters, s0, s_max, ada_tol=2.0,
+                     pcg_tol=1e-8, pcg_tol_mode="rel", pcg_fixed=None, resketch_every=1,
+                     shift_scale=None):
+    """Linearised ADMM for Eq. (9) (Sec. 3.2) with the Nystrom preconditioner
+    from Alg. AdaptiveRandNysAppx.  At every outer iteration k:
+        t = A x~,  w, q from Sec. 3.2,  H = A^T diag(w) A,
+        r = rho z~ - rho u~ + A^T diag(w) q,
+        x = PCG solve of (H + rho I) x = r (warm start x~),
+        z = S_{gamma/rho}(x + u),  u = u + x - z.
+    The rank is chosen adaptively at k = 0; later re-sketches (every
+    resketch_every iterations) reuse the settled rank and the same Omega blocks."""
+    n, d = A.shape
+    b01 = 0.5 * (1.0 + b_pm)
+    x = np.zeros(d)
+    z = np.zeros(d)
+    u = np.zeros(d)
+    rank = None
+    U = lam = None
+    trace = {"pcg_iters": [], "rank": [], "obj": [], "r_p": [], "r_d": []}
+    for k in range(admm_iters):
+        t = A @ x
+        w, q = logistic_weights(t, b01)
+        H_apply = lambda X, w=w: A.T @ (w[:, None] * (A @ X)) if X.ndim == 2 else A.T @ (w * (A @ X))
+        if k == 0:
+            U, lam, nu, ranks = adaptive_nystrom(H_apply, Omega_pool, s0, s_max, rho, ada_tol,
+                                                 shift_scale)
+            rank = ranks[-1]
+        elif resketch_every and k % resketch_every == 0:
+            U, lam, nu, _ = adaptive_nystrom(H_apply, Omega_pool, rank, rank, rho, 0.0,
+                                             shift_scale)
+        r = rho * z - rho * u + A.T @ (w * q)
+        fixed = None
+        if pcg_fixed is not None:
+            fixed = pcg_fixed if isinstance(pcg_fixed, int) else int(pcg_fixed[k])
+        x, it, _ = pcg(H_apply, rho, U, lam, r, x, pcg_tol, pcg_tol_mode, fixed_iters=fixed)
+        z_old = z
+        z = soft_threshold(x + u, gamma / rho)
+        u = u + x - z
+        trace["pcg_iters"].append(it)
+        trace["rank"].append(rank)
+        trace["r_p"].append(float(np.linalg.norm(x - z)))
+        trace["r_d"].append(float(rho * np.linalg.norm(z_old - z)))
+    return {"x": x, "z": z, "u": u, "rank": rank, "trace": trace}
