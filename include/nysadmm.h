@@ -1,0 +1,181 @@
+/*
+ * nysadmm.h -- C ABI of the GB300 NysADMM hot path.
+ *
+ * The library solves  minimize  l(Ax; b) + gamma ||x||_1   (Eq. 1 / Eq. 2 /
+ * Eq. 9 of "NysADMM: faster composite convex optimization via low-rank
+ * approximation") by inexact linearised ADMM whose x-subproblem
+ *     (A^T D A + rho I) x = r            (Eq. ADMMSubProb; D = I for the lasso,
+ *                                         D = diag(sigma(1-sigma)) for Eq. 9)
+ * is solved by conjugate gradients preconditioned with a randomised Nystrom
+ * approximation (App. B: Alg. Randomized Nystrom Approximation, Alg. Nystrom PCG).
+ *
+ * Conventions shared by every entry point
+ *  - Every array argument is a DEVICE pointer on the current CUDA device,
+ *    caller-owned, unless the comment says "host".  The caller keeps it valid
+ *    until the call returns; all work is issued on `stream` (NULL = legacy
+ *    default stream) and every entry point synchronises `stream` before it
+ *    returns, so outputs are ready on return.
+ *  - Matrices (nys_matrix) are dense and ROW-major: element (i, j) of A is at
+ *    data + i*ld + j.  ld >= d, ld * sizeof(element) must be a multiple of 16
+ *    bytes and data must be 16-byte aligned (rows are streamed by TMA bulk
+ *    copies).  Entries j in [d, ld) are never read as data.
+ *  - d x s panels (Omega, U) are COLUMN-major with leading dimension d.
+ *  - Vector precision ("compute type") follows the matrix that PCG runs on:
+ *    FP64 vectors for an NYS_F64 matrix, FP32 vectors for NYS_F32 / NYS_BF16.
+ *    ADMM state (x, z, u, residuals) is always FP64.
+ *  - Errors are returned, never trapped: NYS_EINVAL for bad arguments (checked
+ *    before any launch), NYS_ENOTSPD if the Nystrom core matrix stays
+ *    indefinite after shift retries, NYS_EBREAKDOWN if p^T (H + rho I) p <= 0
+ *    or is not finite in PCG, NYS_ENOCONV when an iteration cap is reached
+ *    (the last iterate is still written), NYS_ETIMEOUT if a device-side wait
+ *    exceeded its bound, NYS_ECUDA for a CUDA runtime error, NYS_ENOMEM if a
+ *    workspace allocation failed.
+ *  - The library allocates its own workspace with cudaMallocAsync on `stream`
+ *    and frees it before returning; nys_precond handles own device memory
+ *    until nys_precond_destroy.
+ */
+#ifndef NYSADMM_H
+#define NYSADMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NYS_OK = 0,
+  NYS_EINVAL = 1,
+  NYS_ENOTSPD = 2,
+  NYS_EBREAKDOWN = 3,
+  NYS_ENOCONV = 4,
+  NYS_ETIMEOUT = 5,
+  NYS_ECUDA = 6,
+  NYS_ENOMEM = 7
+} nys_status;
+
+/* Loss l(Ax; b): the lasso (Eq. 2, D = I) or l1-regularised logistic
+ * regression (Eq. 9 with labels b in {-1,+1} mapped to (1+b)/2). */
+typedef enum { NYS_LASSO = 0, NYS_LOGISTIC = 1 } nys_loss;
+
+typedef enum { NYS_F64 = 0, NYS_F32 = 1, NYS_BF16 = 2 } nys_dtype;
+
+/* PCG stopping test at the top of each iteration (Alg. Nystrom PCG):
+ * REL: ||w|| <= tol ||r||;  ABS: ||w|| <= tol (as printed);
+ * SQRT_RPRD: inside ADMM, tol_k = sqrt(r_p r_d) of the previous ADMM
+ * iteration (Sec. 5 experiments), REL with `tol` at the first iteration. */
+typedef enum { NYS_TOL_REL = 0, NYS_TOL_ABS = 1, NYS_TOL_SQRT_RPRD = 2 } nys_tol_mode;
+
+typedef struct {
+  const void* data;  /* device, row-major n x ld, 16-byte aligned */
+  int32_t dtype;     /* nys_dtype */
+  int64_t n, d, ld;
+} nys_matrix;
+
+/* Opaque Nystrom preconditioner: U (d x s, orthonormal columns), the
+ * eigenvalue estimates lam (descending) and the shift nu (App. B). */
+typedef struct nys_precond_s* nys_precond;
+
+typedef struct {
+  double shift_scale;          /* nu = shift_scale * eps(||Y||_2); <= 0 -> sqrt(d) */
+  int32_t pcg_tol_mode;        /* nys_tol_mode */
+  int32_t pcg_maxit;           /* <= 0 -> min(d, 1000) */
+  const int32_t* pcg_fixed_iters; /* host, length admm_maxit, or NULL: run exactly
+                                      this many PCG iterations at ADMM iteration k */
+  int32_t admm_maxit;          /* ADMM iterations (upper bound when eps_rel > 0) */
+  double eps_abs, eps_rel;     /* residual stop of Sec. 2.1; eps_rel <= 0 -> off */
+  const nys_matrix* A_inner;   /* optional lower-precision copy of A used for the
+                                  sketch and inside PCG (mixed form); NULL -> A */
+  int32_t refine;              /* mixed form: each x-step solves for the correction
+                                  of the exact residual r - (A^T D A + rho I) x
+                                  computed with A (1) or runs PCG on A_inner alone (0) */
+  double* z_trace;             /* device, admm_maxit x d (row k = z after iteration
+                                  k), or NULL */
+  int32_t rank_max;            /* adaptive rank cap (logistic); <= 0 -> rank */
+  double ada_tol;              /* adaptive stop (lam_s + rho)/rho <= ada_tol; <= 0 -> 2 */
+  int32_t resketch_every;      /* logistic: re-sketch period in outer iterations (0 = never) */
+  void* stream;                /* cudaStream_t */
+} nys_opts;
+
+typedef struct {
+  int32_t admm_iters;          /* ADMM iterations run */
+  int32_t pcg_iters_total;     /* sum of PCG iterations */
+  int32_t final_rank;          /* sketch size of the last preconditioner */
+  int32_t status;              /* nys_status of the solve */
+  double r_p, r_d;             /* last primal / dual residual norms (Sec. 2.1) */
+  double emp_cond;             /* (lam_s + rho)/rho of the last preconditioner (Eq. empCondNum) */
+  double nu;                   /* shift of the last sketch */
+} nys_info;
+
+/* Fills *o with the defaults documented in nys_opts. */
+void nys_opts_default(nys_opts* o);
+
+/* H-matvec (Table 1, T_mv; the product inside Alg. Nystrom PCG):
+ *   y = A^T diag(D) A p + rho p,  one read of A per call.
+ * D: device, length n, FP64, or NULL for D = I.  p, y: device, length d, in the
+ * compute type of A (FP64 for NYS_F64, else FP32).  y must not alias p. */
+nys_status nys_hmatvec(const nys_matrix* A, const double* D, double rho, const void* p,
+                       void* y, void* stream);
+
+/* Randomized Nystrom approximation of H = A^T diag(D) A + diag_shift I
+ * (App. B, Alg. Randomized Nystrom Approximation): Omega (device, d x s,
+ * column-major FP64 Gaussian test matrix drawn by the caller) is
+ * orthonormalised (CholQR2), Y = H Omega is sketched (in FP64 for an NYS_F64
+ * matrix, FP32 otherwise), and the FP64 core gives U, lam.  Omega is not
+ * modified.  opts may be NULL (defaults; opts->stream supplies the stream). */
+nys_status nys_sketch(const nys_matrix* A, const double* D, double diag_shift, int32_t s,
+                      const double* Omega, const nys_opts* opts, nys_precond* out);
+
+/* Copies the factors out: U_out (device, d x s column-major FP64) and
+ * lam_out (host, length s, descending) may be NULL.  *s_out, *d_out, *nu_out
+ * (host) are set when non-NULL. */
+nys_status nys_precond_get(nys_precond P, double* U_out, double* lam_out, int32_t* s_out,
+                           int64_t* d_out, double* nu_out, void* stream);
+
+/* P^{-1} applied to k vectors (Eq. Nystrom preconditioner):
+ *   Y = (lam_s + rho) U (Lam + rho I)^{-1} U^T V + (I - U U^T) V,
+ * V, Y: device, d x k column-major, dtype NYS_F64 or NYS_F32.  Y may alias V. */
+nys_status nys_precond_apply(nys_precond P, double rho, const void* V, void* Y, int64_t k,
+                             int32_t dtype, void* stream);
+
+/* Nystrom PCG (App. B, Alg. Nystrom PCG) for (A^T diag(D) A + rho I) x = r.
+ * r, x: device, length d, compute type of A; x holds x0 on entry and the
+ * solution on return.  P may be NULL (plain CG).  tol with opts->pcg_tol_mode
+ * (REL or ABS); opts->pcg_fixed_iters[0], when set, fixes the iteration count.
+ * *iters and *resnorm (host, may be NULL) receive the iteration count and ||w||. */
+nys_status pcg_solve(const nys_matrix* A, const double* D, double rho, nys_precond P,
+                     const void* r, void* x, double tol, const nys_opts* opts,
+                     int32_t* iters, double* resnorm);
+
+/* NysADMM (Alg. NysADMM; Alg. AdaNysADMM for the logistic loss):
+ * loss NYS_LASSO: sketch once, then opts->admm_maxit ADMM iterations with
+ * PCG tolerance `tol` (mode opts->pcg_tol_mode), warm-started at the previous
+ * x, z-update by soft-thresholding at gamma/rho.
+ * loss NYS_LOGISTIC: D and the right-hand side are refreshed from
+ * t = A x~ at every outer iteration (Sec. 3.2); the rank is chosen by
+ * Alg. AdaptiveRandNysAppx from `rank` up to opts->rank_max at the first
+ * iteration and re-sketched every opts->resketch_every iterations.
+ * b: device, length n, FP64 (labels in {-1,+1} for NYS_LOGISTIC).
+ * Omega: device, d x max(rank, rank_max) column-major FP64 Gaussian.
+ * x_out, z_out: device, length d, FP64 (z is the sparse iterate; either may be
+ * NULL).  info: host, may be NULL. */
+nys_status nysadmm_solve(int32_t loss, const nys_matrix* A, const double* b, double gamma,
+                         double rho, int32_t rank, double tol, const double* Omega,
+                         const nys_opts* opts, double* x_out, double* z_out, nys_info* info);
+
+/* Objective and optimality measures at x (FP64, one read of A):
+ * out[0] = l(Ax; b) + gamma ||x||_1 (Eq. 2 or Eq. 9);
+ * out[1] = relative KKT residual eta (Eq. 31; lasso) or ||A^T(sigma(Ax)-b01)||_inf (logistic);
+ * out[2] = duality gap at the scaled-residual dual point (lasso) or 0 (logistic).
+ * x: device, length d, FP64; out: host, length 3. */
+nys_status nys_objective(int32_t loss, const nys_matrix* A, const double* b, double gamma,
+                         const double* x, double* out, void* stream);
+
+void nys_precond_destroy(nys_precond P);
+const char* nys_strerror(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NYSADMM_H */

@@ -1,0 +1,874 @@
+// C ABI of libnysadmm (include/nysadmm.h): argument checks, the Nystrom sketch
+// driver (App. B), the preconditioner handle (Eq. Nystrom preconditioner), the
+// PCG entry point (App. B, Alg. Nystrom PCG) and the NysADMM drivers
+// (Alg. NysADMM for the lasso, Sec. 3.2 + App. C for l1-logistic regression).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "device_util.cuh"
+#include "solver.cuh"
+
+using namespace nys;
+
+struct nys_precond_s {
+  int64_t d = 0;
+  int s = 0;
+  double nu = 0.0;
+  double* U64 = nullptr;  // d x s, column-major
+  float* U32 = nullptr;   // FP32 copy, built on first FP32 use
+  double* lam_d = nullptr;
+  std::vector<double> lam;  // host copy, descending
+};
+
+namespace {
+
+constexpr int kMaxRank = 1024;
+
+cudaStream_t stream_of(const nys_opts* o) { return o ? reinterpret_cast<cudaStream_t>(o->stream) : nullptr; }
+
+bool is_fin(double v) { return std::isfinite(v); }
+
+nys_status check_matrix(const nys_matrix* A) {
+  if (!A || !A->data) return NYS_EINVAL;
+  if (A->n <= 0 || A->d <= 0 || A->ld < A->d) return NYS_EINVAL;
+  if (A->dtype != NYS_F64 && A->dtype != NYS_F32 && A->dtype != NYS_BF16) return NYS_EINVAL;
+  const size_t esz = dtype_size(A->dtype);
+  if ((A->ld * esz) % 16 != 0) return NYS_EINVAL;
+  if (reinterpret_cast<uintptr_t>(A->data) % 16 != 0) return NYS_EINVAL;
+  ApassPlan plan;
+  if (!apass_plan(A, &plan)) return NYS_EINVAL;
+  return NYS_OK;
+}
+
+nys_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return NYS_OK;
+  if (e == cudaErrorMemoryAllocation) return NYS_ENOMEM;
+  return NYS_ECUDA;
+}
+
+#define NYS_TRY(expr)                    \
+  do {                                   \
+    nys_status _s = (expr);              \
+    if (_s != NYS_OK) return _s;         \
+  } while (0)
+#define NYS_CU(expr) NYS_TRY(cuda_status(expr))
+
+double eps_host(double t, int mant_bits) {
+  t = std::fabs(t);
+  if (t == 0.0) return mant_bits == 52 ? std::ldexp(1.0, -1074) : std::ldexp(1.0, -149);
+  int e = 0;
+  std::frexp(t, &e);
+  return std::ldexp(1.0, e - 1 - mant_bits);
+}
+
+// Thin QR of Omega (d x m, in place) by CholQR2: twice G = Om^T Om, C = chol(G), Om <- Om C^{-1}.
+nys_status cholqr2(double* Om, int64_t d, int m, cudaStream_t st) {
+  Pool pool(st);
+  double* G = pool.alloc<double>((size_t)m * m);
+  double* work = pool.alloc<double>(gram_work_bytes(d, m) / sizeof(double) + 1);
+  int* info = pool.alloc<int>(1);
+  if (!pool.ok()) return NYS_ENOMEM;
+  for (int pass = 0; pass < 2; ++pass) {
+    NYS_CU(gram_xty(Om, Om, d, m, G, work, st));
+    NYS_CU(chol_upper(G, m, info, st));
+    int info_h = 0;
+    NYS_CU(cudaMemcpyAsync(&info_h, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NYS_CU(cudaStreamSynchronize(st));
+    if (info_h != 0) return NYS_EINVAL;  // Omega has (numerically) dependent columns
+    NYS_CU(trsm_right_upper(G, m, Om, d, st));
+  }
+  return NYS_OK;
+}
+
+// Y (d x m, FP64) = (A^T diag(D) A + shift I) Om for an FP64 orthonormal panel Om.
+nys_status sketch_panel(const nys_matrix* A, const double* D, double shift, const double* Om, int m, double* Y,
+                        cudaStream_t st) {
+  Pool pool(st);
+  const int64_t n = A->n, d = A->d;
+  const size_t wbytes = sketch_atw_work_bytes(A, m);
+  void* work = pool.alloc<unsigned char>(wbytes);
+  if (A->dtype == NYS_F64) {
+    double* W = pool.alloc<double>((size_t)n * m);
+    if (!pool.ok()) return NYS_ENOMEM;
+    NYS_CU(sketch_aw(A, Om, m, D, W, st));
+    NYS_CU(sketch_atw(A, W, m, Y, work, wbytes, st));
+  } else {
+    float* Om32 = pool.alloc<float>((size_t)d * m);
+    float* W = pool.alloc<float>((size_t)n * m);
+    if (!pool.ok()) return NYS_ENOMEM;
+    NYS_CU(convert_f64_to_f32(Om, Om32, d * m, st));
+    NYS_CU(sketch_aw(A, Om32, m, D, W, st));
+    NYS_CU(sketch_atw(A, W, m, Y, work, wbytes, st));
+  }
+  if (shift != 0.0) NYS_CU(axpy_panel(shift, Om, Y, d * m, st));
+  return NYS_OK;
+}
+
+// FP64 core of App. B from the orthonormal Om and Y = H Om (both d x s):
+// nu, Y_nu, C = chol(Om^T Y_nu) (retrying with 10x nu up to 3 times), B = Y_nu C^{-1},
+// thin SVD of B via Jacobi on B^T B, U = B V Sigma^{-1}, lam = max(0, Sigma^2 - nu).
+nys_status nystrom_core(const double* Om, const double* Y, int64_t d, int s, double shift_scale, int mant_bits,
+                        double* U, double* lam_d, std::vector<double>& lam_h, double* nu_out, cudaStream_t st) {
+  Pool pool(st);
+  double* G = pool.alloc<double>((size_t)s * s);
+  double* gw = pool.alloc<double>(gram_work_bytes(d, s) / sizeof(double) + 1);
+  double* lmax = pool.alloc<double>(1);
+  double* pw = pool.alloc<double>(s);
+  double* Ynu = pool.alloc<double>((size_t)d * s);
+  double* M = pool.alloc<double>((size_t)s * s);
+  int* info = pool.alloc<int>(1);
+  const int N = s + (s & 1);
+  double* V = pool.alloc<double>((size_t)N * N);
+  double* jw = pool.alloc<double>(jacobi_work_bytes(s) / sizeof(double) + 1);
+  double* fw = pool.alloc<double>((size_t)s * s + s);
+  if (!pool.ok()) return NYS_ENOMEM;
+
+  NYS_CU(gram_xty(Y, Y, d, s, G, gw, st));
+  NYS_CU(power_lambda_max(G, s, lmax, pw, st));
+  double lmax_h = 0.0;
+  NYS_CU(cudaMemcpyAsync(&lmax_h, lmax, sizeof(double), cudaMemcpyDeviceToHost, st));
+  NYS_CU(cudaStreamSynchronize(st));
+  if (!is_fin(lmax_h)) return NYS_EINVAL;
+  double nu = shift_scale * eps_host(std::sqrt(std::max(lmax_h, 0.0)), mant_bits);
+  bool ok = false;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    NYS_CU(cudaMemcpyAsync(Ynu, Y, (size_t)d * s * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    NYS_CU(axpy_panel(nu, Om, Ynu, d * s, st));
+    NYS_CU(gram_xty(Om, Ynu, d, s, M, gw, st));
+    NYS_CU(chol_upper(M, s, info, st));
+    int info_h = 0;
+    NYS_CU(cudaMemcpyAsync(&info_h, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NYS_CU(cudaStreamSynchronize(st));
+    if (info_h == 0) {
+      ok = true;
+      break;
+    }
+    nu *= 10.0;
+  }
+  if (!ok) return NYS_ENOTSPD;
+  NYS_CU(trsm_right_upper(M, s, Ynu, d, st));       // B = Y_nu C^{-1} (in Ynu)
+  NYS_CU(gram_xty(Ynu, Ynu, d, s, G, gw, st));      // B^T B
+  int sweeps = 0;
+  NYS_CU(jacobi_eig(G, V, s, jw, &sweeps, st));
+  NYS_CU(nystrom_finish(Ynu, d, s, jw, V, nu, U, lam_d, fw, st));
+  lam_h.resize(s);
+  NYS_CU(cudaMemcpyAsync(lam_h.data(), lam_d, s * sizeof(double), cudaMemcpyDeviceToHost, st));
+  NYS_CU(cudaStreamSynchronize(st));
+  if (nu_out) *nu_out = nu;
+  return NYS_OK;
+}
+
+nys_status precond_alloc(nys_precond_s* P, int64_t d, int s) {
+  P->d = d;
+  P->s = s;
+  if (cudaMalloc(&P->U64, (size_t)d * s * sizeof(double)) != cudaSuccess) return NYS_ENOMEM;
+  if (cudaMalloc(&P->lam_d, (size_t)s * sizeof(double)) != cudaSuccess) return NYS_ENOMEM;
+  return NYS_OK;
+}
+
+void precond_free(nys_precond_s* P) {
+  if (!P) return;
+  if (P->U64) cudaFree(P->U64);
+  if (P->U32) cudaFree(P->U32);
+  if (P->lam_d) cudaFree(P->lam_d);
+  delete P;
+}
+
+// Device view of P^{-1} for one rho in the PCG compute type.
+template <typename C>
+nys_status precond_view(nys_precond_s* P, double rho, C* c, cudaStream_t st, PrecondView* out) {
+  out->s = 0;
+  out->U = nullptr;
+  out->c = nullptr;
+  if (!P || P->s == 0) return NYS_OK;
+  const int s = P->s;
+  std::vector<C> ch(s);
+  const double lam_s = P->lam[s - 1];
+  for (int i = 0; i < s; ++i) ch[i] = (C)((lam_s + rho) / (P->lam[i] + rho) - 1.0);
+  NYS_CU(cudaMemcpyAsync(c, ch.data(), s * sizeof(C), cudaMemcpyHostToDevice, st));
+  NYS_CU(cudaStreamSynchronize(st));  // ch goes out of scope
+  if constexpr (sizeof(C) == 8) {
+    out->U = P->U64;
+  } else {
+    if (!P->U32) {
+      if (cudaMalloc(&P->U32, (size_t)P->d * s * sizeof(float)) != cudaSuccess) return NYS_ENOMEM;
+      NYS_CU(convert_f64_to_f32(P->U64, P->U32, P->d * s, st));
+    }
+    out->U = P->U32;
+  }
+  out->c = c;
+  out->s = s;
+  return NYS_OK;
+}
+
+// Sketch of H = A^T diag(D) A + shift I with Omega blocks already orthonormalised:
+// the panels Om (d x s) and Y (d x s) are given; builds/refreshes P.
+nys_status precond_from_panels(const double* Om, const double* Y, int64_t d, int s, double shift_scale,
+                               int mant_bits, nys_precond_s* P, cudaStream_t st) {
+  if (P->s != s) {
+    if (P->U64) cudaFree(P->U64);
+    if (P->U32) cudaFree(P->U32);
+    if (P->lam_d) cudaFree(P->lam_d);
+    P->U64 = nullptr;
+    P->U32 = nullptr;
+    P->lam_d = nullptr;
+    NYS_TRY(precond_alloc(P, d, s));
+  } else if (P->U32) {
+    cudaFree(P->U32);
+    P->U32 = nullptr;
+  }
+  return nystrom_core(Om, Y, d, s, shift_scale, mant_bits, P->U64, P->lam_d, P->lam, &P->nu, st);
+}
+
+int mant_bits_of(const nys_matrix* A) { return A->dtype == NYS_F64 ? 52 : 23; }
+
+template <typename C>
+nys_status hmatvec_t(const nys_matrix* A, const double* D, double rho, const void* p, void* y, cudaStream_t st) {
+  ApassPlan plan;
+  apass_plan(A, &plan);
+  Pool pool(st);
+  void* part = pool.alloc<unsigned char>(apass_partial_bytes(A, plan));
+  int* dstat = pool.alloc<int>(1);
+  if (!pool.ok()) return NYS_ENOMEM;
+  NYS_CU(cudaMemsetAsync(dstat, 0, sizeof(int), st));
+  ApassArgs a;
+  a.A = A->data;
+  a.n = A->n;
+  a.d = A->d;
+  a.ld = A->ld;
+  a.dtype = A->dtype;
+  a.p = p;
+  a.D = D;
+  a.b = nullptr;
+  a.D_out = nullptr;
+  a.t_out = nullptr;
+  a.mode = D ? MODE_DIAG : MODE_ID;
+  NYS_CU(apass_run(a, plan, part, nullptr, dstat, st));
+  NYS_CU(apass_reduce(a, plan, part, rho, y, nullptr, 0, st));
+  int h = 0;
+  NYS_CU(cudaMemcpyAsync(&h, dstat, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NYS_CU(cudaStreamSynchronize(st));
+  return h ? (nys_status)h : NYS_OK;
+}
+
+// y = A^T phi(A p) for an ADMM helper pass (modes CONST / RESID / LOGIT / LGRAD), rho = 0.
+nys_status aux_pass(const nys_matrix* A, int mode, const void* p, const double* b, double* D_out, double* t_out,
+                    void* y, double* loss_h, cudaStream_t st) {
+  Pool pool(st);
+  ApassPlan plan;
+  apass_plan(A, &plan);
+  void* part = pool.alloc<unsigned char>(apass_partial_bytes(A, plan));
+  double* lp = pool.alloc<double>(plan.grid);
+  int* dstat = pool.alloc<int>(1);
+  if (!pool.ok()) return NYS_ENOMEM;
+  NYS_CU(cudaMemsetAsync(dstat, 0, sizeof(int), st));
+  NYS_CU(cudaMemsetAsync(lp, 0, plan.grid * sizeof(double), st));
+  ApassArgs a;
+  a.A = A->data;
+  a.n = A->n;
+  a.d = A->d;
+  a.ld = A->ld;
+  a.dtype = A->dtype;
+  a.p = p;
+  a.D = nullptr;
+  a.b = b;
+  a.D_out = D_out;
+  a.t_out = t_out;
+  a.mode = mode;
+  NYS_CU(apass_run(a, plan, part, lp, dstat, st));
+  ApassArgs ar = a;
+  ar.p = nullptr;
+  NYS_CU(apass_reduce(ar, plan, part, 0.0, y, nullptr, 0, st));
+  if (loss_h) {
+    std::vector<double> h(plan.grid);
+    NYS_CU(cudaMemcpyAsync(h.data(), lp, plan.grid * sizeof(double), cudaMemcpyDeviceToHost, st));
+    NYS_CU(cudaStreamSynchronize(st));
+    double s = 0.0;
+    for (double v : h) s += v;
+    *loss_h = s;
+  }
+  int hs = 0;
+  NYS_CU(cudaMemcpyAsync(&hs, dstat, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NYS_CU(cudaStreamSynchronize(st));
+  return hs ? (nys_status)hs : NYS_OK;
+}
+
+// Result of a pass in A's compute type -> FP64 vector.
+nys_status to_f64(const nys_matrix* A, const void* y, double* out, int64_t d, cudaStream_t st) {
+  if (A->dtype == NYS_F64) {
+    if (y != out) NYS_CU(cudaMemcpyAsync(out, y, d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return NYS_OK;
+  }
+  NYS_CU(convert_f32_to_f64(reinterpret_cast<const float*>(y), out, d, st));
+  return NYS_OK;
+}
+
+// ---------------------------------------------------------------- lasso NysADMM
+template <typename C>
+nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* b, double gamma, double rho,
+                      int rank, double tol, const double* Omega, const nys_opts& o, double* x_out, double* z_out,
+                      nys_info* info, cudaStream_t st) {
+  const int64_t d = A->d;
+  Pool pool(st);
+  const bool refine = o.refine && (Ain != A);
+  // Sketch on the PCG matrix (App. B; once for a quadratic loss, Thm. NysADMM convergence).
+  nys_precond_s P;
+  double* Om = pool.alloc<double>((size_t)d * rank);
+  double* Y = pool.alloc<double>((size_t)d * rank);
+  if (!pool.ok()) return NYS_ENOMEM;
+  NYS_CU(cudaMemcpyAsync(Om, Omega, (size_t)d * rank * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  NYS_TRY(cholqr2(Om, d, rank, st));
+  NYS_TRY(sketch_panel(Ain, nullptr, 0.0, Om, rank, Y, st));
+  const double shs = o.shift_scale > 0 ? o.shift_scale : std::sqrt((double)d);
+  nys_status ps = precond_from_panels(Om, Y, d, rank, shs, mant_bits_of(Ain), &P, st);
+  struct Guard {
+    nys_precond_s* p;
+    ~Guard() {
+      if (p->U64) cudaFree(p->U64);
+      if (p->U32) cudaFree(p->U32);
+      if (p->lam_d) cudaFree(p->lam_d);
+    }
+  } guard{&P};
+  if (ps != NYS_OK) return ps;
+  PrecondView view;
+  C* cbuf = pool.alloc<C>(rank);
+  if (!pool.ok()) return NYS_ENOMEM;
+  NYS_TRY(precond_view<C>(&P, rho, cbuf, st, &view));
+
+  double* x = pool.alloc<double>(d);
+  double* z = pool.alloc<double>(d);
+  double* u = pool.alloc<double>(d);
+  double* q = pool.alloc<double>(d);
+  double* yres = pool.alloc<double>(d);
+  C* xc = pool.alloc<C>(d);
+  C* rc = pool.alloc<C>(d);
+  void* ytmp = pool.alloc<unsigned char>(d * 8);
+  float* xA32 = pool.alloc<float>(d);
+  const int K = std::max(1, o.admm_maxit);
+  const int nb = admm_blocks(d);
+  double* part5 = pool.alloc<double>((size_t)nb * 5);
+  double* rp = pool.alloc<double>(K);
+  double* rd = pool.alloc<double>(K);
+  double* eps_next = pool.alloc<double>(1);
+  int* stop = pool.alloc<int>(1);
+  if (!pool.ok()) return NYS_ENOMEM;
+  NYS_CU(cudaMemsetAsync(x, 0, d * sizeof(double), st));
+  NYS_CU(cudaMemsetAsync(z, 0, d * sizeof(double), st));
+  NYS_CU(cudaMemsetAsync(u, 0, d * sizeof(double), st));
+  NYS_CU(cudaMemsetAsync(xc, 0, d * sizeof(C), st));
+  NYS_CU(cudaMemsetAsync(stop, 0, sizeof(int), st));
+
+  // q = A^T b
+  NYS_TRY(aux_pass(A, MODE_CONST, nullptr, b, nullptr, nullptr, ytmp, nullptr, st));
+  NYS_TRY(to_f64(A, ytmp, q, d, st));
+
+  PcgProblem pb;
+  pb.A = Ain;
+  pb.D = nullptr;
+  pb.rho = rho;
+  apass_plan(Ain, &pb.plan);
+  const int maxit = o.pcg_maxit > 0 ? o.pcg_maxit : (int)std::min<int64_t>(d, 1000);
+  int total_pcg = 0;
+  nys_status result = NYS_OK;
+  int k = 0;
+  for (; k < K; ++k) {
+    PcgParams prm;
+    prm.maxit = maxit;
+    prm.tol = tol;
+    prm.tol_abs = o.pcg_tol_mode == NYS_TOL_ABS;
+    if (o.pcg_tol_mode == NYS_TOL_SQRT_RPRD && k > 0) prm.dev_tol = eps_next;
+    if (o.pcg_fixed_iters) prm.fixed = o.pcg_fixed_iters[k];
+    if (refine) {
+      // exact residual of the x-subproblem at the current x with the FP64 problem matrix
+      const void* xa = x;
+      if (A->dtype != NYS_F64) {
+        NYS_CU(convert_f64_to_f32(x, xA32, d, st));
+        xa = xA32;
+      }
+      NYS_TRY(aux_pass(A, MODE_RESID, xa, b, nullptr, nullptr, ytmp, nullptr, st));
+      NYS_TRY(to_f64(A, ytmp, yres, d, st));
+      NYS_CU(admm_rhs<C>(d, q, z, u, rho, x, yres, rc, st));
+      NYS_CU(cudaMemsetAsync(xc, 0, d * sizeof(C), st));
+      prm.x0_zero = true;
+      if (sizeof(C) == 4 && !prm.tol_abs) prm.tol = std::max(prm.tol, 1e-6);
+    } else {
+      NYS_CU(admm_rhs<C>(d, q, z, u, rho, nullptr, nullptr, rc, st));
+      prm.x0_zero = (k == 0);
+    }
+    int it = 0;
+    nys_status s = pcg_run<C>(pb, view, rc, xc, prm, st, &it, nullptr);
+    total_pcg += it;
+    if (s == NYS_ENOCONV) {
+      result = NYS_ENOCONV;
+    } else if (s != NYS_OK) {
+      result = s;
+      break;
+    }
+    double* zt = o.z_trace ? o.z_trace + (int64_t)k * d : nullptr;
+    NYS_CU(admm_zu<C>(d, xc, refine ? 1 : 0, x, z, u, gamma / rho, zt, part5, st));
+    NYS_CU(admm_scalar(d, part5, rho, k, rp, rd, eps_next, o.eps_abs, o.eps_rel, stop, st));
+    if (o.eps_rel > 0) {
+      int stop_h = 0;
+      NYS_CU(cudaMemcpyAsync(&stop_h, stop, sizeof(int), cudaMemcpyDeviceToHost, st));
+      NYS_CU(cudaStreamSynchronize(st));
+      if (stop_h) {
+        ++k;
+        break;
+      }
+    }
+  }
+  const int done_k = std::min(k, K);
+  if (x_out) NYS_CU(cudaMemcpyAsync(x_out, x, d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (z_out) NYS_CU(cudaMemcpyAsync(z_out, z, d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (info) {
+    info->admm_iters = done_k;
+    info->pcg_iters_total = total_pcg;
+    info->final_rank = rank;
+    info->status = result;
+    info->nu = P.nu;
+    info->emp_cond = P.lam.empty() ? 1.0 : (P.lam.back() + rho) / rho;
+    if (done_k > 0) {
+      NYS_CU(cudaMemcpyAsync(&info->r_p, rp + done_k - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+      NYS_CU(cudaMemcpyAsync(&info->r_d, rd + done_k - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+  }
+  NYS_CU(cudaStreamSynchronize(st));
+  return result;
+}
+
+// ---------------------------------------------------------------- logistic (Sec. 3.2) + AdaRandNysAppx (App. C)
+template <typename C>
+nys_status logistic_admm(const nys_matrix* A, const nys_matrix* Ain, const double* b, double gamma, double rho,
+                         int rank, double tol, const double* Omega, const nys_opts& o, double* x_out,
+                         double* z_out, nys_info* info, cudaStream_t st) {
+  const int64_t d = A->d, n = A->n;
+  const int smax = o.rank_max > 0 ? std::max(o.rank_max, rank) : rank;
+  const double ada_tol = o.ada_tol > 0 ? o.ada_tol : 2.0;
+  const double shs = o.shift_scale > 0 ? o.shift_scale : std::sqrt((double)d);
+  Pool pool(st);
+  double* Om = pool.alloc<double>((size_t)d * smax);
+  double* Y = pool.alloc<double>((size_t)d * smax);
+  double* Dw = pool.alloc<double>(n);
+  C* cbuf = pool.alloc<C>(smax);
+  double* x = pool.alloc<double>(d);
+  double* z = pool.alloc<double>(d);
+  double* u = pool.alloc<double>(d);
+  double* q = pool.alloc<double>(d);
+  C* xc = pool.alloc<C>(d);
+  C* rc = pool.alloc<C>(d);
+  void* ytmp = pool.alloc<unsigned char>(d * 8);
+  float* xA32 = pool.alloc<float>(d);
+  const int K = std::max(1, o.admm_maxit);
+  const int nb = admm_blocks(d);
+  double* part5 = pool.alloc<double>((size_t)nb * 5);
+  double* rp = pool.alloc<double>(K);
+  double* rd = pool.alloc<double>(K);
+  double* eps_next = pool.alloc<double>(1);
+  int* stop = pool.alloc<int>(1);
+  if (!pool.ok()) return NYS_ENOMEM;
+  NYS_CU(cudaMemcpyAsync(Om, Omega, (size_t)d * smax * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  NYS_CU(cudaMemsetAsync(x, 0, d * sizeof(double), st));
+  NYS_CU(cudaMemsetAsync(z, 0, d * sizeof(double), st));
+  NYS_CU(cudaMemsetAsync(u, 0, d * sizeof(double), st));
+  NYS_CU(cudaMemsetAsync(xc, 0, d * sizeof(C), st));
+  NYS_CU(cudaMemsetAsync(stop, 0, sizeof(int), st));
+
+  nys_precond_s P;
+  struct Guard {
+    nys_precond_s* p;
+    ~Guard() {
+      if (p->U64) cudaFree(p->U64);
+      if (p->U32) cudaFree(p->U32);
+      if (p->lam_d) cudaFree(p->lam_d);
+    }
+  } guard{&P};
+
+  PcgProblem pb;
+  pb.A = Ain;
+  pb.D = Dw;
+  pb.rho = rho;
+  apass_plan(Ain, &pb.plan);
+  const int maxit = o.pcg_maxit > 0 ? o.pcg_maxit : (int)std::min<int64_t>(d, 1000);
+  int total_pcg = 0, cur_rank = 0;
+  nys_status result = NYS_OK;
+  std::vector<int> block_end;  // orthonormalised block boundaries
+  int k = 0;
+  for (; k < K; ++k) {
+    // t = A x~, w, and the right-hand side A^T (w t + b01 - sigma(t)) in one pass (Sec. 3.2)
+    const void* xa = x;
+    if (A->dtype != NYS_F64) {
+      NYS_CU(convert_f64_to_f32(x, xA32, d, st));
+      xa = xA32;
+    }
+    NYS_TRY(aux_pass(A, MODE_LOGIT, xa, b, Dw, nullptr, ytmp, nullptr, st));
+    NYS_TRY(to_f64(A, ytmp, q, d, st));
+    if (k == 0) {
+      // Alg. AdaptiveRandNysAppx: ranks s0, 2 s0, 4 s0, ... until (lam_s + rho)/rho <= Tol,
+      // extended once to s_max when doubling would pass it.
+      int s0 = rank, m = rank, used = 0;
+      for (;;) {
+        NYS_TRY(cholqr2(Om + (int64_t)used * d, d, m, st));
+        NYS_TRY(sketch_panel(Ain, Dw, 0.0, Om + (int64_t)used * d, m, Y + (int64_t)used * d, st));
+        used += m;
+        block_end.push_back(used);
+        NYS_TRY(precond_from_panels(Om, Y, d, used, shs, mant_bits_of(Ain), &P, st));
+        if ((P.lam.back() + rho) / rho <= ada_tol) break;
+        m = s0;
+        s0 = 2 * s0;
+        if (s0 > smax) {
+          s0 = s0 - m;
+          m = smax - s0;
+          if (m > 0) {
+            NYS_TRY(cholqr2(Om + (int64_t)used * d, d, m, st));
+            NYS_TRY(sketch_panel(Ain, Dw, 0.0, Om + (int64_t)used * d, m, Y + (int64_t)used * d, st));
+            used += m;
+            block_end.push_back(used);
+            NYS_TRY(precond_from_panels(Om, Y, d, used, shs, mant_bits_of(Ain), &P, st));
+          }
+          break;
+        }
+      }
+      cur_rank = used;
+    } else if (o.resketch_every > 0 && k % o.resketch_every == 0) {
+      // same orthonormal blocks, new curvature D
+      NYS_TRY(sketch_panel(Ain, Dw, 0.0, Om, cur_rank, Y, st));
+      NYS_TRY(precond_from_panels(Om, Y, d, cur_rank, shs, mant_bits_of(Ain), &P, st));
+    }
+    PrecondView view;
+    NYS_TRY(precond_view<C>(&P, rho, cbuf, st, &view));
+    NYS_CU(admm_rhs<C>(d, q, z, u, rho, nullptr, nullptr, rc, st));
+    PcgParams prm;
+    prm.maxit = maxit;
+    prm.tol = tol;
+    prm.tol_abs = o.pcg_tol_mode == NYS_TOL_ABS;
+    if (o.pcg_tol_mode == NYS_TOL_SQRT_RPRD && k > 0) prm.dev_tol = eps_next;
+    if (o.pcg_fixed_iters) prm.fixed = o.pcg_fixed_iters[k];
+    prm.x0_zero = (k == 0);
+    int it = 0;
+    nys_status s = pcg_run<C>(pb, view, rc, xc, prm, st, &it, nullptr);
+    total_pcg += it;
+    if (s == NYS_ENOCONV) {
+      result = NYS_ENOCONV;
+    } else if (s != NYS_OK) {
+      result = s;
+      break;
+    }
+    double* zt = o.z_trace ? o.z_trace + (int64_t)k * d : nullptr;
+    NYS_CU(admm_zu<C>(d, xc, 0, x, z, u, gamma / rho, zt, part5, st));
+    NYS_CU(admm_scalar(d, part5, rho, k, rp, rd, eps_next, o.eps_abs, o.eps_rel, stop, st));
+    if (o.eps_rel > 0) {
+      int stop_h = 0;
+      NYS_CU(cudaMemcpyAsync(&stop_h, stop, sizeof(int), cudaMemcpyDeviceToHost, st));
+      NYS_CU(cudaStreamSynchronize(st));
+      if (stop_h) {
+        ++k;
+        break;
+      }
+    }
+  }
+  const int done_k = std::min(k, K);
+  if (x_out) NYS_CU(cudaMemcpyAsync(x_out, x, d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (z_out) NYS_CU(cudaMemcpyAsync(z_out, z, d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (info) {
+    info->admm_iters = done_k;
+    info->pcg_iters_total = total_pcg;
+    info->final_rank = cur_rank;
+    info->status = result;
+    info->nu = P.nu;
+    info->emp_cond = P.lam.empty() ? 1.0 : (P.lam.back() + rho) / rho;
+    if (done_k > 0) {
+      NYS_CU(cudaMemcpyAsync(&info->r_p, rp + done_k - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+      NYS_CU(cudaMemcpyAsync(&info->r_d, rd + done_k - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+  }
+  NYS_CU(cudaStreamSynchronize(st));
+  return result;
+}
+
+// ---------------------------------------------------------------- objective helpers
+__global__ void obj_vec_kernel(int64_t d, const double* __restrict__ x, const double* __restrict__ g, double gamma,
+                               double* part4) {
+  __shared__ double sh[kVecThreads / 32];
+  double l1 = 0, l2 = 0, kk = 0, gm = 0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x) {
+    const double xj = x[j], gj = g[j];
+    l1 += fabs(xj);
+    l2 += xj * xj;
+    const double v = xj - gj;
+    const double mag = fabs(v) - gamma;
+    const double pj = mag > 0 ? copysign(mag, v) : 0.0;
+    kk += (xj - pj) * (xj - pj);
+    gm = fmax(gm, fabs(gj));
+  }
+  l1 = block_sum<kVecThreads>(l1, sh);
+  l2 = block_sum<kVecThreads>(l2, sh);
+  kk = block_sum<kVecThreads>(kk, sh);
+  for (int o = 16; o > 0; o >>= 1) gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+  __shared__ double mx[kVecThreads / 32];
+  if ((threadIdx.x & 31) == 0) mx[threadIdx.x >> 5] = gm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0;
+    for (int i = 0; i < kVecThreads / 32; ++i) m = fmax(m, mx[i]);
+    double* o = part4 + (int64_t)blockIdx.x * 4;
+    o[0] = l1;
+    o[1] = l2;
+    o[2] = kk;
+    o[3] = m;
+  }
+}
+
+__global__ void obj_row_kernel(int64_t n, const double* __restrict__ t, const double* __restrict__ b, double* part2) {
+  __shared__ double sh[kVecThreads / 32];
+  double bres = 0, bb = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    bres += b[i] * (t[i] - b[i]);
+    bb += b[i] * b[i];
+  }
+  bres = block_sum<kVecThreads>(bres, sh);
+  bb = block_sum<kVecThreads>(bb, sh);
+  if (threadIdx.x == 0) {
+    part2[2 * blockIdx.x] = bres;
+    part2[2 * blockIdx.x + 1] = bb;
+  }
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" {
+
+void nys_opts_default(nys_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->shift_scale = 0.0;
+  o->pcg_tol_mode = NYS_TOL_REL;
+  o->pcg_maxit = 0;
+  o->pcg_fixed_iters = nullptr;
+  o->admm_maxit = 200;
+  o->eps_abs = 0.0;
+  o->eps_rel = 0.0;
+  o->A_inner = nullptr;
+  o->refine = 1;
+  o->z_trace = nullptr;
+  o->rank_max = 0;
+  o->ada_tol = 2.0;
+  o->resketch_every = 1;
+  o->stream = nullptr;
+}
+
+const char* nys_strerror(int32_t s) {
+  switch (s) {
+    case NYS_OK: return "ok";
+    case NYS_EINVAL: return "invalid argument";
+    case NYS_ENOTSPD: return "Nystrom core matrix not positive definite after shift retries";
+    case NYS_EBREAKDOWN: return "PCG breakdown (p^T (H + rho I) p <= 0 or not finite)";
+    case NYS_ENOCONV: return "iteration cap reached before the tolerance";
+    case NYS_ETIMEOUT: return "device-side wait exceeded its bound";
+    case NYS_ECUDA: return "CUDA runtime error";
+    case NYS_ENOMEM: return "device memory allocation failed";
+    default: return "unknown status";
+  }
+}
+
+nys_status nys_hmatvec(const nys_matrix* A, const double* D, double rho, const void* p, void* y, void* stream) {
+  NYS_TRY(check_matrix(A));
+  if (!p || !y || p == y || !is_fin(rho)) return NYS_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return A->dtype == NYS_F64 ? hmatvec_t<double>(A, D, rho, p, y, st) : hmatvec_t<float>(A, D, rho, p, y, st);
+}
+
+nys_status nys_sketch(const nys_matrix* A, const double* D, double diag_shift, int32_t s, const double* Omega,
+                      const nys_opts* opts, nys_precond* out) {
+  if (!out) return NYS_EINVAL;
+  *out = nullptr;
+  NYS_TRY(check_matrix(A));
+  if (!Omega || s < 1 || s > A->d || s > kMaxRank || !is_fin(diag_shift) || diag_shift < 0) return NYS_EINVAL;
+  cudaStream_t st = stream_of(opts);
+  const int64_t d = A->d;
+  nys_precond_s* P = new (std::nothrow) nys_precond_s();
+  if (!P) return NYS_ENOMEM;
+  nys_status r;
+  {
+    Pool pool(st);
+    double* Om = pool.alloc<double>((size_t)d * s);
+    double* Y = pool.alloc<double>((size_t)d * s);
+    if (!pool.ok()) {
+      precond_free(P);
+      return NYS_ENOMEM;
+    }
+    r = cuda_status(cudaMemcpyAsync(Om, Omega, (size_t)d * s * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (r == NYS_OK) r = cholqr2(Om, d, s, st);
+    if (r == NYS_OK) r = sketch_panel(A, D, diag_shift, Om, s, Y, st);
+    const double shs = (opts && opts->shift_scale > 0) ? opts->shift_scale : std::sqrt((double)d);
+    if (r == NYS_OK) r = precond_from_panels(Om, Y, d, s, shs, mant_bits_of(A), P, st);
+    cudaStreamSynchronize(st);
+  }
+  if (r != NYS_OK) {
+    precond_free(P);
+    return r;
+  }
+  *out = P;
+  return NYS_OK;
+}
+
+nys_status nys_precond_get(nys_precond P, double* U_out, double* lam_out, int32_t* s_out, int64_t* d_out,
+                           double* nu_out, void* stream) {
+  if (!P) return NYS_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (U_out)
+    NYS_CU(cudaMemcpyAsync(U_out, P->U64, (size_t)P->d * P->s * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (lam_out) std::memcpy(lam_out, P->lam.data(), P->s * sizeof(double));
+  if (s_out) *s_out = P->s;
+  if (d_out) *d_out = P->d;
+  if (nu_out) *nu_out = P->nu;
+  NYS_CU(cudaStreamSynchronize(st));
+  return NYS_OK;
+}
+
+nys_status nys_precond_apply(nys_precond P, double rho, const void* V, void* Yv, int64_t k, int32_t dtype,
+                             void* stream) {
+  if (!P || !V || !Yv || k < 1 || !(rho > 0) || !is_fin(rho)) return NYS_EINVAL;
+  if (dtype != NYS_F64 && dtype != NYS_F32) return NYS_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Pool pool(st);
+  void* cbuf = pool.alloc<double>(P->s);
+  if (!pool.ok()) return NYS_ENOMEM;
+  PrecondView view;
+  if (dtype == NYS_F64) {
+    NYS_TRY(precond_view<double>(P, rho, (double*)cbuf, st, &view));
+    return precond_apply_run<double>(view, P->d, (const double*)V, (double*)Yv, k, st);
+  }
+  NYS_TRY(precond_view<float>(P, rho, (float*)cbuf, st, &view));
+  return precond_apply_run<float>(view, P->d, (const float*)V, (float*)Yv, k, st);
+}
+
+nys_status pcg_solve(const nys_matrix* A, const double* D, double rho, nys_precond P, const void* r, void* x,
+                     double tol, const nys_opts* opts, int32_t* iters, double* resnorm) {
+  NYS_TRY(check_matrix(A));
+  if (!r || !x || !(rho > 0) || !is_fin(rho) || !(tol >= 0) || !is_fin(tol)) return NYS_EINVAL;
+  if (P && P->d != A->d) return NYS_EINVAL;
+  nys_opts o;
+  if (opts) o = *opts;
+  else nys_opts_default(&o);
+  cudaStream_t st = stream_of(&o);
+  PcgProblem pb;
+  pb.A = A;
+  pb.D = D;
+  pb.rho = rho;
+  apass_plan(A, &pb.plan);
+  PcgParams prm;
+  prm.tol = tol;
+  prm.tol_abs = o.pcg_tol_mode == NYS_TOL_ABS;
+  prm.maxit = o.pcg_maxit > 0 ? o.pcg_maxit : (int)std::min<int64_t>(A->d, 1000);
+  if (o.pcg_fixed_iters) prm.fixed = o.pcg_fixed_iters[0];
+  Pool pool(st);
+  void* cbuf = pool.alloc<double>(P ? P->s : 1);
+  if (!pool.ok()) return NYS_ENOMEM;
+  PrecondView view;
+  int it = 0;
+  nys_status s;
+  if (A->dtype == NYS_F64) {
+    NYS_TRY(precond_view<double>(P, rho, (double*)cbuf, st, &view));
+    s = pcg_run<double>(pb, view, (const double*)r, (double*)x, prm, st, &it, resnorm);
+  } else {
+    NYS_TRY(precond_view<float>(P, rho, (float*)cbuf, st, &view));
+    s = pcg_run<float>(pb, view, (const float*)r, (float*)x, prm, st, &it, resnorm);
+  }
+  if (iters) *iters = it;
+  return s;
+}
+
+nys_status nysadmm_solve(int32_t loss, const nys_matrix* A, const double* b, double gamma, double rho, int32_t rank,
+                         double tol, const double* Omega, const nys_opts* opts, double* x_out, double* z_out,
+                         nys_info* info) {
+  NYS_TRY(check_matrix(A));
+  if (loss != NYS_LASSO && loss != NYS_LOGISTIC) return NYS_EINVAL;
+  if (!b || !Omega || !(gamma >= 0) || !is_fin(gamma) || !(rho > 0) || !is_fin(rho)) return NYS_EINVAL;
+  if (rank < 1 || rank > A->d || rank > kMaxRank || !(tol >= 0) || !is_fin(tol)) return NYS_EINVAL;
+  nys_opts o;
+  if (opts) o = *opts;
+  else nys_opts_default(&o);
+  if (o.admm_maxit < 1) return NYS_EINVAL;
+  if (o.rank_max > A->d || o.rank_max > kMaxRank) return NYS_EINVAL;
+  const nys_matrix* Ain = o.A_inner ? o.A_inner : A;
+  if (o.A_inner) {
+    NYS_TRY(check_matrix(Ain));
+    if (Ain->n != A->n || Ain->d != A->d) return NYS_EINVAL;
+  }
+  cudaStream_t st = stream_of(&o);
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (loss == NYS_LASSO) {
+    return Ain->dtype == NYS_F64 ? lasso_admm<double>(A, Ain, b, gamma, rho, rank, tol, Omega, o, x_out, z_out, info, st)
+                                 : lasso_admm<float>(A, Ain, b, gamma, rho, rank, tol, Omega, o, x_out, z_out, info, st);
+  }
+  return Ain->dtype == NYS_F64 ? logistic_admm<double>(A, Ain, b, gamma, rho, rank, tol, Omega, o, x_out, z_out, info, st)
+                               : logistic_admm<float>(A, Ain, b, gamma, rho, rank, tol, Omega, o, x_out, z_out, info, st);
+}
+
+nys_status nys_objective(int32_t loss, const nys_matrix* A, const double* b, double gamma, const double* x,
+                         double* out, void* stream) {
+  NYS_TRY(check_matrix(A));
+  if (!b || !x || !out || !(gamma >= 0) || !is_fin(gamma)) return NYS_EINVAL;
+  if (loss != NYS_LASSO && loss != NYS_LOGISTIC) return NYS_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t d = A->d, n = A->n;
+  Pool pool(st);
+  double* g = pool.alloc<double>(d);
+  double* t = pool.alloc<double>(n);
+  void* ytmp = pool.alloc<unsigned char>(d * 8);
+  const int nbd = reduce_blocks(d), nbn = reduce_blocks(n);
+  double* p4 = pool.alloc<double>((size_t)nbd * 4);
+  double* p2 = pool.alloc<double>((size_t)nbn * 2);
+  if (!pool.ok()) return NYS_ENOMEM;
+  float* x32 = pool.alloc<float>(d);
+  if (!pool.ok()) return NYS_ENOMEM;
+  const void* xa = x;
+  if (A->dtype != NYS_F64) {
+    NYS_CU(convert_f64_to_f32(x, x32, d, st));
+    xa = x32;
+  }
+  double lossv = 0.0;
+  NYS_TRY(aux_pass(A, loss == NYS_LASSO ? MODE_RESID : MODE_LGRAD, xa, b, nullptr, t, ytmp, &lossv, st));
+  NYS_TRY(to_f64(A, ytmp, g, d, st));
+  obj_vec_kernel<<<nbd, kVecThreads, 0, st>>>(d, x, g, gamma, p4);
+  NYS_CU(cudaGetLastError());
+  obj_row_kernel<<<nbn, kVecThreads, 0, st>>>(n, t, b, p2);
+  NYS_CU(cudaGetLastError());
+  std::vector<double> h4((size_t)nbd * 4), h2((size_t)nbn * 2);
+  NYS_CU(cudaMemcpyAsync(h4.data(), p4, h4.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  NYS_CU(cudaMemcpyAsync(h2.data(), p2, h2.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  NYS_CU(cudaStreamSynchronize(st));
+  double l1 = 0, l2 = 0, kk = 0, gm = 0, bres = 0, bb = 0;
+  for (int i = 0; i < nbd; ++i) {
+    l1 += h4[4 * i];
+    l2 += h4[4 * i + 1];
+    kk += h4[4 * i + 2];
+    gm = std::max(gm, h4[4 * i + 3]);
+  }
+  for (int i = 0; i < nbn; ++i) {
+    bres += h2[2 * i];
+    bb += h2[2 * i + 1];
+  }
+  const double F = lossv + gamma * l1;
+  out[0] = F;
+  if (loss == NYS_LASSO) {
+    const double res2 = 2.0 * lossv;
+    out[1] = std::sqrt(kk) / (1.0 + std::sqrt(l2) + std::sqrt(res2));
+    const double c = gm > gamma ? gamma / gm : 1.0;
+    const double dual = -c * bres - 0.5 * c * c * res2;
+    out[2] = F - dual;
+  } else {
+    out[1] = gm;
+    out[2] = 0.0;
+  }
+  return NYS_OK;
+}
+
+void nys_precond_destroy(nys_precond P) { precond_free(P); }
+
+}  // extern "C"

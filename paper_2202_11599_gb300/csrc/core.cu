@@ -1,0 +1,660 @@
+// Sketch GEMMs and the FP64 Nystrom core (App. B, Alg. Randomized Nystrom
+// Approximation): Y = A^T D (A Omega), the shift nu = shift_scale * eps(||Y||_2),
+// C = chol(Omega^T Y_nu), B = Y_nu C^{-1}, the thin SVD of B through the
+// symmetric eigendecomposition of B^T B (parallel cyclic Jacobi), U = B V Sigma^{-1}
+// and lam = max(0, Sigma^2 - nu).  Also CholQR2 for the thin QR of Omega.
+//
+// All s x s work is FP64.  GEMM reductions are split into fixed chunks whose
+// partials are summed in a fixed order, so every result is run-to-run
+// deterministic.
+#include "device_util.cuh"
+#include "nys_internal.cuh"
+
+#include <algorithm>
+#include <vector>
+
+namespace nys {
+
+// ------------------------------------------------------------------ generic small GEMM
+// C(m, n) = sum_k a(m, k) b(k, n), FP64, column-major operands:
+//   transA: a(m,k) = A[k + m*lda]   else a(m,k) = A[m + k*lda];   b(k,n) = B[k + n*ldb]
+// Split-K: blockIdx.z handles k in [z*kchunk, min(K,(z+1)*kchunk)); the partial goes to
+// Cp + z*M*N (column-major, ld M).  Tile 64 x 64, 256 threads, 4 x 4 per thread.
+constexpr int GT = 64, GK = 16;
+
+__global__ void __launch_bounds__(256) gemm_f64_kernel(const double* __restrict__ A, int64_t lda, bool transA,
+                                                       const double* __restrict__ B, int64_t ldb, int M, int N,
+                                                       int64_t K, int64_t kchunk, double* __restrict__ Cp) {
+  __shared__ double As[GK][GT + 1];
+  __shared__ double Bs[GK][GT + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int m0 = blockIdx.x * GT, n0 = blockIdx.y * GT;
+  const int64_t kb = (int64_t)blockIdx.z * kchunk;
+  const int64_t ke = min(K, kb + kchunk);
+  double acc[4][4] = {};
+  for (int64_t k0 = kb; k0 < ke; k0 += GK) {
+    for (int idx = threadIdx.x; idx < GK * GT; idx += 256) {
+      int kk, mm;
+      if (transA) {
+        kk = idx % GK;
+        mm = idx / GK;
+      } else {
+        mm = idx % GT;
+        kk = idx / GT;
+      }
+      const int64_t k = k0 + kk;
+      const int m = m0 + mm;
+      double v = 0.0;
+      if (k < ke && m < M) v = transA ? A[k + (int64_t)m * lda] : A[m + k * lda];
+      As[kk][mm] = v;
+      const int nn = idx / GK, kk2 = idx % GK;
+      const int64_t k2 = k0 + kk2;
+      const int n = n0 + nn;
+      Bs[kk2][nn] = (k2 < ke && n < N) ? B[k2 + (int64_t)n * ldb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* C = Cp + (int64_t)blockIdx.z * M * N;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int m = m0 + tx + 16 * i, n = n0 + ty + 16 * j;
+      if (m < M && n < N) C[m + (int64_t)n * M] = acc[i][j];
+    }
+}
+
+// C = alpha * sum_z Cp[z] (fixed order)
+__global__ void sum_partials_kernel(const double* __restrict__ Cp, int nz, int64_t len, double* __restrict__ C) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < nz; ++z) s += Cp[z * len + i];
+    C[i] = s;
+  }
+}
+
+static int64_t gram_kchunk(int64_t K) { return std::max<int64_t>(256, ((K + 63) / 64 + GK - 1) / GK * GK); }
+
+size_t gram_work_bytes(int64_t d, int s) {
+  const int64_t kc = gram_kchunk(d);
+  const int64_t nz = (d + kc - 1) / kc;
+  return (size_t)nz * s * s * sizeof(double);
+}
+
+// C (s x s) = X^T Y, X and Y d x s column-major (ld d)
+cudaError_t gram_xty(const double* X, const double* Y, int64_t d, int s, double* C, double* work,
+                     cudaStream_t st) {
+  const int64_t kc = gram_kchunk(d);
+  const int nz = (int)((d + kc - 1) / kc);
+  dim3 grid((s + GT - 1) / GT, (s + GT - 1) / GT, nz);
+  gemm_f64_kernel<<<grid, 256, 0, st>>>(X, d, true, Y, d, s, s, d, kc, work);
+  NYS_CUDA_TRY(cudaGetLastError());
+  sum_partials_kernel<<<std::min<int64_t>(1024, ((int64_t)s * s + 255) / 256), 256, 0, st>>>(work, nz,
+                                                                                              (int64_t)s * s, C);
+  return cudaGetLastError();
+}
+
+// C (d x s) = B (d x s) * V (s x s), all column-major
+static cudaError_t gemm_nn(const double* B, int64_t d, int s, const double* V, double* C, cudaStream_t st) {
+  dim3 grid((unsigned)((d + GT - 1) / GT), (s + GT - 1) / GT, 1);
+  gemm_f64_kernel<<<grid, 256, 0, st>>>(B, d, false, V, s, (int)d, s, s, s, C);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Cholesky (upper, in place)
+// Single CTA.  M (s x s, column-major) is symmetrised, then overwritten by the upper
+// factor C (C^T C = M); the strict lower triangle is zeroed.  info = 0 or k+1 when
+// the k-th pivot is not positive / not finite.
+__global__ void __launch_bounds__(1024) chol_upper_kernel(double* M, int s, int* info) {
+  const int tid = threadIdx.x, T = blockDim.x;
+  __shared__ int bad;
+  for (int64_t idx = tid; idx < (int64_t)s * s; idx += T) {
+    const int i = (int)(idx % s), j = (int)(idx / s);
+    if (i < j) {
+      const double v = 0.5 * (M[i + (int64_t)j * s] + M[j + (int64_t)i * s]);
+      M[i + (int64_t)j * s] = v;
+    }
+  }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < s; ++j) {
+    if (tid == 0) {
+      const double dj = M[j + (int64_t)j * s];
+      if (!(dj > 0.0) || !isfinite(dj)) {
+        bad = j + 1;
+      } else {
+        M[j + (int64_t)j * s] = sqrt(dj);
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const double piv = M[j + (int64_t)j * s];
+    for (int c = j + 1 + tid; c < s; c += T) M[j + (int64_t)c * s] /= piv;
+    __syncthreads();
+    // trailing update of the upper triangle: M[i][c] -= C[j][i] C[j][c], j < i <= c
+    const int w = s - j - 1;
+    for (int64_t idx = tid; idx < (int64_t)w * w; idx += T) {
+      const int i = (int)(idx % w), c = (int)(idx / w);
+      if (i > c) continue;
+      const int ii = j + 1 + i, cc = j + 1 + c;
+      M[ii + (int64_t)cc * s] -= M[j + (int64_t)ii * s] * M[j + (int64_t)cc * s];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) *info = bad;
+  // zero the strict lower triangle
+  for (int64_t idx = tid; idx < (int64_t)s * s; idx += T) {
+    const int i = (int)(idx % s), j = (int)(idx / s);
+    if (i > j) M[idx] = 0.0;
+  }
+}
+
+cudaError_t chol_upper(double* M, int s, int* info, cudaStream_t st) {
+  chol_upper_kernel<<<1, 1024, 0, st>>>(M, s, info);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ triangular solve B C = Y
+// One thread per row j of Y (d x s, column-major): b_c = (y_c - sum_{k<c} b_k C[k][c]) / C[c][c].
+__global__ void trsm_ru_kernel(const double* __restrict__ Cm, int s, double* Y, int64_t d) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= d) return;
+  for (int c = 0; c < s; ++c) {
+    double acc = Y[j + (int64_t)c * d];
+    const double* col = Cm + (int64_t)c * s;
+    for (int k = 0; k < c; ++k) acc = fma(-Y[j + (int64_t)k * d], col[k], acc);
+    Y[j + (int64_t)c * d] = acc / col[c];
+  }
+}
+
+cudaError_t trsm_right_upper(const double* C, int s, double* Y, int64_t d, cudaStream_t st) {
+  trsm_ru_kernel<<<(unsigned)((d + 127) / 128), 128, 0, st>>>(C, s, Y, d);
+  return cudaGetLastError();
+}
+
+__global__ void axpy_kernel(double a, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], y[i]);
+}
+
+cudaError_t axpy_panel(double nu, const double* X, double* Y, int64_t n, cudaStream_t st) {
+  axpy_kernel<<<(unsigned)std::min<int64_t>(4096, (n + 255) / 256), 256, 0, st>>>(nu, X, Y, n);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ power iteration (lambda_max)
+__global__ void __launch_bounds__(512) power_kernel(const double* __restrict__ G, int s, int iters,
+                                                    double* out, double* v) {
+  __shared__ double sh[16];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < s; i += 512) v[i] = 1.0 + 1e-3 * (double)(i % 7);  // deterministic start
+  __syncthreads();
+  double lam = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    // w = G v (row i: sum_k G[i + k s] v_k), normalised
+    double loc = 0.0;
+    double wi[2] = {0.0, 0.0};
+    for (int r = 0; r < 2; ++r) {
+      const int i = tid + r * 512;
+      if (i < s) {
+        double acc = 0.0;
+        for (int k = 0; k < s; ++k) acc = fma(G[i + (int64_t)k * s], v[k], acc);
+        wi[r] = acc;
+      }
+    }
+    // Rayleigh quotient numerator v^T G v and ||w||^2
+    for (int r = 0; r < 2; ++r) {
+      const int i = tid + r * 512;
+      if (i < s) loc += v[i] * wi[r];
+    }
+    const double num = block_sum<512>(loc, sh);
+    double l2 = 0.0;
+    for (int r = 0; r < 2; ++r) l2 += wi[r] * wi[r];
+    const double nw2 = block_sum<512>(l2, sh);
+    double vv = 0.0;
+    for (int r = 0; r < 2; ++r) {
+      const int i = tid + r * 512;
+      if (i < s) vv += v[i] * v[i];
+    }
+    const double nv2 = block_sum<512>(vv, sh);
+    lam = num / nv2;
+    __syncthreads();
+    const double inv = nw2 > 0 ? 1.0 / sqrt(nw2) : 0.0;
+    for (int r = 0; r < 2; ++r) {
+      const int i = tid + r * 512;
+      if (i < s) v[i] = wi[r] * inv;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) *out = lam;
+}
+
+cudaError_t power_lambda_max(const double* G, int s, double* out, double* work, cudaStream_t st) {
+  if (s > 1024) return cudaErrorInvalidValue;
+  power_kernel<<<1, 512, 0, st>>>(G, s, 60, out, work);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ parallel cyclic Jacobi
+// Round-robin ("circle") pairing of N = even size: round r in [0, N-1):
+//   pair 0 = (N-1, r);  pair m >= 1 = ((r+m) mod (N-1), (r-m+N-1) mod (N-1)).
+__device__ __forceinline__ void rr_pair(int N, int r, int m, int& p, int& q) {
+  if (m == 0) {
+    p = N - 1;
+    q = r;
+  } else {
+    p = (r + m) % (N - 1);
+    q = (r - m + (N - 1)) % (N - 1);
+  }
+}
+
+// Rotation (c, sn) that zeroes a_pq of the 2x2 block [[app, apq], [apq, aqq]] under
+// J^T A J with J_pp = J_qq = c, J_pq = sn, J_qp = -sn (Golub & Van Loan, Alg. 8.4.1).
+__device__ __forceinline__ void jacobi_rot(double app, double aqq, double apq, double& c, double& sn) {
+  if (apq == 0.0 || fabs(apq) <= 1e-300 || fabs(apq) < 1e-17 * sqrt(fabs(app * aqq))) {
+    c = 1.0;
+    sn = 0.0;
+    return;
+  }
+  const double tau = (aqq - app) / (2.0 * apq);
+  const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+  c = 1.0 / sqrt(1.0 + t * t);
+  sn = t * c;
+}
+
+// One round: Aout = J^T Ain J and V <- V J for the round's N/2 disjoint rotations.
+__global__ void jacobi_round_kernel(const double* __restrict__ Ain, double* __restrict__ Aout, double* V,
+                                    int N, int r, const int* __restrict__ done) {
+  if (*done) return;
+  const int H = N / 2;
+  const int64_t nA = (int64_t)H * H;
+  const int64_t total = nA + (int64_t)N * H;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    if (idx < nA) {
+      const int ma = (int)(idx % H), mb = (int)(idx / H);
+      int pa, qa, pb, qb;
+      rr_pair(N, r, ma, pa, qa);
+      rr_pair(N, r, mb, pb, qb);
+      double ca, sa, cb, sb;
+      jacobi_rot(Ain[pa + (int64_t)pa * N], Ain[qa + (int64_t)qa * N], Ain[pa + (int64_t)qa * N], ca, sa);
+      jacobi_rot(Ain[pb + (int64_t)pb * N], Ain[qb + (int64_t)qb * N], Ain[pb + (int64_t)qb * N], cb, sb);
+      const double x_pp = Ain[pa + (int64_t)pb * N], x_pq = Ain[pa + (int64_t)qb * N];
+      const double x_qp = Ain[qa + (int64_t)pb * N], x_qq = Ain[qa + (int64_t)qb * N];
+      // columns: p' = c p - s q, q' = s p + c q
+      const double y_pp = cb * x_pp - sb * x_pq, y_pq = sb * x_pp + cb * x_pq;
+      const double y_qp = cb * x_qp - sb * x_qq, y_qq = sb * x_qp + cb * x_qq;
+      // rows
+      double z_pp = ca * y_pp - sa * y_qp, z_pq = ca * y_pq - sa * y_qq;
+      double z_qp = sa * y_pp + ca * y_qp, z_qq = sa * y_pq + ca * y_qq;
+      if (ma == mb) {  // the rotated pair itself: off-diagonal is zero by construction
+        z_pq = 0.0;
+        z_qp = 0.0;
+      }
+      Aout[pa + (int64_t)pb * N] = z_pp;
+      Aout[pa + (int64_t)qb * N] = z_pq;
+      Aout[qa + (int64_t)pb * N] = z_qp;
+      Aout[qa + (int64_t)qb * N] = z_qq;
+    } else {
+      const int64_t t = idx - nA;
+      const int row = (int)(t % N), m = (int)(t / N);
+      int p, q;
+      rr_pair(N, r, m, p, q);
+      double c, sn;
+      jacobi_rot(Ain[p + (int64_t)p * N], Ain[q + (int64_t)q * N], Ain[p + (int64_t)q * N], c, sn);
+      const double vp = V[row + (int64_t)p * N], vq = V[row + (int64_t)q * N];
+      V[row + (int64_t)p * N] = c * vp - sn * vq;
+      V[row + (int64_t)q * N] = sn * vp + c * vq;
+    }
+  }
+}
+
+// off(A)^2 and ||A||_F^2; sets *done when off <= tol^2 * ||A||_F^2.
+__global__ void __launch_bounds__(256) jacobi_offnorm_kernel(const double* __restrict__ A, int N, double tol2,
+                                                             int* done, double* offout) {
+  __shared__ double sh[8];
+  double off = 0.0, tot = 0.0;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)N * N; idx += 256) {
+    const double v = A[idx];
+    tot += v * v;
+    if (idx % N != idx / N) off += v * v;
+  }
+  off = block_sum<256>(off, sh);
+  tot = block_sum<256>(tot, sh);
+  if (threadIdx.x == 0) {
+    *offout = off;
+    if (off <= tol2 * tot) *done = 1;
+  }
+}
+
+// Pad G (s x s) into N x N (N = s rounded up to even) and set V = I.
+__global__ void jacobi_setup_kernel(const double* __restrict__ G, int s, double* A, double* V, int N, int* done) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)N * N;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % N), j = (int)(idx / N);
+    double g = 0.0;
+    if (i < s && j < s) g = 0.5 * (G[i + (int64_t)j * s] + G[j + (int64_t)i * s]);
+    A[idx] = g;
+    V[idx] = (i == j) ? 1.0 : 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *done = 0;
+}
+
+size_t jacobi_work_bytes(int s) {
+  const int N = s + (s & 1);
+  return (size_t)2 * N * N * sizeof(double) + (size_t)N * N * sizeof(double) + 64;
+}
+
+// Eigendecomposition of the symmetric s x s matrix G.  Results: eigenvalues on the
+// diagonal of `evals_mat` (N x N, in work), eigenvectors in the columns of Vout (N x N).
+// work layout: A0 (N*N), A1 (N*N), V (N*N), flags.
+cudaError_t jacobi_eig(double* G, double* Vout, int s, double* work, int* sweeps_out, cudaStream_t st) {
+  const int N = s + (s & 1);
+  double* A0 = work;
+  double* A1 = work + (size_t)N * N;
+  int* done = reinterpret_cast<int*>(work + (size_t)3 * N * N);
+  double* offv = work + (size_t)3 * N * N + 1;
+  jacobi_setup_kernel<<<std::max(1, std::min(1024, (N * N + 255) / 256)), 256, 0, st>>>(G, s, A0, Vout, N, done);
+  NYS_CUDA_TRY(cudaGetLastError());
+  const int64_t total = (int64_t)(N / 2) * (N / 2) + (int64_t)N * (N / 2);
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (total + 255) / 256));
+  int sweeps = 0;
+  int done_h = 0;
+  const int kMaxSweeps = 30;
+  double* cur = A0;
+  double* nxt = A1;
+  for (; sweeps < kMaxSweeps; ++sweeps) {
+    if (N <= 2 && sweeps > 0) break;
+    for (int r = 0; r < N - 1; ++r) {
+      jacobi_round_kernel<<<blocks, 256, 0, st>>>(cur, nxt, Vout, N, r, done);
+      std::swap(cur, nxt);
+    }
+    NYS_CUDA_TRY(cudaGetLastError());
+    jacobi_offnorm_kernel<<<1, 256, 0, st>>>(cur, N, 1e-28, done, offv);
+    NYS_CUDA_TRY(cudaMemcpyAsync(&done_h, done, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NYS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (done_h) {
+      ++sweeps;
+      break;
+    }
+  }
+  // copy the diagonalised matrix back into G's storage layout (N x N in A0 slot)
+  if (cur != A0) NYS_CUDA_TRY(cudaMemcpyAsync(A0, cur, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (sweeps_out) *sweeps_out = sweeps;
+  return cudaGetLastError();
+}
+
+// Sort eigenpairs (diagonal of Ad, N x N) descending over the first s, build
+// Vs (s x s) = selected eigenvector columns (rows < s), sig2 (s).
+__global__ void __launch_bounds__(512) eig_sort_kernel(const double* __restrict__ Ad, const double* __restrict__ V,
+                                                       int N, int s, double* Vs, double* sig2) {
+  // rank-based ordering over the N eigenvalues (padding row/col, if any, has eigenvalue ~0
+  // and is excluded by keeping the s largest after dropping the pad index's contribution)
+  extern __shared__ double ev[];
+  int* rank = reinterpret_cast<int*>(ev + N);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) ev[i] = Ad[i + (int64_t)i * N];
+  __syncthreads();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    int r = 0;
+    for (int j = 0; j < N; ++j) r += (ev[j] > ev[i]) || (ev[j] == ev[i] && j < i);
+    rank[i] = r;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int r = rank[i];
+    if (r < s) {
+      sig2[r] = ev[i];
+      for (int row = 0; row < s; ++row) Vs[row + (int64_t)r * s] = V[row + (int64_t)i * N];
+    }
+  }
+}
+
+// U[:, c] = BV[:, c] / sigma_c  (sigma_c = sqrt(sig2_c) if sig2_c > 0 else column set to 0),
+// lam_c = max(0, sig2_c - nu)
+__global__ void finish_scale_kernel(double* U, int64_t d, int s, const double* __restrict__ sig2, double nu,
+                                    double* lam) {
+  const int64_t total = d * s;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / d);
+    const double g = sig2[c];
+    U[idx] = g > 0.0 ? U[idx] / sqrt(g) : 0.0;
+  }
+  if (blockIdx.x == 0)
+    for (int c = threadIdx.x; c < s; c += blockDim.x) lam[c] = fmax(0.0, sig2[c] - nu);
+}
+
+cudaError_t nystrom_finish(const double* B, int64_t d, int s, const double* Ad, const double* V, double nu,
+                           double* U, double* lam, double* work, cudaStream_t st) {
+  const int N = s + (s & 1);
+  double* Vs = work;
+  double* sig2 = work + (size_t)s * s;
+  const size_t sm = (size_t)N * sizeof(double) + (size_t)N * sizeof(int);
+  eig_sort_kernel<<<1, 512, sm, st>>>(Ad, V, N, s, Vs, sig2);
+  NYS_CUDA_TRY(cudaGetLastError());
+  NYS_CUDA_TRY(gemm_nn(B, d, s, Vs, U, st));
+  finish_scale_kernel<<<(unsigned)std::min<int64_t>(4096, (d * s + 255) / 256), 256, 0, st>>>(U, d, s, sig2, nu,
+                                                                                              lam);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ sketch GEMMs
+// W (n x s, column-major, ld n, compute type C) = diag(D) A Om, Om d x s column-major (ld d).
+template <int DT>
+__global__ void __launch_bounds__(256) sketch_aw_kernel(const unsigned char* __restrict__ Araw, int64_t n,
+                                                        int64_t d, int64_t ld,
+                                                        const typename Stor<DT>::C* __restrict__ Om, int s,
+                                                        const double* __restrict__ D,
+                                                        typename Stor<DT>::C* __restrict__ W) {
+  using C = typename Stor<DT>::C;
+  __shared__ C As[GK][GT + 1];
+  __shared__ C Bs[GK][GT + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int64_t m0 = (int64_t)blockIdx.x * GT;
+  const int n0 = blockIdx.y * GT;
+  C acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = C(0);
+  for (int64_t k0 = 0; k0 < d; k0 += GK) {
+    for (int idx = threadIdx.x; idx < GK * GT; idx += 256) {
+      const int kk = idx % GK, mm = idx / GK;  // A row-major: consecutive k
+      const int64_t k = k0 + kk, m = m0 + mm;
+      As[kk][mm] = (k < d && m < n) ? load_elem<DT>(Araw, m * ld + k) : C(0);
+      const int nn = idx / GK;
+      const int c = n0 + nn;
+      Bs[kk][nn] = (k < d && c < s) ? Om[k + (int64_t)c * d] : C(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      C a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t m = m0 + tx + 16 * i;
+    if (m >= n) continue;
+    const double dm = D ? D[m] : 1.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = n0 + ty + 16 * j;
+      if (c < s) W[m + (int64_t)c * n] = (C)(dm * (double)acc[i][j]);
+    }
+  }
+}
+
+// Partial Y_z (d x s) = A[rows z]^T W[rows z]
+template <int DT>
+__global__ void __launch_bounds__(256) sketch_atw_kernel(const unsigned char* __restrict__ Araw, int64_t n,
+                                                         int64_t d, int64_t ld,
+                                                         const typename Stor<DT>::C* __restrict__ W, int s,
+                                                         int64_t kchunk, typename Stor<DT>::C* __restrict__ Yp) {
+  using C = typename Stor<DT>::C;
+  __shared__ C As[GK][GT + 1];
+  __shared__ C Bs[GK][GT + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int64_t j0 = (int64_t)blockIdx.x * GT;
+  const int c0 = blockIdx.y * GT;
+  const int64_t kb = (int64_t)blockIdx.z * kchunk, ke = min(n, kb + kchunk);
+  C acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = C(0);
+  for (int64_t k0 = kb; k0 < ke; k0 += GK) {
+    for (int idx = threadIdx.x; idx < GK * GT; idx += 256) {
+      const int jj = idx % GT, kk = idx / GT;  // A row-major: consecutive j
+      const int64_t k = k0 + kk, j = j0 + jj;
+      As[kk][jj] = (k < ke && j < d) ? load_elem<DT>(Araw, k * ld + j) : C(0);
+      const int kk2 = idx % GK, cc = idx / GK;  // W column-major: consecutive k
+      const int64_t k2 = k0 + kk2;
+      const int c = c0 + cc;
+      Bs[kk2][cc] = (k2 < ke && c < s) ? W[k2 + (int64_t)c * n] : C(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      C a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  C* Y = Yp + (int64_t)blockIdx.z * d * s;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t j = j0 + tx + 16 * i;
+    if (j >= d) continue;
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int c = c0 + ty + 16 * jj;
+      if (c < s) Y[j + (int64_t)c * d] = acc[i][jj];
+    }
+  }
+}
+
+template <typename C>
+__global__ void sum_partials_to_f64_kernel(const C* __restrict__ Yp, int nz, int64_t len, double* __restrict__ Y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < nz; ++z) s += (double)Yp[z * len + i];
+    Y[i] = s;
+  }
+}
+
+static int64_t atw_kchunk(int64_t n, int64_t d, int s) {
+  // enough z-splits to give ~4 CTAs per SM worth of tiles, chunks of >= 1024 rows
+  const int64_t tiles = ((d + GT - 1) / GT) * ((s + GT - 1) / GT);
+  int64_t nz = std::max<int64_t>(1, (152 * 4 + tiles - 1) / tiles);
+  nz = std::min<int64_t>(nz, std::max<int64_t>(1, n / 1024));
+  int64_t kc = (n + nz - 1) / nz;
+  kc = (kc + GK - 1) / GK * GK;
+  return kc;
+}
+
+size_t sketch_atw_work_bytes(const nys_matrix* A, int s) {
+  const int64_t kc = atw_kchunk(A->n, A->d, s);
+  const int64_t nz = (A->n + kc - 1) / kc;
+  const size_t csz = compute_is_f64(A->dtype) ? 8 : 4;
+  return (size_t)nz * A->d * s * csz;
+}
+
+cudaError_t sketch_aw(const nys_matrix* A, const void* Omega, int s, const double* D, void* W, cudaStream_t st) {
+  dim3 grid((unsigned)((A->n + GT - 1) / GT), (s + GT - 1) / GT, 1);
+  const unsigned char* Ar = reinterpret_cast<const unsigned char*>(A->data);
+  switch (A->dtype) {
+    case NYS_F64:
+      sketch_aw_kernel<NYS_F64><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const double*)Omega, s, D, (double*)W);
+      break;
+    case NYS_F32:
+      sketch_aw_kernel<NYS_F32><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const float*)Omega, s, D, (float*)W);
+      break;
+    case NYS_BF16:
+      sketch_aw_kernel<NYS_BF16><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const float*)Omega, s, D, (float*)W);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t sketch_atw(const nys_matrix* A, const void* W, int s, double* Y, void* work, size_t work_bytes,
+                       cudaStream_t st) {
+  const int64_t kc = atw_kchunk(A->n, A->d, s);
+  const int nz = (int)((A->n + kc - 1) / kc);
+  if (work_bytes < sketch_atw_work_bytes(A, s)) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)((A->d + GT - 1) / GT), (s + GT - 1) / GT, nz);
+  const unsigned char* Ar = reinterpret_cast<const unsigned char*>(A->data);
+  const int64_t len = A->d * s;
+  const unsigned rb = (unsigned)std::min<int64_t>(4096, (len + 255) / 256);
+  switch (A->dtype) {
+    case NYS_F64:
+      sketch_atw_kernel<NYS_F64><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const double*)W, s, kc, (double*)work);
+      NYS_CUDA_TRY(cudaGetLastError());
+      sum_partials_to_f64_kernel<double><<<rb, 256, 0, st>>>((const double*)work, nz, len, Y);
+      break;
+    case NYS_F32:
+      sketch_atw_kernel<NYS_F32><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const float*)W, s, kc, (float*)work);
+      NYS_CUDA_TRY(cudaGetLastError());
+      sum_partials_to_f64_kernel<float><<<rb, 256, 0, st>>>((const float*)work, nz, len, Y);
+      break;
+    case NYS_BF16:
+      sketch_atw_kernel<NYS_BF16><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const float*)W, s, kc, (float*)work);
+      NYS_CUDA_TRY(cudaGetLastError());
+      sum_partials_to_f64_kernel<float><<<rb, 256, 0, st>>>((const float*)work, nz, len, Y);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ conversions
+__global__ void f64_to_f32_kernel(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+__global__ void f32_to_f64_kernel(const float* __restrict__ x, double* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+cudaError_t convert_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  f64_to_f32_kernel<<<(unsigned)std::min<int64_t>(4096, (n + 255) / 256), 256, 0, st>>>(x, y, n);
+  return cudaGetLastError();
+}
+cudaError_t convert_f32_to_f64(const float* x, double* y, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  f32_to_f64_kernel<<<(unsigned)std::min<int64_t>(4096, (n + 255) / 256), 256, 0, st>>>(x, y, n);
+  return cudaGetLastError();
+}
+
+}  // namespace nys

@@ -1,0 +1,138 @@
+// Device helpers: storage traits, mbarrier / TMA bulk-copy wrappers with bounded
+// waits, warp and block reductions.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nys_internal.cuh"
+
+namespace nys {
+
+// Upper bound on any device-side wait (cycles of clock64, ~2 s at 2 GHz).
+constexpr long long kWaitCycles = 4000000000LL;
+
+template <int DT> struct Stor;
+template <> struct Stor<NYS_F64> {
+  using C = double;
+  static constexpr int VEC = 2;
+  static constexpr int ESZ = 8;
+};
+template <> struct Stor<NYS_F32> {
+  using C = float;
+  static constexpr int VEC = 4;
+  static constexpr int ESZ = 4;
+};
+template <> struct Stor<NYS_BF16> {
+  using C = float;
+  static constexpr int VEC = 8;
+  static constexpr int ESZ = 2;
+};
+
+// Unpack one 16-byte vector of stored elements into compute values.
+template <int DT>
+__device__ __forceinline__ void unpack16(const uint4 r, typename Stor<DT>::C* o);
+template <>
+__device__ __forceinline__ void unpack16<NYS_F64>(const uint4 r, double* o) {
+  o[0] = __hiloint2double((int)r.y, (int)r.x);
+  o[1] = __hiloint2double((int)r.w, (int)r.z);
+}
+template <>
+__device__ __forceinline__ void unpack16<NYS_F32>(const uint4 r, float* o) {
+  o[0] = __uint_as_float(r.x);
+  o[1] = __uint_as_float(r.y);
+  o[2] = __uint_as_float(r.z);
+  o[3] = __uint_as_float(r.w);
+}
+template <>
+__device__ __forceinline__ void unpack16<NYS_BF16>(const uint4 r, float* o) {
+  o[0] = __uint_as_float(r.x << 16);
+  o[1] = __uint_as_float(r.x & 0xffff0000u);
+  o[2] = __uint_as_float(r.y << 16);
+  o[3] = __uint_as_float(r.y & 0xffff0000u);
+  o[4] = __uint_as_float(r.z << 16);
+  o[5] = __uint_as_float(r.z & 0xffff0000u);
+  o[6] = __uint_as_float(r.w << 16);
+  o[7] = __uint_as_float(r.w & 0xffff0000u);
+}
+
+// Load element j of a stored row as a compute value (scalar path for tails / GEMMs).
+template <int DT>
+__device__ __forceinline__ typename Stor<DT>::C load_elem(const void* base, int64_t idx);
+template <>
+__device__ __forceinline__ double load_elem<NYS_F64>(const void* base, int64_t idx) {
+  return __ldg(reinterpret_cast<const double*>(base) + idx);
+}
+template <>
+__device__ __forceinline__ float load_elem<NYS_F32>(const void* base, int64_t idx) {
+  return __ldg(reinterpret_cast<const float*>(base) + idx);
+}
+template <>
+__device__ __forceinline__ float load_elem<NYS_BF16>(const void* base, int64_t idx) {
+  const unsigned short h = __ldg(reinterpret_cast<const unsigned short*>(base) + idx);
+  return __uint_as_float(((unsigned)h) << 16);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// 1-D TMA bulk copy global -> shared, completion signalled on `bar` (bytes % 16 == 0,
+// both addresses 16-byte aligned).
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: returns false if the phase did not complete within kWaitCycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum in fixed order (deterministic); every thread gets the result.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh /* >= NT/32 */) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < NT / 32; ++i) s += sh[i];
+  return s;
+}
+
+}  // namespace nys

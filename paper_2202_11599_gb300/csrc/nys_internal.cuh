@@ -1,0 +1,104 @@
+// Internal declarations shared by the CUDA translation units of libnysadmm.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "nysadmm.h"
+
+namespace nys {
+
+constexpr int kApassThreads = 512;       // threads of the fused A-pass CTA
+constexpr int kVecThreads = 256;         // threads of the vector kernels
+
+// Row modes of the fused A-pass: u_i = phi(t_i), t = A p.
+enum ApassMode : int {
+  MODE_ID = 0,        // u = t                        (H = A^T A)
+  MODE_DIAG = 1,      // u = D_i t                    (H = A^T D A)
+  MODE_LOGIT = 2,     // sigma = sigmoid(t), w = sigma(1-sigma), D_out = w,
+                      // u = w t + b01 - sigma; loss += softplus(t) - b01 t
+  MODE_RESID = 3,     // u = t - b_i; loss += (t - b_i)^2 / 2
+  MODE_CONST = 4,     // u = b_i (no dot product: A^T b)
+  MODE_LGRAD = 5      // u = sigma(t) - b01; loss += softplus(t) - b01 t (logistic gradient)
+};
+
+struct ApassArgs {
+  const void* A;        // row-major n x ld
+  int64_t n, d, ld;
+  int dtype;            // nys_dtype
+  const void* p;        // length d, compute type
+  const double* D;      // length n (MODE_DIAG) or NULL
+  const double* b;      // length n (RESID / CONST / LOGIT labels in {-1,+1})
+  double* D_out;        // length n (MODE_LOGIT) or NULL
+  double* t_out;        // length n or NULL: t = A p
+  int mode;
+  const int* skip = nullptr;  // if non-null and *skip != 0 the pass is skipped
+};
+
+// Workspace-carrying handle for repeated A-passes on one matrix.
+struct ApassPlan {
+  int grid = 0;          // CTAs (partials)
+  int rows_per_step = 1; // R
+  int stages = 2;        // S
+  size_t smem = 0;       // dynamic shared memory bytes
+  int64_t dpad = 0;      // partial row stride (elements of compute type)
+  bool fused = true;     // false -> two-pass fallback
+};
+
+bool apass_plan(const nys_matrix* A, ApassPlan* plan);
+size_t apass_partial_bytes(const nys_matrix* A, const ApassPlan& plan);
+
+// y = sum of partials + rho * p (+ beta * y_prev?) -- y in compute type.
+// dot_part (optional): per-block partials of p^T y (double), count returned via nblk.
+cudaError_t apass_run(const ApassArgs& a, const ApassPlan& plan, void* partial, double* loss_part,
+                      int* dev_status, cudaStream_t st);
+cudaError_t apass_reduce(const ApassArgs& a, const ApassPlan& plan, const void* partial, double rho,
+                         void* y, double* dot_part, int dot_blocks, cudaStream_t st);
+int reduce_blocks(int64_t d);
+
+// ---------------------------------------------------------------- small dense FP64 kernels
+// C (s x s, col-major, ldc = s) = X^T Y for X, Y d x s col-major FP64 (ld = d); deterministic.
+cudaError_t gram_xty(const double* X, const double* Y, int64_t d, int s, double* C, double* work,
+                     cudaStream_t st);
+size_t gram_work_bytes(int64_t d, int s);
+// In-place upper Cholesky of a symmetric s x s matrix (col-major): C^T C = M. info[0] = 0 ok,
+// k+1 if the k-th pivot is not positive.  M is symmetrised as (M + M^T)/2 first.
+cudaError_t chol_upper(double* M, int s, int* info, cudaStream_t st);
+// B (d x s) = Y C^{-1} with C upper (s x s); B may alias Y.
+cudaError_t trsm_right_upper(const double* C, int s, double* Y, int64_t d, cudaStream_t st);
+// Y += nu * X  (d x s)
+cudaError_t axpy_panel(double nu, const double* X, double* Y, int64_t n, cudaStream_t st);
+// lambda_max of a symmetric s x s matrix by power iteration (device scalar out)
+cudaError_t power_lambda_max(const double* G, int s, double* out, double* work, cudaStream_t st);
+// Symmetric eigendecomposition by parallel cyclic Jacobi: G (s x s, overwritten) -> V (s x s),
+// eigenvalues in the diagonal.  Returns sweeps used in *sweeps (host).
+cudaError_t jacobi_eig(double* G, double* V, int s, double* work, int* sweeps, cudaStream_t st);
+size_t jacobi_work_bytes(int s);
+// After Jacobi: sort eigenpairs descending, U = B V Sigma^{-1}, lam = max(0, sigma^2 - nu).
+cudaError_t nystrom_finish(const double* B, int64_t d, int s, const double* G, const double* V,
+                           double nu, double* U, double* lam, double* work, cudaStream_t st);
+
+// ---------------------------------------------------------------- sketch GEMMs
+// W (n x s, col-major, ld n) = diag(D) (A Omega) with Omega d x s col-major (ld d) in compute type
+cudaError_t sketch_aw(const nys_matrix* A, const void* Omega, int s, const double* D, void* W,
+                      cudaStream_t st);
+// Y (d x s, col-major FP64) = A^T W (+ shift * Omega64)
+cudaError_t sketch_atw(const nys_matrix* A, const void* W, int s, double* Y, void* work,
+                       size_t work_bytes, cudaStream_t st);
+size_t sketch_atw_work_bytes(const nys_matrix* A, int s);
+
+// ---------------------------------------------------------------- helpers
+cudaError_t convert_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t st);
+cudaError_t convert_f32_to_f64(const float* x, double* y, int64_t n, cudaStream_t st);
+
+inline size_t dtype_size(int dt) { return dt == NYS_F64 ? 8 : (dt == NYS_F32 ? 4 : 2); }
+inline bool compute_is_f64(int dt) { return dt == NYS_F64; }
+
+}  // namespace nys
+
+#define NYS_CUDA_TRY(expr)                          \
+  do {                                              \
+    cudaError_t _e = (expr);                        \
+    if (_e != cudaSuccess) return _e;               \
+  } while (0)

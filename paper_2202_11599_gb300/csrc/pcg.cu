@@ -1,0 +1,491 @@
+// Nystrom PCG (App. B, Alg. Nystrom PCG) on the device, plus the ADMM vector
+// steps of Alg. NysADMM (z-prox by soft-thresholding, scaled dual update,
+// primal/dual residuals of Sec. 2.1).
+//
+// One PCG iteration is six stream-ordered launches; every scalar (alpha, beta,
+// ||w||, the stop test) lives in a device PcgState, so the host only reads the
+// state once per chunk of iterations.  Kernels launched past convergence see
+// `done` and return at once, which keeps the iterate sequence identical to a
+// host-checked loop.  All reductions are fixed-order (run-to-run identical).
+#include "device_util.cuh"
+#include "solver.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace nys {
+
+// Fixed-order sum of n doubles by one warp; all lanes get the result.
+__device__ __forceinline__ double warp_fixed_sum(const double* a, int n) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s += a[i];
+  return warp_sum(s);
+}
+
+// Block-wide broadcast of warp 0's fixed-order sum.
+__device__ __forceinline__ double block_fixed_sum(const double* a, int n, double* slot) {
+  if (threadIdx.x < 32) {
+    const double s = warp_fixed_sum(a, n);
+    if (threadIdx.x == 0) *slot = s;
+  }
+  __syncthreads();
+  const double r = *slot;
+  __syncthreads();
+  return r;
+}
+
+__global__ void pcg_reset_kernel(PcgState* st, double tol, int tol_abs, int maxit, int fixed,
+                                 const double* dev_tol) {
+  st->wy = 0.0;
+  st->w2 = 0.0;
+  st->r2 = 0.0;
+  st->thresh2 = 0.0;
+  st->tol = dev_tol ? *dev_tol : tol;
+  st->tol_abs = dev_tol ? 1 : tol_abs;
+  st->iters = 0;
+  st->done = 0;
+  st->status = 0;
+  st->maxit = maxit;
+  st->fixed = fixed;
+}
+
+// K3: init  -> w = r - v (v = (H + rho I) x0, or x0 = 0), partial ||r||^2;
+//     step  -> alpha = w^T y / p^T v, x += alpha p, w -= alpha v.
+// Both: partial ||w||^2 and partial U^T w over this block's chunk of w.
+template <typename C>
+__global__ void __launch_bounds__(kVecThreads) pcg_update_kernel(int init, int64_t d, int chunk, C* __restrict__ x,
+                                                                 C* __restrict__ w, const C* __restrict__ r,
+                                                                 const C* __restrict__ v, const C* __restrict__ p,
+                                                                 const C* __restrict__ U, int s,
+                                                                 const double* __restrict__ pv_part, int npv,
+                                                                 const double* __restrict__ wy_part, int nwy,
+                                                                 double* part_w2, double* part_r2, double* part_g,
+                                                                 const PcgState* st) {
+  if (st->done) return;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* wch = reinterpret_cast<C*>(sm_raw);
+  __shared__ double sh[kVecThreads / 32];
+  __shared__ double slot;
+  const int64_t j0 = (int64_t)blockIdx.x * chunk;
+  const int64_t j1 = min(d, j0 + chunk);
+  double alpha = 0.0;
+  if (!init) {
+    const double pv = block_fixed_sum(pv_part, npv, &slot);
+    const double wy = block_fixed_sum(wy_part, nwy, &slot);
+    if (!(pv > 0.0) || !isfinite(pv)) return;  // breakdown: flagged by the scalar kernel
+    alpha = wy / pv;
+  }
+  const C a = (C)alpha;
+  double lw2 = 0.0, lr2 = 0.0;
+  for (int64_t j = j0 + threadIdx.x; j < j1; j += kVecThreads) {
+    C wj;
+    if (init) {
+      const C rj = r[j];
+      wj = v ? rj - v[j] : rj;
+      lr2 += (double)rj * (double)rj;
+    } else {
+      x[j] = fma(a, p[j], x[j]);
+      wj = fma(-a, v[j], w[j]);
+    }
+    w[j] = wj;
+    wch[j - j0] = wj;
+    lw2 += (double)wj * (double)wj;
+  }
+  const double tw2 = block_sum<kVecThreads>(lw2, sh);
+  const double tr2 = block_sum<kVecThreads>(lr2, sh);
+  if (threadIdx.x == 0) {
+    part_w2[blockIdx.x] = tw2;
+    if (init) part_r2[blockIdx.x] = tr2;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int len = (int)(j1 - j0);
+  for (int i = warp; i < s; i += kVecThreads / 32) {
+    const C* Ui = U + (int64_t)i * d + j0;
+    C acc = C(0);
+    for (int jj = lane; jj < len; jj += 32) acc = fma(Ui[jj], wch[jj], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) part_g[(int64_t)blockIdx.x * s + i] = (double)acc;
+  }
+}
+
+// K4 (one block): ||w||^2, stop test, iteration count, g_i = c_i (U^T w)_i.
+template <typename C>
+__global__ void __launch_bounds__(kVecThreads) pcg_scalar_kernel(int init, int nb3, const double* part_w2,
+                                                                 const double* part_r2, const double* part_g, int s,
+                                                                 const C* __restrict__ cvec, C* __restrict__ gs,
+                                                                 const double* pv_part, int npv,
+                                                                 const double* wy_part, int nwy, PcgState* st) {
+  if (st->done) return;
+  __shared__ double slot;
+  const double w2 = block_fixed_sum(part_w2, nb3, &slot);
+  double r2 = 0.0, pv = 1.0, wy = 0.0;
+  if (init) {
+    r2 = block_fixed_sum(part_r2, nb3, &slot);
+  } else {
+    pv = block_fixed_sum(pv_part, npv, &slot);
+    wy = block_fixed_sum(wy_part, nwy, &slot);
+  }
+  if (threadIdx.x == 0) {
+    if (init) {
+      st->r2 = r2;
+      st->thresh2 = st->tol_abs ? st->tol * st->tol : st->tol * st->tol * r2;
+      st->iters = 0;
+    } else {
+      if (!(pv > 0.0) || !isfinite(pv) || !isfinite(w2)) {
+        st->status = NYS_EBREAKDOWN;
+        st->done = 1;
+      } else {
+        st->wy = wy;
+        st->iters += 1;
+      }
+    }
+    if (!st->done) {
+      st->w2 = w2;
+      if (st->fixed >= 0) {
+        if (st->iters >= st->fixed) st->done = 1;
+      } else if (!(w2 > st->thresh2)) {
+        st->done = 1;
+      } else if (st->iters >= st->maxit) {
+        st->done = 1;
+        st->status = NYS_ENOCONV;
+      }
+    }
+  }
+  for (int i = threadIdx.x; i < s; i += kVecThreads) {
+    double g = 0.0;
+    for (int b = 0; b < nb3; ++b) g += part_g[(int64_t)b * s + i];
+    gs[i] = (C)((double)cvec[i] * g);
+  }
+}
+
+// K5: y = w + U gs (= P^{-1} w), partial w^T y.
+template <typename C>
+__global__ void __launch_bounds__(kVecThreads) pcg_tail_kernel(int64_t d, const C* __restrict__ w, C* __restrict__ y,
+                                                               const C* __restrict__ U, int s,
+                                                               const C* __restrict__ gs, double* part_wy,
+                                                               const PcgState* st) {
+  if (st->done) return;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* g = reinterpret_cast<C*>(sm_raw);
+  __shared__ double sh[kVecThreads / 32];
+  for (int i = threadIdx.x; i < s; i += kVecThreads) g[i] = gs[i];
+  __syncthreads();
+  double lwy = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)gridDim.x * kVecThreads) {
+    const C wj = w[j];
+    C acc = wj;
+    for (int i = 0; i < s; ++i) acc = fma(U[(int64_t)i * d + j], g[i], acc);
+    y[j] = acc;
+    lwy += (double)wj * (double)acc;
+  }
+  const double t = block_sum<kVecThreads>(lwy, sh);
+  if (threadIdx.x == 0) part_wy[blockIdx.x] = t;
+}
+
+// K6: beta = (w^T y)_new / (w^T y)_old, p = y + beta p (init: p = y).
+template <typename C>
+__global__ void __launch_bounds__(kVecThreads) pcg_pupdate_kernel(int init, int64_t d, const C* __restrict__ y,
+                                                                  C* __restrict__ p, const double* wy_part, int nwy,
+                                                                  const PcgState* st) {
+  if (st->done) return;
+  __shared__ double slot;
+  double beta = 0.0;
+  if (!init) beta = block_fixed_sum(wy_part, nwy, &slot) / st->wy;
+  const C b = (C)beta;
+  for (int64_t j = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)gridDim.x * kVecThreads)
+    p[j] = init ? y[j] : fma(b, p[j], y[j]);
+}
+
+// ------------------------------------------------------------------ host driver
+
+static int upd_chunk(int64_t d) {
+  // ~2 blocks per SM at large d, >= 256 elements per block
+  int64_t ch = std::max<int64_t>(256, (d + 303) / 304);
+  ch = (ch + 31) / 32 * 32;
+  return (int)ch;
+}
+
+int pcg_nb3(int64_t d) { return (int)((d + upd_chunk(d) - 1) / upd_chunk(d)); }
+
+template <typename C>
+nys_status pcg_run(const PcgProblem& pb, const PrecondView& P, const C* r, C* x, const PcgParams& prm,
+                   cudaStream_t stream, int* iters_out, double* resnorm_out) {
+  Pool pool(stream);
+  const int64_t d = pb.A->d;
+  const int s = P.s;
+  const C* U = reinterpret_cast<const C*>(P.U);
+  const C* cvec = reinterpret_cast<const C*>(P.c);
+  const int chunk = upd_chunk(d);
+  const int nb3 = (int)((d + chunk - 1) / chunk);
+  const int nbr = reduce_blocks(d);
+  const int nb5 = nbr;
+
+  C* w = pool.alloc<C>(d);
+  C* y = pool.alloc<C>(d);
+  C* p = pool.alloc<C>(d);
+  C* v = pool.alloc<C>(d);
+  C* gs = pool.alloc<C>(std::max(1, s));
+  double* part_w2 = pool.alloc<double>(nb3);
+  double* part_r2 = pool.alloc<double>(nb3);
+  double* part_g = pool.alloc<double>((size_t)nb3 * std::max(1, s));
+  double* pv_part = pool.alloc<double>(nbr);
+  double* wy_part = pool.alloc<double>(nb5);
+  void* apart = pool.alloc<unsigned char>(apass_partial_bytes(pb.A, pb.plan));
+  PcgState* st = pool.alloc<PcgState>(1);
+  int* dstat = pool.alloc<int>(1);
+  if (!pool.ok()) return NYS_ENOMEM;
+  if (cudaMemsetAsync(dstat, 0, sizeof(int), stream) != cudaSuccess) return NYS_ECUDA;
+
+  ApassArgs aa;
+  aa.A = pb.A->data;
+  aa.n = pb.A->n;
+  aa.d = d;
+  aa.ld = pb.A->ld;
+  aa.dtype = pb.A->dtype;
+  aa.D = pb.D;
+  aa.b = nullptr;
+  aa.D_out = nullptr;
+  aa.t_out = nullptr;
+  aa.mode = pb.D ? MODE_DIAG : MODE_ID;
+  aa.skip = &st->done;
+
+  const size_t sm_upd = (size_t)chunk * sizeof(C);
+  const size_t sm_tail = (size_t)std::max(1, s) * sizeof(C);
+  cudaError_t e = cudaSuccess;
+#define LAUNCH_OK(x)                \
+  do {                              \
+    e = (x);                        \
+    if (e != cudaSuccess) return NYS_ECUDA; \
+  } while (0)
+
+  pcg_reset_kernel<<<1, 1, 0, stream>>>(st, prm.tol, prm.tol_abs, prm.maxit, prm.fixed, prm.dev_tol);
+  LAUNCH_OK(cudaGetLastError());
+  const C* v0 = nullptr;
+  if (!prm.x0_zero) {
+    aa.p = x;
+    LAUNCH_OK(apass_run(aa, pb.plan, apart, nullptr, dstat, stream));
+    LAUNCH_OK(apass_reduce(aa, pb.plan, apart, pb.rho, v, nullptr, 0, stream));
+    v0 = v;
+  }
+  pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, stream>>>(1, d, chunk, x, w, r, v0, p, U, s, pv_part, nbr,
+                                                             wy_part, nb5, part_w2, part_r2, part_g, st);
+  LAUNCH_OK(cudaGetLastError());
+  pcg_scalar_kernel<C><<<1, kVecThreads, 0, stream>>>(1, nb3, part_w2, part_r2, part_g, s, cvec, gs, pv_part, nbr,
+                                                      wy_part, nb5, st);
+  LAUNCH_OK(cudaGetLastError());
+  pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, stream>>>(d, w, y, U, s, gs, wy_part, st);
+  LAUNCH_OK(cudaGetLastError());
+  pcg_pupdate_kernel<C><<<nb5, kVecThreads, 0, stream>>>(1, d, y, p, wy_part, nb5, st);
+  LAUNCH_OK(cudaGetLastError());
+
+  PcgState* hs = host_state();
+  int launched = 0;
+  const int cap = prm.fixed >= 0 ? prm.fixed : prm.maxit;
+  int chunk_it = std::max(1, std::min(4, cap));
+  for (;;) {
+    for (int c = 0; c < chunk_it && launched < cap; ++c, ++launched) {
+      aa.p = p;
+      LAUNCH_OK(apass_run(aa, pb.plan, apart, nullptr, dstat, stream));
+      LAUNCH_OK(apass_reduce(aa, pb.plan, apart, pb.rho, v, pv_part, nbr, stream));
+      pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, stream>>>(0, d, chunk, x, w, r, v, p, U, s, pv_part, nbr,
+                                                                 wy_part, nb5, part_w2, part_r2, part_g, st);
+      LAUNCH_OK(cudaGetLastError());
+      pcg_scalar_kernel<C><<<1, kVecThreads, 0, stream>>>(0, nb3, part_w2, part_r2, part_g, s, cvec, gs, pv_part,
+                                                          nbr, wy_part, nb5, st);
+      LAUNCH_OK(cudaGetLastError());
+      pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, stream>>>(d, w, y, U, s, gs, wy_part, st);
+      LAUNCH_OK(cudaGetLastError());
+      pcg_pupdate_kernel<C><<<nb5, kVecThreads, 0, stream>>>(0, d, y, p, wy_part, nb5, st);
+      LAUNCH_OK(cudaGetLastError());
+    }
+    LAUNCH_OK(cudaMemcpyAsync(hs, st, sizeof(PcgState), cudaMemcpyDeviceToHost, stream));
+    LAUNCH_OK(cudaStreamSynchronize(stream));
+    if (hs->done || launched >= cap) break;
+    chunk_it = std::min(32, chunk_it * 2);
+  }
+  int dstat_h = 0;
+  LAUNCH_OK(cudaMemcpyAsync(&dstat_h, dstat, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  LAUNCH_OK(cudaStreamSynchronize(stream));
+#undef LAUNCH_OK
+  if (iters_out) *iters_out = hs->iters;
+  if (resnorm_out) *resnorm_out = std::sqrt(hs->w2);
+  if (dstat_h) return (nys_status)dstat_h;
+  if (!hs->done && prm.fixed < 0) return NYS_ENOCONV;
+  return (nys_status)hs->status;
+}
+
+template nys_status pcg_run<double>(const PcgProblem&, const PrecondView&, const double*, double*, const PcgParams&,
+                                    cudaStream_t, int*, double*);
+template nys_status pcg_run<float>(const PcgProblem&, const PrecondView&, const float*, float*, const PcgParams&,
+                                   cudaStream_t, int*, double*);
+
+// ------------------------------------------------------------------ P^{-1} on k vectors (standalone apply)
+template <typename C>
+nys_status precond_apply_run(const PrecondView& P, int64_t d, const C* V, C* Y, int64_t k, cudaStream_t stream) {
+  Pool pool(stream);
+  const int s = P.s;
+  const int chunk = upd_chunk(d);
+  const int nb3 = (int)((d + chunk - 1) / chunk);
+  const int nb5 = reduce_blocks(d);
+  C* w = pool.alloc<C>(d);
+  C* gs = pool.alloc<C>(std::max(1, s));
+  double* part_w2 = pool.alloc<double>(nb3);
+  double* part_r2 = pool.alloc<double>(nb3);
+  double* part_g = pool.alloc<double>((size_t)nb3 * std::max(1, s));
+  double* wy_part = pool.alloc<double>(nb5);
+  PcgState* st = pool.alloc<PcgState>(1);
+  if (!pool.ok()) return NYS_ENOMEM;
+  for (int64_t c = 0; c < k; ++c) {
+    pcg_reset_kernel<<<1, 1, 0, stream>>>(st, 0.0, 1, 1, -1, nullptr);
+    // init-mode update copies V[:, c] into w and forms the partials of U^T w
+    pcg_update_kernel<C><<<nb3, kVecThreads, (size_t)chunk * sizeof(C), stream>>>(
+        1, d, chunk, nullptr, w, V + c * d, nullptr, nullptr, reinterpret_cast<const C*>(P.U), s, nullptr, 0,
+        nullptr, 0, part_w2, part_r2, part_g, st);
+    pcg_scalar_kernel<C><<<1, kVecThreads, 0, stream>>>(1, nb3, part_w2, part_r2, part_g, s,
+                                                        reinterpret_cast<const C*>(P.c), gs, nullptr, 0, nullptr, 0,
+                                                        st);
+    // the scalar kernel may mark the state done (||w|| <= 0 threshold); force the tail to run
+    pcg_reset_kernel<<<1, 1, 0, stream>>>(st, 0.0, 1, 1, -1, nullptr);
+    pcg_tail_kernel<C><<<nb5, kVecThreads, (size_t)std::max(1, s) * sizeof(C), stream>>>(
+        d, w, Y + c * d, reinterpret_cast<const C*>(P.U), s, gs, wy_part, st);
+    if (cudaGetLastError() != cudaSuccess) return NYS_ECUDA;
+  }
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return NYS_ECUDA;
+  return NYS_OK;
+}
+
+template nys_status precond_apply_run<double>(const PrecondView&, int64_t, const double*, double*, int64_t,
+                                              cudaStream_t);
+template nys_status precond_apply_run<float>(const PrecondView&, int64_t, const float*, float*, int64_t, cudaStream_t);
+
+// ------------------------------------------------------------------ ADMM vector kernels (FP64 state)
+
+// r = q + rho (z - u)   or, for the refined x-step, r = rho (z - u - x) - yres
+template <typename C>
+__global__ void admm_rhs_kernel(int64_t d, const double* __restrict__ q, const double* __restrict__ z,
+                                const double* __restrict__ u, double rho, const double* __restrict__ x,
+                                const double* __restrict__ yres, C* __restrict__ r) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x) {
+    const double zu = z[j] - u[j];
+    const double rj = yres ? rho * (zu - x[j]) - yres[j] : fma(rho, zu, q[j]);
+    r[j] = (C)rj;
+  }
+}
+
+// x <- xc (or x += xc), z_old = z, z = S_kappa(x + u), u += x - z, residual partials.
+template <typename C>
+__global__ void __launch_bounds__(kVecThreads) admm_zu_kernel(int64_t d, const C* __restrict__ xc, int accumulate,
+                                                              double* __restrict__ x, double* __restrict__ z,
+                                                              double* __restrict__ u, double kappa,
+                                                              double* __restrict__ ztrace, double* part5) {
+  __shared__ double sh[kVecThreads / 32];
+  double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+  for (int64_t j = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)gridDim.x * kVecThreads) {
+    const double xj = accumulate ? x[j] + (double)xc[j] : (double)xc[j];
+    const double zo = z[j];
+    const double vj = xj + u[j];
+    const double mag = fabs(vj) - kappa;
+    const double zj = mag > 0.0 ? copysign(mag, vj) : 0.0;
+    const double uj = u[j] + xj - zj;
+    x[j] = xj;
+    z[j] = zj;
+    u[j] = uj;
+    if (ztrace) ztrace[j] = zj;
+    a0 += (xj - zj) * (xj - zj);
+    a1 += (zj - zo) * (zj - zo);
+    a2 += xj * xj;
+    a3 += zj * zj;
+    a4 += uj * uj;
+  }
+  a0 = block_sum<kVecThreads>(a0, sh);
+  a1 = block_sum<kVecThreads>(a1, sh);
+  a2 = block_sum<kVecThreads>(a2, sh);
+  a3 = block_sum<kVecThreads>(a3, sh);
+  a4 = block_sum<kVecThreads>(a4, sh);
+  if (threadIdx.x == 0) {
+    double* o = part5 + (int64_t)blockIdx.x * 5;
+    o[0] = a0;
+    o[1] = a1;
+    o[2] = a2;
+    o[3] = a3;
+    o[4] = a4;
+  }
+}
+
+// r_p, r_d (Sec. 2.1), the next PCG tolerance sqrt(r_p r_d) (Sec. 5) and the
+// residual stopping test.
+__global__ void admm_scalar_kernel(int nb, const double* part5, double rho, int k, double* rp_trace,
+                                   double* rd_trace, double* eps_next, double eps_abs, double eps_rel, int* stop) {
+  if (threadIdx.x != 0) return;
+  double a[5] = {0, 0, 0, 0, 0};
+  for (int b = 0; b < nb; ++b)
+    for (int t = 0; t < 5; ++t) a[t] += part5[(int64_t)b * 5 + t];
+  const double rp = sqrt(a[0]);
+  const double rd = rho * sqrt(a[1]);
+  rp_trace[k] = rp;
+  rd_trace[k] = rd;
+  *eps_next = sqrt(rp * rd);
+  if (eps_rel > 0.0) {
+    const double tp = eps_abs + eps_rel * fmax(sqrt(a[2]), sqrt(a[3]));
+    const double td = eps_abs + eps_rel * rho * sqrt(a[4]);
+    if (rp <= tp && rd <= td) *stop = 1;
+  }
+}
+
+int admm_blocks(int64_t d) { return reduce_blocks(d); }
+
+template <typename C>
+cudaError_t admm_rhs(int64_t d, const double* q, const double* z, const double* u, double rho, const double* x,
+                     const double* yres, C* r, cudaStream_t st) {
+  admm_rhs_kernel<C><<<admm_blocks(d), kVecThreads, 0, st>>>(d, q, z, u, rho, x, yres, r);
+  return cudaGetLastError();
+}
+template cudaError_t admm_rhs<double>(int64_t, const double*, const double*, const double*, double, const double*,
+                                      const double*, double*, cudaStream_t);
+template cudaError_t admm_rhs<float>(int64_t, const double*, const double*, const double*, double, const double*,
+                                     const double*, float*, cudaStream_t);
+
+template <typename C>
+cudaError_t admm_zu(int64_t d, const C* xc, int accumulate, double* x, double* z, double* u, double kappa,
+                    double* ztrace, double* part5, cudaStream_t st) {
+  admm_zu_kernel<C><<<admm_blocks(d), kVecThreads, 0, st>>>(d, xc, accumulate, x, z, u, kappa, ztrace, part5);
+  return cudaGetLastError();
+}
+template cudaError_t admm_zu<double>(int64_t, const double*, int, double*, double*, double*, double, double*,
+                                     double*, cudaStream_t);
+template cudaError_t admm_zu<float>(int64_t, const float*, int, double*, double*, double*, double, double*, double*,
+                                    cudaStream_t);
+
+cudaError_t admm_scalar(int64_t d, const double* part5, double rho, int k, double* rp, double* rd, double* eps_next,
+                        double eps_abs, double eps_rel, int* stop, cudaStream_t st) {
+  admm_scalar_kernel<<<1, 32, 0, st>>>(admm_blocks(d), part5, rho, k, rp, rd, eps_next, eps_abs, eps_rel, stop);
+  return cudaGetLastError();
+}
+
+void keep_mempool_cached() {
+  static int done_dev = -1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  if (done_dev == dev) return;
+  cudaMemPool_t mp;
+  if (cudaDeviceGetDefaultMemPool(&mp, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done_dev = dev;
+}
+
+PcgState* host_state() {
+  static PcgState* hs = nullptr;
+  if (!hs) {
+    if (cudaMallocHost((void**)&hs, sizeof(PcgState)) != cudaSuccess) {
+      static PcgState fallback;
+      hs = &fallback;
+    }
+  }
+  return hs;
+}
+
+}  // namespace nys

@@ -1,0 +1,96 @@
+// Host-side solver structures shared by pcg.cu and capi.cu.
+#pragma once
+#include <vector>
+
+#include "nys_internal.cuh"
+
+namespace nys {
+
+struct PcgState {
+  double wy;       // w^T y of the previous iteration (denominator of beta)
+  double w2;       // ||w||^2 of the current residual
+  double r2;       // ||r||^2
+  double thresh2;  // stop when ||w||^2 <= thresh2
+  double tol;
+  int tol_abs;
+  int iters;
+  int done;
+  int status;
+  int maxit;
+  int fixed;       // >= 0: run exactly this many iterations
+};
+
+// Stream-ordered device allocations freed when the pool goes out of scope.
+void keep_mempool_cached();
+
+class Pool {
+ public:
+  explicit Pool(cudaStream_t st) : st_(st) { keep_mempool_cached(); }
+  ~Pool() {
+    for (void* p : ptrs_) cudaFreeAsync(p, st_);
+  }
+  template <typename T>
+  T* alloc(size_t count) {
+    if (count == 0) count = 1;
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, count * sizeof(T), st_) != cudaSuccess) {
+      ok_ = false;
+      cudaGetLastError();
+      return nullptr;
+    }
+    ptrs_.push_back(p);
+    return reinterpret_cast<T*>(p);
+  }
+  bool ok() const { return ok_; }
+
+ private:
+  cudaStream_t st_;
+  std::vector<void*> ptrs_;
+  bool ok_ = true;
+};
+
+struct PcgProblem {
+  const nys_matrix* A;
+  const double* D;    // NULL: H = A^T A
+  double rho;
+  ApassPlan plan;
+};
+
+// Preconditioner in the PCG compute type: U (d x s column-major) and
+// c_i = (lam_s + rho)/(lam_i + rho) - 1 (Eq. Nystrom preconditioner).  s = 0: P = I.
+struct PrecondView {
+  const void* U = nullptr;
+  const void* c = nullptr;
+  int s = 0;
+};
+
+struct PcgParams {
+  double tol = 1e-8;
+  int tol_abs = 0;
+  int maxit = 1000;
+  int fixed = -1;
+  bool x0_zero = false;
+  const double* dev_tol = nullptr;  // device tolerance (absolute), overrides tol
+};
+
+template <typename C>
+nys_status pcg_run(const PcgProblem& pb, const PrecondView& P, const C* r, C* x, const PcgParams& prm,
+                   cudaStream_t stream, int* iters_out, double* resnorm_out);
+
+template <typename C>
+nys_status precond_apply_run(const PrecondView& P, int64_t d, const C* V, C* Y, int64_t k, cudaStream_t stream);
+
+template <typename C>
+cudaError_t admm_rhs(int64_t d, const double* q, const double* z, const double* u, double rho, const double* x,
+                     const double* yres, C* r, cudaStream_t st);
+template <typename C>
+cudaError_t admm_zu(int64_t d, const C* xc, int accumulate, double* x, double* z, double* u, double kappa,
+                    double* ztrace, double* part5, cudaStream_t st);
+cudaError_t admm_scalar(int64_t d, const double* part5, double rho, int k, double* rp, double* rd, double* eps_next,
+                        double eps_abs, double eps_rel, int* stop, cudaStream_t st);
+int admm_blocks(int64_t d);
+int pcg_nb3(int64_t d);
+
+PcgState* host_state();
+
+}  // namespace nys

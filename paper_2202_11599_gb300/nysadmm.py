@@ -1,0 +1,280 @@
+"""Thin Python binding of libnysadmm (include/nysadmm.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+Tensors are torch CUDA tensors (PyTorch supplies device memory and the stream);
+the library is required -- there is no CPU fallback, and a missing or
+unloadable library raises at first use.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from ctypes import POINTER, c_double, c_int32, c_int64, c_void_p
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnysadmm.so")
+
+NYS_OK, NYS_EINVAL, NYS_ENOTSPD, NYS_EBREAKDOWN, NYS_ENOCONV, NYS_ETIMEOUT, NYS_ECUDA, NYS_ENOMEM = range(8)
+NYS_LASSO, NYS_LOGISTIC = 0, 1
+NYS_F64, NYS_F32, NYS_BF16 = 0, 1, 2
+TOL_MODES = {"rel": 0, "abs": 1, "sqrt_rprd": 2}
+_DTYPES = {torch.float64: NYS_F64, torch.float32: NYS_F32, torch.bfloat16: NYS_BF16}
+_LOSSES = {"lasso": NYS_LASSO, "logistic": NYS_LOGISTIC}
+
+
+class NysMatrixC(ctypes.Structure):
+    _fields_ = [("data", c_void_p), ("dtype", c_int32), ("n", c_int64), ("d", c_int64), ("ld", c_int64)]
+
+
+class NysOptsC(ctypes.Structure):
+    _fields_ = [("shift_scale", c_double), ("pcg_tol_mode", c_int32), ("pcg_maxit", c_int32),
+                ("pcg_fixed_iters", POINTER(c_int32)), ("admm_maxit", c_int32),
+                ("eps_abs", c_double), ("eps_rel", c_double), ("A_inner", POINTER(NysMatrixC)),
+                ("refine", c_int32), ("z_trace", c_void_p), ("rank_max", c_int32),
+                ("ada_tol", c_double), ("resketch_every", c_int32), ("stream", c_void_p)]
+
+
+class NysInfoC(ctypes.Structure):
+    _fields_ = [("admm_iters", c_int32), ("pcg_iters_total", c_int32), ("final_rank", c_int32),
+                ("status", c_int32), ("r_p", c_double), ("r_d", c_double), ("emp_cond", c_double),
+                ("nu", c_double)]
+
+
+class NysError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} (status {status})")
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libnysadmm.so (built by __graft_entry__.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(the CUDA library is required; there is no CPU path)")
+    L = ctypes.CDLL(LIB_PATH)
+    P = POINTER
+    L.nys_opts_default.argtypes = [P(NysOptsC)]
+    L.nys_opts_default.restype = None
+    L.nys_strerror.argtypes = [c_int32]
+    L.nys_strerror.restype = ctypes.c_char_p
+    L.nys_hmatvec.argtypes = [P(NysMatrixC), c_void_p, c_double, c_void_p, c_void_p, c_void_p]
+    L.nys_sketch.argtypes = [P(NysMatrixC), c_void_p, c_double, c_int32, c_void_p, P(NysOptsC), P(c_void_p)]
+    L.nys_precond_get.argtypes = [c_void_p, c_void_p, P(c_double), P(c_int32), P(c_int64), P(c_double), c_void_p]
+    L.nys_precond_apply.argtypes = [c_void_p, c_double, c_void_p, c_void_p, c_int64, c_int32, c_void_p]
+    L.pcg_solve.argtypes = [P(NysMatrixC), c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_double,
+                            P(NysOptsC), P(c_int32), P(c_double)]
+    L.nysadmm_solve.argtypes = [c_int32, P(NysMatrixC), c_void_p, c_double, c_double, c_int32, c_double,
+                                c_void_p, P(NysOptsC), c_void_p, c_void_p, P(NysInfoC)]
+    L.nys_objective.argtypes = [c_int32, P(NysMatrixC), c_void_p, c_double, c_void_p, P(c_double), c_void_p]
+    L.nys_precond_destroy.argtypes = [c_void_p]
+    L.nys_precond_destroy.restype = None
+    for name in ("nys_hmatvec", "nys_sketch", "nys_precond_get", "nys_precond_apply", "pcg_solve",
+                 "nysadmm_solve", "nys_objective"):
+        getattr(L, name).restype = c_int32
+    _lib = L
+    return L
+
+
+def strerror(status: int) -> str:
+    return lib().nys_strerror(int(status)).decode()
+
+
+def _check(status: int, where: str, ok=(NYS_OK,)):
+    if status not in ok:
+        raise NysError(status, where)
+    return status
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else c_void_p(t.data_ptr())
+
+
+class Matrix:
+    """Row-major device matrix (n x d, leading dimension ld >= d) for the C ABI."""
+
+    def __init__(self, t: torch.Tensor, d: int | None = None):
+        if not t.is_cuda or t.dim() != 2 or t.stride(1) != 1:
+            raise ValueError("Matrix needs a 2-D CUDA tensor with unit column stride")
+        if t.dtype not in _DTYPES:
+            raise ValueError(f"unsupported dtype {t.dtype}")
+        self.tensor = t
+        self.n = t.shape[0]
+        self.d = t.shape[1] if d is None else d
+        self.ld = t.stride(0)
+        self.c = NysMatrixC(c_void_p(t.data_ptr()), _DTYPES[t.dtype], self.n, self.d, self.ld)
+
+    @property
+    def compute_dtype(self):
+        return torch.float64 if self.tensor.dtype == torch.float64 else torch.float32
+
+    @staticmethod
+    def padded(src: torch.Tensor, dtype=None) -> "Matrix":
+        """Copy src (n x d) into a row-major buffer whose rows start on 16-byte boundaries."""
+        dtype = dtype or src.dtype
+        n, d = src.shape
+        esz = torch.tensor([], dtype=dtype).element_size()
+        vec = 16 // esz
+        ld = (d + vec - 1) // vec * vec
+        buf = torch.zeros(n, ld, dtype=dtype, device=src.device)
+        buf[:, :d] = src.to(dtype)
+        return Matrix(buf, d=d)
+
+
+def _opts(stream=None, **kw) -> NysOptsC:
+    o = NysOptsC()
+    lib().nys_opts_default(ctypes.byref(o))
+    o.stream = c_void_p(_stream_ptr(stream))
+    for k, v in kw.items():
+        if v is not None:
+            setattr(o, k, v)
+    return o
+
+
+def hmatvec(A: Matrix, p: torch.Tensor, rho: float = 0.0, D: torch.Tensor | None = None,
+            stream=None) -> torch.Tensor:
+    """y = A^T diag(D) A p + rho p (Table 1 T_mv), in A's compute precision."""
+    y = torch.empty(A.d, dtype=A.compute_dtype, device=A.tensor.device)
+    p = p.to(A.compute_dtype).contiguous()
+    _check(lib().nys_hmatvec(ctypes.byref(A.c), _ptr(D), float(rho), _ptr(p), _ptr(y),
+                             c_void_p(_stream_ptr(stream))), "nys_hmatvec")
+    return y
+
+
+class Precond:
+    """Randomized Nystrom preconditioner handle (App. B; Eq. Nystrom preconditioner)."""
+
+    def __init__(self, handle: int):
+        self.h = c_void_p(handle)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None and self.h.value:
+            _lib.nys_precond_destroy(self.h)
+            self.h = c_void_p(0)
+
+    def info(self):
+        s = c_int32()
+        d = c_int64()
+        nu = c_double()
+        _check(lib().nys_precond_get(self.h, None, None, ctypes.byref(s), ctypes.byref(d), ctypes.byref(nu),
+                                     c_void_p(_stream_ptr())), "nys_precond_get")
+        return s.value, d.value, nu.value
+
+    @property
+    def lam(self) -> torch.Tensor:
+        s, _, _ = self.info()
+        out = (c_double * s)()
+        _check(lib().nys_precond_get(self.h, None, out, None, None, None, c_void_p(_stream_ptr())),
+               "nys_precond_get")
+        return torch.tensor(list(out), dtype=torch.float64)
+
+    @property
+    def nu(self) -> float:
+        return self.info()[2]
+
+    @property
+    def U(self) -> torch.Tensor:
+        s, d, _ = self.info()
+        U = torch.empty(s, d, dtype=torch.float64, device="cuda")      # column-major d x s
+        _check(lib().nys_precond_get(self.h, _ptr(U), None, None, None, None, c_void_p(_stream_ptr())),
+               "nys_precond_get")
+        return U.T
+
+    def apply(self, V: torch.Tensor, rho: float, stream=None) -> torch.Tensor:
+        """P^{-1} V for V of shape (d,) or (d, k); FP64 or FP32."""
+        squeeze = V.dim() == 1
+        Vc = V.reshape(V.shape[0], -1).T.contiguous()                  # k x d == column-major d x k
+        Y = torch.empty_like(Vc)
+        dt = NYS_F64 if V.dtype == torch.float64 else NYS_F32
+        _check(lib().nys_precond_apply(self.h, float(rho), _ptr(Vc), _ptr(Y), Vc.shape[0], dt,
+                                       c_void_p(_stream_ptr(stream))), "nys_precond_apply")
+        Y = Y.T
+        return Y.reshape(-1) if squeeze else Y
+
+
+def sketch(A: Matrix, Omega: torch.Tensor, D: torch.Tensor | None = None, diag_shift: float = 0.0,
+           shift_scale: float | None = None, stream=None) -> Precond:
+    """Nystrom sketch of H = A^T diag(D) A + diag_shift I from the Gaussian Omega (d x s)."""
+    d, s = Omega.shape
+    Om = Omega.to(torch.float64).T.contiguous()                        # column-major d x s
+    h = c_void_p()
+    o = _opts(stream, shift_scale=shift_scale)
+    _check(lib().nys_sketch(ctypes.byref(A.c), _ptr(D), float(diag_shift), s, _ptr(Om), ctypes.byref(o),
+                            ctypes.byref(h)), "nys_sketch")
+    return Precond(h.value)
+
+
+def pcg_solve(A: Matrix, r: torch.Tensor, rho: float, P: Precond | None = None, x0=None, tol: float = 1e-8,
+              tol_mode: str = "rel", maxit: int | None = None, fixed_iters: int | None = None,
+              D: torch.Tensor | None = None, stream=None, allow_noconv: bool = False):
+    """Nystrom PCG (App. B) for (A^T diag(D) A + rho I) x = r.  Returns (x, iters, ||w||)."""
+    ct = A.compute_dtype
+    r = r.to(ct).contiguous()
+    x = torch.zeros(A.d, dtype=ct, device=r.device) if x0 is None else x0.to(ct).clone().contiguous()
+    fixed = (c_int32 * 1)(fixed_iters) if fixed_iters is not None else None
+    o = _opts(stream, pcg_tol_mode=TOL_MODES[tol_mode], pcg_maxit=maxit or 0,
+              pcg_fixed_iters=ctypes.cast(fixed, POINTER(c_int32)) if fixed is not None else None)
+    it = c_int32()
+    rn = c_double()
+    st = lib().pcg_solve(ctypes.byref(A.c), _ptr(D), float(rho), P.h if P is not None else None, _ptr(r),
+                         _ptr(x), float(tol), ctypes.byref(o), ctypes.byref(it), ctypes.byref(rn))
+    _check(st, "pcg_solve", ok=(NYS_OK, NYS_ENOCONV) if allow_noconv else (NYS_OK,))
+    return x, it.value, rn.value
+
+
+def nysadmm_solve(loss: str, A: Matrix, b: torch.Tensor, gamma: float, rho: float, rank: int, tol: float,
+                  Omega: torch.Tensor, admm_iters: int = 200, A_inner: Matrix | None = None,
+                  refine: bool = True, z_trace: bool = False, pcg_fixed=None, tol_mode: str = "rel",
+                  pcg_maxit: int | None = None, eps_abs: float = 0.0, eps_rel: float = 0.0,
+                  rank_max: int | None = None, ada_tol: float | None = None, resketch_every: int = 1,
+                  shift_scale: float | None = None, stream=None, allow_noconv: bool = True) -> dict:
+    """NysADMM (Alg. NysADMM / AdaNysADMM) through the C ABI.  Returns a dict with
+    x, z (FP64 device tensors), info (dict) and, when requested, the z trace."""
+    d = A.d
+    Om = Omega.to(torch.float64).T.contiguous()                        # column-major d x s
+    x = torch.empty(d, dtype=torch.float64, device="cuda")
+    z = torch.empty(d, dtype=torch.float64, device="cuda")
+    zt = torch.empty(admm_iters, d, dtype=torch.float64, device="cuda") if z_trace else None
+    fixed = None
+    if pcg_fixed is not None:
+        seq = [int(pcg_fixed)] * admm_iters if isinstance(pcg_fixed, int) else [int(v) for v in pcg_fixed]
+        fixed = (c_int32 * len(seq))(*seq)
+    o = _opts(stream, shift_scale=shift_scale, pcg_tol_mode=TOL_MODES[tol_mode], pcg_maxit=pcg_maxit or 0,
+              pcg_fixed_iters=ctypes.cast(fixed, POINTER(c_int32)) if fixed is not None else None,
+              admm_maxit=admm_iters, eps_abs=eps_abs, eps_rel=eps_rel,
+              A_inner=ctypes.pointer(A_inner.c) if A_inner is not None else None,
+              refine=int(bool(refine)), z_trace=c_void_p(zt.data_ptr()) if zt is not None else None,
+              rank_max=rank_max or 0, ada_tol=ada_tol, resketch_every=resketch_every)
+    info = NysInfoC()
+    st = lib().nysadmm_solve(_LOSSES[loss], ctypes.byref(A.c), _ptr(b.to(torch.float64).contiguous()),
+                             float(gamma), float(rho), int(rank), float(tol), _ptr(Om), ctypes.byref(o),
+                             _ptr(x), _ptr(z), ctypes.byref(info))
+    _check(st, "nysadmm_solve", ok=(NYS_OK, NYS_ENOCONV) if allow_noconv else (NYS_OK,))
+    inf = {f: getattr(info, f) for f, _ in NysInfoC._fields_}
+    inf["status"] = st
+    out = {"x": x, "z": z, "info": inf}
+    if zt is not None:
+        out["z_trace"] = zt[: inf["admm_iters"]]
+    return out
+
+
+def objective(loss: str, A: Matrix, b: torch.Tensor, gamma: float, x: torch.Tensor, stream=None):
+    """(objective, KKT measure, duality gap) at x: Eq. (2)/(31) for the lasso, Eq. (9) for logistic."""
+    out = (c_double * 3)()
+    _check(lib().nys_objective(_LOSSES[loss], ctypes.byref(A.c), _ptr(b.to(torch.float64).contiguous()),
+                               float(gamma), _ptr(x.to(torch.float64).contiguous()), out,
+                               c_void_p(_stream_ptr(stream))), "nys_objective")
+    return out[0], out[1], out[2]

@@ -1,0 +1,64 @@
+"""CPU checks of the C ABI boundary: the library builds for sm_103a, loads,
+and exports every function that include/nysadmm.h declares.  No compute call
+is made here (there is no GPU on this host)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nysadmm.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:nys_status|void|const char\*)\s+(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2202_11599_gb300 import build_lib
+    return build_lib.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("nys_sketch", "nys_precond_apply", "pcg_solve", "nysadmm_solve"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_strerror_and_defaults_without_gpu(libpath):
+    from paper_2202_11599_gb300 import nysadmm as nx
+    assert nx.strerror(0) == "ok"
+    assert "invalid" in nx.strerror(1)
+    o = nx.NysOptsC()
+    nx.lib().nys_opts_default(ctypes.byref(o))
+    assert o.admm_maxit == 200 and o.refine == 1 and abs(o.ada_tol - 2.0) < 1e-15
+
+
+def test_struct_layouts_match_header(libpath):
+    from paper_2202_11599_gb300 import nysadmm as nx
+    # offsets follow C natural alignment of the header's structs
+    assert ctypes.sizeof(nx.NysMatrixC) == 40
+    assert nx.NysOptsC.stream.offset == 96 and ctypes.sizeof(nx.NysOptsC) == 104
+    assert ctypes.sizeof(nx.NysInfoC) == 48
+
+
+def test_invalid_arguments_rejected_before_any_launch(libpath):
+    from paper_2202_11599_gb300 import nysadmm as nx
+    L = nx.lib()
+    # NULL matrix / bad shapes are rejected on the host, no CUDA call needed
+    assert L.nys_hmatvec(None, None, 0.0, None, None, None) == nx.NYS_EINVAL
+    m = nx.NysMatrixC(ctypes.c_void_p(16), nx.NYS_F64, 10, 0, 10)
+    assert L.nys_hmatvec(ctypes.byref(m), None, 0.0, None, None, None) == nx.NYS_EINVAL
+    m = nx.NysMatrixC(ctypes.c_void_p(16), nx.NYS_F64, 10, 5, 5)       # 5*8 bytes: not 16-aligned rows
+    assert L.nys_hmatvec(ctypes.byref(m), None, 0.0, ctypes.c_void_p(16), ctypes.c_void_p(32), None) == nx.NYS_EINVAL

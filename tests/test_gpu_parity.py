@@ -1,0 +1,316 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  Tolerances:
+  * FP64 storage: 1e-10 relative (spec bar for the plain FP64 form);
+    single kernels 1e-12 relative to the |A|^T|A||p| scale.
+  * FP32 / BF16 storage: the reference is computed in FP64 from the SAME stored
+    values; the kernel accumulates in FP32, so the bound is ~ (row length) * 2^-24
+    relative to the absolute-value product; 2e-5 is used.
+"""
+import numpy as np
+import pytest
+import torch
+
+import nys_inputs as gen
+import oracle.nysadmm_oracle as o
+
+pytestmark = pytest.mark.gpu
+
+nx = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    global nx
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2202_11599_gb300 import nysadmm
+    nx = nysadmm
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _quantised(A, dtype):
+    """Stored values of A in `dtype`, returned as FP64 numpy (exactly representable)."""
+    return torch.from_numpy(A).to(dtype).to(torch.float64).numpy()
+
+
+SHAPES = [(1000, 300), (777, 129), (3, 5), (5000, 1001), (2, 2000), (1, 17), (4097, 64)]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("n,d", SHAPES)
+def test_hmatvec_matches_definition(dtype, n, d):
+    rng = np.random.default_rng(n * 131 + d)
+    A = rng.standard_normal((n, d)) * gen.column_scales(d, 0.5)[None, :]
+    Aq = _quantised(A, dtype)
+    p = rng.standard_normal(d)
+    Dv = rng.random(n) + 0.1
+    rho = 0.37
+    M = nx.Matrix.padded(_dev(A), dtype)
+    ct = M.compute_dtype
+    pq = torch.from_numpy(p).to(ct).double().numpy()
+    for D in (None, Dv):
+        y = nx.hmatvec(M, _dev(pq), rho, None if D is None else _dev(D)).double().cpu().numpy()
+        w = np.ones(n) if D is None else D
+        ref = Aq.T @ (w * (Aq @ pq)) + rho * pq
+        scale = np.abs(Aq).T @ (w * (np.abs(Aq) @ np.abs(pq))) + rho * np.abs(pq)
+        tol = 1e-12 if dtype == torch.float64 else 2e-5
+        assert np.max(np.abs(y - ref) / (scale + 1e-300)) <= tol
+
+
+def test_hmatvec_deterministic():
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((20000, 700))
+    M = nx.Matrix.padded(_dev(A), torch.float32)
+    p = _dev(rng.standard_normal(700).astype(np.float32))
+    y1 = nx.hmatvec(M, p, 0.5)
+    y2 = nx.hmatvec(M, p, 0.5)
+    assert torch.equal(y1, y2)
+
+
+def _small_problem(n=600, d=150, s=20, seed=3):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, d)) * gen.column_scales(d, 1.0)[None, :]
+    Om = gen.gaussian_test_matrix(d, s, seed)
+    return A, Om
+
+
+@pytest.mark.parametrize("s", [20, 1, 7])
+def test_sketch_parity_fp64(s):
+    A, Om = _small_problem(s=s)
+    d = A.shape[1]
+    H = A.T @ A
+    U, lam, nu, Q, _ = o.nystrom(lambda X: H @ X, Om, shift_scale=np.sqrt(d))
+    P = nx.sketch(nx.Matrix.padded(_dev(A)), _dev(Om))
+    lam_g = P.lam.numpy()
+    Ug = P.U.cpu().numpy()
+    assert abs(np.log2(P.nu / nu)) <= 1.0          # same exponent up to the power-iteration estimate
+    assert np.max(np.abs(lam_g - lam)) <= 1e-10 * lam[0]
+    Hg = (Ug * lam_g) @ Ug.T
+    assert np.linalg.norm(Hg - (U * lam) @ U.T, 2) <= 1e-10 * lam[0]
+    rng = np.random.default_rng(1)
+    V = rng.standard_normal((d, 3))
+    for rho in (1.0, 1e-3):
+        Yg = P.apply(_dev(V), rho).cpu().numpy()
+        for j in range(3):
+            ref = o.precond_apply(U, lam, rho, V[:, j])
+            assert np.linalg.norm(Yg[:, j] - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_sketch_exact_low_rank():
+    A = gen.low_rank_matrix(300, 60, 5, 11)
+    Om = gen.gaussian_test_matrix(60, 12, 11)
+    P = nx.sketch(nx.Matrix.padded(_dev(A)), _dev(Om))
+    lam = P.lam.numpy()
+    ev = np.sort(np.linalg.eigvalsh(A.T @ A))[::-1]
+    assert np.allclose(lam[:5], ev[:5], rtol=1e-9)
+    assert np.all(lam[5:] <= 1e-9 * ev[0])
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_sketch_low_precision_storage(dtype):
+    A, Om = _small_problem(n=2000, d=256, s=24)
+    Aq = _quantised(A, dtype)
+    d = A.shape[1]
+    U, lam, nu, _, _ = o.nystrom(lambda X: Aq.T @ (Aq @ X), Om, shift_scale=np.sqrt(d), mantissa_bits=23)
+    P = nx.sketch(nx.Matrix.padded(_dev(A), dtype), _dev(Om))
+    lam_g = P.lam.numpy()
+    # FP32 sketch of the stored matrix: eigenvalues to ~1e-5 of the largest
+    assert np.max(np.abs(lam_g - lam)) <= 2e-5 * lam[0]
+
+
+def test_sketch_with_weights_and_shift():
+    A, Om = _small_problem(n=500, d=80, s=10, seed=9)
+    Dv = np.random.default_rng(9).random(500) + 0.05
+    H = A.T @ (Dv[:, None] * A) + 0.3 * np.eye(80)
+    U, lam, _, _, _ = o.nystrom(lambda X: H @ X, Om, shift_scale=np.sqrt(80))
+    P = nx.sketch(nx.Matrix.padded(_dev(A)), _dev(Om), D=_dev(Dv), diag_shift=0.3)
+    assert np.max(np.abs(P.lam.numpy() - lam)) <= 1e-10 * lam[0]
+
+
+@pytest.mark.parametrize("k", [1, 4, 9])
+def test_pcg_fixed_iterations_match_oracle(k):
+    A, Om = _small_problem()
+    d = A.shape[1]
+    H = A.T @ A
+    rho = 0.05
+    U, lam, _, _, _ = o.nystrom(lambda X: H @ X, Om, shift_scale=np.sqrt(d))
+    rng = np.random.default_rng(k)
+    r = rng.standard_normal(d)
+    x0 = rng.standard_normal(d)
+    xr, _, _ = o.pcg(lambda v: H @ v, rho, U, lam, r, x0, 0.0, fixed_iters=k)
+    M = nx.Matrix.padded(_dev(A))
+    P = nx.sketch(M, _dev(Om))
+    xg, it, _ = nx.pcg_solve(M, _dev(r), rho, P, x0=_dev(x0), fixed_iters=k)
+    assert it == k
+    assert np.linalg.norm(xg.cpu().numpy() - xr) <= 1e-10 * np.linalg.norm(xr)
+
+
+def test_pcg_converges_to_direct_solve():
+    A, Om = _small_problem(n=900, d=200, s=30, seed=4)
+    H = A.T @ A
+    rho = 1e-3
+    r = np.random.default_rng(0).standard_normal(200)
+    ref = np.linalg.solve(H + rho * np.eye(200), r)
+    M = nx.Matrix.padded(_dev(A))
+    P = nx.sketch(M, _dev(Om))
+    xg, it, rn = nx.pcg_solve(M, _dev(r), rho, P, tol=1e-12)
+    assert np.linalg.norm(xg.cpu().numpy() - ref) <= 1e-9 * np.linalg.norm(ref)
+    # plain CG (no preconditioner) needs more iterations on this decaying spectrum
+    xc, itc, _ = nx.pcg_solve(M, _dev(r), rho, None, tol=1e-12, maxit=2000)
+    assert itc > it
+    assert np.linalg.norm(xc.cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_pcg_one_iteration_when_exact():
+    A = gen.low_rank_matrix(200, 50, 4, 2)
+    Om = gen.gaussian_test_matrix(50, 9, 2)
+    M = nx.Matrix.padded(_dev(A))
+    P = nx.sketch(M, _dev(Om))
+    r = np.random.default_rng(2).standard_normal(50)
+    _, it, _ = nx.pcg_solve(M, _dev(r), 0.7, P, tol=1e-9)
+    assert it == 1
+
+
+def test_pcg_zero_iterations_and_maxit():
+    A, Om = _small_problem(n=300, d=60, s=6)
+    M = nx.Matrix.padded(_dev(A))
+    P = nx.sketch(M, _dev(Om))
+    r = _dev(np.zeros(60))
+    _, it, rn = nx.pcg_solve(M, r, 1.0, P, tol=1e-8)
+    assert it == 0 and rn == 0.0
+    rr = _dev(np.random.default_rng(1).standard_normal(60))
+    with pytest.raises(nx.NysError) as e:
+        nx.pcg_solve(M, rr, 1e-6, None, tol=1e-15, maxit=3)
+    assert e.value.status == nx.NYS_ENOCONV
+
+
+def test_lasso_trajectory_parity_fp64():
+    """The 2,000 x 500 FP64 lasso, rank 50, rho 1, 200 ADMM iterations: the oracle
+    runs PCG to rel-tol 1e-8; the GPU replays the oracle's per-iteration PCG
+    counts, so both follow the same trajectory and x must agree to 1e-10."""
+    p = gen.lasso_small(0)
+    Om = gen.gaussian_test_matrix(500, 50, 0)
+    ref = o.lasso_nysadmm(p.A, p.b, p.gamma, p.rho, Om, 200, pcg_tol=1e-8)
+    M = nx.Matrix.padded(_dev(p.A))
+    out = nx.nysadmm_solve("lasso", M, _dev(p.b), p.gamma, p.rho, 50, 1e-8, _dev(Om), admm_iters=200,
+                           pcg_fixed=ref["trace"]["pcg_iters"], z_trace=True)
+    x = out["x"].cpu().numpy()
+    z = out["z"].cpu().numpy()
+    assert np.linalg.norm(x - ref["x"]) <= 1e-10 * np.linalg.norm(ref["x"])
+    assert np.linalg.norm(z - ref["z"]) <= 1e-10 * np.linalg.norm(ref["z"])
+    zt = out["z_trace"].cpu().numpy()
+    assert np.linalg.norm(zt[57] - ref["trace"]["z"][57]) <= 1e-10 * np.linalg.norm(ref["trace"]["z"][57])
+    assert out["info"]["admm_iters"] == 200
+    assert out["info"]["pcg_iters_total"] == sum(ref["trace"]["pcg_iters"])
+    assert out["info"]["r_p"] == pytest.approx(ref["trace"]["r_p"][-1], rel=1e-6)
+
+
+def test_lasso_tolerance_mode_runs_and_converges():
+    p = gen.lasso_problem(800, 120, nnz=10, seed=21)
+    Om = gen.gaussian_test_matrix(120, 20, 21)
+    ref = o.lasso_nysadmm(p.A, p.b, p.gamma, 10.0, Om, 400, pcg_tol=1e-12)
+    M = nx.Matrix.padded(_dev(p.A))
+    out = nx.nysadmm_solve("lasso", M, _dev(p.b), p.gamma, 10.0, 20, 1e-12, _dev(Om), admm_iters=400)
+    z = out["z"].cpu().numpy()
+    assert np.linalg.norm(z - ref["z"]) <= 1e-9 * np.linalg.norm(ref["z"])
+    F, eta, gap = nx.objective("lasso", M, _dev(p.b), p.gamma, out["z"])
+    assert F == pytest.approx(o.lasso_objective(p.A, p.b, p.gamma, z), rel=1e-12)
+    assert eta == pytest.approx(o.lasso_kkt_eta(p.A, p.b, p.gamma, z), rel=1e-6, abs=1e-15)
+    assert gap == pytest.approx(o.lasso_dual_gap(p.A, p.b, p.gamma, z), rel=1e-6, abs=1e-9)
+    assert eta < 1e-10
+
+
+def test_lasso_residual_stop():
+    p = gen.lasso_problem(600, 90, nnz=8, seed=22)
+    Om = gen.gaussian_test_matrix(90, 15, 22)
+    M = nx.Matrix.padded(_dev(p.A))
+    out = nx.nysadmm_solve("lasso", M, _dev(p.b), p.gamma, 10.0, 15, 1e-10, _dev(Om), admm_iters=500,
+                           eps_abs=0.0, eps_rel=1e-4)
+    ref = o.lasso_nysadmm(p.A, p.b, p.gamma, 10.0, Om, 500, pcg_tol=1e-10, eps_abs=0.0, eps_rel=1e-4)
+    assert out["info"]["admm_iters"] == len(ref["trace"]["pcg_iters"]) < 500
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float32])
+def test_lasso_mixed_precision_reaches_fp64_solution(dtype):
+    """Mixed form: sketch and PCG on the low-precision copy, FP64 residual
+    correction with the FP64 matrix each x-step.  Its fixed point is the FP64
+    problem's solution: compare with the oracle's FP64 solution."""
+    p = gen.lasso_problem(3000, 400, nnz=20, gamma_frac=0.1, seed=23)
+    Om = gen.gaussian_test_matrix(400, 40, 23)
+    ref = o.lasso_nysadmm(p.A, p.b, p.gamma, 10.0, Om, 600, pcg_tol=1e-12)
+    M = nx.Matrix.padded(_dev(p.A))
+    Mi = nx.Matrix.padded(_dev(p.A), dtype)
+    out = nx.nysadmm_solve("lasso", M, _dev(p.b), p.gamma, 10.0, 40, 1e-6, _dev(Om), admm_iters=600,
+                           A_inner=Mi, refine=True)
+    z = out["z"].cpu().numpy()
+    F = o.lasso_objective(p.A, p.b, p.gamma, z)
+    Fr = o.lasso_objective(p.A, p.b, p.gamma, ref["z"])
+    assert (F - Fr) / Fr <= 1e-9
+    assert np.linalg.norm(z - ref["z"]) <= 1e-6 * np.linalg.norm(ref["z"])
+
+
+def test_logistic_trajectory_parity():
+    p = gen.logistic_problem(3000, 100, decay=0.5, nnz=5, seed=24)
+    pool = gen.gaussian_test_matrix(100, 40, 24)
+    gamma = 0.02 * np.max(np.abs(p.A.T @ (0.5 - 0.5 * (1 + p.b))))
+    ref = o.logistic_nysadmm(p.A, p.b, gamma, 1.0, pool, 40, s0=10, s_max=40, ada_tol=1.05, pcg_tol=1e-10)
+    M = nx.Matrix.padded(_dev(p.A))
+    out = nx.nysadmm_solve("logistic", M, _dev(p.b), gamma, 1.0, 10, 1e-10, _dev(pool), admm_iters=40,
+                           pcg_fixed=ref["trace"]["pcg_iters"], rank_max=40, ada_tol=1.05, resketch_every=1)
+    assert out["info"]["final_rank"] == ref["rank"]
+    x = out["x"].cpu().numpy()
+    assert np.linalg.norm(x - ref["x"]) <= 1e-9 * np.linalg.norm(ref["x"])
+    F, g, _ = nx.objective("logistic", M, _dev(p.b), gamma, out["z"])
+    assert F == pytest.approx(o.logistic_objective(p.A, p.b, gamma, out["z"].cpu().numpy()), rel=1e-12)
+
+
+def test_invalid_arguments():
+    A, Om = _small_problem(n=100, d=20, s=4)
+    M = nx.Matrix.padded(_dev(A))
+    with pytest.raises(nx.NysError) as e:
+        nx.sketch(M, _dev(gen.gaussian_test_matrix(20, 21, 0)))      # s > d
+    assert e.value.status == nx.NYS_EINVAL
+    with pytest.raises(nx.NysError):
+        nx.pcg_solve(M, _dev(np.ones(20)), 0.0)                       # rho <= 0
+    with pytest.raises(nx.NysError):
+        nx.nysadmm_solve("lasso", M, _dev(np.ones(100)), -1.0, 1.0, 4, 1e-8, _dev(Om))
+    # a matrix whose rows are not 16-byte aligned is rejected
+    bad = torch.zeros(10, 5, dtype=torch.float64, device="cuda")
+    with pytest.raises(nx.NysError):
+        nx.hmatvec(nx.Matrix(bad), torch.zeros(5, dtype=torch.float64, device="cuda"))
+    # dependent test-matrix columns are rejected by the thin QR
+    Omd = np.repeat(Om[:, :1], 4, axis=1)
+    with pytest.raises(nx.NysError):
+        nx.sketch(M, _dev(Omd))
+
+
+def test_full_size_bf16_hmatvec_sampled():
+    """The 100,000 x 10,000 rotated BF16 lasso matrix: one fused pass, checked on
+    64 sampled outputs computed one by one in FP64 from the stored BF16 values."""
+    n, d = 100_000, 10_000
+    W = gen.lasso_large_torch(n, d, seed=1)
+    Abf = W["A32"].to(torch.bfloat16)
+    del W
+    M = nx.Matrix(Abf)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    p = torch.randn(d, generator=g, device="cuda", dtype=torch.float32)
+    y = nx.hmatvec(M, p, 0.5).double()
+    cols = torch.randperm(d, generator=g, device="cuda")[:64]
+    t = torch.zeros(n, dtype=torch.float64, device="cuda")
+    yref = torch.zeros(64, dtype=torch.float64, device="cuda")
+    scale = torch.zeros(64, dtype=torch.float64, device="cuda")
+    pd = p.double()
+    for r0 in range(0, n, 10_000):
+        blk = Abf[r0:r0 + 10_000].double()
+        tb = blk @ pd
+        t[r0:r0 + 10_000] = tb
+        yref += blk[:, cols].T @ tb
+        scale += blk[:, cols].abs().T @ (blk.abs() @ pd.abs())
+    yref += 0.5 * pd[cols]
+    err = ((y[cols] - yref).abs() / scale).max().item()
+    assert err <= 2e-5
