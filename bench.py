@@ -1,0 +1,473 @@
+#!/usr/bin/env python
+"""Benchmark: NysADMM lasso on one GB300 -- time to a 1e-6 relative objective gap.
+
+Workload (default, "lasso_100000x10000_bf16"): A = G diag((1+j)^-1) Q^T with
+G ~ N(0,1)^{100000 x 10000} and Q a random orthogonal matrix, stored in BF16 (the
+copy the sketch and PCG read) with its exact FP64 widening as the problem
+matrix; x* 1% sparse N(0,1), b = A x* + 1e-3 N(0,1), gamma = 0.05 ||A^T b||_inf,
+Nystrom rank 200, rho = 100 (chosen by a sweep; the configuration does not fix
+rho).  One step = one full solve through the C ABI: sketch + FP64 Nystrom core +
+k* ADMM iterations, where k* is the first iteration whose z reaches
+(F(z) - F*)/F* <= 1e-6 on the FP64 objective (calibrated before timing).
+
+Default run: N = 1 GPU, 3 warm-up and 3 timed steps.  Inputs (2 GB BF16 +
+8 GB FP64) are far larger than the 129 MB L2, so no flush is needed.
+`--impl reference` times the FP64 NumPy oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import nys_inputs as gen  # noqa: E402
+
+METRIC = "time to 1e-6 rel. objective gap (s); A-matvec HBM GB/s vs plain FP64 GPU form"
+GAP = 1e-6
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- workload
+
+def make_workload(device="cuda"):
+    n, d, s = 100_000, 10_000, 200
+    W = gen.lasso_large_torch(n, d, nnz_frac=0.01, noise=1e-3, gamma_frac=0.05, seed=1, device=device)
+    g = torch.Generator(device=device).manual_seed(11)
+    Om = torch.randn(d, s, generator=g, device=device, dtype=torch.float64)
+    return {"n": n, "d": d, "s": s, "rho": 100.0, "pcg_tol": 1e-4, "pcg_tol_fp64": 1e-8,
+            "A32": W["A32"], "b": W["b"], "gamma": W["gamma"], "Omega": Om}
+
+
+WORKLOAD_NAME = "lasso_100000x10000_bf16"
+
+
+def workload_config(w):
+    return {"workload": WORKLOAD_NAME, "n": w["n"], "d": w["d"], "rank": w["s"], "rho": w["rho"],
+            "gamma": "0.05*||A^T b||_inf", "A_storage": "bf16 (PCG + sketch), f64 (problem, A^T b)",
+            "pcg": f"f32, rel-tol {w['pcg_tol']:g}, warm start x_prev",
+            "decay": "(1+j)^-1, rotated", "x_star": "1% sparse", "noise": 1e-3, "seed": 1,
+            "gap": GAP, "l2_flush": "inputs (10 GB) larger than L2 (129 MB)"}
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    from paper_2202_11599_gb300 import nysadmm as nx
+    import __graft_entry__
+    __graft_entry__.build()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = make_workload()
+    A64 = w["A32"].double()
+    Abf = w["A32"].to(torch.bfloat16)
+    M64, Mbf = nx.Matrix(A64), nx.Matrix(Abf)
+    b, gamma, Om, rho, s = w["b"], w["gamma"], w["Omega"], w["rho"], w["s"]
+
+    def F(z):
+        return nx.objective("lasso", M64, b, gamma, z)[0]
+
+    def solve_mixed(iters, trace=False):
+        return nx.nysadmm_solve("lasso", M64, b, gamma, rho, s, w["pcg_tol"], Om, admm_iters=iters,
+                                A_inner=Mbf, refine=False, z_trace=trace)
+
+    def solve_plain(iters, trace=False):
+        return nx.nysadmm_solve("lasso", M64, b, gamma, rho, s, w["pcg_tol_fp64"], Om, admm_iters=iters,
+                                z_trace=trace)
+
+    t0 = time.time()
+    Fstar = None
+    if not (args.admm_iters and args.no_check):
+        # --- F*: FP64-exact refined run (PCG on the FP32 copy, FP64 residual correction each x-step)
+        A32m = nx.Matrix(w["A32"])
+        ref = nx.nysadmm_solve("lasso", M64, b, gamma, rho, s, 1e-6, Om, admm_iters=args.fstar_iters,
+                               A_inner=A32m, refine=True, z_trace=True)
+        zt = ref["z_trace"]
+        ks = list(range(max(0, zt.shape[0] - 400), zt.shape[0], 10)) + [zt.shape[0] - 1]
+        Fstar = min(F(zt[k]) for k in ks)
+        del ref, zt
+
+    def kstar(out):
+        zt = out["z_trace"]
+        K = zt.shape[0]
+        coarse = list(range(9, K, 10))
+        for k in coarse:
+            if (F(zt[k]) - Fstar) / Fstar <= GAP:
+                for kk in range(max(0, k - 9), k + 1):
+                    if (F(zt[kk]) - Fstar) / Fstar <= GAP:
+                        return kk
+        return None
+
+    if args.admm_iters:
+        iters = args.admm_iters
+    else:
+        cal = solve_mixed(args.cal_iters, trace=True)
+        k_mixed = kstar(cal)
+        del cal
+        if k_mixed is None:
+            raise RuntimeError("mixed form did not reach the 1e-6 gap within the calibration budget")
+        iters = k_mixed + 1
+    setup_s = time.time() - t0
+
+    # --- warm-up
+    for _ in range(args.warmup):
+        solve_mixed(iters)
+    torch.cuda.synchronize()
+
+    # --- timed region
+    sampler = ClockSampler(local)
+    sampler.start()
+    nx.stats_enable(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    per_step = []
+    e0.record(stream)
+    last = None
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        c = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        last = solve_mixed(iters)
+        c.record(stream)
+        per_step.append((a, c))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    stats = nx.stats_read()
+    nx.stats_enable(False)
+    clocks = sampler.stop()
+    total_ms = e0.elapsed_time(e1)
+    step_ms = [a.elapsed_time(c) for a, c in per_step]
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    gap_final = (F(last["z"]) - Fstar) / Fstar if Fstar is not None else None
+    info = last["info"]
+
+    # --- roofline of the dominant kernel (fused BF16 A-pass), from the timed region
+    peaks, peak_src = measured_peaks()
+    ap = stats["apass"]["bf16"]
+    mean_ms = ap["ms"] / max(1, ap["launches"])
+    bytes_per = ap["bytes"] / max(1, ap["launches"])
+    achieved = bytes_per / (mean_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": args.traffic,
+                "kernel": "apass_kernel<BF16> (fused y = A^T (A p) + rho p)", "peak_source": peak_src,
+                "launches": ap["launches"], "mean_launch_ms": round(mean_ms, 4),
+                "algorithmic_bytes_per_launch": bytes_per}
+    f64p = stats["apass"]["f64"]
+
+    result = {
+        "metric": METRIC, "value": round(total_ms / args.steps / 1e3, 5), "unit": "s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded; the paper's datasets are not available offline)",
+        "config": dict(workload_config(w), admm_iters_to_gap=iters, pcg_iters_per_solve=info["pcg_iters_total"],
+                       final_gap=gap_final, F_star=Fstar, emp_cond=info["emp_cond"],
+                       step_ms=[round(x, 3) for x in step_ms], parallelism="replicas" if world > 1 else "single"),
+        "roofline": roofline,
+        "gpu_launches": stats["launches"],
+        "clocks": clocks,
+    }
+    if f64p["launches"]:
+        result["config"]["f64_rhs_pass_ms"] = round(f64p["ms"] / f64p["launches"], 4)
+
+    if rank == 0 and not args.no_plain and Fstar is not None:
+        result["plain_fp64"] = plain_fp64(nx, solve_plain, F, Fstar, args)
+        if result["plain_fp64"].get("time_s"):
+            result["plain_fp64"]["speedup_mixed_vs_plain"] = round(result["plain_fp64"]["time_s"] / result["value"], 2)
+
+    if rank == 0 and not args.no_e2e:
+        result["e2e"] = e2e(nx, w, A64, Abf, iters, min(2, args.steps))
+
+    if rank == 0 and not args.no_cpu:
+        k_for_cpu = result.get("plain_fp64", {}).get("admm_iters_to_gap") or iters
+        result["cpu_baseline"] = cpu_baseline(w, A64, k_for_cpu, args.cpu_iters)
+    result["config"]["setup_s"] = round(setup_s, 1)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def plain_fp64(nx, solve_plain, F, Fstar, args):
+    """The plain FP64 GPU form on the same problem: FP64 sketch, FP64 PCG (rel-tol 1e-8)."""
+    out = solve_plain(args.cal_iters_fp64, trace=True)
+    zt = out["z_trace"]
+    k = None
+    for kk in range(9, zt.shape[0], 10):
+        if (F(zt[kk]) - Fstar) / Fstar <= GAP:
+            k = next(j for j in range(max(0, kk - 9), kk + 1) if (F(zt[j]) - Fstar) / Fstar <= GAP)
+            break
+    del out, zt
+    if k is None:
+        return {"admm_iters_to_gap": None, "note": "did not reach the gap within the calibration budget"}
+    nx.stats_enable(True)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    c = torch.cuda.Event(enable_timing=True)
+    a.record()
+    solve_plain(k + 1)
+    c.record()
+    torch.cuda.synchronize()
+    st = nx.stats_read()
+    nx.stats_enable(False)
+    ap = st["apass"]["f64"]
+    mean_ms = ap["ms"] / max(1, ap["launches"])
+    gbs = ap["bytes"] / max(1, ap["launches"]) / (mean_ms * 1e-3) / 1e9
+    return {"time_s": round(a.elapsed_time(c) / 1e3, 4), "admm_iters_to_gap": k + 1,
+            "apass_f64_GBps": round(gbs, 1), "apass_f64_mean_ms": round(mean_ms, 4),
+            "note": "FP64 A-pass is bound by the FP64 FMA rate (~1.2 TFLOP/s measured), not HBM"}
+
+
+def e2e(nx, w, A64, Abf, iters, steps):
+    """Same metric through the C ABI with the inputs in pinned host memory: every step
+    copies A (BF16 and FP64), b and Omega host->device, solves, and reads z back."""
+    h_A64 = torch.empty_like(A64, device="cpu").pin_memory()
+    h_A64.copy_(A64)
+    h_Abf = torch.empty_like(Abf, device="cpu").pin_memory()
+    h_Abf.copy_(Abf)
+    h_b = w["b"].cpu().pin_memory()
+    h_Om = w["Omega"].cpu().pin_memory()
+    d_A64 = torch.empty_like(A64)
+    d_Abf = torch.empty_like(Abf)
+    d_b = torch.empty_like(w["b"])
+    d_Om = torch.empty_like(w["Omega"])
+    h_z = torch.empty(w["d"], dtype=torch.float64).pin_memory()
+    times = []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        c = torch.cuda.Event(enable_timing=True)
+        a.record()
+        d_A64.copy_(h_A64, non_blocking=True)
+        d_Abf.copy_(h_Abf, non_blocking=True)
+        d_b.copy_(h_b, non_blocking=True)
+        d_Om.copy_(h_Om, non_blocking=True)
+        out = nx.nysadmm_solve("lasso", nx.Matrix(d_A64), d_b, w["gamma"], w["rho"], w["s"], w["pcg_tol"], d_Om,
+                               admm_iters=iters, A_inner=nx.Matrix(d_Abf), refine=False)
+        h_z.copy_(out["z"], non_blocking=True)
+        c.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(c))
+    h2d = h_A64.numel() * 8 + h_Abf.numel() * 2 + h_b.numel() * 8 + h_Om.numel() * 8
+    return {"value": round(statistics.mean(times) / 1e3, 5), "unit": "s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(h_z.numel() * 8), "steps": steps}
+
+
+def cpu_baseline(w, A64, k_iters, sample_iters):
+    """The FP64 oracle on the host cores, on a bounded sample of the same workload:
+    the sketch plus `sample_iters` ADMM iterations are timed; the time to the gap
+    is scaled as t_sketch + k_iters * t_iter (k_iters = ADMM iterations the FP64
+    algorithm needs on this workload)."""
+    import oracle.nysadmm_oracle as o
+    A = A64.cpu().numpy()
+    b = w["b"].cpu().numpy()
+    Om = w["Omega"].cpu().numpy()
+    cores = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    U, lam, nu, _, _ = o.nystrom(lambda X: A.T @ (A @ X), Om, shift_scale=math.sqrt(w["d"]))
+    t_sketch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.lasso_nysadmm(A, b, w["gamma"], w["rho"], Om, sample_iters, pcg_tol=w["pcg_tol_fp64"], precond=(U, lam, nu))
+    t_iters = time.perf_counter() - t0
+    per_iter = t_iters / sample_iters
+    value = t_sketch + k_iters * per_iter
+    return {"value": round(value, 2), "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle sketch ({t_sketch:.1f} s) + {sample_iters} ADMM iterations ({t_iters:.1f} s) on the "
+                      f"full 100000x10000 FP64 problem; time to gap = t_sketch + {k_iters} x t_iter"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The FP64 NumPy oracle timed on the host cores (rank 0 only), same workload and metric."""
+    import oracle.nysadmm_oracle as o
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = make_workload("cuda" if torch.cuda.is_available() else "cpu")
+    A = w["A32"].double().cpu().numpy()
+    b = w["b"].cpu().numpy()
+    Om = w["Omega"].cpu().numpy()
+    del w["A32"]
+    n, d = A.shape
+    cores = len(os.sched_getaffinity(0))
+    # iterations to the gap for the FP64 algorithm: the oracle on the exact Gram-reduced form
+    # (A^T A = R^T R, A^T b = R^T b'), whose ADMM iterates are those of the full problem
+    t0 = time.perf_counter()
+    G = A.T @ A
+    R = np.linalg.cholesky(G).T
+    q = A.T @ b
+    bp = np.linalg.solve(R.T, q)
+    const = 0.5 * float(b @ b) - 0.5 * float(bp @ bp)
+    out = o.lasso_nysadmm(R, bp, w["gamma"], w["rho"], Om, args.ref_cal_iters, pcg_tol=w["pcg_tol_fp64"])
+    Fk = [o.lasso_objective(R, bp, w["gamma"], z) + const for z in out["trace"]["z"]]
+    Fstar = min(Fk)
+    k_iters = next((k + 1 for k, f in enumerate(Fk) if (f - Fstar) / Fstar <= GAP), len(Fk))
+    cal_s = time.perf_counter() - t0
+    vals = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        U, lam, nu, _, _ = o.nystrom(lambda X: A.T @ (A @ X), Om, shift_scale=math.sqrt(d))
+        t_sketch = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        o.lasso_nysadmm(A, b, w["gamma"], w["rho"], Om, args.cpu_iters, pcg_tol=w["pcg_tol_fp64"],
+                        precond=(U, lam, nu))
+        per_iter = (time.perf_counter() - t0) / args.cpu_iters
+        if step >= args.warmup:
+            vals.append(t_sketch + k_iters * per_iter)
+    value = statistics.mean(vals)
+    sample = (f"per step: oracle sketch + {args.cpu_iters} ADMM iterations on the full FP64 problem, "
+              f"scaled to {k_iters} iterations (found by the oracle on the Gram-reduced form in {cal_s:.0f} s)")
+    res = {"metric": METRIC, "value": round(value, 3), "unit": "s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value * 1e3, 1),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded)", "impl": "reference",
+           "config": dict(workload_config(w), admm_iters_to_gap=k_iters, F_star=Fstar),
+           "cpu_baseline": {"value": round(value, 3), "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 3), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+
+
+def profile_apass(dt):
+    """Small ncu case: the fused A-pass y = A^T (A p) + rho p on a 50000 x 10000 matrix
+    (1 GB in BF16, larger than L2): 2 warm-up launches, then 6 timed launches."""
+    from paper_2202_11599_gb300 import nysadmm as nx
+    import __graft_entry__
+    __graft_entry__.build()
+    n, d = 50_000, 10_000
+    g = torch.Generator(device="cuda").manual_seed(3)
+    A = torch.randn(n, d, generator=g, device="cuda", dtype=torch.float32)
+    A = A.to({"bf16": torch.bfloat16, "f32": torch.float32, "f64": torch.float64}[dt])
+    M = nx.Matrix(A)
+    p = torch.randn(d, generator=g, device="cuda", dtype=M.compute_dtype)
+    for _ in range(2):                       # module load / first-launch costs stay out of the mean
+        y = nx.hmatvec(M, p, 1.0)
+    torch.cuda.synchronize()
+    nx.stats_enable(True)
+    for _ in range(6):
+        y = nx.hmatvec(M, p, 1.0)
+    torch.cuda.synchronize()
+    st = nx.stats_read()["apass"][dt]
+    ms = st["ms"] / st["launches"]
+    print(json.dumps({"profile_apass": dt, "n": n, "d": d, "mean_ms": ms,
+                      "GBps": st["bytes"] / st["launches"] / (ms * 1e-3) / 1e9, "y0": float(y[0])}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fstar-iters", type=int, default=1500)
+    ap.add_argument("--cal-iters", type=int, default=1500)
+    ap.add_argument("--cal-iters-fp64", type=int, default=1200)
+    ap.add_argument("--cpu-iters", type=int, default=3)
+    ap.add_argument("--ref-cal-iters", type=int, default=1200)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per A-pass launch (from a committed profile), if current")
+    ap.add_argument("--admm-iters", type=int, default=0,
+                    help="use this ADMM iteration count instead of calibrating it (profiling runs)")
+    ap.add_argument("--no-check", action="store_true", help="skip F* and the final gap check (profiling runs)")
+    ap.add_argument("--profile-apass", choices=["bf16", "f32", "f64"], default=None,
+                    help="only run the fused A-pass on a 50000 x 10000 matrix (ncu capture case)")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.profile_apass:
+        profile_apass(args.profile_apass)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -172,6 +172,25 @@ nys_status nysadmm_solve(int32_t loss, const nys_matrix* A, const double* b, dou
 nys_status nys_objective(int32_t loss, const nys_matrix* A, const double* b, double gamma,
                          const double* x, double* out, void* stream);
 
+/* Instrumentation (no counterpart in the paper; used to report measured
+ * bandwidth).  nys_stats_enable(1) resets the counters and starts recording:
+ * every kernel launch of the library is counted, and each fused A-pass launch
+ * (the H-matvec / right-hand-side pass) is bracketed by CUDA events on the
+ * stream it runs on.  nys_stats_read waits for the recorded events and fills
+ * *out (host).  apass_bytes is the algorithmic traffic of those launches:
+ * n*d*sizeof(element) for A plus the vectors read and the partials written. */
+typedef struct {
+  int64_t launches;           /* kernel launches since the last enable */
+  int64_t apass_launches[3];  /* fused A-pass launches that ran (a launch issued after
+                                 PCG converged returns at once and is not counted),
+                                 by nys_dtype of A */
+  double apass_ms[3];         /* summed device time of those launches (ms) */
+  double apass_bytes[3];      /* summed algorithmic bytes of those launches */
+} nys_stats;
+
+void nys_stats_enable(int32_t on);
+nys_status nys_stats_read(nys_stats* out);
+
 void nys_precond_destroy(nys_precond P);
 const char* nys_strerror(int32_t status);
 

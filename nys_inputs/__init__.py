@@ -132,6 +132,21 @@ def low_rank_matrix(n: int, d: int, r: int, seed: int) -> np.ndarray:
 # Large workloads generated on the GPU with torch (data only).
 # ---------------------------------------------------------------------------
 
+def _preload_torch_linalg():
+    """torch loads its CUDA linear-algebra library lazily by name; under a profiler
+    that changes the library search path this fails, so load it by full path."""
+    import ctypes
+    import os
+
+    import torch
+    path = os.path.join(os.path.dirname(torch.__file__), "lib", "libtorch_cuda_linalg.so")
+    if os.path.exists(path):
+        try:
+            ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+        except OSError:
+            pass
+
+
 def lasso_large_torch(n: int, d: int, *, nnz_frac: float = 0.01, noise: float = 1e-3,
                       gamma_frac: float = 0.05, seed: int = 1, rotate: bool = True,
                       device: str = "cuda"):
@@ -144,6 +159,7 @@ def lasso_large_torch(n: int, d: int, *, nnz_frac: float = 0.01, noise: float = 
     Returns dict with A32 (n,d) fp32, b (n,) fp64, x_true (d,) fp64, gamma.
     """
     import torch
+    _preload_torch_linalg()
     g = torch.Generator(device=device)
     g.manual_seed(seed)
     prev = torch.backends.cuda.matmul.allow_tf32

@@ -23,6 +23,7 @@
 #include "nys_internal.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 
 namespace nys {
 
@@ -46,6 +47,7 @@ struct ApassKArgs {
   double* loss_part;
   int* status;
   const int* skip;
+  int* executed;  // instrumentation: set to 1 by CTA 0 when the pass ran (not skipped)
 };
 
 __device__ __forceinline__ double sigmoid_d(double t) {
@@ -71,6 +73,7 @@ __global__ void __launch_bounds__(kApassThreads, 1) apass_kernel(const ApassKArg
   __shared__ C red[2][NW][kRMax];
 
   if (a.skip && *a.skip) return;
+  if (a.executed && blockIdx.x == 0 && threadIdx.x == 0) *a.executed = 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t nvec = (a.d + VEC - 1) / VEC;
   const int64_t rowbytes = a.ld * ESZ;
@@ -251,6 +254,258 @@ __global__ void __launch_bounds__(kApassThreads, 1) apass_kernel(const ApassKArg
   if (tid == 0 && a.loss_part) a.loss_part[blockIdx.x] = loss;
 }
 
+// Float-compute variant (FP32 / BF16 storage).  Same streaming scheme, tuned for
+// the instruction budget of a bandwidth-bound pass:
+//   * the R rows of a stage are loaded from shared memory ONCE into registers (raw
+//     16-byte vectors) and reused by both the dot product and the rank-1 update, so a
+//     stage can be refilled by TMA as soon as every thread has loaded it (all S stages
+//     stay in flight);
+//   * dot products and updates use the packed FP32 FMA (two lanes per instruction);
+//   * the row sums are finished by one warp per row (two barriers per step instead of
+//     every thread re-reading all warp partials).
+template <int DT>
+__device__ __forceinline__ float2 unpack_pair(const uint4& r, int q);
+template <>
+__device__ __forceinline__ float2 unpack_pair<NYS_F32>(const uint4& r, int q) {
+  return q == 0 ? make_float2(__uint_as_float(r.x), __uint_as_float(r.y))
+                : make_float2(__uint_as_float(r.z), __uint_as_float(r.w));
+}
+template <>
+__device__ __forceinline__ float2 unpack_pair<NYS_BF16>(const uint4& r, int q) {
+  const unsigned w = q == 0 ? r.x : (q == 1 ? r.y : (q == 2 ? r.z : r.w));
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+
+// Zero the stored elements of a 16-byte vector from element index `keep` on.
+template <int DT>
+__device__ __forceinline__ void mask_tail(uint4& r, int keep) {
+  constexpr int ESZ = Stor<DT>::ESZ;
+  unsigned* w = reinterpret_cast<unsigned*>(&r);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int first = i * 4 / ESZ;  // first element index held by word i
+    if (ESZ == 4) {
+      if (first >= keep) w[i] = 0u;
+    } else {  // two 16-bit elements per word
+      if (first >= keep) w[i] = 0u;
+      else if (first + 1 >= keep) w[i] &= 0x0000ffffu;
+    }
+  }
+}
+
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(addr));
+  return v;
+}
+
+// Row modes of the pass, applied by the warp that finishes row i: returns u_i.
+__device__ __forceinline__ float row_phi(const ApassKArgs& a, int64_t i, float t, double& loss) {
+  switch (a.mode) {
+    case MODE_CONST: return (float)a.b[i];
+    case MODE_ID: return t;
+    case MODE_DIAG: return (float)(a.D[i] * (double)t);
+    case MODE_RESID: {
+      const double rr = (double)t - a.b[i];
+      loss += 0.5 * rr * rr;
+      return (float)rr;
+    }
+    case MODE_LGRAD: {
+      const double td = (double)t;
+      const double sg = sigmoid_d(td);
+      const double b01 = 0.5 * (1.0 + a.b[i]);
+      loss += fmax(td, 0.0) + log1p(exp(-fabs(td))) - b01 * td;
+      return (float)(sg - b01);
+    }
+    default: {  // MODE_LOGIT
+      const double td = (double)t;
+      const double sg = sigmoid_d(td);
+      const double wv = sg * (1.0 - sg);
+      const double b01 = 0.5 * (1.0 + a.b[i]);
+      if (a.D_out) a.D_out[i] = wv;
+      loss += fmax(td, 0.0) + log1p(exp(-fabs(td))) - b01 * td;
+      return (float)(wv * td + b01 - sg);
+    }
+  }
+}
+
+// Float-compute kernel.  Per step of R rows: every thread loads its slice of the
+// stage from shared memory ONCE into registers (raw 16-byte vectors), forms its
+// partial row dots with packed FP32 FMAs, and after the first barrier the stage is
+// refilled by TMA at once (all S stages stay in flight); warps 0..R-1 finish the row
+// sums and apply phi; after the second barrier every thread applies the rank-R
+// update from the same registers.
+template <int DT, int VPT, int R>
+__global__ void __launch_bounds__(kApassThreads, 1) apass_f_kernel(const ApassKArgs a) {
+  constexpr int VEC = Stor<DT>::VEC;
+  constexpr int ESZ = Stor<DT>::ESZ;
+  constexpr int NP = VEC / 2;
+  constexpr int T = kApassThreads;
+  constexpr int NW = T / 32;
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[kMaxStages];
+  __shared__ float red[2][NW][R];
+  __shared__ float us[2][R];
+  __shared__ double lsh[NW];
+
+  if (a.skip && *a.skip) return;
+  if (a.executed && blockIdx.x == 0 && threadIdx.x == 0) *a.executed = 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nvec = (int)((a.d + VEC - 1) / VEC);
+  const uint32_t rowbytes = (uint32_t)(a.ld * ESZ);
+  const int S = a.S;
+  const uint32_t stage_bytes = (uint32_t)R * rowbytes;
+  const int64_t r0 = a.n * (int64_t)blockIdx.x / gridDim.x;
+  const int64_t r1 = a.n * (int64_t)(blockIdx.x + 1) / gridDim.x;
+  const int nsteps = (int)((r1 - r0 + R - 1) / R);
+  const int tail_vec = (int)(a.d / VEC);
+  const int tail_n = (int)(a.d % VEC);
+  const bool nodot = a.mode == MODE_CONST;
+  const uint32_t sbase = smem_u32(smem);
+
+  const float* p = reinterpret_cast<const float*>(a.p);
+  float2 pr[VPT][NP], acc[VPT][NP];
+#pragma unroll
+  for (int kk = 0; kk < VPT; ++kk) {
+    const int64_t v = tid + (int64_t)kk * T;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const int64_t j = v * VEC + 2 * q;
+      float x0 = 0.f, x1 = 0.f;
+      if (!nodot && v < nvec) {
+        if (j < a.d) x0 = p[j];
+        if (j + 1 < a.d) x1 = p[j + 1];
+      }
+      pr[kk][q] = make_float2(x0, x1);
+      acc[kk][q] = make_float2(0.f, 0.f);
+    }
+  }
+
+  if (tid == 0) {
+    for (int st = 0; st < S; ++st) mbar_init(&bars[st], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto issue = [&](int step) {
+    const int stage = step % S;
+    const int64_t row = r0 + (int64_t)step * R;
+    const int rows = (int)min((int64_t)R, r1 - row);
+    const uint32_t bytes = (uint32_t)rows * rowbytes;
+    mbar_arrive_expect_tx(&bars[stage], bytes);
+    tma_load_1d(smem + (size_t)stage * stage_bytes, a.A + row * (int64_t)rowbytes, bytes, &bars[stage]);
+  };
+  int issued = 0;
+  if (tid == 0) {
+    for (int st = 0; st < S && st < nsteps; ++st) issue(st);
+    issued = min(S, nsteps);
+  }
+
+  double loss = 0.0;
+  bool aborted = false;
+  int k = 0;
+  for (; k < nsteps; ++k) {
+    const int stage = k % S;
+    const uint32_t sb = sbase + (uint32_t)stage * stage_bytes;
+    const int rows_here = (int)min((int64_t)R, r1 - (r0 + (int64_t)k * R));
+    const bool ok = mbar_wait_bounded(&bars[stage], (uint32_t)((k / S) & 1));
+
+    uint4 raw[R][VPT];
+    float2 dacc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) dacc[r] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int kk = 0; kk < VPT; ++kk) {
+      const int v = tid + kk * T;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        uint4 x = make_uint4(0u, 0u, 0u, 0u);
+        if (ok && v < nvec && r < rows_here) x = lds128(sb + (uint32_t)r * rowbytes + (uint32_t)v * 16u);
+        if (v == tail_vec) mask_tail<DT>(x, tail_n);
+        raw[r][kk] = x;
+        if (!nodot) {
+#pragma unroll
+          for (int q = 0; q < NP; ++q) dacc[r] = __ffma2_rn(unpack_pair<DT>(x, q), pr[kk][q], dacc[r]);
+        }
+      }
+    }
+    if (!nodot) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float sdot = warp_sum(dacc[r].x + dacc[r].y);
+        if (lane == 0) red[k & 1][warp][r] = sdot;
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      break;
+    }
+    // every thread holds its slice of this stage in registers: refill it now
+    if (tid == 0 && k + S < nsteps) {
+      issue(k + S);
+      ++issued;
+    }
+    if (warp < R) {
+      float t = 0.f;
+      if (!nodot) t = warp_sum(lane < NW ? red[k & 1][lane][warp] : 0.f);
+      if (lane == 0) {
+        float u = 0.f;
+        if (warp < rows_here) {
+          const int64_t i = r0 + (int64_t)k * R + warp;
+          u = row_phi(a, i, t, loss);
+          if (!nodot && a.t_out) a.t_out[i] = (double)t;
+        }
+        us[k & 1][warp] = u;
+      }
+    }
+    __syncthreads();
+    float2 u2[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float u = us[k & 1][r];
+      u2[r] = make_float2(u, u);
+    }
+#pragma unroll
+    for (int kk = 0; kk < VPT; ++kk) {
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[kk][q] = __ffma2_rn(unpack_pair<DT>(raw[r][kk], q), u2[r], acc[kk][q]);
+      }
+    }
+  }
+
+  if (aborted) {
+    if (tid == 0) {
+      for (int st = k; st < issued; ++st) (void)mbar_wait_bounded(&bars[st % S], (uint32_t)((st / S) & 1));
+      atomicExch(a.status, (int)NYS_ETIMEOUT);
+    }
+    return;
+  }
+
+  float* part = reinterpret_cast<float*>(a.partial) + (int64_t)blockIdx.x * a.dpad;
+#pragma unroll
+  for (int kk = 0; kk < VPT; ++kk) {
+    const int64_t v = tid + (int64_t)kk * T;
+    if (v < nvec) {
+#pragma unroll
+      for (int q = 0; q < NP; ++q) *reinterpret_cast<float2*>(part + v * VEC + 2 * q) = acc[kk][q];
+    }
+  }
+  if (a.loss_part) {
+    if (lane == 0) lsh[warp] = loss;
+    __syncthreads();
+    if (tid == 0) {
+      double sl = 0.0;
+      for (int w = 0; w < NW; ++w) sl += lsh[w];
+      a.loss_part[blockIdx.x] = sl;
+    }
+  }
+}
+
 // y_j = sum_g partial[g][j] (fixed order) + rho p_j; optional per-block partials of p^T y.
 template <typename C>
 __global__ void __launch_bounds__(kVecThreads) apass_reduce_kernel(const C* __restrict__ partial, int G,
@@ -307,6 +562,17 @@ bool apass_plan(const nys_matrix* A, ApassPlan* plan) {
   if (A->dtype == NYS_F64 && vpt > 12) return false;
   const int64_t rowbytes = A->ld * esz;
   int R = (int)std::max<int64_t>(1, std::min<int64_t>(kRMax, (48 * 1024) / rowbytes));
+  if (A->dtype != NYS_F64) {
+    // float path: R is a template parameter bounded by the register budget of raw[R][VPT]
+    R = vpt <= 3 ? 4 : (vpt <= 6 ? 2 : 1);
+    // tuning override (rows per stage), e.g. NYS_APASS_ROWS=2; kept only if the
+    // register-bounded instantiation exists for this width
+    if (const char* env = std::getenv("NYS_APASS_ROWS")) {
+      const int r = std::atoi(env);
+      if ((r == 1) || (r == 2 && vpt <= 6) || (r == 4 && vpt <= 3)) R = r;
+    }
+    while (R > 1 && 2 * R * rowbytes > kSmemBudget) R /= 2;
+  }
   int S = (int)std::min<int64_t>(kMaxStages, kSmemBudget / (R * rowbytes));
   if (S < 2) {
     R = 1;
@@ -336,8 +602,52 @@ static cudaError_t launch_vpt(const ApassKArgs& k, const ApassPlan& plan, cudaSt
     NYS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
     attr_set = true;
   }
+  count_launch();
   fn<<<plan.grid, kApassThreads, plan.smem, st>>>(k);
   return cudaGetLastError();
+}
+
+template <int DT, int VPT, int R>
+static cudaError_t launch_f(const ApassKArgs& k, const ApassPlan& plan, cudaStream_t st) {
+  auto fn = apass_f_kernel<DT, VPT, R>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    NYS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+    attr_set = true;
+  }
+  count_launch();
+  fn<<<plan.grid, kApassThreads, plan.smem, st>>>(k);
+  return cudaGetLastError();
+}
+
+template <int DT, int VPT>
+static cudaError_t launch_fr(const ApassKArgs& k, const ApassPlan& plan, cudaStream_t st) {
+  switch (plan.rows_per_step) {
+    case 4: if constexpr (VPT <= 3) return launch_f<DT, VPT, 4>(k, plan, st); break;
+    case 2: if constexpr (VPT <= 6) return launch_f<DT, VPT, 2>(k, plan, st); break;
+    case 1: return launch_f<DT, VPT, 1>(k, plan, st);
+    default: break;
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int DT>
+static cudaError_t launch_float(const ApassKArgs& k, const ApassPlan& plan, cudaStream_t st) {
+  constexpr int VEC = Stor<DT>::VEC;
+  const int64_t nvec = (k.d + VEC - 1) / VEC;
+  switch (vpt_bucket(nvec)) {
+    case 1: return launch_fr<DT, 1>(k, plan, st);
+    case 2: return launch_fr<DT, 2>(k, plan, st);
+    case 3: return launch_fr<DT, 3>(k, plan, st);
+    case 4: return launch_fr<DT, 4>(k, plan, st);
+    case 5: return launch_fr<DT, 5>(k, plan, st);
+    case 6: return launch_fr<DT, 6>(k, plan, st);
+    case 8: return launch_fr<DT, 8>(k, plan, st);
+    case 10: return launch_fr<DT, 10>(k, plan, st);
+    case 12: return launch_fr<DT, 12>(k, plan, st);
+    case 16: return launch_fr<DT, 16>(k, plan, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <int DT>
@@ -381,22 +691,43 @@ cudaError_t apass_run(const ApassArgs& a, const ApassPlan& plan, void* partial, 
   k.loss_part = loss_part;
   k.status = dev_status;
   k.skip = a.skip;
-  switch (a.dtype) {
-    case NYS_F64: return launch_dt<NYS_F64>(k, plan, st);
-    case NYS_F32: return launch_dt<NYS_F32>(k, plan, st);
-    case NYS_BF16: return launch_dt<NYS_BF16>(k, plan, st);
-    default: return cudaErrorInvalidValue;
+  k.executed = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int* flag = nullptr;
+  const bool prof = stats_enabled() && stats_event_pair(&e0, &e1, &flag) == cudaSuccess;
+  if (prof) {
+    k.executed = flag;
+    NYS_CUDA_TRY(cudaEventRecord(e0, st));
   }
+  cudaError_t err;
+  switch (a.dtype) {
+    case NYS_F64: err = launch_dt<NYS_F64>(k, plan, st); break;
+    case NYS_F32: err = launch_float<NYS_F32>(k, plan, st); break;
+    case NYS_BF16: err = launch_float<NYS_BF16>(k, plan, st); break;
+    default: err = cudaErrorInvalidValue;
+  }
+  if (prof && err == cudaSuccess) {
+    NYS_CUDA_TRY(cudaEventRecord(e1, st));
+    // algorithmic bytes: A read once, p read, partials written, per-row vectors touched
+    const double esz = (double)dtype_size(a.dtype), csz = compute_is_f64(a.dtype) ? 8.0 : 4.0;
+    double bytes = (double)a.n * (double)a.d * esz + (double)a.d * csz + (double)plan.grid * a.d * csz;
+    if (a.mode == MODE_DIAG || a.mode == MODE_RESID || a.mode == MODE_CONST) bytes += 8.0 * a.n;
+    if (a.mode == MODE_LOGIT || a.mode == MODE_LGRAD) bytes += 16.0 * a.n;
+    stats_record_apass(e0, e1, bytes, a.dtype, flag);
+  }
+  return err;
 }
 
 cudaError_t apass_reduce(const ApassArgs& a, const ApassPlan& plan, const void* partial, double rho,
                          void* y, double* dot_part, int dot_blocks, cudaStream_t st) {
   const int nb = dot_blocks > 0 ? dot_blocks : reduce_blocks(a.d);
   if (compute_is_f64(a.dtype)) {
+    count_launch();
     apass_reduce_kernel<double><<<nb, kVecThreads, 0, st>>>(
         reinterpret_cast<const double*>(partial), plan.grid, a.d, plan.dpad, rho,
         reinterpret_cast<const double*>(a.p), reinterpret_cast<double*>(y), dot_part, a.skip);
   } else {
+    count_launch();
     apass_reduce_kernel<float><<<nb, kVecThreads, 0, st>>>(
         reinterpret_cast<const float*>(partial), plan.grid, a.d, plan.dpad, (float)rho,
         reinterpret_cast<const float*>(a.p), reinterpret_cast<float*>(y), dot_part, a.skip);

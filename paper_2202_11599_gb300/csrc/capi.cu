@@ -835,8 +835,10 @@ nys_status nys_objective(int32_t loss, const nys_matrix* A, const double* b, dou
   double lossv = 0.0;
   NYS_TRY(aux_pass(A, loss == NYS_LASSO ? MODE_RESID : MODE_LGRAD, xa, b, nullptr, t, ytmp, &lossv, st));
   NYS_TRY(to_f64(A, ytmp, g, d, st));
+  count_launch();
   obj_vec_kernel<<<nbd, kVecThreads, 0, st>>>(d, x, g, gamma, p4);
   NYS_CU(cudaGetLastError());
+  count_launch();
   obj_row_kernel<<<nbn, kVecThreads, 0, st>>>(n, t, b, p2);
   NYS_CU(cudaGetLastError());
   std::vector<double> h4((size_t)nbd * 4), h2((size_t)nbn * 2);

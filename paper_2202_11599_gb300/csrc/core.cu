@@ -100,8 +100,10 @@ cudaError_t gram_xty(const double* X, const double* Y, int64_t d, int s, double*
   const int64_t kc = gram_kchunk(d);
   const int nz = (int)((d + kc - 1) / kc);
   dim3 grid((s + GT - 1) / GT, (s + GT - 1) / GT, nz);
+  count_launch();
   gemm_f64_kernel<<<grid, 256, 0, st>>>(X, d, true, Y, d, s, s, d, kc, work);
   NYS_CUDA_TRY(cudaGetLastError());
+  count_launch();
   sum_partials_kernel<<<std::min<int64_t>(1024, ((int64_t)s * s + 255) / 256), 256, 0, st>>>(work, nz,
                                                                                               (int64_t)s * s, C);
   return cudaGetLastError();
@@ -110,6 +112,7 @@ cudaError_t gram_xty(const double* X, const double* Y, int64_t d, int s, double*
 // C (d x s) = B (d x s) * V (s x s), all column-major
 static cudaError_t gemm_nn(const double* B, int64_t d, int s, const double* V, double* C, cudaStream_t st) {
   dim3 grid((unsigned)((d + GT - 1) / GT), (s + GT - 1) / GT, 1);
+  count_launch();
   gemm_f64_kernel<<<grid, 256, 0, st>>>(B, d, false, V, s, (int)d, s, s, s, C);
   return cudaGetLastError();
 }
@@ -163,6 +166,7 @@ __global__ void __launch_bounds__(1024) chol_upper_kernel(double* M, int s, int*
 }
 
 cudaError_t chol_upper(double* M, int s, int* info, cudaStream_t st) {
+  count_launch();
   chol_upper_kernel<<<1, 1024, 0, st>>>(M, s, info);
   return cudaGetLastError();
 }
@@ -181,6 +185,7 @@ __global__ void trsm_ru_kernel(const double* __restrict__ Cm, int s, double* Y, 
 }
 
 cudaError_t trsm_right_upper(const double* C, int s, double* Y, int64_t d, cudaStream_t st) {
+  count_launch();
   trsm_ru_kernel<<<(unsigned)((d + 127) / 128), 128, 0, st>>>(C, s, Y, d);
   return cudaGetLastError();
 }
@@ -191,6 +196,7 @@ __global__ void axpy_kernel(double a, const double* __restrict__ x, double* __re
 }
 
 cudaError_t axpy_panel(double nu, const double* X, double* Y, int64_t n, cudaStream_t st) {
+  count_launch();
   axpy_kernel<<<(unsigned)std::min<int64_t>(4096, (n + 255) / 256), 256, 0, st>>>(nu, X, Y, n);
   return cudaGetLastError();
 }
@@ -244,6 +250,7 @@ __global__ void __launch_bounds__(512) power_kernel(const double* __restrict__ G
 
 cudaError_t power_lambda_max(const double* G, int s, double* out, double* work, cudaStream_t st) {
   if (s > 1024) return cudaErrorInvalidValue;
+  count_launch();
   power_kernel<<<1, 512, 0, st>>>(G, s, 60, out, work);
   return cudaGetLastError();
 }
@@ -367,6 +374,7 @@ cudaError_t jacobi_eig(double* G, double* Vout, int s, double* work, int* sweeps
   double* A1 = work + (size_t)N * N;
   int* done = reinterpret_cast<int*>(work + (size_t)3 * N * N);
   double* offv = work + (size_t)3 * N * N + 1;
+  count_launch();
   jacobi_setup_kernel<<<std::max(1, std::min(1024, (N * N + 255) / 256)), 256, 0, st>>>(G, s, A0, Vout, N, done);
   NYS_CUDA_TRY(cudaGetLastError());
   const int64_t total = (int64_t)(N / 2) * (N / 2) + (int64_t)N * (N / 2);
@@ -379,10 +387,12 @@ cudaError_t jacobi_eig(double* G, double* Vout, int s, double* work, int* sweeps
   for (; sweeps < kMaxSweeps; ++sweeps) {
     if (N <= 2 && sweeps > 0) break;
     for (int r = 0; r < N - 1; ++r) {
+      count_launch();
       jacobi_round_kernel<<<blocks, 256, 0, st>>>(cur, nxt, Vout, N, r, done);
       std::swap(cur, nxt);
     }
     NYS_CUDA_TRY(cudaGetLastError());
+    count_launch();
     jacobi_offnorm_kernel<<<1, 256, 0, st>>>(cur, N, 1e-28, done, offv);
     NYS_CUDA_TRY(cudaMemcpyAsync(&done_h, done, sizeof(int), cudaMemcpyDeviceToHost, st));
     NYS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -443,9 +453,11 @@ cudaError_t nystrom_finish(const double* B, int64_t d, int s, const double* Ad, 
   double* Vs = work;
   double* sig2 = work + (size_t)s * s;
   const size_t sm = (size_t)N * sizeof(double) + (size_t)N * sizeof(int);
+  count_launch();
   eig_sort_kernel<<<1, 512, sm, st>>>(Ad, V, N, s, Vs, sig2);
   NYS_CUDA_TRY(cudaGetLastError());
   NYS_CUDA_TRY(gemm_nn(B, d, s, Vs, U, st));
+  count_launch();
   finish_scale_kernel<<<(unsigned)std::min<int64_t>(4096, (d * s + 255) / 256), 256, 0, st>>>(U, d, s, sig2, nu,
                                                                                               lam);
   return cudaGetLastError();
@@ -594,12 +606,15 @@ cudaError_t sketch_aw(const nys_matrix* A, const void* Omega, int s, const doubl
   const unsigned char* Ar = reinterpret_cast<const unsigned char*>(A->data);
   switch (A->dtype) {
     case NYS_F64:
+      count_launch();
       sketch_aw_kernel<NYS_F64><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const double*)Omega, s, D, (double*)W);
       break;
     case NYS_F32:
+      count_launch();
       sketch_aw_kernel<NYS_F32><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const float*)Omega, s, D, (float*)W);
       break;
     case NYS_BF16:
+      count_launch();
       sketch_aw_kernel<NYS_BF16><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const float*)Omega, s, D, (float*)W);
       break;
     default: return cudaErrorInvalidValue;
@@ -618,18 +633,24 @@ cudaError_t sketch_atw(const nys_matrix* A, const void* W, int s, double* Y, voi
   const unsigned rb = (unsigned)std::min<int64_t>(4096, (len + 255) / 256);
   switch (A->dtype) {
     case NYS_F64:
+      count_launch();
       sketch_atw_kernel<NYS_F64><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const double*)W, s, kc, (double*)work);
       NYS_CUDA_TRY(cudaGetLastError());
+      count_launch();
       sum_partials_to_f64_kernel<double><<<rb, 256, 0, st>>>((const double*)work, nz, len, Y);
       break;
     case NYS_F32:
+      count_launch();
       sketch_atw_kernel<NYS_F32><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const float*)W, s, kc, (float*)work);
       NYS_CUDA_TRY(cudaGetLastError());
+      count_launch();
       sum_partials_to_f64_kernel<float><<<rb, 256, 0, st>>>((const float*)work, nz, len, Y);
       break;
     case NYS_BF16:
+      count_launch();
       sketch_atw_kernel<NYS_BF16><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const float*)W, s, kc, (float*)work);
       NYS_CUDA_TRY(cudaGetLastError());
+      count_launch();
       sum_partials_to_f64_kernel<float><<<rb, 256, 0, st>>>((const float*)work, nz, len, Y);
       break;
     default: return cudaErrorInvalidValue;
@@ -648,11 +669,13 @@ __global__ void f32_to_f64_kernel(const float* __restrict__ x, double* __restric
 }
 cudaError_t convert_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  count_launch();
   f64_to_f32_kernel<<<(unsigned)std::min<int64_t>(4096, (n + 255) / 256), 256, 0, st>>>(x, y, n);
   return cudaGetLastError();
 }
 cudaError_t convert_f32_to_f64(const float* x, double* y, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  count_launch();
   f32_to_f64_kernel<<<(unsigned)std::min<int64_t>(4096, (n + 255) / 256), 256, 0, st>>>(x, y, n);
   return cudaGetLastError();
 }

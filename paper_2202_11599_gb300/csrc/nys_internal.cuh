@@ -92,6 +92,14 @@ size_t sketch_atw_work_bytes(const nys_matrix* A, int s);
 cudaError_t convert_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t st);
 cudaError_t convert_f32_to_f64(const float* x, double* y, int64_t n, cudaStream_t st);
 
+// Instrumentation (nys_stats_* in the C ABI): every kernel launch is counted; the
+// fused A-pass launches are bracketed by CUDA events on their stream when enabled.
+void count_launch();
+bool stats_enabled();
+void stats_record_apass(cudaEvent_t start, cudaEvent_t stop, double bytes, int dtype, int* executed);
+// An event pair plus a zeroed device flag that the pass sets when it runs.
+cudaError_t stats_event_pair(cudaEvent_t* start, cudaEvent_t* stop, int** executed);
+
 inline size_t dtype_size(int dt) { return dt == NYS_F64 ? 8 : (dt == NYS_F32 ? 4 : 2); }
 inline bool compute_is_f64(int dt) { return dt == NYS_F64; }
 

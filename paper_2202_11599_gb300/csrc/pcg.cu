@@ -134,7 +134,10 @@ __global__ void __launch_bounds__(kVecThreads) pcg_scalar_kernel(int init, int n
       st->iters = 0;
     } else {
       if (!(pv > 0.0) || !isfinite(pv) || !isfinite(w2)) {
-        st->status = NYS_EBREAKDOWN;
+        // First iteration: H + rho I is not positive definite on p (a bad input).
+        // Later: the recursion has reached the rounding floor of the compute type;
+        // the current x (from the previous iteration) is kept and reported unconverged.
+        st->status = st->iters == 0 ? NYS_EBREAKDOWN : NYS_ENOCONV;
         st->done = 1;
       } else {
         st->wy = wy;
@@ -260,6 +263,7 @@ nys_status pcg_run(const PcgProblem& pb, const PrecondView& P, const C* r, C* x,
     if (e != cudaSuccess) return NYS_ECUDA; \
   } while (0)
 
+  count_launch();
   pcg_reset_kernel<<<1, 1, 0, stream>>>(st, prm.tol, prm.tol_abs, prm.maxit, prm.fixed, prm.dev_tol);
   LAUNCH_OK(cudaGetLastError());
   const C* v0 = nullptr;
@@ -269,14 +273,18 @@ nys_status pcg_run(const PcgProblem& pb, const PrecondView& P, const C* r, C* x,
     LAUNCH_OK(apass_reduce(aa, pb.plan, apart, pb.rho, v, nullptr, 0, stream));
     v0 = v;
   }
+  count_launch();
   pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, stream>>>(1, d, chunk, x, w, r, v0, p, U, s, pv_part, nbr,
                                                              wy_part, nb5, part_w2, part_r2, part_g, st);
   LAUNCH_OK(cudaGetLastError());
+  count_launch();
   pcg_scalar_kernel<C><<<1, kVecThreads, 0, stream>>>(1, nb3, part_w2, part_r2, part_g, s, cvec, gs, pv_part, nbr,
                                                       wy_part, nb5, st);
   LAUNCH_OK(cudaGetLastError());
+  count_launch();
   pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, stream>>>(d, w, y, U, s, gs, wy_part, st);
   LAUNCH_OK(cudaGetLastError());
+  count_launch();
   pcg_pupdate_kernel<C><<<nb5, kVecThreads, 0, stream>>>(1, d, y, p, wy_part, nb5, st);
   LAUNCH_OK(cudaGetLastError());
 
@@ -289,14 +297,18 @@ nys_status pcg_run(const PcgProblem& pb, const PrecondView& P, const C* r, C* x,
       aa.p = p;
       LAUNCH_OK(apass_run(aa, pb.plan, apart, nullptr, dstat, stream));
       LAUNCH_OK(apass_reduce(aa, pb.plan, apart, pb.rho, v, pv_part, nbr, stream));
+      count_launch();
       pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, stream>>>(0, d, chunk, x, w, r, v, p, U, s, pv_part, nbr,
                                                                  wy_part, nb5, part_w2, part_r2, part_g, st);
       LAUNCH_OK(cudaGetLastError());
+      count_launch();
       pcg_scalar_kernel<C><<<1, kVecThreads, 0, stream>>>(0, nb3, part_w2, part_r2, part_g, s, cvec, gs, pv_part,
                                                           nbr, wy_part, nb5, st);
       LAUNCH_OK(cudaGetLastError());
+      count_launch();
       pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, stream>>>(d, w, y, U, s, gs, wy_part, st);
       LAUNCH_OK(cudaGetLastError());
+      count_launch();
       pcg_pupdate_kernel<C><<<nb5, kVecThreads, 0, stream>>>(0, d, y, p, wy_part, nb5, st);
       LAUNCH_OK(cudaGetLastError());
     }
@@ -338,16 +350,21 @@ nys_status precond_apply_run(const PrecondView& P, int64_t d, const C* V, C* Y, 
   PcgState* st = pool.alloc<PcgState>(1);
   if (!pool.ok()) return NYS_ENOMEM;
   for (int64_t c = 0; c < k; ++c) {
+    count_launch();
     pcg_reset_kernel<<<1, 1, 0, stream>>>(st, 0.0, 1, 1, -1, nullptr);
     // init-mode update copies V[:, c] into w and forms the partials of U^T w
+    count_launch();
     pcg_update_kernel<C><<<nb3, kVecThreads, (size_t)chunk * sizeof(C), stream>>>(
         1, d, chunk, nullptr, w, V + c * d, nullptr, nullptr, reinterpret_cast<const C*>(P.U), s, nullptr, 0,
         nullptr, 0, part_w2, part_r2, part_g, st);
+    count_launch();
     pcg_scalar_kernel<C><<<1, kVecThreads, 0, stream>>>(1, nb3, part_w2, part_r2, part_g, s,
                                                         reinterpret_cast<const C*>(P.c), gs, nullptr, 0, nullptr, 0,
                                                         st);
     // the scalar kernel may mark the state done (||w|| <= 0 threshold); force the tail to run
+    count_launch();
     pcg_reset_kernel<<<1, 1, 0, stream>>>(st, 0.0, 1, 1, -1, nullptr);
+    count_launch();
     pcg_tail_kernel<C><<<nb5, kVecThreads, (size_t)std::max(1, s) * sizeof(C), stream>>>(
         d, w, Y + c * d, reinterpret_cast<const C*>(P.U), s, gs, wy_part, st);
     if (cudaGetLastError() != cudaSuccess) return NYS_ECUDA;
@@ -439,6 +456,7 @@ int admm_blocks(int64_t d) { return reduce_blocks(d); }
 template <typename C>
 cudaError_t admm_rhs(int64_t d, const double* q, const double* z, const double* u, double rho, const double* x,
                      const double* yres, C* r, cudaStream_t st) {
+  count_launch();
   admm_rhs_kernel<C><<<admm_blocks(d), kVecThreads, 0, st>>>(d, q, z, u, rho, x, yres, r);
   return cudaGetLastError();
 }
@@ -450,6 +468,7 @@ template cudaError_t admm_rhs<float>(int64_t, const double*, const double*, cons
 template <typename C>
 cudaError_t admm_zu(int64_t d, const C* xc, int accumulate, double* x, double* z, double* u, double kappa,
                     double* ztrace, double* part5, cudaStream_t st) {
+  count_launch();
   admm_zu_kernel<C><<<admm_blocks(d), kVecThreads, 0, st>>>(d, xc, accumulate, x, z, u, kappa, ztrace, part5);
   return cudaGetLastError();
 }
@@ -460,6 +479,7 @@ template cudaError_t admm_zu<float>(int64_t, const float*, int, double*, double*
 
 cudaError_t admm_scalar(int64_t d, const double* part5, double rho, int k, double* rp, double* rd, double* eps_next,
                         double eps_abs, double eps_rel, int* stop, cudaStream_t st) {
+  count_launch();
   admm_scalar_kernel<<<1, 32, 0, st>>>(admm_blocks(d), part5, rho, k, rp, rd, eps_next, eps_abs, eps_rel, stop);
   return cudaGetLastError();
 }

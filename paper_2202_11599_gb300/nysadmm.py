@@ -43,6 +43,11 @@ class NysInfoC(ctypes.Structure):
                 ("nu", c_double)]
 
 
+class NysStatsC(ctypes.Structure):
+    _fields_ = [("launches", c_int64), ("apass_launches", c_int64 * 3), ("apass_ms", c_double * 3),
+                ("apass_bytes", c_double * 3)]
+
+
 class NysError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -75,10 +80,13 @@ def lib() -> ctypes.CDLL:
     L.nysadmm_solve.argtypes = [c_int32, P(NysMatrixC), c_void_p, c_double, c_double, c_int32, c_double,
                                 c_void_p, P(NysOptsC), c_void_p, c_void_p, P(NysInfoC)]
     L.nys_objective.argtypes = [c_int32, P(NysMatrixC), c_void_p, c_double, c_void_p, P(c_double), c_void_p]
+    L.nys_stats_enable.argtypes = [c_int32]
+    L.nys_stats_enable.restype = None
+    L.nys_stats_read.argtypes = [POINTER(NysStatsC)]
     L.nys_precond_destroy.argtypes = [c_void_p]
     L.nys_precond_destroy.restype = None
     for name in ("nys_hmatvec", "nys_sketch", "nys_precond_get", "nys_precond_apply", "pcg_solve",
-                 "nysadmm_solve", "nys_objective"):
+                 "nysadmm_solve", "nys_objective", "nys_stats_read"):
         getattr(L, name).restype = c_int32
     _lib = L
     return L
@@ -278,3 +286,18 @@ def objective(loss: str, A: Matrix, b: torch.Tensor, gamma: float, x: torch.Tens
                                float(gamma), _ptr(x.to(torch.float64).contiguous()), out,
                                c_void_p(_stream_ptr(stream))), "nys_objective")
     return out[0], out[1], out[2]
+
+
+def stats_enable(on: bool = True) -> None:
+    """Reset and (de)activate the library's launch counter and A-pass event timing."""
+    lib().nys_stats_enable(int(bool(on)))
+
+
+def stats_read() -> dict:
+    """Kernel launches and A-pass device time / algorithmic bytes since stats_enable."""
+    s = NysStatsC()
+    _check(lib().nys_stats_read(ctypes.byref(s)), "nys_stats_read")
+    names = {NYS_F64: "f64", NYS_F32: "f32", NYS_BF16: "bf16"}
+    return {"launches": s.launches,
+            "apass": {names[k]: {"launches": s.apass_launches[k], "ms": s.apass_ms[k],
+                                 "bytes": s.apass_bytes[k]} for k in range(3)}}
