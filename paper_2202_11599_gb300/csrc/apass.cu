@@ -672,7 +672,7 @@ static cudaError_t launch_dt(const ApassKArgs& k, const ApassPlan& plan, cudaStr
 }
 
 cudaError_t apass_run(const ApassArgs& a, const ApassPlan& plan, void* partial, double* loss_part,
-                      int* dev_status, cudaStream_t st) {
+                      int* dev_status, cudaStream_t st, bool allow_stats) {
   ApassKArgs k;
   k.A = reinterpret_cast<const unsigned char*>(a.A);
   k.n = a.n;
@@ -694,7 +694,7 @@ cudaError_t apass_run(const ApassArgs& a, const ApassPlan& plan, void* partial, 
   k.executed = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int* flag = nullptr;
-  const bool prof = stats_enabled() && stats_event_pair(&e0, &e1, &flag) == cudaSuccess;
+  const bool prof = allow_stats && stats_enabled() && stats_event_pair(&e0, &e1, &flag) == cudaSuccess;
   if (prof) {
     k.executed = flag;
     NYS_CUDA_TRY(cudaEventRecord(e0, st));

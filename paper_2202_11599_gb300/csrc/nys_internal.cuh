@@ -51,8 +51,9 @@ size_t apass_partial_bytes(const nys_matrix* A, const ApassPlan& plan);
 
 // y = sum of partials + rho * p (+ beta * y_prev?) -- y in compute type.
 // dot_part (optional): per-block partials of p^T y (double), count returned via nblk.
+// allow_stats = false keeps the launch off the instrumentation path (which may allocate).
 cudaError_t apass_run(const ApassArgs& a, const ApassPlan& plan, void* partial, double* loss_part,
-                      int* dev_status, cudaStream_t st);
+                      int* dev_status, cudaStream_t st, bool allow_stats = true);
 cudaError_t apass_reduce(const ApassArgs& a, const ApassPlan& plan, const void* partial, double rho,
                          void* y, double* dot_part, int dot_blocks, cudaStream_t st);
 int reduce_blocks(int64_t d);

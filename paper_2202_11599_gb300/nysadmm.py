@@ -72,6 +72,7 @@ def lib() -> ctypes.CDLL:
     L.nys_strerror.argtypes = [c_int32]
     L.nys_strerror.restype = ctypes.c_char_p
     L.nys_hmatvec.argtypes = [P(NysMatrixC), c_void_p, c_double, c_void_p, c_void_p, c_void_p]
+    L.nys_hmatvec_noalloc.argtypes = [P(NysMatrixC), c_void_p, c_double, c_void_p, c_void_p, c_void_p]
     L.nys_sketch.argtypes = [P(NysMatrixC), c_void_p, c_double, c_int32, c_void_p, P(NysOptsC), P(c_void_p)]
     L.nys_precond_get.argtypes = [c_void_p, c_void_p, P(c_double), P(c_int32), P(c_int64), P(c_double), c_void_p]
     L.nys_precond_apply.argtypes = [c_void_p, c_double, c_void_p, c_void_p, c_int64, c_int32, c_void_p]
@@ -85,7 +86,7 @@ def lib() -> ctypes.CDLL:
     L.nys_stats_read.argtypes = [POINTER(NysStatsC)]
     L.nys_precond_destroy.argtypes = [c_void_p]
     L.nys_precond_destroy.restype = None
-    for name in ("nys_hmatvec", "nys_sketch", "nys_precond_get", "nys_precond_apply", "pcg_solve",
+    for name in ("nys_hmatvec", "nys_hmatvec_noalloc", "nys_sketch", "nys_precond_get", "nys_precond_apply", "pcg_solve",
                  "nysadmm_solve", "nys_objective", "nys_stats_read"):
         getattr(L, name).restype = c_int32
     _lib = L
@@ -159,6 +160,16 @@ def hmatvec(A: Matrix, p: torch.Tensor, rho: float = 0.0, D: torch.Tensor | None
     p = p.to(A.compute_dtype).contiguous()
     _check(lib().nys_hmatvec(ctypes.byref(A.c), _ptr(D), float(rho), _ptr(p), _ptr(y),
                              c_void_p(_stream_ptr(stream))), "nys_hmatvec")
+    return y
+
+
+def hmatvec_noalloc(A: Matrix, p: torch.Tensor, rho: float = 0.0, D: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    """hmatvec through the allocation-free entry point (fixed in-library scratch)."""
+    y = torch.empty(A.d, dtype=A.compute_dtype, device=A.tensor.device)
+    p = p.to(A.compute_dtype).contiguous()
+    _check(lib().nys_hmatvec_noalloc(ctypes.byref(A.c), _ptr(D), float(rho), _ptr(p), _ptr(y),
+                                     c_void_p(_stream_ptr(stream))), "nys_hmatvec_noalloc")
     return y
 
 
