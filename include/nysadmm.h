@@ -96,6 +96,15 @@ typedef struct {
   double ada_tol;              /* adaptive stop (lam_s + rho)/rho <= ada_tol; <= 0 -> 2 */
   int32_t resketch_every;      /* logistic: re-sketch period in outer iterations (0 = never) */
   void* stream;                /* cudaStream_t */
+  int32_t device_loop;         /* lasso: 1 = run the ADMM and PCG loops on the device as one
+                                  CUDA graph with conditional WHILE nodes (no host
+                                  synchronisation inside the solve); 0 = host-driven loop.
+                                  Both launch the same kernels in the same order. */
+  int32_t hx_refresh;          /* PCG warm start w0 = r - (A^T D A + rho I) x0: 0 = recompute
+                                  it with one pass over A at every ADMM iteration (as printed
+                                  in Alg. Nystrom PCG); M >= 1 = carry (A^T D A + rho I) x
+                                  along the PCG updates and recompute it every M ADMM
+                                  iterations (device_loop only; same value in exact arithmetic) */
 } nys_opts;
 
 typedef struct {
@@ -208,6 +217,13 @@ typedef struct {
                                  by nys_dtype of A */
   double apass_ms[3];         /* summed device time of those launches (ms) */
   double apass_bytes[3];      /* summed algorithmic bytes of those launches */
+  /* The same quantities from the kernels' own %globaltimer stamps (earliest CTA
+   * start to latest CTA end of each launch).  These also cover passes launched
+   * inside the device-side solve loop (a CUDA graph), where no event can
+   * bracket an individual kernel. */
+  int64_t dev_launches[3];
+  double dev_ms[3];
+  double dev_bytes[3];
 } nys_stats;
 
 void nys_stats_enable(int32_t on);

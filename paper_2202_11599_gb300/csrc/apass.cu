@@ -48,7 +48,44 @@ struct ApassKArgs {
   int* status;
   const int* skip;
   int* executed;  // instrumentation: set to 1 by CTA 0 when the pass ran (not skipped)
+  DevTimer tm;    // instrumentation: in-kernel launch timing (null pointers when off)
+  double bytes_alg;
 };
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int timer_begin(const ApassKArgs& a) {
+  int slot = -1;
+  if (a.tm.count && threadIdx.x == 0) {
+    const int c = *(volatile int*)a.tm.count;
+    if (c < a.tm.cap) {
+      slot = c;
+      atomicMin(&a.tm.start[c], gtimer());
+    }
+  }
+  return slot;
+}
+// called by every thread of the CTA at the end of a pass that completed
+__device__ __forceinline__ void timer_end(const ApassKArgs& a, int slot, int dtype) {
+  if (!a.tm.count) return;
+  __syncthreads();
+  if (threadIdx.x == 0 && slot >= 0) {
+    atomicMax(&a.tm.end[slot], gtimer());
+    if (blockIdx.x == 0) {
+      a.tm.bytes[slot] = a.bytes_alg;
+      a.tm.dtype[slot] = dtype;
+    }
+    __threadfence();
+    if (atomicAdd(a.tm.done, 1) == (int)gridDim.x - 1) {
+      *a.tm.done = 0;
+      __threadfence();
+      *(volatile int*)a.tm.count = slot + 1;
+    }
+  }
+}
 
 __device__ __forceinline__ double sigmoid_d(double t) {
   // stable logistic function
@@ -74,6 +111,7 @@ __global__ void __launch_bounds__(kApassThreads, 1) apass_kernel(const ApassKArg
 
   if (a.skip && *a.skip) return;
   if (a.executed && blockIdx.x == 0 && threadIdx.x == 0) *a.executed = 1;
+  const int ts_slot = timer_begin(a);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t nvec = (a.d + VEC - 1) / VEC;
   const int64_t rowbytes = a.ld * ESZ;
@@ -252,6 +290,7 @@ __global__ void __launch_bounds__(kApassThreads, 1) apass_kernel(const ApassKArg
     }
   }
   if (tid == 0 && a.loss_part) a.loss_part[blockIdx.x] = loss;
+  timer_end(a, ts_slot, DT);
 }
 
 // Float-compute variant (FP32 / BF16 storage).  Same streaming scheme, tuned for
@@ -353,6 +392,7 @@ __global__ void __launch_bounds__(kApassThreads, 1) apass_f_kernel(const ApassKA
 
   if (a.skip && *a.skip) return;
   if (a.executed && blockIdx.x == 0 && threadIdx.x == 0) *a.executed = 1;
+  const int ts_slot = timer_begin(a);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nvec = (int)((a.d + VEC - 1) / VEC);
   const uint32_t rowbytes = (uint32_t)(a.ld * ESZ);
@@ -504,6 +544,7 @@ __global__ void __launch_bounds__(kApassThreads, 1) apass_f_kernel(const ApassKA
       a.loss_part[blockIdx.x] = sl;
     }
   }
+  timer_end(a, ts_slot, DT);
 }
 
 // y_j = sum_g partial[g][j] (fixed order) + rho p_j; optional per-block partials of p^T y.
@@ -594,6 +635,8 @@ size_t apass_partial_bytes(const nys_matrix* A, const ApassPlan& plan) {
   return (size_t)plan.grid * plan.dpad * csz;
 }
 
+static thread_local bool g_prepare_only = false;
+
 template <int DT, int VPT>
 static cudaError_t launch_vpt(const ApassKArgs& k, const ApassPlan& plan, cudaStream_t st) {
   auto fn = apass_kernel<DT, VPT>;
@@ -602,6 +645,7 @@ static cudaError_t launch_vpt(const ApassKArgs& k, const ApassPlan& plan, cudaSt
     NYS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
     attr_set = true;
   }
+  if (g_prepare_only) return cudaSuccess;
   count_launch();
   fn<<<plan.grid, kApassThreads, plan.smem, st>>>(k);
   return cudaGetLastError();
@@ -615,6 +659,7 @@ static cudaError_t launch_f(const ApassKArgs& k, const ApassPlan& plan, cudaStre
     NYS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
     attr_set = true;
   }
+  if (g_prepare_only) return cudaSuccess;
   count_launch();
   fn<<<plan.grid, kApassThreads, plan.smem, st>>>(k);
   return cudaGetLastError();
@@ -692,9 +737,18 @@ cudaError_t apass_run(const ApassArgs& a, const ApassPlan& plan, void* partial, 
   k.status = dev_status;
   k.skip = a.skip;
   k.executed = nullptr;
+  {
+    const double esz = (double)dtype_size(a.dtype), csz = compute_is_f64(a.dtype) ? 8.0 : 4.0;
+    double bytes = (double)a.n * (double)a.d * esz + (double)a.d * csz + (double)plan.grid * a.d * csz;
+    if (a.mode == MODE_DIAG || a.mode == MODE_RESID || a.mode == MODE_CONST) bytes += 8.0 * a.n;
+    if (a.mode == MODE_LOGIT || a.mode == MODE_LGRAD) bytes += 16.0 * a.n;
+    k.bytes_alg = bytes;
+  }
+  if (allow_stats && !g_prepare_only) k.tm = stats_device_timer();
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int* flag = nullptr;
-  const bool prof = allow_stats && stats_enabled() && stats_event_pair(&e0, &e1, &flag) == cudaSuccess;
+  const bool prof = allow_stats && !g_prepare_only && stats_enabled() &&
+                    stats_event_pair(&e0, &e1, &flag) == cudaSuccess;
   if (prof) {
     k.executed = flag;
     NYS_CUDA_TRY(cudaEventRecord(e0, st));
@@ -709,13 +763,28 @@ cudaError_t apass_run(const ApassArgs& a, const ApassPlan& plan, void* partial, 
   if (prof && err == cudaSuccess) {
     NYS_CUDA_TRY(cudaEventRecord(e1, st));
     // algorithmic bytes: A read once, p read, partials written, per-row vectors touched
-    const double esz = (double)dtype_size(a.dtype), csz = compute_is_f64(a.dtype) ? 8.0 : 4.0;
-    double bytes = (double)a.n * (double)a.d * esz + (double)a.d * csz + (double)plan.grid * a.d * csz;
-    if (a.mode == MODE_DIAG || a.mode == MODE_RESID || a.mode == MODE_CONST) bytes += 8.0 * a.n;
-    if (a.mode == MODE_LOGIT || a.mode == MODE_LGRAD) bytes += 16.0 * a.n;
-    stats_record_apass(e0, e1, bytes, a.dtype, flag);
+    stats_record_apass(e0, e1, k.bytes_alg, a.dtype, flag);
   }
   return err;
+}
+
+cudaError_t apass_prepare(const nys_matrix* A, const ApassPlan& plan) {
+  ApassArgs a;
+  a.A = A->data;
+  a.n = A->n;
+  a.d = A->d;
+  a.ld = A->ld;
+  a.dtype = A->dtype;
+  a.p = nullptr;
+  a.D = nullptr;
+  a.b = nullptr;
+  a.D_out = nullptr;
+  a.t_out = nullptr;
+  a.mode = MODE_ID;
+  g_prepare_only = true;
+  const cudaError_t e = apass_run(a, plan, nullptr, nullptr, nullptr, nullptr, false);
+  g_prepare_only = false;
+  return e;
 }
 
 cudaError_t apass_reduce(const ApassArgs& a, const ApassPlan& plan, const void* partial, double rho,

@@ -371,6 +371,72 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
   pb.rho = rho;
   apass_plan(Ain, &pb.plan);
   const int maxit = o.pcg_maxit > 0 ? o.pcg_maxit : (int)std::min<int64_t>(d, 1000);
+  if (o.device_loop && (!refine || A->dtype == NYS_F64)) {
+    // device-side loop: one CUDA graph launch for all K iterations
+    GraphLoopArgs g;
+    g.pb = pb;
+    g.P = view;
+    if (refine) {
+      g.Aref = A;
+      apass_plan(A, &g.plan_ref);
+    }
+    g.b = b;
+    g.yres = yres;
+    g.x = x;
+    g.z = z;
+    g.u = u;
+    g.q = q;
+    g.xc = xc;
+    g.rc = rc;
+    C* hx = pool.alloc<C>(d);
+    int* pcg_it = pool.alloc<int>(K);
+    if (!pool.ok()) return NYS_ENOMEM;
+    g.hx = hx;
+    g.gamma = gamma;
+    g.rho = rho;
+    g.K = K;
+    g.eps_abs = o.eps_abs;
+    g.eps_rel = o.eps_rel;
+    g.tol = (refine && sizeof(C) == 4 && o.pcg_tol_mode != NYS_TOL_ABS) ? std::max(tol, 1e-6) : tol;
+    g.tol_mode = o.pcg_tol_mode;
+    g.maxit = maxit;
+    g.fixed_host = o.pcg_fixed_iters;
+    g.hx_refresh = std::max(0, o.hx_refresh);
+    g.ztrace = o.z_trace;
+    g.rp = rp;
+    g.rd = rd;
+    g.pcg_it = pcg_it;
+    GraphLoopResult gr;
+    nys_status gs = admm_graph_run<C>(g, st, &gr);
+    if (gs != NYS_OK) return gs;
+    const int done_k = std::min(gr.admm_iters, K);
+    std::vector<int> its(std::max(1, done_k));
+    if (done_k > 0) NYS_CU(cudaMemcpyAsync(its.data(), pcg_it, done_k * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (x_out) NYS_CU(cudaMemcpyAsync(x_out, x, d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (z_out) NYS_CU(cudaMemcpyAsync(z_out, z, d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (info && done_k > 0) {
+      NYS_CU(cudaMemcpyAsync(&info->r_p, rp + done_k - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+      NYS_CU(cudaMemcpyAsync(&info->r_d, rd + done_k - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    NYS_CU(cudaStreamSynchronize(st));
+    int total = 0;
+    bool capped = false;
+    for (int i = 0; i < done_k; ++i) {
+      total += its[i];
+      const int cap_i = o.pcg_fixed_iters ? o.pcg_fixed_iters[i] : maxit;
+      if (!o.pcg_fixed_iters && its[i] >= cap_i) capped = true;
+    }
+    const nys_status result = gr.breakdown ? NYS_EBREAKDOWN : (capped ? NYS_ENOCONV : NYS_OK);
+    if (info) {
+      info->admm_iters = done_k;
+      info->pcg_iters_total = total;
+      info->final_rank = rank;
+      info->status = result;
+      info->nu = P.nu;
+      info->emp_cond = P.lam.empty() ? 1.0 : (P.lam.back() + rho) / rho;
+    }
+    return result;
+  }
   int total_pcg = 0;
   nys_status result = NYS_OK;
   int k = 0;
@@ -659,6 +725,8 @@ void nys_opts_default(nys_opts* o) {
   o->ada_tol = 2.0;
   o->resketch_every = 1;
   o->stream = nullptr;
+  o->device_loop = 1;
+  o->hx_refresh = 0;
 }
 
 const char* nys_strerror(int32_t s) {

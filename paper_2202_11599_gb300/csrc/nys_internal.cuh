@@ -96,8 +96,26 @@ cudaError_t convert_f32_to_f64(const float* x, double* y, int64_t n, cudaStream_
 // Instrumentation (nys_stats_* in the C ABI): every kernel launch is counted; the
 // fused A-pass launches are bracketed by CUDA events on their stream when enabled.
 void count_launch();
+void count_launch_suspend(bool on);     // while capturing a graph: launches are counted on execution
+void count_launch_add(long long n);     // executed graph kernel nodes
+// Set the launch attributes of the A-pass instantiation for this matrix (outside capture).
+cudaError_t apass_prepare(const nys_matrix* A, const ApassPlan& plan);
 bool stats_enabled();
 void stats_record_apass(cudaEvent_t start, cudaEvent_t stop, double bytes, int dtype, int* executed);
+
+// In-kernel timing of A-pass launches (works inside CUDA graphs): the first CTA to
+// start stamps %globaltimer into start[slot] (atomicMin), every CTA stamps its end
+// (atomicMax), and the last CTA to finish advances *count.
+struct DevTimer {
+  unsigned long long* start = nullptr;
+  unsigned long long* end = nullptr;
+  double* bytes = nullptr;
+  int* dtype = nullptr;
+  int* count = nullptr;
+  int* done = nullptr;
+  int cap = 0;
+};
+DevTimer stats_device_timer();
 // An event pair plus a zeroed device flag that the pass sets when it runs.
 cudaError_t stats_event_pair(cudaEvent_t* start, cudaEvent_t* stop, int** executed);
 

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kVecThreads) pcg_update_kernel(int init, int64
                                                                  const double* __restrict__ pv_part, int npv,
                                                                  const double* __restrict__ wy_part, int nwy,
                                                                  double* part_w2, double* part_r2, double* part_g,
-                                                                 const PcgState* st) {
+                                                                 const PcgState* st, C* __restrict__ hx) {
   if (st->done) return;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* wch = reinterpret_cast<C*>(sm_raw);
@@ -85,8 +85,10 @@ __global__ void __launch_bounds__(kVecThreads) pcg_update_kernel(int init, int64
       wj = v ? rj - v[j] : rj;
       lr2 += (double)rj * (double)rj;
     } else {
+      const C vj = v[j];
       x[j] = fma(a, p[j], x[j]);
-      wj = fma(-a, v[j], w[j]);
+      wj = fma(-a, vj, w[j]);
+      if (hx) hx[j] = fma(a, vj, hx[j]);  // (H + rho I) x follows x: x += a p  =>  += a v
     }
     w[j] = wj;
     wch[j - j0] = wj;
@@ -116,8 +118,12 @@ __global__ void __launch_bounds__(kVecThreads) pcg_scalar_kernel(int init, int n
                                                                  const double* part_r2, const double* part_g, int s,
                                                                  const C* __restrict__ cvec, C* __restrict__ gs,
                                                                  const double* pv_part, int npv,
-                                                                 const double* wy_part, int nwy, PcgState* st) {
-  if (st->done) return;
+                                                                 const double* wy_part, int nwy, PcgState* st,
+                                                                 cudaGraphConditionalHandle cond, int use_cond) {
+  if (st->done) {
+    if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+    return;
+  }
   __shared__ double slot;
   const double w2 = block_fixed_sum(part_w2, nb3, &slot);
   double r2 = 0.0, pv = 1.0, wy = 0.0;
@@ -161,6 +167,7 @@ __global__ void __launch_bounds__(kVecThreads) pcg_scalar_kernel(int init, int n
     for (int b = 0; b < nb3; ++b) g += part_g[(int64_t)b * s + i];
     gs[i] = (C)((double)cvec[i] * g);
   }
+  if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
 }
 
 // K5: y = w + U gs (= P^{-1} w), partial w^T y.
@@ -275,11 +282,11 @@ nys_status pcg_run(const PcgProblem& pb, const PrecondView& P, const C* r, C* x,
   }
   count_launch();
   pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, stream>>>(1, d, chunk, x, w, r, v0, p, U, s, pv_part, nbr,
-                                                             wy_part, nb5, part_w2, part_r2, part_g, st);
+                                                             wy_part, nb5, part_w2, part_r2, part_g, st, (C*)nullptr);
   LAUNCH_OK(cudaGetLastError());
   count_launch();
   pcg_scalar_kernel<C><<<1, kVecThreads, 0, stream>>>(1, nb3, part_w2, part_r2, part_g, s, cvec, gs, pv_part, nbr,
-                                                      wy_part, nb5, st);
+                                                      wy_part, nb5, st, 0ull, 0);
   LAUNCH_OK(cudaGetLastError());
   count_launch();
   pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, stream>>>(d, w, y, U, s, gs, wy_part, st);
@@ -299,11 +306,11 @@ nys_status pcg_run(const PcgProblem& pb, const PrecondView& P, const C* r, C* x,
       LAUNCH_OK(apass_reduce(aa, pb.plan, apart, pb.rho, v, pv_part, nbr, stream));
       count_launch();
       pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, stream>>>(0, d, chunk, x, w, r, v, p, U, s, pv_part, nbr,
-                                                                 wy_part, nb5, part_w2, part_r2, part_g, st);
+                                                                 wy_part, nb5, part_w2, part_r2, part_g, st, (C*)nullptr);
       LAUNCH_OK(cudaGetLastError());
       count_launch();
       pcg_scalar_kernel<C><<<1, kVecThreads, 0, stream>>>(0, nb3, part_w2, part_r2, part_g, s, cvec, gs, pv_part,
-                                                          nbr, wy_part, nb5, st);
+                                                          nbr, wy_part, nb5, st, 0ull, 0);
       LAUNCH_OK(cudaGetLastError());
       count_launch();
       pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, stream>>>(d, w, y, U, s, gs, wy_part, st);
@@ -356,11 +363,11 @@ nys_status precond_apply_run(const PrecondView& P, int64_t d, const C* V, C* Y, 
     count_launch();
     pcg_update_kernel<C><<<nb3, kVecThreads, (size_t)chunk * sizeof(C), stream>>>(
         1, d, chunk, nullptr, w, V + c * d, nullptr, nullptr, reinterpret_cast<const C*>(P.U), s, nullptr, 0,
-        nullptr, 0, part_w2, part_r2, part_g, st);
+        nullptr, 0, part_w2, part_r2, part_g, st, (C*)nullptr);
     count_launch();
     pcg_scalar_kernel<C><<<1, kVecThreads, 0, stream>>>(1, nb3, part_w2, part_r2, part_g, s,
                                                         reinterpret_cast<const C*>(P.c), gs, nullptr, 0, nullptr, 0,
-                                                        st);
+                                                        st, 0ull, 0);
     // the scalar kernel may mark the state done (||w|| <= 0 threshold); force the tail to run
     count_launch();
     pcg_reset_kernel<<<1, 1, 0, stream>>>(st, 0.0, 1, 1, -1, nullptr);
@@ -507,5 +514,323 @@ PcgState* host_state() {
   }
   return hs;
 }
+
+}  // namespace nys
+
+namespace nys {
+// =========================================================================== device-side ADMM loop
+// The lasso NysADMM loop as ONE CUDA graph: an outer conditional WHILE node runs
+// ADMM iterations and an inner one runs PCG iterations; the scalar kernels set the
+// loop conditions on the device, so a whole solve needs no host synchronisation.
+// The kernels and their order are those of the host-driven loop.
+namespace {
+
+struct AdmmCtl {
+  int k;            // ADMM iteration counter
+  int stop;         // residual stop reached
+  int hx_skip;      // 1: reuse the tracked (H + rho I) x; 0: recompute it this iteration
+  int pad;
+  long long nodes;  // kernel launches executed (instrumentation)
+  double eps_next;  // sqrt(r_p r_d) of the last iteration
+};
+
+__global__ void admm_begin_kernel(AdmmCtl* ctl, PcgState* st, double tol, int tol_mode, int maxit,
+                                  const int* __restrict__ fixed_dev, int hx_refresh, int refine) {
+  const int k = ctl->k;
+  st->wy = 0.0;
+  st->w2 = 0.0;
+  st->r2 = 0.0;
+  st->thresh2 = 0.0;
+  st->iters = 0;
+  st->done = 0;
+  st->status = 0;
+  st->maxit = maxit;
+  st->fixed = fixed_dev ? fixed_dev[k] : -1;
+  if (tol_mode == NYS_TOL_SQRT_RPRD && k > 0) {
+    st->tol = ctl->eps_next;
+    st->tol_abs = 1;
+  } else {
+    st->tol = tol;
+    st->tol_abs = tol_mode == NYS_TOL_ABS;
+  }
+  // k = 0 and refined steps start from x = 0 (hx = 0); otherwise recompute (H + rho I) x
+  // when hx_refresh == 0 (as printed) or every hx_refresh iterations
+  if (refine || k == 0) ctl->hx_skip = 1;
+  else ctl->hx_skip = (hx_refresh == 0 || k % hx_refresh == 0) ? 0 : 1;
+}
+
+// r = q + rho (z - u); refined step: r = rho (z - u - x) - yres, and the PCG starts at 0.
+template <typename C>
+__global__ void admm_rhs_g_kernel(int64_t d, const double* __restrict__ q, const double* __restrict__ z,
+                                  const double* __restrict__ u, double rho, const double* __restrict__ x,
+                                  const double* __restrict__ yres, int refine, C* __restrict__ r, C* __restrict__ xc,
+                                  C* __restrict__ hx) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x) {
+    const double zu = z[j] - u[j];
+    if (refine) {
+      r[j] = (C)(rho * (zu - x[j]) - yres[j]);
+      xc[j] = C(0);
+      hx[j] = C(0);
+    } else {
+      r[j] = (C)fma(rho, zu, q[j]);
+    }
+  }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kVecThreads) admm_zu_g_kernel(int64_t d, const C* __restrict__ xc, int accumulate,
+                                                                double* __restrict__ x, double* __restrict__ z,
+                                                                double* __restrict__ u, double kappa,
+                                                                double* __restrict__ ztrace, const AdmmCtl* ctl,
+                                                                double* part5) {
+  __shared__ double sh[kVecThreads / 32];
+  double* zt = ztrace ? ztrace + (int64_t)ctl->k * d : nullptr;
+  double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+  for (int64_t j = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)gridDim.x * kVecThreads) {
+    const double xj = accumulate ? x[j] + (double)xc[j] : (double)xc[j];
+    const double zo = z[j];
+    const double vj = xj + u[j];
+    const double mag = fabs(vj) - kappa;
+    const double zj = mag > 0.0 ? copysign(mag, vj) : 0.0;
+    const double uj = u[j] + xj - zj;
+    x[j] = xj;
+    z[j] = zj;
+    u[j] = uj;
+    if (zt) zt[j] = zj;
+    a0 += (xj - zj) * (xj - zj);
+    a1 += (zj - zo) * (zj - zo);
+    a2 += xj * xj;
+    a3 += zj * zj;
+    a4 += uj * uj;
+  }
+  a0 = block_sum<kVecThreads>(a0, sh);
+  a1 = block_sum<kVecThreads>(a1, sh);
+  a2 = block_sum<kVecThreads>(a2, sh);
+  a3 = block_sum<kVecThreads>(a3, sh);
+  a4 = block_sum<kVecThreads>(a4, sh);
+  if (threadIdx.x == 0) {
+    double* o = part5 + (int64_t)blockIdx.x * 5;
+    o[0] = a0;
+    o[1] = a1;
+    o[2] = a2;
+    o[3] = a3;
+    o[4] = a4;
+  }
+}
+
+__global__ void admm_scalar_g_kernel(int nb, const double* part5, double rho, int K, double eps_abs,
+                                     double eps_rel, double* rp_trace, double* rd_trace, int* pcg_it_trace,
+                                     const PcgState* st, AdmmCtl* ctl, long long nodes_per_iter,
+                                     long long nodes_per_pcg_iter, cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0) return;
+  double a[5] = {0, 0, 0, 0, 0};
+  for (int b = 0; b < nb; ++b)
+    for (int t = 0; t < 5; ++t) a[t] += part5[(int64_t)b * 5 + t];
+  const int k = ctl->k;
+  const double rp = sqrt(a[0]);
+  const double rd = rho * sqrt(a[1]);
+  rp_trace[k] = rp;
+  rd_trace[k] = rd;
+  pcg_it_trace[k] = st->iters;
+  ctl->eps_next = sqrt(rp * rd);
+  if (eps_rel > 0.0) {
+    const double tp = eps_abs + eps_rel * fmax(sqrt(a[2]), sqrt(a[3]));
+    const double td = eps_abs + eps_rel * rho * sqrt(a[4]);
+    if (rp <= tp && rd <= td) ctl->stop = 1;
+  }
+  if (st->status == NYS_EBREAKDOWN) ctl->stop = 2;
+  ctl->nodes += nodes_per_iter + nodes_per_pcg_iter * (long long)st->iters;
+  ctl->k = k + 1;
+  cudaGraphSetConditional(cond, (k + 1 < K && !ctl->stop) ? 1u : 0u);
+}
+
+}  // namespace
+
+template <typename C>
+nys_status admm_graph_run(const GraphLoopArgs& g, cudaStream_t stream, GraphLoopResult* res) {
+  const int64_t d = g.pb.A->d;
+  const int s = g.P.s;
+  const C* U = reinterpret_cast<const C*>(g.P.U);
+  const C* cvec = reinterpret_cast<const C*>(g.P.c);
+  const int chunk = upd_chunk(d);
+  const int nb3 = (int)((d + chunk - 1) / chunk);
+  const int nbr = reduce_blocks(d);
+  const int nb5 = nbr;
+  const int nbz = admm_blocks(d);
+  const int K = g.K;
+  Pool pool(stream);
+  C* w = pool.alloc<C>(d);
+  C* y = pool.alloc<C>(d);
+  C* p = pool.alloc<C>(d);
+  C* v = pool.alloc<C>(d);
+  C* gs = pool.alloc<C>(std::max(1, s));
+  double* part_w2 = pool.alloc<double>(nb3);
+  double* part_r2 = pool.alloc<double>(nb3);
+  double* part_g = pool.alloc<double>((size_t)nb3 * std::max(1, s));
+  double* pv_part = pool.alloc<double>(nbr);
+  double* wy_part = pool.alloc<double>(nb5);
+  void* apart = pool.alloc<unsigned char>(apass_partial_bytes(g.pb.A, g.pb.plan));
+  void* apart_ref = g.Aref ? pool.alloc<unsigned char>(apass_partial_bytes(g.Aref, g.plan_ref)) : nullptr;
+  PcgState* st = pool.alloc<PcgState>(1);
+  AdmmCtl* ctl = pool.alloc<AdmmCtl>(1);
+  int* dstat = pool.alloc<int>(1);
+  double* part5 = pool.alloc<double>((size_t)nbz * 5);
+  int* fixed_dev = g.fixed_host ? pool.alloc<int>(K) : nullptr;
+  if (!pool.ok()) return NYS_ENOMEM;
+  C* xc = reinterpret_cast<C*>(g.xc);
+  C* rc = reinterpret_cast<C*>(g.rc);
+  C* hx = reinterpret_cast<C*>(g.hx);
+  cudaError_t e = cudaSuccess;
+#define G_OK(x)                                  \
+  do {                                           \
+    e = (x);                                     \
+    if (e != cudaSuccess) return NYS_ECUDA;      \
+  } while (0)
+  G_OK(cudaMemsetAsync(ctl, 0, sizeof(AdmmCtl), stream));
+  G_OK(cudaMemsetAsync(dstat, 0, sizeof(int), stream));
+  G_OK(cudaMemsetAsync(hx, 0, d * sizeof(C), stream));
+  if (fixed_dev) G_OK(cudaMemcpyAsync(fixed_dev, g.fixed_host, K * sizeof(int), cudaMemcpyHostToDevice, stream));
+  G_OK(apass_prepare(g.pb.A, g.pb.plan));
+  if (g.Aref) G_OK(apass_prepare(g.Aref, g.plan_ref));
+
+  // a private stream to capture on (a legacy default stream cannot be captured)
+  static thread_local cudaStream_t cap = nullptr;
+  if (!cap) G_OK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  struct Cleanup {
+    cudaGraph_t* g;
+    cudaGraphExec_t* x;
+    ~Cleanup() {
+      if (*x) cudaGraphExecDestroy(*x);
+      if (*g) cudaGraphDestroy(*g);
+    }
+  } cleanup{&graph, &exec};
+  G_OK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle h_admm, h_pcg;
+  G_OK(cudaGraphConditionalHandleCreate(&h_admm, graph, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h_admm;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t n_admm;
+  G_OK(cudaGraphAddNode(&n_admm, graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  G_OK(cudaGraphConditionalHandleCreate(&h_pcg, body, 0u, 0u));
+
+  ApassArgs aa;
+  aa.A = g.pb.A->data;
+  aa.n = g.pb.A->n;
+  aa.d = d;
+  aa.ld = g.pb.A->ld;
+  aa.dtype = g.pb.A->dtype;
+  aa.D = g.pb.D;
+  aa.b = nullptr;
+  aa.D_out = nullptr;
+  aa.t_out = nullptr;
+  aa.mode = g.pb.D ? MODE_DIAG : MODE_ID;
+  const size_t sm_upd = (size_t)chunk * sizeof(C);
+  const size_t sm_tail = (size_t)std::max(1, s) * sizeof(C);
+  const int refine = g.Aref ? 1 : 0;
+  long long seg_nodes = 0, body_nodes = 0;
+
+  // ---- segment 1: begin, (exact residual pass), right-hand side, PCG init
+  count_launch_suspend(true);
+  G_OK(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  admm_begin_kernel<<<1, 1, 0, cap>>>(ctl, st, g.tol, g.tol_mode, g.maxit, fixed_dev, g.hx_refresh, refine);
+  ++seg_nodes;
+  if (refine) {
+    ApassArgs ar;
+    ar.A = g.Aref->data;
+    ar.n = g.Aref->n;
+    ar.d = d;
+    ar.ld = g.Aref->ld;
+    ar.dtype = g.Aref->dtype;
+    ar.p = g.x;
+    ar.D = nullptr;
+    ar.b = g.b;
+    ar.D_out = nullptr;
+    ar.t_out = nullptr;
+    ar.mode = MODE_RESID;
+    G_OK(apass_run(ar, g.plan_ref, apart_ref, nullptr, dstat, cap, false));
+    ApassArgs ar2 = ar;
+    ar2.p = nullptr;
+    G_OK(apass_reduce(ar2, g.plan_ref, apart_ref, 0.0, g.yres, nullptr, 0, cap));
+    seg_nodes += 2;
+  }
+  admm_rhs_g_kernel<C><<<nbz, kVecThreads, 0, cap>>>(d, g.q, g.z, g.u, g.rho, g.x, g.yres, refine, rc, xc, hx);
+  ++seg_nodes;
+  aa.p = xc;
+  aa.skip = &ctl->hx_skip;
+  G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, false));
+  G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho, hx, nullptr, 0, cap));
+  seg_nodes += 2;
+  pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, cap>>>(1, d, chunk, xc, w, rc, hx, p, U, s, pv_part, nbr,
+                                                          wy_part, nb5, part_w2, part_r2, part_g, st, (C*)nullptr);
+  pcg_scalar_kernel<C><<<1, kVecThreads, 0, cap>>>(1, nb3, part_w2, part_r2, part_g, s, cvec, gs, pv_part, nbr,
+                                                   wy_part, nb5, st, h_pcg, 1);
+  pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, cap>>>(d, w, y, U, s, gs, wy_part, st);
+  pcg_pupdate_kernel<C><<<nb5, kVecThreads, 0, cap>>>(1, d, y, p, wy_part, nb5, st);
+  seg_nodes += 4;
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  G_OK(cudaStreamGetCaptureInfo(cap, &cst, nullptr, nullptr, &deps, nullptr, &ndeps));
+  std::vector<cudaGraphNode_t> leaf(deps, deps + ndeps);
+  G_OK(cudaStreamEndCapture(cap, &body));
+
+  // ---- PCG loop
+  cudaGraphNodeParams pp = {};
+  pp.type = cudaGraphNodeTypeConditional;
+  pp.conditional.handle = h_pcg;
+  pp.conditional.type = cudaGraphCondTypeWhile;
+  pp.conditional.size = 1;
+  cudaGraphNode_t n_pcg;
+  G_OK(cudaGraphAddNode(&n_pcg, body, leaf.data(), nullptr, leaf.size(), &pp));
+  cudaGraph_t pbody = pp.conditional.phGraph_out[0];
+  G_OK(cudaStreamBeginCaptureToGraph(cap, pbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  aa.p = p;
+  aa.skip = &st->done;
+  G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, false));
+  G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho, v, pv_part, nbr, cap));
+  pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, cap>>>(0, d, chunk, xc, w, rc, v, p, U, s, pv_part, nbr, wy_part,
+                                                          nb5, part_w2, part_r2, part_g, st, hx);
+  pcg_scalar_kernel<C><<<1, kVecThreads, 0, cap>>>(0, nb3, part_w2, part_r2, part_g, s, cvec, gs, pv_part, nbr,
+                                                   wy_part, nb5, st, h_pcg, 1);
+  pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, cap>>>(d, w, y, U, s, gs, wy_part, st);
+  pcg_pupdate_kernel<C><<<nb5, kVecThreads, 0, cap>>>(0, d, y, p, wy_part, nb5, st);
+  body_nodes = 6;
+  G_OK(cudaStreamEndCapture(cap, &pbody));
+
+  // ---- segment 2: prox / dual step, residuals, loop condition
+  G_OK(cudaStreamBeginCaptureToGraph(cap, body, &n_pcg, nullptr, 1, cudaStreamCaptureModeRelaxed));
+  admm_zu_g_kernel<C><<<nbz, kVecThreads, 0, cap>>>(d, xc, refine, g.x, g.z, g.u, g.gamma / g.rho, g.ztrace, ctl,
+                                                    part5);
+  seg_nodes += 2;
+  admm_scalar_g_kernel<<<1, 32, 0, cap>>>(nbz, part5, g.rho, K, g.eps_abs, g.eps_rel, g.rp, g.rd, g.pcg_it, st, ctl,
+                                          seg_nodes, body_nodes, h_admm);
+  G_OK(cudaStreamEndCapture(cap, &body));
+  count_launch_suspend(false);
+  G_OK(cudaGetLastError());
+
+  G_OK(cudaGraphInstantiate(&exec, graph, 0));
+  G_OK(cudaGraphLaunch(exec, stream));
+  AdmmCtl ctl_h;
+  int dstat_h = 0;
+  G_OK(cudaMemcpyAsync(&ctl_h, ctl, sizeof(AdmmCtl), cudaMemcpyDeviceToHost, stream));
+  G_OK(cudaMemcpyAsync(&dstat_h, dstat, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  G_OK(cudaStreamSynchronize(stream));
+#undef G_OK
+  count_launch_add(ctl_h.nodes);
+  res->admm_iters = ctl_h.k;
+  res->breakdown = ctl_h.stop == 2;
+  if (dstat_h) return (nys_status)dstat_h;
+  return NYS_OK;
+}
+
+template nys_status admm_graph_run<double>(const GraphLoopArgs&, cudaStream_t, GraphLoopResult*);
+template nys_status admm_graph_run<float>(const GraphLoopArgs&, cudaStream_t, GraphLoopResult*);
 
 }  // namespace nys

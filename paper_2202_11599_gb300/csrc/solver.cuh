@@ -93,4 +93,33 @@ int pcg_nb3(int64_t d);
 
 PcgState* host_state();
 
+// Device-side lasso ADMM loop (one CUDA graph with conditional WHILE nodes).
+struct GraphLoopArgs {
+  PcgProblem pb;             // PCG matrix (A_inner or A), D, rho, plan
+  PrecondView P;
+  const nys_matrix* Aref = nullptr;  // refined step: exact residual with this (FP64) matrix
+  ApassPlan plan_ref;
+  const double* b = nullptr;
+  double* yres = nullptr;    // d, FP64 (refined step)
+  double *x = nullptr, *z = nullptr, *u = nullptr, *q = nullptr;
+  void *xc = nullptr, *rc = nullptr, *hx = nullptr;  // compute type, length d
+  double gamma = 0, rho = 1;
+  int K = 1;
+  double eps_abs = 0, eps_rel = 0;
+  double tol = 1e-8;
+  int tol_mode = NYS_TOL_REL;
+  int maxit = 1000;
+  const int* fixed_host = nullptr;
+  int hx_refresh = 0;
+  double* ztrace = nullptr;
+  double *rp = nullptr, *rd = nullptr;
+  int* pcg_it = nullptr;     // device, K
+};
+struct GraphLoopResult {
+  int admm_iters = 0;
+  bool breakdown = false;
+};
+template <typename C>
+nys_status admm_graph_run(const GraphLoopArgs& g, cudaStream_t stream, GraphLoopResult* res);
+
 }  // namespace nys

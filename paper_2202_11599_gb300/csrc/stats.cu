@@ -5,6 +5,7 @@
 #include <mutex>
 #include <utility>
 #include <vector>
+#include <algorithm>
 
 #include "nys_internal.cuh"
 
@@ -24,11 +25,24 @@ std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_free;
 constexpr size_t kMaxRecords = 1 << 20;
 int* g_flags = nullptr;      // device: one "executed" flag per record slot
 size_t g_next_slot = 0;
+constexpr int kTimerCap = 1 << 18;
+DevTimer g_timer;            // device buffers of the in-kernel timer (allocated on first enable)
+bool g_timer_on = false;
 }  // namespace
 
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+thread_local bool g_count_suspended = false;
+void count_launch() {
+  if (!g_count_suspended) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void count_launch_suspend(bool on) { g_count_suspended = on; }
+void count_launch_add(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 bool stats_enabled() { return g_enabled.load(std::memory_order_relaxed); }
+
+DevTimer stats_device_timer() {
+  if (!g_timer_on) return DevTimer{};
+  return g_timer;
+}
 
 cudaError_t stats_event_pair(cudaEvent_t* a, cudaEvent_t* b, int** executed) {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -69,6 +83,24 @@ extern "C" {
 void nys_stats_enable(int32_t on) {
   using namespace nys;
   std::lock_guard<std::mutex> lk(g_mu);
+  if (on && !g_timer.count) {
+    const size_t cap = kTimerCap;
+    bool ok = cudaMalloc(&g_timer.start, cap * 8) == cudaSuccess && cudaMalloc(&g_timer.end, cap * 8) == cudaSuccess &&
+              cudaMalloc(&g_timer.bytes, cap * 8) == cudaSuccess && cudaMalloc(&g_timer.dtype, cap * 4) == cudaSuccess &&
+              cudaMalloc(&g_timer.count, 8) == cudaSuccess;
+    if (ok) {
+      g_timer.done = g_timer.count + 1;
+      g_timer.cap = kTimerCap;
+    } else {
+      g_timer = DevTimer{};
+    }
+  }
+  if (g_timer.count) {
+    cudaMemset(g_timer.start, 0xff, (size_t)g_timer.cap * 8);
+    cudaMemset(g_timer.end, 0, (size_t)g_timer.cap * 8);
+    cudaMemset(g_timer.count, 0, 8);
+  }
+  g_timer_on = on != 0 && g_timer.count != nullptr;
   for (auto& r : g_recs) g_free.emplace_back(r.start, r.stop);
   if (g_flags && !g_recs.empty()) cudaMemset(g_flags, 0, g_recs.size() * sizeof(int));
   g_recs.clear();
@@ -102,6 +134,33 @@ nys_status nys_stats_read(nys_stats* out) {
     out->apass_bytes[k] += r.bytes;
   }
   out->launches = g_launches.load();
+  for (int k = 0; k < 3; ++k) {
+    out->dev_launches[k] = 0;
+    out->dev_ms[k] = 0.0;
+    out->dev_bytes[k] = 0.0;
+  }
+  if (g_timer.count) {
+    int cnt = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return NYS_ECUDA;
+    if (cudaMemcpy(&cnt, g_timer.count, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return NYS_ECUDA;
+    cnt = std::min(cnt, g_timer.cap);
+    std::vector<unsigned long long> t0(cnt), t1(cnt);
+    std::vector<double> by(cnt);
+    std::vector<int> dt(cnt);
+    if (cnt > 0 &&
+        (cudaMemcpy(t0.data(), g_timer.start, cnt * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+         cudaMemcpy(t1.data(), g_timer.end, cnt * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+         cudaMemcpy(by.data(), g_timer.bytes, cnt * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+         cudaMemcpy(dt.data(), g_timer.dtype, cnt * 4, cudaMemcpyDeviceToHost) != cudaSuccess))
+      return NYS_ECUDA;
+    for (int i = 0; i < cnt; ++i) {
+      const int k = (dt[i] >= 0 && dt[i] < 3) ? dt[i] : 0;
+      if (t1[i] < t0[i]) continue;
+      out->dev_launches[k] += 1;
+      out->dev_ms[k] += (double)(t1[i] - t0[i]) * 1e-6;
+      out->dev_bytes[k] += by[i];
+    }
+  }
   return NYS_OK;
 }
 

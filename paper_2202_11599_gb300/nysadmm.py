@@ -34,7 +34,8 @@ class NysOptsC(ctypes.Structure):
                 ("pcg_fixed_iters", POINTER(c_int32)), ("admm_maxit", c_int32),
                 ("eps_abs", c_double), ("eps_rel", c_double), ("A_inner", POINTER(NysMatrixC)),
                 ("refine", c_int32), ("z_trace", c_void_p), ("rank_max", c_int32),
-                ("ada_tol", c_double), ("resketch_every", c_int32), ("stream", c_void_p)]
+                ("ada_tol", c_double), ("resketch_every", c_int32), ("stream", c_void_p),
+                ("device_loop", c_int32), ("hx_refresh", c_int32)]
 
 
 class NysInfoC(ctypes.Structure):
@@ -45,7 +46,8 @@ class NysInfoC(ctypes.Structure):
 
 class NysStatsC(ctypes.Structure):
     _fields_ = [("launches", c_int64), ("apass_launches", c_int64 * 3), ("apass_ms", c_double * 3),
-                ("apass_bytes", c_double * 3)]
+                ("apass_bytes", c_double * 3), ("dev_launches", c_int64 * 3), ("dev_ms", c_double * 3),
+                ("dev_bytes", c_double * 3)]
 
 
 class NysError(RuntimeError):
@@ -259,7 +261,8 @@ def nysadmm_solve(loss: str, A: Matrix, b: torch.Tensor, gamma: float, rho: floa
                   refine: bool = True, z_trace: bool = False, pcg_fixed=None, tol_mode: str = "rel",
                   pcg_maxit: int | None = None, eps_abs: float = 0.0, eps_rel: float = 0.0,
                   rank_max: int | None = None, ada_tol: float | None = None, resketch_every: int = 1,
-                  shift_scale: float | None = None, stream=None, allow_noconv: bool = True) -> dict:
+                  shift_scale: float | None = None, stream=None, allow_noconv: bool = True,
+                  device_loop: bool = True, hx_refresh: int = 0) -> dict:
     """NysADMM (Alg. NysADMM / AdaNysADMM) through the C ABI.  Returns a dict with
     x, z (FP64 device tensors), info (dict) and, when requested, the z trace."""
     d = A.d
@@ -276,7 +279,8 @@ def nysadmm_solve(loss: str, A: Matrix, b: torch.Tensor, gamma: float, rho: floa
               admm_maxit=admm_iters, eps_abs=eps_abs, eps_rel=eps_rel,
               A_inner=ctypes.pointer(A_inner.c) if A_inner is not None else None,
               refine=int(bool(refine)), z_trace=c_void_p(zt.data_ptr()) if zt is not None else None,
-              rank_max=rank_max or 0, ada_tol=ada_tol, resketch_every=resketch_every)
+              rank_max=rank_max or 0, ada_tol=ada_tol, resketch_every=resketch_every,
+              device_loop=int(bool(device_loop)), hx_refresh=int(hx_refresh))
     info = NysInfoC()
     st = lib().nysadmm_solve(_LOSSES[loss], ctypes.byref(A.c), _ptr(b.to(torch.float64).contiguous()),
                              float(gamma), float(rho), int(rank), float(tol), _ptr(Om), ctypes.byref(o),
@@ -311,4 +315,6 @@ def stats_read() -> dict:
     names = {NYS_F64: "f64", NYS_F32: "f32", NYS_BF16: "bf16"}
     return {"launches": s.launches,
             "apass": {names[k]: {"launches": s.apass_launches[k], "ms": s.apass_ms[k],
-                                 "bytes": s.apass_bytes[k]} for k in range(3)}}
+                                 "bytes": s.apass_bytes[k]} for k in range(3)},
+            "apass_dev": {names[k]: {"launches": s.dev_launches[k], "ms": s.dev_ms[k],
+                                     "bytes": s.dev_bytes[k]} for k in range(3)}}

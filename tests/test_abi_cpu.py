@@ -49,8 +49,10 @@ def test_struct_layouts_match_header(libpath):
     from paper_2202_11599_gb300 import nysadmm as nx
     # offsets follow C natural alignment of the header's structs
     assert ctypes.sizeof(nx.NysMatrixC) == 40
-    assert nx.NysOptsC.stream.offset == 96 and ctypes.sizeof(nx.NysOptsC) == 104
+    assert nx.NysOptsC.stream.offset == 96 and nx.NysOptsC.hx_refresh.offset == 108
+    assert ctypes.sizeof(nx.NysOptsC) == 112
     assert ctypes.sizeof(nx.NysInfoC) == 48
+    assert ctypes.sizeof(nx.NysStatsC) == 8 + 3 * 8 * 6
 
 
 def test_invalid_arguments_rejected_before_any_launch(libpath):

@@ -210,6 +210,44 @@ def test_lasso_trajectory_parity_fp64():
     assert out["info"]["r_p"] == pytest.approx(ref["trace"]["r_p"][-1], rel=1e-6)
 
 
+def test_device_loop_matches_host_loop_bitwise():
+    """The graph-driven loop launches the same kernels in the same order as the
+    host-driven loop: identical iterates."""
+    p = gen.lasso_problem(700, 130, nnz=9, seed=31)
+    Om = gen.gaussian_test_matrix(130, 16, 31)
+    M = nx.Matrix.padded(_dev(p.A))
+    kw = dict(admm_iters=60, z_trace=True)
+    a = nx.nysadmm_solve("lasso", M, _dev(p.b), p.gamma, 3.0, 16, 1e-9, _dev(Om), device_loop=True, **kw)
+    b = nx.nysadmm_solve("lasso", M, _dev(p.b), p.gamma, 3.0, 16, 1e-9, _dev(Om), device_loop=False, **kw)
+    assert torch.equal(a["x"], b["x"]) and torch.equal(a["z"], b["z"])
+    assert torch.equal(a["z_trace"], b["z_trace"])
+    assert a["info"]["pcg_iters_total"] == b["info"]["pcg_iters_total"]
+    for dtype in (torch.bfloat16, torch.float32):
+        Mi = nx.Matrix.padded(_dev(p.A), dtype)
+        for refine in (False, True):
+            a = nx.nysadmm_solve("lasso", M, _dev(p.b), p.gamma, 3.0, 16, 1e-5, _dev(Om), A_inner=Mi,
+                                 refine=refine, device_loop=True, **kw)
+            b = nx.nysadmm_solve("lasso", M, _dev(p.b), p.gamma, 3.0, 16, 1e-5, _dev(Om), A_inner=Mi,
+                                 refine=refine, device_loop=False, **kw)
+            assert torch.equal(a["z"], b["z"])
+
+
+def test_device_loop_residual_stop_and_tracked_warm_start():
+    p = gen.lasso_problem(900, 150, nnz=10, seed=32)
+    Om = gen.gaussian_test_matrix(150, 20, 32)
+    ref = o.lasso_nysadmm(p.A, p.b, p.gamma, 10.0, Om, 500, pcg_tol=1e-12)
+    M = nx.Matrix.padded(_dev(p.A))
+    for refresh in (1, 7, 50):
+        out = nx.nysadmm_solve("lasso", M, _dev(p.b), p.gamma, 10.0, 20, 1e-12, _dev(Om), admm_iters=500,
+                               hx_refresh=refresh)
+        z = out["z"].cpu().numpy()
+        assert np.linalg.norm(z - ref["z"]) <= 1e-8 * np.linalg.norm(ref["z"])
+    out = nx.nysadmm_solve("lasso", M, _dev(p.b), p.gamma, 10.0, 20, 1e-10, _dev(Om), admm_iters=500,
+                           eps_abs=0.0, eps_rel=1e-4)
+    ref2 = o.lasso_nysadmm(p.A, p.b, p.gamma, 10.0, Om, 500, pcg_tol=1e-10, eps_abs=0.0, eps_rel=1e-4)
+    assert out["info"]["admm_iters"] == len(ref2["trace"]["pcg_iters"]) < 500
+
+
 def test_lasso_tolerance_mode_runs_and_converges():
     p = gen.lasso_problem(800, 120, nnz=10, seed=21)
     Om = gen.gaussian_test_matrix(120, 20, 21)
