@@ -747,7 +747,8 @@ cudaError_t apass_run(const ApassArgs& a, const ApassPlan& plan, void* partial, 
   if (allow_stats && !g_prepare_only) k.tm = stats_device_timer();
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int* flag = nullptr;
-  const bool prof = allow_stats && !g_prepare_only && stats_enabled() &&
+  // events cannot bracket a kernel node being captured into a graph; the in-kernel timer can
+  const bool prof = allow_stats && !g_prepare_only && !launch_capturing() && stats_enabled() &&
                     stats_event_pair(&e0, &e1, &flag) == cudaSuccess;
   if (prof) {
     k.executed = flag;

@@ -98,6 +98,7 @@ cudaError_t convert_f32_to_f64(const float* x, double* y, int64_t n, cudaStream_
 void count_launch();
 void count_launch_suspend(bool on);     // while capturing a graph: launches are counted on execution
 void count_launch_add(long long n);     // executed graph kernel nodes
+bool launch_capturing();                // true between count_launch_suspend(true) and (false)
 // Set the launch attributes of the A-pass instantiation for this matrix (outside capture).
 cudaError_t apass_prepare(const nys_matrix* A, const ApassPlan& plan);
 bool stats_enabled();

@@ -754,7 +754,7 @@ nys_status admm_graph_run(const GraphLoopArgs& g, cudaStream_t stream, GraphLoop
     ar.D_out = nullptr;
     ar.t_out = nullptr;
     ar.mode = MODE_RESID;
-    G_OK(apass_run(ar, g.plan_ref, apart_ref, nullptr, dstat, cap, false));
+    G_OK(apass_run(ar, g.plan_ref, apart_ref, nullptr, dstat, cap, true));
     ApassArgs ar2 = ar;
     ar2.p = nullptr;
     G_OK(apass_reduce(ar2, g.plan_ref, apart_ref, 0.0, g.yres, nullptr, 0, cap));
@@ -764,7 +764,7 @@ nys_status admm_graph_run(const GraphLoopArgs& g, cudaStream_t stream, GraphLoop
   ++seg_nodes;
   aa.p = xc;
   aa.skip = &ctl->hx_skip;
-  G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, false));
+  G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, true));
   G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho, hx, nullptr, 0, cap));
   seg_nodes += 2;
   pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, cap>>>(1, d, chunk, xc, w, rc, hx, p, U, s, pv_part, nbr,
@@ -793,7 +793,7 @@ nys_status admm_graph_run(const GraphLoopArgs& g, cudaStream_t stream, GraphLoop
   G_OK(cudaStreamBeginCaptureToGraph(cap, pbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   aa.p = p;
   aa.skip = &st->done;
-  G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, false));
+  G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, true));
   G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho, v, pv_part, nbr, cap));
   pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, cap>>>(0, d, chunk, xc, w, rc, v, p, U, s, pv_part, nbr, wy_part,
                                                           nb5, part_w2, part_r2, part_g, st, hx);

@@ -35,6 +35,7 @@ void count_launch() {
   if (!g_count_suspended) g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 void count_launch_suspend(bool on) { g_count_suspended = on; }
+bool launch_capturing() { return g_count_suspended; }
 void count_launch_add(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 bool stats_enabled() { return g_enabled.load(std::memory_order_relaxed); }
