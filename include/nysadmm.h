@@ -195,6 +195,19 @@ nys_status nysadmm_solve(int32_t loss, const nys_matrix* A, const double* b, dou
                          double rho, int32_t rank, double tol, const double* Omega,
                          const nys_opts* opts, double* x_out, double* z_out, nys_info* info);
 
+/* Lasso regularisation path: k NysADMM lasso solves (Alg. NysADMM) that share A,
+ * b, rho and the Nystrom preconditioner and differ in gamma (gammas: host, k).
+ * Because the x-subproblem matrix A^T A + rho I (Eq. ADMMSubProb) is common to
+ * all k problems, the k PCG solves run side by side: each matvec reads A (or
+ * opts->A_inner) once for all k right-hand sides as two dense products, and each
+ * column keeps its own PCG scalars and stop test.  opts->admm_maxit ADMM
+ * iterations are run for every gamma (opts->refine and device_loop do not apply).
+ * X_out, Z_out: device, d x k column-major FP64 (column c = problem c), may be
+ * NULL.  pcg_iters: host, k (total PCG iterations per column), may be NULL. */
+nys_status nysadmm_solve_path(const nys_matrix* A, const double* b, const double* gammas, int32_t k, double rho,
+                              int32_t rank, double tol, const double* Omega, const nys_opts* opts, double* X_out,
+                              double* Z_out, nys_info* info, int32_t* pcg_iters);
+
 /* Objective and optimality measures at x (FP64, one read of A):
  * out[0] = l(Ax; b) + gamma ||x||_1 (Eq. 2 or Eq. 9);
  * out[1] = relative KKT residual eta (Eq. 31; lasso) or ||A^T(sigma(Ax)-b01)||_inf (logistic);

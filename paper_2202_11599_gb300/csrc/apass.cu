@@ -488,25 +488,48 @@ __global__ void __launch_bounds__(kApassThreads, 1) apass_f_kernel(const ApassKA
       issue(k + S);
       ++issued;
     }
-    if (warp < R) {
-      float t = 0.f;
-      if (!nodot) t = warp_sum(lane < NW ? red[k & 1][lane][warp] : 0.f);
-      if (lane == 0) {
-        float u = 0.f;
-        if (warp < rows_here) {
-          const int64_t i = r0 + (int64_t)k * R + warp;
-          u = row_phi(a, i, t, loss);
-          if (!nodot && a.t_out) a.t_out[i] = (double)t;
-        }
-        us[k & 1][warp] = u;
-      }
-    }
-    __syncthreads();
     float2 u2[R];
+    // FP32 storage, H-matvec modes: the per-warp finish below removes the second barrier
+    // (measured 5.8 -> 7.0 TB/s).  BF16 keeps the two-barrier step: at R = 4 its raw
+    // registers leave no room for the extra row sums (measured 4.1 -> 2.8 TB/s), and
+    // at R = 2 the per-step overhead dominates (2.7-2.8 TB/s either way).
+    if (DT == NYS_F32 && (a.mode == MODE_ID || a.mode == MODE_DIAG)) {
+      // every warp finishes all R row sums itself (lanes 0..NW-1 hold
+      // the warp partials of each row; a butterfly leaves the sum in every lane), so no
+      // second barrier is needed.  Warp r's lane 0 writes row r's side outputs.
+      float t[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const float u = us[k & 1][r];
-      u2[r] = make_float2(u, u);
+      for (int r = 0; r < R; ++r) t[r] = warp_sum(lane < NW ? red[k & 1][lane][r] : 0.f);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float u = 0.f;
+        if (r < rows_here) {
+          const int64_t i = r0 + (int64_t)k * R + r;
+          u = a.mode == MODE_ID ? t[r] : (float)(a.D[i] * (double)t[r]);
+          if (warp == r && lane == 0 && a.t_out) a.t_out[i] = (double)t[r];
+        }
+        u2[r] = make_float2(u, u);
+      }
+    } else {
+      if (warp < R) {
+        float t = 0.f;
+        if (!nodot) t = warp_sum(lane < NW ? red[k & 1][lane][warp] : 0.f);
+        if (lane == 0) {
+          float u = 0.f;
+          if (warp < rows_here) {
+            const int64_t i = r0 + (int64_t)k * R + warp;
+            u = row_phi(a, i, t, loss);
+            if (!nodot && a.t_out) a.t_out[i] = (double)t;
+          }
+          us[k & 1][warp] = u;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float u = us[k & 1][r];
+        u2[r] = make_float2(u, u);
+      }
     }
 #pragma unroll
     for (int kk = 0; kk < VPT; ++kk) {

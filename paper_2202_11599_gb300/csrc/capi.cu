@@ -505,6 +505,109 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
   return result;
 }
 
+// ---------------------------------------------------------------- lasso regularisation path (k gammas)
+template <typename C>
+nys_status lasso_path(const nys_matrix* A, const nys_matrix* Ain, const double* b, const double* gammas, int k,
+                      double rho, int rank, double tol, const double* Omega, const nys_opts& o, double* X_out,
+                      double* Z_out, nys_info* info, int32_t* iters_out, cudaStream_t st) {
+  const int64_t d = A->d;
+  Pool pool(st);
+  nys_precond_s P;
+  struct Guard {
+    nys_precond_s* p;
+    ~Guard() {
+      if (p->U64) cudaFree(p->U64);
+      if (p->U32) cudaFree(p->U32);
+      if (p->lam_d) cudaFree(p->lam_d);
+    }
+  } guard{&P};
+  double* Om = pool.alloc<double>((size_t)d * rank);
+  double* Y = pool.alloc<double>((size_t)d * rank);
+  if (!pool.ok()) return NYS_ENOMEM;
+  NYS_CU(cudaMemcpyAsync(Om, Omega, (size_t)d * rank * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  NYS_TRY(cholqr2(Om, d, rank, st));
+  NYS_TRY(sketch_panel(Ain, nullptr, 0.0, Om, rank, Y, st));
+  const double shs = o.shift_scale > 0 ? o.shift_scale : std::sqrt((double)d);
+  NYS_TRY(precond_from_panels(Om, Y, d, rank, shs, mant_bits_of(Ain), &P, st));
+  C* cbuf = pool.alloc<C>(rank);
+  const int64_t len = d * k;
+  double* X = pool.alloc<double>(len);
+  double* Z = pool.alloc<double>(len);
+  double* Uu = pool.alloc<double>(len);
+  double* q = pool.alloc<double>(d);
+  double* kappa = pool.alloc<double>(k);
+  C* Xc = pool.alloc<C>(len);
+  C* Rc = pool.alloc<C>(len);
+  void* ytmp = pool.alloc<unsigned char>(d * 8);
+  double* part = pool.alloc<double>((size_t)batched_zu_blocks(d) * k * 2);
+  if (!pool.ok()) return NYS_ENOMEM;
+  PrecondView view;
+  NYS_TRY(precond_view<C>(&P, rho, cbuf, st, &view));
+  std::vector<double> kap(k);
+  for (int c = 0; c < k; ++c) kap[c] = gammas[c] / rho;
+  NYS_CU(cudaMemcpyAsync(kappa, kap.data(), k * sizeof(double), cudaMemcpyHostToDevice, st));
+  NYS_CU(cudaMemsetAsync(X, 0, len * sizeof(double), st));
+  NYS_CU(cudaMemsetAsync(Z, 0, len * sizeof(double), st));
+  NYS_CU(cudaMemsetAsync(Uu, 0, len * sizeof(double), st));
+  NYS_CU(cudaMemsetAsync(Xc, 0, len * sizeof(C), st));
+  NYS_TRY(aux_pass(A, MODE_CONST, nullptr, b, nullptr, nullptr, ytmp, nullptr, st));
+  NYS_TRY(to_f64(A, ytmp, q, d, st));
+  PcgProblem pb;
+  pb.A = Ain;
+  pb.D = nullptr;
+  pb.rho = rho;
+  apass_plan(Ain, &pb.plan);
+  const int maxit = o.pcg_maxit > 0 ? o.pcg_maxit : (int)std::min<int64_t>(d, 1000);
+  const int K = std::max(1, o.admm_maxit);
+  nys_status result = NYS_OK;
+  std::vector<int> its, tot(k, 0);
+  int nbz = 0;
+  for (int it = 0; it < K; ++it) {
+    NYS_CU(batched_rhs<C>(d, k, q, Z, Uu, rho, Rc, st));
+    PcgParams prm;
+    prm.tol = tol;
+    prm.tol_abs = o.pcg_tol_mode == NYS_TOL_ABS;
+    prm.maxit = maxit;
+    prm.x0_zero = it == 0;
+    if (o.pcg_fixed_iters) prm.fixed = o.pcg_fixed_iters[it];
+    nys_status s = batched_pcg_run<C>(pb, view, Rc, Xc, k, prm, st, &its);
+    if (s == NYS_ENOCONV) result = NYS_ENOCONV;
+    else if (s != NYS_OK) return s;
+    for (int c = 0; c < k; ++c) tot[c] += its[c];
+    NYS_CU(batched_zu<C>(d, k, Xc, X, Z, Uu, kappa, part, &nbz, st));
+  }
+  if (X_out) NYS_CU(cudaMemcpyAsync(X_out, X, len * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (Z_out) NYS_CU(cudaMemcpyAsync(Z_out, Z, len * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  std::vector<double> hp((size_t)nbz * k * 2);
+  if (nbz) NYS_CU(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  NYS_CU(cudaStreamSynchronize(st));
+  if (iters_out)
+    for (int c = 0; c < k; ++c) iters_out[c] = tot[c];
+  if (info) {
+    double rp = 0, rd = 0;  // worst column
+    for (int c = 0; c < k; ++c) {
+      double a0 = 0, a1 = 0;
+      for (int bb = 0; bb < nbz; ++bb) {
+        a0 += hp[((size_t)bb * k + c) * 2];
+        a1 += hp[((size_t)bb * k + c) * 2 + 1];
+      }
+      rp = std::max(rp, std::sqrt(a0));
+      rd = std::max(rd, rho * std::sqrt(a1));
+    }
+    int total = 0;
+    for (int c = 0; c < k; ++c) total += tot[c];
+    info->admm_iters = K;
+    info->pcg_iters_total = total;
+    info->final_rank = rank;
+    info->status = result;
+    info->r_p = rp;
+    info->r_d = rd;
+    info->nu = P.nu;
+    info->emp_cond = (P.lam.back() + rho) / rho;
+  }
+  return result;
+}
+
 // ---------------------------------------------------------------- logistic (Sec. 3.2) + AdaRandNysAppx (App. C)
 template <typename C>
 nys_status logistic_admm(const nys_matrix* A, const nys_matrix* Ain, const double* b, double gamma, double rho,
@@ -876,6 +979,29 @@ nys_status nysadmm_solve(int32_t loss, const nys_matrix* A, const double* b, dou
   }
   return Ain->dtype == NYS_F64 ? logistic_admm<double>(A, Ain, b, gamma, rho, rank, tol, Omega, o, x_out, z_out, info, st)
                                : logistic_admm<float>(A, Ain, b, gamma, rho, rank, tol, Omega, o, x_out, z_out, info, st);
+}
+
+nys_status nysadmm_solve_path(const nys_matrix* A, const double* b, const double* gammas, int32_t k, double rho,
+                              int32_t rank, double tol, const double* Omega, const nys_opts* opts, double* X_out,
+                              double* Z_out, nys_info* info, int32_t* pcg_iters) {
+  NYS_TRY(check_matrix(A));
+  if (!b || !Omega || !gammas || k < 1 || k > 4096 || !(rho > 0) || !is_fin(rho)) return NYS_EINVAL;
+  for (int c = 0; c < k; ++c)
+    if (!(gammas[c] >= 0) || !is_fin(gammas[c])) return NYS_EINVAL;
+  if (rank < 1 || rank > A->d || rank > kMaxRank || !(tol >= 0) || !is_fin(tol)) return NYS_EINVAL;
+  nys_opts o;
+  if (opts) o = *opts;
+  else nys_opts_default(&o);
+  const nys_matrix* Ain = o.A_inner ? o.A_inner : A;
+  if (o.A_inner) {
+    NYS_TRY(check_matrix(Ain));
+    if (Ain->n != A->n || Ain->d != A->d) return NYS_EINVAL;
+  }
+  cudaStream_t st = stream_of(&o);
+  if (info) std::memset(info, 0, sizeof(*info));
+  return Ain->dtype == NYS_F64
+             ? lasso_path<double>(A, Ain, b, gammas, k, rho, rank, tol, Omega, o, X_out, Z_out, info, pcg_iters, st)
+             : lasso_path<float>(A, Ain, b, gammas, k, rho, rank, tol, Omega, o, X_out, Z_out, info, pcg_iters, st);
 }
 
 nys_status nys_objective(int32_t loss, const nys_matrix* A, const double* b, double gamma, const double* x,

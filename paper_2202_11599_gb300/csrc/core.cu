@@ -22,16 +22,17 @@ namespace nys {
 // Cp + z*M*N (column-major, ld M).  Tile 64 x 64, 256 threads, 4 x 4 per thread.
 constexpr int GT = 64, GK = 16;
 
-__global__ void __launch_bounds__(256) gemm_f64_kernel(const double* __restrict__ A, int64_t lda, bool transA,
-                                                       const double* __restrict__ B, int64_t ldb, int M, int N,
-                                                       int64_t K, int64_t kchunk, double* __restrict__ Cp) {
-  __shared__ double As[GK][GT + 1];
-  __shared__ double Bs[GK][GT + 1];
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_t_kernel(const T* __restrict__ A, int64_t lda, bool transA,
+                                                     const T* __restrict__ B, int64_t ldb, int M, int N,
+                                                     int64_t K, int64_t kchunk, T* __restrict__ Cp) {
+  __shared__ T As[GK][GT + 1];
+  __shared__ T Bs[GK][GT + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int m0 = blockIdx.x * GT, n0 = blockIdx.y * GT;
   const int64_t kb = (int64_t)blockIdx.z * kchunk;
   const int64_t ke = min(K, kb + kchunk);
-  double acc[4][4] = {};
+  T acc[4][4] = {};
   for (int64_t k0 = kb; k0 < ke; k0 += GK) {
     for (int idx = threadIdx.x; idx < GK * GT; idx += 256) {
       int kk, mm;
@@ -44,18 +45,18 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const double* __restrict_
       }
       const int64_t k = k0 + kk;
       const int m = m0 + mm;
-      double v = 0.0;
+      T v = T(0);
       if (k < ke && m < M) v = transA ? A[k + (int64_t)m * lda] : A[m + k * lda];
       As[kk][mm] = v;
       const int nn = idx / GK, kk2 = idx % GK;
       const int64_t k2 = k0 + kk2;
       const int n = n0 + nn;
-      Bs[kk2][nn] = (k2 < ke && n < N) ? B[k2 + (int64_t)n * ldb] : 0.0;
+      Bs[kk2][nn] = (k2 < ke && n < N) ? B[k2 + (int64_t)n * ldb] : T(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      double a[4], b[4];
+      T a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
 #pragma unroll
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const double* __restrict_
     }
     __syncthreads();
   }
-  double* C = Cp + (int64_t)blockIdx.z * M * N;
+  T* C = Cp + (int64_t)blockIdx.z * M * N;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -76,6 +77,51 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const double* __restrict_
       if (m < M && n < N) C[m + (int64_t)n * M] = acc[i][j];
     }
 }
+#define gemm_f64_kernel gemm_t_kernel<double>
+
+// C (M x N) = sum_z Cp[z] in a fixed order, compute type T
+template <typename T>
+__global__ void sum_partials_t_kernel(const T* __restrict__ Cp, int nz, int64_t len, T* __restrict__ C) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    T s = T(0);
+    for (int z = 0; z < nz; ++z) s += Cp[z * len + i];
+    C[i] = s;
+  }
+}
+
+// C (M x N) = X^T Y with X (K x M), Y (K x N) column-major (ld K); split over K, fixed-order sum.
+template <typename T>
+cudaError_t gemm_tn(const T* X, const T* Y, int64_t K, int M, int N, T* C, T* work, cudaStream_t st) {
+  const int64_t kc = std::max<int64_t>(256, ((K + 63) / 64 + GK - 1) / GK * GK);
+  const int nz = (int)((K + kc - 1) / kc);
+  dim3 grid((M + GT - 1) / GT, (N + GT - 1) / GT, nz);
+  count_launch();
+  gemm_t_kernel<T><<<grid, 256, 0, st>>>(X, K, true, Y, K, M, N, K, kc, work);
+  NYS_CUDA_TRY(cudaGetLastError());
+  count_launch();
+  sum_partials_t_kernel<T><<<(unsigned)std::min<int64_t>(1024, ((int64_t)M * N + 255) / 256), 256, 0, st>>>(
+      work, nz, (int64_t)M * N, C);
+  return cudaGetLastError();
+}
+template <typename T>
+size_t gemm_tn_work_elems(int64_t K, int M, int N) {
+  const int64_t kc = std::max<int64_t>(256, ((K + 63) / 64 + GK - 1) / GK * GK);
+  return (size_t)((K + kc - 1) / kc) * M * N;
+}
+// C (M x N) = B (M x K) V (K x N), column-major
+template <typename T>
+cudaError_t gemm_nn_t(const T* B, int64_t M, int K, const T* V, int N, T* C, cudaStream_t st) {
+  dim3 grid((unsigned)((M + GT - 1) / GT), (N + GT - 1) / GT, 1);
+  count_launch();
+  gemm_t_kernel<T><<<grid, 256, 0, st>>>(B, M, false, V, K, (int)M, N, K, K, C);
+  return cudaGetLastError();
+}
+template cudaError_t gemm_tn<float>(const float*, const float*, int64_t, int, int, float*, float*, cudaStream_t);
+template cudaError_t gemm_tn<double>(const double*, const double*, int64_t, int, int, double*, double*, cudaStream_t);
+template size_t gemm_tn_work_elems<float>(int64_t, int, int);
+template size_t gemm_tn_work_elems<double>(int64_t, int, int);
+template cudaError_t gemm_nn_t<float>(const float*, int64_t, int, const float*, int, float*, cudaStream_t);
+template cudaError_t gemm_nn_t<double>(const double*, int64_t, int, const double*, int, double*, cudaStream_t);
 
 // C = alpha * sum_z Cp[z] (fixed order)
 __global__ void sum_partials_kernel(const double* __restrict__ Cp, int nz, int64_t len, double* __restrict__ C) {
@@ -655,6 +701,31 @@ cudaError_t sketch_atw(const nys_matrix* A, const void* W, int s, double* Y, voi
       break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+// Partials of A^T W only (nz slices of d x s in compute type); returns nz.
+cudaError_t sketch_atw_partials(const nys_matrix* A, const void* W, int s, void* work, size_t work_bytes, int* nz_out,
+                                cudaStream_t st) {
+  const int64_t kc = atw_kchunk(A->n, A->d, s);
+  const int nz = (int)((A->n + kc - 1) / kc);
+  if (work_bytes < sketch_atw_work_bytes(A, s)) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)((A->d + GT - 1) / GT), (s + GT - 1) / GT, nz);
+  const unsigned char* Ar = reinterpret_cast<const unsigned char*>(A->data);
+  count_launch();
+  switch (A->dtype) {
+    case NYS_F64:
+      sketch_atw_kernel<NYS_F64><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const double*)W, s, kc, (double*)work);
+      break;
+    case NYS_F32:
+      sketch_atw_kernel<NYS_F32><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const float*)W, s, kc, (float*)work);
+      break;
+    case NYS_BF16:
+      sketch_atw_kernel<NYS_BF16><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const float*)W, s, kc, (float*)work);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  *nz_out = nz;
   return cudaGetLastError();
 }
 

@@ -88,6 +88,15 @@ cudaError_t sketch_aw(const nys_matrix* A, const void* Omega, int s, const doubl
 cudaError_t sketch_atw(const nys_matrix* A, const void* W, int s, double* Y, void* work,
                        size_t work_bytes, cudaStream_t st);
 size_t sketch_atw_work_bytes(const nys_matrix* A, int s);
+cudaError_t sketch_atw_partials(const nys_matrix* A, const void* W, int s, void* work, size_t work_bytes, int* nz_out,
+                                cudaStream_t st);
+// small dense GEMMs in compute type T (column-major)
+template <typename T>
+cudaError_t gemm_tn(const T* X, const T* Y, int64_t K, int M, int N, T* C, T* work, cudaStream_t st);
+template <typename T>
+size_t gemm_tn_work_elems(int64_t K, int M, int N);
+template <typename T>
+cudaError_t gemm_nn_t(const T* B, int64_t M, int K, const T* V, int N, T* C, cudaStream_t st);
 
 // ---------------------------------------------------------------- helpers
 cudaError_t convert_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t st);

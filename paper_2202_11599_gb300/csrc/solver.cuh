@@ -93,6 +93,18 @@ int pcg_nb3(int64_t d);
 
 PcgState* host_state();
 
+// Multi-RHS PCG (k columns sharing H + rho I and P); R, X: d x k column-major.
+template <typename C>
+nys_status batched_pcg_run(const PcgProblem& pb, const PrecondView& P, const C* R, C* X, int k, const PcgParams& prm,
+                           cudaStream_t st, std::vector<int>* iters_out);
+template <typename C>
+cudaError_t batched_rhs(int64_t d, int k, const double* q, const double* Z, const double* Uu, double rho, C* R,
+                        cudaStream_t st);
+template <typename C>
+cudaError_t batched_zu(int64_t d, int k, const C* Xc, double* X, double* Z, double* Uu, const double* kappa,
+                       double* part, int* nb_out, cudaStream_t st);
+int batched_zu_blocks(int64_t d);
+
 // Device-side lasso ADMM loop (one CUDA graph with conditional WHILE nodes).
 struct GraphLoopArgs {
   PcgProblem pb;             // PCG matrix (A_inner or A), D, rho, plan

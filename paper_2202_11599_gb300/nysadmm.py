@@ -82,6 +82,8 @@ def lib() -> ctypes.CDLL:
                             P(NysOptsC), P(c_int32), P(c_double)]
     L.nysadmm_solve.argtypes = [c_int32, P(NysMatrixC), c_void_p, c_double, c_double, c_int32, c_double,
                                 c_void_p, P(NysOptsC), c_void_p, c_void_p, P(NysInfoC)]
+    L.nysadmm_solve_path.argtypes = [P(NysMatrixC), c_void_p, P(c_double), c_int32, c_double, c_int32, c_double,
+                                     c_void_p, P(NysOptsC), c_void_p, c_void_p, P(NysInfoC), P(c_int32)]
     L.nys_objective.argtypes = [c_int32, P(NysMatrixC), c_void_p, c_double, c_void_p, P(c_double), c_void_p]
     L.nys_stats_enable.argtypes = [c_int32]
     L.nys_stats_enable.restype = None
@@ -89,7 +91,7 @@ def lib() -> ctypes.CDLL:
     L.nys_precond_destroy.argtypes = [c_void_p]
     L.nys_precond_destroy.restype = None
     for name in ("nys_hmatvec", "nys_hmatvec_noalloc", "nys_sketch", "nys_precond_get", "nys_precond_apply", "pcg_solve",
-                 "nysadmm_solve", "nys_objective", "nys_stats_read"):
+                 "nysadmm_solve", "nysadmm_solve_path", "nys_objective", "nys_stats_read"):
         getattr(L, name).restype = c_int32
     _lib = L
     return L
@@ -292,6 +294,36 @@ def nysadmm_solve(loss: str, A: Matrix, b: torch.Tensor, gamma: float, rho: floa
     if zt is not None:
         out["z_trace"] = zt[: inf["admm_iters"]]
     return out
+
+
+def nysadmm_solve_path(A: Matrix, b: torch.Tensor, gammas, rho: float, rank: int, tol: float,
+                       Omega: torch.Tensor, admm_iters: int = 200, A_inner: Matrix | None = None,
+                       tol_mode: str = "rel", pcg_maxit: int | None = None, pcg_fixed=None,
+                       shift_scale: float | None = None, stream=None, allow_noconv: bool = True) -> dict:
+    """k lasso solves along a regularisation path (one gamma per column) with shared
+    multi-right-hand-side PCG.  Returns X, Z (d x k FP64), pcg iterations per column, info."""
+    d = A.d
+    k = len(gammas)
+    Om = Omega.to(torch.float64).T.contiguous()
+    X = torch.empty(k, d, dtype=torch.float64, device="cuda")           # column-major d x k
+    Z = torch.empty(k, d, dtype=torch.float64, device="cuda")
+    g = (c_double * k)(*[float(v) for v in gammas])
+    its = (c_int32 * k)()
+    fixed = None
+    if pcg_fixed is not None:
+        seq = [int(pcg_fixed)] * admm_iters if isinstance(pcg_fixed, int) else [int(v) for v in pcg_fixed]
+        fixed = (c_int32 * len(seq))(*seq)
+    o = _opts(stream, shift_scale=shift_scale, pcg_tol_mode=TOL_MODES[tol_mode], pcg_maxit=pcg_maxit or 0,
+              admm_maxit=admm_iters, A_inner=ctypes.pointer(A_inner.c) if A_inner is not None else None,
+              pcg_fixed_iters=ctypes.cast(fixed, POINTER(c_int32)) if fixed is not None else None)
+    info = NysInfoC()
+    st = lib().nysadmm_solve_path(ctypes.byref(A.c), _ptr(b.to(torch.float64).contiguous()), g, k, float(rho),
+                                  int(rank), float(tol), _ptr(Om), ctypes.byref(o), _ptr(X), _ptr(Z),
+                                  ctypes.byref(info), its)
+    _check(st, "nysadmm_solve_path", ok=(NYS_OK, NYS_ENOCONV) if allow_noconv else (NYS_OK,))
+    inf = {f: getattr(info, f) for f, _ in NysInfoC._fields_}
+    inf["status"] = st
+    return {"X": X.T, "Z": Z.T, "pcg_iters": list(its), "info": inf}
 
 
 def objective(loss: str, A: Matrix, b: torch.Tensor, gamma: float, x: torch.Tensor, stream=None):

@@ -352,3 +352,44 @@ def test_full_size_bf16_hmatvec_sampled():
     yref += 0.5 * pd[cols]
     err = ((y[cols] - yref).abs() / scale).max().item()
     assert err <= 2e-5
+
+
+def test_regularisation_path_matches_single_solves_and_oracle():
+    """k lasso problems sharing A, b, rho (gammas differ): the multi-RHS path gives,
+    column by column, what k independent solves give (FP64: 1e-10), and the oracle's
+    solutions."""
+    p = gen.lasso_problem(1500, 200, nnz=12, seed=41)
+    Om = gen.gaussian_test_matrix(200, 24, 41)
+    gmax = np.max(np.abs(p.A.T @ p.b))
+    gammas = list(gmax * np.logspace(-3, -0.3, 6))
+    M = nx.Matrix.padded(_dev(p.A))
+    K = 250
+    out = nx.nysadmm_solve_path(M, _dev(p.b), gammas, 10.0, 24, 1e-12, _dev(Om), admm_iters=K)
+    Z = out["Z"].cpu().numpy()
+    X = out["X"].cpu().numpy()
+    for c, g in enumerate(gammas):
+        single = nx.nysadmm_solve("lasso", M, _dev(p.b), g, 10.0, 24, 1e-12, _dev(Om), admm_iters=K)
+        zs = single["z"].cpu().numpy()
+        assert np.linalg.norm(Z[:, c] - zs) <= 1e-10 * max(1e-300, np.linalg.norm(zs)) + 1e-14
+        assert np.linalg.norm(X[:, c] - single["x"].cpu().numpy()) <= 1e-10 * np.linalg.norm(X[:, c]) + 1e-14
+    ref = o.lasso_nysadmm(p.A, p.b, gammas[2], 10.0, Om, K, pcg_tol=1e-12)
+    assert np.linalg.norm(Z[:, 2] - ref["z"]) <= 1e-9 * np.linalg.norm(ref["z"])
+    assert len(out["pcg_iters"]) == 6 and min(out["pcg_iters"]) > 0
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_regularisation_path_low_precision(dtype):
+    p = gen.lasso_problem(2000, 256, nnz=12, seed=42)
+    Om = gen.gaussian_test_matrix(256, 24, 42)
+    gmax = np.max(np.abs(p.A.T @ p.b))
+    gammas = list(gmax * np.logspace(-2.5, -0.5, 5))
+    M = nx.Matrix.padded(_dev(p.A))
+    Mi = nx.Matrix.padded(_dev(p.A), dtype)
+    out = nx.nysadmm_solve_path(M, _dev(p.b), gammas, 10.0, 24, 1e-5, _dev(Om), admm_iters=150, A_inner=Mi)
+    Z = out["Z"].cpu().numpy()
+    for c, g in enumerate(gammas):
+        single = nx.nysadmm_solve("lasso", M, _dev(p.b), g, 10.0, 24, 1e-5, _dev(Om), admm_iters=150, A_inner=Mi,
+                                  refine=False)
+        zs = single["z"].cpu().numpy()
+        # same algorithm and stored matrix; FP32 reductions in a different order
+        assert np.linalg.norm(Z[:, c] - zs) <= 1e-4 * max(1.0, np.linalg.norm(zs))
