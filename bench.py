@@ -426,6 +426,76 @@ def run_reference(args):
     print(json.dumps(res), flush=True)
 
 
+def extra_batched(args):
+    """Batched forms (separate JSON line, not the headline metric):
+    (i) a 64-point lasso regularisation path sharing one 50,000 x 4,000 FP32 matrix
+        (decay (1+j)^-1), gamma log-spaced in [1e-3, 1] ||A^T b||_inf, rank 50, rho 100:
+        multi-RHS path vs 64 sequential single solves, same ADMM iterations;
+    (ii) 32 independent lasso instances, d uniform in [500, 8000] (seed 4), n = 10 d,
+        FP32, rank 50: one graph launch vs 32 sequential device-loop solves."""
+    from paper_2202_11599_gb300 import nysadmm as nx
+    import __graft_entry__
+    __graft_entry__.build()
+    K = args.extra_iters
+    dev = "cuda"
+    # (i) path
+    n, d, kpath, s = 50_000, 4_000, 64, 50
+    W = gen.lasso_large_torch(n, d, nnz_frac=0.01, noise=1e-3, gamma_frac=1.0, seed=3, rotate=False, device=dev)
+    A32, b, gmax = W["A32"], W["b"], W["gamma"]
+    M = nx.Matrix(A32)
+    gammas = list(np.logspace(-3, 0, kpath) * gmax)
+    g = torch.Generator(device=dev).manual_seed(13)
+    Om = torch.randn(d, s, generator=g, device=dev, dtype=torch.float64)
+    rho, tol = 100.0, 1e-4
+    nx.nysadmm_solve_path(M, b, gammas[:2], rho, s, tol, Om, admm_iters=2)          # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = nx.nysadmm_solve_path(M, b, gammas, rho, s, tol, Om, admm_iters=K)
+    torch.cuda.synchronize()
+    t_path = time.perf_counter() - t0
+    nx.nysadmm_solve("lasso", M, b, gammas[0], rho, s, tol, Om, admm_iters=2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    zs = []
+    for gm in gammas:
+        zs.append(nx.nysadmm_solve("lasso", M, b, gm, rho, s, tol, Om, admm_iters=K, hx_refresh=10)["z"])
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    Zp = out["Z"]
+    dev_max = max(((Zp[:, c] - zs[c]).norm() / max(zs[c].norm().item(), 1e-30)).item() for c in range(kpath))
+    path = {"n": n, "d": d, "k": kpath, "rank": s, "admm_iters": K, "time_path_s": round(t_path, 3),
+            "time_64_single_s": round(t_single, 3), "speedup": round(t_single / t_path, 2),
+            "max_rel_diff_vs_single": dev_max, "pcg_iters_total": out["info"]["pcg_iters_total"]}
+    del A32, M, W, out, zs
+    torch.cuda.empty_cache()
+    # (ii) uneven batch
+    rng = np.random.default_rng(4)
+    dims = rng.integers(500, 8001, size=32)
+    probs = []
+    for i, di in enumerate(dims):
+        di = int(di)
+        Wi = gen.lasso_large_torch(10 * di, di, nnz_frac=0.01, noise=1e-3, gamma_frac=0.05, seed=100 + i,
+                                   rotate=False, device=dev)
+        gi = torch.Generator(device=dev).manual_seed(200 + i)
+        Omi = torch.randn(di, s, generator=gi, device=dev, dtype=torch.float64)
+        probs.append({"A": nx.Matrix.padded(Wi["A32"]), "b": Wi["b"], "gamma": Wi["gamma"], "rank": s, "Omega": Omi})
+    nx.nysadmm_solve_batch(probs[:2], rho, tol, admm_iters=2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    outs = nx.nysadmm_solve_batch(probs, rho, tol, admm_iters=K, hx_refresh=10)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for pr in probs:
+        nx.nysadmm_solve("lasso", pr["A"], pr["b"], pr["gamma"], rho, s, tol, pr["Omega"], admm_iters=K, hx_refresh=10)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    batch = {"instances": 32, "d_range": [int(dims.min()), int(dims.max())], "admm_iters": K,
+             "time_one_graph_s": round(t_batch, 3), "time_sequential_s": round(t_seq, 3),
+             "speedup": round(t_seq / t_batch, 2)}
+    print(json.dumps({"extra": "batched", "path": path, "uneven_batch": batch}), flush=True)
+
+
 def profile_apass(dt):
     """Small ncu case: the fused A-pass y = A^T (A p) + rho p on a 50000 x 10000 matrix
     (1 GB in BF16, larger than L2): 2 warm-up launches, then 6 timed launches."""
@@ -471,13 +541,18 @@ def main():
     ap.add_argument("--no-check", action="store_true", help="skip F* and the final gap check (profiling runs)")
     ap.add_argument("--profile-apass", choices=["bf16", "f32", "f64"], default=None,
                     help="only run the fused A-pass on a 50000 x 10000 matrix (ncu capture case)")
+    ap.add_argument("--extra", choices=["batched"], default=None,
+                    help="run a secondary workload and print its own JSON line")
+    ap.add_argument("--extra-iters", type=int, default=100)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.profile_apass:
+    if args.extra == "batched":
+        extra_batched(args)
+    elif args.profile_apass:
         profile_apass(args.profile_apass)
     elif args.impl == "reference":
         run_reference(args)

@@ -208,6 +208,27 @@ nys_status nysadmm_solve_path(const nys_matrix* A, const double* b, const double
                               int32_t rank, double tol, const double* Omega, const nys_opts* opts, double* X_out,
                               double* Z_out, nys_info* info, int32_t* pcg_iters);
 
+/* One independent lasso instance of a batch (device pointers). */
+typedef struct {
+  const nys_matrix* A;   /* problem matrix; all instances of a batch share its compute type */
+  const double* b;       /* length n */
+  double gamma;
+  int32_t rank;          /* Nystrom sketch size of this instance */
+  const double* Omega;   /* d x rank column-major Gaussian test matrix */
+  double* x_out;         /* length d FP64, or NULL */
+  double* z_out;         /* length d FP64, or NULL */
+} nys_lasso_instance;
+
+/* A batch of independent lasso problems of different sizes, each solved by
+ * NysADMM (Alg. NysADMM) with its own sketch and preconditioner.  The sketches are
+ * built first; then every instance's device-side ADMM/PCG loop (conditional WHILE
+ * nodes, as with opts->device_loop) becomes one branch of a single CUDA graph, so
+ * the whole batch runs as one graph launch and the GPU overlaps the instances.
+ * Shared: rho, the PCG tolerance tol and opts (admm_maxit, tolerance mode, stops,
+ * hx_refresh).  infos: host array of count entries, may be NULL. */
+nys_status nysadmm_solve_batch(int32_t count, const nys_lasso_instance* inst, double rho, double tol,
+                               const nys_opts* opts, nys_info* infos);
+
 /* Objective and optimality measures at x (FP64, one read of A):
  * out[0] = l(Ax; b) + gamma ||x||_1 (Eq. 2 or Eq. 9);
  * out[1] = relative KKT residual eta (Eq. 31; lasso) or ||A^T(sigma(Ax)-b01)||_inf (logistic);

@@ -608,6 +608,120 @@ nys_status lasso_path(const nys_matrix* A, const nys_matrix* Ain, const double* 
   return result;
 }
 
+// ---------------------------------------------------------------- batch of independent lasso instances
+// Every instance is sketched eagerly, then all device-side ADMM loops run as parallel
+// branches of ONE CUDA graph launch.
+template <typename C>
+nys_status lasso_batch(int count, const nys_lasso_instance* in, double rho, double tol, const nys_opts& o,
+                       nys_info* infos, cudaStream_t st) {
+  Pool pool(st);
+  std::vector<nys_precond_s> Ps(count);
+  struct Guard {
+    std::vector<nys_precond_s>* v;
+    ~Guard() {
+      for (auto& p : *v) {
+        if (p.U64) cudaFree(p.U64);
+        if (p.U32) cudaFree(p.U32);
+        if (p.lam_d) cudaFree(p.lam_d);
+      }
+    }
+  } guard{&Ps};
+  const int K = std::max(1, o.admm_maxit);
+  std::vector<GraphLoopArgs> gs(count);
+  std::vector<int*> pcg_its(count);
+  for (int i = 0; i < count; ++i) {
+    const nys_matrix* A = in[i].A;
+    const int64_t d = A->d;
+    const int rank = in[i].rank;
+    double* Om = pool.alloc<double>((size_t)d * rank);
+    double* Y = pool.alloc<double>((size_t)d * rank);
+    C* cbuf = pool.alloc<C>(rank);
+    double* x = pool.alloc<double>(d);
+    double* z = pool.alloc<double>(d);
+    double* u = pool.alloc<double>(d);
+    double* q = pool.alloc<double>(d);
+    C* xc = pool.alloc<C>(d);
+    C* rc = pool.alloc<C>(d);
+    C* hx = pool.alloc<C>(d);
+    void* ytmp = pool.alloc<unsigned char>(d * 8);
+    double* rp = pool.alloc<double>(K);
+    double* rd = pool.alloc<double>(K);
+    int* pit = pool.alloc<int>(K);
+    if (!pool.ok()) return NYS_ENOMEM;
+    NYS_CU(cudaMemcpyAsync(Om, in[i].Omega, (size_t)d * rank * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    NYS_TRY(cholqr2(Om, d, rank, st));
+    NYS_TRY(sketch_panel(A, nullptr, 0.0, Om, rank, Y, st));
+    const double shs = o.shift_scale > 0 ? o.shift_scale : std::sqrt((double)d);
+    NYS_TRY(precond_from_panels(Om, Y, d, rank, shs, mant_bits_of(A), &Ps[i], st));
+    PrecondView view;
+    NYS_TRY(precond_view<C>(&Ps[i], rho, cbuf, st, &view));
+    NYS_CU(cudaMemsetAsync(x, 0, d * sizeof(double), st));
+    NYS_CU(cudaMemsetAsync(z, 0, d * sizeof(double), st));
+    NYS_CU(cudaMemsetAsync(u, 0, d * sizeof(double), st));
+    NYS_CU(cudaMemsetAsync(xc, 0, d * sizeof(C), st));
+    NYS_TRY(aux_pass(A, MODE_CONST, nullptr, in[i].b, nullptr, nullptr, ytmp, nullptr, st));
+    NYS_TRY(to_f64(A, ytmp, q, d, st));
+    GraphLoopArgs& g = gs[i];
+    g.pb.A = A;
+    g.pb.D = nullptr;
+    g.pb.rho = rho;
+    apass_plan(A, &g.pb.plan);
+    g.P = view;
+    g.b = in[i].b;
+    g.x = x;
+    g.z = z;
+    g.u = u;
+    g.q = q;
+    g.xc = xc;
+    g.rc = rc;
+    g.hx = hx;
+    g.gamma = in[i].gamma;
+    g.rho = rho;
+    g.K = K;
+    g.eps_abs = o.eps_abs;
+    g.eps_rel = o.eps_rel;
+    g.tol = tol;
+    g.tol_mode = o.pcg_tol_mode;
+    g.maxit = o.pcg_maxit > 0 ? o.pcg_maxit : (int)std::min<int64_t>(d, 1000);
+    g.fixed_host = o.pcg_fixed_iters;
+    g.hx_refresh = std::max(0, o.hx_refresh);
+    g.rp = rp;
+    g.rd = rd;
+    g.pcg_it = pit;
+    pcg_its[i] = pit;
+  }
+  std::vector<GraphInstance> insts(count);
+  std::vector<GraphLoopResult> res(count);
+  NYS_TRY(admm_graph_run_many<C>(gs.data(), count, st, insts.data(), res.data()));
+  nys_status worst = NYS_OK;
+  for (int i = 0; i < count; ++i) {
+    const int64_t d = in[i].A->d;
+    const int done_k = std::min(res[i].admm_iters, K);
+    std::vector<int> its(std::max(1, done_k));
+    if (done_k > 0) NYS_CU(cudaMemcpyAsync(its.data(), pcg_its[i], done_k * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (in[i].x_out) NYS_CU(cudaMemcpyAsync(in[i].x_out, gs[i].x, d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (in[i].z_out) NYS_CU(cudaMemcpyAsync(in[i].z_out, gs[i].z, d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    nys_info inf;
+    std::memset(&inf, 0, sizeof(inf));
+    if (done_k > 0) {
+      NYS_CU(cudaMemcpyAsync(&inf.r_p, gs[i].rp + done_k - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+      NYS_CU(cudaMemcpyAsync(&inf.r_d, gs[i].rd + done_k - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    NYS_CU(cudaStreamSynchronize(st));
+    int total = 0;
+    for (int j = 0; j < done_k; ++j) total += its[j];
+    inf.admm_iters = done_k;
+    inf.pcg_iters_total = total;
+    inf.final_rank = in[i].rank;
+    inf.status = res[i].breakdown ? NYS_EBREAKDOWN : NYS_OK;
+    inf.nu = Ps[i].nu;
+    inf.emp_cond = (Ps[i].lam.back() + rho) / rho;
+    if (res[i].breakdown) worst = NYS_EBREAKDOWN;
+    if (infos) infos[i] = inf;
+  }
+  return worst;
+}
+
 // ---------------------------------------------------------------- logistic (Sec. 3.2) + AdaRandNysAppx (App. C)
 template <typename C>
 nys_status logistic_admm(const nys_matrix* A, const nys_matrix* Ain, const double* b, double gamma, double rho,
@@ -1002,6 +1116,26 @@ nys_status nysadmm_solve_path(const nys_matrix* A, const double* b, const double
   return Ain->dtype == NYS_F64
              ? lasso_path<double>(A, Ain, b, gammas, k, rho, rank, tol, Omega, o, X_out, Z_out, info, pcg_iters, st)
              : lasso_path<float>(A, Ain, b, gammas, k, rho, rank, tol, Omega, o, X_out, Z_out, info, pcg_iters, st);
+}
+
+nys_status nysadmm_solve_batch(int32_t count, const nys_lasso_instance* inst, double rho, double tol,
+                               const nys_opts* opts, nys_info* infos) {
+  if (count < 1 || count > 4096 || !inst || !(rho > 0) || !is_fin(rho) || !(tol >= 0) || !is_fin(tol))
+    return NYS_EINVAL;
+  const bool f64 = inst[0].A && inst[0].A->dtype == NYS_F64;
+  for (int i = 0; i < count; ++i) {
+    NYS_TRY(check_matrix(inst[i].A));
+    if ((inst[i].A->dtype == NYS_F64) != f64) return NYS_EINVAL;  // one compute type per batch
+    if (!inst[i].b || !inst[i].Omega || !(inst[i].gamma >= 0) || !is_fin(inst[i].gamma)) return NYS_EINVAL;
+    if (inst[i].rank < 1 || inst[i].rank > inst[i].A->d || inst[i].rank > kMaxRank) return NYS_EINVAL;
+  }
+  nys_opts o;
+  if (opts) o = *opts;
+  else nys_opts_default(&o);
+  if (o.admm_maxit < 1) return NYS_EINVAL;
+  cudaStream_t st = stream_of(&o);
+  return f64 ? lasso_batch<double>(count, inst, rho, tol, o, infos, st)
+             : lasso_batch<float>(count, inst, rho, tol, o, infos, st);
 }
 
 nys_status nys_objective(int32_t loss, const nys_matrix* A, const double* b, double gamma, const double* x,

@@ -523,8 +523,6 @@ namespace nys {
 // ADMM iterations and an inner one runs PCG iterations; the scalar kernels set the
 // loop conditions on the device, so a whole solve needs no host synchronisation.
 // The kernels and their order are those of the host-driven loop.
-namespace {
-
 struct AdmmCtl {
   int k;            // ADMM iteration counter
   int stop;         // residual stop reached
@@ -533,6 +531,9 @@ struct AdmmCtl {
   long long nodes;  // kernel launches executed (instrumentation)
   double eps_next;  // sqrt(r_p r_d) of the last iteration
 };
+
+namespace {
+
 
 __global__ void admm_begin_kernel(AdmmCtl* ctl, PcgState* st, double tol, int tol_mode, int maxit,
                                   const int* __restrict__ fixed_dev, int hx_refresh, int refine) {
@@ -646,8 +647,12 @@ __global__ void admm_scalar_g_kernel(int nb, const double* part5, double rho, in
 
 }  // namespace
 
+// Adds one instance's device-side loop (an outer conditional WHILE over ADMM iterations
+// containing the PCG WHILE) to `graph` as an independent branch.  Buffers come from
+// `pool`, which must outlive the graph's execution; state is initialised on `stream`.
 template <typename C>
-nys_status admm_graph_run(const GraphLoopArgs& g, cudaStream_t stream, GraphLoopResult* res) {
+nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_t stream, Pool& pool,
+                          GraphInstance* inst) {
   const int64_t d = g.pb.A->d;
   const int s = g.P.s;
   const C* U = reinterpret_cast<const C*>(g.P.U);
@@ -658,7 +663,6 @@ nys_status admm_graph_run(const GraphLoopArgs& g, cudaStream_t stream, GraphLoop
   const int nb5 = nbr;
   const int nbz = admm_blocks(d);
   const int K = g.K;
-  Pool pool(stream);
   C* w = pool.alloc<C>(d);
   C* y = pool.alloc<C>(d);
   C* p = pool.alloc<C>(d);
@@ -696,18 +700,6 @@ nys_status admm_graph_run(const GraphLoopArgs& g, cudaStream_t stream, GraphLoop
   // a private stream to capture on (a legacy default stream cannot be captured)
   static thread_local cudaStream_t cap = nullptr;
   if (!cap) G_OK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  struct Cleanup {
-    cudaGraph_t* g;
-    cudaGraphExec_t* x;
-    ~Cleanup() {
-      if (*x) cudaGraphExecDestroy(*x);
-      if (*g) cudaGraphDestroy(*g);
-    }
-  } cleanup{&graph, &exec};
-  G_OK(cudaGraphCreate(&graph, 0));
   cudaGraphConditionalHandle h_admm, h_pcg;
   G_OK(cudaGraphConditionalHandleCreate(&h_admm, graph, 1u, cudaGraphCondAssignDefault));
   cudaGraphNodeParams cp = {};
@@ -815,22 +807,61 @@ nys_status admm_graph_run(const GraphLoopArgs& g, cudaStream_t stream, GraphLoop
   count_launch_suspend(false);
   G_OK(cudaGetLastError());
 
-  G_OK(cudaGraphInstantiate(&exec, graph, 0));
-  G_OK(cudaGraphLaunch(exec, stream));
-  AdmmCtl ctl_h;
-  int dstat_h = 0;
-  G_OK(cudaMemcpyAsync(&ctl_h, ctl, sizeof(AdmmCtl), cudaMemcpyDeviceToHost, stream));
-  G_OK(cudaMemcpyAsync(&dstat_h, dstat, sizeof(int), cudaMemcpyDeviceToHost, stream));
-  G_OK(cudaStreamSynchronize(stream));
-#undef G_OK
-  count_launch_add(ctl_h.nodes);
-  res->admm_iters = ctl_h.k;
-  res->breakdown = ctl_h.stop == 2;
-  if (dstat_h) return (nys_status)dstat_h;
+  inst->ctl = ctl;
+  inst->dstat = dstat;
   return NYS_OK;
+#undef G_OK
+}
+
+// One instance: build, instantiate and launch its graph, then read its control block.
+template <typename C>
+nys_status admm_graph_run(const GraphLoopArgs& g, cudaStream_t stream, GraphLoopResult* res) {
+  GraphInstance inst;
+  return admm_graph_run_many<C>(&g, 1, stream, &inst, res);
+}
+
+template <typename C>
+nys_status admm_graph_run_many(const GraphLoopArgs* gs, int count, cudaStream_t stream, GraphInstance* insts,
+                               GraphLoopResult* res) {
+  Pool pool(stream);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  struct Cleanup {
+    cudaGraph_t* g;
+    cudaGraphExec_t* x;
+    ~Cleanup() {
+      if (*x) cudaGraphExecDestroy(*x);
+      if (*g) cudaGraphDestroy(*g);
+    }
+  } cleanup{&graph, &exec};
+  if (cudaGraphCreate(&graph, 0) != cudaSuccess) return NYS_ECUDA;
+  for (int i = 0; i < count; ++i) {
+    const nys_status s = admm_graph_add<C>(graph, gs[i], stream, pool, &insts[i]);
+    if (s != NYS_OK) return s;
+  }
+  if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) return NYS_ECUDA;
+  if (cudaGraphLaunch(exec, stream) != cudaSuccess) return NYS_ECUDA;
+  nys_status worst = NYS_OK;
+  for (int i = 0; i < count; ++i) {
+    AdmmCtl ctl_h;
+    int dstat_h = 0;
+    if (cudaMemcpyAsync(&ctl_h, insts[i].ctl, sizeof(AdmmCtl), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaMemcpyAsync(&dstat_h, insts[i].dstat, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+      return NYS_ECUDA;
+    count_launch_add(ctl_h.nodes);
+    res[i].admm_iters = ctl_h.k;
+    res[i].breakdown = ctl_h.stop == 2;
+    if (dstat_h) worst = (nys_status)dstat_h;
+  }
+  return worst;
 }
 
 template nys_status admm_graph_run<double>(const GraphLoopArgs&, cudaStream_t, GraphLoopResult*);
 template nys_status admm_graph_run<float>(const GraphLoopArgs&, cudaStream_t, GraphLoopResult*);
+template nys_status admm_graph_run_many<double>(const GraphLoopArgs*, int, cudaStream_t, GraphInstance*,
+                                                GraphLoopResult*);
+template nys_status admm_graph_run_many<float>(const GraphLoopArgs*, int, cudaStream_t, GraphInstance*,
+                                               GraphLoopResult*);
 
 }  // namespace nys

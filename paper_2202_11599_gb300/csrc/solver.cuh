@@ -131,7 +131,16 @@ struct GraphLoopResult {
   int admm_iters = 0;
   bool breakdown = false;
 };
+struct AdmmCtl;
+struct GraphInstance {
+  AdmmCtl* ctl = nullptr;
+  int* dstat = nullptr;
+};
 template <typename C>
 nys_status admm_graph_run(const GraphLoopArgs& g, cudaStream_t stream, GraphLoopResult* res);
+// Several independent instances as parallel branches of ONE graph launch.
+template <typename C>
+nys_status admm_graph_run_many(const GraphLoopArgs* gs, int count, cudaStream_t stream, GraphInstance* insts,
+                               GraphLoopResult* res);
 
 }  // namespace nys

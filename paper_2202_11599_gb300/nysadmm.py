@@ -50,6 +50,11 @@ class NysStatsC(ctypes.Structure):
                 ("dev_bytes", c_double * 3)]
 
 
+class NysInstanceC(ctypes.Structure):
+    _fields_ = [("A", POINTER(NysMatrixC)), ("b", c_void_p), ("gamma", c_double), ("rank", c_int32),
+                ("Omega", c_void_p), ("x_out", c_void_p), ("z_out", c_void_p)]
+
+
 class NysError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -84,6 +89,8 @@ def lib() -> ctypes.CDLL:
                                 c_void_p, P(NysOptsC), c_void_p, c_void_p, P(NysInfoC)]
     L.nysadmm_solve_path.argtypes = [P(NysMatrixC), c_void_p, P(c_double), c_int32, c_double, c_int32, c_double,
                                      c_void_p, P(NysOptsC), c_void_p, c_void_p, P(NysInfoC), P(c_int32)]
+    L.nysadmm_solve_batch.argtypes = [c_int32, POINTER(NysInstanceC), c_double, c_double, P(NysOptsC),
+                                      POINTER(NysInfoC)]
     L.nys_objective.argtypes = [c_int32, P(NysMatrixC), c_void_p, c_double, c_void_p, P(c_double), c_void_p]
     L.nys_stats_enable.argtypes = [c_int32]
     L.nys_stats_enable.restype = None
@@ -91,7 +98,8 @@ def lib() -> ctypes.CDLL:
     L.nys_precond_destroy.argtypes = [c_void_p]
     L.nys_precond_destroy.restype = None
     for name in ("nys_hmatvec", "nys_hmatvec_noalloc", "nys_sketch", "nys_precond_get", "nys_precond_apply", "pcg_solve",
-                 "nysadmm_solve", "nysadmm_solve_path", "nys_objective", "nys_stats_read"):
+                 "nysadmm_solve", "nysadmm_solve_path", "nysadmm_solve_batch", "nys_objective",
+                 "nys_stats_read"):
         getattr(L, name).restype = c_int32
     _lib = L
     return L
@@ -324,6 +332,35 @@ def nysadmm_solve_path(A: Matrix, b: torch.Tensor, gammas, rho: float, rank: int
     inf = {f: getattr(info, f) for f, _ in NysInfoC._fields_}
     inf["status"] = st
     return {"X": X.T, "Z": Z.T, "pcg_iters": list(its), "info": inf}
+
+
+def nysadmm_solve_batch(problems, rho: float, tol: float, admm_iters: int = 200, tol_mode: str = "rel",
+                        pcg_maxit: int | None = None, hx_refresh: int = 0, eps_abs: float = 0.0,
+                        eps_rel: float = 0.0, stream=None, allow_noconv: bool = True) -> list:
+    """Independent lasso instances, one graph launch.  problems: list of dicts with keys
+    A (Matrix), b, gamma, rank, Omega (d x rank).  Returns a list of dicts (x, z, info)."""
+    n = len(problems)
+    arr = (NysInstanceC * n)()
+    keep = []
+    outs = []
+    for i, pr in enumerate(problems):
+        A = pr["A"]
+        Om = pr["Omega"].to(torch.float64).T.contiguous()
+        b = pr["b"].to(torch.float64).contiguous()
+        x = torch.empty(A.d, dtype=torch.float64, device="cuda")
+        z = torch.empty(A.d, dtype=torch.float64, device="cuda")
+        keep += [Om, b, A]
+        arr[i] = NysInstanceC(ctypes.pointer(A.c), c_void_p(b.data_ptr()), float(pr["gamma"]), int(pr["rank"]),
+                              c_void_p(Om.data_ptr()), c_void_p(x.data_ptr()), c_void_p(z.data_ptr()))
+        outs.append({"x": x, "z": z})
+    o = _opts(stream, pcg_tol_mode=TOL_MODES[tol_mode], pcg_maxit=pcg_maxit or 0, admm_maxit=admm_iters,
+              eps_abs=eps_abs, eps_rel=eps_rel, hx_refresh=int(hx_refresh))
+    infos = (NysInfoC * n)()
+    st = lib().nysadmm_solve_batch(n, arr, float(rho), float(tol), ctypes.byref(o), infos)
+    _check(st, "nysadmm_solve_batch", ok=(NYS_OK, NYS_ENOCONV) if allow_noconv else (NYS_OK,))
+    for i in range(n):
+        outs[i]["info"] = {f: getattr(infos[i], f) for f, _ in NysInfoC._fields_}
+    return outs
 
 
 def objective(loss: str, A: Matrix, b: torch.Tensor, gamma: float, x: torch.Tensor, stream=None):

@@ -393,3 +393,22 @@ def test_regularisation_path_low_precision(dtype):
         zs = single["z"].cpu().numpy()
         # same algorithm and stored matrix; FP32 reductions in a different order
         assert np.linalg.norm(Z[:, c] - zs) <= 1e-4 * max(1.0, np.linalg.norm(zs))
+
+
+def test_batch_of_uneven_instances_one_graph():
+    """Independent lasso instances of different sizes in one graph launch: each equals
+    its own single solve bitwise (same kernels, same order) and the oracle."""
+    probs, refs = [], []
+    for i, d in enumerate([60, 257, 130, 401]):
+        p = gen.lasso_problem(6 * d, d, nnz=max(2, d // 30), seed=50 + i)
+        Om = gen.gaussian_test_matrix(d, 12, 50 + i)
+        probs.append({"A": nx.Matrix.padded(_dev(p.A)), "b": _dev(p.b), "gamma": p.gamma, "rank": 12,
+                      "Omega": _dev(Om)})
+        refs.append((p, Om))
+    outs = nx.nysadmm_solve_batch(probs, 10.0, 1e-11, admm_iters=120)
+    for (p, Om), pr, out in zip(refs, probs, outs):
+        single = nx.nysadmm_solve("lasso", pr["A"], pr["b"], p.gamma, 10.0, 12, 1e-11, pr["Omega"], admm_iters=120)
+        assert torch.equal(out["z"], single["z"]) and torch.equal(out["x"], single["x"])
+        assert out["info"]["pcg_iters_total"] == single["info"]["pcg_iters_total"]
+        ref = o.lasso_nysadmm(p.A, p.b, p.gamma, 10.0, Om, 120, pcg_tol=1e-11)
+        assert np.linalg.norm(out["z"].cpu().numpy() - ref["z"]) <= 1e-9 * max(1.0, np.linalg.norm(ref["z"]))
