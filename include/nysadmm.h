@@ -105,6 +105,12 @@ typedef struct {
                                   in Alg. Nystrom PCG); M >= 1 = carry (A^T D A + rho I) x
                                   along the PCG updates and recompute it every M ADMM
                                   iterations (device_loop only; same value in exact arithmetic) */
+  void* warm_model;            /* nys_mlp or NULL (lasso, device_loop): learned warm start,
+                                  PCG starts at x_prev + U c with c = model(features) (see
+                                  nys_mlp_create); the model needs n_in = rank + 3, n_out = rank */
+  float* warm_record;          /* device, admm_maxit x (2 rank + 3) FP32, or NULL (lasso,
+                                  device_loop): row k = [features (rank + 3), target (rank)] of
+                                  ADMM iteration k, the training pairs for the model */
 } nys_opts;
 
 typedef struct {
@@ -262,6 +268,35 @@ typedef struct {
 
 void nys_stats_enable(int32_t on);
 nys_status nys_stats_read(nys_stats* out);
+
+/* Learned warm start for the x-subproblem (no counterpart in the paper; an
+ * AI-systems addition).  A multilayer perceptron n_in -> n_hid -> n_hid -> n_out
+ * with erf-GELU hidden units; BF16 weights in the matrix products with FP32
+ * accumulation, FP32 master weights, Adam (beta 0.9 / 0.999, eps 1e-8).
+ * In NysADMM (opts->warm_model) its input at ADMM iteration k is
+ *   f = [U^T r / ||r||, log10(rho), k / 100, ln ||r||]   (rank + 3 values)
+ * for the x-subproblem right-hand side r and the Nystrom basis U.  The model
+ * predicts the solution's coordinates in range(U) scaled by rho / ||r||, and PCG
+ * starts at x_prev + U c with c = model(f) ||r|| / rho - U^T x_prev (the component
+ * of x_prev in range(U) replaced by the prediction).  The training target recorded
+ * in opts->warm_record is U^T x_new * rho / ||r||.  PCG still runs to the same
+ * tolerance.
+ * Parameters (flat FP32): [W1 (n_hid x n_in), b1, W2 (n_hid x n_hid), b2,
+ * W3 (n_out x n_hid), b3], weights row-major (output x input); init_params (host
+ * or device) supplies the initial values, drawn by the caller.  X, T, Y are device
+ * row-major batches (B x n_in / B x n_out, FP32).  Loss = mean (Y - T)^2. */
+typedef struct nys_mlp_s* nys_mlp;
+nys_status nys_mlp_create(int32_t n_in, int32_t n_hid, int32_t n_out, const float* init_params, nys_mlp* out);
+nys_status nys_mlp_forward(nys_mlp M, const float* X, int32_t B, float* Y, void* stream);
+/* loss (host, may be NULL) and gradient (device, flat, may be NULL) at the current parameters */
+nys_status nys_mlp_grad(nys_mlp M, const float* X, const float* T, int32_t B, float* grad_out, float* loss,
+                        void* stream);
+/* one Adam step on the batch; *loss (host, may be NULL) is the loss before the step */
+nys_status nys_mlp_train_step(nys_mlp M, const float* X, const float* T, int32_t B, float lr, float* loss,
+                              void* stream);
+/* copies the FP32 master parameters to out (host or device; NULL to query *n_params) */
+nys_status nys_mlp_get_params(nys_mlp M, float* out, int64_t* n_params, void* stream);
+void nys_mlp_destroy(nys_mlp M);
 
 void nys_precond_destroy(nys_precond P);
 const char* nys_strerror(int32_t status);

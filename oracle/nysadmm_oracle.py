@@ -407,3 +407,74 @@ def logistic_nysadmm(A, b_pm, gamma, rho, Omega_pool, admm_iters, s0, s_max, ada
         trace["r_p"].append(float(np.linalg.norm(x - z)))
         trace["r_d"].append(float(rho * np.linalg.norm(z_old - z)))
     return {"x": x, "z": z, "u": u, "rank": rank, "trace": trace}
+
+
+# ---------------------------------------------------------------------------
+# Learned warm start: small MLP (two GELU hidden layers), FP64 reference
+# ---------------------------------------------------------------------------
+# Parameters are one flat vector [W1 (h x i), b1 (h), W2 (h x h), b2 (h), W3 (o x h), b3 (o)],
+# weights row-major (output x input).  GELU(z) = z * Phi(z) (erf form).  Loss = mean over
+# batch and outputs of (Y - T)^2.  Adam with bias correction.
+
+def mlp_unpack(theta, n_in, n_hid, n_out):
+    sizes = [(n_hid, n_in), (n_hid,), (n_hid, n_hid), (n_hid,), (n_out, n_hid), (n_out,)]
+    out, off = [], 0
+    for sh in sizes:
+        cnt = int(np.prod(sh))
+        out.append(np.asarray(theta[off:off + cnt], dtype=np.float64).reshape(sh))
+        off += cnt
+    return out
+
+
+def mlp_param_count(n_in, n_hid, n_out):
+    return n_hid * n_in + n_hid + n_hid * n_hid + n_hid + n_out * n_hid + n_out
+
+
+def gelu(z):
+    from scipy.special import erf
+    return 0.5 * z * (1.0 + erf(z / math.sqrt(2.0)))
+
+
+def gelu_grad(z):
+    from scipy.special import erf
+    return 0.5 * (1.0 + erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+
+
+def mlp_forward(theta, X, n_in, n_hid, n_out):
+    """Y = W3 GELU(W2 GELU(W1 x + b1) + b2) + b3 for each row x of X (B x n_in)."""
+    W1, b1, W2, b2, W3, b3 = mlp_unpack(theta, n_in, n_hid, n_out)
+    Z1 = X @ W1.T + b1
+    H1 = gelu(Z1)
+    Z2 = H1 @ W2.T + b2
+    H2 = gelu(Z2)
+    Y = H2 @ W3.T + b3
+    return Y, (Z1, H1, Z2, H2)
+
+
+def mlp_loss_grad(theta, X, T, n_in, n_hid, n_out):
+    """Mean-squared loss and its gradient (backpropagation written out)."""
+    W1, b1, W2, b2, W3, b3 = mlp_unpack(theta, n_in, n_hid, n_out)
+    Y, (Z1, H1, Z2, H2) = mlp_forward(theta, X, n_in, n_hid, n_out)
+    B = X.shape[0]
+    R = Y - T
+    loss = float(np.sum(R * R) / (B * n_out))
+    dY = 2.0 * R / (B * n_out)
+    dW3 = dY.T @ H2
+    db3 = dY.sum(axis=0)
+    dZ2 = (dY @ W3) * gelu_grad(Z2)
+    dW2 = dZ2.T @ H1
+    db2 = dZ2.sum(axis=0)
+    dZ1 = (dZ2 @ W2) * gelu_grad(Z1)
+    dW1 = dZ1.T @ X
+    db1 = dZ1.sum(axis=0)
+    g = np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dW3.ravel(), db3])
+    return loss, g
+
+
+def adam_step(theta, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba) with bias correction; returns (theta, m, v)."""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** t)
+    vh = v / (1 - b2 ** t)
+    return theta - lr * mh / (np.sqrt(vh) + eps), m, v

@@ -406,6 +406,8 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
     g.rp = rp;
     g.rd = rd;
     g.pcg_it = pcg_it;
+    g.warm = reinterpret_cast<const nys_mlp_s*>(o.warm_model);
+    g.warm_record = o.warm_record;
     GraphLoopResult gr;
     nys_status gs = admm_graph_run<C>(g, st, &gr);
     if (gs != NYS_OK) return gs;
@@ -944,6 +946,8 @@ void nys_opts_default(nys_opts* o) {
   o->stream = nullptr;
   o->device_loop = 1;
   o->hx_refresh = 0;
+  o->warm_model = nullptr;
+  o->warm_record = nullptr;
 }
 
 const char* nys_strerror(int32_t s) {

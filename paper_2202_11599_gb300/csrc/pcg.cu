@@ -647,6 +647,71 @@ __global__ void admm_scalar_g_kernel(int nb, const double* part5, double rho, in
 
 }  // namespace
 
+namespace {
+// Learned warm start: features f = [U^T r / ||r||, log10 rho, k / 100, ln ||r||].
+// Block i < s: (U^T r)_i; block s: ||r||^2 (double accumulation, fixed order).
+template <typename C>
+__global__ void __launch_bounds__(kVecThreads) ws_proj_kernel(int64_t d, int s, const C* __restrict__ U,
+                                                              const C* __restrict__ v, const C* __restrict__ vsub,
+                                                              double* out) {
+  __shared__ double sh[kVecThreads / 32];
+  const int i = blockIdx.x;
+  double acc = 0.0;
+  for (int64_t j = threadIdx.x; j < d; j += kVecThreads) {
+    const double vj = vsub ? (double)v[j] - (double)vsub[j] : (double)v[j];
+    acc += (i < s ? (double)U[(int64_t)i * d + j] : vj) * vj;
+  }
+  acc = block_sum<kVecThreads>(acc, sh);
+  if (threadIdx.x == 0) out[i] = acc;
+}
+
+__global__ void ws_features_kernel(int s, const double* proj, double rho, const AdmmCtl* ctl, float* feat,
+                                   double* rnorm) {
+  const double rn = sqrt(proj[s]);
+  const double inv = rn > 0.0 ? 1.0 / rn : 0.0;
+  for (int i = threadIdx.x; i < s; i += blockDim.x) feat[i] = (float)(proj[i] * inv);
+  if (threadIdx.x == 0) {
+    feat[s] = (float)log10(rho);
+    feat[s + 1] = (float)(ctl->k / 100.0);
+    feat[s + 2] = (float)(rn > 0.0 ? log(rn) : 0.0);
+    *rnorm = rn;
+  }
+}
+
+// The model predicts the subspace coordinates of the solution, U^T x ~ m(f) ||r|| / rho;
+// x0 = x_prev + U c with c = m(f) ||r|| / rho - U^T x_prev (uxp).  The warm start
+// changed, so (H + rho I) x0 is recomputed.
+template <typename C>
+__global__ void ws_apply_kernel(int64_t d, int s, const C* __restrict__ U, const float* __restrict__ c,
+                                const double* __restrict__ uxp, const double* rnorm, double rho, C* __restrict__ xc,
+                                C* __restrict__ xprev, AdmmCtl* ctl) {
+  const double scale = *rnorm / rho;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < s; ++i) acc += (double)U[(int64_t)i * d + j] * ((double)c[i] * scale - uxp[i]);
+    const C x0 = xc[j];
+    if (xprev) xprev[j] = x0;
+    xc[j] = (C)((double)x0 + acc);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->hx_skip = 0;
+}
+
+template <typename C>
+__global__ void ws_copy_kernel(int64_t d, const C* __restrict__ x, C* __restrict__ y) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x)
+    y[j] = x[j];
+}
+
+// record row k = [f (s + 3), U^T x_new * rho / ||r|| (s)]
+__global__ void ws_record_kernel(int s, const float* feat, const double* proj, const double* rnorm, double rho,
+                                 const AdmmCtl* ctl, float* rec) {
+  float* row = rec + (int64_t)ctl->k * (2 * s + 3);
+  const double sc = *rnorm > 0.0 ? rho / *rnorm : 0.0;
+  for (int i = threadIdx.x; i < s + 3; i += blockDim.x) row[i] = feat[i];
+  for (int i = threadIdx.x; i < s; i += blockDim.x) row[s + 3 + i] = (float)(proj[i] * sc);
+}
+}  // namespace
+
 // Adds one instance's device-side loop (an outer conditional WHILE over ADMM iterations
 // containing the PCG WHILE) to `graph` as an independent branch.  Buffers come from
 // `pool`, which must outlive the graph's execution; state is initialised on `stream`.
@@ -754,6 +819,37 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   }
   admm_rhs_g_kernel<C><<<nbz, kVecThreads, 0, cap>>>(d, g.q, g.z, g.u, g.rho, g.x, g.yres, refine, rc, xc, hx);
   ++seg_nodes;
+  const bool use_ws = (g.warm || g.warm_record) && s > 0;
+  float* feat = nullptr;
+  double* proj = nullptr;
+  double* rnorm = nullptr;
+  C* xprev = nullptr;
+  if (use_ws) {
+    feat = pool.alloc<float>(s + 3);
+    proj = pool.alloc<double>(s + 1);
+    rnorm = pool.alloc<double>(1);
+    xprev = pool.alloc<C>(d);
+    float* mlp_buf = pool.alloc<float>(4 * 1024 + s);
+    if (!pool.ok()) return NYS_ENOMEM;
+    ws_proj_kernel<C><<<s + 1, kVecThreads, 0, cap>>>(d, s, U, rc, (const C*)nullptr, proj);
+    ws_features_kernel<<<1, 128, 0, cap>>>(s, proj, g.rho, ctl, feat, rnorm);
+    seg_nodes += 2;
+    if (g.warm) {
+      int ni, nh, no;
+      mlp_dims(g.warm, &ni, &nh, &no);
+      if (ni != s + 3 || no != s || nh > 1024) return NYS_EINVAL;
+      float* cout = mlp_buf + 4 * 1024;
+      double* uxp = pool.alloc<double>(s);
+      if (!pool.ok()) return NYS_ENOMEM;
+      ws_proj_kernel<C><<<s, kVecThreads, 0, cap>>>(d, s, U, xc, (const C*)nullptr, uxp);
+      G_OK(mlp_forward_dev(g.warm, feat, 1, mlp_buf, mlp_buf + 1024, mlp_buf + 2048, mlp_buf + 3072, cout, cap));
+      ws_apply_kernel<C><<<nbz, kVecThreads, 0, cap>>>(d, s, U, cout, uxp, rnorm, g.rho, xc, xprev, ctl);
+      seg_nodes += 5;
+    } else {
+      ws_copy_kernel<C><<<nbz, kVecThreads, 0, cap>>>(d, xc, xprev);
+      ++seg_nodes;
+    }
+  }
   aa.p = xc;
   aa.skip = &ctl->hx_skip;
   G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, true));
@@ -798,6 +894,11 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
 
   // ---- segment 2: prox / dual step, residuals, loop condition
   G_OK(cudaStreamBeginCaptureToGraph(cap, body, &n_pcg, nullptr, 1, cudaStreamCaptureModeRelaxed));
+  if (use_ws && g.warm_record) {
+    ws_proj_kernel<C><<<s, kVecThreads, 0, cap>>>(d, s, U, xc, (const C*)nullptr, proj);
+    ws_record_kernel<<<1, 128, 0, cap>>>(s, feat, proj, rnorm, g.rho, ctl, g.warm_record);
+    seg_nodes += 2;
+  }
   admm_zu_g_kernel<C><<<nbz, kVecThreads, 0, cap>>>(d, xc, refine, g.x, g.z, g.u, g.gamma / g.rho, g.ztrace, ctl,
                                                     part5);
   seg_nodes += 2;

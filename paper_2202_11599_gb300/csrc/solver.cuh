@@ -126,12 +126,18 @@ struct GraphLoopArgs {
   double* ztrace = nullptr;
   double *rp = nullptr, *rd = nullptr;
   int* pcg_it = nullptr;     // device, K
+  const nys_mlp_s* warm = nullptr;   // learned warm start model, or null
+  float* warm_record = nullptr;      // K x (2 s + 3) feature/target rows, or null
 };
 struct GraphLoopResult {
   int admm_iters = 0;
   bool breakdown = false;
 };
 struct AdmmCtl;
+// MLP forward on device buffers (no allocation or synchronisation: capturable)
+cudaError_t mlp_forward_dev(const nys_mlp_s* M, const float* X, int B, float* z1, float* h1, float* z2, float* h2,
+                            float* Y, cudaStream_t st);
+int mlp_dims(const nys_mlp_s* M, int* ni, int* nh, int* no);
 struct GraphInstance {
   AdmmCtl* ctl = nullptr;
   int* dstat = nullptr;

@@ -35,7 +35,8 @@ class NysOptsC(ctypes.Structure):
                 ("eps_abs", c_double), ("eps_rel", c_double), ("A_inner", POINTER(NysMatrixC)),
                 ("refine", c_int32), ("z_trace", c_void_p), ("rank_max", c_int32),
                 ("ada_tol", c_double), ("resketch_every", c_int32), ("stream", c_void_p),
-                ("device_loop", c_int32), ("hx_refresh", c_int32)]
+                ("device_loop", c_int32), ("hx_refresh", c_int32), ("warm_model", c_void_p),
+                ("warm_record", c_void_p)]
 
 
 class NysInfoC(ctypes.Structure):
@@ -95,11 +96,20 @@ def lib() -> ctypes.CDLL:
     L.nys_stats_enable.argtypes = [c_int32]
     L.nys_stats_enable.restype = None
     L.nys_stats_read.argtypes = [POINTER(NysStatsC)]
+    L.nys_mlp_create.argtypes = [c_int32, c_int32, c_int32, c_void_p, P(c_void_p)]
+    L.nys_mlp_forward.argtypes = [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]
+    L.nys_mlp_grad.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, P(ctypes.c_float), c_void_p]
+    L.nys_mlp_train_step.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, ctypes.c_float, P(ctypes.c_float),
+                                     c_void_p]
+    L.nys_mlp_get_params.argtypes = [c_void_p, c_void_p, P(c_int64), c_void_p]
+    L.nys_mlp_destroy.argtypes = [c_void_p]
+    L.nys_mlp_destroy.restype = None
     L.nys_precond_destroy.argtypes = [c_void_p]
     L.nys_precond_destroy.restype = None
     for name in ("nys_hmatvec", "nys_hmatvec_noalloc", "nys_sketch", "nys_precond_get", "nys_precond_apply", "pcg_solve",
                  "nysadmm_solve", "nysadmm_solve_path", "nysadmm_solve_batch", "nys_objective",
-                 "nys_stats_read"):
+                 "nys_stats_read", "nys_mlp_create", "nys_mlp_forward", "nys_mlp_grad", "nys_mlp_train_step",
+                 "nys_mlp_get_params"):
         getattr(L, name).restype = c_int32
     _lib = L
     return L
@@ -272,7 +282,8 @@ def nysadmm_solve(loss: str, A: Matrix, b: torch.Tensor, gamma: float, rho: floa
                   pcg_maxit: int | None = None, eps_abs: float = 0.0, eps_rel: float = 0.0,
                   rank_max: int | None = None, ada_tol: float | None = None, resketch_every: int = 1,
                   shift_scale: float | None = None, stream=None, allow_noconv: bool = True,
-                  device_loop: bool = True, hx_refresh: int = 0) -> dict:
+                  device_loop: bool = True, hx_refresh: int = 0, warm_model=None,
+                  warm_record: bool = False) -> dict:
     """NysADMM (Alg. NysADMM / AdaNysADMM) through the C ABI.  Returns a dict with
     x, z (FP64 device tensors), info (dict) and, when requested, the z trace."""
     d = A.d
@@ -280,6 +291,7 @@ def nysadmm_solve(loss: str, A: Matrix, b: torch.Tensor, gamma: float, rho: floa
     x = torch.empty(d, dtype=torch.float64, device="cuda")
     z = torch.empty(d, dtype=torch.float64, device="cuda")
     zt = torch.empty(admm_iters, d, dtype=torch.float64, device="cuda") if z_trace else None
+    rec = torch.zeros(admm_iters, 2 * int(rank) + 3, dtype=torch.float32, device="cuda") if warm_record else None
     fixed = None
     if pcg_fixed is not None:
         seq = [int(pcg_fixed)] * admm_iters if isinstance(pcg_fixed, int) else [int(v) for v in pcg_fixed]
@@ -290,7 +302,9 @@ def nysadmm_solve(loss: str, A: Matrix, b: torch.Tensor, gamma: float, rho: floa
               A_inner=ctypes.pointer(A_inner.c) if A_inner is not None else None,
               refine=int(bool(refine)), z_trace=c_void_p(zt.data_ptr()) if zt is not None else None,
               rank_max=rank_max or 0, ada_tol=ada_tol, resketch_every=resketch_every,
-              device_loop=int(bool(device_loop)), hx_refresh=int(hx_refresh))
+              device_loop=int(bool(device_loop)), hx_refresh=int(hx_refresh),
+              warm_model=warm_model.h if warm_model is not None else None,
+              warm_record=c_void_p(rec.data_ptr()) if rec is not None else None)
     info = NysInfoC()
     st = lib().nysadmm_solve(_LOSSES[loss], ctypes.byref(A.c), _ptr(b.to(torch.float64).contiguous()),
                              float(gamma), float(rho), int(rank), float(tol), _ptr(Om), ctypes.byref(o),
@@ -301,6 +315,8 @@ def nysadmm_solve(loss: str, A: Matrix, b: torch.Tensor, gamma: float, rho: floa
     out = {"x": x, "z": z, "info": inf}
     if zt is not None:
         out["z_trace"] = zt[: inf["admm_iters"]]
+    if rec is not None:
+        out["warm_record"] = rec[: inf["admm_iters"]]
     return out
 
 
@@ -387,3 +403,53 @@ def stats_read() -> dict:
                                  "bytes": s.apass_bytes[k]} for k in range(3)},
             "apass_dev": {names[k]: {"launches": s.dev_launches[k], "ms": s.dev_ms[k],
                                      "bytes": s.dev_bytes[k]} for k in range(3)}}
+
+
+class MLP:
+    """Learned warm-start model (nys_mlp): n_in -> n_hid -> n_hid -> n_out, erf-GELU."""
+
+    def __init__(self, n_in: int, n_hid: int, n_out: int, init_params):
+        self.n_in, self.n_hid, self.n_out = n_in, n_hid, n_out
+        p = torch.as_tensor(init_params, dtype=torch.float32).contiguous().cpu()
+        h = c_void_p()
+        _check(lib().nys_mlp_create(n_in, n_hid, n_out, c_void_p(p.data_ptr()), ctypes.byref(h)), "nys_mlp_create")
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None and self.h.value:
+            _lib.nys_mlp_destroy(self.h)
+            self.h = c_void_p(0)
+
+    def forward(self, X: torch.Tensor, stream=None) -> torch.Tensor:
+        X = X.to(torch.float32).contiguous()
+        Y = torch.empty(X.shape[0], self.n_out, dtype=torch.float32, device="cuda")
+        _check(lib().nys_mlp_forward(self.h, _ptr(X), X.shape[0], _ptr(Y), c_void_p(_stream_ptr(stream))),
+               "nys_mlp_forward")
+        return Y
+
+    def grad(self, X: torch.Tensor, T: torch.Tensor, stream=None):
+        X = X.to(torch.float32).contiguous()
+        T = T.to(torch.float32).contiguous()
+        g = torch.empty(self.n_params(), dtype=torch.float32, device="cuda")
+        loss = ctypes.c_float()
+        _check(lib().nys_mlp_grad(self.h, _ptr(X), _ptr(T), X.shape[0], _ptr(g), ctypes.byref(loss),
+                                  c_void_p(_stream_ptr(stream))), "nys_mlp_grad")
+        return loss.value, g
+
+    def train_step(self, X: torch.Tensor, T: torch.Tensor, lr: float = 1e-3, stream=None) -> float:
+        X = X.to(torch.float32).contiguous()
+        T = T.to(torch.float32).contiguous()
+        loss = ctypes.c_float()
+        _check(lib().nys_mlp_train_step(self.h, _ptr(X), _ptr(T), X.shape[0], float(lr), ctypes.byref(loss),
+                                        c_void_p(_stream_ptr(stream))), "nys_mlp_train_step")
+        return loss.value
+
+    def n_params(self) -> int:
+        n = c_int64()
+        _check(lib().nys_mlp_get_params(self.h, None, ctypes.byref(n), None), "nys_mlp_get_params")
+        return n.value
+
+    def params(self) -> torch.Tensor:
+        out = torch.empty(self.n_params(), dtype=torch.float32, device="cuda")
+        _check(lib().nys_mlp_get_params(self.h, _ptr(out), None, c_void_p(_stream_ptr())), "nys_mlp_get_params")
+        return out

@@ -50,7 +50,7 @@ def test_struct_layouts_match_header(libpath):
     # offsets follow C natural alignment of the header's structs
     assert ctypes.sizeof(nx.NysMatrixC) == 40
     assert nx.NysOptsC.stream.offset == 96 and nx.NysOptsC.hx_refresh.offset == 108
-    assert ctypes.sizeof(nx.NysOptsC) == 112
+    assert ctypes.sizeof(nx.NysOptsC) == 128
     assert ctypes.sizeof(nx.NysInfoC) == 48
     assert ctypes.sizeof(nx.NysStatsC) == 8 + 3 * 8 * 6
 

@@ -455,3 +455,36 @@ def test_adaptive_rank_sequence_and_stop():
     Om = np.hstack(blocks)
     Hdef = o.nystrom_definition(H, Om)
     assert np.linalg.norm((U * lam) @ U.T - Hdef, 2) <= 1e-9 * np.linalg.norm(H, 2)
+
+
+# ---------------------------------------------------------------- MLP (learned warm start)
+
+def test_mlp_gradient_matches_finite_differences():
+    rng = np.random.default_rng(60)
+    ni, nh, no = 7, 9, 5
+    theta = rng.standard_normal(o.mlp_param_count(ni, nh, no)) * 0.4
+    X = rng.standard_normal((6, ni))
+    T = rng.standard_normal((6, no))
+    _, g = o.mlp_loss_grad(theta, X, T, ni, nh, no)
+    h = 1e-6
+    for idx in rng.choice(theta.size, 40, replace=False):
+        e = np.zeros_like(theta)
+        e[idx] = h
+        lp, _ = o.mlp_loss_grad(theta + e, X, T, ni, nh, no)
+        lm, _ = o.mlp_loss_grad(theta - e, X, T, ni, nh, no)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[idx]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_gelu_values_and_derivative():
+    from scipy.stats import norm
+    z = np.linspace(-4, 4, 41)
+    assert np.allclose(o.gelu(z), z * norm.cdf(z), rtol=1e-14, atol=1e-15)
+    h = 1e-6
+    assert np.allclose(o.gelu_grad(z), (o.gelu(z + h) - o.gelu(z - h)) / (2 * h), rtol=1e-7, atol=1e-9)
+
+
+def test_adam_first_step_is_signed_lr():
+    g = np.array([0.3, -2.0, 1e-3])
+    th, m, v = o.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, lr=0.01)
+    assert np.allclose(th, -0.01 * np.sign(g) * np.abs(g) / (np.abs(g) + 1e-8), rtol=1e-12)
