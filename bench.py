@@ -139,6 +139,7 @@ def run_ours(args):
     A64 = w["A32"].double()
     Abf = w["A32"].to(torch.bfloat16)
     M64, Mbf = nx.Matrix(A64), nx.Matrix(Abf)
+    tuned = {"bf16": nx.autotune_apass(Mbf), "f64": nx.autotune_apass(M64)}
     b, gamma, Om, rho, s = w["b"], w["gamma"], w["Omega"], w["rho"], w["s"]
 
     def F(z):
@@ -258,7 +259,8 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded; the paper's datasets are not available offline)",
-        "config": dict(workload_config(w), hx_refresh=args.hx_refresh, admm_iters_to_gap=iters, pcg_iters_per_solve=info["pcg_iters_total"],
+        "config": dict(workload_config(w), hx_refresh=args.hx_refresh, autotuned_rows_per_stage=tuned,
+                       admm_iters_to_gap=iters, pcg_iters_per_solve=info["pcg_iters_total"],
                        final_gap=gap_final, F_star=Fstar, emp_cond=info["emp_cond"],
                        step_ms=[round(x, 3) for x in step_ms], parallelism="replicas" if world > 1 else "single"),
         "roofline": roofline,
@@ -496,6 +498,47 @@ def extra_batched(args):
     print(json.dumps({"extra": "batched", "path": path, "uneven_batch": batch}), flush=True)
 
 
+def extra_logistic(args):
+    """l1-logistic regression (Sec. 3.2) at the size of the logistic configuration:
+    A = N(0, 1/d) diag((1+j)^-1/2), 200,000 x 5,000 (FP64 problem matrix, FP32 copy for
+    the sketch and PCG), labels b = sign(A x* + Logistic(0,1)), x* 2% sparse N(0, 4),
+    gamma = 1e-3 n, rho = 1, adaptive rank 100 -> 400 (Tol 2), FP32 PCG rel-tol 1e-6,
+    re-sketch every 10 outer iterations.  Separate JSON line."""
+    from paper_2202_11599_gb300 import nysadmm as nx
+    import __graft_entry__
+    __graft_entry__.build()
+    n, d = 200_000, 5_000
+    g = torch.Generator(device="cuda").manual_seed(2)
+    A32 = torch.randn(n, d, generator=g, device="cuda", dtype=torch.float32) / math.sqrt(d)
+    A32 *= ((1.0 + torch.arange(d, device="cuda", dtype=torch.float32)) ** -0.5)[None, :]
+    xs = torch.zeros(d, device="cuda", dtype=torch.float64)
+    idx = torch.randperm(d, generator=g, device="cuda")[: d // 50]
+    xs[idx] = 2.0 * torch.randn(idx.numel(), generator=g, device="cuda", dtype=torch.float64)
+    u = torch.rand(n, generator=g, device="cuda", dtype=torch.float64).clamp(1e-12, 1 - 1e-12)
+    b = torch.sign(A32.double() @ xs + torch.log(u / (1 - u)))
+    b[b == 0] = 1.0
+    A64 = A32.double()
+    M64, M32 = nx.Matrix(A64), nx.Matrix(A32)
+    gamma = 1e-3 * n
+    Om = torch.randn(d, 400, generator=g, device="cuda", dtype=torch.float64)
+    K = args.extra_iters
+    nx.nysadmm_solve("logistic", M64, b, gamma, 1.0, 100, 1e-6, Om, admm_iters=2, A_inner=M32, rank_max=400,
+                     ada_tol=2.0, resketch_every=10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = nx.nysadmm_solve("logistic", M64, b, gamma, 1.0, 100, 1e-6, Om, admm_iters=K, A_inner=M32, rank_max=400,
+                           ada_tol=2.0, resketch_every=10)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    F0 = nx.objective("logistic", M64, b, gamma, torch.zeros(d, device="cuda", dtype=torch.float64))[0]
+    F, gmax, _ = nx.objective("logistic", M64, b, gamma, out["z"])
+    print(json.dumps({"extra": "logistic", "n": n, "d": d, "admm_iters": K, "time_s": round(t, 3),
+                      "ms_per_iter": round(1e3 * t / K, 2), "final_rank": out["info"]["final_rank"],
+                      "pcg_iters_total": out["info"]["pcg_iters_total"], "F0": F0, "F": F,
+                      "kkt_grad_inf_over_gamma": gmax / gamma, "nnz": int((out["z"] != 0).sum()),
+                      "emp_cond": out["info"]["emp_cond"]}), flush=True)
+
+
 def profile_apass(dt):
     """Small ncu case: the fused A-pass y = A^T (A p) + rho p on a 50000 x 10000 matrix
     (1 GB in BF16, larger than L2): 2 warm-up launches, then 6 timed launches."""
@@ -541,7 +584,7 @@ def main():
     ap.add_argument("--no-check", action="store_true", help="skip F* and the final gap check (profiling runs)")
     ap.add_argument("--profile-apass", choices=["bf16", "f32", "f64"], default=None,
                     help="only run the fused A-pass on a 50000 x 10000 matrix (ncu capture case)")
-    ap.add_argument("--extra", choices=["batched"], default=None,
+    ap.add_argument("--extra", choices=["batched", "logistic"], default=None,
                     help="run a secondary workload and print its own JSON line")
     ap.add_argument("--extra-iters", type=int, default=100)
     ap.add_argument("--no-plain", action="store_true")
@@ -552,6 +595,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.extra == "batched":
         extra_batched(args)
+    elif args.extra == "logistic":
+        extra_logistic(args)
     elif args.profile_apass:
         profile_apass(args.profile_apass)
     elif args.impl == "reference":

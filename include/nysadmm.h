@@ -298,6 +298,14 @@ nys_status nys_mlp_train_step(nys_mlp M, const float* X, const float* T, int32_t
 nys_status nys_mlp_get_params(nys_mlp M, float* out, int64_t* n_params, void* stream);
 void nys_mlp_destroy(nys_mlp M);
 
+/* Autotuner for the fused pass (no counterpart in the paper): times each supported
+ * rows-per-stage choice (1, 2 or 4 rows per TMA stage, as the register and shared
+ * memory budgets allow) on A with CUDA events (one warm-up and three timed passes
+ * each) and keeps the fastest for every later pass over a matrix of the same
+ * storage type and row width in this process.  *rows_out, *ms_out (host, may be
+ * NULL): the choice and its time per pass. */
+nys_status nys_autotune_apass(const nys_matrix* A, int32_t* rows_out, double* ms_out, void* stream);
+
 void nys_precond_destroy(nys_precond P);
 const char* nys_strerror(int32_t status);
 

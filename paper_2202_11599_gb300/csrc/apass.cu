@@ -24,6 +24,9 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace nys {
 
@@ -617,6 +620,39 @@ static int vpt_bucket(int64_t nvec) {
   return -1;
 }
 
+// Autotuned rows-per-stage, keyed by (dtype, columns per thread, row bytes).
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int64_t>, int> g_tuned_rows;
+
+void apass_set_tuned_rows(const nys_matrix* A, int rows) {
+  const int64_t esz = (int64_t)dtype_size(A->dtype);
+  const int vpt = vpt_bucket((A->d + (16 / esz) - 1) / (16 / esz));
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (rows <= 0) g_tuned_rows.erase({A->dtype, vpt, A->ld * esz});
+  else g_tuned_rows[{A->dtype, vpt, A->ld * esz}] = rows;
+}
+
+static int tuned_rows(int dtype, int vpt, int64_t rowbytes) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned_rows.find({dtype, vpt, rowbytes});
+  return it == g_tuned_rows.end() ? 0 : it->second;
+}
+
+// Rows-per-stage values the kernels support for this matrix (float path: bounded by
+// the register budget of the raw vectors; all: at least two stages must fit).
+int apass_row_candidates(const nys_matrix* A, int* out) {
+  const int64_t esz = (int64_t)dtype_size(A->dtype);
+  const int vpt = vpt_bucket((A->d + (16 / esz) - 1) / (16 / esz));
+  const int64_t rowbytes = A->ld * esz;
+  int n = 0;
+  for (int r : {1, 2, 4}) {
+    if (2 * r * rowbytes > kSmemBudget) continue;
+    if (A->dtype != NYS_F64 && ((r == 2 && vpt > 6) || (r == 4 && vpt > 3))) continue;
+    out[n++] = r;
+  }
+  return n;
+}
+
 bool apass_plan(const nys_matrix* A, ApassPlan* plan) {
   const int64_t esz = (int64_t)dtype_size(A->dtype);
   const int vec = (int)(16 / esz);
@@ -626,9 +662,13 @@ bool apass_plan(const nys_matrix* A, ApassPlan* plan) {
   if (A->dtype == NYS_F64 && vpt > 12) return false;
   const int64_t rowbytes = A->ld * esz;
   int R = (int)std::max<int64_t>(1, std::min<int64_t>(kRMax, (48 * 1024) / rowbytes));
+  if (A->dtype == NYS_F64) {
+    if (const int tr = tuned_rows(A->dtype, vpt, rowbytes)) R = tr;
+  }
   if (A->dtype != NYS_F64) {
     // float path: R is a template parameter bounded by the register budget of raw[R][VPT]
     R = vpt <= 3 ? 4 : (vpt <= 6 ? 2 : 1);
+    if (const int tr = tuned_rows(A->dtype, vpt, rowbytes)) R = tr;
     // tuning override (rows per stage), e.g. NYS_APASS_ROWS=2; kept only if the
     // register-bounded instantiation exists for this width
     if (const char* env = std::getenv("NYS_APASS_ROWS")) {

@@ -1203,6 +1203,65 @@ nys_status nys_objective(int32_t loss, const nys_matrix* A, const double* b, dou
   return NYS_OK;
 }
 
+nys_status nys_autotune_apass(const nys_matrix* A, int32_t* rows_out, double* ms_out, void* stream) {
+  NYS_TRY(check_matrix(A));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int cand[3];
+  const int nc = apass_row_candidates(A, cand);
+  if (nc == 0) return NYS_EINVAL;
+  const bool f64 = A->dtype == NYS_F64;
+  Pool pool(st);
+  void* p = pool.alloc<unsigned char>((size_t)A->d * 8);
+  int* dstat = pool.alloc<int>(1);
+  ApassPlan big;
+  apass_plan(A, &big);
+  // partials for the largest grid any candidate can use
+  void* part = pool.alloc<unsigned char>((size_t)big.dpad * 8 * 256);
+  cudaEvent_t e0, e1;
+  if (!pool.ok()) return NYS_ENOMEM;
+  NYS_CU(cudaMemsetAsync(p, 0, (size_t)A->d * 8, st));
+  NYS_CU(cudaMemsetAsync(dstat, 0, sizeof(int), st));
+  NYS_CU(cudaEventCreate(&e0));
+  NYS_CU(cudaEventCreate(&e1));
+  int best = cand[0];
+  double best_ms = 1e300;
+  for (int c = 0; c < nc; ++c) {
+    apass_set_tuned_rows(A, cand[c]);
+    ApassPlan plan;
+    if (!apass_plan(A, &plan) || plan.grid > 256) continue;
+    ApassArgs a;
+    a.A = A->data;
+    a.n = A->n;
+    a.d = A->d;
+    a.ld = A->ld;
+    a.dtype = A->dtype;
+    a.p = p;
+    a.D = nullptr;
+    a.b = nullptr;
+    a.D_out = nullptr;
+    a.t_out = nullptr;
+    a.mode = MODE_ID;
+    NYS_CU(apass_run(a, plan, part, nullptr, dstat, st, false));  // warm-up
+    NYS_CU(cudaEventRecord(e0, st));
+    for (int rep = 0; rep < 3; ++rep) NYS_CU(apass_run(a, plan, part, nullptr, dstat, st, false));
+    NYS_CU(cudaEventRecord(e1, st));
+    NYS_CU(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    NYS_CU(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms / 3.0 < best_ms) {
+      best_ms = ms / 3.0;
+      best = cand[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  (void)f64;
+  apass_set_tuned_rows(A, best);
+  if (rows_out) *rows_out = best;
+  if (ms_out) *ms_out = best_ms;
+  return NYS_OK;
+}
+
 void nys_precond_destroy(nys_precond P) { precond_free(P); }
 
 }  // extern "C"

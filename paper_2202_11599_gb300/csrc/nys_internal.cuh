@@ -47,6 +47,8 @@ struct ApassPlan {
 };
 
 bool apass_plan(const nys_matrix* A, ApassPlan* plan);
+void apass_set_tuned_rows(const nys_matrix* A, int rows);   // rows <= 0 clears
+int apass_row_candidates(const nys_matrix* A, int* out);      // out: up to 3 values
 size_t apass_partial_bytes(const nys_matrix* A, const ApassPlan& plan);
 
 // y = sum of partials + rho * p (+ beta * y_prev?) -- y in compute type.

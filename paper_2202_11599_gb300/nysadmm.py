@@ -104,6 +104,8 @@ def lib() -> ctypes.CDLL:
     L.nys_mlp_get_params.argtypes = [c_void_p, c_void_p, P(c_int64), c_void_p]
     L.nys_mlp_destroy.argtypes = [c_void_p]
     L.nys_mlp_destroy.restype = None
+    L.nys_autotune_apass.argtypes = [P(NysMatrixC), P(c_int32), P(c_double), c_void_p]
+    L.nys_autotune_apass.restype = c_int32
     L.nys_precond_destroy.argtypes = [c_void_p]
     L.nys_precond_destroy.restype = None
     for name in ("nys_hmatvec", "nys_hmatvec_noalloc", "nys_sketch", "nys_precond_get", "nys_precond_apply", "pcg_solve",
@@ -193,6 +195,16 @@ def hmatvec_noalloc(A: Matrix, p: torch.Tensor, rho: float = 0.0, D: torch.Tenso
     _check(lib().nys_hmatvec_noalloc(ctypes.byref(A.c), _ptr(D), float(rho), _ptr(p), _ptr(y),
                                      c_void_p(_stream_ptr(stream))), "nys_hmatvec_noalloc")
     return y
+
+
+def autotune_apass(A: Matrix, stream=None):
+    """Time the supported rows-per-stage choices of the fused pass on A, keep the best.
+    Returns (rows, ms per pass)."""
+    r = c_int32()
+    ms = c_double()
+    _check(lib().nys_autotune_apass(ctypes.byref(A.c), ctypes.byref(r), ctypes.byref(ms),
+                                    c_void_p(_stream_ptr(stream))), "nys_autotune_apass")
+    return r.value, ms.value
 
 
 class Precond:

@@ -412,3 +412,17 @@ def test_batch_of_uneven_instances_one_graph():
         assert out["info"]["pcg_iters_total"] == single["info"]["pcg_iters_total"]
         ref = o.lasso_nysadmm(p.A, p.b, p.gamma, 10.0, Om, 120, pcg_tol=1e-11)
         assert np.linalg.norm(out["z"].cpu().numpy() - ref["z"]) <= 1e-9 * max(1.0, np.linalg.norm(ref["z"]))
+
+
+def test_autotuner_picks_a_supported_shape_and_results_do_not_change():
+    rng = np.random.default_rng(90)
+    A = rng.standard_normal((20000, 1000))
+    for dtype in (torch.bfloat16, torch.float32, torch.float64):
+        M = nx.Matrix.padded(_dev(A), dtype)
+        p = _dev(rng.standard_normal(1000)).to(M.compute_dtype)
+        y0 = nx.hmatvec(M, p, 0.5)
+        rows, ms = nx.autotune_apass(M)
+        assert rows in (1, 2, 4) and ms > 0
+        y1 = nx.hmatvec(M, p, 0.5)
+        tol = 1e-12 if dtype == torch.float64 else 1e-5
+        assert ((y1.double() - y0.double()).abs().max() / y0.double().abs().max()).item() <= tol
