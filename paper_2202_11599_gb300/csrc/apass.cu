@@ -343,21 +343,30 @@ __device__ __forceinline__ uint4 lds128(uint32_t addr) {
   return v;
 }
 
+// The per-row input of the pass's mode (D_i or b_i), loaded at the start of a step so
+// that its latency overlaps the dot products instead of sitting between the barriers.
+__device__ __forceinline__ double row_input(const ApassKArgs& a, int64_t i) {
+  if (a.mode == MODE_ID) return 0.0;
+  if (a.mode == MODE_DIAG) return a.D[i];
+  return a.b[i];
+}
+
 // Row modes of the pass, applied by the warp that finishes row i: returns u_i.
-__device__ __forceinline__ float row_phi(const ApassKArgs& a, int64_t i, float t, double& loss) {
+// `in` is row_input(a, i).
+__device__ __forceinline__ float row_phi(const ApassKArgs& a, int64_t i, float t, double in, double& loss) {
   switch (a.mode) {
-    case MODE_CONST: return (float)a.b[i];
+    case MODE_CONST: return (float)in;
     case MODE_ID: return t;
-    case MODE_DIAG: return (float)(a.D[i] * (double)t);
+    case MODE_DIAG: return (float)(in * (double)t);
     case MODE_RESID: {
-      const double rr = (double)t - a.b[i];
+      const double rr = (double)t - in;
       loss += 0.5 * rr * rr;
       return (float)rr;
     }
     case MODE_LGRAD: {
       const double td = (double)t;
       const double sg = sigmoid_d(td);
-      const double b01 = 0.5 * (1.0 + a.b[i]);
+      const double b01 = 0.5 * (1.0 + in);
       loss += fmax(td, 0.0) + log1p(exp(-fabs(td))) - b01 * td;
       return (float)(sg - b01);
     }
@@ -365,7 +374,7 @@ __device__ __forceinline__ float row_phi(const ApassKArgs& a, int64_t i, float t
       const double td = (double)t;
       const double sg = sigmoid_d(td);
       const double wv = sg * (1.0 - sg);
-      const double b01 = 0.5 * (1.0 + a.b[i]);
+      const double b01 = 0.5 * (1.0 + in);
       if (a.D_out) a.D_out[i] = wv;
       loss += fmax(td, 0.0) + log1p(exp(-fabs(td))) - b01 * td;
       return (float)(wv * td + b01 - sg);
@@ -379,12 +388,16 @@ __device__ __forceinline__ float row_phi(const ApassKArgs& a, int64_t i, float t
 // refilled by TMA at once (all S stages stay in flight); warps 0..R-1 finish the row
 // sums and apply phi; after the second barrier every thread applies the rank-R
 // update from the same registers.
-template <int DT, int VPT, int R>
-__global__ void __launch_bounds__(kApassThreads, 1) apass_f_kernel(const ApassKArgs a) {
+// ONEBAR selects the finish of a step in the H-matvec modes: false = warps 0..R-1 finish
+// one row sum each and a second barrier publishes them; true = every warp finishes all R
+// row sums itself (one barrier per step, R warp reductions per warp).  A variant that
+// re-read the stage from shared memory for the update instead of holding it in
+// registers (refill one step later) measured slower in every configuration.
+template <int DT, int VPT, int R, int T, bool ONEBAR>
+__global__ void __launch_bounds__(T, 1) apass_f_kernel(const ApassKArgs a) {
   constexpr int VEC = Stor<DT>::VEC;
   constexpr int ESZ = Stor<DT>::ESZ;
   constexpr int NP = VEC / 2;
-  constexpr int T = kApassThreads;
   constexpr int NW = T / 32;
 
   extern __shared__ __align__(128) unsigned char smem[];
@@ -454,6 +467,16 @@ __global__ void __launch_bounds__(kApassThreads, 1) apass_f_kernel(const ApassKA
     const int stage = k % S;
     const uint32_t sb = sbase + (uint32_t)stage * stage_bytes;
     const int rows_here = (int)min((int64_t)R, r1 - (r0 + (int64_t)k * R));
+    // per-row mode inputs: warp r (two-barrier finish) or every warp (one-barrier
+    // finish) needs those of its rows; load them before waiting for the stage
+    double rin[ONEBAR ? R : 1];
+    if (ONEBAR && (a.mode == MODE_ID || a.mode == MODE_DIAG)) {
+#pragma unroll
+      for (int r = 0; r < (ONEBAR ? R : 1); ++r)
+        rin[r] = r < rows_here ? row_input(a, r0 + (int64_t)k * R + r) : 0.0;
+    } else {
+      rin[0] = (warp < rows_here && lane == 0) ? row_input(a, r0 + (int64_t)k * R + warp) : 0.0;
+    }
     const bool ok = mbar_wait_bounded(&bars[stage], (uint32_t)((k / S) & 1));
 
     uint4 raw[R][VPT];
@@ -492,11 +515,10 @@ __global__ void __launch_bounds__(kApassThreads, 1) apass_f_kernel(const ApassKA
       ++issued;
     }
     float2 u2[R];
-    // FP32 storage, H-matvec modes: the per-warp finish below removes the second barrier
-    // (measured 5.8 -> 7.0 TB/s).  BF16 keeps the two-barrier step: at R = 4 its raw
-    // registers leave no room for the extra row sums (measured 4.1 -> 2.8 TB/s), and
-    // at R = 2 the per-step overhead dominates (2.7-2.8 TB/s either way).
-    if (DT == NYS_F32 && (a.mode == MODE_ID || a.mode == MODE_DIAG)) {
+    // ONEBAR (H-matvec modes): the per-warp finish below removes the second barrier
+    // (FP32 storage, 512 threads: measured 5.8 -> 7.0 TB/s).  The host picks ONEBAR per
+    // storage type and block size (register budget of raw[R][VPT]).
+    if (ONEBAR && (a.mode == MODE_ID || a.mode == MODE_DIAG)) {
       // every warp finishes all R row sums itself (lanes 0..NW-1 hold
       // the warp partials of each row; a butterfly leaves the sum in every lane), so no
       // second barrier is needed.  Warp r's lane 0 writes row r's side outputs.
@@ -508,7 +530,7 @@ __global__ void __launch_bounds__(kApassThreads, 1) apass_f_kernel(const ApassKA
         float u = 0.f;
         if (r < rows_here) {
           const int64_t i = r0 + (int64_t)k * R + r;
-          u = a.mode == MODE_ID ? t[r] : (float)(a.D[i] * (double)t[r]);
+          u = a.mode == MODE_ID ? t[r] : (float)(rin[r] * (double)t[r]);
           if (warp == r && lane == 0 && a.t_out) a.t_out[i] = (double)t[r];
         }
         u2[r] = make_float2(u, u);
@@ -521,7 +543,7 @@ __global__ void __launch_bounds__(kApassThreads, 1) apass_f_kernel(const ApassKA
           float u = 0.f;
           if (warp < rows_here) {
             const int64_t i = r0 + (int64_t)k * R + warp;
-            u = row_phi(a, i, t, loss);
+            u = row_phi(a, i, t, rin[0], loss);
             if (!nodot && a.t_out) a.t_out[i] = (double)t;
           }
           us[k & 1][warp] = u;
@@ -612,8 +634,8 @@ int reduce_blocks(int64_t d) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 4 * (int64_t)sm_count()));
 }
 
-static int vpt_bucket(int64_t nvec) {
-  const int64_t need = (nvec + kApassThreads - 1) / kApassThreads;
+static int vpt_bucket(int64_t nvec, int threads = kApassThreads) {
+  const int64_t need = (nvec + threads - 1) / threads;
   static const int buckets[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
   for (int b : buckets)
     if (need <= b) return b;
@@ -638,16 +660,38 @@ static int tuned_rows(int dtype, int vpt, int64_t rowbytes) {
   return it == g_tuned_rows.end() ? 0 : it->second;
 }
 
+// Float-path CTA size and vectors per thread.  BF16: where 512 threads would need 3
+// vectors per thread but 640 need 2, the 640-thread CTA (R = 4) is used instead
+// (d = 10,000 BF16, 100,000 rows: 4.03 -> 4.53 TB/s measured).  Tuning override:
+// NYS_APASS_THREADS (512 or 640; 640 only where it needs <= 4 vectors per thread).
+static void float_layout(const nys_matrix* A, int64_t nvec, int* threads, int* vpt) {
+  *threads = kApassThreads;
+  *vpt = vpt_bucket(nvec);
+  int want = 0;
+  if (A->dtype == NYS_BF16 && *vpt == 3 && vpt_bucket(nvec, kApassThreadsWide) == 2) want = kApassThreadsWide;
+  if (const char* env = std::getenv("NYS_APASS_THREADS")) want = std::atoi(env);
+  if (want == kApassThreadsWide && vpt_bucket(nvec, want) > 0 && vpt_bucket(nvec, want) <= 4) {
+    *threads = want;
+    *vpt = vpt_bucket(nvec, want);
+  }
+}
+
+// Rows per step the float kernel is instantiated for at this many vectors per thread
+// (register budget of raw[R][VPT]).
+static bool float_rows_ok(int r, int vpt) { return r == 1 || (r == 2 && vpt <= 6) || (r == 4 && vpt <= 3); }
+
 // Rows-per-stage values the kernels support for this matrix (float path: bounded by
 // the register budget of the raw vectors; all: at least two stages must fit).
 int apass_row_candidates(const nys_matrix* A, int* out) {
   const int64_t esz = (int64_t)dtype_size(A->dtype);
-  const int vpt = vpt_bucket((A->d + (16 / esz) - 1) / (16 / esz));
+  const int64_t nvec = (A->d + (16 / esz) - 1) / (16 / esz);
+  int threads = kApassThreads, vpt = vpt_bucket(nvec);
+  if (A->dtype != NYS_F64) float_layout(A, nvec, &threads, &vpt);
   const int64_t rowbytes = A->ld * esz;
   int n = 0;
   for (int r : {1, 2, 4}) {
     if (2 * r * rowbytes > kSmemBudget) continue;
-    if (A->dtype != NYS_F64 && ((r == 2 && vpt > 6) || (r == 4 && vpt > 3))) continue;
+    if (A->dtype != NYS_F64 && !float_rows_ok(r, vpt)) continue;
     out[n++] = r;
   }
   return n;
@@ -657,24 +701,33 @@ bool apass_plan(const nys_matrix* A, ApassPlan* plan) {
   const int64_t esz = (int64_t)dtype_size(A->dtype);
   const int vec = (int)(16 / esz);
   const int64_t nvec = (A->d + vec - 1) / vec;
-  int vpt = vpt_bucket(nvec);
-  if (vpt < 0) return false;
-  if (A->dtype == NYS_F64 && vpt > 12) return false;
+  const int vkey = vpt_bucket(nvec);  // tuning key: vectors per thread at 512 threads
+  if (vkey < 0) return false;
+  if (A->dtype == NYS_F64 && vkey > 12) return false;
   const int64_t rowbytes = A->ld * esz;
+  int vpt = vkey;
   int R = (int)std::max<int64_t>(1, std::min<int64_t>(kRMax, (48 * 1024) / rowbytes));
   if (A->dtype == NYS_F64) {
-    if (const int tr = tuned_rows(A->dtype, vpt, rowbytes)) R = tr;
+    if (const int tr = tuned_rows(A->dtype, vkey, rowbytes)) R = tr;
   }
+  int threads = kApassThreads;
+  bool onebar = false;
   if (A->dtype != NYS_F64) {
+    float_layout(A, nvec, &threads, &vpt);
     // float path: R is a template parameter bounded by the register budget of raw[R][VPT]
     R = vpt <= 3 ? 4 : (vpt <= 6 ? 2 : 1);
-    if (const int tr = tuned_rows(A->dtype, vpt, rowbytes)) R = tr;
-    // tuning override (rows per stage), e.g. NYS_APASS_ROWS=2; kept only if the
-    // register-bounded instantiation exists for this width
+    if (const int tr = tuned_rows(A->dtype, vkey, rowbytes)) R = tr;
+    // FP32: one barrier per step (every warp finishes the R row sums itself); BF16: two
+    // barriers (its raw registers leave no room for R row sums in every warp: measured
+    // 4.0 -> 3.1 TB/s with one barrier).  Tuning overrides: NYS_APASS_ROWS (rows per
+    // stage; kept only if the instantiation exists for this width), NYS_APASS_ONEBAR (0/1).
+    onebar = A->dtype == NYS_F32;
     if (const char* env = std::getenv("NYS_APASS_ROWS")) {
       const int r = std::atoi(env);
-      if ((r == 1) || (r == 2 && vpt <= 6) || (r == 4 && vpt <= 3)) R = r;
+      if (float_rows_ok(r, vpt)) R = r;
     }
+    if (const char* env = std::getenv("NYS_APASS_ONEBAR")) onebar = std::atoi(env) != 0;
+    if (!float_rows_ok(R, vpt)) R = 1;
     while (R > 1 && 2 * R * rowbytes > kSmemBudget) R /= 2;
   }
   int S = (int)std::min<int64_t>(kMaxStages, kSmemBudget / (R * rowbytes));
@@ -685,6 +738,9 @@ bool apass_plan(const nys_matrix* A, ApassPlan* plan) {
   if (S < 2) return false;
   plan->rows_per_step = R;
   plan->stages = S;
+  plan->threads = threads;
+  plan->vpt = vpt;
+  plan->onebar = onebar;
   plan->smem = (size_t)S * R * rowbytes;
   plan->dpad = nvec * vec;
   const int64_t steps_total = (A->n + R - 1) / R;
@@ -714,9 +770,9 @@ static cudaError_t launch_vpt(const ApassKArgs& k, const ApassPlan& plan, cudaSt
   return cudaGetLastError();
 }
 
-template <int DT, int VPT, int R>
+template <int DT, int VPT, int R, int T, bool OB>
 static cudaError_t launch_f(const ApassKArgs& k, const ApassPlan& plan, cudaStream_t st) {
-  auto fn = apass_f_kernel<DT, VPT, R>;
+  auto fn = apass_f_kernel<DT, VPT, R, T, OB>;
   static bool attr_set = false;
   if (!attr_set) {
     NYS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
@@ -724,16 +780,22 @@ static cudaError_t launch_f(const ApassKArgs& k, const ApassPlan& plan, cudaStre
   }
   if (g_prepare_only) return cudaSuccess;
   count_launch();
-  fn<<<plan.grid, kApassThreads, plan.smem, st>>>(k);
+  fn<<<plan.grid, T, plan.smem, st>>>(k);
   return cudaGetLastError();
 }
 
-template <int DT, int VPT>
+template <int DT, int VPT, int R, int T>
+static cudaError_t launch_fo(const ApassKArgs& k, const ApassPlan& plan, cudaStream_t st) {
+  if (plan.onebar) return launch_f<DT, VPT, R, T, true>(k, plan, st);
+  return launch_f<DT, VPT, R, T, false>(k, plan, st);
+}
+
+template <int DT, int VPT, int T>
 static cudaError_t launch_fr(const ApassKArgs& k, const ApassPlan& plan, cudaStream_t st) {
   switch (plan.rows_per_step) {
-    case 4: if constexpr (VPT <= 3) return launch_f<DT, VPT, 4>(k, plan, st); break;
-    case 2: if constexpr (VPT <= 6) return launch_f<DT, VPT, 2>(k, plan, st); break;
-    case 1: return launch_f<DT, VPT, 1>(k, plan, st);
+    case 4: if constexpr (VPT <= 3) return launch_fo<DT, VPT, 4, T>(k, plan, st); break;
+    case 2: if constexpr (VPT <= 6) return launch_fo<DT, VPT, 2, T>(k, plan, st); break;
+    case 1: return launch_fo<DT, VPT, 1, T>(k, plan, st);
     default: break;
   }
   return cudaErrorInvalidValue;
@@ -741,19 +803,27 @@ static cudaError_t launch_fr(const ApassKArgs& k, const ApassPlan& plan, cudaStr
 
 template <int DT>
 static cudaError_t launch_float(const ApassKArgs& k, const ApassPlan& plan, cudaStream_t st) {
-  constexpr int VEC = Stor<DT>::VEC;
-  const int64_t nvec = (k.d + VEC - 1) / VEC;
-  switch (vpt_bucket(nvec)) {
-    case 1: return launch_fr<DT, 1>(k, plan, st);
-    case 2: return launch_fr<DT, 2>(k, plan, st);
-    case 3: return launch_fr<DT, 3>(k, plan, st);
-    case 4: return launch_fr<DT, 4>(k, plan, st);
-    case 5: return launch_fr<DT, 5>(k, plan, st);
-    case 6: return launch_fr<DT, 6>(k, plan, st);
-    case 8: return launch_fr<DT, 8>(k, plan, st);
-    case 10: return launch_fr<DT, 10>(k, plan, st);
-    case 12: return launch_fr<DT, 12>(k, plan, st);
-    case 16: return launch_fr<DT, 16>(k, plan, st);
+  if (plan.threads == kApassThreadsWide) {
+    switch (plan.vpt) {
+      case 1: return launch_fr<DT, 1, kApassThreadsWide>(k, plan, st);
+      case 2: return launch_fr<DT, 2, kApassThreadsWide>(k, plan, st);
+      case 3: return launch_fr<DT, 3, kApassThreadsWide>(k, plan, st);
+      case 4: return launch_fr<DT, 4, kApassThreadsWide>(k, plan, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (plan.threads != kApassThreads) return cudaErrorInvalidValue;
+  switch (plan.vpt) {
+    case 1: return launch_fr<DT, 1, kApassThreads>(k, plan, st);
+    case 2: return launch_fr<DT, 2, kApassThreads>(k, plan, st);
+    case 3: return launch_fr<DT, 3, kApassThreads>(k, plan, st);
+    case 4: return launch_fr<DT, 4, kApassThreads>(k, plan, st);
+    case 5: return launch_fr<DT, 5, kApassThreads>(k, plan, st);
+    case 6: return launch_fr<DT, 6, kApassThreads>(k, plan, st);
+    case 8: return launch_fr<DT, 8, kApassThreads>(k, plan, st);
+    case 10: return launch_fr<DT, 10, kApassThreads>(k, plan, st);
+    case 12: return launch_fr<DT, 12, kApassThreads>(k, plan, st);
+    case 16: return launch_fr<DT, 16, kApassThreads>(k, plan, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -3,7 +3,10 @@
 // PCG entry point (App. B, Alg. Nystrom PCG) and the NysADMM drivers
 // (Alg. NysADMM for the lasso, Sec. 3.2 + App. C for l1-logistic regression).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -26,6 +29,27 @@ struct nys_precond_s {
 namespace {
 
 constexpr int kMaxRank = 1024;
+
+// Phase trace (set NYS_TRACE=1): wall time of each sketch / core phase, the stream
+// synchronised at both ends, printed to stderr.
+struct PhaseTimer {
+  const char* name;
+  cudaStream_t st;
+  std::chrono::steady_clock::time_point t0;
+  bool on;
+  PhaseTimer(const char* n, cudaStream_t s) : name(n), st(s), on(std::getenv("NYS_TRACE") != nullptr) {
+    if (on) {
+      cudaStreamSynchronize(st);
+      t0 = std::chrono::steady_clock::now();
+    }
+  }
+  ~PhaseTimer() {
+    if (!on) return;
+    cudaStreamSynchronize(st);
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    std::fprintf(stderr, "[nys] %-22s %9.3f ms\n", name, ms);
+  }
+};
 
 cudaStream_t stream_of(const nys_opts* o) { return o ? reinterpret_cast<cudaStream_t>(o->stream) : nullptr; }
 
@@ -66,6 +90,7 @@ double eps_host(double t, int mant_bits) {
 
 // Thin QR of Omega (d x m, in place) by CholQR2: twice G = Om^T Om, C = chol(G), Om <- Om C^{-1}.
 nys_status cholqr2(double* Om, int64_t d, int m, cudaStream_t st) {
+  PhaseTimer pt("cholqr2", st);
   Pool pool(st);
   double* G = pool.alloc<double>((size_t)m * m);
   double* work = pool.alloc<double>(gram_work_bytes(d, m) / sizeof(double) + 1);
@@ -86,6 +111,7 @@ nys_status cholqr2(double* Om, int64_t d, int m, cudaStream_t st) {
 // Y (d x m, FP64) = (A^T diag(D) A + shift I) Om for an FP64 orthonormal panel Om.
 nys_status sketch_panel(const nys_matrix* A, const double* D, double shift, const double* Om, int m, double* Y,
                         cudaStream_t st) {
+  PhaseTimer pt("sketch Y = H Omega", st);
   Pool pool(st);
   const int64_t n = A->n, d = A->d;
   const size_t wbytes = sketch_atw_work_bytes(A, m);
@@ -126,14 +152,19 @@ nys_status nystrom_core(const double* Om, const double* Y, int64_t d, int s, dou
   double* fw = pool.alloc<double>((size_t)s * s + s);
   if (!pool.ok()) return NYS_ENOMEM;
 
-  NYS_CU(gram_xty(Y, Y, d, s, G, gw, st));
-  NYS_CU(power_lambda_max(G, s, lmax, pw, st));
+  PhaseTimer pt_all("nystrom core (total)", st);
+  {
+    PhaseTimer pt("core: Y^T Y + power", st);
+    NYS_CU(gram_xty(Y, Y, d, s, G, gw, st));
+    NYS_CU(power_lambda_max(G, s, lmax, pw, st));
+  }
   double lmax_h = 0.0;
   NYS_CU(cudaMemcpyAsync(&lmax_h, lmax, sizeof(double), cudaMemcpyDeviceToHost, st));
   NYS_CU(cudaStreamSynchronize(st));
   if (!is_fin(lmax_h)) return NYS_EINVAL;
   double nu = shift_scale * eps_host(std::sqrt(std::max(lmax_h, 0.0)), mant_bits);
   bool ok = false;
+  PhaseTimer* pt_chol = new PhaseTimer("core: shift + chol", st);
   for (int attempt = 0; attempt < 4; ++attempt) {
     NYS_CU(cudaMemcpyAsync(Ynu, Y, (size_t)d * s * sizeof(double), cudaMemcpyDeviceToDevice, st));
     NYS_CU(axpy_panel(nu, Om, Ynu, d * s, st));
@@ -148,12 +179,23 @@ nys_status nystrom_core(const double* Om, const double* Y, int64_t d, int s, dou
     }
     nu *= 10.0;
   }
+  delete pt_chol;
   if (!ok) return NYS_ENOTSPD;
-  NYS_CU(trsm_right_upper(M, s, Ynu, d, st));       // B = Y_nu C^{-1} (in Ynu)
-  NYS_CU(gram_xty(Ynu, Ynu, d, s, G, gw, st));      // B^T B
+  {
+    PhaseTimer pt("core: trsm + B^T B", st);
+    NYS_CU(trsm_right_upper(M, s, Ynu, d, st));       // B = Y_nu C^{-1} (in Ynu)
+    NYS_CU(gram_xty(Ynu, Ynu, d, s, G, gw, st));      // B^T B
+  }
   int sweeps = 0;
-  NYS_CU(jacobi_eig(G, V, s, jw, &sweeps, st));
-  NYS_CU(nystrom_finish(Ynu, d, s, jw, V, nu, U, lam_d, fw, st));
+  {
+    PhaseTimer pt("core: jacobi", st);
+    NYS_CU(jacobi_eig(G, V, s, jw, &sweeps, st));
+  }
+  {
+    PhaseTimer pt("core: finish (U = BV)", st);
+    NYS_CU(nystrom_finish(Ynu, d, s, jw, V, nu, U, lam_d, fw, st));
+  }
+  if (std::getenv("NYS_TRACE")) std::fprintf(stderr, "[nys] jacobi sweeps %d (s = %d)\n", sweeps, s);
   lam_h.resize(s);
   NYS_CU(cudaMemcpyAsync(lam_h.data(), lam_d, s * sizeof(double), cudaMemcpyDeviceToHost, st));
   NYS_CU(cudaStreamSynchronize(st));

@@ -7,6 +7,9 @@
 // All s x s work is FP64.  GEMM reductions are split into fixed chunks whose
 // partials are summed in a fixed order, so every result is run-to-run
 // deterministic.
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include "device_util.cuh"
 #include "nys_internal.cuh"
 
@@ -329,45 +332,63 @@ __device__ __forceinline__ void jacobi_rot(double app, double aqq, double apq, d
 }
 
 // One round: Aout = J^T Ain J and V <- V J for the round's N/2 disjoint rotations.
-__global__ void jacobi_round_kernel(const double* __restrict__ Ain, double* __restrict__ Aout, double* V,
-                                    int N, int r, const int* __restrict__ done) {
+// Block (bx, by) owns a 16 x 16 tile of 2x2 pair-blocks of A (pairs ma = bx*16 + tx,
+// mb = by*16 + ty); the 32 rotations it needs are computed once into shared memory.
+// Every block also applies its 16 column rotations to one row slice of V.
+constexpr int JT = 16;
+__global__ void __launch_bounds__(JT * JT) jacobi_round_kernel(const double* __restrict__ Ain, double* __restrict__ Aout,
+                                                               double* V, int N, int r, const int* __restrict__ done) {
   if (*done) return;
+  __shared__ double rc[2][JT], rs[2][JT];
+  __shared__ int rp[2][JT], rq[2][JT];
   const int H = N / 2;
-  const int64_t nA = (int64_t)H * H;
-  const int64_t total = nA + (int64_t)N * H;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    if (idx < nA) {
-      const int ma = (int)(idx % H), mb = (int)(idx / H);
-      int pa, qa, pb, qb;
-      rr_pair(N, r, ma, pa, qa);
-      rr_pair(N, r, mb, pb, qb);
-      double ca, sa, cb, sb;
-      jacobi_rot(Ain[pa + (int64_t)pa * N], Ain[qa + (int64_t)qa * N], Ain[pa + (int64_t)qa * N], ca, sa);
-      jacobi_rot(Ain[pb + (int64_t)pb * N], Ain[qb + (int64_t)qb * N], Ain[pb + (int64_t)qb * N], cb, sb);
-      const double x_pp = Ain[pa + (int64_t)pb * N], x_pq = Ain[pa + (int64_t)qb * N];
-      const double x_qp = Ain[qa + (int64_t)pb * N], x_qq = Ain[qa + (int64_t)qb * N];
-      // columns: p' = c p - s q, q' = s p + c q
-      const double y_pp = cb * x_pp - sb * x_pq, y_pq = sb * x_pp + cb * x_pq;
-      const double y_qp = cb * x_qp - sb * x_qq, y_qq = sb * x_qp + cb * x_qq;
-      // rows
-      double z_pp = ca * y_pp - sa * y_qp, z_pq = ca * y_pq - sa * y_qq;
-      double z_qp = sa * y_pp + ca * y_qp, z_qq = sa * y_pq + ca * y_qq;
-      if (ma == mb) {  // the rotated pair itself: off-diagonal is zero by construction
-        z_pq = 0.0;
-        z_qp = 0.0;
-      }
-      Aout[pa + (int64_t)pb * N] = z_pp;
-      Aout[pa + (int64_t)qb * N] = z_pq;
-      Aout[qa + (int64_t)pb * N] = z_qp;
-      Aout[qa + (int64_t)qb * N] = z_qq;
-    } else {
-      const int64_t t = idx - nA;
-      const int row = (int)(t % N), m = (int)(t / N);
-      int p, q;
+  const int tx = threadIdx.x % JT, ty = threadIdx.x / JT;
+  if (threadIdx.x < 2 * JT) {
+    const int side = threadIdx.x / JT, t = threadIdx.x % JT;
+    const int m = (side == 0 ? blockIdx.x : blockIdx.y) * JT + t;
+    int p = 0, q = 1;
+    double c = 1.0, sn = 0.0;
+    if (m < H) {
       rr_pair(N, r, m, p, q);
-      double c, sn;
       jacobi_rot(Ain[p + (int64_t)p * N], Ain[q + (int64_t)q * N], Ain[p + (int64_t)q * N], c, sn);
+    }
+    rc[side][t] = c;
+    rs[side][t] = sn;
+    rp[side][t] = p;
+    rq[side][t] = q;
+  }
+  __syncthreads();
+  const int ma = blockIdx.x * JT + tx, mb = blockIdx.y * JT + ty;
+  if (ma < H && mb < H) {
+    const int pa = rp[0][tx], qa = rq[0][tx], pb = rp[1][ty], qb = rq[1][ty];
+    const double ca = rc[0][tx], sa = rs[0][tx], cb = rc[1][ty], sb = rs[1][ty];
+    const double x_pp = Ain[pa + (int64_t)pb * N], x_pq = Ain[pa + (int64_t)qb * N];
+    const double x_qp = Ain[qa + (int64_t)pb * N], x_qq = Ain[qa + (int64_t)qb * N];
+    // columns: p' = c p - s q, q' = s p + c q
+    const double y_pp = cb * x_pp - sb * x_pq, y_pq = sb * x_pp + cb * x_pq;
+    const double y_qp = cb * x_qp - sb * x_qq, y_qq = sb * x_qp + cb * x_qq;
+    // rows
+    double z_pp = ca * y_pp - sa * y_qp, z_pq = ca * y_pq - sa * y_qq;
+    double z_qp = sa * y_pp + ca * y_qp, z_qq = sa * y_pq + ca * y_qq;
+    if (ma == mb) {  // the rotated pair itself: off-diagonal is zero by construction
+      z_pq = 0.0;
+      z_qp = 0.0;
+    }
+    Aout[pa + (int64_t)pb * N] = z_pp;
+    Aout[pa + (int64_t)qb * N] = z_pq;
+    Aout[qa + (int64_t)pb * N] = z_qp;
+    Aout[qa + (int64_t)qb * N] = z_qq;
+  }
+  // V <- V J for this block's 16 pairs, rows [lo, hi) of slice blockIdx.y (the pairs of a
+  // round are disjoint, so every (row, pair) element is independent of the others).
+  {
+    const int npair = min(JT, H - (int)blockIdx.x * JT);
+    const int lo = (int)((int64_t)N * blockIdx.y / gridDim.y), hi = (int)((int64_t)N * (blockIdx.y + 1) / gridDim.y);
+    const int rows = hi - lo;
+    for (int e = threadIdx.x; e < npair * rows; e += JT * JT) {
+      const int t = e / rows, row = lo + e % rows;
+      const int p = rp[0][t], q = rq[0][t];
+      const double c = rc[0][t], sn = rs[0][t];
       const double vp = V[row + (int64_t)p * N], vq = V[row + (int64_t)q * N];
       V[row + (int64_t)p * N] = c * vp - sn * vq;
       V[row + (int64_t)q * N] = sn * vp + c * vq;
@@ -423,30 +444,76 @@ cudaError_t jacobi_eig(double* G, double* Vout, int s, double* work, int* sweeps
   count_launch();
   jacobi_setup_kernel<<<std::max(1, std::min(1024, (N * N + 255) / 256)), 256, 0, st>>>(G, s, A0, Vout, N, done);
   NYS_CUDA_TRY(cudaGetLastError());
-  const int64_t total = (int64_t)(N / 2) * (N / 2) + (int64_t)N * (N / 2);
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (total + 255) / 256));
+  const int HT = (N / 2 + JT - 1) / JT;
+  const dim3 blocks(HT, HT);
   int sweeps = 0;
   int done_h = 0;
   const int kMaxSweeps = 30;
+  // One sweep = N - 1 round launches (ping-pong between A0 and A1; N - 1 is odd for even
+  // N, so after a sweep the roles of A0 and A1 swap).  Sweeps are captured once as two CUDA
+  // graphs (A0 -> A1 and A1 -> A0 starting buffers) and replayed, which removes the
+  // per-launch host overhead of ~N launches per sweep.
   double* cur = A0;
   double* nxt = A1;
+  cudaGraphExec_t sweep_exec[2] = {nullptr, nullptr};
+  const bool trace = std::getenv("NYS_TRACE") != nullptr;
+  auto t_cap = std::chrono::steady_clock::now();
+  bool graphs_ok = N > 2;
+  if (graphs_ok) {
+    cudaStream_t cap = nullptr;
+    graphs_ok = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess;
+    for (int gi = 0; gi < 2 && graphs_ok; ++gi) {
+      double* c = gi == 0 ? A0 : A1;
+      double* x = gi == 0 ? A1 : A0;
+      cudaGraph_t gr = nullptr;
+      count_launch_suspend(true);
+      graphs_ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+      for (int r = 0; r < N - 1 && graphs_ok; ++r) {
+        jacobi_round_kernel<<<blocks, JT * JT, 0, cap>>>(c, x, Vout, N, r, done);
+        std::swap(c, x);
+      }
+      graphs_ok = cudaStreamEndCapture(cap, &gr) == cudaSuccess && graphs_ok;
+      count_launch_suspend(false);
+      if (graphs_ok) graphs_ok = cudaGraphInstantiate(&sweep_exec[gi], gr, 0) == cudaSuccess;
+      if (gr) cudaGraphDestroy(gr);
+    }
+    if (cap) cudaStreamDestroy(cap);
+    cudaGetLastError();
+  }
+  if (trace) {
+    cudaStreamSynchronize(st);
+    std::fprintf(stderr, "[nys] jacobi capture+inst   %9.3f ms\n",
+                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_cap).count());
+  }
   for (; sweeps < kMaxSweeps; ++sweeps) {
+    auto t_sw = std::chrono::steady_clock::now();
     if (N <= 2 && sweeps > 0) break;
-    for (int r = 0; r < N - 1; ++r) {
-      count_launch();
-      jacobi_round_kernel<<<blocks, 256, 0, st>>>(cur, nxt, Vout, N, r, done);
-      std::swap(cur, nxt);
+    if (graphs_ok) {
+      NYS_CUDA_TRY(cudaGraphLaunch(sweep_exec[cur == A0 ? 0 : 1], st));
+      count_launch_add(N - 1);
+      if ((N - 1) % 2 == 1) std::swap(cur, nxt);
+    } else {
+      for (int r = 0; r < N - 1; ++r) {
+        count_launch();
+        jacobi_round_kernel<<<blocks, JT * JT, 0, st>>>(cur, nxt, Vout, N, r, done);
+        std::swap(cur, nxt);
+      }
     }
     NYS_CUDA_TRY(cudaGetLastError());
     count_launch();
-    jacobi_offnorm_kernel<<<1, 256, 0, st>>>(cur, N, 1e-28, done, offv);
+    jacobi_offnorm_kernel<<<1, 256, 0, st>>>(cur, N, 1e-24, done, offv);
     NYS_CUDA_TRY(cudaMemcpyAsync(&done_h, done, sizeof(int), cudaMemcpyDeviceToHost, st));
     NYS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (trace)
+      std::fprintf(stderr, "[nys] jacobi sweep %2d       %9.3f ms\n", sweeps,
+                   std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_sw).count());
     if (done_h) {
       ++sweeps;
       break;
     }
   }
+  for (auto& e : sweep_exec)
+    if (e) cudaGraphExecDestroy(e);
   // copy the diagonalised matrix back into G's storage layout (N x N in A0 slot)
   if (cur != A0) NYS_CUDA_TRY(cudaMemcpyAsync(A0, cur, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (sweeps_out) *sweeps_out = sweeps;
@@ -510,6 +577,115 @@ cudaError_t nystrom_finish(const double* B, int64_t d, int s, const double* Ad, 
 }
 
 // ------------------------------------------------------------------ sketch GEMMs
+// ------------------------------------------------------------------ fast float-compute sketch GEMM
+// C (M x N, column-major, ld ldc) = op(A) B for FP32 / BF16 storage of A, FP32 B:
+//   AW  (transA = 0): M = n rows of A, K = d:  op(A)[m][k] = A[m*ld + k]   (W = A Omega)
+//   ATW (transA = 1): M = d cols of A, K = n:  op(A)[m][k] = A[k*ld + m]   (Y_z = A^T W, rows kb..ke)
+// B is K x N column-major (ld ldb).  128 x 64 block tile, 256 threads, each thread an
+// 8 x 4 sub-tile with packed FP32 FMAs; the next K tile is prefetched into registers
+// while the current one is in shared memory (k-slow layout As[16][128], Bs[16][64]).
+constexpr int FBM = 128, FBN = 64, FBK = 16;
+
+template <int DT, bool TRANS>
+__global__ void __launch_bounds__(256) fgemm_kernel(const unsigned char* __restrict__ Araw, int64_t lda, int64_t M,
+                                                    int N, int64_t K, int64_t kchunk, const float* __restrict__ B,
+                                                    int64_t ldb, const double* __restrict__ Drow,
+                                                    float* __restrict__ Cout_base, int64_t ldc,
+                                                    int64_t slice_stride) {
+  __shared__ __align__(16) float As[2][FBK][FBM];
+  __shared__ __align__(16) float Bs[2][FBK][FBN];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t m0 = (int64_t)blockIdx.x * FBM;
+  const int n0 = blockIdx.y * FBN;
+  // split-K: slice z covers k in [z * kchunk, min(K, (z + 1) * kchunk)) and writes its own partial
+  const int64_t kb = (int64_t)blockIdx.z * kchunk;
+  const int64_t ke = min(K, kb + kchunk);
+  float* Cout = Cout_base + (int64_t)blockIdx.z * slice_stride;
+  // --- global -> register staging of one K tile
+  // A tile: 128 (m) x 16 (k) values; 8 values per thread.
+  // B tile: 16 (k) x 64 (n) values; 4 values per thread.
+  float ra[8], rb[4];
+  auto load_tile = [&](int64_t k0) {
+    if (!TRANS) {
+      // thread -> row m = tid >> 1, k half = (tid & 1) * 8: 8 consecutive k of one row
+      const int64_t m = m0 + (tid >> 1);
+      const int64_t k = k0 + (tid & 1) * 8;
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        ra[e] = (m < M && k + e < ke) ? load_elem<DT>(Araw, m * lda + k + e) : 0.f;
+    } else {
+      // thread -> k row = tid >> 4, 8 consecutive m at (tid & 15) * 8
+      const int64_t k = k0 + (tid >> 4);
+      const int64_t m = m0 + (tid & 15) * 8;
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        ra[e] = (k < ke && m + e < M) ? load_elem<DT>(Araw, k * lda + m + e) : 0.f;
+    }
+    // B: column n = tid >> 2, 4 consecutive k at (tid & 3) * 4
+    const int n = n0 + (tid >> 2);
+    const int64_t k = k0 + (tid & 3) * 4;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) rb[e] = (n < N && k + e < ke) ? B[(int64_t)n * ldb + k + e] : 0.f;
+  };
+  auto store_tile = [&](int buf) {
+    if (!TRANS) {
+      const int m = tid >> 1, kk = (tid & 1) * 8;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) As[buf][kk + e][m] = ra[e];
+    } else {
+      const int kk = tid >> 4, m = (tid & 15) * 8;
+      *reinterpret_cast<float4*>(&As[buf][kk][m]) = make_float4(ra[0], ra[1], ra[2], ra[3]);
+      *reinterpret_cast<float4*>(&As[buf][kk][m + 4]) = make_float4(ra[4], ra[5], ra[6], ra[7]);
+    }
+    const int n = tid >> 2, kk = (tid & 3) * 4;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) Bs[buf][kk + e][n] = rb[e];
+  };
+  float2 acc[8][2];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
+  int buf = 0;
+  load_tile(kb);
+  store_tile(0);
+  __syncthreads();
+  for (int64_t k0 = kb; k0 < ke; k0 += FBK) {
+    const bool more = k0 + FBK < ke;
+    if (more) load_tile(k0 + FBK);
+#pragma unroll
+    for (int kk = 0; kk < FBK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8 + 4]);
+      const float4 bv = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float2 b01 = make_float2(bv.x, bv.y), b23 = make_float2(bv.z, bv.w);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float2 ai = make_float2(av[i], av[i]);
+        acc[i][0] = __ffma2_rn(ai, b01, acc[i][0]);
+        acc[i][1] = __ffma2_rn(ai, b23, acc[i][1]);
+      }
+    }
+    if (more) {
+      store_tile(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t m = m0 + ty * 8 + i;
+    if (m >= M) continue;
+    const float dm = Drow ? (float)Drow[m] : 1.f;
+    const float v[4] = {acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx * 4 + j;
+      if (n < N) Cout[m + (int64_t)n * ldc] = dm * v[j];
+    }
+  }
+}
+
 // W (n x s, column-major, ld n, compute type C) = diag(D) A Om, Om d x s column-major (ld d).
 template <int DT>
 __global__ void __launch_bounds__(256) sketch_aw_kernel(const unsigned char* __restrict__ Araw, int64_t n,
@@ -687,14 +863,16 @@ cudaError_t sketch_atw(const nys_matrix* A, const void* W, int s, double* Y, voi
       break;
     case NYS_F32:
       count_launch();
-      sketch_atw_kernel<NYS_F32><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const float*)W, s, kc, (float*)work);
+      fgemm_kernel<NYS_F32, true><<<dim3((unsigned)((A->d + FBM - 1) / FBM), (s + FBN - 1) / FBN, nz), 256, 0, st>>>(
+          Ar, A->ld, A->d, s, A->n, kc, (const float*)W, A->n, nullptr, (float*)work, A->d, A->d * s);
       NYS_CUDA_TRY(cudaGetLastError());
       count_launch();
       sum_partials_to_f64_kernel<float><<<rb, 256, 0, st>>>((const float*)work, nz, len, Y);
       break;
     case NYS_BF16:
       count_launch();
-      sketch_atw_kernel<NYS_BF16><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const float*)W, s, kc, (float*)work);
+      fgemm_kernel<NYS_BF16, true><<<dim3((unsigned)((A->d + FBM - 1) / FBM), (s + FBN - 1) / FBN, nz), 256, 0, st>>>(
+          Ar, A->ld, A->d, s, A->n, kc, (const float*)W, A->n, nullptr, (float*)work, A->d, A->d * s);
       NYS_CUDA_TRY(cudaGetLastError());
       count_launch();
       sum_partials_to_f64_kernel<float><<<rb, 256, 0, st>>>((const float*)work, nz, len, Y);
@@ -718,10 +896,12 @@ cudaError_t sketch_atw_partials(const nys_matrix* A, const void* W, int s, void*
       sketch_atw_kernel<NYS_F64><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const double*)W, s, kc, (double*)work);
       break;
     case NYS_F32:
-      sketch_atw_kernel<NYS_F32><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const float*)W, s, kc, (float*)work);
+      fgemm_kernel<NYS_F32, true><<<dim3((unsigned)((A->d + FBM - 1) / FBM), (s + FBN - 1) / FBN, nz), 256, 0, st>>>(
+          Ar, A->ld, A->d, s, A->n, kc, (const float*)W, A->n, nullptr, (float*)work, A->d, A->d * s);
       break;
     case NYS_BF16:
-      sketch_atw_kernel<NYS_BF16><<<grid, 256, 0, st>>>(Ar, A->n, A->d, A->ld, (const float*)W, s, kc, (float*)work);
+      fgemm_kernel<NYS_BF16, true><<<dim3((unsigned)((A->d + FBM - 1) / FBM), (s + FBN - 1) / FBN, nz), 256, 0, st>>>(
+          Ar, A->ld, A->d, s, A->n, kc, (const float*)W, A->n, nullptr, (float*)work, A->d, A->d * s);
       break;
     default: return cudaErrorInvalidValue;
   }

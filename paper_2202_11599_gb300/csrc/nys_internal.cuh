@@ -10,6 +10,7 @@
 namespace nys {
 
 constexpr int kApassThreads = 512;       // threads of the fused A-pass CTA
+constexpr int kApassThreadsWide = 640;   // float-path CTA for narrow rows (<= 4 vectors per thread)
 constexpr int kVecThreads = 256;         // threads of the vector kernels
 
 // Row modes of the fused A-pass: u_i = phi(t_i), t = A p.
@@ -44,6 +45,9 @@ struct ApassPlan {
   size_t smem = 0;       // dynamic shared memory bytes
   int64_t dpad = 0;      // partial row stride (elements of compute type)
   bool fused = true;     // false -> two-pass fallback
+  int threads = 512;     // CTA size (float path: 512 or 640)
+  int vpt = 0;           // 16-byte column vectors owned per thread
+  bool onebar = false;   // float path, H-matvec modes: one barrier per step
 };
 
 bool apass_plan(const nys_matrix* A, ApassPlan* plan);
