@@ -114,6 +114,11 @@ nys_status sketch_panel(const nys_matrix* A, const double* D, double shift, cons
   PhaseTimer pt("sketch Y = H Omega", st);
   Pool pool(st);
   const int64_t n = A->n, d = A->d;
+  if (sketch_tc_supported(A)) {
+    NYS_CU(sketch_tc_bf16(A, D, Om, m, Y, st));
+    if (shift != 0.0) NYS_CU(axpy_panel(shift, Om, Y, d * m, st));
+    return NYS_OK;
+  }
   const size_t wbytes = sketch_atw_work_bytes(A, m);
   void* work = pool.alloc<unsigned char>(wbytes);
   if (A->dtype == NYS_F64) {

@@ -94,6 +94,10 @@ cudaError_t sketch_aw(const nys_matrix* A, const void* Omega, int s, const doubl
 cudaError_t sketch_atw(const nys_matrix* A, const void* W, int s, double* Y, void* work,
                        size_t work_bytes, cudaStream_t st);
 size_t sketch_atw_work_bytes(const nys_matrix* A, int s);
+// Y (d x m, col-major FP64) = A^T diag(D) A Om on the tensor cores (tcgen05), BF16 storage.
+bool sketch_tc_supported(const nys_matrix* A);
+cudaError_t sketch_tc_bf16(const nys_matrix* A, const double* D, const double* Om, int m, double* Y,
+                           cudaStream_t st);
 cudaError_t sketch_atw_partials(const nys_matrix* A, const void* W, int s, void* work, size_t work_bytes, int* nz_out,
                                 cudaStream_t st);
 // small dense GEMMs in compute type T (column-major)

@@ -536,7 +536,8 @@ namespace {
 
 
 __global__ void admm_begin_kernel(AdmmCtl* ctl, PcgState* st, double tol, int tol_mode, int maxit,
-                                  const int* __restrict__ fixed_dev, int hx_refresh, int refine) {
+                                  const int* __restrict__ fixed_dev, int hx_refresh, int refine,
+                                  cudaGraphConditionalHandle hx_cond, long long hx_nodes) {
   const int k = ctl->k;
   st->wy = 0.0;
   st->w2 = 0.0;
@@ -558,6 +559,9 @@ __global__ void admm_begin_kernel(AdmmCtl* ctl, PcgState* st, double tol, int to
   // when hx_refresh == 0 (as printed) or every hx_refresh iterations
   if (refine || k == 0) ctl->hx_skip = 1;
   else ctl->hx_skip = (hx_refresh == 0 || k % hx_refresh == 0) ? 0 : 1;
+  // the recompute pass sits in a conditional IF node: skipped iterations launch nothing
+  if (!ctl->hx_skip) ctl->nodes += hx_nodes;
+  cudaGraphSetConditional(hx_cond, ctl->hx_skip ? 0u : 1u);
 }
 
 // r = q + rho (z - u); refined step: r = rho (z - u - x) - yres, and the PCG starts at 0.
@@ -684,7 +688,8 @@ __global__ void ws_features_kernel(int s, const double* proj, double rho, const 
 template <typename C>
 __global__ void ws_apply_kernel(int64_t d, int s, const C* __restrict__ U, const float* __restrict__ c,
                                 const double* __restrict__ uxp, const double* rnorm, double rho, C* __restrict__ xc,
-                                C* __restrict__ xprev, AdmmCtl* ctl) {
+                                C* __restrict__ xprev, AdmmCtl* ctl, cudaGraphConditionalHandle hx_cond,
+                                long long hx_nodes) {
   const double scale = *rnorm / rho;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
@@ -693,7 +698,12 @@ __global__ void ws_apply_kernel(int64_t d, int s, const C* __restrict__ U, const
     if (xprev) xprev[j] = x0;
     xc[j] = (C)((double)x0 + acc);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->hx_skip = 0;
+  // x moved off x_prev: the tracked (H + rho I) x is stale, open the recompute node
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (ctl->hx_skip) ctl->nodes += hx_nodes;
+    ctl->hx_skip = 0;
+    cudaGraphSetConditional(hx_cond, 1u);
+  }
 }
 
 template <typename C>
@@ -776,6 +786,8 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   G_OK(cudaGraphAddNode(&n_admm, graph, nullptr, nullptr, 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   G_OK(cudaGraphConditionalHandleCreate(&h_pcg, body, 0u, 0u));
+  cudaGraphConditionalHandle h_hx;
+  G_OK(cudaGraphConditionalHandleCreate(&h_hx, body, 0u, 0u));
 
   ApassArgs aa;
   aa.A = g.pb.A->data;
@@ -796,7 +808,8 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   // ---- segment 1: begin, (exact residual pass), right-hand side, PCG init
   count_launch_suspend(true);
   G_OK(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  admm_begin_kernel<<<1, 1, 0, cap>>>(ctl, st, g.tol, g.tol_mode, g.maxit, fixed_dev, g.hx_refresh, refine);
+  admm_begin_kernel<<<1, 1, 0, cap>>>(ctl, st, g.tol, g.tol_mode, g.maxit, fixed_dev, g.hx_refresh, refine, h_hx,
+                                      2);
   ++seg_nodes;
   if (refine) {
     ApassArgs ar;
@@ -843,18 +856,38 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
       if (!pool.ok()) return NYS_ENOMEM;
       ws_proj_kernel<C><<<s, kVecThreads, 0, cap>>>(d, s, U, xc, (const C*)nullptr, uxp);
       G_OK(mlp_forward_dev(g.warm, feat, 1, mlp_buf, mlp_buf + 1024, mlp_buf + 2048, mlp_buf + 3072, cout, cap));
-      ws_apply_kernel<C><<<nbz, kVecThreads, 0, cap>>>(d, s, U, cout, uxp, rnorm, g.rho, xc, xprev, ctl);
+      ws_apply_kernel<C><<<nbz, kVecThreads, 0, cap>>>(d, s, U, cout, uxp, rnorm, g.rho, xc, xprev, ctl, h_hx, 2);
       seg_nodes += 5;
     } else {
       ws_copy_kernel<C><<<nbz, kVecThreads, 0, cap>>>(d, xc, xprev);
       ++seg_nodes;
     }
   }
-  aa.p = xc;
-  aa.skip = &ctl->hx_skip;
-  G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, true));
-  G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho, hx, nullptr, 0, cap));
-  seg_nodes += 2;
+  // (H + rho I) x recompute: an IF node that admm_begin_kernel opens every hx_refresh
+  // iterations (counted there when it runs)
+  {
+    cudaStreamCaptureStatus cst1;
+    const cudaGraphNode_t* deps1 = nullptr;
+    size_t ndeps1 = 0;
+    G_OK(cudaStreamGetCaptureInfo(cap, &cst1, nullptr, nullptr, &deps1, nullptr, &ndeps1));
+    std::vector<cudaGraphNode_t> leaf1(deps1, deps1 + ndeps1);
+    G_OK(cudaStreamEndCapture(cap, &body));
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = h_hx;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t n_hx;
+    G_OK(cudaGraphAddNode(&n_hx, body, leaf1.data(), nullptr, leaf1.size(), &ip));
+    cudaGraph_t hbody = ip.conditional.phGraph_out[0];
+    G_OK(cudaStreamBeginCaptureToGraph(cap, hbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    aa.p = xc;
+    aa.skip = nullptr;
+    G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, true));
+    G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho, hx, nullptr, 0, cap));
+    G_OK(cudaStreamEndCapture(cap, &hbody));
+    G_OK(cudaStreamBeginCaptureToGraph(cap, body, &n_hx, nullptr, 1, cudaStreamCaptureModeRelaxed));
+  }
   pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, cap>>>(1, d, chunk, xc, w, rc, hx, p, U, s, pv_part, nbr,
                                                           wy_part, nb5, part_w2, part_r2, part_g, st, (C*)nullptr);
   pcg_scalar_kernel<C><<<1, kVecThreads, 0, cap>>>(1, nb3, part_w2, part_r2, part_g, s, cvec, gs, pv_part, nbr,

@@ -1,0 +1,524 @@
+// Sketch GEMMs of the Nystrom preconditioner (App. B: Y = H Omega with H = A^T D A) on
+// the 5th-generation tensor cores, for BF16 storage of A:
+//
+//   W  = diag(D) A Omega        (n x s)   GEMM 1: M = n (rows of A), N = s, K = d
+//   Y  = A^T W                  (d x s)   GEMM 2: M = d, N = s, K = n (split over K)
+//
+// The FP32 operand of each product (Omega, then W) is written as the sum of three BF16
+// terms (x = t1 + t2 + t3 holds exactly for every float x: each term takes the next 8
+// significant bits), and A is BF16 already, so every product a * t_k is exact and the
+// tensor core accumulates them in FP32: the result is an FP32-class GEMM at tensor-core
+// rates (3 MMAs per K step instead of 1).
+//
+// Kernel design (one CTA = one 128-row tile of the output, the full N = s <= 256 in TMEM):
+//   * both operands are K-major: GEMM 1 reads the rows of A directly, GEMM 2 reads a
+//     transposed copy of A made once per sketch (2 GB of the 280 GB HBM for the paper's
+//     largest single-GPU problem); W is written by GEMM 1 already in the K-major layout
+//     GEMM 2 wants;
+//   * tiles are staged by cp.async (16-byte chunks, zero-filled outside the matrix) into
+//     the canonical no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix;
+//     core matrices 128 B apart along K, 512 B apart along M/N), 4 stages of 32 K;
+//   * one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32 in TMEM, M = 128,
+//     N = s rounded up to 16) and tcgen05.commit to the stage's mbarrier, which frees the
+//     stage for the next cp.async; all waits are bounded;
+//   * the epilogue reads TMEM with tcgen05.ld (warp w reads lanes 32 (w % 4) .. + 31):
+//     GEMM 1 scales row i by D_i and writes the three BF16 terms of W; GEMM 2 writes its
+//     K-slice's FP32 partial, and a final kernel sums the slices in a fixed order in FP64.
+#include <cuda_bf16.h>
+
+#include "device_util.cuh"
+#include "nys_internal.cuh"
+#include "solver.cuh"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+
+namespace nys {
+namespace {
+
+constexpr int TC_BM = 128;      // output rows per CTA = TMEM lanes
+constexpr int TC_BK = 32;       // K per stage (two MMA K-steps of 16)
+constexpr int TC_STAGES = 4;
+constexpr int TC_THREADS = 256;
+constexpr int TC_TERMS = 3;     // FP32 operand = t1 + t2 + t3 (BF16)
+constexpr int TC_NMAX = 256;    // MMA N limit; TMEM columns allocated
+constexpr uint32_t TC_LBO = 128;                 // K-direction core-matrix stride (bytes)
+constexpr uint32_t TC_SBO = (TC_BK / 8) * 128;   // 8-row-group stride (bytes)
+
+struct TcArgs {
+  const uint16_t* A;     // row-major [Mrows][lda] BF16, K contiguous
+  int64_t lda, Mrows, Kvalid;
+  const uint16_t* B;     // [TERMS][NP][ldb] BF16, K contiguous, zero outside the data
+  int64_t ldb, bterm;
+  int NP;                // MMA N (multiple of 16, <= 256)
+  int64_t ktiles;        // K tiles of TC_BK in the whole product
+  int64_t kslice;        // K tiles per split-K slice (blockIdx.y)
+  // epilogue 0: Wt[t][c][i] = BF16 terms of D_i * acc(i, c), rows i < wrows (zero for i >= Mrows)
+  const double* D;
+  uint16_t* Wt;
+  int64_t ldw, wterm, wrows;
+  // epilogue 1: P[z][c][j] = acc(j, c) (FP32, slice z = blockIdx.y)
+  float* P;
+  int64_t ldp;
+  uint32_t desc_swap;    // 0: LBO along K, SBO along M/N (the canonical K-major form)
+  int* status;
+};
+
+// ---- PTX wrappers (tcgen05, cp.async, proxy fences)
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading (K) and stride
+// (M/N) byte offsets, all in 16-byte units; bits 46-48 hold the fixed value 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9 and
+// 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t mma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// 32 lanes x 8 columns of 32 bits: thread l of the warp gets lane (base + l), 8 columns.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr)
+               : "memory");
+}
+// the registers are operands so that no use of them is scheduled before the wait
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&v)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float bf16_val(uint16_t h) { return __uint_as_float(((uint32_t)h) << 16); }
+// x = t[0] + t[1] + t[2] (+ a remainder below 2^-24 |x|)
+__device__ __forceinline__ void split3(float x, uint16_t (&t)[3]) {
+  t[0] = bf16_bits(x);
+  const float r1 = x - bf16_val(t[0]);
+  t[1] = bf16_bits(r1);
+  const float r2 = r1 - bf16_val(t[1]);
+  t[2] = bf16_bits(r2);
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mma_bar[TC_STAGES];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * TC_BM;
+  const int64_t kt0 = (int64_t)blockIdx.y * a.kslice;
+  const int64_t kt1 = min(a.ktiles, kt0 + a.kslice);
+  const int nkt = (int)max((int64_t)0, kt1 - kt0);
+  const uint32_t a_bytes = TC_BM * TC_BK * 2;
+  const uint32_t b_bytes = (uint32_t)a.NP * TC_BK * 2;
+  const uint32_t stage_bytes = a_bytes + TC_TERMS * b_bytes;
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t lbo = a.desc_swap ? TC_SBO : TC_LBO, sbo = a.desc_swap ? TC_LBO : TC_SBO;
+  const uint32_t idesc = mma_idesc_bf16(TC_BM, a.NP);
+
+  if (warp == 0) {
+    tmem_alloc(&tmem_slot, TC_NMAX);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) mbar_init(&mma_bar[s], 1);
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  // Stage layout: chunk q (16 bytes = 8 elements of one row) of a tile with 4 chunks per
+  // row sits at byte 16 q, with q = 32 g + 8 c + r8 for row 8 g + r8 and K chunk c: that is
+  // the core-matrix layout with LBO = 128 (along K) and SBO = 512 (along rows).
+  auto load_stage = [&](int ktl, int stage) {
+    const int64_t k0 = (kt0 + ktl) * TC_BK;
+    const uint32_t st = sbase + (uint32_t)stage * stage_bytes;
+    for (int q = tid; q < TC_BM * 4; q += TC_THREADS) {
+      const int r8 = q & 7, c = (q >> 3) & 3, g = q >> 5;
+      const int64_t row = m0 + g * 8 + r8, k = k0 + c * 8;
+      uint32_t bytes = 0;
+      const uint16_t* src = a.A;
+      if (row < a.Mrows && k < a.Kvalid) {
+        bytes = (uint32_t)min((int64_t)16, (a.Kvalid - k) * 2);
+        src = a.A + row * a.lda + k;
+      }
+      cp_async16(st + (uint32_t)q * 16u, src, bytes);
+    }
+    const int per_term = a.NP * 4;
+    for (int q = tid; q < TC_TERMS * per_term; q += TC_THREADS) {
+      const int t = q / per_term, qq = q - t * per_term;
+      const int r8 = qq & 7, c = (qq >> 3) & 3, g = qq >> 5;
+      const uint16_t* src = a.B + t * a.bterm + (int64_t)(g * 8 + r8) * a.ldb + k0 + c * 8;
+      cp_async16(st + a_bytes + (uint32_t)t * b_bytes + (uint32_t)qq * 16u, src, 16u);
+    }
+  };
+
+  bool ok = true;
+  for (int s = 0; s < TC_STAGES - 1; ++s) {
+    if (s < nkt) load_stage(s, s);
+    cp_async_commit();
+  }
+  for (int kt = 0; kt < nkt; ++kt) {
+    const int stage = kt % TC_STAGES;
+    cp_async_wait<TC_STAGES - 2>();  // this thread's copies of k-tile kt have landed
+    fence_proxy_async_smem();        // make them visible to the tensor core (async proxy)
+    ok = __syncthreads_and(ok);
+    if (tid == 0 && ok) {
+      tc_fence_after();
+      const uint32_t st = sbase + (uint32_t)stage * stage_bytes;
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 16; ++kk) {
+        const uint64_t ad = smem_desc(st + kk * 256u, lbo, sbo);
+#pragma unroll
+        for (int t = 0; t < TC_TERMS; ++t) {
+          const uint64_t bd = smem_desc(st + a_bytes + (uint32_t)t * b_bytes + kk * 256u, lbo, sbo);
+          mma_bf16(tmem, ad, bd, idesc, (kt | kk | t) != 0 ? 1u : 0u);
+        }
+      }
+      mma_commit(&mma_bar[stage]);
+    }
+    // refill the stage of k-tile kt - 1 with k-tile kt + STAGES - 1 once the MMAs of kt - 1
+    // are done reading it (those of kt are queued behind them, so the tensor core stays busy)
+    const int kn = kt + TC_STAGES - 1;
+    if (kn < nkt) {
+      const int sn = kn % TC_STAGES;
+      if (kn >= TC_STAGES) ok = ok && mbar_wait_bounded(&mma_bar[sn], (uint32_t)(((kn - TC_STAGES) / TC_STAGES) & 1));
+      if (ok) load_stage(kn, sn);
+    }
+    cp_async_commit();
+  }
+  cp_async_wait<0>();
+  // the last commit tracks every MMA this CTA issued
+  if (nkt > 0) {
+    const int last = nkt - 1;
+    if (ok) ok = mbar_wait_bounded(&mma_bar[last % TC_STAGES], (uint32_t)((last / TC_STAGES) & 1));
+  }
+  ok = __syncthreads_and(ok);
+  tc_fence_after();
+
+  if (ok) {
+    const int quad = warp & 3;
+    const int64_t row = m0 + 32 * quad + lane;
+    const int half = a.NP / 2;
+    const int cb = (warp >> 2) * half;
+    const uint32_t trow = tmem + ((uint32_t)(32 * quad) << 16);
+    double dr = 1.0;
+    if (EPI == 0 && a.D && row < a.Mrows) dr = a.D[row];
+    for (int c0 = cb; c0 < cb + half; c0 += 8) {
+      uint32_t v[8];
+      tmem_ld8(trow + (uint32_t)c0, v);
+      tmem_ld_wait(v);
+      if (nkt == 0) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = 0u;
+      }
+      if (EPI == 0) {
+        if (row < a.wrows) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const float x = row < a.Mrows ? (float)(dr * (double)__uint_as_float(v[e])) : 0.f;
+            uint16_t t3[3];
+            split3(x, t3);
+#pragma unroll
+            for (int t = 0; t < TC_TERMS; ++t) a.Wt[t * a.wterm + (int64_t)(c0 + e) * a.ldw + row] = t3[t];
+          }
+        }
+      } else {
+        if (row < a.Mrows) {
+          float* P = a.P + (int64_t)blockIdx.y * a.NP * a.ldp;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) P[(int64_t)(c0 + e) * a.ldp + row] = __uint_as_float(v[e]);
+        }
+      }
+    }
+  } else if (tid == 0) {
+    // a wait gave up: report, give the tensor core a bounded last chance to finish
+    atomicExch(a.status, (int)NYS_ETIMEOUT);
+    if (nkt > 0) (void)mbar_wait_bounded(&mma_bar[(nkt - 1) % TC_STAGES], (uint32_t)(((nkt - 1) / TC_STAGES) & 1));
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, TC_NMAX);
+}
+
+// Omega terms: Ot[t][c][k] (c < NP, k < KP) = t-th BF16 term of float(Om[k + (c0 + c) d]),
+// zero outside c < mp, k < d.
+__global__ void split_omega_kernel(const double* __restrict__ Om, int64_t d, int c0, int mp, int NP, int64_t KP,
+                                   uint16_t* __restrict__ Ot) {
+  const int64_t total = (int64_t)NP * KP;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / KP);
+    const int64_t k = idx - (int64_t)c * KP;
+    float x = 0.f;
+    if (c < mp && k < d) x = (float)Om[k + (int64_t)(c0 + c) * d];
+    uint16_t t3[3];
+    split3(x, t3);
+#pragma unroll
+    for (int t = 0; t < TC_TERMS; ++t) Ot[t * total + idx] = t3[t];
+  }
+}
+
+// At[j][i] = A[i][j] (BF16), j < d, i < nP (zero for i >= n).  64 x 64 tiles.
+__global__ void __launch_bounds__(256) transpose_bf16_kernel(const uint16_t* __restrict__ A, int64_t n, int64_t d,
+                                                             int64_t lda, uint16_t* __restrict__ At, int64_t nP) {
+  __shared__ uint16_t tile[64][66];
+  const int64_t i0 = (int64_t)blockIdx.x * 64, j0 = (int64_t)blockIdx.y * 64;
+  const int tid = threadIdx.x;
+  {
+    const int r = tid >> 2, cq = (tid & 3) * 16;  // row i0 + r, columns j0 + cq .. + 15
+    const int64_t i = i0 + r, j = j0 + cq;
+    uint16_t v[16];
+    if (i < n && j + 16 <= d) {
+      const uint4* src = reinterpret_cast<const uint4*>(A + i * lda + j);
+      const uint4 x0 = src[0], x1 = src[1];
+      const uint32_t w[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        v[2 * e] = (uint16_t)(w[e] & 0xffffu);
+        v[2 * e + 1] = (uint16_t)(w[e] >> 16);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 16; ++e) v[e] = (i < n && j + e < d) ? A[i * lda + j + e] : (uint16_t)0;
+    }
+#pragma unroll
+    for (int e = 0; e < 16; ++e) tile[r][cq + e] = v[e];
+  }
+  __syncthreads();
+  {
+    const int r = tid >> 2, cq = (tid & 3) * 16;  // output row j0 + r, columns i0 + cq .. + 15
+    const int64_t j = j0 + r, i = i0 + cq;
+    if (j < d && i < nP) {
+      uint32_t w[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) w[e] = (uint32_t)tile[cq + 2 * e][r] | ((uint32_t)tile[cq + 2 * e + 1][r] << 16);
+      if (i + 16 <= nP) {
+        uint4* dst = reinterpret_cast<uint4*>(At + j * nP + i);
+        dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+      } else {
+        for (int e = 0; e < 16 && i + e < nP; ++e) At[j * nP + i + e] = tile[cq + e][r];
+      }
+    }
+  }
+}
+
+// Y[j + (c0 + c) d] = sum_z P[z][c][j] (fixed order, FP64), c < mp.
+__global__ void sum_slices_kernel(const float* __restrict__ P, int Z, int NP, int64_t d, int c0, int mp,
+                                  double* __restrict__ Y) {
+  const int64_t total = (int64_t)mp * d;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / d);
+    const int64_t j = idx - (int64_t)c * d;
+    double s = 0.0;
+    for (int z = 0; z < Z; ++z) s += (double)P[((int64_t)z * NP + c) * d + j];
+    Y[j + (int64_t)(c0 + c) * d] = s;
+  }
+}
+
+int sm_count_tc() {
+  int dev = 0, c = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+  return c > 0 ? c : 1;
+}
+
+// split-K slices for GEMM 2: the count (<= 32, each slice >= 16 K tiles) whose CTA count
+// fills the last wave best.
+int pick_slices(int64_t mtiles, int64_t ktiles, int sms) {
+  int best = 1;
+  double best_fill = 0.0;
+  for (int z = 1; z <= 32; ++z) {
+    if (z > 1 && ktiles / z < 16) break;
+    const int64_t units = mtiles * z;
+    const int64_t waves = (units + sms - 1) / sms;
+    const double fill = (double)units / (double)(waves * sms);
+    if (fill > best_fill + 1e-9) {
+      best_fill = fill;
+      best = z;
+    }
+  }
+  return best;
+}
+
+template <int EPI>
+cudaError_t launch_tc(const TcArgs& a, dim3 grid, cudaStream_t st) {
+  const size_t smem = (size_t)TC_STAGES * (TC_BM * TC_BK * 2 + (size_t)TC_TERMS * a.NP * TC_BK * 2);
+  static bool attr = false;
+  if (!attr) {
+    const size_t max_smem = (size_t)TC_STAGES * (TC_BM * TC_BK * 2 + (size_t)TC_TERMS * TC_NMAX * TC_BK * 2);
+    NYS_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)max_smem));
+    attr = true;
+  }
+  count_launch();
+  sketch_tc_kernel<EPI><<<grid, TC_THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool sketch_tc_supported(const nys_matrix* A) {
+  if (A->dtype != NYS_BF16) return false;
+  if (const char* env = std::getenv("NYS_SKETCH_TC")) return std::atoi(env) != 0;
+  return true;
+}
+
+cudaError_t sketch_tc_bf16(const nys_matrix* A, const double* D, const double* Om, int m, double* Y,
+                           cudaStream_t st) {
+  if (A->dtype != NYS_BF16 || m <= 0) return cudaErrorInvalidValue;
+  const int64_t n = A->n, d = A->d;
+  const int64_t nP = (n + TC_BK - 1) / TC_BK * TC_BK;
+  const int64_t dP = (d + TC_BK - 1) / TC_BK * TC_BK;
+  const int NPmax = std::min(TC_NMAX, (m + 15) / 16 * 16);
+  const uint32_t swap = std::getenv("NYS_TC_DESC_SWAP") ? (uint32_t)std::atoi(std::getenv("NYS_TC_DESC_SWAP")) : 0u;
+  const int sms = sm_count_tc();
+  const int64_t mt2 = (d + TC_BM - 1) / TC_BM;
+  const int64_t kt2 = nP / TC_BK;
+  const int Z = pick_slices(mt2, kt2, sms);
+  const int64_t kslice2 = (kt2 + Z - 1) / Z;
+  const int Zeff = (int)((kt2 + kslice2 - 1) / kslice2);
+
+  // NYS_TRACE: per-kernel device times of this sketch on stderr
+  const bool trace = std::getenv("NYS_TRACE") != nullptr;
+  cudaEvent_t ev[8] = {};
+  int nev = 0;
+  auto mark = [&]() {
+    if (!trace || nev >= 8) return;
+    if (cudaEventCreate(&ev[nev]) == cudaSuccess) cudaEventRecord(ev[nev], st);
+    ++nev;
+  };
+  mark();
+  Pool pool(st);
+  uint16_t* Ot = pool.alloc<uint16_t>((size_t)TC_TERMS * NPmax * dP);
+  uint16_t* Wt = pool.alloc<uint16_t>((size_t)TC_TERMS * NPmax * nP);
+  uint16_t* At = pool.alloc<uint16_t>((size_t)d * nP);
+  float* P = pool.alloc<float>((size_t)Zeff * NPmax * d);
+  int* status = pool.alloc<int>(1);
+  if (!pool.ok()) return cudaErrorMemoryAllocation;
+  NYS_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+  mark();
+
+  count_launch();
+  transpose_bf16_kernel<<<dim3((unsigned)(nP + 63) / 64, (unsigned)(d + 63) / 64), 256, 0, st>>>(
+      reinterpret_cast<const uint16_t*>(A->data), n, d, A->ld, At, nP);
+  NYS_CUDA_TRY(cudaGetLastError());
+  mark();
+
+  for (int c0 = 0; c0 < m; c0 += TC_NMAX) {
+    const int mp = std::min(TC_NMAX, m - c0);
+    const int NP = (mp + 15) / 16 * 16;
+    count_launch();
+    split_omega_kernel<<<(unsigned)std::min<int64_t>(4096, ((int64_t)NP * dP + 255) / 256), 256, 0, st>>>(
+        Om, d, c0, mp, NP, dP, Ot);
+    NYS_CUDA_TRY(cudaGetLastError());
+    if (c0 == 0) mark();
+
+    TcArgs g1 = {};
+    g1.A = reinterpret_cast<const uint16_t*>(A->data);
+    g1.lda = A->ld;
+    g1.Mrows = n;
+    g1.Kvalid = d;
+    g1.B = Ot;
+    g1.ldb = dP;
+    g1.bterm = (int64_t)NP * dP;
+    g1.NP = NP;
+    g1.ktiles = dP / TC_BK;
+    g1.kslice = g1.ktiles;
+    g1.D = D;
+    g1.Wt = Wt;
+    g1.ldw = nP;
+    g1.wterm = (int64_t)NP * nP;
+    g1.wrows = nP;
+    g1.desc_swap = swap;
+    g1.status = status;
+    NYS_CUDA_TRY(launch_tc<0>(g1, dim3((unsigned)((n + TC_BM - 1) / TC_BM), 1), st));
+    if (c0 == 0) mark();
+
+    TcArgs g2 = {};
+    g2.A = At;
+    g2.lda = nP;
+    g2.Mrows = d;
+    g2.Kvalid = nP;
+    g2.B = Wt;
+    g2.ldb = nP;
+    g2.bterm = (int64_t)NP * nP;
+    g2.NP = NP;
+    g2.ktiles = kt2;
+    g2.kslice = kslice2;
+    g2.P = P;
+    g2.ldp = d;
+    g2.desc_swap = swap;
+    g2.status = status;
+    NYS_CUDA_TRY(launch_tc<1>(g2, dim3((unsigned)mt2, (unsigned)Zeff), st));
+    if (c0 == 0) mark();
+
+    count_launch();
+    sum_slices_kernel<<<(unsigned)std::min<int64_t>(4096, ((int64_t)mp * d + 255) / 256), 256, 0, st>>>(
+        P, Zeff, NP, d, c0, mp, Y);
+    NYS_CUDA_TRY(cudaGetLastError());
+    if (c0 == 0) mark();
+  }
+  if (trace) {
+    cudaStreamSynchronize(st);
+    static const char* names[] = {"alloc", "transpose A", "split Omega", "GEMM1 W = D A Om", "GEMM2 A^T W",
+                                  "sum slices"};
+    for (int i = 1; i < nev && i < 7; ++i) {
+      float ms = 0.f;
+      if (ev[i - 1] && ev[i]) cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
+      std::fprintf(stderr, "[nys]   tc %-18s %8.3f ms\n", names[i - 1], ms);
+    }
+    std::fprintf(stderr, "[nys]   tc split-K slices %d, NP %d\n", Zeff, NPmax);
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  int status_h = 0;
+  NYS_CUDA_TRY(cudaMemcpyAsync(&status_h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NYS_CUDA_TRY(cudaStreamSynchronize(st));
+  return status_h ? cudaErrorLaunchTimeout : cudaSuccess;
+}
+
+}  // namespace nys
