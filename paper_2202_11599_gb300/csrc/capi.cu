@@ -383,7 +383,10 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
   PrecondView view;
   C* cbuf = pool.alloc<C>(rank);
   if (!pool.ok()) return NYS_ENOMEM;
-  NYS_TRY(precond_view<C>(&P, rho, cbuf, st, &view));
+  {
+    PhaseTimer pt("precond view", st);
+    NYS_TRY(precond_view<C>(&P, rho, cbuf, st, &view));
+  }
 
   double* x = pool.alloc<double>(d);
   double* z = pool.alloc<double>(d);
@@ -409,8 +412,11 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
   NYS_CU(cudaMemsetAsync(stop, 0, sizeof(int), st));
 
   // q = A^T b
-  NYS_TRY(aux_pass(A, MODE_CONST, nullptr, b, nullptr, nullptr, ytmp, nullptr, st));
-  NYS_TRY(to_f64(A, ytmp, q, d, st));
+  {
+    PhaseTimer pt("q = A^T b", st);
+    NYS_TRY(aux_pass(A, MODE_CONST, nullptr, b, nullptr, nullptr, ytmp, nullptr, st));
+    NYS_TRY(to_f64(A, ytmp, q, d, st));
+  }
 
   PcgProblem pb;
   pb.A = Ain;

@@ -11,7 +11,10 @@
 #include "solver.cuh"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 
 namespace nys {
 
@@ -35,6 +38,41 @@ __device__ __forceinline__ double block_fixed_sum(const double* a, int n, double
   return r;
 }
 
+// Same sums reading through L2 (__ldcg): for partials written by other blocks of the
+// running kernel, which this block's L1 may not see.
+__device__ __forceinline__ double warp_fixed_sum_cg(const double* a, int n) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s += __ldcg(a + i);
+  return warp_sum(s);
+}
+__device__ __forceinline__ double block_fixed_sum_cg(const double* a, int n, double* slot) {
+  if (threadIdx.x < 32) {
+    const double s = warp_fixed_sum_cg(a, n);
+    if (threadIdx.x == 0) *slot = s;
+  }
+  __syncthreads();
+  const double r = *slot;
+  __syncthreads();
+  return r;
+}
+
+// Last-block election for a kernel that ends with a grid-wide scalar step: every block
+// calls it after writing its partials; it returns true (to every thread) only in the block
+// that arrived last, which then sees the other blocks' writes, and resets the ticket for
+// the next launch.  This replaces a separate one-block kernel launch.
+__device__ __forceinline__ bool last_block_done(unsigned int* ticket) {
+  __shared__ unsigned int prev;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) prev = atomicAdd(ticket, 1u);
+  __syncthreads();
+  if (prev != gridDim.x - 1) return false;
+  __threadfence();
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
 __global__ void pcg_reset_kernel(PcgState* st, double tol, int tol_abs, int maxit, int fixed,
                                  const double* dev_tol) {
   st->wy = 0.0;
@@ -48,87 +86,22 @@ __global__ void pcg_reset_kernel(PcgState* st, double tol, int tol_abs, int maxi
   st->status = 0;
   st->maxit = maxit;
   st->fixed = fixed;
+  st->ticket[0] = 0u;
+  st->ticket[1] = 0u;
 }
 
-// K3: init  -> w = r - v (v = (H + rho I) x0, or x0 = 0), partial ||r||^2;
-//     step  -> alpha = w^T y / p^T v, x += alpha p, w -= alpha v.
-// Both: partial ||w||^2 and partial U^T w over this block's chunk of w.
+// K4 body (run by the last block of K3): ||w||^2, stop test, iteration count,
+// g_i = c_i (U^T w)_i.
 template <typename C>
-__global__ void __launch_bounds__(kVecThreads) pcg_update_kernel(int init, int64_t d, int chunk, C* __restrict__ x,
-                                                                 C* __restrict__ w, const C* __restrict__ r,
-                                                                 const C* __restrict__ v, const C* __restrict__ p,
-                                                                 const C* __restrict__ U, int s,
-                                                                 const double* __restrict__ pv_part, int npv,
-                                                                 const double* __restrict__ wy_part, int nwy,
-                                                                 double* part_w2, double* part_r2, double* part_g,
-                                                                 const PcgState* st, C* __restrict__ hx) {
-  if (st->done) return;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  C* wch = reinterpret_cast<C*>(sm_raw);
-  __shared__ double sh[kVecThreads / 32];
+__device__ void pcg_scalar_body(int init, int nb3, const double* part_w2, const double* part_r2,
+                                const double* part_g, int s, const C* __restrict__ cvec, C* __restrict__ gs,
+                                const double* pv_part, int npv, const double* wy_part, int nwy, PcgState* st,
+                                cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ double slot;
-  const int64_t j0 = (int64_t)blockIdx.x * chunk;
-  const int64_t j1 = min(d, j0 + chunk);
-  double alpha = 0.0;
-  if (!init) {
-    const double pv = block_fixed_sum(pv_part, npv, &slot);
-    const double wy = block_fixed_sum(wy_part, nwy, &slot);
-    if (!(pv > 0.0) || !isfinite(pv)) return;  // breakdown: flagged by the scalar kernel
-    alpha = wy / pv;
-  }
-  const C a = (C)alpha;
-  double lw2 = 0.0, lr2 = 0.0;
-  for (int64_t j = j0 + threadIdx.x; j < j1; j += kVecThreads) {
-    C wj;
-    if (init) {
-      const C rj = r[j];
-      wj = v ? rj - v[j] : rj;
-      lr2 += (double)rj * (double)rj;
-    } else {
-      const C vj = v[j];
-      x[j] = fma(a, p[j], x[j]);
-      wj = fma(-a, vj, w[j]);
-      if (hx) hx[j] = fma(a, vj, hx[j]);  // (H + rho I) x follows x: x += a p  =>  += a v
-    }
-    w[j] = wj;
-    wch[j - j0] = wj;
-    lw2 += (double)wj * (double)wj;
-  }
-  const double tw2 = block_sum<kVecThreads>(lw2, sh);
-  const double tr2 = block_sum<kVecThreads>(lr2, sh);
-  if (threadIdx.x == 0) {
-    part_w2[blockIdx.x] = tw2;
-    if (init) part_r2[blockIdx.x] = tr2;
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int len = (int)(j1 - j0);
-  for (int i = warp; i < s; i += kVecThreads / 32) {
-    const C* Ui = U + (int64_t)i * d + j0;
-    C acc = C(0);
-    for (int jj = lane; jj < len; jj += 32) acc = fma(Ui[jj], wch[jj], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) part_g[(int64_t)blockIdx.x * s + i] = (double)acc;
-  }
-}
-
-// K4 (one block): ||w||^2, stop test, iteration count, g_i = c_i (U^T w)_i.
-template <typename C>
-__global__ void __launch_bounds__(kVecThreads) pcg_scalar_kernel(int init, int nb3, const double* part_w2,
-                                                                 const double* part_r2, const double* part_g, int s,
-                                                                 const C* __restrict__ cvec, C* __restrict__ gs,
-                                                                 const double* pv_part, int npv,
-                                                                 const double* wy_part, int nwy, PcgState* st,
-                                                                 cudaGraphConditionalHandle cond, int use_cond) {
-  if (st->done) {
-    if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
-    return;
-  }
-  __shared__ double slot;
-  const double w2 = block_fixed_sum(part_w2, nb3, &slot);
+  const double w2 = block_fixed_sum_cg(part_w2, nb3, &slot);
   double r2 = 0.0, pv = 1.0, wy = 0.0;
   if (init) {
-    r2 = block_fixed_sum(part_r2, nb3, &slot);
+    r2 = block_fixed_sum_cg(part_r2, nb3, &slot);
   } else {
     pv = block_fixed_sum(pv_part, npv, &slot);
     wy = block_fixed_sum(wy_part, nwy, &slot);
@@ -164,48 +137,139 @@ __global__ void __launch_bounds__(kVecThreads) pcg_scalar_kernel(int init, int n
   }
   for (int i = threadIdx.x; i < s; i += kVecThreads) {
     double g = 0.0;
-    for (int b = 0; b < nb3; ++b) g += part_g[(int64_t)b * s + i];
+#pragma unroll 8
+    for (int b = 0; b < nb3; ++b) g += __ldcg(part_g + (int64_t)b * s + i);
     gs[i] = (C)((double)cvec[i] * g);
   }
+  __syncthreads();
   if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
 }
 
-// K5: y = w + U gs (= P^{-1} w), partial w^T y.
+// K3: init  -> w = r - v (v = (H + rho I) x0, or x0 = 0), partial ||r||^2;
+//     step  -> alpha = w^T y / p^T v, x += alpha p, w -= alpha v.
+// Both: partial ||w||^2 and partial U^T w over this block's chunk of w; the last block
+// to finish then runs the scalar step K4 (pcg_scalar_body) and sets the loop condition.
+template <typename C>
+__global__ void __launch_bounds__(kVecThreads) pcg_update_kernel(int init, int64_t d, int chunk, C* __restrict__ x,
+                                                                 C* __restrict__ w, const C* __restrict__ r,
+                                                                 const C* __restrict__ v, const C* __restrict__ p,
+                                                                 const C* __restrict__ U, int s,
+                                                                 const double* __restrict__ pv_part, int npv,
+                                                                 const double* __restrict__ wy_part, int nwy,
+                                                                 double* part_w2, double* part_r2, double* part_g,
+                                                                 PcgState* st, C* __restrict__ hx,
+                                                                 const C* __restrict__ cvec, C* __restrict__ gs,
+                                                                 cudaGraphConditionalHandle cond, int use_cond) {
+  if (st->done) {
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+    return;
+  }
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* wch = reinterpret_cast<C*>(sm_raw);
+  __shared__ double sh[kVecThreads / 32];
+  __shared__ double slot;
+  const int64_t j0 = (int64_t)blockIdx.x * chunk;
+  const int64_t j1 = min(d, j0 + chunk);
+  double alpha = 0.0;
+  bool bad = false;
+  if (!init) {
+    const double pv = block_fixed_sum(pv_part, npv, &slot);
+    const double wy = block_fixed_sum(wy_part, nwy, &slot);
+    bad = !(pv > 0.0) || !isfinite(pv);  // breakdown: flagged by the scalar step
+    if (!bad) alpha = wy / pv;
+  }
+  if (!bad) {
+    const C a = (C)alpha;
+    double lw2 = 0.0, lr2 = 0.0;
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += kVecThreads) {
+      C wj;
+      if (init) {
+        const C rj = r[j];
+        wj = v ? rj - v[j] : rj;
+        lr2 += (double)rj * (double)rj;
+      } else {
+        const C vj = v[j];
+        x[j] = fma(a, p[j], x[j]);
+        wj = fma(-a, vj, w[j]);
+        if (hx) hx[j] = fma(a, vj, hx[j]);  // (H + rho I) x follows x: x += a p  =>  += a v
+      }
+      w[j] = wj;
+      wch[j - j0] = wj;
+      lw2 += (double)wj * (double)wj;
+    }
+    const double tw2 = block_sum<kVecThreads>(lw2, sh);
+    const double tr2 = block_sum<kVecThreads>(lr2, sh);
+    if (threadIdx.x == 0) {
+      part_w2[blockIdx.x] = tw2;
+      if (init) part_r2[blockIdx.x] = tr2;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int len = (int)(j1 - j0);
+    // four rows of U per warp pass: independent accumulators keep four loads and four
+    // reductions in flight (each dot keeps its lane-strided order, then a warp sum)
+    constexpr int RW = 4;
+    for (int i0 = warp * RW; i0 < s; i0 += (kVecThreads / 32) * RW) {
+      C acc[RW];
+#pragma unroll
+      for (int q = 0; q < RW; ++q) acc[q] = C(0);
+#pragma unroll 8
+      for (int jj = lane; jj < len; jj += 32) {
+        const C wv = wch[jj];
+#pragma unroll
+        for (int q = 0; q < RW; ++q)
+          if (i0 + q < s) acc[q] = fma(U[(int64_t)(i0 + q) * d + j0 + jj], wv, acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < RW; ++q) acc[q] = warp_sum(acc[q]);
+      if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < RW; ++q)
+          if (i0 + q < s) part_g[(int64_t)blockIdx.x * s + i0 + q] = (double)acc[q];
+      }
+    }
+  }
+  if (!last_block_done(&st->ticket[0])) return;
+  pcg_scalar_body<C>(init, (int)gridDim.x, part_w2, part_r2, part_g, s, cvec, gs, pv_part, npv, wy_part, nwy, st,
+                     cond, use_cond);
+}
+
+// K5: y = w + U gs (= P^{-1} w), partial w^T y; when p is given, the last block to finish
+// runs K6 over the whole vector: beta = (w^T y)_new / (w^T y)_old, p = y + beta p
+// (init: p = y).
 template <typename C>
 __global__ void __launch_bounds__(kVecThreads) pcg_tail_kernel(int64_t d, const C* __restrict__ w, C* __restrict__ y,
                                                                const C* __restrict__ U, int s,
                                                                const C* __restrict__ gs, double* part_wy,
-                                                               const PcgState* st) {
+                                                               PcgState* st, int init, C* __restrict__ p) {
   if (st->done) return;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* g = reinterpret_cast<C*>(sm_raw);
   __shared__ double sh[kVecThreads / 32];
+  __shared__ double slot;
   for (int i = threadIdx.x; i < s; i += kVecThreads) g[i] = gs[i];
   __syncthreads();
   double lwy = 0.0;
   for (int64_t j = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)gridDim.x * kVecThreads) {
     const C wj = w[j];
     C acc = wj;
+    // same sequential order; the unroll keeps 16 independent loads of U in flight
+#pragma unroll 16
     for (int i = 0; i < s; ++i) acc = fma(U[(int64_t)i * d + j], g[i], acc);
     y[j] = acc;
     lwy += (double)wj * (double)acc;
   }
   const double t = block_sum<kVecThreads>(lwy, sh);
   if (threadIdx.x == 0) part_wy[blockIdx.x] = t;
-}
-
-// K6: beta = (w^T y)_new / (w^T y)_old, p = y + beta p (init: p = y).
-template <typename C>
-__global__ void __launch_bounds__(kVecThreads) pcg_pupdate_kernel(int init, int64_t d, const C* __restrict__ y,
-                                                                  C* __restrict__ p, const double* wy_part, int nwy,
-                                                                  const PcgState* st) {
-  if (st->done) return;
-  __shared__ double slot;
+  if (!p) return;
+  if (!last_block_done(&st->ticket[1])) return;
   double beta = 0.0;
-  if (!init) beta = block_fixed_sum(wy_part, nwy, &slot) / st->wy;
+  if (!init) beta = block_fixed_sum_cg(part_wy, (int)gridDim.x, &slot) / st->wy;
   const C b = (C)beta;
-  for (int64_t j = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)gridDim.x * kVecThreads)
-    p[j] = init ? y[j] : fma(b, p[j], y[j]);
+  for (int64_t j = threadIdx.x; j < d; j += kVecThreads) {
+    const C yj = __ldcg(y + j);
+    p[j] = init ? yj : fma(b, p[j], yj);
+  }
 }
 
 // ------------------------------------------------------------------ host driver
@@ -282,17 +346,11 @@ nys_status pcg_run(const PcgProblem& pb, const PrecondView& P, const C* r, C* x,
   }
   count_launch();
   pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, stream>>>(1, d, chunk, x, w, r, v0, p, U, s, pv_part, nbr,
-                                                             wy_part, nb5, part_w2, part_r2, part_g, st, (C*)nullptr);
+                                                             wy_part, nb5, part_w2, part_r2, part_g, st, (C*)nullptr,
+                                                             cvec, gs, 0ull, 0);
   LAUNCH_OK(cudaGetLastError());
   count_launch();
-  pcg_scalar_kernel<C><<<1, kVecThreads, 0, stream>>>(1, nb3, part_w2, part_r2, part_g, s, cvec, gs, pv_part, nbr,
-                                                      wy_part, nb5, st, 0ull, 0);
-  LAUNCH_OK(cudaGetLastError());
-  count_launch();
-  pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, stream>>>(d, w, y, U, s, gs, wy_part, st);
-  LAUNCH_OK(cudaGetLastError());
-  count_launch();
-  pcg_pupdate_kernel<C><<<nb5, kVecThreads, 0, stream>>>(1, d, y, p, wy_part, nb5, st);
+  pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, stream>>>(d, w, y, U, s, gs, wy_part, st, 1, p);
   LAUNCH_OK(cudaGetLastError());
 
   PcgState* hs = host_state();
@@ -306,17 +364,11 @@ nys_status pcg_run(const PcgProblem& pb, const PrecondView& P, const C* r, C* x,
       LAUNCH_OK(apass_reduce(aa, pb.plan, apart, pb.rho, v, pv_part, nbr, stream));
       count_launch();
       pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, stream>>>(0, d, chunk, x, w, r, v, p, U, s, pv_part, nbr,
-                                                                 wy_part, nb5, part_w2, part_r2, part_g, st, (C*)nullptr);
+                                                                 wy_part, nb5, part_w2, part_r2, part_g, st, (C*)nullptr,
+                                                                 cvec, gs, 0ull, 0);
       LAUNCH_OK(cudaGetLastError());
       count_launch();
-      pcg_scalar_kernel<C><<<1, kVecThreads, 0, stream>>>(0, nb3, part_w2, part_r2, part_g, s, cvec, gs, pv_part,
-                                                          nbr, wy_part, nb5, st, 0ull, 0);
-      LAUNCH_OK(cudaGetLastError());
-      count_launch();
-      pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, stream>>>(d, w, y, U, s, gs, wy_part, st);
-      LAUNCH_OK(cudaGetLastError());
-      count_launch();
-      pcg_pupdate_kernel<C><<<nb5, kVecThreads, 0, stream>>>(0, d, y, p, wy_part, nb5, st);
+      pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, stream>>>(d, w, y, U, s, gs, wy_part, st, 0, p);
       LAUNCH_OK(cudaGetLastError());
     }
     LAUNCH_OK(cudaMemcpyAsync(hs, st, sizeof(PcgState), cudaMemcpyDeviceToHost, stream));
@@ -363,17 +415,13 @@ nys_status precond_apply_run(const PrecondView& P, int64_t d, const C* V, C* Y, 
     count_launch();
     pcg_update_kernel<C><<<nb3, kVecThreads, (size_t)chunk * sizeof(C), stream>>>(
         1, d, chunk, nullptr, w, V + c * d, nullptr, nullptr, reinterpret_cast<const C*>(P.U), s, nullptr, 0,
-        nullptr, 0, part_w2, part_r2, part_g, st, (C*)nullptr);
-    count_launch();
-    pcg_scalar_kernel<C><<<1, kVecThreads, 0, stream>>>(1, nb3, part_w2, part_r2, part_g, s,
-                                                        reinterpret_cast<const C*>(P.c), gs, nullptr, 0, nullptr, 0,
-                                                        st, 0ull, 0);
-    // the scalar kernel may mark the state done (||w|| <= 0 threshold); force the tail to run
+        nullptr, 0, part_w2, part_r2, part_g, st, (C*)nullptr, reinterpret_cast<const C*>(P.c), gs, 0ull, 0);
+    // the scalar step may mark the state done (||w|| <= 0 threshold); force the tail to run
     count_launch();
     pcg_reset_kernel<<<1, 1, 0, stream>>>(st, 0.0, 1, 1, -1, nullptr);
     count_launch();
     pcg_tail_kernel<C><<<nb5, kVecThreads, (size_t)std::max(1, s) * sizeof(C), stream>>>(
-        d, w, Y + c * d, reinterpret_cast<const C*>(P.U), s, gs, wy_part, st);
+        d, w, Y + c * d, reinterpret_cast<const C*>(P.U), s, gs, wy_part, st, 1, (C*)nullptr);
     if (cudaGetLastError() != cudaSuccess) return NYS_ECUDA;
   }
   if (cudaStreamSynchronize(stream) != cudaSuccess) return NYS_ECUDA;
@@ -438,14 +486,32 @@ __global__ void __launch_bounds__(kVecThreads) admm_zu_kernel(int64_t d, const C
   }
 }
 
+// Sum of the per-block partials part5[b * 5 + t] over b = 0 .. nb-1 in increasing b (the
+// same order as a sequential loop): the warp stages them in shared memory with coalesced
+// loads first, so lane 0 adds from shared memory instead of waiting on each global load.
+constexpr int kPart5Max = 256;
+__device__ __forceinline__ void sum_part5(int nb, const double* part5, double (&a)[5]) {
+  __shared__ double sp[kPart5Max * 5];
+  const int lane = threadIdx.x & 31;
+  const bool staged = nb <= kPart5Max;
+  if (staged) {
+    for (int i = lane; i < nb * 5; i += 32) sp[i] = __ldcg(part5 + i);
+    __syncwarp();
+  }
+  for (int t = 0; t < 5; ++t) a[t] = 0.0;
+  if (lane == 0) {
+    for (int b = 0; b < nb; ++b)
+      for (int t = 0; t < 5; ++t) a[t] += staged ? sp[b * 5 + t] : __ldcg(part5 + (int64_t)b * 5 + t);
+  }
+}
+
 // r_p, r_d (Sec. 2.1), the next PCG tolerance sqrt(r_p r_d) (Sec. 5) and the
 // residual stopping test.
 __global__ void admm_scalar_kernel(int nb, const double* part5, double rho, int k, double* rp_trace,
                                    double* rd_trace, double* eps_next, double eps_abs, double eps_rel, int* stop) {
+  double a[5];
+  sum_part5(nb, part5, a);
   if (threadIdx.x != 0) return;
-  double a[5] = {0, 0, 0, 0, 0};
-  for (int b = 0; b < nb; ++b)
-    for (int t = 0; t < 5; ++t) a[t] += part5[(int64_t)b * 5 + t];
   const double rp = sqrt(a[0]);
   const double rd = rho * sqrt(a[1]);
   rp_trace[k] = rp;
@@ -527,7 +593,7 @@ struct AdmmCtl {
   int k;            // ADMM iteration counter
   int stop;         // residual stop reached
   int hx_skip;      // 1: reuse the tracked (H + rho I) x; 0: recompute it this iteration
-  int pad;
+  unsigned int ticket;  // last-block election of the fused zu / scalar kernel
   long long nodes;  // kernel launches executed (instrumentation)
   double eps_next;  // sqrt(r_p r_d) of the last iteration
 };
@@ -548,6 +614,8 @@ __global__ void admm_begin_kernel(AdmmCtl* ctl, PcgState* st, double tol, int to
   st->status = 0;
   st->maxit = maxit;
   st->fixed = fixed_dev ? fixed_dev[k] : -1;
+  st->ticket[0] = 0u;
+  st->ticket[1] = 0u;
   if (tol_mode == NYS_TOL_SQRT_RPRD && k > 0) {
     st->tol = ctl->eps_next;
     st->tol_abs = 1;
@@ -582,12 +650,43 @@ __global__ void admm_rhs_g_kernel(int64_t d, const double* __restrict__ q, const
   }
 }
 
+// Scalar step of an ADMM iteration in the graph (one warp of the last zu block): r_p, r_d,
+// the next PCG tolerance, the stop test and the WHILE condition.
+__device__ void admm_scalar_g_body(int nb, const double* part5, double rho, int K, double eps_abs,
+                                     double eps_rel, double* rp_trace, double* rd_trace, int* pcg_it_trace,
+                                     const PcgState* st, AdmmCtl* ctl, long long nodes_per_iter,
+                                     long long nodes_per_pcg_iter, cudaGraphConditionalHandle cond) {
+  double a[5];
+  sum_part5(nb, part5, a);  // partials of the running kernel: read through L2
+  if (threadIdx.x != 0) return;
+  const int k = ctl->k;
+  const double rp = sqrt(a[0]);
+  const double rd = rho * sqrt(a[1]);
+  rp_trace[k] = rp;
+  rd_trace[k] = rd;
+  pcg_it_trace[k] = st->iters;
+  ctl->eps_next = sqrt(rp * rd);
+  if (eps_rel > 0.0) {
+    const double tp = eps_abs + eps_rel * fmax(sqrt(a[2]), sqrt(a[3]));
+    const double td = eps_abs + eps_rel * rho * sqrt(a[4]);
+    if (rp <= tp && rd <= td) ctl->stop = 1;
+  }
+  if (st->status == NYS_EBREAKDOWN) ctl->stop = 2;
+  ctl->nodes += nodes_per_iter + nodes_per_pcg_iter * (long long)st->iters;
+  ctl->k = k + 1;
+  cudaGraphSetConditional(cond, (k + 1 < K && !ctl->stop) ? 1u : 0u);
+}
+
 template <typename C>
 __global__ void __launch_bounds__(kVecThreads) admm_zu_g_kernel(int64_t d, const C* __restrict__ xc, int accumulate,
                                                                 double* __restrict__ x, double* __restrict__ z,
                                                                 double* __restrict__ u, double kappa,
-                                                                double* __restrict__ ztrace, const AdmmCtl* ctl,
-                                                                double* part5) {
+                                                                double* __restrict__ ztrace, AdmmCtl* ctl,
+                                                                double* part5, double rho, int K, double eps_abs,
+                                                                double eps_rel, double* rp_trace, double* rd_trace,
+                                                                int* pcg_it_trace, const PcgState* st,
+                                                                long long nodes_per_iter, long long nodes_per_pcg_iter,
+                                                                cudaGraphConditionalHandle cond) {
   __shared__ double sh[kVecThreads / 32];
   double* zt = ztrace ? ztrace + (int64_t)ctl->k * d : nullptr;
   double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
@@ -621,33 +720,13 @@ __global__ void __launch_bounds__(kVecThreads) admm_zu_g_kernel(int64_t d, const
     o[3] = a3;
     o[4] = a4;
   }
+  // the last block to finish runs the scalar step of the iteration
+  if (!last_block_done(&ctl->ticket)) return;
+  if (threadIdx.x < 32)
+    admm_scalar_g_body((int)gridDim.x, part5, rho, K, eps_abs, eps_rel, rp_trace, rd_trace, pcg_it_trace, st, ctl,
+                       nodes_per_iter, nodes_per_pcg_iter, cond);
 }
 
-__global__ void admm_scalar_g_kernel(int nb, const double* part5, double rho, int K, double eps_abs,
-                                     double eps_rel, double* rp_trace, double* rd_trace, int* pcg_it_trace,
-                                     const PcgState* st, AdmmCtl* ctl, long long nodes_per_iter,
-                                     long long nodes_per_pcg_iter, cudaGraphConditionalHandle cond) {
-  if (threadIdx.x != 0) return;
-  double a[5] = {0, 0, 0, 0, 0};
-  for (int b = 0; b < nb; ++b)
-    for (int t = 0; t < 5; ++t) a[t] += part5[(int64_t)b * 5 + t];
-  const int k = ctl->k;
-  const double rp = sqrt(a[0]);
-  const double rd = rho * sqrt(a[1]);
-  rp_trace[k] = rp;
-  rd_trace[k] = rd;
-  pcg_it_trace[k] = st->iters;
-  ctl->eps_next = sqrt(rp * rd);
-  if (eps_rel > 0.0) {
-    const double tp = eps_abs + eps_rel * fmax(sqrt(a[2]), sqrt(a[3]));
-    const double td = eps_abs + eps_rel * rho * sqrt(a[4]);
-    if (rp <= tp && rd <= td) ctl->stop = 1;
-  }
-  if (st->status == NYS_EBREAKDOWN) ctl->stop = 2;
-  ctl->nodes += nodes_per_iter + nodes_per_pcg_iter * (long long)st->iters;
-  ctl->k = k + 1;
-  cudaGraphSetConditional(cond, (k + 1 < K && !ctl->stop) ? 1u : 0u);
-}
 
 }  // namespace
 
@@ -889,12 +968,10 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
     G_OK(cudaStreamBeginCaptureToGraph(cap, body, &n_hx, nullptr, 1, cudaStreamCaptureModeRelaxed));
   }
   pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, cap>>>(1, d, chunk, xc, w, rc, hx, p, U, s, pv_part, nbr,
-                                                          wy_part, nb5, part_w2, part_r2, part_g, st, (C*)nullptr);
-  pcg_scalar_kernel<C><<<1, kVecThreads, 0, cap>>>(1, nb3, part_w2, part_r2, part_g, s, cvec, gs, pv_part, nbr,
-                                                   wy_part, nb5, st, h_pcg, 1);
-  pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, cap>>>(d, w, y, U, s, gs, wy_part, st);
-  pcg_pupdate_kernel<C><<<nb5, kVecThreads, 0, cap>>>(1, d, y, p, wy_part, nb5, st);
-  seg_nodes += 4;
+                                                          wy_part, nb5, part_w2, part_r2, part_g, st, (C*)nullptr,
+                                                          cvec, gs, h_pcg, 1);
+  pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, cap>>>(d, w, y, U, s, gs, wy_part, st, 1, p);
+  seg_nodes += 2;
   cudaStreamCaptureStatus cst;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
@@ -917,12 +994,9 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, true));
   G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho, v, pv_part, nbr, cap));
   pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, cap>>>(0, d, chunk, xc, w, rc, v, p, U, s, pv_part, nbr, wy_part,
-                                                          nb5, part_w2, part_r2, part_g, st, hx);
-  pcg_scalar_kernel<C><<<1, kVecThreads, 0, cap>>>(0, nb3, part_w2, part_r2, part_g, s, cvec, gs, pv_part, nbr,
-                                                   wy_part, nb5, st, h_pcg, 1);
-  pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, cap>>>(d, w, y, U, s, gs, wy_part, st);
-  pcg_pupdate_kernel<C><<<nb5, kVecThreads, 0, cap>>>(0, d, y, p, wy_part, nb5, st);
-  body_nodes = 6;
+                                                          nb5, part_w2, part_r2, part_g, st, hx, cvec, gs, h_pcg, 1);
+  pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, cap>>>(d, w, y, U, s, gs, wy_part, st, 0, p);
+  body_nodes = 4;
   G_OK(cudaStreamEndCapture(cap, &pbody));
 
   // ---- segment 2: prox / dual step, residuals, loop condition
@@ -932,11 +1006,10 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
     ws_record_kernel<<<1, 128, 0, cap>>>(s, feat, proj, rnorm, g.rho, ctl, g.warm_record);
     seg_nodes += 2;
   }
+  seg_nodes += 1;
   admm_zu_g_kernel<C><<<nbz, kVecThreads, 0, cap>>>(d, xc, refine, g.x, g.z, g.u, g.gamma / g.rho, g.ztrace, ctl,
-                                                    part5);
-  seg_nodes += 2;
-  admm_scalar_g_kernel<<<1, 32, 0, cap>>>(nbz, part5, g.rho, K, g.eps_abs, g.eps_rel, g.rp, g.rd, g.pcg_it, st, ctl,
-                                          seg_nodes, body_nodes, h_admm);
+                                                    part5, g.rho, K, g.eps_abs, g.eps_rel, g.rp, g.rd, g.pcg_it, st,
+                                                    seg_nodes, body_nodes, h_admm);
   G_OK(cudaStreamEndCapture(cap, &body));
   count_launch_suspend(false);
   G_OK(cudaGetLastError());
@@ -968,13 +1041,27 @@ nys_status admm_graph_run_many(const GraphLoopArgs* gs, int count, cudaStream_t 
       if (*g) cudaGraphDestroy(*g);
     }
   } cleanup{&graph, &exec};
+  const bool trace = std::getenv("NYS_TRACE") != nullptr;
+  auto now = [&]() {
+    if (trace) cudaStreamSynchronize(stream);
+    return std::chrono::steady_clock::now();
+  };
+  auto t0 = now();
   if (cudaGraphCreate(&graph, 0) != cudaSuccess) return NYS_ECUDA;
   for (int i = 0; i < count; ++i) {
     const nys_status s = admm_graph_add<C>(graph, gs[i], stream, pool, &insts[i]);
     if (s != NYS_OK) return s;
   }
+  auto t1 = now();
   if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) return NYS_ECUDA;
+  auto t2 = now();
   if (cudaGraphLaunch(exec, stream) != cudaSuccess) return NYS_ECUDA;
+  if (trace) {
+    auto t3 = now();
+    auto ms = [](auto a, auto b) { return std::chrono::duration<double, std::milli>(b - a).count(); };
+    std::fprintf(stderr, "[nys] graph build %.3f ms, instantiate %.3f ms, run %.3f ms\n", ms(t0, t1), ms(t1, t2),
+                 ms(t2, t3));
+  }
   nys_status worst = NYS_OK;
   for (int i = 0; i < count; ++i) {
     AdmmCtl ctl_h;

@@ -18,6 +18,7 @@ struct PcgState {
   int status;
   int maxit;
   int fixed;       // >= 0: run exactly this many iterations
+  unsigned int ticket[2];  // last-block election of the fused update / tail kernels (zero between launches)
 };
 
 // Stream-ordered device allocations freed when the pool goes out of scope.
