@@ -147,7 +147,8 @@ def run_ours(args):
 
     def solve_mixed(iters, trace=False):
         return nx.nysadmm_solve("lasso", M64, b, gamma, rho, s, w["pcg_tol"], Om, admm_iters=iters,
-                                A_inner=Mbf, refine=False, z_trace=trace, hx_refresh=args.hx_refresh)
+                                A_inner=Mbf, refine=False, z_trace=trace, hx_refresh=args.hx_refresh,
+                                device_loop=not args.host_loop)
 
     def solve_plain(iters, trace=False):
         return nx.nysadmm_solve("lasso", M64, b, gamma, rho, s, w["pcg_tol_fp64"], Om, admm_iters=iters,
@@ -543,6 +544,26 @@ def extra_logistic(args):
                       "emp_cond": out["info"]["emp_cond"]}), flush=True)
 
 
+def profile_sketch():
+    """Small ncu case: the tensor-core sketch Y = A^T A Omega (rank 200) of a 50000 x 10000
+    BF16 matrix (1 GB): one warm-up sketch, then one more."""
+    from paper_2202_11599_gb300 import nysadmm as nx
+    import __graft_entry__
+    __graft_entry__.build()
+    n, d, s = 50_000, 10_000, 200
+    g = torch.Generator(device="cuda").manual_seed(3)
+    A = torch.randn(n, d, generator=g, device="cuda", dtype=torch.float32).to(torch.bfloat16)
+    Om = torch.randn(d, s, generator=g, device="cuda", dtype=torch.float64)
+    M = nx.Matrix(A)
+    P = nx.sketch(M, Om)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    P = nx.sketch(M, Om)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_sketch": "bf16", "n": n, "d": d, "rank": s, "sketch_s": time.time() - t0,
+                      "lam0": float(P.lam[0])}))
+
+
 def profile_apass(dt):
     """Small ncu case: the fused A-pass y = A^T (A p) + rho p on a 50000 x 10000 matrix
     (1 GB in BF16, larger than L2): 2 warm-up launches, then 6 timed launches."""
@@ -579,7 +600,11 @@ def main():
     ap.add_argument("--cal-iters-fp64", type=int, default=1200)
     ap.add_argument("--cpu-iters", type=int, default=3)
     ap.add_argument("--ref-cal-iters", type=int, default=1200)
-    ap.add_argument("--traffic", type=float, default=None,
+    # DRAM bytes (read + write) per launch of the BF16 A-pass on this workload: ncu
+    # --set full of apass_f_kernel<BF16, 2, 4, 640> on 50,000 x 10,000 (1.000163 GB read,
+    # 3.49 MB of partials written), rows doubled to 100,000 -- equal to the algorithmic
+    # bytes (no re-reads).  Pass --traffic none after changing that kernel.
+    ap.add_argument("--traffic", type=lambda v: None if v == "none" else float(v), default=2.0038e9,
                     help="ncu dram bytes per A-pass launch (from a committed profile), if current")
     ap.add_argument("--hx-refresh", type=int, default=50,
                     help="recompute (H + rho I) x for the PCG warm start every this many ADMM iterations")
@@ -588,6 +613,10 @@ def main():
     ap.add_argument("--no-check", action="store_true", help="skip F* and the final gap check (profiling runs)")
     ap.add_argument("--profile-apass", choices=["bf16", "f32", "f64"], default=None,
                     help="only run the fused A-pass on a 50000 x 10000 matrix (ncu capture case)")
+    ap.add_argument("--profile-sketch", action="store_true",
+                    help="only run the tensor-core sketch on a 50000 x 10000 BF16 matrix (ncu capture case)")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="run the ADMM loop from the host (kernel launches that ncu can list one by one)")
     ap.add_argument("--extra", choices=["batched", "logistic"], default=None,
                     help="run a secondary workload and print its own JSON line")
     ap.add_argument("--extra-iters", type=int, default=100)
@@ -603,6 +632,8 @@ def main():
         extra_logistic(args)
     elif args.profile_apass:
         profile_apass(args.profile_apass)
+    elif args.profile_sketch:
+        profile_sketch()
     elif args.impl == "reference":
         run_reference(args)
     else:
