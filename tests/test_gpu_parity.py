@@ -123,6 +123,22 @@ def test_sketch_low_precision_storage(dtype):
     assert np.max(np.abs(lam_g - lam)) <= 2e-5 * lam[0]
 
 
+@pytest.mark.parametrize("n,d,s", [(3001, 517, 37), (2500, 600, 260), (130, 40, 3)])
+def test_sketch_bf16_tensor_core_ragged(n, d, s):
+    """BF16 storage takes the tcgen05 sketch: ragged rows (M tail), a K tail (d not a
+    multiple of 32), N padding (s not a multiple of 16) and two column panels (s > 256),
+    with and without row weights D; eigenvalues against the oracle on the stored matrix."""
+    A, Om = _small_problem(n=n, d=d, s=s, seed=n + s)
+    Aq = _quantised(A, torch.bfloat16)
+    Dv = np.random.default_rng(s).random(n) + 0.1
+    for D in (None, Dv):
+        w = np.ones(n) if D is None else D
+        U, lam, _, _, _ = o.nystrom(lambda X: Aq.T @ (w[:, None] * (Aq @ X)), Om, shift_scale=np.sqrt(d),
+                                    mantissa_bits=23)
+        P = nx.sketch(nx.Matrix.padded(_dev(A), torch.bfloat16), _dev(Om), D=None if D is None else _dev(D))
+        assert np.max(np.abs(P.lam.numpy() - lam)) <= 2e-5 * lam[0]
+
+
 def test_sketch_with_weights_and_shift():
     A, Om = _small_problem(n=500, d=80, s=10, seed=9)
     Dv = np.random.default_rng(9).random(500) + 0.05
