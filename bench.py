@@ -433,7 +433,9 @@ def extra_batched(args):
     """Batched forms (separate JSON line, not the headline metric):
     (i) a 64-point lasso regularisation path sharing one 50,000 x 4,000 FP32 matrix
         (decay (1+j)^-1), gamma log-spaced in [1e-3, 1] ||A^T b||_inf, rank 50, rho 100:
-        multi-RHS path vs 64 sequential single solves, same ADMM iterations;
+        multi-RHS path vs 64 sequential single solves, same ADMM iterations; then the same
+        with a BF16 inner copy, whose k-column matvecs run on the tensor cores (also timed
+        with the CUDA-core matvec for comparison);
     (ii) 32 independent lasso instances, d uniform in [500, 8000] (seed 4), n = 10 d,
         FP32, rank 50: one graph launch vs 32 sequential device-loop solves."""
     from paper_2202_11599_gb300 import nysadmm as nx
@@ -450,26 +452,44 @@ def extra_batched(args):
     g = torch.Generator(device=dev).manual_seed(13)
     Om = torch.randn(d, s, generator=g, device=dev, dtype=torch.float64)
     rho, tol = 100.0, 1e-4
-    nx.nysadmm_solve_path(M, b, gammas[:2], rho, s, tol, Om, admm_iters=2)          # warm-up
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    out = nx.nysadmm_solve_path(M, b, gammas, rho, s, tol, Om, admm_iters=K)
-    torch.cuda.synchronize()
-    t_path = time.perf_counter() - t0
-    nx.nysadmm_solve("lasso", M, b, gammas[0], rho, s, tol, Om, admm_iters=2)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    zs = []
-    for gm in gammas:
-        zs.append(nx.nysadmm_solve("lasso", M, b, gm, rho, s, tol, Om, admm_iters=K, hx_refresh=10)["z"])
-    torch.cuda.synchronize()
-    t_single = time.perf_counter() - t0
-    Zp = out["Z"]
-    dev_max = max(((Zp[:, c] - zs[c]).norm() / max(zs[c].norm().item(), 1e-30)).item() for c in range(kpath))
-    path = {"n": n, "d": d, "k": kpath, "rank": s, "admm_iters": K, "time_path_s": round(t_path, 3),
-            "time_64_single_s": round(t_single, 3), "speedup": round(t_single / t_path, 2),
-            "max_rel_diff_vs_single": dev_max, "pcg_iters_total": out["info"]["pcg_iters_total"]}
-    del A32, M, W, out, zs
+
+    def run_path(inner, singles=True):
+        kw = {} if inner is None else {"A_inner": inner}
+        skw = {} if inner is None else {"A_inner": inner, "refine": False}
+        nx.nysadmm_solve_path(M, b, gammas[:2], rho, s, tol, Om, admm_iters=2, **kw)          # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = nx.nysadmm_solve_path(M, b, gammas, rho, s, tol, Om, admm_iters=K, **kw)
+        torch.cuda.synchronize()
+        t_path = time.perf_counter() - t0
+        res = {"time_path_s": round(t_path, 3), "pcg_iters_total": out["info"]["pcg_iters_total"]}
+        if singles:
+            nx.nysadmm_solve("lasso", M, b, gammas[0], rho, s, tol, Om, admm_iters=2, **skw)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            zs = []
+            for gm in gammas:
+                zs.append(nx.nysadmm_solve("lasso", M, b, gm, rho, s, tol, Om, admm_iters=K, hx_refresh=10, **skw)["z"])
+            torch.cuda.synchronize()
+            t_single = time.perf_counter() - t0
+            Zp = out["Z"]
+            dev_max = max(((Zp[:, c] - zs[c]).norm() / max(zs[c].norm().item(), 1e-30)).item() for c in range(kpath))
+            res.update({"time_64_single_s": round(t_single, 3), "speedup": round(t_single / t_path, 2),
+                        "max_rel_diff_vs_single": dev_max})
+        return res
+
+    path = {"n": n, "d": d, "k": kpath, "rank": s, "admm_iters": K, "A": "fp32 (CUDA-core multi-RHS matvec)"}
+    path.update(run_path(None))
+    # BF16 inner copy: the k-column matvecs run on the tcgen05 tensor cores
+    Mi = nx.Matrix(A32.to(torch.bfloat16))
+    path_bf16 = {"A_inner": "bf16 (tcgen05 multi-RHS matvec)"}
+    path_bf16.update(run_path(Mi))
+    os.environ["NYS_SKETCH_TC"] = "0"
+    try:
+        path_bf16["time_path_cuda_cores_s"] = run_path(Mi, singles=False)["time_path_s"]
+    finally:
+        os.environ.pop("NYS_SKETCH_TC", None)
+    del A32, M, Mi, W
     torch.cuda.empty_cache()
     # (ii) uneven batch
     rng = np.random.default_rng(4)
@@ -496,7 +516,7 @@ def extra_batched(args):
     batch = {"instances": 32, "d_range": [int(dims.min()), int(dims.max())], "admm_iters": K,
              "time_one_graph_s": round(t_batch, 3), "time_sequential_s": round(t_seq, 3),
              "speedup": round(t_seq / t_batch, 2)}
-    print(json.dumps({"extra": "batched", "path": path, "uneven_batch": batch}), flush=True)
+    print(json.dumps({"extra": "batched", "path": path, "path_bf16": path_bf16, "uneven_batch": batch}), flush=True)
 
 
 def extra_logistic(args):

@@ -98,6 +98,13 @@ size_t sketch_atw_work_bytes(const nys_matrix* A, int s);
 bool sketch_tc_supported(const nys_matrix* A);
 cudaError_t sketch_tc_bf16(const nys_matrix* A, const double* D, const double* Om, int m, double* Y,
                            cudaStream_t st);
+// Tensor-core multi-RHS H-matvec for BF16 storage: Y (d x k) = A^T diag(D) A X + rho X, FP32
+// X and Y column-major; At is the transposed copy of A from tc_transpose (d x
+// tc_transposed_rows(A) BF16 elements, caller-owned).
+int64_t tc_transposed_rows(const nys_matrix* A);
+cudaError_t tc_transpose(const nys_matrix* A, uint16_t* At, cudaStream_t st);
+cudaError_t tc_hmm_bf16(const nys_matrix* A, const uint16_t* At, const double* D, const float* X, int k, double rho,
+                        float* Y, cudaStream_t st);
 cudaError_t sketch_atw_partials(const nys_matrix* A, const void* W, int s, void* work, size_t work_bytes, int* nz_out,
                                 cudaStream_t st);
 // small dense GEMMs in compute type T (column-major)

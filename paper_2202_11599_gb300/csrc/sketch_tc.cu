@@ -282,17 +282,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const TcArgs a
   if (warp == 0) tmem_dealloc(tmem, TC_NMAX);
 }
 
-// Omega terms: Ot[t][c][k] (c < NP, k < KP) = t-th BF16 term of float(Om[k + (c0 + c) d]),
-// zero outside c < mp, k < d.
-__global__ void split_omega_kernel(const double* __restrict__ Om, int64_t d, int c0, int mp, int NP, int64_t KP,
-                                   uint16_t* __restrict__ Ot) {
+// Operand terms: Ot[t][c][k] (c < NP, k < KP) = t-th BF16 term of float(X[k + (c0 + c) d]),
+// zero outside c < mp, k < d.  X is d x m column-major (FP64 or FP32).
+template <typename T>
+__global__ void split_operand_kernel(const T* __restrict__ X, int64_t d, int c0, int mp, int NP, int64_t KP,
+                                     uint16_t* __restrict__ Ot) {
   const int64_t total = (int64_t)NP * KP;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(idx / KP);
     const int64_t k = idx - (int64_t)c * KP;
     float x = 0.f;
-    if (c < mp && k < d) x = (float)Om[k + (int64_t)(c0 + c) * d];
+    if (c < mp && k < d) x = (float)X[k + (int64_t)(c0 + c) * d];
     uint16_t t3[3];
     split3(x, t3);
 #pragma unroll
@@ -345,9 +346,10 @@ __global__ void __launch_bounds__(256) transpose_bf16_kernel(const uint16_t* __r
   }
 }
 
-// Y[j + (c0 + c) d] = sum_z P[z][c][j] (fixed order, FP64), c < mp.
+// Y[j + (c0 + c) d] = sum_z P[z][c][j] (fixed order, FP64) + rho X[j + (c0 + c) d], c < mp.
+template <typename TY, typename TX>
 __global__ void sum_slices_kernel(const float* __restrict__ P, int Z, int NP, int64_t d, int c0, int mp,
-                                  double* __restrict__ Y) {
+                                  double rho, const TX* __restrict__ X, TY* __restrict__ Y) {
   const int64_t total = (int64_t)mp * d;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -355,7 +357,9 @@ __global__ void sum_slices_kernel(const float* __restrict__ P, int Z, int NP, in
     const int64_t j = idx - (int64_t)c * d;
     double s = 0.0;
     for (int z = 0; z < Z; ++z) s += (double)P[((int64_t)z * NP + c) * d + j];
-    Y[j + (int64_t)(c0 + c) * d] = s;
+    const int64_t o = j + (int64_t)(c0 + c) * d;
+    if (X && rho != 0.0) s += rho * (double)X[o];
+    Y[o] = (TY)s;
   }
 }
 
@@ -407,11 +411,13 @@ bool sketch_tc_supported(const nys_matrix* A) {
   return true;
 }
 
-cudaError_t sketch_tc_bf16(const nys_matrix* A, const double* D, const double* Om, int m, double* Y,
-                           cudaStream_t st) {
-  if (A->dtype != NYS_BF16 || m <= 0) return cudaErrorInvalidValue;
+namespace {
+// Y (d x m, column-major) = A^T diag(D) A X (+ rho X) on the tensor cores, given the
+// transposed copy At (d x nP) of A.  X and Y are FP64 (sketch) or FP32 (batched PCG).
+template <typename TX, typename TY>
+cudaError_t tc_product(const nys_matrix* A, const uint16_t* At, int64_t nP, const double* D, const TX* X, int m,
+                       double rho, TY* Y, cudaStream_t st, bool trace) {
   const int64_t n = A->n, d = A->d;
-  const int64_t nP = (n + TC_BK - 1) / TC_BK * TC_BK;
   const int64_t dP = (d + TC_BK - 1) / TC_BK * TC_BK;
   const int NPmax = std::min(TC_NMAX, (m + 15) / 16 * 16);
   const uint32_t swap = std::getenv("NYS_TC_DESC_SWAP") ? (uint32_t)std::atoi(std::getenv("NYS_TC_DESC_SWAP")) : 0u;
@@ -422,8 +428,6 @@ cudaError_t sketch_tc_bf16(const nys_matrix* A, const double* D, const double* O
   const int64_t kslice2 = (kt2 + Z - 1) / Z;
   const int Zeff = (int)((kt2 + kslice2 - 1) / kslice2);
 
-  // NYS_TRACE: per-kernel device times of this sketch on stderr
-  const bool trace = std::getenv("NYS_TRACE") != nullptr;
   cudaEvent_t ev[8] = {};
   int nev = 0;
   auto mark = [&]() {
@@ -435,25 +439,17 @@ cudaError_t sketch_tc_bf16(const nys_matrix* A, const double* D, const double* O
   Pool pool(st);
   uint16_t* Ot = pool.alloc<uint16_t>((size_t)TC_TERMS * NPmax * dP);
   uint16_t* Wt = pool.alloc<uint16_t>((size_t)TC_TERMS * NPmax * nP);
-  uint16_t* At = pool.alloc<uint16_t>((size_t)d * nP);
   float* P = pool.alloc<float>((size_t)Zeff * NPmax * d);
   int* status = pool.alloc<int>(1);
   if (!pool.ok()) return cudaErrorMemoryAllocation;
   NYS_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
   mark();
-
-  count_launch();
-  transpose_bf16_kernel<<<dim3((unsigned)(nP + 63) / 64, (unsigned)(d + 63) / 64), 256, 0, st>>>(
-      reinterpret_cast<const uint16_t*>(A->data), n, d, A->ld, At, nP);
-  NYS_CUDA_TRY(cudaGetLastError());
-  mark();
-
   for (int c0 = 0; c0 < m; c0 += TC_NMAX) {
     const int mp = std::min(TC_NMAX, m - c0);
     const int NP = (mp + 15) / 16 * 16;
     count_launch();
-    split_omega_kernel<<<(unsigned)std::min<int64_t>(4096, ((int64_t)NP * dP + 255) / 256), 256, 0, st>>>(
-        Om, d, c0, mp, NP, dP, Ot);
+    split_operand_kernel<TX><<<(unsigned)std::min<int64_t>(4096, ((int64_t)NP * dP + 255) / 256), 256, 0, st>>>(
+        X, d, c0, mp, NP, dP, Ot);
     NYS_CUDA_TRY(cudaGetLastError());
     if (c0 == 0) mark();
 
@@ -497,16 +493,17 @@ cudaError_t sketch_tc_bf16(const nys_matrix* A, const double* D, const double* O
     if (c0 == 0) mark();
 
     count_launch();
-    sum_slices_kernel<<<(unsigned)std::min<int64_t>(4096, ((int64_t)mp * d + 255) / 256), 256, 0, st>>>(
-        P, Zeff, NP, d, c0, mp, Y);
+    sum_slices_kernel<TY, TX><<<(unsigned)std::min<int64_t>(4096, ((int64_t)mp * d + 255) / 256), 256, 0, st>>>(
+        P, Zeff, NP, d, c0, mp, rho, X, Y);
     NYS_CUDA_TRY(cudaGetLastError());
     if (c0 == 0) mark();
   }
+  int status_h = 0;
+  NYS_CUDA_TRY(cudaMemcpyAsync(&status_h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NYS_CUDA_TRY(cudaStreamSynchronize(st));
   if (trace) {
-    cudaStreamSynchronize(st);
-    static const char* names[] = {"alloc", "transpose A", "split Omega", "GEMM1 W = D A Om", "GEMM2 A^T W",
-                                  "sum slices"};
-    for (int i = 1; i < nev && i < 7; ++i) {
+    static const char* names[] = {"alloc", "split operand", "GEMM1 W = D A X", "GEMM2 A^T W", "sum slices"};
+    for (int i = 1; i < nev && i < 6; ++i) {
       float ms = 0.f;
       if (ev[i - 1] && ev[i]) cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
       std::fprintf(stderr, "[nys]   tc %-18s %8.3f ms\n", names[i - 1], ms);
@@ -515,10 +512,52 @@ cudaError_t sketch_tc_bf16(const nys_matrix* A, const double* D, const double* O
   }
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);
-  int status_h = 0;
-  NYS_CUDA_TRY(cudaMemcpyAsync(&status_h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
-  NYS_CUDA_TRY(cudaStreamSynchronize(st));
   return status_h ? cudaErrorLaunchTimeout : cudaSuccess;
+}
+}  // namespace
+
+int64_t tc_transposed_rows(const nys_matrix* A) { return (A->n + TC_BK - 1) / TC_BK * TC_BK; }
+
+cudaError_t tc_transpose(const nys_matrix* A, uint16_t* At, cudaStream_t st) {
+  if (A->dtype != NYS_BF16) return cudaErrorInvalidValue;
+  const int64_t nP = tc_transposed_rows(A);
+  count_launch();
+  transpose_bf16_kernel<<<dim3((unsigned)((nP + 63) / 64), (unsigned)((A->d + 63) / 64)), 256, 0, st>>>(
+      reinterpret_cast<const uint16_t*>(A->data), A->n, A->d, A->ld, At, nP);
+  return cudaGetLastError();
+}
+
+cudaError_t sketch_tc_bf16(const nys_matrix* A, const double* D, const double* Om, int m, double* Y,
+                           cudaStream_t st) {
+  if (A->dtype != NYS_BF16 || m <= 0) return cudaErrorInvalidValue;
+  const bool trace = std::getenv("NYS_TRACE") != nullptr;
+  const int64_t nP = tc_transposed_rows(A);
+  Pool pool(st);
+  uint16_t* At = pool.alloc<uint16_t>((size_t)A->d * nP);
+  if (!pool.ok()) return cudaErrorMemoryAllocation;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (trace) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+  }
+  NYS_CUDA_TRY(tc_transpose(A, At, st));
+  if (trace) {
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    std::fprintf(stderr, "[nys]   tc %-18s %8.3f ms\n", "transpose A", ms);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  return tc_product<double, double>(A, At, nP, D, Om, m, 0.0, Y, st, trace);
+}
+
+cudaError_t tc_hmm_bf16(const nys_matrix* A, const uint16_t* At, const double* D, const float* X, int k, double rho,
+                        float* Y, cudaStream_t st) {
+  if (A->dtype != NYS_BF16 || k <= 0) return cudaErrorInvalidValue;
+  return tc_product<float, float>(A, At, tc_transposed_rows(A), D, X, k, rho, Y, st, false);
 }
 
 }  // namespace nys
