@@ -433,9 +433,9 @@ def extra_batched(args):
     """Batched forms (separate JSON line, not the headline metric):
     (i) a 64-point lasso regularisation path sharing one 50,000 x 4,000 FP32 matrix
         (decay (1+j)^-1), gamma log-spaced in [1e-3, 1] ||A^T b||_inf, rank 50, rho 100:
-        multi-RHS path vs 64 sequential single solves, same ADMM iterations; then the same
-        with a BF16 inner copy, whose k-column matvecs run on the tensor cores (also timed
-        with the CUDA-core matvec for comparison);
+        multi-RHS path (k-column matvecs on the tensor cores) vs 64 sequential single
+        solves, same ADMM iterations, also timed with the CUDA-core matvec; then the same
+        with a BF16 inner copy;
     (ii) 32 independent lasso instances, d uniform in [500, 8000] (seed 4), n = 10 d,
         FP32, rank 50: one graph launch vs 32 sequential device-loop solves."""
     from paper_2202_11599_gb300 import nysadmm as nx
@@ -478,17 +478,23 @@ def extra_batched(args):
                         "max_rel_diff_vs_single": dev_max})
         return res
 
-    path = {"n": n, "d": d, "k": kpath, "rank": s, "admm_iters": K, "A": "fp32 (CUDA-core multi-RHS matvec)"}
+    def cuda_core_time(inner):
+        os.environ["NYS_SKETCH_TC"] = "0"
+        try:
+            return run_path(inner, singles=False)["time_path_s"]
+        finally:
+            os.environ.pop("NYS_SKETCH_TC", None)
+
+    # FP32 storage: the k-column matvecs run on the tcgen05 tensor cores with A split once
+    # into three BF16 terms (six term products per K step)
+    path = {"n": n, "d": d, "k": kpath, "rank": s, "admm_iters": K, "A": "fp32 (tcgen05 multi-RHS matvec, 3-term split)"}
     path.update(run_path(None))
-    # BF16 inner copy: the k-column matvecs run on the tcgen05 tensor cores
+    path["time_path_cuda_cores_s"] = cuda_core_time(None)
+    # BF16 inner copy
     Mi = nx.Matrix(A32.to(torch.bfloat16))
     path_bf16 = {"A_inner": "bf16 (tcgen05 multi-RHS matvec)"}
     path_bf16.update(run_path(Mi))
-    os.environ["NYS_SKETCH_TC"] = "0"
-    try:
-        path_bf16["time_path_cuda_cores_s"] = run_path(Mi, singles=False)["time_path_s"]
-    finally:
-        os.environ.pop("NYS_SKETCH_TC", None)
+    path_bf16["time_path_cuda_cores_s"] = cuda_core_time(Mi)
     del A32, M, Mi, W
     torch.cuda.empty_cache()
     # (ii) uneven batch

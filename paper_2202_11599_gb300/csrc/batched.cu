@@ -186,19 +186,21 @@ nys_status batched_pcg_run(const PcgProblem& pb, const PrecondView& P, const C* 
   // BF16 storage: the k-column products run on the tensor cores (the same tcgen05 GEMMs
   // as the sketch, FP32 operand as three BF16 terms), with a transposed copy of A made
   // once for the whole solve
-  uint16_t* At = nullptr;
+  TcPrepared tcp;
+  bool use_tc = false;
   if constexpr (sizeof(C) == 4) {
     if (sketch_tc_supported(pb.A)) {
-      At = pool.alloc<uint16_t>((size_t)d * tc_transposed_rows(pb.A));
+      void* tcs = pool.alloc<unsigned char>(tc_prepare_bytes(pb.A));
       if (!pool.ok()) return NYS_ENOMEM;
-      if (tc_transpose(pb.A, At, st) != cudaSuccess) return NYS_ECUDA;
+      if (tc_prepare(pb.A, tcs, &tcp, st) != cudaSuccess) return NYS_ECUDA;
+      use_tc = true;
     }
   }
   // V = A^T (A P) + rho P for the k columns of P (reads A once)
   auto bmatvec = [&](const C* Pin, C* Vout) -> bool {
     if constexpr (sizeof(C) == 4) {
-      if (At) return tc_hmm_bf16(pb.A, At, pb.D, reinterpret_cast<const float*>(Pin), k, pb.rho,
-                                 reinterpret_cast<float*>(Vout), st) == cudaSuccess;
+      if (use_tc) return tc_hmm(pb.A, tcp, pb.D, reinterpret_cast<const float*>(Pin), k, pb.rho,
+                                reinterpret_cast<float*>(Vout), st) == cudaSuccess;
     }
     if (sketch_aw(pb.A, Pin, k, pb.D, Wn, st) != cudaSuccess) return false;
     int nz = 0;

@@ -115,7 +115,7 @@ nys_status sketch_panel(const nys_matrix* A, const double* D, double shift, cons
   Pool pool(st);
   const int64_t n = A->n, d = A->d;
   if (sketch_tc_supported(A)) {
-    NYS_CU(sketch_tc_bf16(A, D, Om, m, Y, st));
+    NYS_CU(sketch_tc(A, D, Om, m, Y, st));
     if (shift != 0.0) NYS_CU(axpy_panel(shift, Om, Y, d * m, st));
     return NYS_OK;
   }

@@ -94,17 +94,24 @@ cudaError_t sketch_aw(const nys_matrix* A, const void* Omega, int s, const doubl
 cudaError_t sketch_atw(const nys_matrix* A, const void* W, int s, double* Y, void* work,
                        size_t work_bytes, cudaStream_t st);
 size_t sketch_atw_work_bytes(const nys_matrix* A, int s);
-// Y (d x m, col-major FP64) = A^T diag(D) A Om on the tensor cores (tcgen05), BF16 storage.
+// Tensor-core (tcgen05) products for BF16 storage and for FP32 storage (split exactly into
+// three BF16 terms): tc_prepare builds the operands once (transposed copy of A; for FP32
+// also the terms) in caller-owned scratch of tc_prepare_bytes(A) bytes.
+struct TcPrepared {
+  int at = 1;                    // A terms: 1 (BF16) or 3 (FP32 split)
+  const uint16_t* A = nullptr;   // row-major terms, n x lda, term stride aterm
+  int64_t lda = 0, aterm = 0;
+  const uint16_t* At = nullptr;  // transposed terms, d x nP, term stride atterm
+  int64_t nP = 0, atterm = 0;
+};
 bool sketch_tc_supported(const nys_matrix* A);
-cudaError_t sketch_tc_bf16(const nys_matrix* A, const double* D, const double* Om, int m, double* Y,
-                           cudaStream_t st);
-// Tensor-core multi-RHS H-matvec for BF16 storage: Y (d x k) = A^T diag(D) A X + rho X, FP32
-// X and Y column-major; At is the transposed copy of A from tc_transpose (d x
-// tc_transposed_rows(A) BF16 elements, caller-owned).
-int64_t tc_transposed_rows(const nys_matrix* A);
-cudaError_t tc_transpose(const nys_matrix* A, uint16_t* At, cudaStream_t st);
-cudaError_t tc_hmm_bf16(const nys_matrix* A, const uint16_t* At, const double* D, const float* X, int k, double rho,
-                        float* Y, cudaStream_t st);
+size_t tc_prepare_bytes(const nys_matrix* A);
+cudaError_t tc_prepare(const nys_matrix* A, void* scratch, TcPrepared* prep, cudaStream_t st);
+// Y (d x m, col-major FP64) = A^T diag(D) A Om (the sketch of App. B) on the tensor cores.
+cudaError_t sketch_tc(const nys_matrix* A, const double* D, const double* Om, int m, double* Y, cudaStream_t st);
+// Y (d x k) = A^T diag(D) A X + rho X, FP32 X and Y column-major (multi-RHS H-matvec).
+cudaError_t tc_hmm(const nys_matrix* A, const TcPrepared& prep, const double* D, const float* X, int k, double rho,
+                   float* Y, cudaStream_t st);
 cudaError_t sketch_atw_partials(const nys_matrix* A, const void* W, int s, void* work, size_t work_bytes, int* nz_out,
                                 cudaStream_t st);
 // small dense GEMMs in compute type T (column-major)

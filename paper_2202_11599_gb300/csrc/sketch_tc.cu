@@ -47,8 +47,9 @@ constexpr uint32_t TC_LBO = 128;                 // K-direction core-matrix stri
 constexpr uint32_t TC_SBO = (TC_BK / 8) * 128;   // 8-row-group stride (bytes)
 
 struct TcArgs {
-  const uint16_t* A;     // row-major [Mrows][lda] BF16, K contiguous
+  const uint16_t* A;     // row-major [AT][Mrows][lda] BF16 terms, K contiguous
   int64_t lda, Mrows, Kvalid;
+  int64_t aterm;         // element stride between the A terms (AT = 3)
   const uint16_t* B;     // [TERMS][NP][ldb] BF16, K contiguous, zero outside the data
   int64_t ldb, bterm;
   int NP;                // MMA N (multiple of 16, <= 256)
@@ -138,8 +139,22 @@ __device__ __forceinline__ void split3(float x, uint16_t (&t)[3]) {
   t[2] = bf16_bits(r2);
 }
 
-template <int EPI>
+// AT = number of BF16 terms of the A operand: 1 (BF16 storage) or 3 (FP32 storage split
+// exactly into three BF16 terms).  With AT = 3 a K step issues the six MMAs a_i x b_j with
+// i + j <= 2 (0-based): the three dropped products are below 2^-24 of the result.
+template <int AT> constexpr int tc_npairs() { return AT == 1 ? 3 : 6; }
+// pair pr -> (A term, B term): AT = 1: (0,0) (0,1) (0,2); AT = 3: (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+template <int AT> __host__ __device__ constexpr int tc_pair_a(int pr) {
+  return AT == 1 ? 0 : (pr == 2 || pr == 4 ? 1 : (pr == 5 ? 2 : 0));
+}
+template <int AT> __host__ __device__ constexpr int tc_pair_b(int pr) {
+  return AT == 1 ? pr : (pr == 1 || pr == 4 ? 1 : (pr == 3 ? 2 : 0));
+}
+template <int AT> constexpr int tc_stages() { return AT == 1 ? TC_STAGES : 3; }
+
+template <int EPI, int AT>
 __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const TcArgs a) {
+  constexpr int TC_STAGES = tc_stages<AT>();
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mma_bar[TC_STAGES];
   __shared__ uint32_t tmem_slot;
@@ -150,7 +165,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const TcArgs a
   const int nkt = (int)max((int64_t)0, kt1 - kt0);
   const uint32_t a_bytes = TC_BM * TC_BK * 2;
   const uint32_t b_bytes = (uint32_t)a.NP * TC_BK * 2;
-  const uint32_t stage_bytes = a_bytes + TC_TERMS * b_bytes;
+  const uint32_t stage_bytes = AT * a_bytes + TC_TERMS * b_bytes;
   const uint32_t sbase = smem_u32(smem);
   const uint32_t lbo = a.desc_swap ? TC_SBO : TC_LBO, sbo = a.desc_swap ? TC_LBO : TC_SBO;
   const uint32_t idesc = mma_idesc_bf16(TC_BM, a.NP);
@@ -174,23 +189,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const TcArgs a
   auto load_stage = [&](int ktl, int stage) {
     const int64_t k0 = (kt0 + ktl) * TC_BK;
     const uint32_t st = sbase + (uint32_t)stage * stage_bytes;
-    for (int q = tid; q < TC_BM * 4; q += TC_THREADS) {
-      const int r8 = q & 7, c = (q >> 3) & 3, g = q >> 5;
+    for (int q = tid; q < AT * TC_BM * 4; q += TC_THREADS) {
+      const int ta = q / (TC_BM * 4), qa = q - ta * (TC_BM * 4);
+      const int r8 = qa & 7, c = (qa >> 3) & 3, g = qa >> 5;
       const int64_t row = m0 + g * 8 + r8, k = k0 + c * 8;
       uint32_t bytes = 0;
       const uint16_t* src = a.A;
       if (row < a.Mrows && k < a.Kvalid) {
         bytes = (uint32_t)min((int64_t)16, (a.Kvalid - k) * 2);
-        src = a.A + row * a.lda + k;
+        src = a.A + ta * a.aterm + row * a.lda + k;
       }
-      cp_async16(st + (uint32_t)q * 16u, src, bytes);
+      cp_async16(st + (uint32_t)ta * a_bytes + (uint32_t)qa * 16u, src, bytes);
     }
     const int per_term = a.NP * 4;
     for (int q = tid; q < TC_TERMS * per_term; q += TC_THREADS) {
       const int t = q / per_term, qq = q - t * per_term;
       const int r8 = qq & 7, c = (qq >> 3) & 3, g = qq >> 5;
       const uint16_t* src = a.B + t * a.bterm + (int64_t)(g * 8 + r8) * a.ldb + k0 + c * 8;
-      cp_async16(st + a_bytes + (uint32_t)t * b_bytes + (uint32_t)qq * 16u, src, 16u);
+      cp_async16(st + AT * a_bytes + (uint32_t)t * b_bytes + (uint32_t)qq * 16u, src, 16u);
     }
   };
 
@@ -209,11 +225,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const TcArgs a
       const uint32_t st = sbase + (uint32_t)stage * stage_bytes;
 #pragma unroll
       for (int kk = 0; kk < TC_BK / 16; ++kk) {
-        const uint64_t ad = smem_desc(st + kk * 256u, lbo, sbo);
 #pragma unroll
-        for (int t = 0; t < TC_TERMS; ++t) {
-          const uint64_t bd = smem_desc(st + a_bytes + (uint32_t)t * b_bytes + kk * 256u, lbo, sbo);
-          mma_bf16(tmem, ad, bd, idesc, (kt | kk | t) != 0 ? 1u : 0u);
+        for (int pr = 0; pr < tc_npairs<AT>(); ++pr) {
+          const uint64_t ad = smem_desc(st + (uint32_t)tc_pair_a<AT>(pr) * a_bytes + kk * 256u, lbo, sbo);
+          const uint64_t bd =
+              smem_desc(st + AT * a_bytes + (uint32_t)tc_pair_b<AT>(pr) * b_bytes + kk * 256u, lbo, sbo);
+          mma_bf16(tmem, ad, bd, idesc, (kt | kk | pr) != 0 ? 1u : 0u);
         }
       }
       mma_commit(&mma_bar[stage]);
@@ -388,36 +405,54 @@ int pick_slices(int64_t mtiles, int64_t ktiles, int sms) {
   return best;
 }
 
-template <int EPI>
+template <int EPI, int AT>
 cudaError_t launch_tc(const TcArgs& a, dim3 grid, cudaStream_t st) {
-  const size_t smem = (size_t)TC_STAGES * (TC_BM * TC_BK * 2 + (size_t)TC_TERMS * a.NP * TC_BK * 2);
+  constexpr int ST = tc_stages<AT>();
+  const size_t smem = (size_t)ST * (AT * TC_BM * TC_BK * 2 + (size_t)TC_TERMS * a.NP * TC_BK * 2);
   static bool attr = false;
   if (!attr) {
-    const size_t max_smem = (size_t)TC_STAGES * (TC_BM * TC_BK * 2 + (size_t)TC_TERMS * TC_NMAX * TC_BK * 2);
-    NYS_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t max_smem = (size_t)ST * (AT * TC_BM * TC_BK * 2 + (size_t)TC_TERMS * TC_NMAX * TC_BK * 2);
+    NYS_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<EPI, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)max_smem));
     attr = true;
   }
   count_launch();
-  sketch_tc_kernel<EPI><<<grid, TC_THREADS, smem, st>>>(a);
+  sketch_tc_kernel<EPI, AT><<<grid, TC_THREADS, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int EPI>
+cudaError_t launch_tc_at(int at, const TcArgs& a, dim3 grid, cudaStream_t st) {
+  return at == 3 ? launch_tc<EPI, 3>(a, grid, st) : launch_tc<EPI, 1>(a, grid, st);
+}
+
+// FP32 storage: A (n x lda, row-major) -> three BF16 terms As[t][i][j] (row stride ldS,
+// zero for j >= d) whose sum is the FP32 value exactly.
+__global__ void split_matrix_kernel(const float* __restrict__ A, int64_t n, int64_t d, int64_t lda, int64_t ldS,
+                                    uint16_t* __restrict__ As) {
+  const int64_t total = n * ldS;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / ldS, j = idx - i * ldS;
+    const float x = j < d ? A[i * lda + j] : 0.f;
+    uint16_t t3[3];
+    split3(x, t3);
+#pragma unroll
+    for (int t = 0; t < TC_TERMS; ++t) As[t * total + idx] = t3[t];
+  }
 }
 
 }  // namespace
 
-bool sketch_tc_supported(const nys_matrix* A) {
-  if (A->dtype != NYS_BF16) return false;
-  if (const char* env = std::getenv("NYS_SKETCH_TC")) return std::atoi(env) != 0;
-  return true;
-}
 
 namespace {
 // Y (d x m, column-major) = A^T diag(D) A X (+ rho X) on the tensor cores, given the
 // transposed copy At (d x nP) of A.  X and Y are FP64 (sketch) or FP32 (batched PCG).
 template <typename TX, typename TY>
-cudaError_t tc_product(const nys_matrix* A, const uint16_t* At, int64_t nP, const double* D, const TX* X, int m,
+cudaError_t tc_product(const nys_matrix* A, const TcPrepared& prep, const double* D, const TX* X, int m,
                        double rho, TY* Y, cudaStream_t st, bool trace) {
   const int64_t n = A->n, d = A->d;
+  const int64_t nP = prep.nP;
   const int64_t dP = (d + TC_BK - 1) / TC_BK * TC_BK;
   const int NPmax = std::min(TC_NMAX, (m + 15) / 16 * 16);
   const uint32_t swap = std::getenv("NYS_TC_DESC_SWAP") ? (uint32_t)std::atoi(std::getenv("NYS_TC_DESC_SWAP")) : 0u;
@@ -454,8 +489,9 @@ cudaError_t tc_product(const nys_matrix* A, const uint16_t* At, int64_t nP, cons
     if (c0 == 0) mark();
 
     TcArgs g1 = {};
-    g1.A = reinterpret_cast<const uint16_t*>(A->data);
-    g1.lda = A->ld;
+    g1.A = prep.A;
+    g1.lda = prep.lda;
+    g1.aterm = prep.aterm;
     g1.Mrows = n;
     g1.Kvalid = d;
     g1.B = Ot;
@@ -471,12 +507,13 @@ cudaError_t tc_product(const nys_matrix* A, const uint16_t* At, int64_t nP, cons
     g1.wrows = nP;
     g1.desc_swap = swap;
     g1.status = status;
-    NYS_CUDA_TRY(launch_tc<0>(g1, dim3((unsigned)((n + TC_BM - 1) / TC_BM), 1), st));
+    NYS_CUDA_TRY(launch_tc_at<0>(prep.at, g1, dim3((unsigned)((n + TC_BM - 1) / TC_BM), 1), st));
     if (c0 == 0) mark();
 
     TcArgs g2 = {};
-    g2.A = At;
+    g2.A = prep.At;
     g2.lda = nP;
+    g2.aterm = prep.atterm;
     g2.Mrows = d;
     g2.Kvalid = nP;
     g2.B = Wt;
@@ -489,7 +526,7 @@ cudaError_t tc_product(const nys_matrix* A, const uint16_t* At, int64_t nP, cons
     g2.ldp = d;
     g2.desc_swap = swap;
     g2.status = status;
-    NYS_CUDA_TRY(launch_tc<1>(g2, dim3((unsigned)mt2, (unsigned)Zeff), st));
+    NYS_CUDA_TRY(launch_tc_at<1>(prep.at, g2, dim3((unsigned)mt2, (unsigned)Zeff), st));
     if (c0 == 0) mark();
 
     count_launch();
@@ -516,24 +553,66 @@ cudaError_t tc_product(const nys_matrix* A, const uint16_t* At, int64_t nP, cons
 }
 }  // namespace
 
-int64_t tc_transposed_rows(const nys_matrix* A) { return (A->n + TC_BK - 1) / TC_BK * TC_BK; }
-
-cudaError_t tc_transpose(const nys_matrix* A, uint16_t* At, cudaStream_t st) {
-  if (A->dtype != NYS_BF16) return cudaErrorInvalidValue;
-  const int64_t nP = tc_transposed_rows(A);
-  count_launch();
-  transpose_bf16_kernel<<<dim3((unsigned)((nP + 63) / 64), (unsigned)((A->d + 63) / 64)), 256, 0, st>>>(
-      reinterpret_cast<const uint16_t*>(A->data), A->n, A->d, A->ld, At, nP);
-  return cudaGetLastError();
+bool sketch_tc_supported(const nys_matrix* A) {
+  if (A->dtype != NYS_BF16 && A->dtype != NYS_F32) return false;
+  if (const char* env = std::getenv("NYS_SKETCH_TC")) return std::atoi(env) != 0;
+  return true;
 }
 
-cudaError_t sketch_tc_bf16(const nys_matrix* A, const double* D, const double* Om, int m, double* Y,
-                           cudaStream_t st) {
-  if (A->dtype != NYS_BF16 || m <= 0) return cudaErrorInvalidValue;
+// Scratch of the prepared operands: BF16 storage keeps A itself and adds the transposed
+// copy (d x nP); FP32 storage adds its three BF16 terms (n x ldS each) and their
+// transposes (d x nP each).
+size_t tc_prepare_bytes(const nys_matrix* A) {
+  const int64_t nP = (A->n + TC_BK - 1) / TC_BK * TC_BK;
+  const int64_t ldS = (A->d + 7) / 8 * 8;
+  if (A->dtype == NYS_BF16) return (size_t)A->d * nP * 2;
+  return (size_t)TC_TERMS * ((size_t)A->n * ldS + (size_t)A->d * nP) * 2;
+}
+
+cudaError_t tc_prepare(const nys_matrix* A, void* scratch, TcPrepared* prep, cudaStream_t st) {
+  const int64_t n = A->n, d = A->d;
+  const int64_t nP = (n + TC_BK - 1) / TC_BK * TC_BK;
+  const dim3 tgrid((unsigned)((nP + 63) / 64), (unsigned)((d + 63) / 64));
+  uint16_t* buf = reinterpret_cast<uint16_t*>(scratch);
+  prep->nP = nP;
+  if (A->dtype == NYS_BF16) {
+    prep->at = 1;
+    prep->A = reinterpret_cast<const uint16_t*>(A->data);
+    prep->lda = A->ld;
+    prep->aterm = 0;
+    prep->At = buf;
+    prep->atterm = 0;
+    count_launch();
+    transpose_bf16_kernel<<<tgrid, 256, 0, st>>>(reinterpret_cast<const uint16_t*>(A->data), n, d, A->ld, buf, nP);
+    return cudaGetLastError();
+  }
+  if (A->dtype != NYS_F32) return cudaErrorInvalidValue;
+  const int64_t ldS = (d + 7) / 8 * 8;
+  uint16_t* As = buf;
+  uint16_t* Ats = buf + (size_t)TC_TERMS * n * ldS;
+  prep->at = 3;
+  prep->A = As;
+  prep->lda = ldS;
+  prep->aterm = n * ldS;
+  prep->At = Ats;
+  prep->atterm = d * nP;
+  count_launch();
+  split_matrix_kernel<<<(unsigned)std::min<int64_t>(8192, (n * ldS + 255) / 256), 256, 0, st>>>(
+      reinterpret_cast<const float*>(A->data), n, d, A->ld, ldS, As);
+  NYS_CUDA_TRY(cudaGetLastError());
+  for (int t = 0; t < TC_TERMS; ++t) {
+    count_launch();
+    transpose_bf16_kernel<<<tgrid, 256, 0, st>>>(As + (size_t)t * n * ldS, n, d, ldS, Ats + (size_t)t * d * nP, nP);
+    NYS_CUDA_TRY(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
+cudaError_t sketch_tc(const nys_matrix* A, const double* D, const double* Om, int m, double* Y, cudaStream_t st) {
+  if ((A->dtype != NYS_BF16 && A->dtype != NYS_F32) || m <= 0) return cudaErrorInvalidValue;
   const bool trace = std::getenv("NYS_TRACE") != nullptr;
-  const int64_t nP = tc_transposed_rows(A);
   Pool pool(st);
-  uint16_t* At = pool.alloc<uint16_t>((size_t)A->d * nP);
+  void* scratch = pool.alloc<unsigned char>(tc_prepare_bytes(A));
   if (!pool.ok()) return cudaErrorMemoryAllocation;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (trace) {
@@ -541,23 +620,24 @@ cudaError_t sketch_tc_bf16(const nys_matrix* A, const double* D, const double* O
     cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
   }
-  NYS_CUDA_TRY(tc_transpose(A, At, st));
+  TcPrepared prep;
+  NYS_CUDA_TRY(tc_prepare(A, scratch, &prep, st));
   if (trace) {
     cudaEventRecord(e1, st);
     cudaEventSynchronize(e1);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    std::fprintf(stderr, "[nys]   tc %-18s %8.3f ms\n", "transpose A", ms);
+    std::fprintf(stderr, "[nys]   tc %-18s %8.3f ms\n", "prepare A", ms);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
-  return tc_product<double, double>(A, At, nP, D, Om, m, 0.0, Y, st, trace);
+  return tc_product<double, double>(A, prep, D, Om, m, 0.0, Y, st, trace);
 }
 
-cudaError_t tc_hmm_bf16(const nys_matrix* A, const uint16_t* At, const double* D, const float* X, int k, double rho,
-                        float* Y, cudaStream_t st) {
-  if (A->dtype != NYS_BF16 || k <= 0) return cudaErrorInvalidValue;
-  return tc_product<float, float>(A, At, tc_transposed_rows(A), D, X, k, rho, Y, st, false);
+cudaError_t tc_hmm(const nys_matrix* A, const TcPrepared& prep, const double* D, const float* X, int k, double rho,
+                   float* Y, cudaStream_t st) {
+  if (k <= 0) return cudaErrorInvalidValue;
+  return tc_product<float, float>(A, prep, D, X, k, rho, Y, st, false);
 }
 
 }  // namespace nys
