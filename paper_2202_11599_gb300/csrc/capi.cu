@@ -109,13 +109,15 @@ nys_status cholqr2(double* Om, int64_t d, int m, cudaStream_t st) {
 }
 
 // Y (d x m, FP64) = (A^T diag(D) A + shift I) Om for an FP64 orthonormal panel Om.
+// prep: tensor-core operands of A prepared once by the caller (repeated sketches of the
+// same matrix), or NULL.
 nys_status sketch_panel(const nys_matrix* A, const double* D, double shift, const double* Om, int m, double* Y,
-                        cudaStream_t st) {
+                        cudaStream_t st, const TcPrepared* prep = nullptr) {
   PhaseTimer pt("sketch Y = H Omega", st);
   Pool pool(st);
   const int64_t n = A->n, d = A->d;
   if (sketch_tc_supported(A)) {
-    NYS_CU(sketch_tc(A, D, Om, m, Y, st));
+    NYS_CU(prep ? sketch_tc_with(A, *prep, D, Om, m, Y, st) : sketch_tc(A, D, Om, m, Y, st));
     if (shift != 0.0) NYS_CU(axpy_panel(shift, Om, Y, d * m, st));
     return NYS_OK;
   }
@@ -833,6 +835,16 @@ nys_status logistic_admm(const nys_matrix* A, const nys_matrix* Ain, const doubl
   int total_pcg = 0, cur_rank = 0;
   nys_status result = NYS_OK;
   std::vector<int> block_end;  // orthonormalised block boundaries
+  // the curvature D changes every iteration but A does not: prepare its tensor-core
+  // operands once for all re-sketches
+  TcPrepared tcp;
+  const TcPrepared* tcpp = nullptr;
+  if (sketch_tc_supported(Ain)) {
+    void* tcs = pool.alloc<unsigned char>(tc_prepare_bytes(Ain));
+    if (!pool.ok()) return NYS_ENOMEM;
+    NYS_CU(tc_prepare(Ain, tcs, &tcp, st));
+    tcpp = &tcp;
+  }
   int k = 0;
   for (; k < K; ++k) {
     // t = A x~, w, and the right-hand side A^T (w t + b01 - sigma(t)) in one pass (Sec. 3.2)
@@ -849,7 +861,7 @@ nys_status logistic_admm(const nys_matrix* A, const nys_matrix* Ain, const doubl
       int s0 = rank, m = rank, used = 0;
       for (;;) {
         NYS_TRY(cholqr2(Om + (int64_t)used * d, d, m, st));
-        NYS_TRY(sketch_panel(Ain, Dw, 0.0, Om + (int64_t)used * d, m, Y + (int64_t)used * d, st));
+        NYS_TRY(sketch_panel(Ain, Dw, 0.0, Om + (int64_t)used * d, m, Y + (int64_t)used * d, st, tcpp));
         used += m;
         block_end.push_back(used);
         NYS_TRY(precond_from_panels(Om, Y, d, used, shs, mant_bits_of(Ain), &P, st));
@@ -861,7 +873,7 @@ nys_status logistic_admm(const nys_matrix* A, const nys_matrix* Ain, const doubl
           m = smax - s0;
           if (m > 0) {
             NYS_TRY(cholqr2(Om + (int64_t)used * d, d, m, st));
-            NYS_TRY(sketch_panel(Ain, Dw, 0.0, Om + (int64_t)used * d, m, Y + (int64_t)used * d, st));
+            NYS_TRY(sketch_panel(Ain, Dw, 0.0, Om + (int64_t)used * d, m, Y + (int64_t)used * d, st, tcpp));
             used += m;
             block_end.push_back(used);
             NYS_TRY(precond_from_panels(Om, Y, d, used, shs, mant_bits_of(Ain), &P, st));
@@ -872,7 +884,7 @@ nys_status logistic_admm(const nys_matrix* A, const nys_matrix* Ain, const doubl
       cur_rank = used;
     } else if (o.resketch_every > 0 && k % o.resketch_every == 0) {
       // same orthonormal blocks, new curvature D
-      NYS_TRY(sketch_panel(Ain, Dw, 0.0, Om, cur_rank, Y, st));
+      NYS_TRY(sketch_panel(Ain, Dw, 0.0, Om, cur_rank, Y, st, tcpp));
       NYS_TRY(precond_from_panels(Om, Y, d, cur_rank, shs, mant_bits_of(Ain), &P, st));
     }
     PrecondView view;

@@ -109,6 +109,8 @@ size_t tc_prepare_bytes(const nys_matrix* A);
 cudaError_t tc_prepare(const nys_matrix* A, void* scratch, TcPrepared* prep, cudaStream_t st);
 // Y (d x m, col-major FP64) = A^T diag(D) A Om (the sketch of App. B) on the tensor cores.
 cudaError_t sketch_tc(const nys_matrix* A, const double* D, const double* Om, int m, double* Y, cudaStream_t st);
+cudaError_t sketch_tc_with(const nys_matrix* A, const TcPrepared& prep, const double* D, const double* Om, int m,
+                           double* Y, cudaStream_t st);
 // Y (d x k) = A^T diag(D) A X + rho X, FP32 X and Y column-major (multi-RHS H-matvec).
 cudaError_t tc_hmm(const nys_matrix* A, const TcPrepared& prep, const double* D, const float* X, int k, double rho,
                    float* Y, cudaStream_t st);

@@ -634,6 +634,12 @@ cudaError_t sketch_tc(const nys_matrix* A, const double* D, const double* Om, in
   return tc_product<double, double>(A, prep, D, Om, m, 0.0, Y, st, trace);
 }
 
+cudaError_t sketch_tc_with(const nys_matrix* A, const TcPrepared& prep, const double* D, const double* Om, int m,
+                           double* Y, cudaStream_t st) {
+  if (m <= 0) return cudaErrorInvalidValue;
+  return tc_product<double, double>(A, prep, D, Om, m, 0.0, Y, st, std::getenv("NYS_TRACE") != nullptr);
+}
+
 cudaError_t tc_hmm(const nys_matrix* A, const TcPrepared& prep, const double* D, const float* X, int k, double rho,
                    float* Y, cudaStream_t st) {
   if (k <= 0) return cudaErrorInvalidValue;
