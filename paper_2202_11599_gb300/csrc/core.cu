@@ -214,7 +214,64 @@ __global__ void __launch_bounds__(1024) chol_upper_kernel(double* M, int s, int*
   }
 }
 
+// Same algorithm and operation order with the upper triangle held in shared memory
+// (packed by columns: (i, c), i <= c, at c (c + 1) / 2 + i), so that every step's
+// pivot, row scaling and trailing update touch on-chip data instead of L2.
+__global__ void __launch_bounds__(1024) chol_upper_smem_kernel(double* M, int s, int* info) {
+  extern __shared__ double up[];
+  const int tid = threadIdx.x, T = blockDim.x;
+  __shared__ int bad;
+  auto at = [](int i, int c) { return c * (c + 1) / 2 + i; };
+  for (int64_t idx = tid; idx < (int64_t)s * s; idx += T) {
+    const int i = (int)(idx % s), j = (int)(idx / s);
+    if (i < j) up[at(i, j)] = 0.5 * (M[i + (int64_t)j * s] + M[j + (int64_t)i * s]);
+    else if (i == j) up[at(i, i)] = M[i + (int64_t)i * s];
+  }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < s; ++j) {
+    if (tid == 0) {
+      const double dj = up[at(j, j)];
+      if (!(dj > 0.0) || !isfinite(dj)) {
+        bad = j + 1;
+      } else {
+        up[at(j, j)] = sqrt(dj);
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const double piv = up[at(j, j)];
+    for (int c = j + 1 + tid; c < s; c += T) up[at(j, c)] /= piv;
+    __syncthreads();
+    // trailing update of the upper triangle: M[i][c] -= C[j][i] C[j][c], j < i <= c
+    const int w = s - j - 1;
+    for (int64_t idx = tid; idx < (int64_t)w * w; idx += T) {
+      const int i = (int)(idx % w), c = (int)(idx / w);
+      if (i > c) continue;
+      const int ii = j + 1 + i, cc = j + 1 + c;
+      up[at(ii, cc)] -= up[at(j, ii)] * up[at(j, cc)];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) *info = bad;
+  for (int64_t idx = tid; idx < (int64_t)s * s; idx += T) {
+    const int i = (int)(idx % s), j = (int)(idx / s);
+    M[idx] = i <= j ? up[at(i, j)] : 0.0;
+  }
+}
+
 cudaError_t chol_upper(double* M, int s, int* info, cudaStream_t st) {
+  const size_t smem = (size_t)s * (s + 1) / 2 * sizeof(double);
+  if (smem <= 200 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      NYS_CUDA_TRY(cudaFuncSetAttribute(chol_upper_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr = true;
+    }
+    count_launch();
+    chol_upper_smem_kernel<<<1, 1024, smem, st>>>(M, s, info);
+    return cudaGetLastError();
+  }
   count_launch();
   chol_upper_kernel<<<1, 1024, 0, st>>>(M, s, info);
   return cudaGetLastError();
@@ -233,7 +290,38 @@ __global__ void trsm_ru_kernel(const double* __restrict__ Cm, int s, double* Y, 
   }
 }
 
+// Same recurrence and order, 64 rows per block (d = 10,000 rows spread over ~160 SMs
+// instead of 79) with each row's solved prefix b_0 .. b_{c-1} kept in shared memory
+// ([k][64], conflict-free) instead of re-read from global memory.
+constexpr int kTrsmRows = 64;
+__global__ void __launch_bounds__(kTrsmRows) trsm_ru_smem_kernel(const double* __restrict__ Cm, int s, double* Y,
+                                                                 int64_t d) {
+  extern __shared__ double bs[];  // [s][kTrsmRows]
+  const int t = threadIdx.x;
+  const int64_t j = blockIdx.x * (int64_t)kTrsmRows + t;
+  const bool act = j < d;
+  for (int c = 0; c < s; ++c) {
+    double acc = act ? Y[j + (int64_t)c * d] : 0.0;
+    const double* col = Cm + (int64_t)c * s;
+    for (int k = 0; k < c; ++k) acc = fma(-bs[k * kTrsmRows + t], col[k], acc);
+    const double b = acc / col[c];
+    bs[c * kTrsmRows + t] = b;
+    if (act) Y[j + (int64_t)c * d] = b;
+  }
+}
+
 cudaError_t trsm_right_upper(const double* C, int s, double* Y, int64_t d, cudaStream_t st) {
+  const size_t smem = (size_t)s * kTrsmRows * sizeof(double);
+  if (smem <= 200 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      NYS_CUDA_TRY(cudaFuncSetAttribute(trsm_ru_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr = true;
+    }
+    count_launch();
+    trsm_ru_smem_kernel<<<(unsigned)((d + kTrsmRows - 1) / kTrsmRows), kTrsmRows, smem, st>>>(C, s, Y, d);
+    return cudaGetLastError();
+  }
   count_launch();
   trsm_ru_kernel<<<(unsigned)((d + 127) / 128), 128, 0, st>>>(C, s, Y, d);
   return cudaGetLastError();
