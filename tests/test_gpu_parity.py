@@ -62,6 +62,27 @@ def test_hmatvec_matches_definition(dtype, n, d):
         assert np.max(np.abs(y - ref) / (scale + 1e-300)) <= tol
 
 
+@pytest.mark.parametrize("n,d", [(20000, 4000), (12000, 9999), (10000, 2049)])
+def test_hmatvec_bf16_wide_rows(n, d):
+    """BF16 pass on wide rows (640-thread CTA shapes and a ragged d), with and without D:
+    the bar of the other shapes against the FP64 definition, bitwise repeatable."""
+    rng = np.random.default_rng(n + d)
+    A = rng.standard_normal((n, d)) * gen.column_scales(d, 0.5)[None, :]
+    Aq = _quantised(A, torch.bfloat16)
+    p = rng.standard_normal(d)
+    Dv = rng.random(n) + 0.1
+    M = nx.Matrix.padded(_dev(A), torch.bfloat16)
+    pq = torch.from_numpy(p).float().double().numpy()
+    for D in (None, Dv):
+        y = nx.hmatvec(M, _dev(pq), 0.37, None if D is None else _dev(D))
+        y2 = nx.hmatvec(M, _dev(pq), 0.37, None if D is None else _dev(D))
+        assert torch.equal(y, y2)
+        w = np.ones(n) if D is None else D
+        ref = Aq.T @ (w * (Aq @ pq)) + 0.37 * pq
+        scale = np.abs(Aq).T @ (w * (np.abs(Aq) @ np.abs(pq))) + 0.37 * np.abs(pq)
+        assert np.max(np.abs(y.double().cpu().numpy() - ref) / scale) <= 2e-5
+
+
 def test_hmatvec_deterministic():
     rng = np.random.default_rng(5)
     A = rng.standard_normal((20000, 700))
