@@ -531,6 +531,60 @@ def extra_batched(args):
     print(json.dumps({"extra": "batched", "path": path, "path_bf16": path_bf16, "uneven_batch": batch}), flush=True)
 
 
+def extra_fp8(args):
+    """FP8 variant of the mixed form (separate JSON line, not the headline metric): the
+    100,000 x 10,000 lasso with the PCG matrix stored as FP8 E4M3 codes and one FP32 scale
+    per column.  Reports the fused pass on FP8 against BF16 (device time, algorithmic
+    GB/s) and the relative objective gap F(z_k)/F* - 1 the FP8 solve reaches after K
+    iterations (F* from the FP64-exact refined run, as in the main line)."""
+    from paper_2202_11599_gb300 import nysadmm as nx
+    import __graft_entry__
+    __graft_entry__.build()
+    w = make_workload()
+    A64 = w["A32"].double()
+    M64 = nx.Matrix(A64)
+    Mbf = nx.Matrix(w["A32"].to(torch.bfloat16))
+    M8 = nx.Matrix.fp8(w["A32"])
+    b, gamma, Om, rho, s = w["b"], w["gamma"], w["Omega"], w["rho"], w["s"]
+    # fused pass: FP8 vs BF16
+    p = torch.randn(w["d"], device="cuda", dtype=torch.float32)
+    passes = {}
+    for name, M in (("fp8", M8), ("bf16", Mbf)):
+        for _ in range(3):
+            nx.hmatvec(M, p, rho)
+        torch.cuda.synchronize()
+        nx.stats_enable(True)
+        for _ in range(20):
+            nx.hmatvec(M, p, rho)
+        torch.cuda.synchronize()
+        st = nx.stats_read()["apass"][name]
+        nx.stats_enable(False)
+        ms = st["ms"] / st["launches"]
+        passes[name] = {"ms": round(ms, 4), "GBps": round(st["bytes"] / st["launches"] / (ms * 1e-3) / 1e9, 1),
+                        "algorithmic_bytes": st["bytes"] / st["launches"]}
+
+    def F(z):
+        return nx.objective("lasso", M64, b, gamma, z)[0]
+
+    ref = nx.nysadmm_solve("lasso", M64, b, gamma, rho, s, 1e-6, Om, admm_iters=args.fstar_iters,
+                           A_inner=nx.Matrix(w["A32"]), refine=True, z_trace=True)
+    zt = ref["z_trace"]
+    Fstar = min(F(zt[k]) for k in list(range(max(0, zt.shape[0] - 400), zt.shape[0], 10)) + [zt.shape[0] - 1])
+    del ref, zt
+    K = args.extra_iters if args.extra_iters > 100 else 1500
+    gaps = {}
+    for name, M in (("fp8", M8), ("bf16", Mbf)):
+        out = nx.nysadmm_solve("lasso", M64, b, gamma, rho, s, w["pcg_tol"], Om, admm_iters=K, A_inner=M,
+                               refine=False, z_trace=True, hx_refresh=args.hx_refresh)
+        zt = out["z_trace"]
+        marks = [k for k in (99, 299, 609, 999, K - 1) if k < zt.shape[0]]
+        gaps[name] = {str(k + 1): (F(zt[k]) - Fstar) / Fstar for k in marks}
+        gaps[name]["min_over_run"] = min((F(zt[k]) - Fstar) / Fstar for k in range(9, zt.shape[0], 10))
+        del out, zt
+    print(json.dumps({"extra": "fp8", "workload": WORKLOAD_NAME, "fused_pass": passes, "F_star": Fstar,
+                      "admm_iters": K, "rel_gap_after_k": gaps}), flush=True)
+
+
 def extra_logistic(args):
     """l1-logistic regression (Sec. 3.2) at the size of the logistic configuration:
     A = N(0, 1/d) diag((1+j)^-1/2), 200,000 x 5,000 (FP64 problem matrix, FP32 copy for
@@ -652,7 +706,7 @@ def main():
                     help="only run the tensor-core sketch on a 50000 x 10000 BF16 matrix (ncu capture case)")
     ap.add_argument("--host-loop", action="store_true",
                     help="run the ADMM loop from the host (kernel launches that ncu can list one by one)")
-    ap.add_argument("--extra", choices=["batched", "logistic"], default=None,
+    ap.add_argument("--extra", choices=["batched", "logistic", "fp8"], default=None,
                     help="run a secondary workload and print its own JSON line")
     ap.add_argument("--extra-iters", type=int, default=100)
     ap.add_argument("--no-plain", action="store_true")
@@ -663,6 +717,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.extra == "batched":
         extra_batched(args)
+    elif args.extra == "fp8":
+        extra_fp8(args)
     elif args.extra == "logistic":
         extra_logistic(args)
     elif args.profile_apass:

@@ -21,7 +21,8 @@
  *    copies).  Entries j in [d, ld) are never read as data.
  *  - d x s panels (Omega, U) are COLUMN-major with leading dimension d.
  *  - Vector precision ("compute type") follows the matrix that PCG runs on:
- *    FP64 vectors for an NYS_F64 matrix, FP32 vectors for NYS_F32 / NYS_BF16.
+ *    FP64 vectors for an NYS_F64 matrix, FP32 vectors for NYS_F32 / NYS_BF16 /
+ *    NYS_FP8E4M3.
  *    ADMM state (x, z, u, residuals) is always FP64.
  *  - Errors are returned, never trapped: NYS_EINVAL for bad arguments (checked
  *    before any launch), NYS_ENOTSPD if the Nystrom core matrix stays
@@ -59,7 +60,11 @@ typedef enum {
  * regression (Eq. 9 with labels b in {-1,+1} mapped to (1+b)/2). */
 typedef enum { NYS_LASSO = 0, NYS_LOGISTIC = 1 } nys_loss;
 
-typedef enum { NYS_F64 = 0, NYS_F32 = 1, NYS_BF16 = 2 } nys_dtype;
+/* Storage of A.  NYS_FP8E4M3: 8-bit E4M3 codes q with one FP32 scale per column,
+ * A_ij = col_scale[j] * q_ij (the per-column-scaled FP8 form of the mixed precision
+ * variant); accepted where A is the matrix PCG runs on (nys_hmatvec, nys_sketch,
+ * pcg_solve, opts->A_inner of nysadmm_solve), with FP32 vectors. */
+typedef enum { NYS_F64 = 0, NYS_F32 = 1, NYS_BF16 = 2, NYS_FP8E4M3 = 3 } nys_dtype;
 
 /* PCG stopping test at the top of each iteration (Alg. Nystrom PCG):
  * REL: ||w|| <= tol ||r||;  ABS: ||w|| <= tol (as printed);
@@ -68,9 +73,10 @@ typedef enum { NYS_F64 = 0, NYS_F32 = 1, NYS_BF16 = 2 } nys_dtype;
 typedef enum { NYS_TOL_REL = 0, NYS_TOL_ABS = 1, NYS_TOL_SQRT_RPRD = 2 } nys_tol_mode;
 
 typedef struct {
-  const void* data;  /* device, row-major n x ld, 16-byte aligned */
-  int32_t dtype;     /* nys_dtype */
+  const void* data;        /* device, row-major n x ld, 16-byte aligned */
+  int32_t dtype;           /* nys_dtype */
   int64_t n, d, ld;
+  const float* col_scale;  /* NYS_FP8E4M3: device, length d; NULL for the other types */
 } nys_matrix;
 
 /* Opaque Nystrom preconditioner: U (d x s, orthonormal columns), the
@@ -252,18 +258,18 @@ nys_status nys_objective(int32_t loss, const nys_matrix* A, const double* b, dou
  * n*d*sizeof(element) for A plus the vectors read and the partials written. */
 typedef struct {
   int64_t launches;           /* kernel launches since the last enable */
-  int64_t apass_launches[3];  /* fused A-pass launches that ran (a launch issued after
+  int64_t apass_launches[4];  /* fused A-pass launches that ran (a launch issued after
                                  PCG converged returns at once and is not counted),
                                  by nys_dtype of A */
-  double apass_ms[3];         /* summed device time of those launches (ms) */
-  double apass_bytes[3];      /* summed algorithmic bytes of those launches */
+  double apass_ms[4];         /* summed device time of those launches (ms) */
+  double apass_bytes[4];      /* summed algorithmic bytes of those launches */
   /* The same quantities from the kernels' own %globaltimer stamps (earliest CTA
    * start to latest CTA end of each launch).  These also cover passes launched
    * inside the device-side solve loop (a CUDA graph), where no event can
    * bracket an individual kernel. */
-  int64_t dev_launches[3];
-  double dev_ms[3];
-  double dev_bytes[3];
+  int64_t dev_launches[4];
+  double dev_ms[4];
+  double dev_bytes[4];
 } nys_stats;
 
 void nys_stats_enable(int32_t on);

@@ -19,6 +19,8 @@
 //     status;
 //   * per-CTA partials go to a [grid x d] buffer that a second kernel sums in a
 //     fixed order (deterministic, run-to-run bitwise identical) and adds rho p.
+#include <cuda_fp8.h>
+
 #include "device_util.cuh"
 #include "nys_internal.cuh"
 
@@ -53,6 +55,7 @@ struct ApassKArgs {
   int* executed;  // instrumentation: set to 1 by CTA 0 when the pass ran (not skipped)
   DevTimer tm;    // instrumentation: in-kernel launch timing (null pointers when off)
   double bytes_alg;
+  const float* col_scale;  // FP8: p is read as col_scale o p (the reduce scales the sums)
 };
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -319,6 +322,16 @@ __device__ __forceinline__ float2 unpack_pair<NYS_BF16>(const uint4& r, int q) {
   return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
 }
 
+// FP8 E4M3: 16-bit half (q & 1) of word q / 2 holds elements 2q and 2q + 1 (the per-column
+// scales are folded into p and into the final sum, so only the codes are decoded here).
+template <>
+__device__ __forceinline__ float2 unpack_pair<NYS_FP8E4M3>(const uint4& r, int q) {
+  const unsigned w = (q >> 1) == 0 ? r.x : ((q >> 1) == 1 ? r.y : ((q >> 1) == 2 ? r.z : r.w));
+  const __nv_fp8x2_storage_t pair = (__nv_fp8x2_storage_t)((q & 1) ? (w >> 16) : (w & 0xffffu));
+  const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2(pair, __NV_E4M3);
+  return __half22float2(*reinterpret_cast<const __half2*>(&h));
+}
+
 // Zero the stored elements of a 16-byte vector from element index `keep` on.
 template <int DT>
 __device__ __forceinline__ void mask_tail(uint4& r, int keep) {
@@ -329,6 +342,10 @@ __device__ __forceinline__ void mask_tail(uint4& r, int keep) {
     const int first = i * 4 / ESZ;  // first element index held by word i
     if (ESZ == 4) {
       if (first >= keep) w[i] = 0u;
+    } else if (ESZ == 1) {  // four 8-bit elements per word
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (first + b >= keep) w[i] &= ~(0xffu << (8 * b));
     } else {  // two 16-bit elements per word
       if (first >= keep) w[i] = 0u;
       else if (first + 1 >= keep) w[i] &= 0x0000ffffu;
@@ -435,6 +452,10 @@ __global__ void __launch_bounds__(T, 1) apass_f_kernel(const ApassKArgs a) {
       if (!nodot && v < nvec) {
         if (j < a.d) x0 = p[j];
         if (j + 1 < a.d) x1 = p[j + 1];
+        if (DT == NYS_FP8E4M3) {  // A_ij = s_j q_ij: a_i . p = q_i . (s o p)
+          if (j < a.d) x0 *= a.col_scale[j];
+          if (j + 1 < a.d) x1 *= a.col_scale[j + 1];
+        }
       }
       pr[kk][q] = make_float2(x0, x1);
       acc[kk][q] = make_float2(0.f, 0.f);
@@ -602,7 +623,8 @@ template <typename C>
 __global__ void __launch_bounds__(kVecThreads) apass_reduce_kernel(const C* __restrict__ partial, int G,
                                                                    int64_t d, int64_t dpad, C rho,
                                                                    const C* __restrict__ p, C* __restrict__ y,
-                                                                   double* dot_part, const int* skip) {
+                                                                   double* dot_part, const int* skip,
+                                                                   const float* __restrict__ cscale) {
   if (skip && *skip) return;
   __shared__ double sh[kVecThreads / 32];
   double dacc = 0.0;
@@ -611,6 +633,7 @@ __global__ void __launch_bounds__(kVecThreads) apass_reduce_kernel(const C* __re
     // fixed order over the CTAs' partials; the unroll keeps 16 loads in flight
 #pragma unroll 16
     for (int g = 0; g < G; ++g) s += partial[(int64_t)g * dpad + j];
+    if (cscale) s *= (C)cscale[j];  // FP8: sum_i q_ij u_i -> sum_i A_ij u_i
     const C pj = p ? p[j] : C(0);
     const C yj = fma(rho, pj, s);
     y[j] = yj;
@@ -877,6 +900,7 @@ cudaError_t apass_run(const ApassArgs& a, const ApassPlan& plan, void* partial, 
   k.status = dev_status;
   k.skip = a.skip;
   k.executed = nullptr;
+  k.col_scale = a.col_scale;
   {
     const double esz = (double)dtype_size(a.dtype), csz = compute_is_f64(a.dtype) ? 8.0 : 4.0;
     double bytes = (double)a.n * (double)a.d * esz + (double)a.d * csz + (double)plan.grid * a.d * csz;
@@ -899,6 +923,7 @@ cudaError_t apass_run(const ApassArgs& a, const ApassPlan& plan, void* partial, 
     case NYS_F64: err = launch_dt<NYS_F64>(k, plan, st); break;
     case NYS_F32: err = launch_float<NYS_F32>(k, plan, st); break;
     case NYS_BF16: err = launch_float<NYS_BF16>(k, plan, st); break;
+    case NYS_FP8E4M3: err = launch_float<NYS_FP8E4M3>(k, plan, st); break;
     default: err = cudaErrorInvalidValue;
   }
   if (prof && err == cudaSuccess) {
@@ -916,6 +941,7 @@ cudaError_t apass_prepare(const nys_matrix* A, const ApassPlan& plan) {
   a.d = A->d;
   a.ld = A->ld;
   a.dtype = A->dtype;
+  a.col_scale = A->col_scale;
   a.p = nullptr;
   a.D = nullptr;
   a.b = nullptr;
@@ -935,12 +961,13 @@ cudaError_t apass_reduce(const ApassArgs& a, const ApassPlan& plan, const void* 
     count_launch();
     apass_reduce_kernel<double><<<nb, kVecThreads, 0, st>>>(
         reinterpret_cast<const double*>(partial), plan.grid, a.d, plan.dpad, rho,
-        reinterpret_cast<const double*>(a.p), reinterpret_cast<double*>(y), dot_part, a.skip);
+        reinterpret_cast<const double*>(a.p), reinterpret_cast<double*>(y), dot_part, a.skip, nullptr);
   } else {
     count_launch();
     apass_reduce_kernel<float><<<nb, kVecThreads, 0, st>>>(
         reinterpret_cast<const float*>(partial), plan.grid, a.d, plan.dpad, (float)rho,
-        reinterpret_cast<const float*>(a.p), reinterpret_cast<float*>(y), dot_part, a.skip);
+        reinterpret_cast<const float*>(a.p), reinterpret_cast<float*>(y), dot_part, a.skip,
+        a.dtype == NYS_FP8E4M3 ? a.col_scale : nullptr);
   }
   return cudaGetLastError();
 }

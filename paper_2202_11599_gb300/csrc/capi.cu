@@ -58,7 +58,9 @@ bool is_fin(double v) { return std::isfinite(v); }
 nys_status check_matrix(const nys_matrix* A) {
   if (!A || !A->data) return NYS_EINVAL;
   if (A->n <= 0 || A->d <= 0 || A->ld < A->d) return NYS_EINVAL;
-  if (A->dtype != NYS_F64 && A->dtype != NYS_F32 && A->dtype != NYS_BF16) return NYS_EINVAL;
+  if (A->dtype != NYS_F64 && A->dtype != NYS_F32 && A->dtype != NYS_BF16 && A->dtype != NYS_FP8E4M3)
+    return NYS_EINVAL;
+  if ((A->dtype == NYS_FP8E4M3) != (A->col_scale != nullptr)) return NYS_EINVAL;  // scales iff FP8
   const size_t esz = dtype_size(A->dtype);
   if ((A->ld * esz) % 16 != 0) return NYS_EINVAL;
   if (reinterpret_cast<uintptr_t>(A->data) % 16 != 0) return NYS_EINVAL;
@@ -116,6 +118,18 @@ nys_status sketch_panel(const nys_matrix* A, const double* D, double shift, cons
   PhaseTimer pt("sketch Y = H Omega", st);
   Pool pool(st);
   const int64_t n = A->n, d = A->d;
+  if (A->dtype == NYS_FP8E4M3) {
+    // FP8: sketch the dequantised matrix (s_j q_ij in FP32, exact products of the 4-bit
+    // codes and the scales up to FP32 rounding) through the FP32 path
+    float* A32 = pool.alloc<float>((size_t)n * A->ld);
+    if (!pool.ok()) return NYS_ENOMEM;
+    NYS_CU(dequantize_fp8(A, A32, st));
+    nys_matrix M32 = *A;
+    M32.data = A32;
+    M32.dtype = NYS_F32;
+    M32.col_scale = nullptr;
+    return sketch_panel(&M32, D, shift, Om, m, Y, st, nullptr);
+  }
   if (sketch_tc_supported(A)) {
     NYS_CU(prep ? sketch_tc_with(A, *prep, D, Om, m, Y, st) : sketch_tc(A, D, Om, m, Y, st));
     if (shift != 0.0) NYS_CU(axpy_panel(shift, Om, Y, d * m, st));
@@ -289,6 +303,7 @@ nys_status hmatvec_t(const nys_matrix* A, const double* D, double rho, const voi
   a.d = A->d;
   a.ld = A->ld;
   a.dtype = A->dtype;
+  a.col_scale = A->col_scale;
   a.p = p;
   a.D = D;
   a.b = nullptr;
@@ -321,6 +336,7 @@ nys_status aux_pass(const nys_matrix* A, int mode, const void* p, const double* 
   a.d = A->d;
   a.ld = A->ld;
   a.dtype = A->dtype;
+  a.col_scale = A->col_scale;
   a.p = p;
   a.D = nullptr;
   a.b = b;
@@ -1180,6 +1196,7 @@ nys_status nysadmm_solve_path(const nys_matrix* A, const double* b, const double
     NYS_TRY(check_matrix(Ain));
     if (Ain->n != A->n || Ain->d != A->d) return NYS_EINVAL;
   }
+  if (A->dtype == NYS_FP8E4M3 || Ain->dtype == NYS_FP8E4M3) return NYS_EINVAL;  // multi-RHS: F64/F32/BF16
   cudaStream_t st = stream_of(&o);
   if (info) std::memset(info, 0, sizeof(*info));
   return Ain->dtype == NYS_F64
@@ -1195,6 +1212,7 @@ nys_status nysadmm_solve_batch(int32_t count, const nys_lasso_instance* inst, do
   for (int i = 0; i < count; ++i) {
     NYS_TRY(check_matrix(inst[i].A));
     if ((inst[i].A->dtype == NYS_F64) != f64) return NYS_EINVAL;  // one compute type per batch
+    if (inst[i].A->dtype == NYS_FP8E4M3) return NYS_EINVAL;
     if (!inst[i].b || !inst[i].Omega || !(inst[i].gamma >= 0) || !is_fin(inst[i].gamma)) return NYS_EINVAL;
     if (inst[i].rank < 1 || inst[i].rank > inst[i].A->d || inst[i].rank > kMaxRank) return NYS_EINVAL;
   }
@@ -1300,6 +1318,7 @@ nys_status nys_autotune_apass(const nys_matrix* A, int32_t* rows_out, double* ms
     a.d = A->d;
     a.ld = A->ld;
     a.dtype = A->dtype;
+    a.col_scale = A->col_scale;
     a.p = p;
     a.D = nullptr;
     a.b = nullptr;

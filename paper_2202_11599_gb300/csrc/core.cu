@@ -10,6 +10,8 @@
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
+#include <cuda_fp8.h>
+
 #include "device_util.cuh"
 #include "nys_internal.cuh"
 
@@ -1006,6 +1008,30 @@ __global__ void f32_to_f64_kernel(const float* __restrict__ x, double* __restric
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = (double)x[i];
 }
+// FP8 E4M3 with per-column scales -> FP32 (same row-major layout and ld).
+__global__ void dequantize_fp8_kernel(const unsigned char* __restrict__ q, int64_t n, int64_t d, int64_t ld,
+                                      const float* __restrict__ scale, float* __restrict__ out) {
+  const int64_t total = n * ld;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = idx % ld;
+    float v = 0.f;
+    if (j < d) {
+      const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)q[idx], __NV_E4M3);
+      v = __half2float(*reinterpret_cast<const __half*>(&h)) * scale[j];
+    }
+    out[idx] = v;
+  }
+}
+
+cudaError_t dequantize_fp8(const nys_matrix* A, float* out, cudaStream_t st) {
+  if (A->dtype != NYS_FP8E4M3 || !A->col_scale) return cudaErrorInvalidValue;
+  count_launch();
+  dequantize_fp8_kernel<<<(unsigned)std::min<int64_t>(8192, (A->n * A->ld + 255) / 256), 256, 0, st>>>(
+      reinterpret_cast<const unsigned char*>(A->data), A->n, A->d, A->ld, A->col_scale, out);
+  return cudaGetLastError();
+}
+
 cudaError_t convert_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   count_launch();

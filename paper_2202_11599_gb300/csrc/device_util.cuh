@@ -27,6 +27,11 @@ template <> struct Stor<NYS_BF16> {
   static constexpr int VEC = 8;
   static constexpr int ESZ = 2;
 };
+template <> struct Stor<NYS_FP8E4M3> {
+  using C = float;
+  static constexpr int VEC = 16;
+  static constexpr int ESZ = 1;
+};
 
 // Unpack one 16-byte vector of stored elements into compute values.
 template <int DT>

@@ -66,6 +66,7 @@ extern "C" nys_status nys_hmatvec_noalloc(const nys_matrix* A, const double* D, 
   a.d = A->d;
   a.ld = A->ld;
   a.dtype = A->dtype;
+  a.col_scale = A->col_scale;
   a.p = p;
   a.D = D;
   a.b = nullptr;

@@ -35,6 +35,7 @@ struct ApassArgs {
   double* t_out;        // length n or NULL: t = A p
   int mode;
   const int* skip = nullptr;  // if non-null and *skip != 0 the pass is skipped
+  const float* col_scale = nullptr;  // FP8: per-column scales (A_ij = col_scale[j] q_ij)
 };
 
 // Workspace-carrying handle for repeated A-passes on one matrix.
@@ -126,6 +127,8 @@ cudaError_t gemm_nn_t(const T* B, int64_t M, int K, const T* V, int N, T* C, cud
 
 // ---------------------------------------------------------------- helpers
 cudaError_t convert_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t st);
+// FP8 E4M3 matrix with per-column scales -> FP32 values (n x ld, same layout)
+cudaError_t dequantize_fp8(const nys_matrix* A, float* out, cudaStream_t st);
 cudaError_t convert_f32_to_f64(const float* x, double* y, int64_t n, cudaStream_t st);
 
 // Instrumentation (nys_stats_* in the C ABI): every kernel launch is counted; the
@@ -155,7 +158,7 @@ DevTimer stats_device_timer();
 // An event pair plus a zeroed device flag that the pass sets when it runs.
 cudaError_t stats_event_pair(cudaEvent_t* start, cudaEvent_t* stop, int** executed);
 
-inline size_t dtype_size(int dt) { return dt == NYS_F64 ? 8 : (dt == NYS_F32 ? 4 : 2); }
+inline size_t dtype_size(int dt) { return dt == NYS_F64 ? 8 : (dt == NYS_F32 ? 4 : (dt == NYS_BF16 ? 2 : 1)); }
 inline bool compute_is_f64(int dt) { return dt == NYS_F64; }
 
 }  // namespace nys

@@ -318,6 +318,7 @@ nys_status pcg_run(const PcgProblem& pb, const PrecondView& P, const C* r, C* x,
   aa.d = d;
   aa.ld = pb.A->ld;
   aa.dtype = pb.A->dtype;
+  aa.col_scale = pb.A->col_scale;
   aa.D = pb.D;
   aa.b = nullptr;
   aa.D_out = nullptr;
@@ -874,6 +875,7 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   aa.d = d;
   aa.ld = g.pb.A->ld;
   aa.dtype = g.pb.A->dtype;
+  aa.col_scale = g.pb.A->col_scale;
   aa.D = g.pb.D;
   aa.b = nullptr;
   aa.D_out = nullptr;
@@ -897,6 +899,7 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
     ar.d = d;
     ar.ld = g.Aref->ld;
     ar.dtype = g.Aref->dtype;
+    ar.col_scale = g.Aref->col_scale;
     ar.p = g.x;
     ar.D = nullptr;
     ar.b = g.b;

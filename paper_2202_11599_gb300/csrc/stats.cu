@@ -114,7 +114,7 @@ nys_status nys_stats_read(nys_stats* out) {
   using namespace nys;
   if (!out) return NYS_EINVAL;
   std::lock_guard<std::mutex> lk(g_mu);
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 4; ++k) {
     out->apass_launches[k] = 0;
     out->apass_ms[k] = 0.0;
     out->apass_bytes[k] = 0.0;
@@ -129,13 +129,13 @@ nys_status nys_stats_read(nys_stats* out) {
     if (cudaEventSynchronize(r.stop) != cudaSuccess) return NYS_ECUDA;
     float t = 0.f;
     if (cudaEventElapsedTime(&t, r.start, r.stop) != cudaSuccess) return NYS_ECUDA;
-    const int k = (r.dtype >= 0 && r.dtype < 3) ? r.dtype : 0;
+    const int k = (r.dtype >= 0 && r.dtype < 4) ? r.dtype : 0;
     out->apass_launches[k] += 1;
     out->apass_ms[k] += t;
     out->apass_bytes[k] += r.bytes;
   }
   out->launches = g_launches.load();
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 4; ++k) {
     out->dev_launches[k] = 0;
     out->dev_ms[k] = 0.0;
     out->dev_bytes[k] = 0.0;
@@ -155,7 +155,7 @@ nys_status nys_stats_read(nys_stats* out) {
          cudaMemcpy(dt.data(), g_timer.dtype, cnt * 4, cudaMemcpyDeviceToHost) != cudaSuccess))
       return NYS_ECUDA;
     for (int i = 0; i < cnt; ++i) {
-      const int k = (dt[i] >= 0 && dt[i] < 3) ? dt[i] : 0;
+      const int k = (dt[i] >= 0 && dt[i] < 4) ? dt[i] : 0;
       if (t1[i] < t0[i]) continue;
       out->dev_launches[k] += 1;
       out->dev_ms[k] += (double)(t1[i] - t0[i]) * 1e-6;

@@ -19,14 +19,17 @@ LIB_PATH = os.path.join(_HERE, "libnysadmm.so")
 
 NYS_OK, NYS_EINVAL, NYS_ENOTSPD, NYS_EBREAKDOWN, NYS_ENOCONV, NYS_ETIMEOUT, NYS_ECUDA, NYS_ENOMEM = range(8)
 NYS_LASSO, NYS_LOGISTIC = 0, 1
-NYS_F64, NYS_F32, NYS_BF16 = 0, 1, 2
+NYS_F64, NYS_F32, NYS_BF16, NYS_FP8E4M3 = 0, 1, 2, 3
 TOL_MODES = {"rel": 0, "abs": 1, "sqrt_rprd": 2}
-_DTYPES = {torch.float64: NYS_F64, torch.float32: NYS_F32, torch.bfloat16: NYS_BF16}
+_DTYPES = {torch.float64: NYS_F64, torch.float32: NYS_F32, torch.bfloat16: NYS_BF16,
+           torch.float8_e4m3fn: NYS_FP8E4M3}
+FP8_E4M3_MAX = 448.0
 _LOSSES = {"lasso": NYS_LASSO, "logistic": NYS_LOGISTIC}
 
 
 class NysMatrixC(ctypes.Structure):
-    _fields_ = [("data", c_void_p), ("dtype", c_int32), ("n", c_int64), ("d", c_int64), ("ld", c_int64)]
+    _fields_ = [("data", c_void_p), ("dtype", c_int32), ("n", c_int64), ("d", c_int64), ("ld", c_int64),
+                ("col_scale", c_void_p)]
 
 
 class NysOptsC(ctypes.Structure):
@@ -46,9 +49,9 @@ class NysInfoC(ctypes.Structure):
 
 
 class NysStatsC(ctypes.Structure):
-    _fields_ = [("launches", c_int64), ("apass_launches", c_int64 * 3), ("apass_ms", c_double * 3),
-                ("apass_bytes", c_double * 3), ("dev_launches", c_int64 * 3), ("dev_ms", c_double * 3),
-                ("dev_bytes", c_double * 3)]
+    _fields_ = [("launches", c_int64), ("apass_launches", c_int64 * 4), ("apass_ms", c_double * 4),
+                ("apass_bytes", c_double * 4), ("dev_launches", c_int64 * 4), ("dev_ms", c_double * 4),
+                ("dev_bytes", c_double * 4)]
 
 
 class NysInstanceC(ctypes.Structure):
@@ -139,7 +142,7 @@ def _ptr(t):
 class Matrix:
     """Row-major device matrix (n x d, leading dimension ld >= d) for the C ABI."""
 
-    def __init__(self, t: torch.Tensor, d: int | None = None):
+    def __init__(self, t: torch.Tensor, d: int | None = None, col_scale: torch.Tensor | None = None):
         if not t.is_cuda or t.dim() != 2 or t.stride(1) != 1:
             raise ValueError("Matrix needs a 2-D CUDA tensor with unit column stride")
         if t.dtype not in _DTYPES:
@@ -148,7 +151,13 @@ class Matrix:
         self.n = t.shape[0]
         self.d = t.shape[1] if d is None else d
         self.ld = t.stride(0)
-        self.c = NysMatrixC(c_void_p(t.data_ptr()), _DTYPES[t.dtype], self.n, self.d, self.ld)
+        self.col_scale = None
+        if t.dtype == torch.float8_e4m3fn:
+            if col_scale is None or col_scale.dtype != torch.float32 or not col_scale.is_cuda:
+                raise ValueError("an FP8 matrix needs FP32 per-column scales on the device")
+            self.col_scale = col_scale.contiguous()
+        self.c = NysMatrixC(c_void_p(t.data_ptr()), _DTYPES[t.dtype], self.n, self.d, self.ld,
+                            c_void_p(self.col_scale.data_ptr() if self.col_scale is not None else 0))
 
     @property
     def compute_dtype(self):
@@ -165,6 +174,23 @@ class Matrix:
         buf = torch.zeros(n, ld, dtype=dtype, device=src.device)
         buf[:, :d] = src.to(dtype)
         return Matrix(buf, d=d)
+
+    @staticmethod
+    def fp8(src: torch.Tensor) -> "Matrix":
+        """FP8 E4M3 codes with one FP32 scale per column, A_ij ~ scale_j * q_ij (scale_j maps
+        the column's largest magnitude to the E4M3 maximum), rows on 16-byte boundaries."""
+        n, d = src.shape
+        a = src.to(torch.float32)
+        scale = (a.abs().amax(dim=0) / FP8_E4M3_MAX).clamp_min(torch.finfo(torch.float32).tiny)
+        ld = (d + 15) // 16 * 16
+        buf = torch.zeros(n, ld, dtype=torch.float8_e4m3fn, device=src.device)
+        buf[:, :d] = (a / scale[None, :]).to(torch.float8_e4m3fn)
+        return Matrix(buf, d=d, col_scale=scale)
+
+    def dequantized(self) -> torch.Tensor:
+        """The stored values as FP64 (FP8: scale_j * q_ij), n x d."""
+        t = self.tensor[:, : self.d].to(torch.float64)
+        return t * self.col_scale.to(torch.float64)[None, :] if self.col_scale is not None else t
 
 
 def _opts(stream=None, **kw) -> NysOptsC:
@@ -409,12 +435,12 @@ def stats_read() -> dict:
     """Kernel launches and A-pass device time / algorithmic bytes since stats_enable."""
     s = NysStatsC()
     _check(lib().nys_stats_read(ctypes.byref(s)), "nys_stats_read")
-    names = {NYS_F64: "f64", NYS_F32: "f32", NYS_BF16: "bf16"}
+    names = {NYS_F64: "f64", NYS_F32: "f32", NYS_BF16: "bf16", NYS_FP8E4M3: "fp8"}
     return {"launches": s.launches,
             "apass": {names[k]: {"launches": s.apass_launches[k], "ms": s.apass_ms[k],
-                                 "bytes": s.apass_bytes[k]} for k in range(3)},
+                                 "bytes": s.apass_bytes[k]} for k in range(4)},
             "apass_dev": {names[k]: {"launches": s.dev_launches[k], "ms": s.dev_ms[k],
-                                     "bytes": s.dev_bytes[k]} for k in range(3)}}
+                                     "bytes": s.dev_bytes[k]} for k in range(4)}}
 
 
 class MLP:

@@ -48,11 +48,11 @@ def test_strerror_and_defaults_without_gpu(libpath):
 def test_struct_layouts_match_header(libpath):
     from paper_2202_11599_gb300 import nysadmm as nx
     # offsets follow C natural alignment of the header's structs
-    assert ctypes.sizeof(nx.NysMatrixC) == 40
+    assert ctypes.sizeof(nx.NysMatrixC) == 48
     assert nx.NysOptsC.stream.offset == 96 and nx.NysOptsC.hx_refresh.offset == 108
     assert ctypes.sizeof(nx.NysOptsC) == 128
     assert ctypes.sizeof(nx.NysInfoC) == 48
-    assert ctypes.sizeof(nx.NysStatsC) == 8 + 3 * 8 * 6
+    assert ctypes.sizeof(nx.NysStatsC) == 8 + 4 * 8 * 6
 
 
 def test_invalid_arguments_rejected_before_any_launch(libpath):
@@ -63,4 +63,9 @@ def test_invalid_arguments_rejected_before_any_launch(libpath):
     m = nx.NysMatrixC(ctypes.c_void_p(16), nx.NYS_F64, 10, 0, 10)
     assert L.nys_hmatvec(ctypes.byref(m), None, 0.0, None, None, None) == nx.NYS_EINVAL
     m = nx.NysMatrixC(ctypes.c_void_p(16), nx.NYS_F64, 10, 5, 5)       # 5*8 bytes: not 16-aligned rows
+    assert L.nys_hmatvec(ctypes.byref(m), None, 0.0, ctypes.c_void_p(16), ctypes.c_void_p(32), None) == nx.NYS_EINVAL
+    # FP8 storage needs its per-column scales, and scales belong to FP8 only
+    m = nx.NysMatrixC(ctypes.c_void_p(16), nx.NYS_FP8E4M3, 10, 16, 16)
+    assert L.nys_hmatvec(ctypes.byref(m), None, 0.0, ctypes.c_void_p(16), ctypes.c_void_p(32), None) == nx.NYS_EINVAL
+    m = nx.NysMatrixC(ctypes.c_void_p(16), nx.NYS_F32, 10, 16, 16, ctypes.c_void_p(64))
     assert L.nys_hmatvec(ctypes.byref(m), None, 0.0, ctypes.c_void_p(16), ctypes.c_void_p(32), None) == nx.NYS_EINVAL

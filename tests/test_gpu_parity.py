@@ -83,6 +83,34 @@ def test_hmatvec_bf16_wide_rows(n, d):
         assert np.max(np.abs(y.double().cpu().numpy() - ref) / scale) <= 2e-5
 
 
+@pytest.mark.parametrize("n,d", [(1000, 300), (777, 129), (5000, 1001), (20000, 4000)])
+def test_hmatvec_fp8_per_column_scales(n, d):
+    """FP8 E4M3 storage with per-column scales: the pass against the FP64 definition on the
+    dequantised values (scale_j * q_ij), with and without D."""
+    rng = np.random.default_rng(n * 7 + d)
+    A = rng.standard_normal((n, d)) * gen.column_scales(d, 0.5)[None, :]
+    M = nx.Matrix.fp8(_dev(A))
+    Aq = M.dequantized().cpu().numpy()
+    p = rng.standard_normal(d)
+    pq = torch.from_numpy(p).float().double().numpy()
+    Dv = rng.random(n) + 0.1
+    for D in (None, Dv):
+        y = nx.hmatvec(M, _dev(pq), 0.37, None if D is None else _dev(D)).double().cpu().numpy()
+        w = np.ones(n) if D is None else D
+        ref = Aq.T @ (w * (Aq @ pq)) + 0.37 * pq
+        scale = np.abs(Aq).T @ (w * (np.abs(Aq) @ np.abs(pq))) + 0.37 * np.abs(pq)
+        assert np.max(np.abs(y - ref) / scale) <= 2e-5
+
+
+def test_sketch_fp8_per_column_scales():
+    A, Om = _small_problem(n=3000, d=400, s=30, seed=31)
+    M = nx.Matrix.fp8(_dev(A))
+    Aq = M.dequantized().cpu().numpy()
+    U, lam, _, _, _ = o.nystrom(lambda X: Aq.T @ (Aq @ X), Om, shift_scale=np.sqrt(400), mantissa_bits=23)
+    P = nx.sketch(M, _dev(Om))
+    assert np.max(np.abs(P.lam.numpy() - lam)) <= 2e-5 * lam[0]
+
+
 def test_hmatvec_deterministic():
     rng = np.random.default_rng(5)
     A = rng.standard_normal((20000, 700))
