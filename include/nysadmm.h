@@ -275,6 +275,15 @@ typedef struct {
 void nys_stats_enable(int32_t on);
 nys_status nys_stats_read(nys_stats* out);
 
+/* Diagnostic of the device-side wait bound (no counterpart in the paper).  Every
+ * device-side wait of the library (TMA stages, tensor-core completions, grid steps) is
+ * bounded; when a bound runs out the kernel stops waiting, records NYS_ETIMEOUT and
+ * returns, so the host gets a status and the CUDA context stays usable.  This call runs
+ * one such wait on a barrier that nothing completes, with a bound of wait_us
+ * microseconds (0 < wait_us <= 5e6), and returns NYS_ETIMEOUT when the bound works.
+ * NYS_EINVAL for a bound outside that range. */
+nys_status nys_check_wait_bound(double wait_us, void* stream);
+
 /* Learned warm start for the x-subproblem (no counterpart in the paper; an
  * AI-systems addition).  A multilayer perceptron n_in -> n_hid -> n_hid -> n_out
  * with erf-GELU hidden units; BF16 weights in the matrix products with FP32

@@ -7,6 +7,7 @@
 #include <vector>
 #include <algorithm>
 
+#include "device_util.cuh"
 #include "nys_internal.cuh"
 
 namespace nys {
@@ -163,6 +164,46 @@ nys_status nys_stats_read(nys_stats* out) {
     }
   }
   return NYS_OK;
+}
+
+// Diagnostic: one CTA whose thread 0 waits, with the bounded mbarrier wait every kernel of
+// the library uses, on a barrier that expects two arrivals and receives one, so the wait
+// must run out; the kernel then reports NYS_ETIMEOUT the way the passes do.
+__global__ void wait_bound_check_kernel(long long cycles, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    nys::mbar_init(&bar, 2);
+    nys::fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(nys::smem_u32(&bar)) : "memory");
+    const bool ok = nys::mbar_wait_bounded(&bar, 0u, cycles);
+    *status = ok ? (int)NYS_OK : (int)NYS_ETIMEOUT;
+  }
+}
+
+nys_status nys_check_wait_bound(double wait_us, void* stream) {
+  if (!(wait_us > 0.0) || wait_us > 5e6) return NYS_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int dev = 0, khz = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NYS_ECUDA;
+  if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || khz <= 0) {
+    cudaGetLastError();
+    khz = 2000000;  // the bound is in clock ticks; ~2 GHz when the rate is not reported
+  }
+  const long long cycles = (long long)(wait_us * 1e-3 * khz);
+  int* d_status = nullptr;
+  if (cudaMallocAsync(&d_status, sizeof(int), st) != cudaSuccess) return NYS_ENOMEM;
+  int h = -1;
+  nys::count_launch();
+  wait_bound_check_kernel<<<1, 32, 0, st>>>(cycles, d_status);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(d_status, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return NYS_ECUDA;
+  return (nys_status)h;
 }
 
 }  // extern "C"

@@ -84,6 +84,7 @@ def lib() -> ctypes.CDLL:
     L.nys_strerror.restype = ctypes.c_char_p
     L.nys_hmatvec.argtypes = [P(NysMatrixC), c_void_p, c_double, c_void_p, c_void_p, c_void_p]
     L.nys_hmatvec_noalloc.argtypes = [P(NysMatrixC), c_void_p, c_double, c_void_p, c_void_p, c_void_p]
+    L.nys_check_wait_bound.argtypes = [c_double, c_void_p]
     L.nys_sketch.argtypes = [P(NysMatrixC), c_void_p, c_double, c_int32, c_void_p, P(NysOptsC), P(c_void_p)]
     L.nys_precond_get.argtypes = [c_void_p, c_void_p, P(c_double), P(c_int32), P(c_int64), P(c_double), c_void_p]
     L.nys_precond_apply.argtypes = [c_void_p, c_double, c_void_p, c_void_p, c_int64, c_int32, c_void_p]
@@ -441,6 +442,12 @@ def stats_read() -> dict:
                                  "bytes": s.apass_bytes[k]} for k in range(4)},
             "apass_dev": {names[k]: {"launches": s.dev_launches[k], "ms": s.dev_ms[k],
                                      "bytes": s.dev_bytes[k]} for k in range(4)}}
+
+
+def check_wait_bound(wait_us: float = 2000.0, stream=None) -> int:
+    """Run the library's bounded device-side wait on a barrier nothing completes; returns
+    the status (NYS_ETIMEOUT = 5 when the bound works)."""
+    return lib().nys_check_wait_bound(float(wait_us), c_void_p(_stream_ptr(stream)))
 
 
 class MLP:

@@ -491,3 +491,21 @@ def test_autotuner_picks_a_supported_shape_and_results_do_not_change():
         y1 = nx.hmatvec(M, p, 0.5)
         tol = 1e-12 if dtype == torch.float64 else 1e-5
         assert ((y1.double() - y0.double()).abs().max() / y0.double().abs().max()).item() <= tol
+
+
+def test_device_wait_bound_reports_timeout_and_context_survives():
+    """Every device-side wait of the library is bounded: a wait on a barrier that nothing
+    completes runs out after the bound, the kernel reports NYS_ETIMEOUT, and the CUDA
+    context stays usable (a pass right after matches the definition)."""
+    import time
+    assert nx.check_wait_bound(0.0) == nx.NYS_EINVAL
+    t0 = time.time()
+    assert nx.check_wait_bound(20000.0) == nx.NYS_ETIMEOUT
+    assert time.time() - t0 < 10.0
+    rng = np.random.default_rng(77)
+    A = rng.standard_normal((500, 64))
+    M = nx.Matrix.padded(_dev(A))
+    p = rng.standard_normal(64)
+    y = nx.hmatvec(M, _dev(p), 0.5).cpu().numpy()
+    ref = A.T @ (A @ p) + 0.5 * p
+    assert np.max(np.abs(y - ref)) <= 1e-12 * np.max(np.abs(A.T) @ (np.abs(A) @ np.abs(p)))
