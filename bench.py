@@ -120,6 +120,18 @@ def workload_config(w):
             "gap": GAP, "l2_flush": "inputs (10 GB) larger than L2 (129 MB)"}
 
 
+def max_over_ranks(value: float, dist=None) -> float:
+    """The job's time is its slowest rank's: max of a per-rank scalar over all ranks
+    (replicas: every rank solves its own copy of the workload).  NCCL reduces on the
+    GPU, gloo on the CPU."""
+    if dist is None:
+        return float(value)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -227,10 +239,7 @@ def run_ours(args):
     clocks = sampler.stop()
     total_ms = e0.elapsed_time(e1)
     step_ms = [a.elapsed_time(c) for a, c in per_step]
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = max_over_ranks(total_ms, dist)
     gap_final = (F(last["z"]) - Fstar) / Fstar if Fstar is not None else None
     info = last["info"]
 
