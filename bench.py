@@ -704,7 +704,7 @@ def main():
     ap.add_argument("--pcg-tol", type=float, default=None, help="PCG tolerance of the mixed solve (default 1e-4)")
     ap.add_argument("--pcg-mode", choices=["rel", "abs", "sqrt_rprd"], default="rel",
                     help="PCG stop rule of the mixed solve (sqrt_rprd: the paper's eps = sqrt(r_p r_d))")
-    ap.add_argument("--hx-refresh", type=int, default=50,
+    ap.add_argument("--hx-refresh", type=int, default=100,
                     help="recompute (H + rho I) x for the PCG warm start every this many ADMM iterations")
     ap.add_argument("--admm-iters", type=int, default=0,
                     help="use this ADMM iteration count instead of calibrating it (profiling runs)")
