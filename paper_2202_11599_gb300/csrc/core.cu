@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(512) power_kernel(const double* __restrict__ G
 cudaError_t power_lambda_max(const double* G, int s, double* out, double* work, cudaStream_t st) {
   if (s > 1024) return cudaErrorInvalidValue;
   count_launch();
-  power_kernel<<<1, 512, 0, st>>>(G, s, 60, out, work);
+  power_kernel<<<1, 512, 0, st>>>(G, s, 30, out, work);
   return cudaGetLastError();
 }
 

@@ -159,7 +159,11 @@ __global__ void __launch_bounds__(kVecThreads) pcg_update_kernel(int init, int64
                                                                  double* part_w2, double* part_r2, double* part_g,
                                                                  PcgState* st, C* __restrict__ hx,
                                                                  const C* __restrict__ cvec, C* __restrict__ gs,
-                                                                 cudaGraphConditionalHandle cond, int use_cond) {
+                                                                 cudaGraphConditionalHandle cond, int use_cond,
+                                                                 const double* __restrict__ rq,
+                                                                 const double* __restrict__ rz,
+                                                                 const double* __restrict__ ru, double rrho,
+                                                                 C* __restrict__ r_out) {
   if (st->done) {
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
     return;
@@ -184,7 +188,14 @@ __global__ void __launch_bounds__(kVecThreads) pcg_update_kernel(int init, int64
     for (int64_t j = j0 + threadIdx.x; j < j1; j += kVecThreads) {
       C wj;
       if (init) {
-        const C rj = r[j];
+        // with rq: the ADMM right-hand side r = q + rho (z - u) is formed here (and stored)
+        C rj;
+        if (rq) {
+          rj = (C)fma(rrho, rz[j] - ru[j], rq[j]);
+          r_out[j] = rj;
+        } else {
+          rj = r[j];
+        }
         wj = v ? rj - v[j] : rj;
         lr2 += (double)rj * (double)rj;
       } else {
@@ -348,7 +359,8 @@ nys_status pcg_run(const PcgProblem& pb, const PrecondView& P, const C* r, C* x,
   count_launch();
   pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, stream>>>(1, d, chunk, x, w, r, v0, p, U, s, pv_part, nbr,
                                                              wy_part, nb5, part_w2, part_r2, part_g, st, (C*)nullptr,
-                                                             cvec, gs, 0ull, 0);
+                                                             cvec, gs, 0ull, 0, nullptr, nullptr, nullptr, 0.0,
+                                                             (C*)nullptr);
   LAUNCH_OK(cudaGetLastError());
   count_launch();
   pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, stream>>>(d, w, y, U, s, gs, wy_part, st, 1, p);
@@ -366,7 +378,8 @@ nys_status pcg_run(const PcgProblem& pb, const PrecondView& P, const C* r, C* x,
       count_launch();
       pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, stream>>>(0, d, chunk, x, w, r, v, p, U, s, pv_part, nbr,
                                                                  wy_part, nb5, part_w2, part_r2, part_g, st, (C*)nullptr,
-                                                                 cvec, gs, 0ull, 0);
+                                                                 cvec, gs, 0ull, 0, nullptr, nullptr, nullptr, 0.0,
+                                                                 (C*)nullptr);
       LAUNCH_OK(cudaGetLastError());
       count_launch();
       pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, stream>>>(d, w, y, U, s, gs, wy_part, st, 0, p);
@@ -416,7 +429,8 @@ nys_status precond_apply_run(const PrecondView& P, int64_t d, const C* V, C* Y, 
     count_launch();
     pcg_update_kernel<C><<<nb3, kVecThreads, (size_t)chunk * sizeof(C), stream>>>(
         1, d, chunk, nullptr, w, V + c * d, nullptr, nullptr, reinterpret_cast<const C*>(P.U), s, nullptr, 0,
-        nullptr, 0, part_w2, part_r2, part_g, st, (C*)nullptr, reinterpret_cast<const C*>(P.c), gs, 0ull, 0);
+        nullptr, 0, part_w2, part_r2, part_g, st, (C*)nullptr, reinterpret_cast<const C*>(P.c), gs, 0ull, 0, nullptr,
+        nullptr, nullptr, 0.0, (C*)nullptr);
     // the scalar step may mark the state done (||w|| <= 0 threshold); force the tail to run
     count_launch();
     pcg_reset_kernel<<<1, 1, 0, stream>>>(st, 0.0, 1, 1, -1, nullptr);
@@ -912,9 +926,14 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
     G_OK(apass_reduce(ar2, g.plan_ref, apart_ref, 0.0, g.yres, nullptr, 0, cap));
     seg_nodes += 2;
   }
-  admm_rhs_g_kernel<C><<<nbz, kVecThreads, 0, cap>>>(d, g.q, g.z, g.u, g.rho, g.x, g.yres, refine, rc, xc, hx);
-  ++seg_nodes;
   const bool use_ws = (g.warm || g.warm_record) && s > 0;
+  // without a refined step or a warm-start model the right-hand side is formed by the
+  // PCG-init update kernel itself (one launch fewer per iteration)
+  const bool fuse_rhs = !refine && !use_ws;
+  if (!fuse_rhs) {
+    admm_rhs_g_kernel<C><<<nbz, kVecThreads, 0, cap>>>(d, g.q, g.z, g.u, g.rho, g.x, g.yres, refine, rc, xc, hx);
+    ++seg_nodes;
+  }
   float* feat = nullptr;
   double* proj = nullptr;
   double* rnorm = nullptr;
@@ -972,7 +991,8 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   }
   pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, cap>>>(1, d, chunk, xc, w, rc, hx, p, U, s, pv_part, nbr,
                                                           wy_part, nb5, part_w2, part_r2, part_g, st, (C*)nullptr,
-                                                          cvec, gs, h_pcg, 1);
+                                                          cvec, gs, h_pcg, 1, fuse_rhs ? g.q : nullptr,
+                                                          fuse_rhs ? g.z : nullptr, fuse_rhs ? g.u : nullptr, g.rho, rc);
   pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, cap>>>(d, w, y, U, s, gs, wy_part, st, 1, p);
   seg_nodes += 2;
   cudaStreamCaptureStatus cst;
@@ -997,7 +1017,8 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, true));
   G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho, v, pv_part, nbr, cap));
   pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, cap>>>(0, d, chunk, xc, w, rc, v, p, U, s, pv_part, nbr, wy_part,
-                                                          nb5, part_w2, part_r2, part_g, st, hx, cvec, gs, h_pcg, 1);
+                                                          nb5, part_w2, part_r2, part_g, st, hx, cvec, gs, h_pcg, 1,
+                                                          nullptr, nullptr, nullptr, 0.0, (C*)nullptr);
   pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, cap>>>(d, w, y, U, s, gs, wy_part, st, 0, p);
   body_nodes = 4;
   G_OK(cudaStreamEndCapture(cap, &pbody));
