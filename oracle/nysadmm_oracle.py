@@ -246,12 +246,14 @@ def lasso_nysadmm(A: np.ndarray, b: np.ndarray, gamma: float, rho: float, Omega:
                   admm_iters: int, pcg_tol: float = 1e-8, pcg_tol_mode: str = "rel",
                   shift_scale: float | None = None, pcg_fixed=None, pcg_maxit=None,
                   eps_abs: float | None = None, eps_rel: float | None = None,
-                  precond=None):
-    """Alg. NysADMM for the lasso.
+                  precond=None, mu: float = 0.0):
+    """Alg. NysADMM for the lasso, and for any problem whose smooth part adds
+    g(x) = mu/2 ||x||^2 (the elastic net of Sec. 3.1 has mu = 1 - gamma).
 
-    Sketch once (App. B) with H = A^T A, then for k = 0, 1, ...:
-        r^k     = rho z - rho u + A^T b            (Eq. ADMMSubProb with l = 1/2||.-b||^2)
-        x^{k+1} = PCG solve of (A^T A + rho I) x = r^k, warm-started at x^k
+    Sketch once (App. B) with H = A^T A + H^g, H^g = mu I, then for k = 0, 1, ...:
+        r^k     = rho z - rho u + A^T b            (Eq. ADMMSubProb with l = 1/2||.-b||^2;
+                                                    the H^g x and grad g terms cancel)
+        x^{k+1} = PCG solve of (A^T A + mu I + rho I) x = r^k, warm-started at x^k
         z^{k+1} = S_{gamma/rho}(x^{k+1} + u^k)
         u^{k+1} = u^k + x^{k+1} - z^{k+1}
         r_p     = ||x^{k+1} - z^{k+1}||,  r_d = rho ||z^k - z^{k+1}||   (Sec. 2.1)
@@ -262,7 +264,7 @@ def lasso_nysadmm(A: np.ndarray, b: np.ndarray, gamma: float, rho: float, Omega:
     n, d = A.shape
     if shift_scale is None:
         shift_scale = math.sqrt(d)
-    H_apply = lambda X: A.T @ (A @ X)
+    H_apply = lambda X: A.T @ (A @ X) + mu * X
     if precond is None:
         U, lam, nu, Q, _ = nystrom(H_apply, Omega, shift_scale)
     else:
@@ -293,6 +295,32 @@ def lasso_nysadmm(A: np.ndarray, b: np.ndarray, gamma: float, rho: float, Omega:
                     r_d <= eps_abs + eps_rel * np.linalg.norm(rho * u)):
                 break
     return {"x": x, "z": z, "u": u, "U": U, "lam": lam, "nu": nu, "trace": trace}
+
+
+# ---------------------------------------------------------------------------
+# Elastic net (Sec. 3.1, Eq. 6)
+# ---------------------------------------------------------------------------
+
+def elastic_net_objective(A, b, gamma, x) -> float:
+    """Eq. (6): 1/2 ||A x - b||^2 + 1/2 (1 - gamma) ||x||^2 + gamma ||x||_1."""
+    res = A @ x - b
+    return (0.5 * float(res @ res) + 0.5 * (1.0 - gamma) * float(x @ x)
+            + gamma * float(np.sum(np.abs(x))))
+
+
+def elastic_net_kkt_eta(A, b, gamma, x) -> float:
+    """Relative prox-gradient fixed-point residual of Eq. (6), the analogue of
+    Eq. (31) with the smooth part's gradient A^T(Ax - b) + (1 - gamma) x."""
+    res = A @ x - b
+    g = A.T @ res + (1.0 - gamma) * x
+    num = np.linalg.norm(x - soft_threshold(x - g, gamma))
+    return float(num / (1.0 + np.linalg.norm(x) + np.linalg.norm(res)))
+
+
+def elastic_net_nysadmm(A, b, gamma, rho, Omega, admm_iters, **kw):
+    """Alg. NysADMM applied to Eq. (6): l = 1/2||. - b||^2, g = 1/2 (1 - gamma)||.||^2,
+    h = gamma ||.||_1, so the sketched Hessian is A^T A + (1 - gamma) I (Sec. 3.1)."""
+    return lasso_nysadmm(A, b, gamma, rho, Omega, admm_iters, mu=1.0 - gamma, **kw)
 
 
 # ---------------------------------------------------------------------------

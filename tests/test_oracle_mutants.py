@@ -14,6 +14,7 @@ _orig_precond = o.precond_apply
 _orig_sketch = o.nystrom_from_sketch
 _orig_pcg = o.pcg
 _orig_soft = o.soft_threshold
+_orig_lasso = o.lasso_nysadmm
 
 
 def _precond_drop_scale(U, lam, rho, v):          # (lam_s + rho) factor dropped
@@ -84,6 +85,16 @@ def _pcg_no_rho(H_apply, rho, U, lam, r, x0, tol, tol_mode="rel", maxit=None, fi
                      fixed_iters)
 
 
+def _enet_no_hessian_of_g(A, b, gamma, rho, Omega, admm_iters, **kw):
+    # H^g = (1 - gamma) I dropped from the subproblem and the sketch
+    return _orig_lasso(A, b, gamma, rho, Omega, admm_iters, **kw)
+
+
+def _enet_swapped_weights(A, b, gamma, rho, Omega, admm_iters, **kw):
+    # l2 weight gamma and l1 weight 1 - gamma
+    return _orig_lasso(A, b, 1.0 - gamma, rho, Omega, admm_iters, mu=gamma, **kw)
+
+
 def _soft_wrong_sign(v, kappa):
     return np.sign(v) * np.maximum(np.abs(v) + kappa, 0.0)
 
@@ -97,6 +108,10 @@ MUTANTS = [
     ("pcg", _pcg_wrong_beta, [pins.check_pcg_iterates_match_scipy]),
     ("pcg", _pcg_no_rho, [pins.check_pcg_direct]),
     ("soft_threshold", _soft_wrong_sign, [pins.check_soft_threshold, pins.check_lasso_orthonormal]),
+    ("elastic_net_nysadmm", _enet_no_hessian_of_g, [pins.check_elastic_net_orthonormal,
+                                                    pins.check_elastic_net_augmented_brute_force]),
+    ("elastic_net_nysadmm", _enet_swapped_weights, [pins.check_elastic_net_orthonormal,
+                                                    pins.check_elastic_net_augmented_brute_force]),
 ]
 
 

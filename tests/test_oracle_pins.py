@@ -366,6 +366,70 @@ def test_lasso_residuals_decrease_and_record():
     assert max(tr["pcg_iters"][1:]) <= 30
 
 
+# ---------------------------------------------------------------- elastic net
+
+def _enet_run(A, b, gamma, rho=1.0, s=None, iters=300, seed=0):
+    d = A.shape[1]
+    s = s or min(d, 8)
+    Om = gen.gaussian_test_matrix(d, s, seed)
+    return o.elastic_net_nysadmm(A, b, gamma, rho, Om, iters, pcg_tol=1e-13)
+
+
+def check_elastic_net_orthonormal(seed=21):
+    # A^T A = I: the minimiser of Eq. (6) is S_gamma(A^T b) / (2 - gamma)
+    A = gen.orthonormal_columns(60, 12, seed)
+    b = np.random.default_rng(seed).standard_normal(60) * 2
+    gamma = 0.6
+    out = _enet_run(A, b, gamma, rho=1.0, s=4, iters=200)
+    ref = np.sign(A.T @ b) * np.maximum(np.abs(A.T @ b) - gamma, 0) / (2.0 - gamma)
+    assert np.linalg.norm(out["z"] - ref) <= 1e-9 * max(1.0, np.linalg.norm(ref))
+
+
+def test_elastic_net_orthonormal_closed_form():
+    check_elastic_net_orthonormal()
+
+
+def check_elastic_net_augmented_brute_force(seed=22):
+    # Eq. (6) is the lasso of the stacked data [A; sqrt(1-gamma) I], [b; 0]:
+    # its sign-pattern enumeration is independent of the ADMM iteration
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((20, 5)) * gen.column_scales(5, 0.5)[None, :]
+    b = rng.standard_normal(20)
+    gamma = 0.3
+    At = np.vstack([A, math.sqrt(1.0 - gamma) * np.eye(5)])
+    bt = np.concatenate([b, np.zeros(5)])
+    ref, fref = _lasso_brute_force(At, bt, gamma)
+    out = _enet_run(A, b, gamma, rho=1.0, s=3, iters=1500)
+    assert np.linalg.norm(out["z"] - ref) <= 1e-7 * max(1, np.linalg.norm(ref))
+    assert o.elastic_net_objective(A, b, gamma, out["z"]) == pytest.approx(fref, rel=1e-10)
+
+
+def test_elastic_net_augmented_lasso_brute_force():
+    check_elastic_net_augmented_brute_force()
+
+
+def check_elastic_net_kkt(seed=23):
+    p = gen.lasso_problem(300, 60, nnz=6, seed=seed)
+    gamma = 0.5 * np.max(np.abs(p.A.T @ p.b)) / (1 + np.max(np.abs(p.A.T @ p.b)))
+    out = _enet_run(p.A, p.b, gamma, rho=10.0, s=20, iters=600)
+    assert o.elastic_net_kkt_eta(p.A, p.b, gamma, out["z"]) <= 1e-10
+    # the minimiser of the lasso part alone is worse for Eq. (6)
+    lz = _lasso_run(p.A, p.b, gamma, rho=10.0, s=20, iters=600)["z"]
+    assert o.elastic_net_objective(p.A, p.b, gamma, out["z"]) < o.elastic_net_objective(p.A, p.b, gamma, lz)
+
+
+def test_elastic_net_kkt_at_convergence():
+    check_elastic_net_kkt()
+
+
+def test_elastic_net_gamma_one_is_the_lasso():
+    p = gen.lasso_small(0)
+    Om = gen.gaussian_test_matrix(500, 50, 0)
+    a = o.elastic_net_nysadmm(p.A, p.b, 1.0, p.rho, Om, 5, pcg_fixed=4)
+    c = o.lasso_nysadmm(p.A, p.b, 1.0, p.rho, Om, 5, pcg_fixed=4)
+    assert np.array_equal(a["z"], c["z"])
+
+
 # ---------------------------------------------------------------- logistic
 
 def test_logistic_weights_identities():
