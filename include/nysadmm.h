@@ -58,7 +58,7 @@ typedef enum {
 
 /* Loss l(Ax; b): the lasso (Eq. 2, D = I) or l1-regularised logistic
  * regression (Eq. 9 with labels b in {-1,+1} mapped to (1+b)/2). */
-typedef enum { NYS_LASSO = 0, NYS_LOGISTIC = 1 } nys_loss;
+typedef enum { NYS_LASSO = 0, NYS_LOGISTIC = 1, NYS_ELASTIC_NET = 2 } nys_loss;
 
 /* Storage of A.  NYS_FP8E4M3: 8-bit E4M3 codes q with one FP32 scale per column,
  * A_ij = col_scale[j] * q_ij (the per-column-scaled FP8 form of the mixed precision
@@ -195,6 +195,10 @@ nys_status pcg_solve(const nys_matrix* A, const double* D, double rho, nys_preco
  * loss NYS_LASSO: sketch once, then opts->admm_maxit ADMM iterations with
  * PCG tolerance `tol` (mode opts->pcg_tol_mode), warm-started at the previous
  * x, z-update by soft-thresholding at gamma/rho.
+ * loss NYS_ELASTIC_NET (Sec. 3.1, Eq. 6; 0 < gamma <= 1, else NYS_EINVAL):
+ * as NYS_LASSO with g(x) = (1 - gamma)/2 ||x||^2, so the sketched Hessian is
+ * A^T A + (1 - gamma) I, the PCG matrix A^T A + (1 - gamma + rho) I, and the
+ * z-update soft-thresholds at gamma/rho.
  * loss NYS_LOGISTIC: D and the right-hand side are refreshed from
  * t = A x~ at every outer iteration (Sec. 3.2); the rank is chosen by
  * Alg. AdaptiveRandNysAppx from `rank` up to opts->rank_max at the first
@@ -242,9 +246,11 @@ nys_status nysadmm_solve_batch(int32_t count, const nys_lasso_instance* inst, do
                                const nys_opts* opts, nys_info* infos);
 
 /* Objective and optimality measures at x (FP64, one read of A):
- * out[0] = l(Ax; b) + gamma ||x||_1 (Eq. 2 or Eq. 9);
- * out[1] = relative KKT residual eta (Eq. 31; lasso) or ||A^T(sigma(Ax)-b01)||_inf (logistic);
- * out[2] = duality gap at the scaled-residual dual point (lasso) or 0 (logistic).
+ * out[0] = l(Ax; b) + g(x) + gamma ||x||_1 (Eq. 2, Eq. 6 or Eq. 9);
+ * out[1] = relative KKT residual eta (Eq. 31, with the gradient of g added for the
+ *          elastic net) or ||A^T(sigma(Ax)-b01)||_inf (logistic);
+ * out[2] = duality gap at the scaled-residual dual point (lasso; the elastic net as
+ *          the lasso of the stacked data [A; sqrt(1-gamma) I], [b; 0]) or 0 (logistic).
  * x: device, length d, FP64; out: host, length 3. */
 nys_status nys_objective(int32_t loss, const nys_matrix* A, const double* b, double gamma,
                          const double* x, double* out, void* stream);

@@ -317,6 +317,22 @@ def elastic_net_kkt_eta(A, b, gamma, x) -> float:
     return float(num / (1.0 + np.linalg.norm(x) + np.linalg.norm(res)))
 
 
+def elastic_net_dual_gap(A, b, gamma, x) -> float:
+    """Duality gap of Eq. (6) written as the lasso of the stacked data
+    [A; sqrt(1 - gamma) I], [b; 0]: primal minus the lasso dual at the scaled
+    stacked residual theta = [b - A x; -sqrt(1 - gamma) x] * min(1, gamma / ||stacked A^T theta||_inf)."""
+    mu = 1.0 - gamma
+    d = A.shape[1]
+    At = np.vstack([A, math.sqrt(mu) * np.eye(d)])
+    bt = np.concatenate([b, np.zeros(d)])
+    theta = bt - At @ x
+    s = np.max(np.abs(At.T @ theta))
+    if s > gamma:
+        theta = theta * (gamma / s)
+    dual = 0.5 * float(bt @ bt) - 0.5 * float((bt - theta) @ (bt - theta))
+    return elastic_net_objective(A, b, gamma, x) - dual
+
+
 def elastic_net_nysadmm(A, b, gamma, rho, Omega, admm_iters, **kw):
     """Alg. NysADMM applied to Eq. (6): l = 1/2||. - b||^2, g = 1/2 (1 - gamma)||.||^2,
     h = gamma ||.||_1, so the sketched Hessian is A^T A + (1 - gamma) I (Sec. 3.1)."""

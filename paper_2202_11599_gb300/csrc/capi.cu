@@ -371,11 +371,14 @@ nys_status to_f64(const nys_matrix* A, const void* y, double* out, int64_t d, cu
   return NYS_OK;
 }
 
-// ---------------------------------------------------------------- lasso NysADMM
+// ---------------------------------------------------------------- lasso / elastic-net NysADMM
+// mu: H^g = mu I of a quadratic g (0 for the lasso; 1 - gamma for the elastic net of Eq. 6).
+// The sketched Hessian is A^T A + mu I (Alg. NysADMM), the PCG matrix A^T A + (mu + rho) I,
+// and the right-hand side stays q + rho (z - u) (the H^g x and grad g terms of Eq. ADMMSubProb cancel).
 template <typename C>
-nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* b, double gamma, double rho,
-                      int rank, double tol, const double* Omega, const nys_opts& o, double* x_out, double* z_out,
-                      nys_info* info, cudaStream_t st) {
+nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* b, double gamma, double mu,
+                      double rho, int rank, double tol, const double* Omega, const nys_opts& o, double* x_out,
+                      double* z_out, nys_info* info, cudaStream_t st) {
   const int64_t d = A->d;
   Pool pool(st);
   const bool refine = o.refine && (Ain != A);
@@ -386,7 +389,7 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
   if (!pool.ok()) return NYS_ENOMEM;
   NYS_CU(cudaMemcpyAsync(Om, Omega, (size_t)d * rank * sizeof(double), cudaMemcpyDeviceToDevice, st));
   NYS_TRY(cholqr2(Om, d, rank, st));
-  NYS_TRY(sketch_panel(Ain, nullptr, 0.0, Om, rank, Y, st));
+  NYS_TRY(sketch_panel(Ain, nullptr, mu, Om, rank, Y, st));
   const double shs = o.shift_scale > 0 ? o.shift_scale : std::sqrt((double)d);
   nys_status ps = precond_from_panels(Om, Y, d, rank, shs, mant_bits_of(Ain), &P, st);
   struct Guard {
@@ -439,7 +442,7 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
   PcgProblem pb;
   pb.A = Ain;
   pb.D = nullptr;
-  pb.rho = rho;
+  pb.rho = rho + mu;
   apass_plan(Ain, &pb.plan);
   const int maxit = o.pcg_maxit > 0 ? o.pcg_maxit : (int)std::min<int64_t>(d, 1000);
   if (o.device_loop && (!refine || A->dtype == NYS_F64)) {
@@ -465,6 +468,7 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
     g.hx = hx;
     g.gamma = gamma;
     g.rho = rho;
+    g.mu = mu;
     g.K = K;
     g.eps_abs = o.eps_abs;
     g.eps_rel = o.eps_rel;
@@ -529,7 +533,7 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
       }
       NYS_TRY(aux_pass(A, MODE_RESID, xa, b, nullptr, nullptr, ytmp, nullptr, st));
       NYS_TRY(to_f64(A, ytmp, yres, d, st));
-      NYS_CU(admm_rhs<C>(d, q, z, u, rho, x, yres, rc, st));
+      NYS_CU(admm_rhs<C>(d, q, z, u, rho, x, yres, rc, st, mu));
       NYS_CU(cudaMemsetAsync(xc, 0, d * sizeof(C), st));
       prm.x0_zero = true;
       if (sizeof(C) == 4 && !prm.tol_abs) prm.tol = std::max(prm.tol, 1e-6);
@@ -955,12 +959,13 @@ nys_status logistic_admm(const nys_matrix* A, const nys_matrix* Ain, const doubl
 }
 
 // ---------------------------------------------------------------- objective helpers
+// g: gradient of the loss term; mu x (g = mu/2 ||x||^2, elastic net) is added to it here
 __global__ void obj_vec_kernel(int64_t d, const double* __restrict__ x, const double* __restrict__ g, double gamma,
-                               double* part4) {
+                               double mu, double* part4) {
   __shared__ double sh[kVecThreads / 32];
   double l1 = 0, l2 = 0, kk = 0, gm = 0;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x) {
-    const double xj = x[j], gj = g[j];
+    const double xj = x[j], gj = fma(mu, xj, g[j]);
     l1 += fabs(xj);
     l2 += xj * xj;
     const double v = xj - gj;
@@ -1157,8 +1162,9 @@ nys_status nysadmm_solve(int32_t loss, const nys_matrix* A, const double* b, dou
                          double tol, const double* Omega, const nys_opts* opts, double* x_out, double* z_out,
                          nys_info* info) {
   NYS_TRY(check_matrix(A));
-  if (loss != NYS_LASSO && loss != NYS_LOGISTIC) return NYS_EINVAL;
+  if (loss != NYS_LASSO && loss != NYS_LOGISTIC && loss != NYS_ELASTIC_NET) return NYS_EINVAL;
   if (!b || !Omega || !(gamma >= 0) || !is_fin(gamma) || !(rho > 0) || !is_fin(rho)) return NYS_EINVAL;
+  if (loss == NYS_ELASTIC_NET && !(gamma > 0 && gamma <= 1)) return NYS_EINVAL;  // Eq. 6: 0 < gamma <= 1
   if (rank < 1 || rank > A->d || rank > kMaxRank || !(tol >= 0) || !is_fin(tol)) return NYS_EINVAL;
   nys_opts o;
   if (opts) o = *opts;
@@ -1172,9 +1178,11 @@ nys_status nysadmm_solve(int32_t loss, const nys_matrix* A, const double* b, dou
   }
   cudaStream_t st = stream_of(&o);
   if (info) std::memset(info, 0, sizeof(*info));
-  if (loss == NYS_LASSO) {
-    return Ain->dtype == NYS_F64 ? lasso_admm<double>(A, Ain, b, gamma, rho, rank, tol, Omega, o, x_out, z_out, info, st)
-                                 : lasso_admm<float>(A, Ain, b, gamma, rho, rank, tol, Omega, o, x_out, z_out, info, st);
+  if (loss == NYS_LASSO || loss == NYS_ELASTIC_NET) {
+    const double mu = loss == NYS_ELASTIC_NET ? 1.0 - gamma : 0.0;
+    return Ain->dtype == NYS_F64
+               ? lasso_admm<double>(A, Ain, b, gamma, mu, rho, rank, tol, Omega, o, x_out, z_out, info, st)
+               : lasso_admm<float>(A, Ain, b, gamma, mu, rho, rank, tol, Omega, o, x_out, z_out, info, st);
   }
   return Ain->dtype == NYS_F64 ? logistic_admm<double>(A, Ain, b, gamma, rho, rank, tol, Omega, o, x_out, z_out, info, st)
                                : logistic_admm<float>(A, Ain, b, gamma, rho, rank, tol, Omega, o, x_out, z_out, info, st);
@@ -1229,7 +1237,9 @@ nys_status nys_objective(int32_t loss, const nys_matrix* A, const double* b, dou
                          double* out, void* stream) {
   NYS_TRY(check_matrix(A));
   if (!b || !x || !out || !(gamma >= 0) || !is_fin(gamma)) return NYS_EINVAL;
-  if (loss != NYS_LASSO && loss != NYS_LOGISTIC) return NYS_EINVAL;
+  if (loss != NYS_LASSO && loss != NYS_LOGISTIC && loss != NYS_ELASTIC_NET) return NYS_EINVAL;
+  if (loss == NYS_ELASTIC_NET && !(gamma > 0 && gamma <= 1)) return NYS_EINVAL;
+  const double mu = loss == NYS_ELASTIC_NET ? 1.0 - gamma : 0.0;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int64_t d = A->d, n = A->n;
   Pool pool(st);
@@ -1248,10 +1258,10 @@ nys_status nys_objective(int32_t loss, const nys_matrix* A, const double* b, dou
     xa = x32;
   }
   double lossv = 0.0;
-  NYS_TRY(aux_pass(A, loss == NYS_LASSO ? MODE_RESID : MODE_LGRAD, xa, b, nullptr, t, ytmp, &lossv, st));
+  NYS_TRY(aux_pass(A, loss == NYS_LOGISTIC ? MODE_LGRAD : MODE_RESID, xa, b, nullptr, t, ytmp, &lossv, st));
   NYS_TRY(to_f64(A, ytmp, g, d, st));
   count_launch();
-  obj_vec_kernel<<<nbd, kVecThreads, 0, st>>>(d, x, g, gamma, p4);
+  obj_vec_kernel<<<nbd, kVecThreads, 0, st>>>(d, x, g, gamma, mu, p4);
   NYS_CU(cudaGetLastError());
   count_launch();
   obj_row_kernel<<<nbn, kVecThreads, 0, st>>>(n, t, b, p2);
@@ -1271,13 +1281,15 @@ nys_status nys_objective(int32_t loss, const nys_matrix* A, const double* b, dou
     bres += h2[2 * i];
     bb += h2[2 * i + 1];
   }
-  const double F = lossv + gamma * l1;
+  const double F = lossv + 0.5 * mu * l2 + gamma * l1;
   out[0] = F;
-  if (loss == NYS_LASSO) {
+  if (loss != NYS_LOGISTIC) {
+    // lasso dual at the scaled residual; the elastic net as the lasso of the stacked data
+    // [A; sqrt(mu) I], [b; 0], whose residual adds -sqrt(mu) x (squared norm mu ||x||^2)
     const double res2 = 2.0 * lossv;
     out[1] = std::sqrt(kk) / (1.0 + std::sqrt(l2) + std::sqrt(res2));
     const double c = gm > gamma ? gamma / gm : 1.0;
-    const double dual = -c * bres - 0.5 * c * c * res2;
+    const double dual = -c * bres - 0.5 * c * c * (res2 + mu * l2);
     out[2] = F - dual;
   } else {
     out[1] = gm;

@@ -449,14 +449,15 @@ template nys_status precond_apply_run<float>(const PrecondView&, int64_t, const 
 
 // ------------------------------------------------------------------ ADMM vector kernels (FP64 state)
 
-// r = q + rho (z - u)   or, for the refined x-step, r = rho (z - u - x) - yres
+// r = q + rho (z - u)   or, for the refined x-step, the residual of Eq. ADMMSubProb at x:
+// r = rho (z - u - x) - mu x - yres  (yres = A^T (A x - b); mu = 0 except for H^g = mu I)
 template <typename C>
 __global__ void admm_rhs_kernel(int64_t d, const double* __restrict__ q, const double* __restrict__ z,
                                 const double* __restrict__ u, double rho, const double* __restrict__ x,
-                                const double* __restrict__ yres, C* __restrict__ r) {
+                                const double* __restrict__ yres, C* __restrict__ r, double mu) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x) {
     const double zu = z[j] - u[j];
-    const double rj = yres ? rho * (zu - x[j]) - yres[j] : fma(rho, zu, q[j]);
+    const double rj = yres ? rho * (zu - x[j]) - mu * x[j] - yres[j] : fma(rho, zu, q[j]);
     r[j] = (C)rj;
   }
 }
@@ -543,15 +544,15 @@ int admm_blocks(int64_t d) { return reduce_blocks(d); }
 
 template <typename C>
 cudaError_t admm_rhs(int64_t d, const double* q, const double* z, const double* u, double rho, const double* x,
-                     const double* yres, C* r, cudaStream_t st) {
+                     const double* yres, C* r, cudaStream_t st, double mu) {
   count_launch();
-  admm_rhs_kernel<C><<<admm_blocks(d), kVecThreads, 0, st>>>(d, q, z, u, rho, x, yres, r);
+  admm_rhs_kernel<C><<<admm_blocks(d), kVecThreads, 0, st>>>(d, q, z, u, rho, x, yres, r, mu);
   return cudaGetLastError();
 }
 template cudaError_t admm_rhs<double>(int64_t, const double*, const double*, const double*, double, const double*,
-                                      const double*, double*, cudaStream_t);
+                                      const double*, double*, cudaStream_t, double);
 template cudaError_t admm_rhs<float>(int64_t, const double*, const double*, const double*, double, const double*,
-                                     const double*, float*, cudaStream_t);
+                                     const double*, float*, cudaStream_t, double);
 
 template <typename C>
 cudaError_t admm_zu(int64_t d, const C* xc, int accumulate, double* x, double* z, double* u, double kappa,
@@ -647,16 +648,16 @@ __global__ void admm_begin_kernel(AdmmCtl* ctl, PcgState* st, double tol, int to
   cudaGraphSetConditional(hx_cond, ctl->hx_skip ? 0u : 1u);
 }
 
-// r = q + rho (z - u); refined step: r = rho (z - u - x) - yres, and the PCG starts at 0.
+// r = q + rho (z - u); refined step: r = rho (z - u - x) - mu x - yres, and the PCG starts at 0.
 template <typename C>
 __global__ void admm_rhs_g_kernel(int64_t d, const double* __restrict__ q, const double* __restrict__ z,
-                                  const double* __restrict__ u, double rho, const double* __restrict__ x,
+                                  const double* __restrict__ u, double rho, double mu, const double* __restrict__ x,
                                   const double* __restrict__ yres, int refine, C* __restrict__ r, C* __restrict__ xc,
                                   C* __restrict__ hx) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x) {
     const double zu = z[j] - u[j];
     if (refine) {
-      r[j] = (C)(rho * (zu - x[j]) - yres[j]);
+      r[j] = (C)(rho * (zu - x[j]) - mu * x[j] - yres[j]);
       xc[j] = C(0);
       hx[j] = C(0);
     } else {
@@ -931,7 +932,8 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   // PCG-init update kernel itself (one launch fewer per iteration)
   const bool fuse_rhs = !refine && !use_ws;
   if (!fuse_rhs) {
-    admm_rhs_g_kernel<C><<<nbz, kVecThreads, 0, cap>>>(d, g.q, g.z, g.u, g.rho, g.x, g.yres, refine, rc, xc, hx);
+    admm_rhs_g_kernel<C><<<nbz, kVecThreads, 0, cap>>>(d, g.q, g.z, g.u, g.rho, g.mu, g.x, g.yres, refine, rc, xc,
+                                                        hx);
     ++seg_nodes;
   }
   float* feat = nullptr;
@@ -985,7 +987,7 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
     aa.p = xc;
     aa.skip = nullptr;
     G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, true));
-    G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho, hx, nullptr, 0, cap));
+    G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho + g.mu, hx, nullptr, 0, cap));
     G_OK(cudaStreamEndCapture(cap, &hbody));
     G_OK(cudaStreamBeginCaptureToGraph(cap, body, &n_hx, nullptr, 1, cudaStreamCaptureModeRelaxed));
   }
@@ -1015,7 +1017,7 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   aa.p = p;
   aa.skip = &st->done;
   G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, true));
-  G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho, v, pv_part, nbr, cap));
+  G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho + g.mu, v, pv_part, nbr, cap));
   pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, cap>>>(0, d, chunk, xc, w, rc, v, p, U, s, pv_part, nbr, wy_part,
                                                           nb5, part_w2, part_r2, part_g, st, hx, cvec, gs, h_pcg, 1,
                                                           nullptr, nullptr, nullptr, 0.0, (C*)nullptr);

@@ -83,7 +83,7 @@ nys_status precond_apply_run(const PrecondView& P, int64_t d, const C* V, C* Y, 
 
 template <typename C>
 cudaError_t admm_rhs(int64_t d, const double* q, const double* z, const double* u, double rho, const double* x,
-                     const double* yres, C* r, cudaStream_t st);
+                     const double* yres, C* r, cudaStream_t st, double mu = 0.0);
 template <typename C>
 cudaError_t admm_zu(int64_t d, const C* xc, int accumulate, double* x, double* z, double* u, double kappa,
                     double* ztrace, double* part5, cudaStream_t st);
@@ -117,6 +117,7 @@ struct GraphLoopArgs {
   double *x = nullptr, *z = nullptr, *u = nullptr, *q = nullptr;
   void *xc = nullptr, *rc = nullptr, *hx = nullptr;  // compute type, length d
   double gamma = 0, rho = 1;
+  double mu = 0;             // H^g = mu I (elastic net): the H-matvec shift is rho + mu
   int K = 1;
   double eps_abs = 0, eps_rel = 0;
   double tol = 1e-8;

@@ -69,3 +69,20 @@ def test_invalid_arguments_rejected_before_any_launch(libpath):
     assert L.nys_hmatvec(ctypes.byref(m), None, 0.0, ctypes.c_void_p(16), ctypes.c_void_p(32), None) == nx.NYS_EINVAL
     m = nx.NysMatrixC(ctypes.c_void_p(16), nx.NYS_F32, 10, 16, 16, ctypes.c_void_p(64))
     assert L.nys_hmatvec(ctypes.byref(m), None, 0.0, ctypes.c_void_p(16), ctypes.c_void_p(32), None) == nx.NYS_EINVAL
+
+
+def test_elastic_net_gamma_range_checked_on_host(libpath):
+    from paper_2202_11599_gb300 import nysadmm as nx
+    L = nx.lib()
+    m = nx.NysMatrixC(ctypes.c_void_p(16), nx.NYS_F64, 10, 16, 16)
+    p = ctypes.c_void_p(64)
+    for gamma in (0.0, -0.5, 1.5, float("nan")):
+        # Eq. 6 needs 0 < gamma <= 1: rejected before any device work
+        assert L.nysadmm_solve(nx.NYS_ELASTIC_NET, ctypes.byref(m), p, ctypes.c_double(gamma),
+                               ctypes.c_double(1.0), 4, ctypes.c_double(1e-6), p, None, None, None,
+                               None) == nx.NYS_EINVAL
+        out = (ctypes.c_double * 3)()
+        assert L.nys_objective(nx.NYS_ELASTIC_NET, ctypes.byref(m), p, ctypes.c_double(gamma), p,
+                               out, None) == nx.NYS_EINVAL
+    assert L.nysadmm_solve(7, ctypes.byref(m), p, ctypes.c_double(0.5), ctypes.c_double(1.0), 4,
+                           ctypes.c_double(1e-6), p, None, None, None, None) == nx.NYS_EINVAL

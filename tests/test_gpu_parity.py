@@ -357,6 +357,84 @@ def test_lasso_mixed_precision_reaches_fp64_solution(dtype):
     assert np.linalg.norm(z - ref["z"]) <= 1e-6 * np.linalg.norm(ref["z"])
 
 
+def _enet_case():
+    """Elastic net (Eq. 6) on the 800 x 120 lasso matrix scaled by 10 (so that
+    gamma = 1/2 leaves a sparse but non-trivial solution), rho = 100, rank 20."""
+    p = gen.lasso_problem(800, 120, nnz=10, seed=21)
+    return 10.0 * p.A, p.b, 0.5, 100.0, gen.gaussian_test_matrix(120, 20, 21)
+
+
+def test_elastic_net_trajectory_parity_fp64():
+    """Elastic net, 2,000 x 500 FP64 (the lasso matrix scaled by 10), gamma 1/2,
+    rho 100, rank 50, 200 ADMM iterations: the GPU replays the oracle's PCG counts
+    (device loop and host loop), so x must agree to 1e-10."""
+    p = gen.lasso_small(0)
+    A = 10.0 * p.A
+    Om = gen.gaussian_test_matrix(500, 50, 0)
+    ref = o.elastic_net_nysadmm(A, p.b, 0.5, 100.0, Om, 200, pcg_tol=1e-8)
+    assert np.count_nonzero(ref["z"]) > 10
+    M = nx.Matrix.padded(_dev(A))
+    for loop in (True, False):
+        out = nx.nysadmm_solve("elastic_net", M, _dev(p.b), 0.5, 100.0, 50, 1e-8, _dev(Om), admm_iters=200,
+                               pcg_fixed=ref["trace"]["pcg_iters"], z_trace=True, device_loop=loop)
+        x = out["x"].cpu().numpy()
+        z = out["z"].cpu().numpy()
+        assert np.linalg.norm(x - ref["x"]) <= 1e-10 * np.linalg.norm(ref["x"])
+        assert np.linalg.norm(z - ref["z"]) <= 1e-10 * np.linalg.norm(ref["z"])
+        zt = out["z_trace"].cpu().numpy()
+        assert np.linalg.norm(zt[57] - ref["trace"]["z"][57]) <= 1e-10 * np.linalg.norm(ref["trace"]["z"][57])
+        assert out["info"]["pcg_iters_total"] == sum(ref["trace"]["pcg_iters"])
+        assert out["info"]["nu"] > 0
+
+
+def test_elastic_net_converges_objective_kkt_and_gap():
+    A, b, gamma, rho, Om = _enet_case()
+    ref = o.elastic_net_nysadmm(A, b, gamma, rho, Om, 600, pcg_tol=1e-12)
+    M = nx.Matrix.padded(_dev(A))
+    out = nx.nysadmm_solve("elastic_net", M, _dev(b), gamma, rho, 20, 1e-12, _dev(Om), admm_iters=600,
+                           hx_refresh=50)
+    z = out["z"].cpu().numpy()
+    assert np.linalg.norm(z - ref["z"]) <= 1e-9 * np.linalg.norm(ref["z"])
+    F, eta, gap = nx.objective("elastic_net", M, _dev(b), gamma, out["z"])
+    assert F == pytest.approx(o.elastic_net_objective(A, b, gamma, z), rel=1e-12)
+    # at the solution eta is a difference of nearly equal terms (x and the prox of a
+    # gradient step): on the ~15 nonzeros it is the gradient's own rounding, where the two
+    # sides sum A^T (A x - b) in different orders (800 terms, |A|^T |A x - b| <= 71:
+    # ~71 * sqrt(800) * 2^-53 ~ 2e-13 per entry), so the bound is absolute, 2e-12
+    assert eta == pytest.approx(o.elastic_net_kkt_eta(A, b, gamma, z), rel=1e-6, abs=2e-12)
+    assert gap == pytest.approx(o.elastic_net_dual_gap(A, b, gamma, z), rel=1e-6, abs=1e-9)
+    assert eta < 1e-10
+    # a perturbed point: measures of the objective only (no solve), against the oracle
+    zb = out["z"] + 0.01
+    F2, eta2, gap2 = nx.objective("elastic_net", M, _dev(b), gamma, zb)
+    zbn = zb.cpu().numpy()
+    assert F2 == pytest.approx(o.elastic_net_objective(A, b, gamma, zbn), rel=1e-12)
+    assert eta2 == pytest.approx(o.elastic_net_kkt_eta(A, b, gamma, zbn), rel=1e-10)
+    assert gap2 == pytest.approx(o.elastic_net_dual_gap(A, b, gamma, zbn), rel=1e-10)
+    for bad in (0.0, 1.5):
+        with pytest.raises(nx.NysError) as e:
+            nx.objective("elastic_net", M, _dev(b), bad, out["z"])
+        assert e.value.status == nx.NYS_EINVAL
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float32])
+def test_elastic_net_mixed_precision_reaches_fp64_solution(dtype):
+    """Sketch and PCG on the low-precision copy (A^T A + (1 - gamma + rho) I), FP64
+    residual correction with the FP64 matrix (which carries the (1 - gamma) x term)."""
+    A, b, gamma, rho, Om = _enet_case()
+    ref = o.elastic_net_nysadmm(A, b, gamma, rho, Om, 600, pcg_tol=1e-12)
+    M = nx.Matrix.padded(_dev(A))
+    Mi = nx.Matrix.padded(_dev(A), dtype)
+    for loop in (True, False):
+        out = nx.nysadmm_solve("elastic_net", M, _dev(b), gamma, rho, 20, 1e-6, _dev(Om), admm_iters=600,
+                               A_inner=Mi, refine=True, device_loop=loop)
+        z = out["z"].cpu().numpy()
+        F = o.elastic_net_objective(A, b, gamma, z)
+        Fr = o.elastic_net_objective(A, b, gamma, ref["z"])
+        assert (F - Fr) / Fr <= 1e-9
+        assert np.linalg.norm(z - ref["z"]) <= 1e-6 * np.linalg.norm(ref["z"])
+
+
 def test_logistic_trajectory_parity():
     p = gen.logistic_problem(3000, 100, decay=0.5, nnz=5, seed=24)
     pool = gen.gaussian_test_matrix(100, 40, 24)

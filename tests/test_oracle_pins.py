@@ -412,7 +412,12 @@ def check_elastic_net_kkt(seed=23):
     p = gen.lasso_problem(300, 60, nnz=6, seed=seed)
     gamma = 0.5 * np.max(np.abs(p.A.T @ p.b)) / (1 + np.max(np.abs(p.A.T @ p.b)))
     out = _enet_run(p.A, p.b, gamma, rho=10.0, s=20, iters=600)
-    assert o.elastic_net_kkt_eta(p.A, p.b, gamma, out["z"]) <= 1e-10
+    z = out["z"]
+    assert o.elastic_net_kkt_eta(p.A, p.b, gamma, z) <= 1e-10
+    F = o.elastic_net_objective(p.A, p.b, gamma, z)
+    assert 0 <= o.elastic_net_dual_gap(p.A, p.b, gamma, z) <= 1e-10 * F
+    zb = z + 0.01      # the gap bounds the suboptimality of any point
+    assert o.elastic_net_dual_gap(p.A, p.b, gamma, zb) >= o.elastic_net_objective(p.A, p.b, gamma, zb) - F > 0
     # the minimiser of the lasso part alone is worse for Eq. (6)
     lz = _lasso_run(p.A, p.b, gamma, rho=10.0, s=20, iters=600)["z"]
     assert o.elastic_net_objective(p.A, p.b, gamma, out["z"]) < o.elastic_net_objective(p.A, p.b, gamma, lz)
