@@ -6,8 +6,10 @@ G ~ N(0,1)^{100000 x 10000} and Q a random orthogonal matrix, stored in BF16 (th
 copy the sketch and PCG read) with its exact FP64 widening as the problem
 matrix; x* 1% sparse N(0,1), b = A x* + 1e-3 N(0,1), gamma = 0.05 ||A^T b||_inf,
 Nystrom rank 200, rho = 100 (chosen by a sweep; the configuration does not fix
-rho).  One step = one full solve through the C ABI: sketch + FP64 Nystrom core +
-k* ADMM iterations, where k* is the first iteration whose z reaches
+rho).  PCG runs in FP32 on the BF16 copy with the decaying tolerance schedule
+||w|| <= ||r^k|| / k^2 of the paper's Sec. 5.  One step = one full solve through the
+C ABI: sketch + FP64 Nystrom core + k* ADMM iterations, where k* is the first
+iteration whose z reaches
 (F(z) - F*)/F* <= 1e-6 on the FP64 objective (calibrated before timing).
 
 Default run: N = 1 GPU, 3 warm-up and 3 timed steps.  Inputs (2 GB BF16 +
@@ -103,7 +105,7 @@ def make_workload(device="cuda"):
     W = gen.lasso_large_torch(n, d, nnz_frac=0.01, noise=1e-3, gamma_frac=0.05, seed=1, device=device)
     g = torch.Generator(device=device).manual_seed(11)
     Om = torch.randn(d, s, generator=g, device=device, dtype=torch.float64)
-    return {"n": n, "d": d, "s": s, "rho": 100.0, "pcg_tol": 1e-4, "pcg_tol_fp64": 1e-8,
+    return {"n": n, "d": d, "s": s, "rho": 100.0, "pcg_tol": 1e-4, "pcg_beta": 2.0, "pcg_tol_fp64": 1e-8,
             "A32": W["A32"], "b": W["b"], "gamma": W["gamma"], "Omega": Om}
 
 
@@ -114,6 +116,8 @@ def workload_config(w):
     return {"workload": WORKLOAD_NAME, "n": w["n"], "d": w["d"], "rank": w["s"], "rho": w["rho"],
             "gamma": "0.05*||A^T b||_inf", "A_storage": "bf16 (PCG + sketch), f64 (problem, A^T b)",
             "pcg": (f"f32, rel-tol {w['pcg_tol']:g}, warm start x_prev" if w.get("pcg_mode", "rel") == "rel"
+                    else f"f32, ||r^k|| / k^beta with beta = {w['pcg_tol']:g}, warm start x_prev"
+                    if w["pcg_mode"] == "rnorm_pow"
                     else f"f32, tol mode {w['pcg_mode']} (first solve rel-tol {w['pcg_tol']:g}), warm start x_prev"),
             "loop": "device-side (one CUDA graph per solve)",
             "decay": "(1+j)^-1, rotated", "x_star": "1% sparse", "noise": 1e-3, "seed": 1,
@@ -160,6 +164,8 @@ def run_ours(args):
 
     if args.pcg_tol is not None:
         w["pcg_tol"] = args.pcg_tol
+    elif args.pcg_mode == "rnorm_pow":
+        w["pcg_tol"] = w["pcg_beta"]
     w["pcg_mode"] = args.pcg_mode
 
     def solve_mixed(iters, trace=False):
@@ -766,9 +772,12 @@ def main():
     # bytes (no re-reads).  Pass --traffic none after changing that kernel.
     ap.add_argument("--traffic", type=lambda v: None if v == "none" else float(v), default=2.0038e9,
                     help="ncu dram bytes per A-pass launch (from a committed profile), if current")
-    ap.add_argument("--pcg-tol", type=float, default=None, help="PCG tolerance of the mixed solve (default 1e-4)")
-    ap.add_argument("--pcg-mode", choices=["rel", "abs", "sqrt_rprd"], default="rel",
-                    help="PCG stop rule of the mixed solve (sqrt_rprd: the paper's eps = sqrt(r_p r_d))")
+    ap.add_argument("--pcg-tol", type=float, default=None,
+                    help="PCG tolerance of the mixed solve (beta for rnorm_pow, default 2; rel-tol otherwise, "
+                         "default 1e-4)")
+    ap.add_argument("--pcg-mode", choices=["rel", "abs", "sqrt_rprd", "rnorm_pow"], default="rnorm_pow",
+                    help="PCG stop rule of the mixed solve (sqrt_rprd: the paper's eps = sqrt(r_p r_d); "
+                         "rnorm_pow: ||r^k|| / k^beta with beta = --pcg-tol)")
     ap.add_argument("--hx-refresh", type=int, default=100,
                     help="recompute (H + rho I) x for the PCG warm start every this many ADMM iterations")
     ap.add_argument("--admm-iters", type=int, default=0,

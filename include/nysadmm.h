@@ -69,8 +69,10 @@ typedef enum { NYS_F64 = 0, NYS_F32 = 1, NYS_BF16 = 2, NYS_FP8E4M3 = 3 } nys_dty
 /* PCG stopping test at the top of each iteration (Alg. Nystrom PCG):
  * REL: ||w|| <= tol ||r||;  ABS: ||w|| <= tol (as printed);
  * SQRT_RPRD: inside ADMM, tol_k = sqrt(r_p r_d) of the previous ADMM
- * iteration (Sec. 5 experiments), REL with `tol` at the first iteration. */
-typedef enum { NYS_TOL_REL = 0, NYS_TOL_ABS = 1, NYS_TOL_SQRT_RPRD = 2 } nys_tol_mode;
+ * iteration (Sec. 5 experiments), REL with `tol` at the first iteration;
+ * RNORM_POW: inside ADMM, ||w|| <= ||r^k|| / k^beta with beta = `tol` and k = 1, 2, ...
+ * the ADMM iteration (the decaying schedule of Sec. 5); pcg_solve rejects it. */
+typedef enum { NYS_TOL_REL = 0, NYS_TOL_ABS = 1, NYS_TOL_SQRT_RPRD = 2, NYS_TOL_RNORM_POW = 3 } nys_tol_mode;
 
 typedef struct {
   const void* data;        /* device, row-major n x ld, 16-byte aligned */
@@ -195,6 +197,9 @@ nys_status pcg_solve(const nys_matrix* A, const double* D, double rho, nys_preco
  * loss NYS_LASSO: sketch once, then opts->admm_maxit ADMM iterations with
  * PCG tolerance `tol` (mode opts->pcg_tol_mode), warm-started at the previous
  * x, z-update by soft-thresholding at gamma/rho.
+ * With opts->rank_max > rank (lasso, elastic net) the sketch size is chosen once,
+ * before the iterations, by Alg. AdaptiveRandNysAppx from `rank` up to rank_max with
+ * stop (lam_s + rho)/rho <= opts->ada_tol (Alg. AdaNysADMM); info->final_rank reports it.
  * loss NYS_ELASTIC_NET (Sec. 3.1, Eq. 6; 0 < gamma <= 1, else NYS_EINVAL):
  * as NYS_LASSO with g(x) = (1 - gamma)/2 ||x||^2, so the sketched Hessian is
  * A^T A + (1 - gamma) I, the PCG matrix A^T A + (1 - gamma + rho) I, and the

@@ -257,6 +257,8 @@ def lasso_nysadmm(A: np.ndarray, b: np.ndarray, gamma: float, rho: float, Omega:
         z^{k+1} = S_{gamma/rho}(x^{k+1} + u^k)
         u^{k+1} = u^k + x^{k+1} - z^{k+1}
         r_p     = ||x^{k+1} - z^{k+1}||,  r_d = rho ||z^k - z^{k+1}||   (Sec. 2.1)
+    pcg_tol_mode 'rnorm_pow': the decaying schedule of Sec. 5, ||w|| <= ||r^k|| / k^beta with
+    beta = pcg_tol and k = 1, 2, ... (k = 0 would divide by zero), i.e. a relative test.
     pcg_fixed: None, an int, or a per-iteration sequence of PCG iteration counts.
     Stops after admm_iters, or earlier when eps_abs/eps_rel are given and the
     residual test of Sec. 2.1 holds.
@@ -273,20 +275,26 @@ def lasso_nysadmm(A: np.ndarray, b: np.ndarray, gamma: float, rho: float, Omega:
     z = np.zeros(d)
     u = np.zeros(d)
     q = A.T @ b
-    trace = {"pcg_iters": [], "r_p": [], "r_d": [], "z": []}
+    trace = {"pcg_iters": [], "r_p": [], "r_d": [], "z": [], "pcg_res": [], "r_norm": []}
     for k in range(admm_iters):
         r = rho * z - rho * u + q
         fixed = None
         if pcg_fixed is not None:
             fixed = pcg_fixed if isinstance(pcg_fixed, int) else int(pcg_fixed[k])
-        x, it, _ = pcg(H_apply, rho, U, lam, r, x, pcg_tol, pcg_tol_mode,
-                       maxit=pcg_maxit, fixed_iters=fixed)
+        if pcg_tol_mode == "rnorm_pow":
+            tol_k, mode_k = (k + 1.0) ** (-pcg_tol), "rel"
+        else:
+            tol_k, mode_k = pcg_tol, pcg_tol_mode
+        x, it, res = pcg(H_apply, rho, U, lam, r, x, tol_k, mode_k,
+                         maxit=pcg_maxit, fixed_iters=fixed)
         z_old = z
         z = soft_threshold(x + u, gamma / rho)
         u = u + x - z
         r_p = float(np.linalg.norm(x - z))
         r_d = float(rho * np.linalg.norm(z_old - z))
         trace["pcg_iters"].append(it)
+        trace["pcg_res"].append(res)
+        trace["r_norm"].append(float(np.linalg.norm(r)))
         trace["r_p"].append(r_p)
         trace["r_d"].append(r_d)
         trace["z"].append(z.copy())

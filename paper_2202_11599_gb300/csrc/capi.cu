@@ -371,6 +371,42 @@ nys_status to_f64(const nys_matrix* A, const void* y, double* out, int64_t d, cu
   return NYS_OK;
 }
 
+// PCG tolerance of ADMM iteration k (0-based): the decaying schedule ||r^k|| / k^beta of
+// Sec. 5 (beta = tol, k counted from 1, a relative test) or the fixed tol.
+double sched_tol(int mode, double tol, int k) {
+  return mode == NYS_TOL_RNORM_POW ? std::pow((double)(k + 1), -tol) : tol;
+}
+
+// Alg. AdaptiveRandNysAppx (App. C): ranks s0, 2 s0, 4 s0, ... until (lam_s + rho)/rho <= Tol,
+// extended once to s_max when doubling would pass it.  Each new block of the Gaussian Om
+// (d x s_max) is orthonormalised on its own and its sketch H Om_block (H = A^T D A + shift I)
+// is appended to Y; the approximation is rebuilt from all blocks so far.  *used_out: the rank.
+nys_status adaptive_sketch(const nys_matrix* Ain, const double* D, double shift, double* Om, double* Y, int64_t d,
+                           int rank, int smax, double ada_tol, double rho, double shs, const TcPrepared* tcpp,
+                           nys_precond_s* P, int* used_out, cudaStream_t st) {
+  int s0 = rank, m = rank, used = 0;
+  auto add_block = [&](int cols) -> nys_status {
+    NYS_TRY(cholqr2(Om + (int64_t)used * d, d, cols, st));
+    NYS_TRY(sketch_panel(Ain, D, shift, Om + (int64_t)used * d, cols, Y + (int64_t)used * d, st, tcpp));
+    used += cols;
+    return precond_from_panels(Om, Y, d, used, shs, mant_bits_of(Ain), P, st);
+  };
+  for (;;) {
+    NYS_TRY(add_block(m));
+    if ((P->lam.back() + rho) / rho <= ada_tol) break;
+    m = s0;
+    s0 = 2 * s0;
+    if (s0 > smax) {
+      s0 = s0 - m;
+      m = smax - s0;
+      if (m > 0) NYS_TRY(add_block(m));
+      break;
+    }
+  }
+  *used_out = used;
+  return NYS_OK;
+}
+
 // ---------------------------------------------------------------- lasso / elastic-net NysADMM
 // mu: H^g = mu I of a quadratic g (0 for the lasso; 1 - gamma for the elastic net of Eq. 6).
 // The sketched Hessian is A^T A + mu I (Alg. NysADMM), the PCG matrix A^T A + (mu + rho) I,
@@ -383,15 +419,10 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
   Pool pool(st);
   const bool refine = o.refine && (Ain != A);
   // Sketch on the PCG matrix (App. B; once for a quadratic loss, Thm. NysADMM convergence).
+  // With opts.rank_max > rank the sketch size is chosen by Alg. AdaptiveRandNysAppx
+  // (Alg. AdaNysADMM); it is fixed for all iterations afterwards.
+  const int smax = o.rank_max > 0 ? std::max(o.rank_max, rank) : rank;
   nys_precond_s P;
-  double* Om = pool.alloc<double>((size_t)d * rank);
-  double* Y = pool.alloc<double>((size_t)d * rank);
-  if (!pool.ok()) return NYS_ENOMEM;
-  NYS_CU(cudaMemcpyAsync(Om, Omega, (size_t)d * rank * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  NYS_TRY(cholqr2(Om, d, rank, st));
-  NYS_TRY(sketch_panel(Ain, nullptr, mu, Om, rank, Y, st));
-  const double shs = o.shift_scale > 0 ? o.shift_scale : std::sqrt((double)d);
-  nys_status ps = precond_from_panels(Om, Y, d, rank, shs, mant_bits_of(Ain), &P, st);
   struct Guard {
     nys_precond_s* p;
     ~Guard() {
@@ -400,7 +431,19 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
       if (p->lam_d) cudaFree(p->lam_d);
     }
   } guard{&P};
-  if (ps != NYS_OK) return ps;
+  double* Om = pool.alloc<double>((size_t)d * smax);
+  double* Y = pool.alloc<double>((size_t)d * smax);
+  if (!pool.ok()) return NYS_ENOMEM;
+  NYS_CU(cudaMemcpyAsync(Om, Omega, (size_t)d * smax * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  const double shs = o.shift_scale > 0 ? o.shift_scale : std::sqrt((double)d);
+  if (smax > rank) {
+    NYS_TRY(adaptive_sketch(Ain, nullptr, mu, Om, Y, d, rank, smax, o.ada_tol > 0 ? o.ada_tol : 2.0, rho, shs,
+                            nullptr, &P, &rank, st));
+  } else {
+    NYS_TRY(cholqr2(Om, d, rank, st));
+    NYS_TRY(sketch_panel(Ain, nullptr, mu, Om, rank, Y, st));
+    NYS_TRY(precond_from_panels(Om, Y, d, rank, shs, mant_bits_of(Ain), &P, st));
+  }
   PrecondView view;
   C* cbuf = pool.alloc<C>(rank);
   if (!pool.ok()) return NYS_ENOMEM;
@@ -472,7 +515,8 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
     g.K = K;
     g.eps_abs = o.eps_abs;
     g.eps_rel = o.eps_rel;
-    g.tol = (refine && sizeof(C) == 4 && o.pcg_tol_mode != NYS_TOL_ABS) ? std::max(tol, 1e-6) : tol;
+    g.tol = tol;
+    g.tol_floor = (refine && sizeof(C) == 4) ? 1e-6 : 0.0;
     g.tol_mode = o.pcg_tol_mode;
     g.maxit = maxit;
     g.fixed_host = o.pcg_fixed_iters;
@@ -520,7 +564,7 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
   for (; k < K; ++k) {
     PcgParams prm;
     prm.maxit = maxit;
-    prm.tol = tol;
+    prm.tol = sched_tol(o.pcg_tol_mode, tol, k);
     prm.tol_abs = o.pcg_tol_mode == NYS_TOL_ABS;
     if (o.pcg_tol_mode == NYS_TOL_SQRT_RPRD && k > 0) prm.dev_tol = eps_next;
     if (o.pcg_fixed_iters) prm.fixed = o.pcg_fixed_iters[k];
@@ -642,7 +686,7 @@ nys_status lasso_path(const nys_matrix* A, const nys_matrix* Ain, const double* 
   for (int it = 0; it < K; ++it) {
     NYS_CU(batched_rhs<C>(d, k, q, Z, Uu, rho, Rc, st));
     PcgParams prm;
-    prm.tol = tol;
+    prm.tol = sched_tol(o.pcg_tol_mode, tol, it);
     prm.tol_abs = o.pcg_tol_mode == NYS_TOL_ABS;
     prm.maxit = maxit;
     prm.x0_zero = it == 0;
@@ -854,7 +898,6 @@ nys_status logistic_admm(const nys_matrix* A, const nys_matrix* Ain, const doubl
   const int maxit = o.pcg_maxit > 0 ? o.pcg_maxit : (int)std::min<int64_t>(d, 1000);
   int total_pcg = 0, cur_rank = 0;
   nys_status result = NYS_OK;
-  std::vector<int> block_end;  // orthonormalised block boundaries
   // the curvature D changes every iteration but A does not: prepare its tensor-core
   // operands once for all re-sketches
   TcPrepared tcp;
@@ -876,32 +919,7 @@ nys_status logistic_admm(const nys_matrix* A, const nys_matrix* Ain, const doubl
     NYS_TRY(aux_pass(A, MODE_LOGIT, xa, b, Dw, nullptr, ytmp, nullptr, st));
     NYS_TRY(to_f64(A, ytmp, q, d, st));
     if (k == 0) {
-      // Alg. AdaptiveRandNysAppx: ranks s0, 2 s0, 4 s0, ... until (lam_s + rho)/rho <= Tol,
-      // extended once to s_max when doubling would pass it.
-      int s0 = rank, m = rank, used = 0;
-      for (;;) {
-        NYS_TRY(cholqr2(Om + (int64_t)used * d, d, m, st));
-        NYS_TRY(sketch_panel(Ain, Dw, 0.0, Om + (int64_t)used * d, m, Y + (int64_t)used * d, st, tcpp));
-        used += m;
-        block_end.push_back(used);
-        NYS_TRY(precond_from_panels(Om, Y, d, used, shs, mant_bits_of(Ain), &P, st));
-        if ((P.lam.back() + rho) / rho <= ada_tol) break;
-        m = s0;
-        s0 = 2 * s0;
-        if (s0 > smax) {
-          s0 = s0 - m;
-          m = smax - s0;
-          if (m > 0) {
-            NYS_TRY(cholqr2(Om + (int64_t)used * d, d, m, st));
-            NYS_TRY(sketch_panel(Ain, Dw, 0.0, Om + (int64_t)used * d, m, Y + (int64_t)used * d, st, tcpp));
-            used += m;
-            block_end.push_back(used);
-            NYS_TRY(precond_from_panels(Om, Y, d, used, shs, mant_bits_of(Ain), &P, st));
-          }
-          break;
-        }
-      }
-      cur_rank = used;
+      NYS_TRY(adaptive_sketch(Ain, Dw, 0.0, Om, Y, d, rank, smax, ada_tol, rho, shs, tcpp, &P, &cur_rank, st));
     } else if (o.resketch_every > 0 && k % o.resketch_every == 0) {
       // same orthonormal blocks, new curvature D
       NYS_TRY(sketch_panel(Ain, Dw, 0.0, Om, cur_rank, Y, st, tcpp));
@@ -912,7 +930,7 @@ nys_status logistic_admm(const nys_matrix* A, const nys_matrix* Ain, const doubl
     NYS_CU(admm_rhs<C>(d, q, z, u, rho, nullptr, nullptr, rc, st));
     PcgParams prm;
     prm.maxit = maxit;
-    prm.tol = tol;
+    prm.tol = sched_tol(o.pcg_tol_mode, tol, k);
     prm.tol_abs = o.pcg_tol_mode == NYS_TOL_ABS;
     if (o.pcg_tol_mode == NYS_TOL_SQRT_RPRD && k > 0) prm.dev_tol = eps_next;
     if (o.pcg_fixed_iters) prm.fixed = o.pcg_fixed_iters[k];
@@ -1130,6 +1148,8 @@ nys_status pcg_solve(const nys_matrix* A, const double* D, double rho, nys_preco
   nys_opts o;
   if (opts) o = *opts;
   else nys_opts_default(&o);
+  // no ADMM iteration here: the schedules of Sec. 5 do not apply
+  if (o.pcg_tol_mode < NYS_TOL_REL || o.pcg_tol_mode >= NYS_TOL_RNORM_POW) return NYS_EINVAL;
   cudaStream_t st = stream_of(&o);
   PcgProblem pb;
   pb.A = A;
@@ -1171,6 +1191,7 @@ nys_status nysadmm_solve(int32_t loss, const nys_matrix* A, const double* b, dou
   else nys_opts_default(&o);
   if (o.admm_maxit < 1) return NYS_EINVAL;
   if (o.rank_max > A->d || o.rank_max > kMaxRank) return NYS_EINVAL;
+  if (o.pcg_tol_mode < NYS_TOL_REL || o.pcg_tol_mode > NYS_TOL_RNORM_POW) return NYS_EINVAL;
   const nys_matrix* Ain = o.A_inner ? o.A_inner : A;
   if (o.A_inner) {
     NYS_TRY(check_matrix(Ain));
@@ -1199,6 +1220,7 @@ nys_status nysadmm_solve_path(const nys_matrix* A, const double* b, const double
   nys_opts o;
   if (opts) o = *opts;
   else nys_opts_default(&o);
+  if (o.pcg_tol_mode < NYS_TOL_REL || o.pcg_tol_mode > NYS_TOL_RNORM_POW) return NYS_EINVAL;
   const nys_matrix* Ain = o.A_inner ? o.A_inner : A;
   if (o.A_inner) {
     NYS_TRY(check_matrix(Ain));
@@ -1228,6 +1250,7 @@ nys_status nysadmm_solve_batch(int32_t count, const nys_lasso_instance* inst, do
   if (opts) o = *opts;
   else nys_opts_default(&o);
   if (o.admm_maxit < 1) return NYS_EINVAL;
+  if (o.pcg_tol_mode < NYS_TOL_REL || o.pcg_tol_mode > NYS_TOL_RNORM_POW) return NYS_EINVAL;
   cudaStream_t st = stream_of(&o);
   return f64 ? lasso_batch<double>(count, inst, rho, tol, o, infos, st)
              : lasso_batch<float>(count, inst, rho, tol, o, infos, st);

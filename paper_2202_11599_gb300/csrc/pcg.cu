@@ -617,7 +617,7 @@ struct AdmmCtl {
 namespace {
 
 
-__global__ void admm_begin_kernel(AdmmCtl* ctl, PcgState* st, double tol, int tol_mode, int maxit,
+__global__ void admm_begin_kernel(AdmmCtl* ctl, PcgState* st, double tol, double tol_floor, int tol_mode, int maxit,
                                   const int* __restrict__ fixed_dev, int hx_refresh, int refine,
                                   cudaGraphConditionalHandle hx_cond, long long hx_nodes) {
   const int k = ctl->k;
@@ -635,9 +635,14 @@ __global__ void admm_begin_kernel(AdmmCtl* ctl, PcgState* st, double tol, int to
   if (tol_mode == NYS_TOL_SQRT_RPRD && k > 0) {
     st->tol = ctl->eps_next;
     st->tol_abs = 1;
-  } else {
+  } else if (tol_mode == NYS_TOL_ABS) {
     st->tol = tol;
-    st->tol_abs = tol_mode == NYS_TOL_ABS;
+    st->tol_abs = 1;
+  } else {
+    // REL, or the decaying schedule ||r^k|| / k^beta (beta = tol, k counted from 1)
+    const double t = tol_mode == NYS_TOL_RNORM_POW ? pow((double)(k + 1), -tol) : tol;
+    st->tol = fmax(t, tol_floor);
+    st->tol_abs = 0;
   }
   // k = 0 and refined steps start from x = 0 (hx = 0); otherwise recompute (H + rho I) x
   // when hx_refresh == 0 (as printed) or every hx_refresh iterations
@@ -904,7 +909,7 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   // ---- segment 1: begin, (exact residual pass), right-hand side, PCG init
   count_launch_suspend(true);
   G_OK(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  admm_begin_kernel<<<1, 1, 0, cap>>>(ctl, st, g.tol, g.tol_mode, g.maxit, fixed_dev, g.hx_refresh, refine, h_hx,
+  admm_begin_kernel<<<1, 1, 0, cap>>>(ctl, st, g.tol, g.tol_floor, g.tol_mode, g.maxit, fixed_dev, g.hx_refresh, refine, h_hx,
                                       2);
   ++seg_nodes;
   if (refine) {

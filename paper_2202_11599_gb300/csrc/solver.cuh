@@ -120,7 +120,8 @@ struct GraphLoopArgs {
   double mu = 0;             // H^g = mu I (elastic net): the H-matvec shift is rho + mu
   int K = 1;
   double eps_abs = 0, eps_rel = 0;
-  double tol = 1e-8;
+  double tol = 1e-8;          // beta for NYS_TOL_RNORM_POW
+  double tol_floor = 0;       // lower bound of a relative PCG tolerance (FP32 refined step)
   int tol_mode = NYS_TOL_REL;
   int maxit = 1000;
   const int* fixed_host = nullptr;

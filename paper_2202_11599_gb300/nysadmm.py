@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libnysadmm.so")
 NYS_OK, NYS_EINVAL, NYS_ENOTSPD, NYS_EBREAKDOWN, NYS_ENOCONV, NYS_ETIMEOUT, NYS_ECUDA, NYS_ENOMEM = range(8)
 NYS_LASSO, NYS_LOGISTIC, NYS_ELASTIC_NET = 0, 1, 2
 NYS_F64, NYS_F32, NYS_BF16, NYS_FP8E4M3 = 0, 1, 2, 3
-TOL_MODES = {"rel": 0, "abs": 1, "sqrt_rprd": 2}
+TOL_MODES = {"rel": 0, "abs": 1, "sqrt_rprd": 2, "rnorm_pow": 3}
 _DTYPES = {torch.float64: NYS_F64, torch.float32: NYS_F32, torch.bfloat16: NYS_BF16,
            torch.float8_e4m3fn: NYS_FP8E4M3}
 FP8_E4M3_MAX = 448.0

@@ -86,3 +86,15 @@ def test_elastic_net_gamma_range_checked_on_host(libpath):
                                out, None) == nx.NYS_EINVAL
     assert L.nysadmm_solve(7, ctypes.byref(m), p, ctypes.c_double(0.5), ctypes.c_double(1.0), 4,
                            ctypes.c_double(1e-6), p, None, None, None, None) == nx.NYS_EINVAL
+
+
+def test_unknown_tolerance_mode_rejected_on_host(libpath):
+    from paper_2202_11599_gb300 import nysadmm as nx
+    L = nx.lib()
+    m = nx.NysMatrixC(ctypes.c_void_p(16), nx.NYS_F64, 10, 16, 16)
+    p = ctypes.c_void_p(64)
+    o = nx.NysOptsC()
+    L.nys_opts_default(ctypes.byref(o))
+    o.pcg_tol_mode = 4
+    assert L.nysadmm_solve(nx.NYS_LASSO, ctypes.byref(m), p, ctypes.c_double(0.5), ctypes.c_double(1.0), 4,
+                           ctypes.c_double(1.0), p, ctypes.byref(o), None, None, None) == nx.NYS_EINVAL

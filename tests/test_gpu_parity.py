@@ -435,6 +435,59 @@ def test_elastic_net_mixed_precision_reaches_fp64_solution(dtype):
         assert np.linalg.norm(z - ref["z"]) <= 1e-6 * np.linalg.norm(ref["z"])
 
 
+@pytest.mark.parametrize("ada_tol,ranks", [(2.0, [10, 20, 40]), (1.05, [10, 20, 40, 70])])
+def test_ada_nysadmm_lasso_rank_and_trajectory(ada_tol, ranks):
+    """Alg. AdaNysADMM on the 2,000 x 500 lasso: the sketch size chosen by
+    Alg. AdaptiveRandNysAppx from 10 up to 70 (the second case doubles past 70 and is
+    extended to it), then the trajectory with the oracle's PCG counts replayed."""
+    p = gen.lasso_small(0)
+    pool = gen.gaussian_test_matrix(500, 70, 5)
+    U, lam, nu, tried = o.adaptive_nystrom(lambda X: p.A.T @ (p.A @ X), pool, 10, 70, p.rho, ada_tol)
+    assert tried == ranks
+    ref = o.lasso_nysadmm(p.A, p.b, p.gamma, p.rho, None, 60, pcg_tol=1e-8, precond=(U, lam, nu))
+    M = nx.Matrix.padded(_dev(p.A))
+    out = nx.nysadmm_solve("lasso", M, _dev(p.b), p.gamma, p.rho, 10, 1e-8, _dev(pool), admm_iters=60,
+                           pcg_fixed=ref["trace"]["pcg_iters"], rank_max=70, ada_tol=ada_tol)
+    assert out["info"]["final_rank"] == ranks[-1]
+    assert out["info"]["emp_cond"] == pytest.approx((lam[-1] + p.rho) / p.rho, rel=1e-8)
+    x = out["x"].cpu().numpy()
+    assert np.linalg.norm(x - ref["x"]) <= 1e-10 * np.linalg.norm(ref["x"])
+
+
+def test_ada_nysadmm_elastic_net_sketches_shifted_hessian():
+    p = gen.lasso_small(0)
+    A = 10.0 * p.A
+    pool = gen.gaussian_test_matrix(500, 70, 5)
+    U, lam, nu, tried = o.adaptive_nystrom(lambda X: A.T @ (A @ X) + 0.5 * X, pool, 10, 70, 100.0, 2.0)
+    ref = o.elastic_net_nysadmm(A, p.b, 0.5, 100.0, None, 40, pcg_tol=1e-8, precond=(U, lam, nu))
+    M = nx.Matrix.padded(_dev(A))
+    out = nx.nysadmm_solve("elastic_net", M, _dev(p.b), 0.5, 100.0, 10, 1e-8, _dev(pool), admm_iters=40,
+                           pcg_fixed=ref["trace"]["pcg_iters"], rank_max=70, ada_tol=2.0)
+    assert out["info"]["final_rank"] == tried[-1]
+    x = out["x"].cpu().numpy()
+    assert np.linalg.norm(x - ref["x"]) <= 1e-10 * np.linalg.norm(ref["x"])
+
+
+def test_rnorm_pow_schedule_matches_oracle():
+    """The decaying PCG schedule ||r^k|| / k^beta (Sec. 5) on the 2,000 x 500 FP64 lasso:
+    every stop decision is taken on FP64 norms on both sides, so the PCG counts (their
+    total) and the iterates agree; the device and host loops agree bit for bit."""
+    p = gen.lasso_small(0)
+    Om = gen.gaussian_test_matrix(500, 50, 0)
+    ref = o.lasso_nysadmm(p.A, p.b, p.gamma, p.rho, Om, 100, pcg_tol=1.5, pcg_tol_mode="rnorm_pow")
+    M = nx.Matrix.padded(_dev(p.A))
+    outs = [nx.nysadmm_solve("lasso", M, _dev(p.b), p.gamma, p.rho, 50, 1.5, _dev(Om), admm_iters=100,
+                             tol_mode="rnorm_pow", device_loop=loop, hx_refresh=0) for loop in (True, False)]
+    assert torch.equal(outs[0]["z"], outs[1]["z"])
+    for out in outs:
+        assert out["info"]["pcg_iters_total"] == sum(ref["trace"]["pcg_iters"])
+        x = out["x"].cpu().numpy()
+        assert np.linalg.norm(x - ref["x"]) <= 1e-9 * np.linalg.norm(ref["x"])
+    with pytest.raises(nx.NysError) as e:
+        nx.pcg_solve(M, _dev(p.b[:500].copy()), 1.0, None, tol=1.5, tol_mode="rnorm_pow")
+    assert e.value.status == nx.NYS_EINVAL
+
+
 def test_logistic_trajectory_parity():
     p = gen.logistic_problem(3000, 100, decay=0.5, nnz=5, seed=24)
     pool = gen.gaussian_test_matrix(100, 40, 24)

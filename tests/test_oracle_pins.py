@@ -366,6 +366,53 @@ def test_lasso_residuals_decrease_and_record():
     assert max(tr["pcg_iters"][1:]) <= 30
 
 
+def check_rnorm_pow_schedule(seed=14, beta=1.5):
+    """Sec. 5's decaying schedule: every x-step stops at the first PCG iterate with
+    ||w|| <= ||r^k|| / k^beta (k = 1, 2, ...), and the summable tolerances reach the
+    lasso solution (KKT eta)."""
+    p = gen.lasso_problem(300, 60, nnz=6, seed=seed)
+    Om = gen.gaussian_test_matrix(60, 20, seed)
+    out = o.lasso_nysadmm(p.A, p.b, p.gamma, 10.0, Om, 300, pcg_tol=beta, pcg_tol_mode="rnorm_pow")
+    tr = out["trace"]
+    for k in range(300):
+        assert tr["pcg_res"][k] <= tr["r_norm"][k] / (k + 1.0) ** beta
+    # minimality at a few iterations: one PCG iteration fewer misses the threshold
+    U, lam = out["U"], out["lam"]
+    H = lambda X: p.A.T @ (p.A @ X)
+    x = np.zeros(60); z = np.zeros(60); u = np.zeros(60); q = p.A.T @ p.b
+    checked = 0
+    for k in range(40):
+        r = 10.0 * (z - u) + q
+        it = tr["pcg_iters"][k]
+        if it > 0 and checked < 5:
+            _, _, res_short = o.pcg(H, 10.0, U, lam, r, x, 0.0, "abs", fixed_iters=it - 1)
+            assert res_short > np.linalg.norm(r) / (k + 1.0) ** beta
+            checked += 1
+        x, _, _ = o.pcg(H, 10.0, U, lam, r, x, 0.0, "abs", fixed_iters=it)
+        zn = o.soft_threshold(x + u, p.gamma / 10.0)
+        u = u + x - zn
+        z = zn
+    assert checked == 5
+    # summable tolerances (beta > 1): the iterates approach the solution, at a rate that
+    # follows the schedule (the error of an inexact step is O(k^-beta))
+    e300 = o.lasso_kkt_eta(p.A, p.b, p.gamma, out["z"])
+    out2 = o.lasso_nysadmm(p.A, p.b, p.gamma, 10.0, Om, 800, pcg_tol=2.0, pcg_tol_mode="rnorm_pow")
+    e800 = o.lasso_kkt_eta(p.A, p.b, p.gamma, out2["z"])
+    assert e800 < e300 and e800 <= 3e-6
+
+
+def test_rnorm_pow_schedule_threshold_minimal_and_converges():
+    check_rnorm_pow_schedule()
+
+
+def test_rnorm_pow_beta_zero_takes_no_first_step():
+    # beta = 0: the first threshold is ||r^0|| itself, met by x0 = 0 before any iteration
+    p = gen.lasso_small(0)
+    Om = gen.gaussian_test_matrix(500, 50, 0)
+    out = o.lasso_nysadmm(p.A, p.b, p.gamma, p.rho, Om, 3, pcg_tol=0.0, pcg_tol_mode="rnorm_pow")
+    assert out["trace"]["pcg_iters"][0] == 0
+
+
 # ---------------------------------------------------------------- elastic net
 
 def _enet_run(A, b, gamma, rho=1.0, s=None, iters=300, seed=0):
