@@ -124,6 +124,15 @@ def workload_config(w):
             "gap": GAP, "l2_flush": "inputs (10 GB) larger than L2 (129 MB)"}
 
 
+def apply_pcg_args(w, args):
+    """PCG stop rule of the mixed solve from the command line (both arms name it in config)."""
+    if args.pcg_tol is not None:
+        w["pcg_tol"] = args.pcg_tol
+    elif args.pcg_mode == "rnorm_pow":
+        w["pcg_tol"] = w["pcg_beta"]
+    w["pcg_mode"] = args.pcg_mode
+
+
 def max_over_ranks(value: float, dist=None) -> float:
     """The job's time is its slowest rank's: max of a per-rank scalar over all ranks
     (replicas: every rank solves its own copy of the workload).  NCCL reduces on the
@@ -162,11 +171,7 @@ def run_ours(args):
     def F(z):
         return nx.objective("lasso", M64, b, gamma, z)[0]
 
-    if args.pcg_tol is not None:
-        w["pcg_tol"] = args.pcg_tol
-    elif args.pcg_mode == "rnorm_pow":
-        w["pcg_tol"] = w["pcg_beta"]
-    w["pcg_mode"] = args.pcg_mode
+    apply_pcg_args(w, args)
 
     def solve_mixed(iters, trace=False):
         return nx.nysadmm_solve("lasso", M64, b, gamma, rho, s, w["pcg_tol"], Om, admm_iters=iters,
@@ -407,6 +412,7 @@ def run_reference(args):
     if rank != 0:
         return
     w = make_workload("cuda" if torch.cuda.is_available() else "cpu")
+    apply_pcg_args(w, args)
     A = w["A32"].double().cpu().numpy()
     b = w["b"].cpu().numpy()
     Om = w["Omega"].cpu().numpy()
@@ -444,7 +450,8 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value * 1e3, 1),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded)", "impl": "reference",
-           "config": dict(workload_config(w), admm_iters_to_gap=k_iters, F_star=Fstar),
+           "config": dict(workload_config(w), admm_iters_to_gap=k_iters, F_star=Fstar,
+                          oracle_pcg=f"f64, rel-tol {w['pcg_tol_fp64']:g} (the oracle's plain FP64 form)"),
            "cpu_baseline": {"value": round(value, 3), "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": round(value, 3), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(res), flush=True)
