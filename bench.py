@@ -293,6 +293,8 @@ def run_ours(args):
         "gpu_launches": stats["launches"],
         "clocks": clocks,
     }
+    if args.host_loop:
+        result["config"]["loop"] = "host-driven (one launch per kernel; profiling runs)"
     if f64p["launches"]:
         result["config"]["f64_rhs_pass_ms"] = round(f64p["ms"] / f64p["launches"], 4)
 
