@@ -22,6 +22,11 @@ Readings where the paper is silent or ambiguous (all listed in the design doc):
   * Adaptive rank: stop at the first rank whose empirical condition number
     (lam_s + rho)/rho <= Tol; otherwise double, and when doubling would pass
     s_max, extend to s_max once and stop.
+  * PCG schedule 'rnorm_pow' (Sec. 5's ||r^k|| / k^beta): k counts ADMM
+    iterations from 1 (k = 0 would divide by zero).
+  * Elastic net (Sec. 3.1): H^g = (1 - gamma) I enters the sketched matrix and the
+    PCG matrix, not the preconditioner's rho; its duality gap is that of the lasso
+    of the stacked data [A; sqrt(1 - gamma) I], [b; 0].
 
 Functions with no independent pin: none (every function here is pinned by a
 test in tests/test_oracle_pins.py against closed forms, library solvers,
