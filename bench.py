@@ -164,6 +164,8 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     w = make_workload()
+    if args.rho is not None:
+        w["rho"] = args.rho
     A64 = w["A32"].double()
     Abf = w["A32"].to(torch.bfloat16)
     M64, Mbf = nx.Matrix(A64), nx.Matrix(Abf)
@@ -417,6 +419,8 @@ def run_reference(args):
         return
     w = make_workload("cuda" if torch.cuda.is_available() else "cpu")
     apply_pcg_args(w, args)
+    if args.rho is not None:
+        w["rho"] = args.rho
     A = w["A32"].double().cpu().numpy()
     b = w["b"].cpu().numpy()
     Om = w["Omega"].cpu().numpy()
@@ -789,6 +793,7 @@ def main():
     ap.add_argument("--pcg-mode", choices=["rel", "abs", "sqrt_rprd", "rnorm_pow"], default="rnorm_pow",
                     help="PCG stop rule of the mixed solve (sqrt_rprd: the paper's eps = sqrt(r_p r_d); "
                          "rnorm_pow: ||r^k|| / k^beta with beta = --pcg-tol)")
+    ap.add_argument("--rho", type=float, default=None, help="ADMM step size of the main line (default 70)")
     ap.add_argument("--hx-refresh", type=int, default=100,
                     help="recompute (H + rho I) x for the PCG warm start every this many ADMM iterations")
     ap.add_argument("--admm-iters", type=int, default=0,
