@@ -11,7 +11,7 @@ Each function names the passage of the paper it restates.  NumPy / SciPy
 library routines (matmul, QR, Cholesky, SVD, triangular solve) serve as single
 steps; nothing is blocked, fused or reordered beyond the paper's algorithms.
 
-Readings where the paper is silent or ambiguous (all listed in the design doc):
+Readings where the paper is silent or ambiguous (the same readings as the CUDA path):
   * shift nu = shift_scale * eps(||Y||_2); eps(t) is the spacing of the working
     precision at t (MATLAB eps); default shift_scale = sqrt(d) (the adaptive
     algorithm's form, App. B), used for the fixed-rank sketch as well.

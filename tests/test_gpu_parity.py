@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
 same seeded inputs.  Tolerances:
-  * FP64 storage: 1e-10 relative (spec bar for the plain FP64 form);
+  * FP64 storage: 1e-10 relative (the bar for the plain FP64 form);
     single kernels 1e-12 relative to the |A|^T|A||p| scale.
   * FP32 / BF16 storage: the reference is computed in FP64 from the SAME stored
     values; the kernel accumulates in FP32, so the bound is ~ (row length) * 2^-24
