@@ -98,3 +98,24 @@ def test_unknown_tolerance_mode_rejected_on_host(libpath):
     o.pcg_tol_mode = 4
     assert L.nysadmm_solve(nx.NYS_LASSO, ctypes.byref(m), p, ctypes.c_double(0.5), ctypes.c_double(1.0), 4,
                            ctypes.c_double(1.0), p, ctypes.byref(o), None, None, None) == nx.NYS_EINVAL
+
+
+def _header_enums():
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    vals = {}
+    for body in re.findall(r"typedef enum\s*\{(.*?)\}", src, flags=re.S):
+        for name, v in re.findall(r"(\w+)\s*=\s*(-?\d+)", body):
+            vals[name] = int(v)
+    return vals
+
+
+def test_binding_constants_match_header_enums():
+    from paper_2202_11599_gb300 import nysadmm as nx
+    h = _header_enums()
+    for name in ("NYS_OK", "NYS_EINVAL", "NYS_ENOTSPD", "NYS_EBREAKDOWN", "NYS_ENOCONV", "NYS_ETIMEOUT",
+                 "NYS_ECUDA", "NYS_ENOMEM", "NYS_LASSO", "NYS_LOGISTIC", "NYS_ELASTIC_NET", "NYS_F64",
+                 "NYS_F32", "NYS_BF16", "NYS_FP8E4M3"):
+        assert getattr(nx, name) == h[name], name
+    modes = {"rel": "NYS_TOL_REL", "abs": "NYS_TOL_ABS", "sqrt_rprd": "NYS_TOL_SQRT_RPRD",
+             "rnorm_pow": "NYS_TOL_RNORM_POW"}
+    assert {k: h[v] for k, v in modes.items()} == nx.TOL_MODES
