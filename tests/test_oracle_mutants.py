@@ -109,7 +109,8 @@ MUTANTS = [
     ("pcg", _pcg_no_rho, [pins.check_pcg_direct]),
     ("soft_threshold", _soft_wrong_sign, [pins.check_soft_threshold, pins.check_lasso_orthonormal]),
     ("elastic_net_nysadmm", _enet_no_hessian_of_g, [pins.check_elastic_net_orthonormal,
-                                                    pins.check_elastic_net_augmented_brute_force]),
+                                                    pins.check_elastic_net_augmented_brute_force,
+                                                    pins.check_elastic_net_small_gamma_is_ridge]),
     ("elastic_net_nysadmm", _enet_swapped_weights, [pins.check_elastic_net_orthonormal,
                                                     pins.check_elastic_net_augmented_brute_force]),
 ]

@@ -474,6 +474,20 @@ def test_elastic_net_kkt_at_convergence():
     check_elastic_net_kkt()
 
 
+def check_elastic_net_small_gamma_is_ridge(seed=24):
+    # gamma -> 0: Eq. (6) tends to ridge regression with weight 1,
+    # x = (A^T A + I)^{-1} A^T b; the l1 term moves the minimiser by O(gamma)
+    p = gen.lasso_problem(200, 40, nnz=5, seed=seed)
+    gamma = 1e-9
+    out = _enet_run(p.A, p.b, gamma, rho=1.0, s=10, iters=300)
+    ref = np.linalg.solve(p.A.T @ p.A + np.eye(40), p.A.T @ p.b)
+    assert np.linalg.norm(out["x"] - ref) <= 1e-7 * np.linalg.norm(ref)
+
+
+def test_elastic_net_small_gamma_is_ridge():
+    check_elastic_net_small_gamma_is_ridge()
+
+
 def test_elastic_net_gamma_one_is_the_lasso():
     p = gen.lasso_small(0)
     Om = gen.gaussian_test_matrix(500, 50, 0)
