@@ -23,7 +23,9 @@ Readings where the paper is silent or ambiguous (the same readings as the CUDA p
     (lam_s + rho)/rho <= Tol; otherwise double, and when doubling would pass
     s_max, extend to s_max once and stop.
   * PCG schedule 'rnorm_pow' (Sec. 5's ||r^k|| / k^beta): k counts ADMM
-    iterations from 1 (k = 0 would divide by zero).
+    iterations from 1 (k = 0 would divide by zero).  Schedule 'sqrt_rprd'
+    (sqrt(r_p r_d) of the previous iteration): the first solve, which has no
+    residuals yet, uses pcg_tol as a relative tolerance.
   * Elastic net (Sec. 3.1): H^g = (1 - gamma) I enters the sketched matrix and the
     PCG matrix, not the preconditioner's rho; its duality gap is that of the lasso
     of the stacked data [A; sqrt(1 - gamma) I], [b; 0].
@@ -264,6 +266,8 @@ def lasso_nysadmm(A: np.ndarray, b: np.ndarray, gamma: float, rho: float, Omega:
         r_p     = ||x^{k+1} - z^{k+1}||,  r_d = rho ||z^k - z^{k+1}||   (Sec. 2.1)
     pcg_tol_mode 'rnorm_pow': the decaying schedule of Sec. 5, ||w|| <= ||r^k|| / k^beta with
     beta = pcg_tol and k = 1, 2, ... (k = 0 would divide by zero), i.e. a relative test.
+    pcg_tol_mode 'sqrt_rprd': the schedule of Sec. 5's experiments, ||w|| <= sqrt(r_p r_d) of
+    the previous ADMM iteration (absolute), pcg_tol relative for the first solve.
     pcg_fixed: None, an int, or a per-iteration sequence of PCG iteration counts.
     Stops after admm_iters, or earlier when eps_abs/eps_rel are given and the
     residual test of Sec. 2.1 holds.
@@ -288,6 +292,13 @@ def lasso_nysadmm(A: np.ndarray, b: np.ndarray, gamma: float, rho: float, Omega:
             fixed = pcg_fixed if isinstance(pcg_fixed, int) else int(pcg_fixed[k])
         if pcg_tol_mode == "rnorm_pow":
             tol_k, mode_k = (k + 1.0) ** (-pcg_tol), "rel"
+        elif pcg_tol_mode == "sqrt_rprd":
+            # Sec. 5's experiments: eps^{k+1} = sqrt(r_p^k r_d^k), absolute; the first
+            # solve has no residuals yet and uses pcg_tol relative
+            if k == 0:
+                tol_k, mode_k = pcg_tol, "rel"
+            else:
+                tol_k, mode_k = math.sqrt(trace["r_p"][-1] * trace["r_d"][-1]), "abs"
         else:
             tol_k, mode_k = pcg_tol, pcg_tol_mode
         x, it, res = pcg(H_apply, rho, U, lam, r, x, tol_k, mode_k,

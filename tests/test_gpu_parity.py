@@ -488,6 +488,26 @@ def test_rnorm_pow_schedule_matches_oracle():
     assert e.value.status == nx.NYS_EINVAL
 
 
+def test_sqrt_rprd_schedule_matches_oracle():
+    """The PCG schedule of Sec. 5's experiments, ||w|| <= sqrt(r_p r_d) of the previous ADMM
+    iteration (first solve rel-tol 1e-4), on the 2,000 x 500 FP64 lasso, 60 iterations:
+    thresholds stay >= 1e-5 of ||r|| and every stop lands >= 4 % inside its threshold on
+    the oracle, so both sides take the same FP64 decisions: equal PCG totals, x at 1e-9,
+    device and host loops bit-identical."""
+    p = gen.lasso_small(0)
+    Om = gen.gaussian_test_matrix(500, 50, 0)
+    ref = o.lasso_nysadmm(p.A, p.b, p.gamma, p.rho, Om, 60, pcg_tol=1e-4, pcg_tol_mode="sqrt_rprd")
+    M = nx.Matrix.padded(_dev(p.A))
+    outs = [nx.nysadmm_solve("lasso", M, _dev(p.b), p.gamma, p.rho, 50, 1e-4, _dev(Om), admm_iters=60,
+                             tol_mode="sqrt_rprd", device_loop=loop, hx_refresh=0) for loop in (True, False)]
+    assert torch.equal(outs[0]["z"], outs[1]["z"])
+    for out in outs:
+        assert out["info"]["pcg_iters_total"] == sum(ref["trace"]["pcg_iters"])
+        x = out["x"].cpu().numpy()
+        assert np.linalg.norm(x - ref["x"]) <= 1e-9 * np.linalg.norm(ref["x"])
+        assert out["info"]["r_p"] == pytest.approx(ref["trace"]["r_p"][-1], rel=1e-6)
+
+
 def test_logistic_trajectory_parity():
     p = gen.logistic_problem(3000, 100, decay=0.5, nnz=5, seed=24)
     pool = gen.gaussian_test_matrix(100, 40, 24)

@@ -405,6 +405,40 @@ def test_rnorm_pow_schedule_threshold_minimal_and_converges():
     check_rnorm_pow_schedule()
 
 
+def check_sqrt_rprd_schedule(seed=15):
+    """Sec. 5's experiment schedule: the x-step of iteration k >= 1 stops at the first PCG
+    iterate with ||w|| <= sqrt(r_p r_d) of iteration k - 1 (one iteration fewer misses it),
+    the first at pcg_tol relative; the iterates reach the lasso solution."""
+    p = gen.lasso_problem(300, 60, nnz=6, seed=seed)
+    Om = gen.gaussian_test_matrix(60, 20, seed)
+    out = o.lasso_nysadmm(p.A, p.b, p.gamma, 10.0, Om, 200, pcg_tol=1e-3, pcg_tol_mode="sqrt_rprd")
+    tr = out["trace"]
+    assert tr["pcg_res"][0] <= 1e-3 * tr["r_norm"][0]
+    for k in range(1, 200):
+        assert tr["pcg_res"][k] <= math.sqrt(tr["r_p"][k - 1] * tr["r_d"][k - 1])
+    U, lam = out["U"], out["lam"]
+    H = lambda X: p.A.T @ (p.A @ X)
+    x = np.zeros(60); z = np.zeros(60); u = np.zeros(60); q = p.A.T @ p.b
+    checked = 0
+    for k in range(30):
+        r = 10.0 * (z - u) + q
+        it = tr["pcg_iters"][k]
+        if k > 0 and it > 0 and checked < 5:
+            _, _, res_short = o.pcg(H, 10.0, U, lam, r, x, 0.0, "abs", fixed_iters=it - 1)
+            assert res_short > math.sqrt(tr["r_p"][k - 1] * tr["r_d"][k - 1])
+            checked += 1
+        x, _, _ = o.pcg(H, 10.0, U, lam, r, x, 0.0, "abs", fixed_iters=it)
+        zn = o.soft_threshold(x + u, p.gamma / 10.0)
+        u = u + x - zn
+        z = zn
+    assert checked == 5
+    assert o.lasso_kkt_eta(p.A, p.b, p.gamma, out["z"]) <= 1e-9
+
+
+def test_sqrt_rprd_schedule_threshold_minimal_and_converges():
+    check_sqrt_rprd_schedule()
+
+
 def test_rnorm_pow_beta_zero_takes_no_first_step():
     # beta = 0: the first threshold is ||r^0|| itself, met by x0 = 0 before any iteration
     p = gen.lasso_small(0)
