@@ -187,13 +187,14 @@ nys_status nys_precond_apply(nys_precond P, double rho, const void* V, void* Y, 
 /* Nystrom PCG (App. B, Alg. Nystrom PCG) for (A^T diag(D) A + rho I) x = r.
  * r, x: device, length d, compute type of A; x holds x0 on entry and the
  * solution on return.  P may be NULL (plain CG).  tol with opts->pcg_tol_mode
- * (REL or ABS); opts->pcg_fixed_iters[0], when set, fixes the iteration count.
+ * (REL or ABS; SQRT_RPRD acts as REL outside ADMM, RNORM_POW and unknown modes give
+ * NYS_EINVAL); opts->pcg_fixed_iters[0], when set, fixes the iteration count.
  * *iters and *resnorm (host, may be NULL) receive the iteration count and ||w||. */
 nys_status pcg_solve(const nys_matrix* A, const double* D, double rho, nys_precond P,
                      const void* r, void* x, double tol, const nys_opts* opts,
                      int32_t* iters, double* resnorm);
 
-/* NysADMM (Alg. NysADMM; Alg. AdaNysADMM for the logistic loss):
+/* NysADMM (Alg. NysADMM; Alg. AdaNysADMM with opts->rank_max > rank):
  * loss NYS_LASSO: sketch once, then opts->admm_maxit ADMM iterations with
  * PCG tolerance `tol` (mode opts->pcg_tol_mode), warm-started at the previous
  * x, z-update by soft-thresholding at gamma/rho.
@@ -208,6 +209,8 @@ nys_status pcg_solve(const nys_matrix* A, const double* D, double rho, nys_preco
  * t = A x~ at every outer iteration (Sec. 3.2); the rank is chosen by
  * Alg. AdaptiveRandNysAppx from `rank` up to opts->rank_max at the first
  * iteration and re-sketched every opts->resketch_every iterations.
+ * PCG tolerance schedules (opts->pcg_tol_mode, nys_tol_mode): with RNORM_POW `tol`
+ * is beta.  An unknown mode gives NYS_EINVAL.
  * b: device, length n, FP64 (labels in {-1,+1} for NYS_LOGISTIC).
  * Omega: device, d x max(rank, rank_max) column-major FP64 Gaussian.
  * x_out, z_out: device, length d, FP64 (z is the sparse iterate; either may be
