@@ -142,17 +142,19 @@ nys_status nys_hmatvec(const nys_matrix* A, const double* D, double rho, const v
                        void* y, void* stream);
 
 /* Allocation-free variant of nys_hmatvec (the paper has no counterpart; this is a
- * deployment convenience).  Same arguments, same result, but it allocates no
- * device memory: its scratch (the per-block partial sums and a status word) is a
- * fixed 16 MiB array compiled into the library, which every GPU that loads the
- * library holds until the process exits.  It is meant for callers that cannot
- * call cudaMalloc/cudaFree on the request path: for example a service whose device
- * memory is entirely owned by another allocator (a framework's caching allocator
- * or a preallocated arena), or a latency-critical caller that cannot take the
- * device-wide synchronisation cudaFree implies.
+ * deployment convenience).  Same arguments, same checks and the same result, bit for
+ * bit, for every storage type nys_hmatvec accepts (FP8 E4M3 included), but it allocates
+ * no device memory: its scratch (the per-block partial sums and a status word) is a
+ * fixed 16 MiB array compiled into the library, which every GPU that loads the library
+ * holds until the process exits.  It is meant for callers that cannot call
+ * cudaMalloc/cudaFree on the request path: for example a service whose device memory is
+ * entirely owned by another allocator (a framework's caching allocator or a
+ * preallocated arena), or a latency-critical caller that cannot take the device-wide
+ * synchronisation cudaFree implies.
  *  - The first call on a device looks up the array's device address (once per
- *    device, with that device current); make that first call before any stream
- *    capture.
+ *    device, with that device current).
+ *  - Like every entry point it ends by reading the status word back and synchronising
+ *    `stream`, so it cannot be called while `stream` is being captured into a graph.
  *  - Scratch needed = (#blocks of the pass, at most the SM count) x d rounded up
  *    to 16 bytes x (8 for NYS_F64, else 4) bytes; a call that needs more than
  *    16 MiB returns NYS_EINVAL without launching anything.

@@ -29,6 +29,11 @@ Readings where the paper is silent or ambiguous (the same readings as the CUDA p
   * Elastic net (Sec. 3.1): H^g = (1 - gamma) I enters the sketched matrix and the
     PCG matrix, not the preconditioner's rho; its duality gap is that of the lasso
     of the stacked data [A; sqrt(1 - gamma) I], [b; 0].
+  * Mixed precision form without a correction pass: a low-precision copy A_inner
+    (its stored values, given in FP64) builds the sketch and the x-subproblem matrix,
+    while A^T b comes from the problem matrix A, so the iteration solves the perturbed
+    problem 1/2 x^T A_inner^T A_inner x - (A^T b)^T x + gamma ||x||_1; the sketch shift
+    then uses the FP32 eps (mantissa_bits = 23).
 
 Functions with no independent pin: none (every function here is pinned by a
 test in tests/test_oracle_pins.py against closed forms, library solvers,
@@ -253,9 +258,19 @@ def lasso_nysadmm(A: np.ndarray, b: np.ndarray, gamma: float, rho: float, Omega:
                   admm_iters: int, pcg_tol: float = 1e-8, pcg_tol_mode: str = "rel",
                   shift_scale: float | None = None, pcg_fixed=None, pcg_maxit=None,
                   eps_abs: float | None = None, eps_rel: float | None = None,
-                  precond=None, mu: float = 0.0):
+                  precond=None, mu: float = 0.0, A_inner: np.ndarray | None = None,
+                  mantissa_bits: int = 52):
     """Alg. NysADMM for the lasso, and for any problem whose smooth part adds
     g(x) = mu/2 ||x||^2 (the elastic net of Sec. 3.1 has mu = 1 - gamma).
+
+    A_inner (mixed form without residual correction): the matrix H of the sketch and of
+    the x-subproblem is built from A_inner (the stored low-precision values, given in
+    FP64), while q = A^T b keeps the problem matrix A.  This is the reading of the mixed
+    precision form in which the low-precision copy serves only the sketch and PCG and no
+    correction pass is made; its fixed point solves the perturbed problem
+        min 1/2 x^T (A_inner^T A_inner + mu I) x - (A^T b)^T x + gamma ||x||_1.
+    mantissa_bits: precision whose eps enters the sketch shift nu (52 for an FP64
+    sketch, 23 for the FP32-class sketch of a low-precision copy).
 
     Sketch once (App. B) with H = A^T A + H^g, H^g = mu I, then for k = 0, 1, ...:
         r^k     = rho z - rho u + A^T b            (Eq. ADMMSubProb with l = 1/2||.-b||^2;
@@ -275,9 +290,10 @@ def lasso_nysadmm(A: np.ndarray, b: np.ndarray, gamma: float, rho: float, Omega:
     n, d = A.shape
     if shift_scale is None:
         shift_scale = math.sqrt(d)
-    H_apply = lambda X: A.T @ (A @ X) + mu * X
+    Ah = A if A_inner is None else A_inner
+    H_apply = lambda X: Ah.T @ (Ah @ X) + mu * X
     if precond is None:
-        U, lam, nu, Q, _ = nystrom(H_apply, Omega, shift_scale)
+        U, lam, nu, Q, _ = nystrom(H_apply, Omega, shift_scale, mantissa_bits)
     else:
         U, lam, nu = precond
     x = np.zeros(d)
@@ -319,6 +335,14 @@ def lasso_nysadmm(A: np.ndarray, b: np.ndarray, gamma: float, rho: float, Omega:
                     r_d <= eps_abs + eps_rel * np.linalg.norm(rho * u)):
                 break
     return {"x": x, "z": z, "u": u, "U": U, "lam": lam, "nu": nu, "trace": trace}
+
+
+def quadratic_l1_kkt_eta(G, q, gamma, x) -> float:
+    """Prox-gradient fixed-point residual of min 1/2 x^T G x - q^T x + gamma ||x||_1,
+    ||x - S_gamma(x - (G x - q))|| / (1 + ||x||): the analogue of Eq. (31) for the problem
+    the mixed form without correction solves (G = A_inner^T A_inner, q = A^T b)."""
+    g = G @ x - q
+    return float(np.linalg.norm(x - soft_threshold(x - g, gamma)) / (1.0 + np.linalg.norm(x)))
 
 
 # ---------------------------------------------------------------------------

@@ -645,17 +645,6 @@ __global__ void __launch_bounds__(kVecThreads) apass_reduce_kernel(const C* __re
   }
 }
 
-static int sm_count() {
-  static int c = 0;
-  if (c == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
-    if (c <= 0) c = 1;
-  }
-  return c;
-}
-
 // Blocks of the vector kernels over d elements: one element per thread, at most 4 blocks
 // per SM (measured: spreading a 10,000-element vector over 4x more blocks made the
 // ADMM iteration slower, 78 -> 104 us of small-kernel time).
@@ -672,21 +661,24 @@ static int vpt_bucket(int64_t nvec, int threads = kApassThreads) {
   return -1;
 }
 
-// Autotuned rows-per-stage, keyed by (dtype, columns per thread, row bytes).
+// Autotuned rows-per-stage, keyed by (device, dtype, columns per thread, row bytes): a
+// choice timed on one GPU is not applied to another.
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int64_t>, int> g_tuned_rows;
+static std::map<std::tuple<int, int, int, int64_t>, int> g_tuned_rows;
 
 void apass_set_tuned_rows(const nys_matrix* A, int rows) {
   const int64_t esz = (int64_t)dtype_size(A->dtype);
   const int vpt = vpt_bucket((A->d + (16 / esz) - 1) / (16 / esz));
+  const int dev = current_device();
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  if (rows <= 0) g_tuned_rows.erase({A->dtype, vpt, A->ld * esz});
-  else g_tuned_rows[{A->dtype, vpt, A->ld * esz}] = rows;
+  if (rows <= 0) g_tuned_rows.erase({dev, A->dtype, vpt, A->ld * esz});
+  else g_tuned_rows[{dev, A->dtype, vpt, A->ld * esz}] = rows;
 }
 
 static int tuned_rows(int dtype, int vpt, int64_t rowbytes) {
+  const int dev = current_device();
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  auto it = g_tuned_rows.find({dtype, vpt, rowbytes});
+  auto it = g_tuned_rows.find({dev, dtype, vpt, rowbytes});
   return it == g_tuned_rows.end() ? 0 : it->second;
 }
 
@@ -789,11 +781,7 @@ static thread_local bool g_prepare_only = false;
 template <int DT, int VPT>
 static cudaError_t launch_vpt(const ApassKArgs& k, const ApassPlan& plan, cudaStream_t st) {
   auto fn = apass_kernel<DT, VPT>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    NYS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
-    attr_set = true;
-  }
+  NYS_CUDA_TRY(ensure_max_dyn_smem((const void*)fn, kSmemBudget));
   if (g_prepare_only) return cudaSuccess;
   count_launch();
   fn<<<plan.grid, kApassThreads, plan.smem, st>>>(k);
@@ -803,11 +791,7 @@ static cudaError_t launch_vpt(const ApassKArgs& k, const ApassPlan& plan, cudaSt
 template <int DT, int VPT, int R, int T, bool OB>
 static cudaError_t launch_f(const ApassKArgs& k, const ApassPlan& plan, cudaStream_t st) {
   auto fn = apass_f_kernel<DT, VPT, R, T, OB>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    NYS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
-    attr_set = true;
-  }
+  NYS_CUDA_TRY(ensure_max_dyn_smem((const void*)fn, kSmemBudget));
   if (g_prepare_only) return cudaSuccess;
   count_launch();
   fn<<<plan.grid, T, plan.smem, st>>>(k);

@@ -26,6 +26,32 @@ struct nys_precond_s {
   std::vector<double> lam;  // host copy, descending
 };
 
+namespace nys {
+
+nys_status check_matrix(const nys_matrix* A) {
+  if (!A || !A->data) return NYS_EINVAL;
+  if (A->n <= 0 || A->d <= 0 || A->ld < A->d) return NYS_EINVAL;
+  if (A->dtype != NYS_F64 && A->dtype != NYS_F32 && A->dtype != NYS_BF16 && A->dtype != NYS_FP8E4M3)
+    return NYS_EINVAL;
+  if ((A->dtype == NYS_FP8E4M3) != (A->col_scale != nullptr)) return NYS_EINVAL;  // scales iff FP8
+  const size_t esz = dtype_size(A->dtype);
+  if ((A->ld * esz) % 16 != 0) return NYS_EINVAL;
+  if (reinterpret_cast<uintptr_t>(A->data) % 16 != 0) return NYS_EINVAL;
+  ApassPlan plan;
+  if (!apass_plan(A, &plan)) return NYS_EINVAL;
+  return NYS_OK;
+}
+
+// Arguments of the H-matvec entry points (nys_hmatvec and its allocation-free variant).
+nys_status check_hmatvec_args(const nys_matrix* A, double rho, const void* p, const void* y) {
+  const nys_status s = check_matrix(A);
+  if (s != NYS_OK) return s;
+  if (!p || !y || p == y || !std::isfinite(rho)) return NYS_EINVAL;
+  return NYS_OK;
+}
+
+}  // namespace nys
+
 namespace {
 
 constexpr int kMaxRank = 1024;
@@ -54,20 +80,6 @@ struct PhaseTimer {
 cudaStream_t stream_of(const nys_opts* o) { return o ? reinterpret_cast<cudaStream_t>(o->stream) : nullptr; }
 
 bool is_fin(double v) { return std::isfinite(v); }
-
-nys_status check_matrix(const nys_matrix* A) {
-  if (!A || !A->data) return NYS_EINVAL;
-  if (A->n <= 0 || A->d <= 0 || A->ld < A->d) return NYS_EINVAL;
-  if (A->dtype != NYS_F64 && A->dtype != NYS_F32 && A->dtype != NYS_BF16 && A->dtype != NYS_FP8E4M3)
-    return NYS_EINVAL;
-  if ((A->dtype == NYS_FP8E4M3) != (A->col_scale != nullptr)) return NYS_EINVAL;  // scales iff FP8
-  const size_t esz = dtype_size(A->dtype);
-  if ((A->ld * esz) % 16 != 0) return NYS_EINVAL;
-  if (reinterpret_cast<uintptr_t>(A->data) % 16 != 0) return NYS_EINVAL;
-  ApassPlan plan;
-  if (!apass_plan(A, &plan)) return NYS_EINVAL;
-  return NYS_OK;
-}
 
 nys_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return NYS_OK;
@@ -1069,8 +1081,7 @@ const char* nys_strerror(int32_t s) {
 }
 
 nys_status nys_hmatvec(const nys_matrix* A, const double* D, double rho, const void* p, void* y, void* stream) {
-  NYS_TRY(check_matrix(A));
-  if (!p || !y || p == y || !is_fin(rho)) return NYS_EINVAL;
+  NYS_TRY(check_hmatvec_args(A, rho, p, y));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   return A->dtype == NYS_F64 ? hmatvec_t<double>(A, D, rho, p, y, st) : hmatvec_t<float>(A, D, rho, p, y, st);
 }

@@ -265,11 +265,7 @@ __global__ void __launch_bounds__(1024) chol_upper_smem_kernel(double* M, int s,
 cudaError_t chol_upper(double* M, int s, int* info, cudaStream_t st) {
   const size_t smem = (size_t)s * (s + 1) / 2 * sizeof(double);
   if (smem <= 200 * 1024) {
-    static bool attr = false;
-    if (!attr) {
-      NYS_CUDA_TRY(cudaFuncSetAttribute(chol_upper_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr = true;
-    }
+    NYS_CUDA_TRY(ensure_max_dyn_smem((const void*)chol_upper_smem_kernel, 200 * 1024));
     count_launch();
     chol_upper_smem_kernel<<<1, 1024, smem, st>>>(M, s, info);
     return cudaGetLastError();
@@ -315,11 +311,7 @@ __global__ void __launch_bounds__(kTrsmRows) trsm_ru_smem_kernel(const double* _
 cudaError_t trsm_right_upper(const double* C, int s, double* Y, int64_t d, cudaStream_t st) {
   const size_t smem = (size_t)s * kTrsmRows * sizeof(double);
   if (smem <= 200 * 1024) {
-    static bool attr = false;
-    if (!attr) {
-      NYS_CUDA_TRY(cudaFuncSetAttribute(trsm_ru_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr = true;
-    }
+    NYS_CUDA_TRY(ensure_max_dyn_smem((const void*)trsm_ru_smem_kernel, 200 * 1024));
     count_launch();
     trsm_ru_smem_kernel<<<(unsigned)((d + kTrsmRows - 1) / kTrsmRows), kTrsmRows, smem, st>>>(C, s, Y, d);
     return cudaGetLastError();

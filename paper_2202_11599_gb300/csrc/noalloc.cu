@@ -46,11 +46,8 @@ cudaError_t scratch_address(unsigned char** out) {
 extern "C" nys_status nys_hmatvec_noalloc(const nys_matrix* A, const double* D, double rho, const void* p,
                                           void* y, void* stream) {
   using namespace nys;
-  if (!A || !A->data || A->n <= 0 || A->d <= 0 || A->ld < A->d) return NYS_EINVAL;
-  if (A->dtype != NYS_F64 && A->dtype != NYS_F32 && A->dtype != NYS_BF16) return NYS_EINVAL;
-  if ((A->ld * dtype_size(A->dtype)) % 16 != 0 || reinterpret_cast<uintptr_t>(A->data) % 16 != 0)
-    return NYS_EINVAL;
-  if (!p || !y || p == y || !(rho == rho) || rho - rho != 0.0) return NYS_EINVAL;
+  const nys_status chk = check_hmatvec_args(A, rho, p, y);   // the checks of nys_hmatvec
+  if (chk != NYS_OK) return chk;
   ApassPlan plan;
   if (!apass_plan(A, &plan)) return NYS_EINVAL;
   const size_t need = apass_partial_bytes(A, plan);

@@ -12,6 +12,13 @@ namespace nys {
 constexpr int kApassThreads = 512;       // threads of the fused A-pass CTA
 constexpr int kApassThreadsWide = 640;   // float-path CTA for narrow rows (<= 4 vectors per thread)
 constexpr int kVecThreads = 256;         // threads of the vector kernels
+constexpr int kMaxDevices = 64;          // device ordinals the per-device caches cover
+
+// Per-device runtime state (runtime.cu): the device current at the call selects the entry.
+int current_device();                                       // -1 if none
+int sm_count();                                             // SMs of the current device
+cudaError_t ensure_max_dyn_smem(const void* fn, int bytes); // once per (kernel, device)
+cudaStream_t capture_stream();                              // private capture stream per (thread, device)
 
 // Row modes of the fused A-pass: u_i = phi(t_i), t = A p.
 enum ApassMode : int {
@@ -52,6 +59,11 @@ struct ApassPlan {
 };
 
 bool apass_plan(const nys_matrix* A, ApassPlan* plan);
+// Argument checks shared by the entry points (capi.cu): NYS_EINVAL for a malformed matrix
+// (null data, bad sizes, unknown dtype, col_scale present iff FP8, unaligned rows, no pass
+// plan) and, for the H-matvec entry points, null / aliased vectors or a non-finite rho.
+nys_status check_matrix(const nys_matrix* A);
+nys_status check_hmatvec_args(const nys_matrix* A, double rho, const void* p, const void* y);
 void apass_set_tuned_rows(const nys_matrix* A, int rows);   // rows <= 0 clears
 int apass_row_candidates(const nys_matrix* A, int* out);      // out: up to 3 values
 size_t apass_partial_bytes(const nys_matrix* A, const ApassPlan& plan);

@@ -11,6 +11,7 @@
 #include "solver.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -574,23 +575,26 @@ cudaError_t admm_scalar(int64_t d, const double* part5, double rho, int k, doubl
 }
 
 void keep_mempool_cached() {
-  static int done_dev = -1;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return;
-  if (done_dev == dev) return;
+  static std::atomic<unsigned long long> done_mask{0};   // one bit per device ordinal
+  const int dev = current_device();
+  if (dev < 0 || dev >= kMaxDevices) return;
+  const unsigned long long bit = 1ull << dev;
+  if (done_mask.load(std::memory_order_relaxed) & bit) return;
   cudaMemPool_t mp;
   if (cudaDeviceGetDefaultMemPool(&mp, dev) == cudaSuccess) {
     uint64_t thr = UINT64_MAX;
     cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &thr);
   }
-  done_dev = dev;
+  done_mask.fetch_or(bit);
 }
 
+// Pinned host slot the host-driven PCG loop reads its convergence flags through: one per
+// host thread, so threads driving different GPUs (or streams) never share it.
 PcgState* host_state() {
-  static PcgState* hs = nullptr;
+  static thread_local PcgState* hs = nullptr;
   if (!hs) {
     if (cudaMallocHost((void**)&hs, sizeof(PcgState)) != cudaSuccess) {
-      static PcgState fallback;
+      static thread_local PcgState fallback;
       hs = &fallback;
     }
   }
@@ -873,8 +877,8 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   if (g.Aref) G_OK(apass_prepare(g.Aref, g.plan_ref));
 
   // a private stream to capture on (a legacy default stream cannot be captured)
-  static thread_local cudaStream_t cap = nullptr;
-  if (!cap) G_OK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaStream_t cap = capture_stream();
+  if (!cap) return NYS_ECUDA;
   cudaGraphConditionalHandle h_admm, h_pcg;
   G_OK(cudaGraphConditionalHandleCreate(&h_admm, graph, 1u, cudaGraphCondAssignDefault));
   cudaGraphNodeParams cp = {};

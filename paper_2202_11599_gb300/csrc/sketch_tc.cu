@@ -380,12 +380,7 @@ __global__ void sum_slices_kernel(const float* __restrict__ P, int Z, int NP, in
   }
 }
 
-int sm_count_tc() {
-  int dev = 0, c = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
-  return c > 0 ? c : 1;
-}
+int sm_count_tc() { return sm_count(); }
 
 // split-K slices for GEMM 2: the count (<= 32, each slice >= 16 K tiles) whose CTA count
 // fills the last wave best.
@@ -409,12 +404,9 @@ template <int EPI, int AT>
 cudaError_t launch_tc(const TcArgs& a, dim3 grid, cudaStream_t st) {
   constexpr int ST = tc_stages<AT>();
   const size_t smem = (size_t)ST * (AT * TC_BM * TC_BK * 2 + (size_t)TC_TERMS * a.NP * TC_BK * 2);
-  static bool attr = false;
-  if (!attr) {
+  {
     const size_t max_smem = (size_t)ST * (AT * TC_BM * TC_BK * 2 + (size_t)TC_TERMS * TC_NMAX * TC_BK * 2);
-    NYS_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<EPI, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)max_smem));
-    attr = true;
+    NYS_CUDA_TRY(ensure_max_dyn_smem((const void*)sketch_tc_kernel<EPI, AT>, (int)max_smem));
   }
   count_launch();
   sketch_tc_kernel<EPI, AT><<<grid, TC_THREADS, smem, st>>>(a);

@@ -95,6 +95,17 @@ def _enet_swapped_weights(A, b, gamma, rho, Omega, admm_iters, **kw):
     return _orig_lasso(A, b, 1.0 - gamma, rho, Omega, admm_iters, mu=gamma, **kw)
 
 
+def _mixed_q_from_inner(A, b, gamma, rho, Omega, admm_iters, A_inner=None, **kw):
+    # mixed form: A^T b taken from the low-precision copy instead of the problem matrix
+    return _orig_lasso(A if A_inner is None else A_inner, b, gamma, rho, Omega, admm_iters,
+                       A_inner=A_inner, **kw)
+
+
+def _mixed_inner_ignored(A, b, gamma, rho, Omega, admm_iters, A_inner=None, **kw):
+    # mixed form: the low-precision copy dropped (H from the problem matrix)
+    return _orig_lasso(A, b, gamma, rho, Omega, admm_iters, **kw)
+
+
 def _soft_wrong_sign(v, kappa):
     return np.sign(v) * np.maximum(np.abs(v) + kappa, 0.0)
 
@@ -113,6 +124,8 @@ MUTANTS = [
                                                     pins.check_elastic_net_small_gamma_is_ridge]),
     ("elastic_net_nysadmm", _enet_swapped_weights, [pins.check_elastic_net_orthonormal,
                                                     pins.check_elastic_net_augmented_brute_force]),
+    ("lasso_nysadmm", _mixed_q_from_inner, [pins.check_mixed_form_fixed_point]),
+    ("lasso_nysadmm", _mixed_inner_ignored, [pins.check_mixed_form_fixed_point]),
 ]
 
 

@@ -356,6 +356,89 @@ def test_lasso_kkt_and_duality_gap_at_convergence():
     check_lasso_kkt_and_gap()
 
 
+# ---------------------------------------------------------------- mixed form without correction
+# (BF16 copy of A for the sketch and the x-subproblem, A^T b from the FP64 matrix)
+
+def _bf16_values(A):
+    """Values of A rounded to BF16 (round to nearest even), returned in FP64."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(A)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _quadratic_l1_brute_force(G, q, gamma):
+    """min 1/2 x^T G x - q^T x + gamma ||x||_1 by enumerating sign patterns s in {-1,0,1}^d:
+    on the support solve G_SS x_S = q_S - gamma s_S, keep the sign-consistent candidate of
+    least objective."""
+    import itertools
+    d = G.shape[0]
+    best, best_x = np.inf, None
+    for pat in itertools.product((-1, 0, 1), repeat=d):
+        S = [j for j in range(d) if pat[j] != 0]
+        x = np.zeros(d)
+        if S:
+            sg = np.array([pat[j] for j in S], float)
+            xs = np.linalg.solve(G[np.ix_(S, S)], q[S] - gamma * sg)
+            if np.any(np.sign(xs) != sg):
+                continue
+            x[S] = xs
+        f = 0.5 * x @ G @ x - q @ x + gamma * np.sum(np.abs(x))
+        if f < best:
+            best, best_x = f, x
+    return best_x, best
+
+
+def check_mixed_form_inner_equal_to_A_is_plain(seed=30):
+    p = gen.lasso_problem(200, 30, nnz=5, seed=seed)
+    Om = gen.gaussian_test_matrix(30, 8, seed)
+    a = o.lasso_nysadmm(p.A, p.b, p.gamma, 1.0, Om, 40, pcg_tol=1e-10)
+    b = o.lasso_nysadmm(p.A, p.b, p.gamma, 1.0, Om, 40, pcg_tol=1e-10, A_inner=p.A)
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["z"], b["z"])
+
+
+def test_mixed_form_with_inner_equal_to_A_is_the_plain_method():
+    check_mixed_form_inner_equal_to_A_is_plain()
+
+
+def check_mixed_form_fixed_point(seed=31):
+    """The mixed form without correction converges to the minimiser of the perturbed
+    problem 1/2 x^T (Aq^T Aq) x - (A^T b)^T x + gamma ||x||_1 (Aq = BF16 values of A):
+    brute force over sign patterns and its prox-gradient residual.  The perturbation is
+    visible: the lasso minimiser of A, and the problem with q = Aq^T b, differ from it."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((40, 5)) * gen.column_scales(5, 0.5)[None, :]
+    b = rng.standard_normal(40)
+    gamma = 0.2 * np.max(np.abs(A.T @ b))
+    Aq = _bf16_values(A)
+    Om = gen.gaussian_test_matrix(5, 3, seed)
+    out = o.lasso_nysadmm(A, b, gamma, 1.0, Om, 3000, pcg_tol=1e-13, A_inner=Aq, mantissa_bits=23)
+    G, q = Aq.T @ Aq, A.T @ b
+    ref, _ = _quadratic_l1_brute_force(G, q, gamma)
+    z = out["z"]
+    assert np.linalg.norm(z - ref) <= 1e-8 * max(1.0, np.linalg.norm(ref))
+    assert o.quadratic_l1_kkt_eta(G, q, gamma, z) <= 1e-10
+    plain, _ = _lasso_brute_force(A, b, gamma)
+    other_q, _ = _quadratic_l1_brute_force(G, Aq.T @ b, gamma)
+    assert np.linalg.norm(ref - plain) >= 1e-5 * np.linalg.norm(ref)
+    assert np.linalg.norm(ref - other_q) >= 1e-5 * np.linalg.norm(ref)
+
+
+def test_mixed_form_fixed_point_solves_the_perturbed_problem():
+    check_mixed_form_fixed_point()
+
+
+def test_quadratic_l1_eta_is_the_lasso_eta_numerator():
+    """With G = A^T A and q = A^T b the quadratic problem is the lasso: both residuals
+    share the numerator ||x - S_gamma(x - grad)|| (Eq. 31) and differ in the scaling."""
+    p = gen.lasso_problem(60, 12, seed=32)
+    x = np.random.default_rng(32).standard_normal(12)
+    res = p.A @ x - p.b
+    num_q = o.quadratic_l1_kkt_eta(p.A.T @ p.A, p.A.T @ p.b, p.gamma, x) * (1 + np.linalg.norm(x))
+    num_l = o.lasso_kkt_eta(p.A, p.b, p.gamma, x) * (1 + np.linalg.norm(x) + np.linalg.norm(res))
+    assert num_q == pytest.approx(num_l, rel=1e-12)
+    xs, _ = _quadratic_l1_brute_force(p.A[:, :5].T @ p.A[:, :5], p.A[:, :5].T @ p.b, p.gamma)
+    assert o.quadratic_l1_kkt_eta(p.A[:, :5].T @ p.A[:, :5], p.A[:, :5].T @ p.b, p.gamma, xs) <= 1e-12
+
+
 def test_lasso_residuals_decrease_and_record():
     p = gen.lasso_small(0)
     Om = gen.gaussian_test_matrix(500, 50, 0)
