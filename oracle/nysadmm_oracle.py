@@ -176,13 +176,16 @@ def effective_dimension(H: np.ndarray, rho: float) -> float:
 # ---------------------------------------------------------------------------
 
 def pcg(H_apply, rho: float, U, lam, r: np.ndarray, x0: np.ndarray, tol: float,
-        tol_mode: str = "rel", maxit: int | None = None, fixed_iters: int | None = None):
+        tol_mode: str = "rel", maxit: int | None = None, fixed_iters: int | None = None,
+        wnorms: list | None = None):
     """Solve (H + rho I) x = r by PCG with the Nystrom preconditioner.
 
     U = None (or an empty basis) gives plain CG (P = I).
     Stopping test at the top of the loop, as printed: ||w||_2 > eps.
       tol_mode 'rel': eps = tol * ||r||;  'abs': eps = tol.
     fixed_iters: run exactly this many iterations (no stopping test).
+    wnorms: if a list is given, ||w|| at every loop-top test is appended to it (a record
+    only: it shows how far each stop decision lay from its threshold).
     Returns (x, iterations, ||w||)."""
     d = r.shape[0]
     if maxit is None:
@@ -203,6 +206,8 @@ def pcg(H_apply, rho: float, U, lam, r: np.ndarray, x0: np.ndarray, tol: float,
     thresh = tol * np.linalg.norm(r) if tol_mode == "rel" else tol
     it = 0
     while True:
+        if wnorms is not None:
+            wnorms.append(float(np.linalg.norm(w)))
         if fixed_iters is not None:
             if it >= fixed_iters:
                 break
@@ -300,7 +305,8 @@ def lasso_nysadmm(A: np.ndarray, b: np.ndarray, gamma: float, rho: float, Omega:
     z = np.zeros(d)
     u = np.zeros(d)
     q = A.T @ b
-    trace = {"pcg_iters": [], "r_p": [], "r_d": [], "z": [], "pcg_res": [], "r_norm": []}
+    trace = {"pcg_iters": [], "r_p": [], "r_d": [], "z": [], "pcg_res": [], "r_norm": [],
+             "pcg_thresh": [], "pcg_wnorms": []}
     for k in range(admm_iters):
         r = rho * z - rho * u + q
         fixed = None
@@ -317,8 +323,11 @@ def lasso_nysadmm(A: np.ndarray, b: np.ndarray, gamma: float, rho: float, Omega:
                 tol_k, mode_k = math.sqrt(trace["r_p"][-1] * trace["r_d"][-1]), "abs"
         else:
             tol_k, mode_k = pcg_tol, pcg_tol_mode
+        wn = []
         x, it, res = pcg(H_apply, rho, U, lam, r, x, tol_k, mode_k,
-                         maxit=pcg_maxit, fixed_iters=fixed)
+                         maxit=pcg_maxit, fixed_iters=fixed, wnorms=wn)
+        trace["pcg_thresh"].append(tol_k * float(np.linalg.norm(r)) if mode_k == "rel" else tol_k)
+        trace["pcg_wnorms"].append(wn)
         z_old = z
         z = soft_threshold(x + u, gamma / rho)
         u = u + x - z

@@ -19,10 +19,7 @@
 //     status;
 //   * per-CTA partials go to a [grid x d] buffer that a second kernel sums in a
 //     fixed order (deterministic, run-to-run bitwise identical) and adds rho p.
-#include <cuda_fp8.h>
-
-#include "device_util.cuh"
-#include "nys_internal.cuh"
+#include "apass_common.cuh"
 
 #include <algorithm>
 #include <cstdlib>
@@ -31,77 +28,6 @@
 #include <tuple>
 
 namespace nys {
-
-constexpr int kMaxStages = 8;
-constexpr int kRMax = 4;
-constexpr int kSmemBudget = 200 * 1024;
-
-struct ApassKArgs {
-  const unsigned char* A;
-  int64_t n, d, ld;
-  const void* p;
-  const double* D;
-  const double* b;
-  double* D_out;
-  double* t_out;
-  int mode;
-  int R;          // rows per stage (<= kRMax)
-  int S;          // stages
-  int64_t dpad;   // partial stride
-  void* partial;
-  double* loss_part;
-  int* status;
-  const int* skip;
-  int* executed;  // instrumentation: set to 1 by CTA 0 when the pass ran (not skipped)
-  DevTimer tm;    // instrumentation: in-kernel launch timing (null pointers when off)
-  double bytes_alg;
-  const float* col_scale;  // FP8: p is read as col_scale o p (the reduce scales the sums)
-};
-
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ int timer_begin(const ApassKArgs& a) {
-  int slot = -1;
-  if (a.tm.count && threadIdx.x == 0) {
-    const int c = *(volatile int*)a.tm.count;
-    if (c < a.tm.cap) {
-      slot = c;
-      atomicMin(&a.tm.start[c], gtimer());
-    }
-  }
-  return slot;
-}
-// called by every thread of the CTA at the end of a pass that completed
-__device__ __forceinline__ void timer_end(const ApassKArgs& a, int slot, int dtype) {
-  if (!a.tm.count) return;
-  __syncthreads();
-  if (threadIdx.x == 0 && slot >= 0) {
-    atomicMax(&a.tm.end[slot], gtimer());
-    if (blockIdx.x == 0) {
-      a.tm.bytes[slot] = a.bytes_alg;
-      a.tm.dtype[slot] = dtype;
-    }
-    __threadfence();
-    if (atomicAdd(a.tm.done, 1) == (int)gridDim.x - 1) {
-      *a.tm.done = 0;
-      __threadfence();
-      *(volatile int*)a.tm.count = slot + 1;
-    }
-  }
-}
-
-__device__ __forceinline__ double sigmoid_d(double t) {
-  // stable logistic function
-  if (t >= 0) {
-    const double e = exp(-t);
-    return 1.0 / (1.0 + e);
-  }
-  const double e = exp(t);
-  return e / (1.0 + e);
-}
 
 template <int DT, int VPT>
 __global__ void __launch_bounds__(kApassThreads, 1) apass_kernel(const ApassKArgs a) {
@@ -309,97 +235,7 @@ __global__ void __launch_bounds__(kApassThreads, 1) apass_kernel(const ApassKArg
 //   * dot products and updates use the packed FP32 FMA (two lanes per instruction);
 //   * the row sums are finished by one warp per row (two barriers per step instead of
 //     every thread re-reading all warp partials).
-template <int DT>
-__device__ __forceinline__ float2 unpack_pair(const uint4& r, int q);
-template <>
-__device__ __forceinline__ float2 unpack_pair<NYS_F32>(const uint4& r, int q) {
-  return q == 0 ? make_float2(__uint_as_float(r.x), __uint_as_float(r.y))
-                : make_float2(__uint_as_float(r.z), __uint_as_float(r.w));
-}
-template <>
-__device__ __forceinline__ float2 unpack_pair<NYS_BF16>(const uint4& r, int q) {
-  const unsigned w = q == 0 ? r.x : (q == 1 ? r.y : (q == 2 ? r.z : r.w));
-  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
-}
-
-// FP8 E4M3: 16-bit half (q & 1) of word q / 2 holds elements 2q and 2q + 1 (the per-column
-// scales are folded into p and into the final sum, so only the codes are decoded here).
-template <>
-__device__ __forceinline__ float2 unpack_pair<NYS_FP8E4M3>(const uint4& r, int q) {
-  const unsigned w = (q >> 1) == 0 ? r.x : ((q >> 1) == 1 ? r.y : ((q >> 1) == 2 ? r.z : r.w));
-  const __nv_fp8x2_storage_t pair = (__nv_fp8x2_storage_t)((q & 1) ? (w >> 16) : (w & 0xffffu));
-  const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2(pair, __NV_E4M3);
-  return __half22float2(*reinterpret_cast<const __half2*>(&h));
-}
-
-// Zero the stored elements of a 16-byte vector from element index `keep` on.
-template <int DT>
-__device__ __forceinline__ void mask_tail(uint4& r, int keep) {
-  constexpr int ESZ = Stor<DT>::ESZ;
-  unsigned* w = reinterpret_cast<unsigned*>(&r);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int first = i * 4 / ESZ;  // first element index held by word i
-    if (ESZ == 4) {
-      if (first >= keep) w[i] = 0u;
-    } else if (ESZ == 1) {  // four 8-bit elements per word
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-        if (first + b >= keep) w[i] &= ~(0xffu << (8 * b));
-    } else {  // two 16-bit elements per word
-      if (first >= keep) w[i] = 0u;
-      else if (first + 1 >= keep) w[i] &= 0x0000ffffu;
-    }
-  }
-}
-
-__device__ __forceinline__ uint4 lds128(uint32_t addr) {
-  uint4 v;
-  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "r"(addr));
-  return v;
-}
-
-// The per-row input of the pass's mode (D_i or b_i), loaded at the start of a step so
-// that its latency overlaps the dot products instead of sitting between the barriers.
-__device__ __forceinline__ double row_input(const ApassKArgs& a, int64_t i) {
-  if (a.mode == MODE_ID) return 0.0;
-  if (a.mode == MODE_DIAG) return a.D[i];
-  return a.b[i];
-}
-
-// Row modes of the pass, applied by the warp that finishes row i: returns u_i.
-// `in` is row_input(a, i).
-__device__ __forceinline__ float row_phi(const ApassKArgs& a, int64_t i, float t, double in, double& loss) {
-  switch (a.mode) {
-    case MODE_CONST: return (float)in;
-    case MODE_ID: return t;
-    case MODE_DIAG: return (float)(in * (double)t);
-    case MODE_RESID: {
-      const double rr = (double)t - in;
-      loss += 0.5 * rr * rr;
-      return (float)rr;
-    }
-    case MODE_LGRAD: {
-      const double td = (double)t;
-      const double sg = sigmoid_d(td);
-      const double b01 = 0.5 * (1.0 + in);
-      loss += fmax(td, 0.0) + log1p(exp(-fabs(td))) - b01 * td;
-      return (float)(sg - b01);
-    }
-    default: {  // MODE_LOGIT
-      const double td = (double)t;
-      const double sg = sigmoid_d(td);
-      const double wv = sg * (1.0 - sg);
-      const double b01 = 0.5 * (1.0 + in);
-      if (a.D_out) a.D_out[i] = wv;
-      loss += fmax(td, 0.0) + log1p(exp(-fabs(td))) - b01 * td;
-      return (float)(wv * td + b01 - sg);
-    }
-  }
-}
-
+//
 // Float-compute kernel.  Per step of R rows: every thread loads its slice of the
 // stage from shared memory ONCE into registers (raw 16-byte vectors), forms its
 // partial row dots with packed FP32 FMAs, and after the first barrier the stage is
@@ -668,7 +504,8 @@ static std::map<std::tuple<int, int, int, int64_t>, int> g_tuned_rows;
 
 void apass_set_tuned_rows(const nys_matrix* A, int rows) {
   const int64_t esz = (int64_t)dtype_size(A->dtype);
-  const int vpt = vpt_bucket((A->d + (16 / esz) - 1) / (16 / esz));
+  const int vb = vpt_bucket((A->d + (16 / esz) - 1) / (16 / esz));
+  const int vpt = vb < 0 ? 99 : vb;   // the key apass_plan looks up
   const int dev = current_device();
   std::lock_guard<std::mutex> lk(g_tune_mu);
   if (rows <= 0) g_tuned_rows.erase({dev, A->dtype, vpt, A->ld * esz});
@@ -702,15 +539,39 @@ static void float_layout(const nys_matrix* A, int64_t nvec, int* threads, int* v
 // (register budget of raw[R][VPT]).
 static bool float_rows_ok(int r, int vpt) { return r == 1 || (r == 2 && vpt <= 6) || (r == 4 && vpt <= 3); }
 
+// Warp-specialised pass: used for wide rows, where the classic step's per-row block
+// reductions dominate (NYS_APASS_WS = 0 / 1 overrides the choice).
+static bool ws_wanted(const nys_matrix* A) {
+  if (const char* env = std::getenv("NYS_APASS_WS")) return std::atoi(env) != 0;
+  const int64_t rowbytes = A->ld * (int64_t)dtype_size(A->dtype);
+  if (A->dtype == NYS_F64) return A->d >= 2048;
+  return rowbytes >= 4096;
+}
+
+// Stages of the warp-specialised ring for R rows per stage (0 if fewer than two fit).
+static int ws_stages(int64_t rowbytes, int R) {
+  return (int)std::min<int64_t>(12, kSmemBudget / (R * rowbytes));
+}
+
 // Rows-per-stage values the kernels support for this matrix (float path: bounded by
-// the register budget of the raw vectors; all: at least two stages must fit).
+// the register budget of the raw vectors; all: at least two stages must fit; the
+// warp-specialised pass: 1, 2 or 4 rows with at least three stages, or two for 1 row).
 int apass_row_candidates(const nys_matrix* A, int* out) {
   const int64_t esz = (int64_t)dtype_size(A->dtype);
   const int64_t nvec = (A->d + (16 / esz) - 1) / (16 / esz);
-  int threads = kApassThreads, vpt = vpt_bucket(nvec);
-  if (A->dtype != NYS_F64) float_layout(A, nvec, &threads, &vpt);
   const int64_t rowbytes = A->ld * esz;
   int n = 0;
+  int wthreads = 0, wvpt = 0;
+  if (ws_wanted(A) && apass_ws_layout(A->dtype, A->d, &wthreads, &wvpt)) {
+    for (int r : {1, 2, 4}) {
+      if (A->dtype == NYS_F64 && r == 4) continue;
+      const int S = ws_stages(rowbytes, r);
+      if (S >= (r == 1 ? 2 : 3)) out[n++] = r;
+    }
+    return n;
+  }
+  int threads = kApassThreads, vpt = vpt_bucket(nvec);
+  if (A->dtype != NYS_F64) float_layout(A, nvec, &threads, &vpt);
   for (int r : {1, 2, 4}) {
     if (2 * r * rowbytes > kSmemBudget) continue;
     if (A->dtype != NYS_F64 && !float_rows_ok(r, vpt)) continue;
@@ -724,9 +585,38 @@ bool apass_plan(const nys_matrix* A, ApassPlan* plan) {
   const int vec = (int)(16 / esz);
   const int64_t nvec = (A->d + vec - 1) / vec;
   const int vkey = vpt_bucket(nvec);  // tuning key: vectors per thread at 512 threads
+  const int64_t rowbytes = A->ld * esz;
+  int wthreads = 0, wvpt = 0;
+  if (ws_wanted(A) && apass_ws_layout(A->dtype, A->d, &wthreads, &wvpt)) {
+    // warp-specialised: 2 rows per stage by default (1 for rows over 64 KB, 4 under 8 KB)
+    int R = rowbytes > 64 * 1024 ? 1 : (rowbytes < 8 * 1024 ? 4 : 2);
+    if (A->dtype == NYS_F64 && R > 2) R = 2;
+    if (const int tr = tuned_rows(A->dtype, vkey < 0 ? 99 : vkey, rowbytes)) R = tr;
+    if (R != 1 && R != 2 && R != 4) R = 2;
+    if (A->dtype == NYS_F64 && R > 2) R = 2;
+    if (const char* env = std::getenv("NYS_APASS_ROWS")) {
+      const int r = std::atoi(env);
+      if (r == 1 || r == 2 || (r == 4 && A->dtype != NYS_F64)) R = r;
+    }
+    while (R > 1 && ws_stages(rowbytes, R) < 3) R /= 2;
+    const int S = ws_stages(rowbytes, R);
+    if (S >= 2) {
+      plan->ws = true;
+      plan->rows_per_step = R;
+      plan->stages = S;
+      plan->threads = wthreads;
+      plan->vpt = wvpt;
+      plan->onebar = false;
+      plan->smem = (size_t)S * R * rowbytes;
+      plan->dpad = nvec * vec;
+      const int64_t steps_total = (A->n + R - 1) / R;
+      plan->grid = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count(), steps_total));
+      plan->fused = true;
+      return true;
+    }
+  }
   if (vkey < 0) return false;
   if (A->dtype == NYS_F64 && vkey > 12) return false;
-  const int64_t rowbytes = A->ld * esz;
   int vpt = vkey;
   int R = (int)std::max<int64_t>(1, std::min<int64_t>(kRMax, (48 * 1024) / rowbytes));
   if (A->dtype == NYS_F64) {
@@ -758,6 +648,7 @@ bool apass_plan(const nys_matrix* A, ApassPlan* plan) {
     S = (int)std::min<int64_t>(kMaxStages, kSmemBudget / rowbytes);
   }
   if (S < 2) return false;
+  plan->ws = false;
   plan->rows_per_step = R;
   plan->stages = S;
   plan->threads = threads;
@@ -903,7 +794,9 @@ cudaError_t apass_run(const ApassArgs& a, const ApassPlan& plan, void* partial, 
     NYS_CUDA_TRY(cudaEventRecord(e0, st));
   }
   cudaError_t err;
-  switch (a.dtype) {
+  if (plan.ws) {
+    err = apass_ws_launch(k, plan, a.dtype, st, g_prepare_only);
+  } else switch (a.dtype) {
     case NYS_F64: err = launch_dt<NYS_F64>(k, plan, st); break;
     case NYS_F32: err = launch_float<NYS_F32>(k, plan, st); break;
     case NYS_BF16: err = launch_float<NYS_BF16>(k, plan, st); break;

@@ -56,6 +56,7 @@ struct ApassPlan {
   int threads = 512;     // CTA size (float path: 512 or 640)
   int vpt = 0;           // 16-byte column vectors owned per thread
   bool onebar = false;   // float path, H-matvec modes: one barrier per step
+  bool ws = false;       // warp-specialised pass (apass_ws.cu): threads / vpt / R / S of its layout
 };
 
 bool apass_plan(const nys_matrix* A, ApassPlan* plan);
