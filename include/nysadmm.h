@@ -119,6 +119,9 @@ typedef struct {
   float* warm_record;          /* device, admm_maxit x (2 rank + 3) FP32, or NULL (lasso,
                                   device_loop): row k = [features (rank + 3), target (rank)] of
                                   ADMM iteration k, the training pairs for the model */
+  uint64_t seed;               /* Omega == NULL in nys_sketch / nysadmm_solve / nysadmm_solve_path:
+                                  the Gaussian test matrix is drawn in the library from this seed
+                                  (nys_gaussian_test_matrix); default 0 */
 } nys_opts;
 
 typedef struct {
@@ -164,6 +167,17 @@ nys_status nys_hmatvec(const nys_matrix* A, const double* D, double rho, const v
  *    status word itself. */
 nys_status nys_hmatvec_noalloc(const nys_matrix* A, const double* D, double rho, const void* p,
                                void* y, void* stream);
+
+/* Gaussian test matrix of the sketch (App. B, Alg. Randomized Nystrom Approximation draws
+ * Omega with independent N(0,1) entries), drawn on the device: Omega (device, d x s
+ * column-major FP64) from the counter-based generator Philox-4x32-10 (Salmon et al., SC 2011)
+ * and the Box-Muller transform.  Element e = i + j d is member e mod 2 of pair m = e / 2,
+ * drawn with counter (lo32(m), hi32(m), 0, 0) and key (lo32(seed), hi32(seed)); the 4 output
+ * words give u1 = (((w0 2^32 + w1) >> 11) + 1) 2^-53 and u2 = ((w2 2^32 + w3) >> 11) 2^-53, and
+ * the pair is sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).  The panel depends only on (seed, d, s)
+ * (a d x s draw is the first d s values of a (d s) x 1 draw).  NYS_EINVAL for d < 1, s < 1 or a
+ * NULL Omega. */
+nys_status nys_gaussian_test_matrix(uint64_t seed, int64_t d, int32_t s, double* Omega, void* stream);
 
 /* Randomized Nystrom approximation of H = A^T diag(D) A + diag_shift I
  * (App. B, Alg. Randomized Nystrom Approximation): Omega (device, d x s,
@@ -214,7 +228,8 @@ nys_status pcg_solve(const nys_matrix* A, const double* D, double rho, nys_preco
  * PCG tolerance schedules (opts->pcg_tol_mode, nys_tol_mode): with RNORM_POW `tol`
  * is beta.  An unknown mode gives NYS_EINVAL.
  * b: device, length n, FP64 (labels in {-1,+1} for NYS_LOGISTIC).
- * Omega: device, d x max(rank, rank_max) column-major FP64 Gaussian.
+ * Omega: device, d x max(rank, rank_max) column-major FP64 Gaussian, or NULL: drawn in the
+ * library by nys_gaussian_test_matrix with opts->seed.
  * x_out, z_out: device, length d, FP64 (z is the sparse iterate; either may be
  * NULL).  info: host, may be NULL. */
 nys_status nysadmm_solve(int32_t loss, const nys_matrix* A, const double* b, double gamma,

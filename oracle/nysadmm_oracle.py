@@ -78,6 +78,61 @@ def soft_threshold(v: np.ndarray, kappa: float) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
+# Gaussian test matrix drawn by a counter-based generator (App. B draws Omega ~ N(0,1))
+# ---------------------------------------------------------------------------
+
+PHILOX_M = (0xD2511F53, 0xCD9E8D57)      # round multipliers of Philox-4x32
+PHILOX_W = (0x9E3779B9, 0xBB67AE85)      # Weyl increments of its key schedule
+
+
+def philox4x32_10(ctr, key):
+    """Philox-4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, "Parallel random numbers:
+    as easy as 1, 2, 3", SC 2011), vectorised over the leading axis.
+    ctr: uint64 array (..., 4) of 32-bit words, key: (..., 2).  One round maps
+    (c0, c1, c2, c3) to (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0));
+    the key is bumped by the Weyl increments between rounds."""
+    mask = np.uint64(0xFFFFFFFF)
+    c = [np.asarray(ctr, dtype=np.uint64)[..., i] & mask for i in range(4)]
+    k = [np.asarray(key, dtype=np.uint64)[..., i] & mask for i in range(2)]
+    m0, m1 = np.uint64(PHILOX_M[0]), np.uint64(PHILOX_M[1])
+    for _ in range(10):
+        p0 = m0 * c[0]                       # < 2^64: exact in uint64
+        p1 = m1 * c[2]
+        hi0, lo0 = p0 >> np.uint64(32), p0 & mask
+        hi1, lo1 = p1 >> np.uint64(32), p1 & mask
+        c = [hi1 ^ c[1] ^ k[0], lo1, hi0 ^ c[3] ^ k[1], lo0]
+        k = [(k[0] + np.uint64(PHILOX_W[0])) & mask, (k[1] + np.uint64(PHILOX_W[1])) & mask]
+    return np.stack(c, axis=-1)
+
+
+def gaussian_test_matrix_philox(seed: int, d: int, s: int) -> np.ndarray:
+    """Omega (d x s) with iid N(0,1) entries from Philox-4x32-10 and the Box-Muller
+    transform; element e = i + j d (column-major) is member e mod 2 of pair m = e // 2:
+      counter (lo32(m), hi32(m), 0, 0), key (lo32(seed), hi32(seed)) -> words w0..w3,
+      u1 = ((w0 2^32 + w1) >> 11 + 1) 2^-53  in (0, 1],
+      u2 = ((w2 2^32 + w3) >> 11) 2^-53      in [0, 1),
+      g_even = sqrt(-2 ln u1) cos(2 pi u2),  g_odd = sqrt(-2 ln u1) sin(2 pi u2).
+    The same definition is implemented on the device (nys_gaussian_test_matrix)."""
+    n = d * s
+    m = np.arange((n + 1) // 2, dtype=np.uint64)
+    ctr = np.zeros((m.size, 4), dtype=np.uint64)
+    ctr[:, 0] = m & np.uint64(0xFFFFFFFF)
+    ctr[:, 1] = m >> np.uint64(32)
+    seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    key = np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint64)
+    w = philox4x32_10(ctr, np.broadcast_to(key, (m.size, 2)))
+    a = ((w[:, 0] << np.uint64(32)) | w[:, 1]) >> np.uint64(11)
+    b = ((w[:, 2] << np.uint64(32)) | w[:, 3]) >> np.uint64(11)
+    u1 = (a.astype(np.float64) + 1.0) * 2.0 ** -53
+    u2 = b.astype(np.float64) * 2.0 ** -53
+    r = np.sqrt(-2.0 * np.log(u1))
+    g = np.empty(2 * m.size)
+    g[0::2] = r * np.cos(2.0 * np.pi * u2)
+    g[1::2] = r * np.sin(2.0 * np.pi * u2)
+    return g[:n].reshape(s, d).T.copy()
+
+
+# ---------------------------------------------------------------------------
 # Randomized Nystrom approximation (App. B, Alg. Randomized Nystrom Approximation)
 # ---------------------------------------------------------------------------
 

@@ -335,6 +335,7 @@ __global__ void __launch_bounds__((3 * G + 2) * 32, 1) apass_ws64_kernel(const A
   if (warp < G) {
     if (!nodot) {
       const double* p = reinterpret_cast<const double*>(a.p);
+      const bool p16 = (reinterpret_cast<uintptr_t>(p) & 15u) == 0;   // 16-byte loads allowed
       const int nv_dot = (nvec + TG - 1) / TG;
       for (int k = 0; k < nsteps; ++k) {
         const int st = k % S;
@@ -354,6 +355,9 @@ __global__ void __launch_bounds__((3 * G + 2) * 32, 1) apass_ws64_kernel(const A
             if (odd && v == tail_vec) {
               p0 = __ldg(p + 2 * (int64_t)v);
               p1 = 0.0;
+            } else if (!p16) {
+              p0 = __ldg(p + 2 * (int64_t)v);
+              p1 = __ldg(p + 2 * (int64_t)v + 1);
             } else {
               const double2 pv = __ldg(reinterpret_cast<const double2*>(p) + v);
               p0 = pv.x;

@@ -298,6 +298,13 @@ nys_status precond_from_panels(const double* Om, const double* Y, int64_t d, int
   return nystrom_core(Om, Y, d, s, shift_scale, mant_bits, P->U64, P->lam_d, P->lam, &P->nu, st);
 }
 
+// Omega of a solve: the caller's panel (d x m, copied) or, when Omega is NULL, a panel drawn
+// in the library from `seed` (Philox-4x32-10 + Box-Muller, nys_gaussian_test_matrix).
+nys_status omega_panel(const double* Omega, uint64_t seed, int64_t d, int m, double* Om, cudaStream_t st) {
+  if (Omega) return cuda_status(cudaMemcpyAsync(Om, Omega, (size_t)d * m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return cuda_status(gaussian_panel(seed, d, m, Om, st));
+}
+
 int mant_bits_of(const nys_matrix* A) { return A->dtype == NYS_F64 ? 52 : 23; }
 
 template <typename C>
@@ -446,7 +453,7 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
   double* Om = pool.alloc<double>((size_t)d * smax);
   double* Y = pool.alloc<double>((size_t)d * smax);
   if (!pool.ok()) return NYS_ENOMEM;
-  NYS_CU(cudaMemcpyAsync(Om, Omega, (size_t)d * smax * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  NYS_TRY(omega_panel(Omega, o.seed, d, smax, Om, st));
   const double shs = o.shift_scale > 0 ? o.shift_scale : std::sqrt((double)d);
   if (smax > rank) {
     NYS_TRY(adaptive_sketch(Ain, nullptr, mu, Om, Y, d, rank, smax, o.ada_tol > 0 ? o.ada_tol : 2.0, rho, shs,
@@ -657,7 +664,7 @@ nys_status lasso_path(const nys_matrix* A, const nys_matrix* Ain, const double* 
   double* Om = pool.alloc<double>((size_t)d * rank);
   double* Y = pool.alloc<double>((size_t)d * rank);
   if (!pool.ok()) return NYS_ENOMEM;
-  NYS_CU(cudaMemcpyAsync(Om, Omega, (size_t)d * rank * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  NYS_TRY(omega_panel(Omega, o.seed, d, rank, Om, st));
   NYS_TRY(cholqr2(Om, d, rank, st));
   NYS_TRY(sketch_panel(Ain, nullptr, 0.0, Om, rank, Y, st));
   const double shs = o.shift_scale > 0 ? o.shift_scale : std::sqrt((double)d);
@@ -885,7 +892,7 @@ nys_status logistic_admm(const nys_matrix* A, const nys_matrix* Ain, const doubl
   double* eps_next = pool.alloc<double>(1);
   int* stop = pool.alloc<int>(1);
   if (!pool.ok()) return NYS_ENOMEM;
-  NYS_CU(cudaMemcpyAsync(Om, Omega, (size_t)d * smax * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  NYS_TRY(omega_panel(Omega, o.seed, d, smax, Om, st));
   NYS_CU(cudaMemsetAsync(x, 0, d * sizeof(double), st));
   NYS_CU(cudaMemsetAsync(z, 0, d * sizeof(double), st));
   NYS_CU(cudaMemsetAsync(u, 0, d * sizeof(double), st));
@@ -1064,6 +1071,15 @@ void nys_opts_default(nys_opts* o) {
   o->hx_refresh = 0;
   o->warm_model = nullptr;
   o->warm_record = nullptr;
+  o->seed = 0;
+}
+
+nys_status nys_gaussian_test_matrix(uint64_t seed, int64_t d, int32_t s, double* Omega, void* stream) {
+  if (d < 1 || s < 1 || !Omega) return NYS_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  NYS_CU(gaussian_panel(seed, d, s, Omega, st));
+  NYS_CU(cudaStreamSynchronize(st));
+  return NYS_OK;
 }
 
 const char* nys_strerror(int32_t s) {
@@ -1091,7 +1107,7 @@ nys_status nys_sketch(const nys_matrix* A, const double* D, double diag_shift, i
   if (!out) return NYS_EINVAL;
   *out = nullptr;
   NYS_TRY(check_matrix(A));
-  if (!Omega || s < 1 || s > A->d || s > kMaxRank || !is_fin(diag_shift) || diag_shift < 0) return NYS_EINVAL;
+  if (s < 1 || s > A->d || s > kMaxRank || !is_fin(diag_shift) || diag_shift < 0) return NYS_EINVAL;
   cudaStream_t st = stream_of(opts);
   const int64_t d = A->d;
   nys_precond_s* P = new (std::nothrow) nys_precond_s();
@@ -1105,7 +1121,7 @@ nys_status nys_sketch(const nys_matrix* A, const double* D, double diag_shift, i
       precond_free(P);
       return NYS_ENOMEM;
     }
-    r = cuda_status(cudaMemcpyAsync(Om, Omega, (size_t)d * s * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    r = omega_panel(Omega, opts ? opts->seed : 0, d, s, Om, st);
     if (r == NYS_OK) r = cholqr2(Om, d, s, st);
     if (r == NYS_OK) r = sketch_panel(A, D, diag_shift, Om, s, Y, st);
     const double shs = (opts && opts->shift_scale > 0) ? opts->shift_scale : std::sqrt((double)d);
@@ -1194,7 +1210,7 @@ nys_status nysadmm_solve(int32_t loss, const nys_matrix* A, const double* b, dou
                          nys_info* info) {
   NYS_TRY(check_matrix(A));
   if (loss != NYS_LASSO && loss != NYS_LOGISTIC && loss != NYS_ELASTIC_NET) return NYS_EINVAL;
-  if (!b || !Omega || !(gamma >= 0) || !is_fin(gamma) || !(rho > 0) || !is_fin(rho)) return NYS_EINVAL;
+  if (!b || !(gamma >= 0) || !is_fin(gamma) || !(rho > 0) || !is_fin(rho)) return NYS_EINVAL;
   if (loss == NYS_ELASTIC_NET && !(gamma > 0 && gamma <= 1)) return NYS_EINVAL;  // Eq. 6: 0 < gamma <= 1
   if (rank < 1 || rank > A->d || rank > kMaxRank || !(tol >= 0) || !is_fin(tol)) return NYS_EINVAL;
   nys_opts o;
@@ -1224,7 +1240,7 @@ nys_status nysadmm_solve_path(const nys_matrix* A, const double* b, const double
                               int32_t rank, double tol, const double* Omega, const nys_opts* opts, double* X_out,
                               double* Z_out, nys_info* info, int32_t* pcg_iters) {
   NYS_TRY(check_matrix(A));
-  if (!b || !Omega || !gammas || k < 1 || k > 4096 || !(rho > 0) || !is_fin(rho)) return NYS_EINVAL;
+  if (!b || !gammas || k < 1 || k > 4096 || !(rho > 0) || !is_fin(rho)) return NYS_EINVAL;
   for (int c = 0; c < k; ++c)
     if (!(gammas[c] >= 0) || !is_fin(gammas[c])) return NYS_EINVAL;
   if (rank < 1 || rank > A->d || rank > kMaxRank || !(tol >= 0) || !is_fin(tol)) return NYS_EINVAL;

@@ -39,7 +39,7 @@ class NysOptsC(ctypes.Structure):
                 ("refine", c_int32), ("z_trace", c_void_p), ("rank_max", c_int32),
                 ("ada_tol", c_double), ("resketch_every", c_int32), ("stream", c_void_p),
                 ("device_loop", c_int32), ("hx_refresh", c_int32), ("warm_model", c_void_p),
-                ("warm_record", c_void_p)]
+                ("warm_record", c_void_p), ("seed", ctypes.c_uint64)]
 
 
 class NysInfoC(ctypes.Structure):
@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
     L.nys_hmatvec_noalloc.argtypes = [P(NysMatrixC), c_void_p, c_double, c_void_p, c_void_p, c_void_p]
     L.nys_check_wait_bound.argtypes = [c_double, c_void_p]
     L.nys_sketch.argtypes = [P(NysMatrixC), c_void_p, c_double, c_int32, c_void_p, P(NysOptsC), P(c_void_p)]
+    L.nys_gaussian_test_matrix.argtypes = [ctypes.c_uint64, c_int64, c_int32, c_void_p, c_void_p]
     L.nys_precond_get.argtypes = [c_void_p, c_void_p, P(c_double), P(c_int32), P(c_int64), P(c_double), c_void_p]
     L.nys_precond_apply.argtypes = [c_void_p, c_double, c_void_p, c_void_p, c_int64, c_int32, c_void_p]
     L.pcg_solve.argtypes = [P(NysMatrixC), c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_double,
@@ -112,7 +113,7 @@ def lib() -> ctypes.CDLL:
     L.nys_autotune_apass.restype = c_int32
     L.nys_precond_destroy.argtypes = [c_void_p]
     L.nys_precond_destroy.restype = None
-    for name in ("nys_hmatvec", "nys_hmatvec_noalloc", "nys_sketch", "nys_precond_get", "nys_precond_apply", "pcg_solve",
+    for name in ("nys_hmatvec", "nys_hmatvec_noalloc", "nys_gaussian_test_matrix", "nys_sketch", "nys_precond_get", "nys_precond_apply", "pcg_solve",
                  "nysadmm_solve", "nysadmm_solve_path", "nysadmm_solve_batch", "nys_objective",
                  "nys_stats_read", "nys_mlp_create", "nys_mlp_forward", "nys_mlp_grad", "nys_mlp_train_step",
                  "nys_mlp_get_params"):
@@ -285,14 +286,26 @@ class Precond:
         return Y.reshape(-1) if squeeze else Y
 
 
-def sketch(A: Matrix, Omega: torch.Tensor, D: torch.Tensor | None = None, diag_shift: float = 0.0,
-           shift_scale: float | None = None, stream=None) -> Precond:
-    """Nystrom sketch of H = A^T diag(D) A + diag_shift I from the Gaussian Omega (d x s)."""
-    d, s = Omega.shape
-    Om = Omega.to(torch.float64).T.contiguous()                        # column-major d x s
+def gaussian_test_matrix(seed: int, d: int, s: int, stream=None) -> torch.Tensor:
+    """Omega (d x s, FP64, device) ~ N(0,1) drawn in the library (Philox-4x32-10 + Box-Muller)."""
+    Om = torch.empty(s, d, dtype=torch.float64, device="cuda")          # column-major d x s
+    _check(lib().nys_gaussian_test_matrix(int(seed) & (2**64 - 1), int(d), int(s), _ptr(Om),
+                                          c_void_p(_stream_ptr(stream))), "nys_gaussian_test_matrix")
+    return Om.T
+
+
+def sketch(A: Matrix, Omega: torch.Tensor | None, D: torch.Tensor | None = None, diag_shift: float = 0.0,
+           shift_scale: float | None = None, stream=None, s: int | None = None, seed: int = 0) -> Precond:
+    """Nystrom sketch of H = A^T diag(D) A + diag_shift I from the Gaussian Omega (d x s), or,
+    with Omega None, from s columns drawn in the library from `seed`."""
+    if Omega is None:
+        Om = None
+    else:
+        s = Omega.shape[1]
+        Om = Omega.to(torch.float64).T.contiguous()                    # column-major d x s
     h = c_void_p()
-    o = _opts(stream, shift_scale=shift_scale)
-    _check(lib().nys_sketch(ctypes.byref(A.c), _ptr(D), float(diag_shift), s, _ptr(Om), ctypes.byref(o),
+    o = _opts(stream, shift_scale=shift_scale, seed=int(seed) & (2**64 - 1))
+    _check(lib().nys_sketch(ctypes.byref(A.c), _ptr(D), float(diag_shift), int(s), _ptr(Om), ctypes.byref(o),
                             ctypes.byref(h)), "nys_sketch")
     return Precond(h.value)
 
@@ -322,11 +335,12 @@ def nysadmm_solve(loss: str, A: Matrix, b: torch.Tensor, gamma: float, rho: floa
                   rank_max: int | None = None, ada_tol: float | None = None, resketch_every: int = 1,
                   shift_scale: float | None = None, stream=None, allow_noconv: bool = True,
                   device_loop: bool = True, hx_refresh: int = 0, warm_model=None,
-                  warm_record: bool = False) -> dict:
+                  warm_record: bool = False, seed: int = 0) -> dict:
     """NysADMM (Alg. NysADMM / AdaNysADMM) through the C ABI.  Returns a dict with
-    x, z (FP64 device tensors), info (dict) and, when requested, the z trace."""
+    x, z (FP64 device tensors), info (dict) and, when requested, the z trace.
+    Omega None: the test matrix is drawn in the library from `seed`."""
     d = A.d
-    Om = Omega.to(torch.float64).T.contiguous()                        # column-major d x s
+    Om = None if Omega is None else Omega.to(torch.float64).T.contiguous()   # column-major d x s
     x = torch.empty(d, dtype=torch.float64, device="cuda")
     z = torch.empty(d, dtype=torch.float64, device="cuda")
     zt = torch.empty(admm_iters, d, dtype=torch.float64, device="cuda") if z_trace else None
@@ -343,7 +357,8 @@ def nysadmm_solve(loss: str, A: Matrix, b: torch.Tensor, gamma: float, rho: floa
               rank_max=rank_max or 0, ada_tol=ada_tol, resketch_every=resketch_every,
               device_loop=int(bool(device_loop)), hx_refresh=int(hx_refresh),
               warm_model=warm_model.h if warm_model is not None else None,
-              warm_record=c_void_p(rec.data_ptr()) if rec is not None else None)
+              warm_record=c_void_p(rec.data_ptr()) if rec is not None else None,
+              seed=int(seed) & (2**64 - 1))
     info = NysInfoC()
     st = lib().nysadmm_solve(_LOSSES[loss], ctypes.byref(A.c), _ptr(b.to(torch.float64).contiguous()),
                              float(gamma), float(rho), int(rank), float(tol), _ptr(Om), ctypes.byref(o),

@@ -50,7 +50,8 @@ def test_struct_layouts_match_header(libpath):
     # offsets follow C natural alignment of the header's structs
     assert ctypes.sizeof(nx.NysMatrixC) == 48
     assert nx.NysOptsC.stream.offset == 96 and nx.NysOptsC.hx_refresh.offset == 108
-    assert ctypes.sizeof(nx.NysOptsC) == 128
+    assert nx.NysOptsC.seed.offset == 128
+    assert ctypes.sizeof(nx.NysOptsC) == 136
     assert ctypes.sizeof(nx.NysInfoC) == 48
     assert ctypes.sizeof(nx.NysStatsC) == 8 + 4 * 8 * 6
 
@@ -119,3 +120,28 @@ def test_binding_constants_match_header_enums():
     modes = {"rel": "NYS_TOL_REL", "abs": "NYS_TOL_ABS", "sqrt_rprd": "NYS_TOL_SQRT_RPRD",
              "rnorm_pow": "NYS_TOL_RNORM_POW"}
     assert {k: h[v] for k, v in modes.items()} == nx.TOL_MODES
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """sizeof / offsetof of the header's structs from the C compiler equal the binding's."""
+    import shutil
+    import subprocess
+    from paper_2202_11599_gb300 import nysadmm as nx
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    prog = tmp_path / "layout.c"
+    fields = [f for f, _ in nx.NysOptsC._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nysadmm.h"', 'int main(void) {',
+             'printf("%zu %zu %zu %zu\\n", sizeof(nys_matrix), sizeof(nys_opts), sizeof(nys_info), sizeof(nys_stats));']
+    lines += [f'printf("%zu\\n", offsetof(nys_opts, {f}));' for f in fields]
+    lines += ['return 0; }']
+    prog.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    sizes = [int(v) for v in out[:4]]
+    assert sizes == [ctypes.sizeof(nx.NysMatrixC), ctypes.sizeof(nx.NysOptsC), ctypes.sizeof(nx.NysInfoC),
+                     ctypes.sizeof(nx.NysStatsC)]
+    offs = [int(v) for v in out[4:]]
+    assert offs == [getattr(nx.NysOptsC, f).offset for f in fields]

@@ -735,3 +735,51 @@ def test_adam_first_step_is_signed_lr():
     g = np.array([0.3, -2.0, 1e-3])
     th, m, v = o.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, lr=0.01)
     assert np.allclose(th, -0.01 * np.sign(g) * np.abs(g) / (np.abs(g) + 1e-8), rtol=1e-12)
+
+
+# ---------------------------------------------------------------- counter-based Gaussian test matrix
+
+def _kat_rows():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = []
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        ctr, key, out = (part.split() for part in line.split("|"))
+        rows.append(([int(v, 16) for v in ctr], [int(v, 16) for v in key], [int(v, 16) for v in out]))
+    return rows
+
+
+def test_philox_known_answer_vectors():
+    """Philox-4x32-10 against the generator's published known-answer vectors."""
+    rows = _kat_rows()
+    assert len(rows) == 3
+    ctr = np.array([r[0] for r in rows], dtype=np.uint64)
+    key = np.array([r[1] for r in rows], dtype=np.uint64)
+    out = o.philox4x32_10(ctr, key)
+    assert out.tolist() == [r[2] for r in rows]
+
+
+def test_philox_gaussian_moments_and_layout():
+    """N(0,1) moments of 2 x 10^6 draws (mean, variance, skewness, excess kurtosis within
+    ~5 standard errors; Kolmogorov-Smirnov against the normal CDF), determinism, seeds,
+    and the column-major element numbering (a d x s draw is the first d s values of a
+    (d s) x 1 draw)."""
+    from scipy import stats
+    G = o.gaussian_test_matrix_philox(7, 2000, 1000)
+    g = G.ravel()
+    n = g.size
+    assert abs(g.mean()) <= 5 / np.sqrt(n)
+    assert abs(g.var() - 1.0) <= 5 * np.sqrt(2.0 / n)
+    assert abs(stats.skew(g)) <= 5 * np.sqrt(6.0 / n)
+    assert abs(stats.kurtosis(g)) <= 5 * np.sqrt(24.0 / n)
+    assert stats.kstest(g[:200000], "norm").pvalue > 1e-3
+    assert np.array_equal(G, o.gaussian_test_matrix_philox(7, 2000, 1000))
+    assert not np.array_equal(G[:, 0], o.gaussian_test_matrix_philox(8, 2000, 1)[:, 0])
+    H = o.gaussian_test_matrix_philox(7, 2000 * 1000, 1)
+    assert np.array_equal(G.ravel(order="F"), H[:, 0])
+    # odd element count: the last pair contributes its even member only
+    K = o.gaussian_test_matrix_philox(7, 7, 3)
+    assert np.array_equal(K.ravel(order="F"), H[:21, 0])
