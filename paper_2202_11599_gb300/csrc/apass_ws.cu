@@ -21,6 +21,8 @@
 // drains its copies still in flight and the pass reports NYS_ETIMEOUT.
 // Partial sums are written per CTA and summed in a fixed order by apass_reduce, so the
 // result is bitwise reproducible from run to run.
+#include <type_traits>
+
 #include "apass_common.cuh"
 
 namespace nys {
@@ -43,6 +45,36 @@ __device__ __forceinline__ void ws_init(WsBars& b, int S, int G, int GU) {
     mbar_init(&b.empty[st], GU);
   }
   fence_mbar_init();
+}
+
+// Warp sums of R per-lane values (R = 1, 2, 4) by a reduce-scatter over the lane bits:
+// the first log2(R) exchanges split the rows between lane halves, the rest finish each
+// row; the fixed order makes the sums bitwise reproducible.  Returns, in lane r (32 / R),
+// the total of row r (every other lane holds a partial).
+template <int R, typename T>
+__device__ __forceinline__ T warp_sum_rows(const T (&v)[R], int lane) {
+  constexpr unsigned F = 0xffffffffu;
+  if constexpr (R == 1) {
+    return warp_sum(v[0]);
+  } else if constexpr (R == 2) {
+    const bool hi = (lane & 16) != 0;
+    T keep = hi ? v[1] : v[0];
+    keep += __shfl_xor_sync(F, hi ? v[0] : v[1], 16);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(F, keep, o);
+    return keep;
+  } else {
+    static_assert(R == 4, "rows per stage: 1, 2 or 4");
+    const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
+    T ka = b4 ? v[2] : v[0], kb = b4 ? v[3] : v[1];
+    ka += __shfl_xor_sync(F, b4 ? v[0] : v[2], 16);
+    kb += __shfl_xor_sync(F, b4 ? v[1] : v[3], 16);
+    T keep = b3 ? kb : ka;
+    keep += __shfl_xor_sync(F, b3 ? ka : kb, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) keep += __shfl_xor_sync(F, keep, o);
+    return keep;
+  }
 }
 
 // Producer (lane 0 of its warp): issues stage k once stage k - S has been released.
@@ -140,11 +172,15 @@ __global__ void __launch_bounds__((2 * G + 2) * 32, 1) apass_ws_kernel(const Apa
   const int64_t r0 = a.n * (int64_t)blockIdx.x / gridDim.x;
   const int64_t r1 = a.n * (int64_t)(blockIdx.x + 1) / gridDim.x;
   const int nsteps = (int)((r1 - r0 + R - 1) / R);
-  const int tail_vec = (int)(a.d / VEC);
   const int tail_n = (int)(a.d % VEC);
   const bool nodot = a.mode == MODE_CONST;
   const uint32_t sbase = smem_u32(smem);
   volatile int* abort_v = &abort_flag;
+  // group slot j of this thread (dot: tid, update: tid - TG): its vectors j + kk TG exist
+  // for kk < nfull, and the ragged last vector (when d is not a multiple of VEC) is kk = tail_kk
+  const int jg = tid < TG ? tid : tid - TG;
+  const int nfull = jg < nvec ? min(VPT, (nvec - 1 - jg) / TG + 1) : 0;
+  const int tail_kk = (tail_n != 0 && (nvec - 1) % TG == jg) ? (nvec - 1) / TG : -1;
 
   if (tid == 0) {
     ws_init(bars, S, G, G);
@@ -186,30 +222,36 @@ __global__ void __launch_bounds__((2 * G + 2) * 32, 1) apass_ws_kernel(const Apa
           break;
         }
         const int rows_here = (int)min((int64_t)R, r1 - (r0 + (int64_t)k * R));
-        const uint32_t sb = sbase + (uint32_t)st * stage_bytes;
+        const uint32_t sbj = sbase + (uint32_t)st * stage_bytes + (uint32_t)j * 16u;
         float2 dacc[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) dacc[r] = make_float2(0.f, 0.f);
+        // full stages take the branch-free body; vector kk sits at a compile-time offset
+        auto body = [&](auto full) {
 #pragma unroll
-        for (int kk = 0; kk < VPT; ++kk) {
-          const int v = j + kk * TG;
-          if (v < nvec) {
+          for (int kk = 0; kk < VPT; ++kk) {
+            if (kk < nfull) {
+              const bool tl = kk == tail_kk;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-              if (r < rows_here) {
-                uint4 x = lds128(sb + (uint32_t)r * rowbytes + (uint32_t)v * 16u);
-                if (v == tail_vec) mask_tail<DT>(x, tail_n);
+              for (int r = 0; r < R; ++r) {
+                if (decltype(full)::value || r < rows_here) {
+                  uint4 x = lds128(sbj + (uint32_t)r * rowbytes + (uint32_t)(kk * TG * 16));
+                  if (tl) mask_tail<DT>(x, tail_n);
 #pragma unroll
-                for (int q = 0; q < NP; ++q) dacc[r] = __ffma2_rn(unpack_pair<DT>(x, q), pr[kk][q], dacc[r]);
+                  for (int q = 0; q < NP; ++q) dacc[r] = __ffma2_rn(unpack_pair<DT>(x, q), pr[kk][q], dacc[r]);
+                }
               }
             }
           }
-        }
+        };
+        if (rows_here == R) body(std::true_type{});
+        else body(std::false_type{});
+        float sums[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const float sr = warp_sum(dacc[r].x + dacc[r].y);
-          if (lane == 0) red[st][warp][r] = sr;
-        }
+        for (int r = 0; r < R; ++r) sums[r] = dacc[r].x + dacc[r].y;
+        const float tot = warp_sum_rows<R>(sums, lane);
+        if ((lane & (32 / R - 1)) == 0) red[st][warp][lane / (32 / R)] = tot;
+        __syncwarp();
         if (lane == 0) mbar_arrive(&bars.dotted[st]);
       }
     }
@@ -228,28 +270,32 @@ __global__ void __launch_bounds__((2 * G + 2) * 32, 1) apass_ws_kernel(const Apa
         break;
       }
       const int rows_here = (int)min((int64_t)R, r1 - (r0 + (int64_t)k * R));
-      const uint32_t sb = sbase + (uint32_t)st * stage_bytes;
+      const uint32_t sbj = sbase + (uint32_t)st * stage_bytes + (uint32_t)j * 16u;
       float2 u2[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const float u = us[st][r];
         u2[r] = make_float2(u, u);
       }
+      auto body = [&](auto full) {
 #pragma unroll
-      for (int kk = 0; kk < VPT; ++kk) {
-        const int v = j + kk * TG;
-        if (v < nvec) {
+        for (int kk = 0; kk < VPT; ++kk) {
+          if (kk < nfull) {
+            const bool tl = kk == tail_kk;
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
-            if (r < rows_here) {
-              uint4 x = lds128(sb + (uint32_t)r * rowbytes + (uint32_t)v * 16u);
-              if (v == tail_vec) mask_tail<DT>(x, tail_n);
+            for (int r = 0; r < R; ++r) {
+              if (decltype(full)::value || r < rows_here) {
+                uint4 x = lds128(sbj + (uint32_t)r * rowbytes + (uint32_t)(kk * TG * 16));
+                if (tl) mask_tail<DT>(x, tail_n);
 #pragma unroll
-              for (int q = 0; q < NP; ++q) acc[kk][q] = __ffma2_rn(unpack_pair<DT>(x, q), u2[r], acc[kk][q]);
+                for (int q = 0; q < NP; ++q) acc[kk][q] = __ffma2_rn(unpack_pair<DT>(x, q), u2[r], acc[kk][q]);
+              }
             }
           }
         }
-      }
+      };
+      if (rows_here == R) body(std::true_type{});
+      else body(std::false_type{});
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars.empty[st]);
     }
@@ -374,11 +420,12 @@ __global__ void __launch_bounds__((3 * G + 2) * 32, 1) apass_ws64_kernel(const A
             }
           }
         }
+        double sums[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const double sr = warp_sum(dacc[r]);
-          if (lane == 0) red[st][warp][r] = sr;
-        }
+        for (int r = 0; r < R; ++r) sums[r] = dacc[r];
+        const double tot = warp_sum_rows<R>(sums, lane);
+        if ((lane & (32 / R - 1)) == 0) red[st][warp][lane / (32 / R)] = tot;
+        __syncwarp();
         if (lane == 0) mbar_arrive(&bars.dotted[st]);
       }
     }

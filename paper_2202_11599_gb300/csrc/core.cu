@@ -416,34 +416,37 @@ __device__ __forceinline__ void jacobi_rot(double app, double aqq, double apq, d
 // One round: Aout = J^T Ain J and V <- V J for the round's N/2 disjoint rotations.
 // Block (bx, by) owns a 16 x 16 tile of 2x2 pair-blocks of A (pairs ma = bx*16 + tx,
 // mb = by*16 + ty); the 32 rotations it needs are computed once into shared memory.
-// Every block also applies its 16 column rotations to one row slice of V.
+// Every block also applies its 16 column rotations to one row slice of V (slice by of gy).
 constexpr int JT = 16;
-__global__ void __launch_bounds__(JT * JT) jacobi_round_kernel(const double* __restrict__ Ain, double* __restrict__ Aout,
-                                                               double* V, int N, int r, const int* __restrict__ done) {
-  if (*done) return;
-  __shared__ double rc[2][JT], rs[2][JT];
-  __shared__ int rp[2][JT], rq[2][JT];
+struct JacobiRoundSmem {
+  double rc[2][JT], rs[2][JT];
+  int rp[2][JT], rq[2][JT];
+};
+// (Plain pointers: in the persistent form Ain was written by other blocks earlier in the same
+// launch, so its loads must not take the non-coherent read-only path.)
+__device__ __forceinline__ void jacobi_round(const double* Ain, double* Aout, double* V, int N, int r, int bx, int by,
+                                             int gy, JacobiRoundSmem& sh) {
   const int H = N / 2;
   const int tx = threadIdx.x % JT, ty = threadIdx.x / JT;
   if (threadIdx.x < 2 * JT) {
     const int side = threadIdx.x / JT, t = threadIdx.x % JT;
-    const int m = (side == 0 ? blockIdx.x : blockIdx.y) * JT + t;
+    const int m = (side == 0 ? bx : by) * JT + t;
     int p = 0, q = 1;
     double c = 1.0, sn = 0.0;
     if (m < H) {
       rr_pair(N, r, m, p, q);
       jacobi_rot(Ain[p + (int64_t)p * N], Ain[q + (int64_t)q * N], Ain[p + (int64_t)q * N], c, sn);
     }
-    rc[side][t] = c;
-    rs[side][t] = sn;
-    rp[side][t] = p;
-    rq[side][t] = q;
+    sh.rc[side][t] = c;
+    sh.rs[side][t] = sn;
+    sh.rp[side][t] = p;
+    sh.rq[side][t] = q;
   }
   __syncthreads();
-  const int ma = blockIdx.x * JT + tx, mb = blockIdx.y * JT + ty;
+  const int ma = bx * JT + tx, mb = by * JT + ty;
   if (ma < H && mb < H) {
-    const int pa = rp[0][tx], qa = rq[0][tx], pb = rp[1][ty], qb = rq[1][ty];
-    const double ca = rc[0][tx], sa = rs[0][tx], cb = rc[1][ty], sb = rs[1][ty];
+    const int pa = sh.rp[0][tx], qa = sh.rq[0][tx], pb = sh.rp[1][ty], qb = sh.rq[1][ty];
+    const double ca = sh.rc[0][tx], sa = sh.rs[0][tx], cb = sh.rc[1][ty], sb = sh.rs[1][ty];
     const double x_pp = Ain[pa + (int64_t)pb * N], x_pq = Ain[pa + (int64_t)qb * N];
     const double x_qp = Ain[qa + (int64_t)pb * N], x_qq = Ain[qa + (int64_t)qb * N];
     // columns: p' = c p - s q, q' = s p + c q
@@ -461,20 +464,115 @@ __global__ void __launch_bounds__(JT * JT) jacobi_round_kernel(const double* __r
     Aout[qa + (int64_t)pb * N] = z_qp;
     Aout[qa + (int64_t)qb * N] = z_qq;
   }
-  // V <- V J for this block's 16 pairs, rows [lo, hi) of slice blockIdx.y (the pairs of a
-  // round are disjoint, so every (row, pair) element is independent of the others).
+  // V <- V J for this block's 16 pairs, rows [lo, hi) of slice by (the pairs of a round
+  // are disjoint, so every (row, pair) element is independent of the others).
   {
-    const int npair = min(JT, H - (int)blockIdx.x * JT);
-    const int lo = (int)((int64_t)N * blockIdx.y / gridDim.y), hi = (int)((int64_t)N * (blockIdx.y + 1) / gridDim.y);
+    const int npair = min(JT, H - bx * JT);
+    const int lo = (int)((int64_t)N * by / gy), hi = (int)((int64_t)N * (by + 1) / gy);
     const int rows = hi - lo;
     for (int e = threadIdx.x; e < npair * rows; e += JT * JT) {
       const int t = e / rows, row = lo + e % rows;
-      const int p = rp[0][t], q = rq[0][t];
-      const double c = rc[0][t], sn = rs[0][t];
+      const int p = sh.rp[0][t], q = sh.rq[0][t];
+      const double c = sh.rc[0][t], sn = sh.rs[0][t];
       const double vp = V[row + (int64_t)p * N], vq = V[row + (int64_t)q * N];
       V[row + (int64_t)p * N] = c * vp - sn * vq;
       V[row + (int64_t)q * N] = sn * vp + c * vq;
     }
+  }
+}
+
+__global__ void __launch_bounds__(JT * JT) jacobi_round_kernel(const double* __restrict__ Ain, double* __restrict__ Aout,
+                                                               double* V, int N, int r, const int* __restrict__ done) {
+  if (*done) return;
+  __shared__ JacobiRoundSmem sh;
+  jacobi_round(Ain, Aout, V, N, r, blockIdx.x, blockIdx.y, gridDim.y, sh);
+}
+
+// The whole eigensolve in one launch: the grid (co-resident, cooperative launch) runs the
+// rounds of every sweep separated by grid barriers, then takes off(A)^2 / ||A||_F^2 from
+// per-block partials summed by every block in the same fixed order, so all blocks take
+// the same stop decision.  The rotations and their order are those of jacobi_round_kernel,
+// so the result is bitwise that of the round-per-launch form.  ctl[0] = barrier count,
+// ctl[1] = barrier generation, ctl[2] = sweeps done, ctl[3] = 1 if a barrier wait ran out.
+__global__ void __launch_bounds__(JT * JT) jacobi_persistent_kernel(double* A0, double* A1, double* V, int N,
+                                                                    int max_sweeps, double tol2, double* part,
+                                                                    unsigned* ctl) {
+  __shared__ JacobiRoundSmem sh;
+  __shared__ double red[2][JT * JT / 32];
+  const int nblk = gridDim.x * gridDim.y;
+  const int bid = blockIdx.x + blockIdx.y * gridDim.x;
+  const int H = N / 2;
+  double* cur = A0;
+  double* nxt = A1;
+  int sweeps = 0;
+  for (; sweeps < max_sweeps; ++sweeps) {
+    for (int r = 0; r < N - 1; ++r) {
+      jacobi_round(cur, nxt, V, N, r, blockIdx.x, blockIdx.y, gridDim.y, sh);
+      if (!grid_barrier(&ctl[0], &ctl[1], (unsigned)nblk)) {
+        if (threadIdx.x == 0) atomicExch(&ctl[3], 1u);
+        return;
+      }
+      double* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+    // off-diagonal and total squares of this block's tile of the current matrix
+    double off = 0.0, tot = 0.0;
+    {
+      const int tx = threadIdx.x % JT, ty = threadIdx.x / JT;
+      const int ma = blockIdx.x * JT + tx, mb = blockIdx.y * JT + ty;
+      if (ma < H && mb < H) {
+        const int ia[2] = {2 * ma, 2 * ma + 1}, ib[2] = {2 * mb, 2 * mb + 1};
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            const double x = cur[ia[u] + (int64_t)ib[v] * N];
+            tot += x * x;
+            if (ia[u] != ib[v]) off += x * x;
+          }
+      }
+    }
+    off = warp_sum(off);
+    tot = warp_sum(tot);
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = off;
+      red[1][threadIdx.x >> 5] = tot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double o = 0.0, t = 0.0;
+      for (int w = 0; w < JT * JT / 32; ++w) {
+        o += red[0][w];
+        t += red[1][w];
+      }
+      part[2 * bid] = o;
+      part[2 * bid + 1] = t;
+    }
+    if (!grid_barrier(&ctl[0], &ctl[1], (unsigned)nblk)) {
+      if (threadIdx.x == 0) atomicExch(&ctl[3], 1u);
+      return;
+    }
+    double o = 0.0, t = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+      o += ((volatile double*)part)[2 * b];
+      t += ((volatile double*)part)[2 * b + 1];
+    }
+    // every block has read the partials before any block overwrites them next sweep
+    if (!grid_barrier(&ctl[0], &ctl[1], (unsigned)nblk)) {
+      if (threadIdx.x == 0) atomicExch(&ctl[3], 1u);
+      return;
+    }
+    if (o <= tol2 * t) {
+      ++sweeps;
+      break;
+    }
+  }
+  if (bid == 0 && threadIdx.x == 0) ctl[2] = (unsigned)sweeps;
+  // leave the diagonalised matrix in A0
+  if (cur != A0) {
+    for (int64_t idx = (int64_t)bid * blockDim.x + threadIdx.x; idx < (int64_t)N * N; idx += (int64_t)nblk * blockDim.x)
+      A0[idx] = cur[idx];
   }
 }
 
@@ -511,7 +609,9 @@ __global__ void jacobi_setup_kernel(const double* __restrict__ G, int s, double*
 
 size_t jacobi_work_bytes(int s) {
   const int N = s + (s & 1);
-  return (size_t)2 * N * N * sizeof(double) + (size_t)N * N * sizeof(double) + 64;
+  const int HT = (N / 2 + 15) / 16;
+  // A0, A1, spare N x N, flags, per-block partials of the persistent form, its barrier words
+  return (size_t)3 * N * N * sizeof(double) + 64 + (size_t)2 * HT * HT * sizeof(double) + 64;
 }
 
 // Eigendecomposition of the symmetric s x s matrix G.  Results: eigenvalues on the
@@ -528,9 +628,36 @@ cudaError_t jacobi_eig(double* G, double* Vout, int s, double* work, int* sweeps
   NYS_CUDA_TRY(cudaGetLastError());
   const int HT = (N / 2 + JT - 1) / JT;
   const dim3 blocks(HT, HT);
+  const int kMaxSweeps = 30;
+  // one cooperative launch for all sweeps when the grid can be co-resident
+  const char* jp = std::getenv("NYS_JACOBI_PERSISTENT");   // "0" selects the round-per-launch form
+  if (N > 2 && (jp == nullptr || std::atoi(jp) != 0)) {
+    int dev = 0, coop = 0, per_sm = 0;
+    NYS_CUDA_TRY(cudaGetDevice(&dev));
+    NYS_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    NYS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_persistent_kernel, JT * JT, 0));
+    if (N > 2 && coop && (int64_t)per_sm * sm_count() >= (int64_t)HT * HT) {
+      double* part = work + (size_t)3 * N * N + 8;                       // 2 doubles per block
+      unsigned* ctl = reinterpret_cast<unsigned*>(part + 2 * (size_t)HT * HT);
+      NYS_CUDA_TRY(cudaMemsetAsync(ctl, 0, 4 * sizeof(unsigned), st));
+      double* a0 = A0;
+      double* a1 = A1;
+      double* vv = Vout;
+      int n = N, ms = kMaxSweeps;
+      double tol2 = 1e-24;
+      void* args[] = {&a0, &a1, &vv, &n, &ms, &tol2, &part, &ctl};
+      count_launch();
+      NYS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_persistent_kernel, blocks, dim3(JT * JT), args, 0, st));
+      unsigned h[4] = {0, 0, 0, 0};
+      NYS_CUDA_TRY(cudaMemcpyAsync(h, ctl, sizeof(h), cudaMemcpyDeviceToHost, st));
+      NYS_CUDA_TRY(cudaStreamSynchronize(st));
+      if (h[3]) return cudaErrorLaunchTimeout;   // a barrier wait ran out (reported as NYS_ECUDA)
+      if (sweeps_out) *sweeps_out = (int)h[2];
+      return cudaSuccess;
+    }
+  }
   int sweeps = 0;
   int done_h = 0;
-  const int kMaxSweeps = 30;
   // One sweep = N - 1 round launches (ping-pong between A0 and A1; N - 1 is odd for even
   // N, so after a sweep the roles of A0 and A1 swap).  Sweeps are captured once as two CUDA
   // graphs (A0 -> A1 and A1 -> A0 starting buffers) and replayed, which removes the
