@@ -298,7 +298,8 @@ def run_ours(args):
     chk_gbs = chk["bytes"] / (chk["ms"] * 1e-3) / 1e9 if chk["launches"] else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": args.traffic,
-                "kernel": "apass_f_kernel<BF16> (fused y = A^T (A p) + rho p)", "peak_source": peak_src,
+                "kernel": "apass_ws_kernel<BF16> (warp-specialised fused y = A^T (A p) + rho p)",
+                "peak_source": peak_src,
                 "launches": ap["launches"], "mean_launch_ms": round(mean_ms, 4),
                 "algorithmic_bytes_per_launch": bytes_per,
                 "timing": "in-kernel %globaltimer over the timed region (kernels run inside a CUDA graph)",
@@ -822,11 +823,10 @@ def main():
     ap.add_argument("--cal-iters-fp64", type=int, default=1200)
     ap.add_argument("--cpu-iters", type=int, default=3)
     ap.add_argument("--ref-cal-iters", type=int, default=1200)
-    # DRAM bytes (read + write) per launch of the BF16 A-pass on this workload: ncu
-    # --set full of apass_f_kernel<BF16, 2, 4, 640> on 50,000 x 10,000 (1.000163 GB read,
-    # 3.49 MB of partials written), rows doubled to 100,000 -- equal to the algorithmic
-    # bytes (no re-reads).  Pass --traffic none after changing that kernel.
-    ap.add_argument("--traffic", type=lambda v: None if v == "none" else float(v), default=2.0038e9,
+    # DRAM bytes (read + write) per launch of the BF16 A-pass on this workload, from the ncu
+    # capture of the warp-specialised kernel on 50,000 x 10,000 (profiles/), rows doubled to
+    # 100,000.  None until a capture of the current kernel is recorded.
+    ap.add_argument("--traffic", type=lambda v: None if v == "none" else float(v), default=None,
                     help="ncu dram bytes per A-pass launch (from a committed profile), if current")
     ap.add_argument("--pcg-tol", type=float, default=None,
                     help="PCG tolerance of the mixed solve (beta for rnorm_pow, default 1.75; rel-tol otherwise, "
