@@ -616,10 +616,36 @@ struct AdmmCtl {
   unsigned int ticket;  // last-block election of the fused zu / scalar kernel
   long long nodes;  // kernel launches executed (instrumentation)
   double eps_next;  // sqrt(r_p r_d) of the last iteration
+  unsigned int bar_count, bar_gen;  // grid barrier of the fused no-step kernel
 };
 
 namespace {
 
+
+// PCG tolerance of ADMM iteration k: SQRT_RPRD uses sqrt(r_p r_d) of the previous
+// iteration (absolute), ABS the fixed tol, REL the fixed relative tol, and the decaying
+// schedule ||r^k|| / k^beta (beta = tol, k counted from 1) a relative tol.
+__device__ __forceinline__ void iter_tol(int tol_mode, double tol, double tol_floor, int k, double eps_next,
+                                         double* tol_out, int* abs_out) {
+  if (tol_mode == NYS_TOL_SQRT_RPRD && k > 0) {
+    *tol_out = eps_next;
+    *abs_out = 1;
+  } else if (tol_mode == NYS_TOL_ABS) {
+    *tol_out = tol;
+    *abs_out = 1;
+  } else {
+    const double t = tol_mode == NYS_TOL_RNORM_POW ? pow((double)(k + 1), -tol) : tol;
+    *tol_out = fmax(t, tol_floor);
+    *abs_out = 0;
+  }
+}
+
+// k = 0 and refined steps start from x = 0 (hx = 0); otherwise (H + rho I) x is recomputed
+// when hx_refresh == 0 (as printed) or every hx_refresh iterations.  1 = reuse the tracked hx.
+__device__ __forceinline__ int iter_hx_skip(int refine, int k, int hx_refresh) {
+  if (refine || k == 0) return 1;
+  return (hx_refresh == 0 || k % hx_refresh == 0) ? 0 : 1;
+}
 
 __global__ void admm_begin_kernel(AdmmCtl* ctl, PcgState* st, double tol, double tol_floor, int tol_mode, int maxit,
                                   const int* __restrict__ fixed_dev, int hx_refresh, int refine,
@@ -636,22 +662,8 @@ __global__ void admm_begin_kernel(AdmmCtl* ctl, PcgState* st, double tol, double
   st->fixed = fixed_dev ? fixed_dev[k] : -1;
   st->ticket[0] = 0u;
   st->ticket[1] = 0u;
-  if (tol_mode == NYS_TOL_SQRT_RPRD && k > 0) {
-    st->tol = ctl->eps_next;
-    st->tol_abs = 1;
-  } else if (tol_mode == NYS_TOL_ABS) {
-    st->tol = tol;
-    st->tol_abs = 1;
-  } else {
-    // REL, or the decaying schedule ||r^k|| / k^beta (beta = tol, k counted from 1)
-    const double t = tol_mode == NYS_TOL_RNORM_POW ? pow((double)(k + 1), -tol) : tol;
-    st->tol = fmax(t, tol_floor);
-    st->tol_abs = 0;
-  }
-  // k = 0 and refined steps start from x = 0 (hx = 0); otherwise recompute (H + rho I) x
-  // when hx_refresh == 0 (as printed) or every hx_refresh iterations
-  if (refine || k == 0) ctl->hx_skip = 1;
-  else ctl->hx_skip = (hx_refresh == 0 || k % hx_refresh == 0) ? 0 : 1;
+  iter_tol(tol_mode, tol, tol_floor, k, ctl->eps_next, &st->tol, &st->tol_abs);
+  ctl->hx_skip = iter_hx_skip(refine, k, hx_refresh);
   // the recompute pass sits in a conditional IF node: skipped iterations launch nothing
   if (!ctl->hx_skip) ctl->nodes += hx_nodes;
   cudaGraphSetConditional(hx_cond, ctl->hx_skip ? 0u : 1u);
@@ -751,6 +763,169 @@ __global__ void __launch_bounds__(kVecThreads) admm_zu_g_kernel(int64_t d, const
     admm_scalar_g_body((int)gridDim.x, part5, rho, K, eps_abs, eps_rel, rp_trace, rd_trace, pcg_it_trace, st, ctl,
                        nodes_per_iter, nodes_per_pcg_iter, cond);
 }
+
+
+// Fused ADMM iterations whose x-subproblem needs no PCG step (the warm start already meets
+// the iteration's PCG tolerance, or the replayed count is 0), the common case late in a
+// solve under the decaying schedules.  One cooperative launch runs such iterations back to
+// back with two grid barriers each, instead of the begin / right-hand side / PCG-init /
+// P^{-1} / prox-dual launches and conditional nodes of the general body:
+//   1. r = q + rho (z - u), w = r - (H + rho I) x (tracked), partial ||w||^2, ||r||^2
+//      (blocks and thread mapping of pcg_update_kernel's init step);
+//   2. every block sums the partials in the order of pcg_scalar_body and takes the same stop
+//      decision; if PCG would step (or (H + rho I) x is due for a recompute) the kernel
+//      hands iteration k to the general body (h_slow = 1) and returns;
+//   3. otherwise x is unchanged: z = S_kappa(x + u), u += x - z and the residual partials
+//      (blocks of admm_zu_g_kernel), then every block forms r_p, r_d, the stop test and the
+//      next tolerance as admm_scalar_g_body does; block 0 records them.
+// The arithmetic and its order are those of the general body, so iterates are bitwise
+// those of a solve without this kernel.  The barrier waits are bounded (NYS_ETIMEOUT).
+template <typename C>
+__global__ void __launch_bounds__(kVecThreads) admm_nostep_kernel(
+    int64_t d, int chunk, int nb3, int nbz, const double* __restrict__ q, double* __restrict__ x,
+    double* __restrict__ z, double* __restrict__ u, const C* __restrict__ xc, const C* __restrict__ hx, double rho,
+    double kappa, double* part_w2, double* part_r2, double* part5, AdmmCtl* ctl, double tol, double tol_floor,
+    int tol_mode, const int* __restrict__ fixed_dev, int hx_refresh, int K, double eps_abs, double eps_rel,
+    double* ztrace, double* rp_trace, double* rd_trace, int* pcg_it_trace, int* dstat,
+    cudaGraphConditionalHandle h_admm, cudaGraphConditionalHandle h_slow) {
+  __shared__ double sh[kVecThreads / 32];
+  __shared__ double slot;
+  __shared__ int s_go;
+  const int b = blockIdx.x;
+  const unsigned nblk = gridDim.x;
+  int k = ctl->k;
+  double eps_next = ctl->eps_next;
+  for (;;) {
+    // ---- iteration k: hand it to the general body when hx is due for a recompute
+    if (!iter_hx_skip(0, k, hx_refresh)) break;
+    double tolk;
+    int tol_abs;
+    iter_tol(tol_mode, tol, tol_floor, k, eps_next, &tolk, &tol_abs);
+    // ---- 1. right-hand side and warm-start residual partials
+    if (b < nb3) {
+      const int64_t j0 = (int64_t)b * chunk;
+      const int64_t j1 = min(d, j0 + chunk);
+      double lw2 = 0.0, lr2 = 0.0;
+      for (int64_t j = j0 + threadIdx.x; j < j1; j += kVecThreads) {
+        const C rj = (C)fma(rho, z[j] - u[j], q[j]);
+        const C wj = rj - hx[j];
+        lr2 += (double)rj * (double)rj;
+        lw2 += (double)wj * (double)wj;
+      }
+      const double tw2 = block_sum<kVecThreads>(lw2, sh);
+      const double tr2 = block_sum<kVecThreads>(lr2, sh);
+      if (threadIdx.x == 0) {
+        part_w2[b] = tw2;
+        part_r2[b] = tr2;
+      }
+    }
+    if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, nblk)) {
+      if (b == 0 && threadIdx.x == 0) {
+        atomicExch(dstat, (int)NYS_ETIMEOUT);
+        cudaGraphSetConditional(h_admm, 0u);
+        cudaGraphSetConditional(h_slow, 0u);
+      }
+      return;
+    }
+    // ---- 2. stop decision of the PCG warm start (every block, same order)
+    const double w2 = block_fixed_sum_cg(part_w2, nb3, &slot);
+    const double r2 = block_fixed_sum_cg(part_r2, nb3, &slot);
+    const double thresh2 = tol_abs ? tolk * tolk : tolk * tolk * r2;
+    const int fixed = fixed_dev ? fixed_dev[k] : -1;
+    const bool nostep = fixed >= 0 ? fixed == 0 : !(w2 > thresh2);
+    if (!nostep) break;
+    // ---- 3. prox / dual step with x unchanged, residual partials
+    if (b < nbz) {
+      double* zt = ztrace ? ztrace + (int64_t)k * d : nullptr;
+      double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+      for (int64_t j = b * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)nbz * kVecThreads) {
+        const double xj = (double)xc[j];
+        const double zo = z[j];
+        const double vj = xj + u[j];
+        const double mag = fabs(vj) - kappa;
+        const double zj = mag > 0.0 ? copysign(mag, vj) : 0.0;
+        const double uj = u[j] + xj - zj;
+        x[j] = xj;
+        z[j] = zj;
+        u[j] = uj;
+        if (zt) zt[j] = zj;
+        a0 += (xj - zj) * (xj - zj);
+        a1 += (zj - zo) * (zj - zo);
+        a2 += xj * xj;
+        a3 += zj * zj;
+        a4 += uj * uj;
+      }
+      a0 = block_sum<kVecThreads>(a0, sh);
+      a1 = block_sum<kVecThreads>(a1, sh);
+      a2 = block_sum<kVecThreads>(a2, sh);
+      a3 = block_sum<kVecThreads>(a3, sh);
+      a4 = block_sum<kVecThreads>(a4, sh);
+      if (threadIdx.x == 0) {
+        double* o = part5 + (int64_t)b * 5;
+        o[0] = a0;
+        o[1] = a1;
+        o[2] = a2;
+        o[3] = a3;
+        o[4] = a4;
+      }
+    }
+    if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, nblk)) {
+      if (b == 0 && threadIdx.x == 0) {
+        atomicExch(dstat, (int)NYS_ETIMEOUT);
+        cudaGraphSetConditional(h_admm, 0u);
+        cudaGraphSetConditional(h_slow, 0u);
+      }
+      return;
+    }
+    // ---- 4. scalars of the iteration (every block; block 0 records them)
+    if (threadIdx.x < 32) {
+      double a[5];
+      sum_part5(nbz, part5, a);
+      if (threadIdx.x == 0) {
+        const double rp = sqrt(a[0]);
+        const double rd = rho * sqrt(a[1]);
+        eps_next = sqrt(rp * rd);
+        int stop = 0;
+        if (eps_rel > 0.0) {
+          const double tp = eps_abs + eps_rel * fmax(sqrt(a[2]), sqrt(a[3]));
+          const double td = eps_abs + eps_rel * rho * sqrt(a[4]);
+          if (rp <= tp && rd <= td) stop = 1;
+        }
+        if (b == 0) {
+          rp_trace[k] = rp;
+          rd_trace[k] = rd;
+          pcg_it_trace[k] = 0;
+          ctl->eps_next = eps_next;
+          ctl->stop = stop;
+          ctl->k = k + 1;
+        }
+        s_go = (k + 1 < K && !stop) ? 1 : 0;
+        slot = eps_next;
+      }
+    }
+    __syncthreads();
+    eps_next = slot;
+    const int go = s_go;
+    __syncthreads();
+    k += 1;
+    if (!go) {
+      if (b == 0 && threadIdx.x == 0) {
+        ctl->nodes += 1;
+        cudaGraphSetConditional(h_admm, 0u);
+        cudaGraphSetConditional(h_slow, 0u);
+      }
+      return;
+    }
+    // the partials of steps 1 and 3 are rewritten only after the next barrier, which every
+    // block reaches after its reads above
+  }
+  // iteration k goes to the general body
+  if (b == 0 && threadIdx.x == 0) {
+    ctl->nodes += 1;
+    cudaGraphSetConditional(h_slow, 1u);
+  }
+}
+
 
 
 }  // namespace
@@ -888,7 +1063,57 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   cp.conditional.size = 1;
   cudaGraphNode_t n_admm;
   G_OK(cudaGraphAddNode(&n_admm, graph, nullptr, nullptr, 0, &cp));
-  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaGraph_t wbody = cp.conditional.phGraph_out[0];
+  // ADMM iterations that need no PCG step run in one fused cooperative kernel at the top of
+  // the WHILE body; it hands any other iteration to the general body below, which sits in
+  // an IF node (h_slow).  Used for the tracked warm start (hx_refresh > 0) without a refined
+  // step or warm-start model, for a single instance; NYS_ADMM_NOSTEP=0 turns it off.
+  cudaGraph_t body = wbody;
+  {
+    const bool use_model = (g.warm || g.warm_record) && s > 0;
+    const char* env = std::getenv("NYS_ADMM_NOSTEP");
+    bool fast = !g.Aref && !use_model && g.hx_refresh > 0 && g.allow_nostep && !(env && std::atoi(env) == 0);
+    const int nbf = std::max(nb3, nbz);
+    if (fast) {
+      int per_sm = 0, coop = 0;
+      G_OK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, current_device()));
+      G_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, admm_nostep_kernel<C>, kVecThreads, 0));
+      fast = coop && (int64_t)per_sm * sm_count() >= nbf && nbz <= kPart5Max;
+    }
+    if (fast) {
+      cudaGraphConditionalHandle h_slow;
+      G_OK(cudaGraphConditionalHandleCreate(&h_slow, wbody, 0u, 0u));
+      G_OK(cudaStreamBeginCaptureToGraph(cap, wbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)nbf);
+      cfg.blockDim = dim3(kVecThreads);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = cap;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      G_OK(cudaLaunchKernelEx(&cfg, admm_nostep_kernel<C>, d, chunk, nb3, nbz, (const double*)g.q, g.x, g.z, g.u,
+                              (const C*)xc, (const C*)hx, g.rho, g.gamma / g.rho, part_w2, part_r2, part5, ctl, g.tol,
+                              g.tol_floor, g.tol_mode, (const int*)fixed_dev, g.hx_refresh, K, g.eps_abs, g.eps_rel,
+                              g.ztrace, g.rp, g.rd, g.pcg_it, dstat, h_admm, h_slow));
+      cudaStreamCaptureStatus cst0;
+      const cudaGraphNode_t* deps0 = nullptr;
+      size_t ndeps0 = 0;
+      G_OK(cudaStreamGetCaptureInfo(cap, &cst0, nullptr, nullptr, &deps0, nullptr, &ndeps0));
+      std::vector<cudaGraphNode_t> leaf0(deps0, deps0 + ndeps0);
+      G_OK(cudaStreamEndCapture(cap, &wbody));
+      cudaGraphNodeParams sp = {};
+      sp.type = cudaGraphNodeTypeConditional;
+      sp.conditional.handle = h_slow;
+      sp.conditional.type = cudaGraphCondTypeIf;
+      sp.conditional.size = 1;
+      cudaGraphNode_t n_slow;
+      G_OK(cudaGraphAddNode(&n_slow, wbody, leaf0.data(), nullptr, leaf0.size(), &sp));
+      body = sp.conditional.phGraph_out[0];
+    }
+  }
   G_OK(cudaGraphConditionalHandleCreate(&h_pcg, body, 0u, 0u));
   cudaGraphConditionalHandle h_hx;
   G_OK(cudaGraphConditionalHandleCreate(&h_hx, body, 0u, 0u));
@@ -1084,7 +1309,9 @@ nys_status admm_graph_run_many(const GraphLoopArgs* gs, int count, cudaStream_t 
   auto t0 = now();
   if (cudaGraphCreate(&graph, 0) != cudaSuccess) return NYS_ECUDA;
   for (int i = 0; i < count; ++i) {
-    const nys_status s = admm_graph_add<C>(graph, gs[i], stream, pool, &insts[i]);
+    GraphLoopArgs gi = gs[i];
+    if (count > 1) gi.allow_nostep = false;   // branches run concurrently
+    const nys_status s = admm_graph_add<C>(graph, gi, stream, pool, &insts[i]);
     if (s != NYS_OK) return s;
   }
   auto t1 = now();

@@ -131,6 +131,8 @@ struct GraphLoopArgs {
   int* pcg_it = nullptr;     // device, K
   const nys_mlp_s* warm = nullptr;   // learned warm start model, or null
   float* warm_record = nullptr;      // K x (2 s + 3) feature/target rows, or null
+  bool allow_nostep = true;          // fused no-PCG-step iterations (off for graph branches that
+                                     // run concurrently: its grid barrier wants the grid co-resident)
 };
 struct GraphLoopResult {
   int admm_iters = 0;
