@@ -85,6 +85,11 @@ typedef struct {
  * eigenvalue estimates lam (descending) and the shift nu (App. B). */
 typedef struct nys_precond_s* nys_precond;
 
+/* Sum over the ranks of a row-sharded solve, completed in place on buf (device, count
+ * values of dtype NYS_F64 or NYS_F32), ordered on `stream`: the callback either enqueues
+ * the reduction on that stream or synchronises it.  Returns NYS_OK or an error status. */
+typedef int32_t (*nys_allreduce_fn)(void* buf, int64_t count, int32_t dtype, void* stream, void* ctx);
+
 typedef struct {
   double shift_scale;          /* nu = shift_scale * eps(||Y||_2); <= 0 -> sqrt(d) */
   int32_t pcg_tol_mode;        /* nys_tol_mode */
@@ -122,6 +127,19 @@ typedef struct {
   uint64_t seed;               /* Omega == NULL in nys_sketch / nysadmm_solve / nysadmm_solve_path:
                                   the Gaussian test matrix is drawn in the library from this seed
                                   (nys_gaussian_test_matrix); default 0 */
+  nys_allreduce_fn allreduce;  /* row-sharded operation (Table 1's T_mv and the sketch are sums
+                                  over row blocks, A^T D A = sum_g A_g^T D_g A_g): each process
+                                  passes its own contiguous block of rows A_g, b_g; every sum
+                                  over rows -- the sketch A^T D A Omega (one d x s reduction),
+                                  A^T b, each PCG matvec (one d-vector reduction per iteration),
+                                  the refined step's residual -- is completed by this callback;
+                                  all d-space state is replicated and stays identical on every
+                                  rank.  Supported by nys_sketch, pcg_solve and nysadmm_solve
+                                  (lasso / elastic net, device_loop = 0, no warm_model); other
+                                  calls with a callback return NYS_EINVAL.  NULL: unsharded. */
+  void* allreduce_ctx;         /* passed to allreduce */
+  int32_t* pcg_trace;          /* host, admm_maxit, or NULL: PCG iterations of each ADMM
+                                  iteration of nysadmm_solve (lasso / elastic net) */
 } nys_opts;
 
 typedef struct {

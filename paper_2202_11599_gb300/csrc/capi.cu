@@ -144,6 +144,7 @@ nys_status sketch_panel(const nys_matrix* A, const double* D, double shift, cons
   }
   if (sketch_tc_supported(A)) {
     NYS_CU(prep ? sketch_tc_with(A, *prep, D, Om, m, Y, st) : sketch_tc(A, D, Om, m, Y, st));
+    NYS_TRY(shard_sum(Y, d * m, NYS_F64, st));   // row-sharded: sum of the ranks' A_g^T D_g A_g Omega
     if (shift != 0.0) NYS_CU(axpy_panel(shift, Om, Y, d * m, st));
     return NYS_OK;
   }
@@ -162,6 +163,7 @@ nys_status sketch_panel(const nys_matrix* A, const double* D, double shift, cons
     NYS_CU(sketch_aw(A, Om32, m, D, W, st));
     NYS_CU(sketch_atw(A, W, m, Y, work, wbytes, st));
   }
+  NYS_TRY(shard_sum(Y, d * m, NYS_F64, st));   // row-sharded: sum of the ranks' A_g^T D_g A_g Omega
   if (shift != 0.0) NYS_CU(axpy_panel(shift, Om, Y, d * m, st));
   return NYS_OK;
 }
@@ -499,6 +501,7 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
     PhaseTimer pt("q = A^T b", st);
     NYS_TRY(aux_pass(A, MODE_CONST, nullptr, b, nullptr, nullptr, ytmp, nullptr, st));
     NYS_TRY(to_f64(A, ytmp, q, d, st));
+    NYS_TRY(shard_sum(q, d, NYS_F64, st));
   }
 
   PcgProblem pb;
@@ -562,6 +565,7 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
     int total = 0;
     bool capped = false;
     for (int i = 0; i < done_k; ++i) {
+      if (o.pcg_trace) o.pcg_trace[i] = its[i];
       total += its[i];
       const int cap_i = o.pcg_fixed_iters ? o.pcg_fixed_iters[i] : maxit;
       if (!o.pcg_fixed_iters && its[i] >= cap_i) capped = true;
@@ -596,6 +600,7 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
       }
       NYS_TRY(aux_pass(A, MODE_RESID, xa, b, nullptr, nullptr, ytmp, nullptr, st));
       NYS_TRY(to_f64(A, ytmp, yres, d, st));
+      NYS_TRY(shard_sum(yres, d, NYS_F64, st));
       NYS_CU(admm_rhs<C>(d, q, z, u, rho, x, yres, rc, st, mu));
       NYS_CU(cudaMemsetAsync(xc, 0, d * sizeof(C), st));
       prm.x0_zero = true;
@@ -607,6 +612,7 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
     int it = 0;
     nys_status s = pcg_run<C>(pb, view, rc, xc, prm, st, &it, nullptr);
     total_pcg += it;
+    if (o.pcg_trace) o.pcg_trace[k] = it;
     if (s == NYS_ENOCONV) {
       result = NYS_ENOCONV;
     } else if (s != NYS_OK) {
@@ -957,6 +963,7 @@ nys_status logistic_admm(const nys_matrix* A, const nys_matrix* Ain, const doubl
     int it = 0;
     nys_status s = pcg_run<C>(pb, view, rc, xc, prm, st, &it, nullptr);
     total_pcg += it;
+    if (o.pcg_trace) o.pcg_trace[k] = it;
     if (s == NYS_ENOCONV) {
       result = NYS_ENOCONV;
     } else if (s != NYS_OK) {
@@ -1072,6 +1079,9 @@ void nys_opts_default(nys_opts* o) {
   o->warm_model = nullptr;
   o->warm_record = nullptr;
   o->seed = 0;
+  o->allreduce = nullptr;
+  o->allreduce_ctx = nullptr;
+  o->pcg_trace = nullptr;
 }
 
 nys_status nys_gaussian_test_matrix(uint64_t seed, int64_t d, int32_t s, double* Omega, void* stream) {
@@ -1110,6 +1120,7 @@ nys_status nys_sketch(const nys_matrix* A, const double* D, double diag_shift, i
   if (s < 1 || s > A->d || s > kMaxRank || !is_fin(diag_shift) || diag_shift < 0) return NYS_EINVAL;
   cudaStream_t st = stream_of(opts);
   const int64_t d = A->d;
+  ShardScope shard(opts);
   nys_precond_s* P = new (std::nothrow) nys_precond_s();
   if (!P) return NYS_ENOMEM;
   nys_status r;
@@ -1178,6 +1189,7 @@ nys_status pcg_solve(const nys_matrix* A, const double* D, double rho, nys_preco
   // no ADMM iteration here: the schedules of Sec. 5 do not apply
   if (o.pcg_tol_mode < NYS_TOL_REL || o.pcg_tol_mode >= NYS_TOL_RNORM_POW) return NYS_EINVAL;
   cudaStream_t st = stream_of(&o);
+  ShardScope shard(&o);
   PcgProblem pb;
   pb.A = A;
   pb.D = D;
@@ -1219,6 +1231,9 @@ nys_status nysadmm_solve(int32_t loss, const nys_matrix* A, const double* b, dou
   if (o.admm_maxit < 1) return NYS_EINVAL;
   if (o.rank_max > A->d || o.rank_max > kMaxRank) return NYS_EINVAL;
   if (o.pcg_tol_mode < NYS_TOL_REL || o.pcg_tol_mode > NYS_TOL_RNORM_POW) return NYS_EINVAL;
+  // row-sharded solves run the host-driven loop (the device-side graph cannot call back)
+  if (o.allreduce && (loss == NYS_LOGISTIC || o.device_loop || o.warm_model || o.warm_record)) return NYS_EINVAL;
+  ShardScope shard(&o);
   const nys_matrix* Ain = o.A_inner ? o.A_inner : A;
   if (o.A_inner) {
     NYS_TRY(check_matrix(Ain));
@@ -1248,6 +1263,7 @@ nys_status nysadmm_solve_path(const nys_matrix* A, const double* b, const double
   if (opts) o = *opts;
   else nys_opts_default(&o);
   if (o.pcg_tol_mode < NYS_TOL_REL || o.pcg_tol_mode > NYS_TOL_RNORM_POW) return NYS_EINVAL;
+  if (o.allreduce) return NYS_EINVAL;   // the path is not row-sharded
   const nys_matrix* Ain = o.A_inner ? o.A_inner : A;
   if (o.A_inner) {
     NYS_TRY(check_matrix(Ain));
@@ -1276,6 +1292,7 @@ nys_status nysadmm_solve_batch(int32_t count, const nys_lasso_instance* inst, do
   nys_opts o;
   if (opts) o = *opts;
   else nys_opts_default(&o);
+  if (o.allreduce) return NYS_EINVAL;   // independent instances are not row-sharded
   if (o.admm_maxit < 1) return NYS_EINVAL;
   if (o.pcg_tol_mode < NYS_TOL_REL || o.pcg_tol_mode > NYS_TOL_RNORM_POW) return NYS_EINVAL;
   cudaStream_t st = stream_of(&o);

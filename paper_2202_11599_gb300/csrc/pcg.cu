@@ -284,6 +284,43 @@ __global__ void __launch_bounds__(kVecThreads) pcg_tail_kernel(int64_t d, const 
   }
 }
 
+// Row-sharded matvec, after the sum over ranks of the local A_g^T D_g A_g p (in v):
+// v = rho p + v and the per-block partials of p^T v, with the loop and order of
+// apass_reduce_kernel (so an unsharded run and a one-rank sharded run agree bitwise).
+template <typename C>
+__global__ void __launch_bounds__(kVecThreads) shard_finish_kernel(int64_t d, C rho, const C* __restrict__ p,
+                                                                   C* __restrict__ v, double* dot_part, const int* skip) {
+  if (skip && *skip) return;
+  __shared__ double sh[kVecThreads / 32];
+  double dacc = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x) {
+    const C pj = p ? p[j] : C(0);
+    const C yj = fma(rho, pj, v[j]);
+    v[j] = yj;
+    dacc += (double)pj * (double)yj;
+  }
+  if (dot_part) {
+    const double t = block_sum<kVecThreads>(dacc, sh);
+    if (threadIdx.x == 0) dot_part[blockIdx.x] = t;
+  }
+}
+
+// v = (A^T D A + rho I) p with the row sum completed over the ranks of a sharded solve.
+template <typename C>
+static cudaError_t sharded_reduce(const ApassArgs& aa, const ApassPlan& plan, const void* apart, double rho, C* v,
+                                  double* dot_part, int nblk, cudaStream_t stream, nys_status* comm_status) {
+  NYS_CUDA_TRY(apass_reduce(aa, plan, apart, 0.0, v, nullptr, 0, stream));  // local sum, no shift
+  const nys_status cs = shard_sum(v, aa.d, sizeof(C) == 8 ? NYS_F64 : NYS_F32, stream);
+  if (cs != NYS_OK) {
+    *comm_status = cs;
+    return cudaErrorUnknown;
+  }
+  count_launch();
+  shard_finish_kernel<C><<<nblk, kVecThreads, 0, stream>>>(aa.d, (C)rho, reinterpret_cast<const C*>(aa.p), v, dot_part,
+                                                             aa.skip);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ host driver
 
 static int upd_chunk(int64_t d) {
@@ -350,11 +387,26 @@ nys_status pcg_run(const PcgProblem& pb, const PrecondView& P, const C* r, C* x,
   count_launch();
   pcg_reset_kernel<<<1, 1, 0, stream>>>(st, prm.tol, prm.tol_abs, prm.maxit, prm.fixed, prm.dev_tol);
   LAUNCH_OK(cudaGetLastError());
+  const bool sharded = shard_comm().fn != nullptr;
+  nys_status comm_status = NYS_OK;
+#define MATVEC_REDUCE(rho_, dots_, nd_)                                                                  \
+  do {                                                                                                  \
+    if (sharded) {                                                                                      \
+      e = sharded_reduce<C>(aa, pb.plan, apart, (rho_), v, (dots_), nbr, stream, &comm_status);          \
+      if (comm_status != NYS_OK) return comm_status;                                                    \
+      if (e != cudaSuccess) return NYS_ECUDA;                                                           \
+    } else {                                                                                            \
+      LAUNCH_OK(apass_reduce(aa, pb.plan, apart, (rho_), v, (dots_), (nd_), stream));                  \
+    }                                                                                                   \
+  } while (0)
   const C* v0 = nullptr;
   if (!prm.x0_zero) {
     aa.p = x;
+    const int* skip0 = aa.skip;
+    aa.skip = nullptr;
     LAUNCH_OK(apass_run(aa, pb.plan, apart, nullptr, dstat, stream));
-    LAUNCH_OK(apass_reduce(aa, pb.plan, apart, pb.rho, v, nullptr, 0, stream));
+    MATVEC_REDUCE(pb.rho, nullptr, 0);
+    aa.skip = skip0;
     v0 = v;
   }
   count_launch();
@@ -375,7 +427,7 @@ nys_status pcg_run(const PcgProblem& pb, const PrecondView& P, const C* r, C* x,
     for (int c = 0; c < chunk_it && launched < cap; ++c, ++launched) {
       aa.p = p;
       LAUNCH_OK(apass_run(aa, pb.plan, apart, nullptr, dstat, stream));
-      LAUNCH_OK(apass_reduce(aa, pb.plan, apart, pb.rho, v, pv_part, nbr, stream));
+      MATVEC_REDUCE(pb.rho, pv_part, nbr);
       count_launch();
       pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, stream>>>(0, d, chunk, x, w, r, v, p, U, s, pv_part, nbr,
                                                                  wy_part, nb5, part_w2, part_r2, part_g, st, (C*)nullptr,
@@ -395,6 +447,7 @@ nys_status pcg_run(const PcgProblem& pb, const PrecondView& P, const C* r, C* x,
   LAUNCH_OK(cudaMemcpyAsync(&dstat_h, dstat, sizeof(int), cudaMemcpyDeviceToHost, stream));
   LAUNCH_OK(cudaStreamSynchronize(stream));
 #undef LAUNCH_OK
+#undef MATVEC_REDUCE
   if (iters_out) *iters_out = hs->iters;
   if (resnorm_out) *resnorm_out = std::sqrt(hs->w2);
   if (dstat_h) return (nys_status)dstat_h;

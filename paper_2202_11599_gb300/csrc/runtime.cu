@@ -10,6 +10,7 @@
 #include <utility>
 
 #include "nys_internal.cuh"
+#include "solver.cuh"
 
 namespace nys {
 namespace {
@@ -55,5 +56,22 @@ cudaStream_t capture_stream() {
     streams[dev] = nullptr;
   return streams[dev];
 }
+
+ShardComm& shard_comm() {
+  static thread_local ShardComm c;
+  return c;
+}
+
+nys_status shard_sum(void* buf, int64_t count, int dtype, cudaStream_t st) {
+  const ShardComm& c = shard_comm();
+  if (!c.fn || count <= 0) return NYS_OK;
+  return (nys_status)c.fn(buf, count, dtype, reinterpret_cast<void*>(st), c.ctx);
+}
+
+ShardScope::ShardScope(const nys_opts* o) : saved(shard_comm()) {
+  shard_comm().fn = o ? o->allreduce : nullptr;
+  shard_comm().ctx = o ? o->allreduce_ctx : nullptr;
+}
+ShardScope::~ShardScope() { shard_comm() = saved; }
 
 }  // namespace nys

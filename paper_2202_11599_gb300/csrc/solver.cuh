@@ -50,6 +50,20 @@ class Pool {
   bool ok_ = true;
 };
 
+// Row-sharded operation: the communicator of the calling thread's current entry point
+// (set from nys_opts for the duration of the call).  shard_sum is a no-op without one.
+struct ShardComm {
+  nys_allreduce_fn fn = nullptr;
+  void* ctx = nullptr;
+};
+ShardComm& shard_comm();
+nys_status shard_sum(void* buf, int64_t count, int dtype, cudaStream_t st);
+struct ShardScope {
+  explicit ShardScope(const nys_opts* o);
+  ~ShardScope();
+  ShardComm saved;
+};
+
 struct PcgProblem {
   const nys_matrix* A;
   const double* D;    // NULL: H = A^T A

@@ -39,7 +39,8 @@ class NysOptsC(ctypes.Structure):
                 ("refine", c_int32), ("z_trace", c_void_p), ("rank_max", c_int32),
                 ("ada_tol", c_double), ("resketch_every", c_int32), ("stream", c_void_p),
                 ("device_loop", c_int32), ("hx_refresh", c_int32), ("warm_model", c_void_p),
-                ("warm_record", c_void_p), ("seed", ctypes.c_uint64)]
+                ("warm_record", c_void_p), ("seed", ctypes.c_uint64), ("allreduce", c_void_p),
+                ("allreduce_ctx", c_void_p), ("pcg_trace", POINTER(c_int32))]
 
 
 class NysInfoC(ctypes.Structure):
@@ -57,6 +58,52 @@ class NysStatsC(ctypes.Structure):
 class NysInstanceC(ctypes.Structure):
     _fields_ = [("A", POINTER(NysMatrixC)), ("b", c_void_p), ("gamma", c_double), ("rank", c_int32),
                 ("Omega", c_void_p), ("x_out", c_void_p), ("z_out", c_void_p)]
+
+
+_ALLREDUCE_FN = ctypes.CFUNCTYPE(c_int32, c_void_p, c_int64, c_int32, c_void_p, c_void_p)
+
+
+class _DeviceView:
+    """Zero-copy view of a library-owned device buffer for torch (CUDA array interface)."""
+
+    def __init__(self, ptr: int, count: int, dtype: int):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": (int(count),),
+                                         "typestr": "<f8" if dtype == NYS_F64 else "<f4", "strides": None,
+                                         "version": 2}
+
+
+def _allreduce_callback(fn):
+    """Wrap fn(tensor) -- an in-place sum over the ranks -- as the library's nys_allreduce_fn.
+    The tensor views the library's buffer; fn runs with the library's stream current."""
+    def cb(buf, count, dtype, stream, ctx):
+        try:
+            t = torch.as_tensor(_DeviceView(buf, count, dtype), device="cuda")
+            s = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+            with torch.cuda.stream(s):
+                fn(t)
+            return NYS_OK
+        except Exception:  # noqa: BLE001 -- reported to the library as a status, never raised through C
+            return NYS_ECUDA
+    return _ALLREDUCE_FN(cb)
+
+
+def row_block(n: int, world: int, rank: int) -> tuple[int, int]:
+    """Contiguous block of rows [r0, r1) of rank `rank` in a row-sharded solve (sizes differ by
+    at most one row; the blocks cover 0..n-1 once, in rank order)."""
+    if not (0 <= rank < world) or n < world:
+        raise ValueError("need 0 <= rank < world <= n")
+    return n * rank // world, n * (rank + 1) // world
+
+
+def host_staged_allreduce(dist, group=None):
+    """An allreduce for row-sharded solves over any torch.distributed backend (gloo included):
+    the device buffer is copied to the host, summed over the ranks, and copied back on the
+    library's stream."""
+    def fn(t):
+        c = t.cpu()
+        dist.all_reduce(c, group=group)
+        t.copy_(c)
+    return fn
 
 
 class NysError(RuntimeError):
@@ -295,7 +342,8 @@ def gaussian_test_matrix(seed: int, d: int, s: int, stream=None) -> torch.Tensor
 
 
 def sketch(A: Matrix, Omega: torch.Tensor | None, D: torch.Tensor | None = None, diag_shift: float = 0.0,
-           shift_scale: float | None = None, stream=None, s: int | None = None, seed: int = 0) -> Precond:
+           shift_scale: float | None = None, stream=None, s: int | None = None, seed: int = 0,
+           allreduce=None) -> Precond:
     """Nystrom sketch of H = A^T diag(D) A + diag_shift I from the Gaussian Omega (d x s), or,
     with Omega None, from s columns drawn in the library from `seed`."""
     if Omega is None:
@@ -304,7 +352,9 @@ def sketch(A: Matrix, Omega: torch.Tensor | None, D: torch.Tensor | None = None,
         s = Omega.shape[1]
         Om = Omega.to(torch.float64).T.contiguous()                    # column-major d x s
     h = c_void_p()
-    o = _opts(stream, shift_scale=shift_scale, seed=int(seed) & (2**64 - 1))
+    cb = _allreduce_callback(allreduce) if allreduce is not None else None
+    o = _opts(stream, shift_scale=shift_scale, seed=int(seed) & (2**64 - 1),
+              allreduce=ctypes.cast(cb, c_void_p) if cb is not None else None)
     _check(lib().nys_sketch(ctypes.byref(A.c), _ptr(D), float(diag_shift), int(s), _ptr(Om), ctypes.byref(o),
                             ctypes.byref(h)), "nys_sketch")
     return Precond(h.value)
@@ -312,14 +362,16 @@ def sketch(A: Matrix, Omega: torch.Tensor | None, D: torch.Tensor | None = None,
 
 def pcg_solve(A: Matrix, r: torch.Tensor, rho: float, P: Precond | None = None, x0=None, tol: float = 1e-8,
               tol_mode: str = "rel", maxit: int | None = None, fixed_iters: int | None = None,
-              D: torch.Tensor | None = None, stream=None, allow_noconv: bool = False):
+              D: torch.Tensor | None = None, stream=None, allow_noconv: bool = False, allreduce=None):
     """Nystrom PCG (App. B) for (A^T diag(D) A + rho I) x = r.  Returns (x, iters, ||w||)."""
     ct = A.compute_dtype
     r = r.to(ct).contiguous()
     x = torch.zeros(A.d, dtype=ct, device=r.device) if x0 is None else x0.to(ct).clone().contiguous()
     fixed = (c_int32 * 1)(fixed_iters) if fixed_iters is not None else None
+    cb = _allreduce_callback(allreduce) if allreduce is not None else None
     o = _opts(stream, pcg_tol_mode=TOL_MODES[tol_mode], pcg_maxit=maxit or 0,
-              pcg_fixed_iters=ctypes.cast(fixed, POINTER(c_int32)) if fixed is not None else None)
+              pcg_fixed_iters=ctypes.cast(fixed, POINTER(c_int32)) if fixed is not None else None,
+              allreduce=ctypes.cast(cb, c_void_p) if cb is not None else None)
     it = c_int32()
     rn = c_double()
     st = lib().pcg_solve(ctypes.byref(A.c), _ptr(D), float(rho), P.h if P is not None else None, _ptr(r),
@@ -335,10 +387,12 @@ def nysadmm_solve(loss: str, A: Matrix, b: torch.Tensor, gamma: float, rho: floa
                   rank_max: int | None = None, ada_tol: float | None = None, resketch_every: int = 1,
                   shift_scale: float | None = None, stream=None, allow_noconv: bool = True,
                   device_loop: bool = True, hx_refresh: int = 0, warm_model=None,
-                  warm_record: bool = False, seed: int = 0) -> dict:
+                  warm_record: bool = False, seed: int = 0, pcg_trace: bool = False, allreduce=None) -> dict:
     """NysADMM (Alg. NysADMM / AdaNysADMM) through the C ABI.  Returns a dict with
-    x, z (FP64 device tensors), info (dict) and, when requested, the z trace.
-    Omega None: the test matrix is drawn in the library from `seed`."""
+    x, z (FP64 device tensors), info (dict) and, when requested, the z trace and the PCG
+    iterations of each ADMM iteration.  Omega None: the test matrix is drawn in the library
+    from `seed`.  allreduce: fn(tensor) summing a device tensor over the ranks in place, for a
+    row-sharded solve (A, b: this rank's rows; host-driven loop)."""
     d = A.d
     Om = None if Omega is None else Omega.to(torch.float64).T.contiguous()   # column-major d x s
     x = torch.empty(d, dtype=torch.float64, device="cuda")
@@ -349,8 +403,14 @@ def nysadmm_solve(loss: str, A: Matrix, b: torch.Tensor, gamma: float, rho: floa
     if pcg_fixed is not None:
         seq = [int(pcg_fixed)] * admm_iters if isinstance(pcg_fixed, int) else [int(v) for v in pcg_fixed]
         fixed = (c_int32 * len(seq))(*seq)
+    ptrace = (c_int32 * admm_iters)() if pcg_trace else None
+    cb = _allreduce_callback(allreduce) if allreduce is not None else None
+    if cb is not None:
+        device_loop = False
     o = _opts(stream, shift_scale=shift_scale, pcg_tol_mode=TOL_MODES[tol_mode], pcg_maxit=pcg_maxit or 0,
               pcg_fixed_iters=ctypes.cast(fixed, POINTER(c_int32)) if fixed is not None else None,
+              pcg_trace=ctypes.cast(ptrace, POINTER(c_int32)) if ptrace is not None else None,
+              allreduce=ctypes.cast(cb, c_void_p) if cb is not None else None,
               admm_maxit=admm_iters, eps_abs=eps_abs, eps_rel=eps_rel,
               A_inner=ctypes.pointer(A_inner.c) if A_inner is not None else None,
               refine=int(bool(refine)), z_trace=c_void_p(zt.data_ptr()) if zt is not None else None,
@@ -371,6 +431,8 @@ def nysadmm_solve(loss: str, A: Matrix, b: torch.Tensor, gamma: float, rho: floa
         out["z_trace"] = zt[: inf["admm_iters"]]
     if rec is not None:
         out["warm_record"] = rec[: inf["admm_iters"]]
+    if ptrace is not None:
+        out["pcg_trace"] = list(ptrace)[: inf["admm_iters"]]
     return out
 
 

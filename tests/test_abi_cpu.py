@@ -51,7 +51,7 @@ def test_struct_layouts_match_header(libpath):
     assert ctypes.sizeof(nx.NysMatrixC) == 48
     assert nx.NysOptsC.stream.offset == 96 and nx.NysOptsC.hx_refresh.offset == 108
     assert nx.NysOptsC.seed.offset == 128
-    assert ctypes.sizeof(nx.NysOptsC) == 136
+    assert ctypes.sizeof(nx.NysOptsC) == 160
     assert ctypes.sizeof(nx.NysInfoC) == 48
     assert ctypes.sizeof(nx.NysStatsC) == 8 + 4 * 8 * 6
 
