@@ -100,14 +100,16 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- workload
 
-def make_workload(device="cuda"):
+def make_workload(device="cuda", seed=1):
+    """The benchmark lasso; seed 1 is the workload of the main line, other seeds give held-out
+    instances of the same recipe (the Gaussian test matrix uses seed + 10)."""
     n, d, s = 100_000, 10_000, 200
-    W = gen.lasso_large_torch(n, d, nnz_frac=0.01, noise=1e-3, gamma_frac=0.05, seed=1, device=device)
-    g = torch.Generator(device=device).manual_seed(11)
+    W = gen.lasso_large_torch(n, d, nnz_frac=0.01, noise=1e-3, gamma_frac=0.05, seed=seed, device=device)
+    g = torch.Generator(device=device).manual_seed(10 + seed)
     Om = torch.randn(d, s, generator=g, device=device, dtype=torch.float64)
     # rho_extra: the rho of the secondary lines (--extra fp8 / elastic_net)
     return {"n": n, "d": d, "s": s, "rho": 70.0, "rho_extra": 100.0, "pcg_tol": 1e-4, "pcg_beta": 1.75,
-            "pcg_tol_fp64": 1e-8,
+            "pcg_tol_fp64": 1e-8, "seed": seed,
             "A32": W["A32"], "b": W["b"], "gamma": W["gamma"], "Omega": Om}
 
 
@@ -122,7 +124,7 @@ def workload_config(w):
                     if w["pcg_mode"] == "rnorm_pow"
                     else f"f32, tol mode {w['pcg_mode']} (first solve rel-tol {w['pcg_tol']:g}), warm start x_prev"),
             "loop": "device-side (one CUDA graph per solve)",
-            "decay": "(1+j)^-1, rotated", "x_star": "1% sparse", "noise": 1e-3, "seed": 1,
+            "decay": "(1+j)^-1, rotated", "x_star": "1% sparse", "noise": 1e-3, "seed": w.get("seed", 1),
             "gap": GAP, "l2_flush": "inputs (10 GB) larger than L2 (129 MB)"}
 
 
@@ -163,7 +165,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    w = make_workload()
+    w = make_workload(seed=args.seed)
     if args.rho is not None:
         w["rho"] = args.rho
     A64 = w["A32"].double()
@@ -453,7 +455,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = make_workload("cuda" if torch.cuda.is_available() else "cpu")
+    w = make_workload("cuda" if torch.cuda.is_available() else "cpu", seed=args.seed)
     apply_pcg_args(w, args)
     if args.rho is not None:
         w["rho"] = args.rho
@@ -767,6 +769,146 @@ def extra_logistic(args):
                       "emp_cond": out["info"]["emp_cond"]}), flush=True)
 
 
+def extra_learned(args):
+    """Learned warm start on the stream-of-instances workload (separate JSON line): a fixed
+    40,000 x 4,000 FP64 matrix A = G diag((1+j)^-1) shared by 1,000 lasso instances, each with
+    a fresh 1%-sparse x* and b = A x* + 1e-3 noise, gamma = 0.05 ||A^T b||_inf, rho = 1,
+    rank 100 (one sketch of A^T A serves every instance), FP64 PCG at rel-tol 1e-8, K ADMM
+    iterations per instance.  The MLP (rank + 3 -> 256 -> 256 -> rank, erf-GELU, BF16 weights
+    with FP32 accumulation) is trained with the library's own kernels on the (feature, target)
+    pairs the device loop records on instances 0..199, then instances 200..999 are solved with
+    the plain x_prev start and with the learned start; the line reports PCG iterations and
+    solve time of both and their difference (learned minus plain)."""
+    from paper_2202_11599_gb300 import nysadmm as nx
+    import __graft_entry__
+    __graft_entry__.build()
+    n, d, s, count, n_train = 40_000, 4_000, 100, args.learned_instances, args.learned_instances // 5
+    K, rho, tol = args.learned_iters, 1.0, 1e-8
+    g = torch.Generator(device="cuda").manual_seed(5)
+    A = torch.randn(n, d, generator=g, device="cuda", dtype=torch.float64)
+    A *= ((1.0 + torch.arange(d, device="cuda", dtype=torch.float64)) ** -1.0)[None, :]
+    M = nx.Matrix(A)
+    Om = torch.randn(d, s, generator=g, device="cuda", dtype=torch.float64)
+    insts = []
+    for i in range(count):
+        xs = torch.zeros(d, device="cuda", dtype=torch.float64)
+        idx = torch.randperm(d, generator=g, device="cuda")[: d // 100]
+        xs[idx] = torch.randn(idx.numel(), generator=g, device="cuda", dtype=torch.float64)
+        b = A @ xs + 1e-3 * torch.randn(n, generator=g, device="cuda", dtype=torch.float64)
+        insts.append((b, 0.05 * float((A.T @ b).abs().max())))
+
+    def solve(i, model=None, record=False):
+        b, gamma = insts[i]
+        return nx.nysadmm_solve("lasso", M, b, gamma, rho, s, tol, Om, admm_iters=K, warm_model=model,
+                                warm_record=record)
+
+    t0 = time.perf_counter()
+    rows = [solve(i, record=True)["warm_record"] for i in range(n_train)]
+    R = torch.cat(rows)
+    X, T = R[:, : s + 3].contiguous(), R[:, s + 3:].contiguous()
+    t_record = time.perf_counter() - t0
+    # He-style uniform initialisation drawn on the host (seeded)
+    rng = np.random.default_rng(55)
+    parts = []
+    for fo, fi in [(256, s + 3), (256, None), (256, 256), (256, None), (s, 256), (s, None)]:
+        parts.append(np.zeros(fo) if fi is None else rng.uniform(-1, 1, (fo, fi)).ravel() * np.sqrt(6.0 / (fi + fo)))
+    model = nx.MLP(s + 3, 256, s, np.concatenate(parts).astype(np.float32))
+    t0 = time.perf_counter()
+    perm_g = torch.Generator(device="cuda").manual_seed(56)
+    losses = []
+    for ep in range(args.learned_epochs):
+        perm = torch.randperm(X.shape[0], generator=perm_g, device="cuda")
+        for j in range(0, X.shape[0], 256):
+            sel = perm[j:j + 256]
+            losses.append(model.train_step(X[sel].contiguous(), T[sel].contiguous(), lr=1e-3))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    res = {"plain": {"pcg_iters": 0, "time_s": 0.0}, "learned": {"pcg_iters": 0, "time_s": 0.0}}
+    max_dz = 0.0
+    solve(n_train)
+    solve(n_train, model)
+    torch.cuda.synchronize()
+    for i in range(n_train, count):
+        outs = {}
+        for name, mdl in (("plain", None), ("learned", model)):
+            a = torch.cuda.Event(enable_timing=True)
+            c = torch.cuda.Event(enable_timing=True)
+            a.record()
+            out = solve(i, mdl)
+            c.record()
+            torch.cuda.synchronize()
+            res[name]["pcg_iters"] += out["info"]["pcg_iters_total"]
+            res[name]["time_s"] += a.elapsed_time(c) / 1e3
+            outs[name] = out["z"]
+        max_dz = max(max_dz, float((outs["learned"] - outs["plain"]).norm() / max(outs["plain"].norm(), 1e-30)))
+    for r in res.values():
+        r["time_s"] = round(r["time_s"], 3)
+    print(json.dumps({"extra": "learned", "workload": f"lasso_stream_{n}x{d}_f64", "instances": count,
+                      "train_instances": n_train, "admm_iters_per_instance": K, "rank": s, "rho": rho,
+                      "pcg": f"f64, rel-tol {tol:g}", "pairs": int(X.shape[0]), "epochs": args.learned_epochs,
+                      "loss_first": losses[0], "loss_last": losses[-1], "record_s": round(t_record, 2),
+                      "train_s": round(t_train, 2), "plain": res["plain"], "learned": res["learned"],
+                      "learned_minus_plain": {"pcg_iters": res["learned"]["pcg_iters"] - res["plain"]["pcg_iters"],
+                                              "time_s": round(res["learned"]["time_s"] - res["plain"]["time_s"], 3)},
+                      "max_rel_dz_learned_vs_plain": max_dz}), flush=True)
+
+
+def extra_small(args):
+    """The 2,000 x 500 FP64 lasso of the small configuration (A = G diag((1+j)^-1), 25 nonzeros,
+    b = A x* + 0.01 noise, gamma = 0.1 ||A^T b||_inf, rho = 1, rank 50, PCG rel-tol 1e-8), the
+    latency-bound plain form (separate JSON line): time to a 1e-6 relative objective gap on the
+    GPU (device-side loop, one graph launch) and, at this size, the FP64 oracle's whole solve on
+    the host cores (not extrapolated).  F* is the oracle's value after 3,000 iterations at
+    PCG rel-tol 1e-12, certified by its duality gap."""
+    from paper_2202_11599_gb300 import nysadmm as nx
+    import oracle.nysadmm_oracle as o
+    import __graft_entry__
+    __graft_entry__.build()
+    p = gen.lasso_small(0)
+    Om = gen.gaussian_test_matrix(500, 50, 0)
+    ref = o.lasso_nysadmm(p.A, p.b, p.gamma, p.rho, Om, 3000, pcg_tol=1e-12)
+    Fstar = o.lasso_objective(p.A, p.b, p.gamma, ref["z"])
+    gap_star = o.lasso_dual_gap(p.A, p.b, p.gamma, ref["z"])
+    M = nx.Matrix.padded(torch.from_numpy(p.A).cuda())
+    b = torch.from_numpy(p.b).cuda()
+    Omd = torch.from_numpy(Om).cuda()
+    lines = {}
+    for name, kw in (("rel_tol_1e-8", dict(tol=1e-8, tol_mode="rel", hx_refresh=0)),
+                     ("rnorm_pow_2", dict(tol=2.0, tol_mode="rnorm_pow", hx_refresh=20))):
+        cal = nx.nysadmm_solve("lasso", M, b, p.gamma, p.rho, 50, kw["tol"], Omd, admm_iters=3000, z_trace=True,
+                               tol_mode=kw["tol_mode"], hx_refresh=kw["hx_refresh"])
+        zt = cal["z_trace"].cpu().numpy()
+        k = next((k for k in range(zt.shape[0])
+                  if (o.lasso_objective(p.A, p.b, p.gamma, zt[k]) - Fstar) / Fstar <= GAP), None)
+        if k is None:
+            lines[name] = {"admm_iters_to_gap": None}
+            continue
+        iters = k + 1
+        for _ in range(max(3, args.warmup)):
+            nx.nysadmm_solve("lasso", M, b, p.gamma, p.rho, 50, kw["tol"], Omd, admm_iters=iters,
+                             tol_mode=kw["tol_mode"], hx_refresh=kw["hx_refresh"])
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(max(5, args.steps)):
+            a = torch.cuda.Event(enable_timing=True)
+            c = torch.cuda.Event(enable_timing=True)
+            a.record()
+            out = nx.nysadmm_solve("lasso", M, b, p.gamma, p.rho, 50, kw["tol"], Omd, admm_iters=iters,
+                                   tol_mode=kw["tol_mode"], hx_refresh=kw["hx_refresh"])
+            c.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(c) / 1e3)
+        t0 = time.perf_counter()
+        o.lasso_nysadmm(p.A, p.b, p.gamma, p.rho, Om, iters, pcg_tol=kw["tol"], pcg_tol_mode=kw["tol_mode"])
+        t_cpu = time.perf_counter() - t0
+        lines[name] = {"admm_iters_to_gap": iters, "pcg_iters": out["info"]["pcg_iters_total"],
+                       "gpu_s": round(statistics.median(ts), 5), "oracle_s": round(t_cpu, 3),
+                       "oracle_cores": len(os.sched_getaffinity(0)),
+                       "gpu_us_per_admm_iter": round(1e6 * statistics.median(ts) / iters, 1)}
+    print(json.dumps({"extra": "small", "workload": "lasso_2000x500_f64", "F_star": Fstar,
+                      "F_star_dual_gap": gap_star, "gap": GAP, "rho": p.rho, "rank": 50, "lines": lines}), flush=True)
+
+
 def profile_sketch():
     """Small ncu case: the tensor-core sketch Y = A^T A Omega (rank 200) of a 50000 x 10000
     BF16 matrix (1 GB): one warm-up sketch, then one more."""
@@ -846,7 +988,11 @@ def main():
                     help="only run the tensor-core sketch on a 50000 x 10000 BF16 matrix (ncu capture case)")
     ap.add_argument("--host-loop", action="store_true",
                     help="run the ADMM loop from the host (kernel launches that ncu can list one by one)")
-    ap.add_argument("--extra", choices=["batched", "logistic", "fp8", "elastic_net"], default=None,
+    ap.add_argument("--learned-instances", type=int, default=1000)
+    ap.add_argument("--learned-iters", type=int, default=20)
+    ap.add_argument("--learned-epochs", type=int, default=50)
+    ap.add_argument("--seed", type=int, default=1, help="workload seed (1 = the main line's; others: held out)")
+    ap.add_argument("--extra", choices=["batched", "logistic", "fp8", "elastic_net", "learned", "small"], default=None,
                     help="run a secondary workload and print its own JSON line")
     ap.add_argument("--extra-iters", type=int, default=100)
     ap.add_argument("--no-plain", action="store_true")
@@ -863,6 +1009,10 @@ def main():
         extra_logistic(args)
     elif args.extra == "elastic_net":
         extra_elastic_net(args)
+    elif args.extra == "learned":
+        extra_learned(args)
+    elif args.extra == "small":
+        extra_small(args)
     elif args.profile_apass:
         profile_apass(args.profile_apass)
     elif args.profile_sketch:

@@ -669,7 +669,8 @@ struct AdmmCtl {
   unsigned int ticket;  // last-block election of the fused zu / scalar kernel
   long long nodes;  // kernel launches executed (instrumentation)
   double eps_next;  // sqrt(r_p r_d) of the last iteration
-  unsigned int bar_count, bar_gen;  // grid barrier of the fused no-step kernel
+  unsigned int bar_count, bar_gen;  // grid barrier of admm_head_kernel
+  int hx_pending;   // admm_head_kernel asked for the (H + rho I) x recompute of iteration k
 };
 
 namespace {
@@ -818,89 +819,205 @@ __global__ void __launch_bounds__(kVecThreads) admm_zu_g_kernel(int64_t d, const
 }
 
 
-// Fused ADMM iterations whose x-subproblem needs no PCG step (the warm start already meets
-// the iteration's PCG tolerance, or the replayed count is 0), the common case late in a
-// solve under the decaying schedules.  One cooperative launch runs such iterations back to
-// back with two grid barriers each, instead of the begin / right-hand side / PCG-init /
-// P^{-1} / prox-dual launches and conditional nodes of the general body:
-//   1. r = q + rho (z - u), w = r - (H + rho I) x (tracked), partial ||w||^2, ||r||^2
-//      (blocks and thread mapping of pcg_update_kernel's init step);
+// Head of the device loop's ADMM iteration, one cooperative launch (tracked warm start,
+// no refined step or warm-start model).  It replaces the begin / right-hand side / PCG-init
+// (P^{-1} w) launches of the general body, and it runs the iterations whose x-subproblem
+// needs no PCG step -- the common case under the decaying schedules of Sec. 5, where the
+// tracked warm start often already meets the iteration's tolerance -- back to back:
+//   1. r = q + rho (z - u), w = r - (H + rho I) x (tracked), partial ||w||^2, ||r||^2 and
+//      U^T w (blocks, thread mapping and order of pcg_update_kernel's init step);
 //   2. every block sums the partials in the order of pcg_scalar_body and takes the same stop
-//      decision; if PCG would step (or (H + rho I) x is due for a recompute) the kernel
-//      hands iteration k to the general body (h_slow = 1) and returns;
-//   3. otherwise x is unchanged: z = S_kappa(x + u), u += x - z and the residual partials
-//      (blocks of admm_zu_g_kernel), then every block forms r_p, r_d, the stop test and the
-//      next tolerance as admm_scalar_g_body does; block 0 records them.
-// The arithmetic and its order are those of the general body, so iterates are bitwise
-// those of a solve without this kernel.  The barrier waits are bounded (NYS_ETIMEOUT).
+//      decision;
+//   3a. no step: x stays; z = S_kappa(x + u), u += x - z and the residual partials (blocks of
+//      admm_zu_g_kernel); every block forms r_p, r_d, the stop test and the next tolerance as
+//      admm_scalar_g_body does (block 0 records them) and goes on with iteration k + 1;
+//   3b. a step: g = c o U^T w (order of pcg_scalar_body), y = w + U g, p = y and the partials
+//      of w^T y (blocks and order of pcg_tail_kernel), the PCG state as the begin and init
+//      kernels leave it; the PCG WHILE node and the prox/dual kernel finish iteration k.
+// When (H + rho I) x is due for a recompute at iteration k the kernel requests it (IF node
+// before it) and returns; the next launch continues at k.  The arithmetic and its order are
+// those of the general body, so the iterates are bitwise those of a solve without this
+// kernel.  Grid barriers are bounded (NYS_ETIMEOUT).
+struct HeadArgs {
+  int64_t d;
+  int chunk, nb3, nbz, nb5, s;
+  const double* q;
+  double *x, *z, *u;
+  double rho, kappa;
+  double *part_w2, *part_r2, *part_g, *wy_part, *part5;
+  AdmmCtl* ctl;
+  PcgState* st;
+  double tol, tol_floor;
+  int tol_mode, maxit, hx_refresh, K;
+  const int* fixed_dev;
+  double eps_abs, eps_rel;
+  double *ztrace, *rp_trace, *rd_trace;
+  int* pcg_it_trace;
+  int* dstat;
+  cudaGraphConditionalHandle h_admm, h_pcg, h_zu, h_hx;
+};
+
 template <typename C>
-__global__ void __launch_bounds__(kVecThreads) admm_nostep_kernel(
-    int64_t d, int chunk, int nb3, int nbz, const double* __restrict__ q, double* __restrict__ x,
-    double* __restrict__ z, double* __restrict__ u, const C* __restrict__ xc, const C* __restrict__ hx, double rho,
-    double kappa, double* part_w2, double* part_r2, double* part5, AdmmCtl* ctl, double tol, double tol_floor,
-    int tol_mode, const int* __restrict__ fixed_dev, int hx_refresh, int K, double eps_abs, double eps_rel,
-    double* ztrace, double* rp_trace, double* rd_trace, int* pcg_it_trace, int* dstat,
-    cudaGraphConditionalHandle h_admm, cudaGraphConditionalHandle h_slow) {
+__global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, const C* __restrict__ xc,
+                                                                const C* __restrict__ hx, C* __restrict__ w,
+                                                                C* __restrict__ rc, C* __restrict__ y,
+                                                                C* __restrict__ p, const C* __restrict__ U,
+                                                                const C* __restrict__ cvec, C* __restrict__ gs) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* wch = reinterpret_cast<C*>(sm_raw);   // chunk of w (U^T w), then g (y = w + U g)
   __shared__ double sh[kVecThreads / 32];
   __shared__ double slot;
   __shared__ int s_go;
   const int b = blockIdx.x;
   const unsigned nblk = gridDim.x;
+  const int64_t d = a.d;
+  const int s = a.s;
+  AdmmCtl* ctl = a.ctl;
   int k = ctl->k;
   double eps_next = ctl->eps_next;
+  const int refreshed = ctl->hx_pending;   // the recompute of iteration k ran just before this launch
+  auto fail = [&]() {
+    if (b == 0 && threadIdx.x == 0) {
+      atomicExch(a.dstat, (int)NYS_ETIMEOUT);
+      cudaGraphSetConditional(a.h_admm, 0u);
+      cudaGraphSetConditional(a.h_pcg, 0u);
+      cudaGraphSetConditional(a.h_zu, 0u);
+      cudaGraphSetConditional(a.h_hx, 0u);
+    }
+  };
+  bool first = true;
   for (;;) {
-    // ---- iteration k: hand it to the general body when hx is due for a recompute
-    if (!iter_hx_skip(0, k, hx_refresh)) break;
+    // ---- (H + rho I) x due for a recompute at iteration k: request it and return
+    if (!iter_hx_skip(0, k, a.hx_refresh) && !(first && refreshed)) {
+      if (b == 0 && threadIdx.x == 0) {
+        ctl->hx_pending = 1;
+        ctl->nodes += 1;
+        cudaGraphSetConditional(a.h_hx, 1u);
+        cudaGraphSetConditional(a.h_pcg, 0u);
+        cudaGraphSetConditional(a.h_zu, 0u);
+      }
+      return;
+    }
     double tolk;
     int tol_abs;
-    iter_tol(tol_mode, tol, tol_floor, k, eps_next, &tolk, &tol_abs);
-    // ---- 1. right-hand side and warm-start residual partials
-    if (b < nb3) {
-      const int64_t j0 = (int64_t)b * chunk;
-      const int64_t j1 = min(d, j0 + chunk);
+    iter_tol(a.tol_mode, a.tol, a.tol_floor, k, eps_next, &tolk, &tol_abs);
+    // ---- 1. right-hand side, warm-start residual, ||w||^2, ||r||^2, U^T w partials
+    if (b < a.nb3) {
+      const int64_t j0 = (int64_t)b * a.chunk;
+      const int64_t j1 = min(d, j0 + a.chunk);
       double lw2 = 0.0, lr2 = 0.0;
       for (int64_t j = j0 + threadIdx.x; j < j1; j += kVecThreads) {
-        const C rj = (C)fma(rho, z[j] - u[j], q[j]);
+        const C rj = (C)fma(a.rho, a.z[j] - a.u[j], a.q[j]);
+        rc[j] = rj;
         const C wj = rj - hx[j];
         lr2 += (double)rj * (double)rj;
+        w[j] = wj;
+        wch[j - j0] = wj;
         lw2 += (double)wj * (double)wj;
       }
       const double tw2 = block_sum<kVecThreads>(lw2, sh);
       const double tr2 = block_sum<kVecThreads>(lr2, sh);
       if (threadIdx.x == 0) {
-        part_w2[b] = tw2;
-        part_r2[b] = tr2;
+        a.part_w2[b] = tw2;
+        a.part_r2[b] = tr2;
+      }
+      __syncthreads();
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      const int len = (int)(j1 - j0);
+      constexpr int RW = 4;
+      for (int i0 = warp * RW; i0 < s; i0 += (kVecThreads / 32) * RW) {
+        C acc[RW];
+#pragma unroll
+        for (int qq = 0; qq < RW; ++qq) acc[qq] = C(0);
+#pragma unroll 8
+        for (int jj = lane; jj < len; jj += 32) {
+          const C wv = wch[jj];
+#pragma unroll
+          for (int qq = 0; qq < RW; ++qq)
+            if (i0 + qq < s) acc[qq] = fma(U[(int64_t)(i0 + qq) * d + j0 + jj], wv, acc[qq]);
+        }
+#pragma unroll
+        for (int qq = 0; qq < RW; ++qq) acc[qq] = warp_sum(acc[qq]);
+        if (lane == 0) {
+#pragma unroll
+          for (int qq = 0; qq < RW; ++qq)
+            if (i0 + qq < s) a.part_g[(int64_t)b * s + i0 + qq] = (double)acc[qq];
+        }
       }
     }
-    if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, nblk)) {
+    if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, nblk)) return fail();
+    if (first && refreshed && b == 0 && threadIdx.x == 0) {
+      ctl->hx_pending = 0;
+      cudaGraphSetConditional(a.h_hx, 0u);
+    }
+    first = false;
+    // ---- 2. stop decision of the warm start (every block, the order of pcg_scalar_body)
+    const double w2 = block_fixed_sum_cg(a.part_w2, a.nb3, &slot);
+    const double r2 = block_fixed_sum_cg(a.part_r2, a.nb3, &slot);
+    const double thresh2 = tol_abs ? tolk * tolk : tolk * tolk * r2;
+    const int fixed = a.fixed_dev ? a.fixed_dev[k] : -1;
+    const bool nostep = fixed >= 0 ? fixed == 0 : !(w2 > thresh2);
+    if (!nostep) {
+      // ---- 3b. P^{-1} w and the PCG state; the PCG WHILE node takes over
+      __syncthreads();
+      for (int i = threadIdx.x; i < s; i += kVecThreads) {
+        double gsum = 0.0;
+#pragma unroll 8
+        for (int bb = 0; bb < a.nb3; ++bb) gsum += __ldcg(a.part_g + (int64_t)bb * s + i);
+        const C gi = (C)((double)cvec[i] * gsum);
+        wch[i] = gi;
+        if (b == 0) gs[i] = gi;
+      }
+      __syncthreads();
+      if (b < a.nb5) {
+        double lwy = 0.0;
+        for (int64_t j = b * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)a.nb5 * kVecThreads) {
+          const C wj = __ldcg(w + j);
+          C acc = wj;
+#pragma unroll 16
+          for (int i = 0; i < s; ++i) acc = fma(U[(int64_t)i * d + j], wch[i], acc);
+          y[j] = acc;
+          p[j] = acc;
+          lwy += (double)wj * (double)acc;
+        }
+        const double t = block_sum<kVecThreads>(lwy, sh);
+        if (threadIdx.x == 0) a.wy_part[b] = t;
+      }
       if (b == 0 && threadIdx.x == 0) {
-        atomicExch(dstat, (int)NYS_ETIMEOUT);
-        cudaGraphSetConditional(h_admm, 0u);
-        cudaGraphSetConditional(h_slow, 0u);
+        PcgState* st = a.st;
+        st->wy = 0.0;
+        st->w2 = w2;
+        st->r2 = r2;
+        st->thresh2 = thresh2;
+        st->tol = tolk;
+        st->tol_abs = tol_abs;
+        st->iters = 0;
+        st->done = 0;
+        st->status = 0;
+        st->maxit = a.maxit;
+        st->fixed = fixed;
+        st->ticket[0] = 0u;
+        st->ticket[1] = 0u;
+        ctl->nodes += 1;
+        cudaGraphSetConditional(a.h_pcg, 1u);
+        cudaGraphSetConditional(a.h_zu, 1u);
       }
       return;
     }
-    // ---- 2. stop decision of the PCG warm start (every block, same order)
-    const double w2 = block_fixed_sum_cg(part_w2, nb3, &slot);
-    const double r2 = block_fixed_sum_cg(part_r2, nb3, &slot);
-    const double thresh2 = tol_abs ? tolk * tolk : tolk * tolk * r2;
-    const int fixed = fixed_dev ? fixed_dev[k] : -1;
-    const bool nostep = fixed >= 0 ? fixed == 0 : !(w2 > thresh2);
-    if (!nostep) break;
-    // ---- 3. prox / dual step with x unchanged, residual partials
-    if (b < nbz) {
-      double* zt = ztrace ? ztrace + (int64_t)k * d : nullptr;
+    // ---- 3a. prox / dual step with x unchanged, residual partials
+    if (b < a.nbz) {
+      double* zt = a.ztrace ? a.ztrace + (int64_t)k * d : nullptr;
       double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
-      for (int64_t j = b * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)nbz * kVecThreads) {
+      for (int64_t j = b * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)a.nbz * kVecThreads) {
         const double xj = (double)xc[j];
-        const double zo = z[j];
-        const double vj = xj + u[j];
-        const double mag = fabs(vj) - kappa;
+        const double zo = a.z[j];
+        const double vj = xj + a.u[j];
+        const double mag = fabs(vj) - a.kappa;
         const double zj = mag > 0.0 ? copysign(mag, vj) : 0.0;
-        const double uj = u[j] + xj - zj;
-        x[j] = xj;
-        z[j] = zj;
-        u[j] = uj;
+        const double uj = a.u[j] + xj - zj;
+        a.x[j] = xj;
+        a.z[j] = zj;
+        a.u[j] = uj;
         if (zt) zt[j] = zj;
         a0 += (xj - zj) * (xj - zj);
         a1 += (zj - zo) * (zj - zo);
@@ -914,7 +1031,7 @@ __global__ void __launch_bounds__(kVecThreads) admm_nostep_kernel(
       a3 = block_sum<kVecThreads>(a3, sh);
       a4 = block_sum<kVecThreads>(a4, sh);
       if (threadIdx.x == 0) {
-        double* o = part5 + (int64_t)b * 5;
+        double* o = a.part5 + (int64_t)b * 5;
         o[0] = a0;
         o[1] = a1;
         o[2] = a2;
@@ -922,37 +1039,30 @@ __global__ void __launch_bounds__(kVecThreads) admm_nostep_kernel(
         o[4] = a4;
       }
     }
-    if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, nblk)) {
-      if (b == 0 && threadIdx.x == 0) {
-        atomicExch(dstat, (int)NYS_ETIMEOUT);
-        cudaGraphSetConditional(h_admm, 0u);
-        cudaGraphSetConditional(h_slow, 0u);
-      }
-      return;
-    }
+    if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, nblk)) return fail();
     // ---- 4. scalars of the iteration (every block; block 0 records them)
     if (threadIdx.x < 32) {
-      double a[5];
-      sum_part5(nbz, part5, a);
+      double sums[5];
+      sum_part5(a.nbz, a.part5, sums);
       if (threadIdx.x == 0) {
-        const double rp = sqrt(a[0]);
-        const double rd = rho * sqrt(a[1]);
+        const double rp = sqrt(sums[0]);
+        const double rd = a.rho * sqrt(sums[1]);
         eps_next = sqrt(rp * rd);
         int stop = 0;
-        if (eps_rel > 0.0) {
-          const double tp = eps_abs + eps_rel * fmax(sqrt(a[2]), sqrt(a[3]));
-          const double td = eps_abs + eps_rel * rho * sqrt(a[4]);
+        if (a.eps_rel > 0.0) {
+          const double tp = a.eps_abs + a.eps_rel * fmax(sqrt(sums[2]), sqrt(sums[3]));
+          const double td = a.eps_abs + a.eps_rel * a.rho * sqrt(sums[4]);
           if (rp <= tp && rd <= td) stop = 1;
         }
         if (b == 0) {
-          rp_trace[k] = rp;
-          rd_trace[k] = rd;
-          pcg_it_trace[k] = 0;
+          a.rp_trace[k] = rp;
+          a.rd_trace[k] = rd;
+          a.pcg_it_trace[k] = 0;
           ctl->eps_next = eps_next;
           ctl->stop = stop;
           ctl->k = k + 1;
         }
-        s_go = (k + 1 < K && !stop) ? 1 : 0;
+        s_go = (k + 1 < a.K && !stop) ? 1 : 0;
         slot = eps_next;
       }
     }
@@ -964,22 +1074,16 @@ __global__ void __launch_bounds__(kVecThreads) admm_nostep_kernel(
     if (!go) {
       if (b == 0 && threadIdx.x == 0) {
         ctl->nodes += 1;
-        cudaGraphSetConditional(h_admm, 0u);
-        cudaGraphSetConditional(h_slow, 0u);
+        cudaGraphSetConditional(a.h_admm, 0u);
+        cudaGraphSetConditional(a.h_pcg, 0u);
+        cudaGraphSetConditional(a.h_zu, 0u);
       }
       return;
     }
-    // the partials of steps 1 and 3 are rewritten only after the next barrier, which every
+    // the partials of steps 1 and 3a are rewritten only after the next barrier, which every
     // block reaches after its reads above
   }
-  // iteration k goes to the general body
-  if (b == 0 && threadIdx.x == 0) {
-    ctl->nodes += 1;
-    cudaGraphSetConditional(h_slow, 1u);
-  }
 }
-
-
 
 }  // namespace
 
@@ -1116,60 +1220,7 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   cp.conditional.size = 1;
   cudaGraphNode_t n_admm;
   G_OK(cudaGraphAddNode(&n_admm, graph, nullptr, nullptr, 0, &cp));
-  cudaGraph_t wbody = cp.conditional.phGraph_out[0];
-  // ADMM iterations that need no PCG step run in one fused cooperative kernel at the top of
-  // the WHILE body; it hands any other iteration to the general body below, which sits in
-  // an IF node (h_slow).  Used for the tracked warm start (hx_refresh > 0) without a refined
-  // step or warm-start model, for a single instance; NYS_ADMM_NOSTEP=0 turns it off.
-  cudaGraph_t body = wbody;
-  {
-    const bool use_model = (g.warm || g.warm_record) && s > 0;
-    const char* env = std::getenv("NYS_ADMM_NOSTEP");
-    bool fast = !g.Aref && !use_model && g.hx_refresh > 0 && g.allow_nostep && !(env && std::atoi(env) == 0);
-    const int nbf = std::max(nb3, nbz);
-    if (fast) {
-      int per_sm = 0, coop = 0;
-      G_OK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, current_device()));
-      G_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, admm_nostep_kernel<C>, kVecThreads, 0));
-      fast = coop && (int64_t)per_sm * sm_count() >= nbf && nbz <= kPart5Max;
-    }
-    if (fast) {
-      cudaGraphConditionalHandle h_slow;
-      G_OK(cudaGraphConditionalHandleCreate(&h_slow, wbody, 0u, 0u));
-      G_OK(cudaStreamBeginCaptureToGraph(cap, wbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3((unsigned)nbf);
-      cfg.blockDim = dim3(kVecThreads);
-      cfg.dynamicSmemBytes = 0;
-      cfg.stream = cap;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeCooperative;
-      attr[0].val.cooperative = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      G_OK(cudaLaunchKernelEx(&cfg, admm_nostep_kernel<C>, d, chunk, nb3, nbz, (const double*)g.q, g.x, g.z, g.u,
-                              (const C*)xc, (const C*)hx, g.rho, g.gamma / g.rho, part_w2, part_r2, part5, ctl, g.tol,
-                              g.tol_floor, g.tol_mode, (const int*)fixed_dev, g.hx_refresh, K, g.eps_abs, g.eps_rel,
-                              g.ztrace, g.rp, g.rd, g.pcg_it, dstat, h_admm, h_slow));
-      cudaStreamCaptureStatus cst0;
-      const cudaGraphNode_t* deps0 = nullptr;
-      size_t ndeps0 = 0;
-      G_OK(cudaStreamGetCaptureInfo(cap, &cst0, nullptr, nullptr, &deps0, nullptr, &ndeps0));
-      std::vector<cudaGraphNode_t> leaf0(deps0, deps0 + ndeps0);
-      G_OK(cudaStreamEndCapture(cap, &wbody));
-      cudaGraphNodeParams sp = {};
-      sp.type = cudaGraphNodeTypeConditional;
-      sp.conditional.handle = h_slow;
-      sp.conditional.type = cudaGraphCondTypeIf;
-      sp.conditional.size = 1;
-      cudaGraphNode_t n_slow;
-      G_OK(cudaGraphAddNode(&n_slow, wbody, leaf0.data(), nullptr, leaf0.size(), &sp));
-      body = sp.conditional.phGraph_out[0];
-    }
-  }
-  G_OK(cudaGraphConditionalHandleCreate(&h_pcg, body, 0u, 0u));
-  cudaGraphConditionalHandle h_hx;
-  G_OK(cudaGraphConditionalHandleCreate(&h_hx, body, 0u, 0u));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
 
   ApassArgs aa;
   aa.A = g.pb.A->data;
@@ -1183,6 +1234,143 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   aa.D_out = nullptr;
   aa.t_out = nullptr;
   aa.mode = g.pb.D ? MODE_DIAG : MODE_ID;
+
+  // Fast body (tracked warm start, no refined step or warm-start model, a single instance):
+  //   IF (h_hx) [ (H + rho I) x recompute ] -> admm_head_kernel (cooperative) ->
+  //   WHILE (h_pcg) [ A-pass, reduce, update, P^{-1} tail ] -> IF (h_zu) [ prox / dual + scalars ]
+  // The head kernel runs the iterations that need no PCG step itself and prepares the PCG
+  // state of the others.  NYS_ADMM_NOSTEP=0 selects the general body for every solve.
+  {
+    const bool use_model = (g.warm || g.warm_record) && s > 0;
+    const char* env = std::getenv("NYS_ADMM_NOSTEP");
+    bool fast = !g.Aref && !use_model && g.hx_refresh > 0 && g.allow_nostep && !(env && std::atoi(env) == 0);
+    const int nbf = std::max(std::max(nb3, nbz), nbr);
+    const size_t sm_head = (size_t)std::max(chunk, std::max(1, s)) * sizeof(C);
+    if (fast) {
+      int per_sm = 0, coop = 0;
+      G_OK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, current_device()));
+      G_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, admm_head_kernel<C>, kVecThreads, sm_head));
+      fast = coop && (int64_t)per_sm * sm_count() >= nbf && nbz <= kPart5Max;
+    }
+    if (fast) {
+      cudaGraphConditionalHandle h_hx, h_zu;
+      G_OK(cudaGraphConditionalHandleCreate(&h_hx, body, 0u, 0u));
+      G_OK(cudaGraphConditionalHandleCreate(&h_pcg, body, 0u, 0u));
+      G_OK(cudaGraphConditionalHandleCreate(&h_zu, body, 0u, 0u));
+      auto add_cond = [&](cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                          const std::vector<cudaGraphNode_t>& deps, cudaGraphNode_t* node, cudaGraph_t* child) {
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = type;
+        np.conditional.size = 1;
+        const cudaError_t ce = cudaGraphAddNode(node, body, deps.data(), nullptr, deps.size(), &np);
+        *child = np.conditional.phGraph_out[0];
+        return ce;
+      };
+      // IF (h_hx): (H + rho I) x with one pass over A
+      cudaGraphNode_t n_hx;
+      cudaGraph_t hbody;
+      G_OK(add_cond(h_hx, cudaGraphCondTypeIf, {}, &n_hx, &hbody));
+      count_launch_suspend(true);
+      G_OK(cudaStreamBeginCaptureToGraph(cap, hbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      aa.p = xc;
+      aa.skip = nullptr;
+      G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, true));
+      G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho + g.mu, hx, nullptr, 0, cap));
+      G_OK(cudaStreamEndCapture(cap, &hbody));
+      // head kernel
+      G_OK(cudaStreamBeginCaptureToGraph(cap, body, &n_hx, nullptr, 1, cudaStreamCaptureModeRelaxed));
+      HeadArgs ha;
+      ha.d = d;
+      ha.chunk = chunk;
+      ha.nb3 = nb3;
+      ha.nbz = nbz;
+      ha.nb5 = nb5;
+      ha.s = s;
+      ha.q = g.q;
+      ha.x = g.x;
+      ha.z = g.z;
+      ha.u = g.u;
+      ha.rho = g.rho;
+      ha.kappa = g.gamma / g.rho;
+      ha.part_w2 = part_w2;
+      ha.part_r2 = part_r2;
+      ha.part_g = part_g;
+      ha.wy_part = wy_part;
+      ha.part5 = part5;
+      ha.ctl = ctl;
+      ha.st = st;
+      ha.tol = g.tol;
+      ha.tol_floor = g.tol_floor;
+      ha.tol_mode = g.tol_mode;
+      ha.maxit = g.maxit;
+      ha.hx_refresh = g.hx_refresh;
+      ha.K = K;
+      ha.fixed_dev = fixed_dev;
+      ha.eps_abs = g.eps_abs;
+      ha.eps_rel = g.eps_rel;
+      ha.ztrace = g.ztrace;
+      ha.rp_trace = g.rp;
+      ha.rd_trace = g.rd;
+      ha.pcg_it_trace = g.pcg_it;
+      ha.dstat = dstat;
+      ha.h_admm = h_admm;
+      ha.h_pcg = h_pcg;
+      ha.h_zu = h_zu;
+      ha.h_hx = h_hx;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)nbf);
+      cfg.blockDim = dim3(kVecThreads);
+      cfg.dynamicSmemBytes = sm_head;
+      cfg.stream = cap;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      G_OK(cudaLaunchKernelEx(&cfg, admm_head_kernel<C>, ha, (const C*)xc, (const C*)hx, w, rc, y, p, U, cvec, gs));
+      cudaStreamCaptureStatus cst0;
+      const cudaGraphNode_t* deps0 = nullptr;
+      size_t ndeps0 = 0;
+      G_OK(cudaStreamGetCaptureInfo(cap, &cst0, nullptr, nullptr, &deps0, nullptr, &ndeps0));
+      std::vector<cudaGraphNode_t> leaf0(deps0, deps0 + ndeps0);
+      G_OK(cudaStreamEndCapture(cap, &body));
+      // WHILE (h_pcg): PCG iterations
+      cudaGraphNode_t n_pcg;
+      cudaGraph_t pbody;
+      G_OK(add_cond(h_pcg, cudaGraphCondTypeWhile, leaf0, &n_pcg, &pbody));
+      G_OK(cudaStreamBeginCaptureToGraph(cap, pbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      aa.p = p;
+      aa.skip = &st->done;
+      G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, true));
+      G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho + g.mu, v, pv_part, nbr, cap));
+      pcg_update_kernel<C><<<nb3, kVecThreads, (size_t)chunk * sizeof(C), cap>>>(
+          0, d, chunk, xc, w, rc, v, p, U, s, pv_part, nbr, wy_part, nb5, part_w2, part_r2, part_g, st, hx, cvec, gs,
+          h_pcg, 1, nullptr, nullptr, nullptr, 0.0, (C*)nullptr);
+      pcg_tail_kernel<C><<<nb5, kVecThreads, (size_t)std::max(1, s) * sizeof(C), cap>>>(d, w, y, U, s, gs, wy_part, st,
+                                                                                       0, p);
+      G_OK(cudaStreamEndCapture(cap, &pbody));
+      // IF (h_zu): prox / dual step of an iteration that took PCG steps
+      cudaGraphNode_t n_zu;
+      cudaGraph_t zbody;
+      G_OK(add_cond(h_zu, cudaGraphCondTypeIf, {n_pcg}, &n_zu, &zbody));
+      G_OK(cudaStreamBeginCaptureToGraph(cap, zbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      admm_zu_g_kernel<C><<<nbz, kVecThreads, 0, cap>>>(d, xc, 0, g.x, g.z, g.u, g.gamma / g.rho, g.ztrace, ctl,
+                                                        part5, g.rho, K, g.eps_abs, g.eps_rel, g.rp, g.rd, g.pcg_it,
+                                                        st, 1, 4, h_admm);
+      G_OK(cudaStreamEndCapture(cap, &zbody));
+      count_launch_suspend(false);
+      G_OK(cudaGetLastError());
+      inst->ctl = ctl;
+      inst->dstat = dstat;
+      return NYS_OK;
+    }
+  }
+  G_OK(cudaGraphConditionalHandleCreate(&h_pcg, body, 0u, 0u));
+  cudaGraphConditionalHandle h_hx;
+  G_OK(cudaGraphConditionalHandleCreate(&h_hx, body, 0u, 0u));
+
   const size_t sm_upd = (size_t)chunk * sizeof(C);
   const size_t sm_tail = (size_t)std::max(1, s) * sizeof(C);
   const int refine = g.Aref ? 1 : 0;
