@@ -428,6 +428,65 @@ nys_status adaptive_sketch(const nys_matrix* Ain, const double* D, double shift,
   return NYS_OK;
 }
 
+// A helper pass y = A^T phi(.) issued on a side stream and joined later (its buffers are
+// allocated on the main stream before the fork and stay valid until the join).  With no side
+// stream it runs on the main stream.
+struct SidePass {
+  cudaStream_t side = nullptr, main = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  void* part = nullptr;
+  double* lp = nullptr;
+  int* dstat = nullptr;
+  ApassArgs a;
+  ApassPlan plan;
+  ~SidePass() {
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (part) cudaFreeAsync(part, main);
+    if (lp) cudaFreeAsync(lp, main);
+    if (dstat) cudaFreeAsync(dstat, main);
+  }
+  nys_status start(const nys_matrix* A, int mode, const double* b, void* y, cudaStream_t side_st, cudaStream_t st) {
+    main = st;
+    side = side_st ? side_st : st;
+    apass_plan(A, &plan);
+    NYS_CU(cudaMallocAsync(&part, apass_partial_bytes(A, plan), st));
+    NYS_CU(cudaMallocAsync((void**)&lp, plan.grid * sizeof(double), st));
+    NYS_CU(cudaMallocAsync((void**)&dstat, sizeof(int), st));
+    NYS_CU(cudaMemsetAsync(dstat, 0, sizeof(int), st));
+    a.A = A->data;
+    a.n = A->n;
+    a.d = A->d;
+    a.ld = A->ld;
+    a.dtype = A->dtype;
+    a.col_scale = A->col_scale;
+    a.p = nullptr;
+    a.D = nullptr;
+    a.b = b;
+    a.D_out = nullptr;
+    a.t_out = nullptr;
+    a.mode = mode;
+    if (side != st) {
+      NYS_CU(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+      NYS_CU(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+      NYS_CU(cudaEventRecord(fork, st));
+      NYS_CU(cudaStreamWaitEvent(side, fork, 0));
+    }
+    NYS_CU(apass_run(a, plan, part, lp, dstat, side));
+    ApassArgs ar = a;
+    NYS_CU(apass_reduce(ar, plan, part, 0.0, y, nullptr, 0, side));
+    if (side != st) NYS_CU(cudaEventRecord(join, side));
+    return NYS_OK;
+  }
+  nys_status finish(cudaStream_t st) {
+    if (join) NYS_CU(cudaStreamWaitEvent(st, join, 0));
+    int hs = 0;
+    NYS_CU(cudaMemcpyAsync(&hs, dstat, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NYS_CU(cudaStreamSynchronize(st));
+    return hs ? (nys_status)hs : NYS_OK;
+  }
+};
+
 // ---------------------------------------------------------------- lasso / elastic-net NysADMM
 // mu: H^g = mu I of a quadratic g (0 for the lasso; 1 - gamma for the elastic net of Eq. 6).
 // The sketched Hessian is A^T A + mu I (Alg. NysADMM), the PCG matrix A^T A + (mu + rho) I,
@@ -454,7 +513,14 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
   } guard{&P};
   double* Om = pool.alloc<double>((size_t)d * smax);
   double* Y = pool.alloc<double>((size_t)d * smax);
+  double* q = pool.alloc<double>(d);
+  void* ytmp = pool.alloc<unsigned char>(d * 8);
   if (!pool.ok()) return NYS_ENOMEM;
+  // q = A^T b does not depend on the sketch: it runs on a side stream while the sketch and
+  // the Nystrom core run on `st` (joined before the iterations).  Row-sharded solves keep it
+  // on `st` (the reduction callback is ordered on one stream).
+  SidePass qpass;
+  NYS_TRY(qpass.start(A, MODE_CONST, b, ytmp, shard_comm().fn ? nullptr : side_stream(), st));
   NYS_TRY(omega_panel(Omega, o.seed, d, smax, Om, st));
   const double shs = o.shift_scale > 0 ? o.shift_scale : std::sqrt((double)d);
   if (smax > rank) {
@@ -476,11 +542,9 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
   double* x = pool.alloc<double>(d);
   double* z = pool.alloc<double>(d);
   double* u = pool.alloc<double>(d);
-  double* q = pool.alloc<double>(d);
   double* yres = pool.alloc<double>(d);
   C* xc = pool.alloc<C>(d);
   C* rc = pool.alloc<C>(d);
-  void* ytmp = pool.alloc<unsigned char>(d * 8);
   float* xA32 = pool.alloc<float>(d);
   const int K = std::max(1, o.admm_maxit);
   const int nb = admm_blocks(d);
@@ -496,10 +560,10 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
   NYS_CU(cudaMemsetAsync(xc, 0, d * sizeof(C), st));
   NYS_CU(cudaMemsetAsync(stop, 0, sizeof(int), st));
 
-  // q = A^T b
+  // q = A^T b: join the side pass
   {
-    PhaseTimer pt("q = A^T b", st);
-    NYS_TRY(aux_pass(A, MODE_CONST, nullptr, b, nullptr, nullptr, ytmp, nullptr, st));
+    PhaseTimer pt("q = A^T b (join)", st);
+    NYS_TRY(qpass.finish(st));
     NYS_TRY(to_f64(A, ytmp, q, d, st));
     NYS_TRY(shard_sum(q, d, NYS_F64, st));
   }

@@ -417,38 +417,84 @@ __device__ __forceinline__ void jacobi_rot(double app, double aqq, double apq, d
 // Block (bx, by) owns a 16 x 16 tile of 2x2 pair-blocks of A (pairs ma = bx*16 + tx,
 // mb = by*16 + ty); the 32 rotations it needs are computed once into shared memory.
 // Every block also applies its 16 column rotations to one row slice of V (slice by of gy).
+// The pair indices of a round depend only on (N, r), so every load of the round -- the
+// three entries behind each rotation, the tile's four entries, the V entries -- is issued
+// before any rotation is formed: one memory latency per round instead of three.
+// (Plain pointers: in the persistent form Ain was written by other blocks earlier in the
+// same launch, so its loads must not take the non-coherent read-only path.)
 constexpr int JT = 16;
+constexpr int kJacVMax = 4;   // V (row, pair) elements per thread: rows <= kJacVMax * 256 / 16
 struct JacobiRoundSmem {
   double rc[2][JT], rs[2][JT];
   int rp[2][JT], rq[2][JT];
 };
-// (Plain pointers: in the persistent form Ain was written by other blocks earlier in the same
-// launch, so its loads must not take the non-coherent read-only path.)
 __device__ __forceinline__ void jacobi_round(const double* Ain, double* Aout, double* V, int N, int r, int bx, int by,
                                              int gy, JacobiRoundSmem& sh) {
   const int H = N / 2;
   const int tx = threadIdx.x % JT, ty = threadIdx.x / JT;
+  // rotation inputs (threads < 32)
+  int rp_ = 0, rq_ = 1;
+  double app = 0.0, aqq = 0.0, apq = 0.0;
+  bool have_rot = false;
   if (threadIdx.x < 2 * JT) {
     const int side = threadIdx.x / JT, t = threadIdx.x % JT;
     const int m = (side == 0 ? bx : by) * JT + t;
-    int p = 0, q = 1;
-    double c = 1.0, sn = 0.0;
     if (m < H) {
-      rr_pair(N, r, m, p, q);
-      jacobi_rot(Ain[p + (int64_t)p * N], Ain[q + (int64_t)q * N], Ain[p + (int64_t)q * N], c, sn);
+      rr_pair(N, r, m, rp_, rq_);
+      app = Ain[rp_ + (int64_t)rp_ * N];
+      aqq = Ain[rq_ + (int64_t)rq_ * N];
+      apq = Ain[rp_ + (int64_t)rq_ * N];
+      have_rot = true;
     }
+  }
+  // tile entries
+  const int ma = bx * JT + tx, mb = by * JT + ty;
+  const bool in_tile = ma < H && mb < H;
+  int pa = 0, qa = 1, pb = 0, qb = 1;
+  double x_pp = 0.0, x_pq = 0.0, x_qp = 0.0, x_qq = 0.0;
+  if (in_tile) {
+    rr_pair(N, r, ma, pa, qa);
+    rr_pair(N, r, mb, pb, qb);
+    x_pp = Ain[pa + (int64_t)pb * N];
+    x_pq = Ain[pa + (int64_t)qb * N];
+    x_qp = Ain[qa + (int64_t)pb * N];
+    x_qq = Ain[qa + (int64_t)qb * N];
+  }
+  // V entries: this block's 16 pairs (those of bx) over rows [lo, hi)
+  const int npair = min(JT, H - bx * JT);
+  const int lo = (int)((int64_t)N * by / gy), hi = (int)((int64_t)N * (by + 1) / gy);
+  const int rows = hi - lo;
+  const int nel = npair > 0 ? npair * rows : 0;
+  double vp[kJacVMax], vq[kJacVMax];
+  int vrow[kJacVMax], vpi[kJacVMax], vqi[kJacVMax], vt[kJacVMax];
+#pragma unroll
+  for (int c = 0; c < kJacVMax; ++c) {
+    const int e = threadIdx.x + c * JT * JT;
+    vt[c] = -1;
+    if (e < nel) {
+      const int t = e / rows, row = lo + e % rows;
+      int p, q;
+      rr_pair(N, r, bx * JT + t, p, q);
+      vt[c] = t;
+      vrow[c] = row;
+      vpi[c] = p;
+      vqi[c] = q;
+      vp[c] = V[row + (int64_t)p * N];
+      vq[c] = V[row + (int64_t)q * N];
+    }
+  }
+  if (threadIdx.x < 2 * JT) {
+    const int side = threadIdx.x / JT, t = threadIdx.x % JT;
+    double c = 1.0, sn = 0.0;
+    if (have_rot) jacobi_rot(app, aqq, apq, c, sn);
     sh.rc[side][t] = c;
     sh.rs[side][t] = sn;
-    sh.rp[side][t] = p;
-    sh.rq[side][t] = q;
+    sh.rp[side][t] = rp_;
+    sh.rq[side][t] = rq_;
   }
   __syncthreads();
-  const int ma = bx * JT + tx, mb = by * JT + ty;
-  if (ma < H && mb < H) {
-    const int pa = sh.rp[0][tx], qa = sh.rq[0][tx], pb = sh.rp[1][ty], qb = sh.rq[1][ty];
+  if (in_tile) {
     const double ca = sh.rc[0][tx], sa = sh.rs[0][tx], cb = sh.rc[1][ty], sb = sh.rs[1][ty];
-    const double x_pp = Ain[pa + (int64_t)pb * N], x_pq = Ain[pa + (int64_t)qb * N];
-    const double x_qp = Ain[qa + (int64_t)pb * N], x_qq = Ain[qa + (int64_t)qb * N];
     // columns: p' = c p - s q, q' = s p + c q
     const double y_pp = cb * x_pp - sb * x_pq, y_pq = sb * x_pp + cb * x_pq;
     const double y_qp = cb * x_qp - sb * x_qq, y_qq = sb * x_qp + cb * x_qq;
@@ -464,20 +510,23 @@ __device__ __forceinline__ void jacobi_round(const double* Ain, double* Aout, do
     Aout[qa + (int64_t)pb * N] = z_qp;
     Aout[qa + (int64_t)qb * N] = z_qq;
   }
-  // V <- V J for this block's 16 pairs, rows [lo, hi) of slice by (the pairs of a round
-  // are disjoint, so every (row, pair) element is independent of the others).
-  {
-    const int npair = min(JT, H - bx * JT);
-    const int lo = (int)((int64_t)N * by / gy), hi = (int)((int64_t)N * (by + 1) / gy);
-    const int rows = hi - lo;
-    for (int e = threadIdx.x; e < npair * rows; e += JT * JT) {
-      const int t = e / rows, row = lo + e % rows;
-      const int p = sh.rp[0][t], q = sh.rq[0][t];
-      const double c = sh.rc[0][t], sn = sh.rs[0][t];
-      const double vp = V[row + (int64_t)p * N], vq = V[row + (int64_t)q * N];
-      V[row + (int64_t)p * N] = c * vp - sn * vq;
-      V[row + (int64_t)q * N] = sn * vp + c * vq;
+  // V <- V J (the pairs of a round are disjoint: every (row, pair) element is independent)
+#pragma unroll
+  for (int c = 0; c < kJacVMax; ++c) {
+    if (vt[c] >= 0) {
+      const double cc = sh.rc[0][vt[c]], sn = sh.rs[0][vt[c]];
+      V[vrow[c] + (int64_t)vpi[c] * N] = cc * vp[c] - sn * vq[c];
+      V[vrow[c] + (int64_t)vqi[c] * N] = sn * vp[c] + cc * vq[c];
     }
+  }
+  // elements beyond kJacVMax per thread (only for very tall slices): the plain loop
+  for (int e = threadIdx.x + kJacVMax * JT * JT; e < nel; e += JT * JT) {
+    const int t = e / rows, row = lo + e % rows;
+    const int p = sh.rp[0][t], q = sh.rq[0][t];
+    const double c = sh.rc[0][t], sn = sh.rs[0][t];
+    const double a = V[row + (int64_t)p * N], bq = V[row + (int64_t)q * N];
+    V[row + (int64_t)p * N] = c * a - sn * bq;
+    V[row + (int64_t)q * N] = sn * a + c * bq;
   }
 }
 

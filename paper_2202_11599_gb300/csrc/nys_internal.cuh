@@ -19,6 +19,7 @@ int current_device();                                       // -1 if none
 int sm_count();                                             // SMs of the current device
 cudaError_t ensure_max_dyn_smem(const void* fn, int bytes); // once per (kernel, device)
 cudaStream_t capture_stream();                              // private capture stream per (thread, device)
+cudaStream_t side_stream();                                 // second work stream per (thread, device)
 
 // Row modes of the fused A-pass: u_i = phi(t_i), t = A p.
 enum ApassMode : int {

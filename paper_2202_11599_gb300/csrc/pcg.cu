@@ -907,7 +907,7 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
       const int64_t j1 = min(d, j0 + a.chunk);
       double lw2 = 0.0, lr2 = 0.0;
       for (int64_t j = j0 + threadIdx.x; j < j1; j += kVecThreads) {
-        const C rj = (C)fma(a.rho, a.z[j] - a.u[j], a.q[j]);
+        const C rj = (C)fma(a.rho, __ldcg(a.z + j) - __ldcg(a.u + j), a.q[j]);
         rc[j] = rj;
         const C wj = rj - hx[j];
         lr2 += (double)rj * (double)rj;
@@ -1010,11 +1010,12 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
       double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
       for (int64_t j = b * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)a.nbz * kVecThreads) {
         const double xj = (double)xc[j];
-        const double zo = a.z[j];
-        const double vj = xj + a.u[j];
+        const double zo = __ldcg(a.z + j);
+        const double uo = __ldcg(a.u + j);
+        const double vj = xj + uo;
         const double mag = fabs(vj) - a.kappa;
         const double zj = mag > 0.0 ? copysign(mag, vj) : 0.0;
-        const double uj = a.u[j] + xj - zj;
+        const double uj = uo + xj - zj;
         a.x[j] = xj;
         a.z[j] = zj;
         a.u[j] = uj;

@@ -57,6 +57,15 @@ cudaStream_t capture_stream() {
   return streams[dev];
 }
 
+cudaStream_t side_stream() {
+  static thread_local cudaStream_t streams[kMaxDevices] = {};
+  const int dev = current_device();
+  if (dev < 0 || dev >= kMaxDevices) return nullptr;
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+    streams[dev] = nullptr;
+  return streams[dev];
+}
+
 ShardComm& shard_comm() {
   static thread_local ShardComm c;
   return c;
