@@ -25,7 +25,9 @@
  *    NYS_FP8E4M3.
  *    ADMM state (x, z, u, residuals) is always FP64.
  *  - Errors are returned, never trapped: NYS_EINVAL for bad arguments (checked
- *    before any launch), NYS_ENOTSPD if the Nystrom core matrix stays
+ *    before any launch; NaN or infinite data -- in b, in A, in Omega, in the PCG
+ *    right-hand side or start -- is detected on the device where it first enters a
+ *    reduction and also gives NYS_EINVAL), NYS_ENOTSPD if the Nystrom core matrix stays
  *    indefinite after shift retries, NYS_EBREAKDOWN if p^T (H + rho I) p <= 0
  *    or is not finite in PCG, NYS_ENOCONV when an iteration cap is reached
  *    (the last iterate is still written), NYS_ETIMEOUT if a device-side wait

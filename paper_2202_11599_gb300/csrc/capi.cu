@@ -478,12 +478,18 @@ struct SidePass {
     if (side != st) NYS_CU(cudaEventRecord(join, side));
     return NYS_OK;
   }
-  nys_status finish(cudaStream_t st) {
+  // Joins the pass; NYS_EINVAL when its result has a NaN or an infinity (a non-finite
+  // entry of b or of A reaches A^T b).
+  nys_status finish(cudaStream_t st, const void* y, int64_t d, bool f32) {
     if (join) NYS_CU(cudaStreamWaitEvent(st, join, 0));
-    int hs = 0;
-    NYS_CU(cudaMemcpyAsync(&hs, dstat, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NYS_CU(cudaMemsetAsync(lp, 0, sizeof(int), st));
+    NYS_CU(any_nonfinite(y, d, f32, reinterpret_cast<int*>(lp), st));
+    int hs[2] = {0, 0};
+    NYS_CU(cudaMemcpyAsync(&hs[0], dstat, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NYS_CU(cudaMemcpyAsync(&hs[1], lp, sizeof(int), cudaMemcpyDeviceToHost, st));
     NYS_CU(cudaStreamSynchronize(st));
-    return hs ? (nys_status)hs : NYS_OK;
+    if (hs[0]) return (nys_status)hs[0];
+    return hs[1] ? NYS_EINVAL : NYS_OK;
   }
 };
 
@@ -563,7 +569,7 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
   // q = A^T b: join the side pass
   {
     PhaseTimer pt("q = A^T b (join)", st);
-    NYS_TRY(qpass.finish(st));
+    NYS_TRY(qpass.finish(st, ytmp, d, A->dtype != NYS_F64));
     NYS_TRY(to_f64(A, ytmp, q, d, st));
     NYS_TRY(shard_sum(q, d, NYS_F64, st));
   }
@@ -1266,7 +1272,18 @@ nys_status pcg_solve(const nys_matrix* A, const double* D, double rho, nys_preco
   if (o.pcg_fixed_iters) prm.fixed = o.pcg_fixed_iters[0];
   Pool pool(st);
   void* cbuf = pool.alloc<double>(P ? P->s : 1);
+  int* bad = pool.alloc<int>(1);
   if (!pool.ok()) return NYS_ENOMEM;
+  {
+    // a NaN or an infinity in r or in x0 is a bad argument, not a breakdown of the iteration
+    int bad_h = 0;
+    NYS_CU(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    NYS_CU(any_nonfinite(r, A->d, A->dtype != NYS_F64, bad, st));
+    NYS_CU(any_nonfinite(x, A->d, A->dtype != NYS_F64, bad, st));
+    NYS_CU(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NYS_CU(cudaStreamSynchronize(st));
+    if (bad_h) return NYS_EINVAL;
+  }
   PrecondView view;
   int it = 0;
   nys_status s;

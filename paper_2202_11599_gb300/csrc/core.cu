@@ -1167,6 +1167,24 @@ cudaError_t sketch_atw_partials(const nys_matrix* A, const void* W, int s, void*
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ input checks
+// *flag |= 1 when any of the n values (FP64, or FP32 when f32) is NaN or infinite.
+__global__ void nonfinite_kernel(const void* __restrict__ x, int64_t n, int f32, int* flag) {
+  int bad = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = f32 ? (double)reinterpret_cast<const float*>(x)[i] : reinterpret_cast<const double*>(x)[i];
+    bad |= !isfinite(v);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+cudaError_t any_nonfinite(const void* x, int64_t n, bool f32, int* flag, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  count_launch();
+  nonfinite_kernel<<<(unsigned)std::min<int64_t>(1024, (n + 255) / 256), 256, 0, st>>>(x, n, f32 ? 1 : 0, flag);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ conversions
 __global__ void f64_to_f32_kernel(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)

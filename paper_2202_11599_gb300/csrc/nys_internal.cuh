@@ -143,6 +143,8 @@ cudaError_t gemm_nn_t(const T* B, int64_t M, int K, const T* V, int N, T* C, cud
 // Omega (d x s column-major FP64) ~ N(0,1) from Philox-4x32-10 + Box-Muller (random.cu).
 cudaError_t gaussian_panel(uint64_t seed, int64_t d, int s, double* Omega, cudaStream_t st);
 cudaError_t convert_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t st);
+// *flag |= 1 (device int, caller-zeroed) if any of x[0..n) (FP64, or FP32) is NaN or infinite
+cudaError_t any_nonfinite(const void* x, int64_t n, bool f32, int* flag, cudaStream_t st);
 // FP8 E4M3 matrix with per-column scales -> FP32 values (n x ld, same layout)
 cudaError_t dequantize_fp8(const nys_matrix* A, float* out, cudaStream_t st);
 cudaError_t convert_f32_to_f64(const float* x, double* y, int64_t n, cudaStream_t st);
