@@ -112,7 +112,9 @@ nys_status cholqr2(double* Om, int64_t d, int m, cudaStream_t st) {
   if (!pool.ok()) return NYS_ENOMEM;
   for (int pass = 0; pass < 2; ++pass) {
     NYS_CU(gram_xty(Om, Om, d, m, G, work, st));
-    NYS_CU(chol_upper(G, m, info, st));
+    // a pivot below 1e-10 of the largest column norm^2: columns dependent to ~1e-5, which
+    // CholQR cannot orthonormalise -- refused as a bad test matrix
+    NYS_CU(chol_upper(G, m, info, st, 1e-10));
     int info_h = 0;
     NYS_CU(cudaMemcpyAsync(&info_h, info, sizeof(int), cudaMemcpyDeviceToHost, st));
     NYS_CU(cudaStreamSynchronize(st));

@@ -172,9 +172,10 @@ static cudaError_t gemm_nn(const double* B, int64_t d, int s, const double* V, d
 // Single CTA.  M (s x s, column-major) is symmetrised, then overwritten by the upper
 // factor C (C^T C = M); the strict lower triangle is zeroed.  info = 0 or k+1 when
 // the k-th pivot is not positive / not finite.
-__global__ void __launch_bounds__(1024) chol_upper_kernel(double* M, int s, int* info) {
+__global__ void __launch_bounds__(1024) chol_upper_kernel(double* M, int s, int* info, double rel_tol) {
   const int tid = threadIdx.x, T = blockDim.x;
   __shared__ int bad;
+  __shared__ double thresh;
   for (int64_t idx = tid; idx < (int64_t)s * s; idx += T) {
     const int i = (int)(idx % s), j = (int)(idx / s);
     if (i < j) {
@@ -182,12 +183,17 @@ __global__ void __launch_bounds__(1024) chol_upper_kernel(double* M, int s, int*
       M[i + (int64_t)j * s] = v;
     }
   }
-  if (tid == 0) bad = 0;
+  if (tid == 0) {
+    bad = 0;
+    double mx = 0.0;
+    for (int j = 0; j < s; ++j) mx = fmax(mx, fabs(M[j + (int64_t)j * s]));
+    thresh = rel_tol * mx;
+  }
   __syncthreads();
   for (int j = 0; j < s; ++j) {
     if (tid == 0) {
       const double dj = M[j + (int64_t)j * s];
-      if (!(dj > 0.0) || !isfinite(dj)) {
+      if (!(dj > 0.0) || !(dj > thresh) || !isfinite(dj)) {
         bad = j + 1;
       } else {
         M[j + (int64_t)j * s] = sqrt(dj);
@@ -219,22 +225,28 @@ __global__ void __launch_bounds__(1024) chol_upper_kernel(double* M, int s, int*
 // Same algorithm and operation order with the upper triangle held in shared memory
 // (packed by columns: (i, c), i <= c, at c (c + 1) / 2 + i), so that every step's
 // pivot, row scaling and trailing update touch on-chip data instead of L2.
-__global__ void __launch_bounds__(1024) chol_upper_smem_kernel(double* M, int s, int* info) {
+__global__ void __launch_bounds__(1024) chol_upper_smem_kernel(double* M, int s, int* info, double rel_tol) {
   extern __shared__ double up[];
   const int tid = threadIdx.x, T = blockDim.x;
   __shared__ int bad;
+  __shared__ double thresh;
   auto at = [](int i, int c) { return c * (c + 1) / 2 + i; };
   for (int64_t idx = tid; idx < (int64_t)s * s; idx += T) {
     const int i = (int)(idx % s), j = (int)(idx / s);
     if (i < j) up[at(i, j)] = 0.5 * (M[i + (int64_t)j * s] + M[j + (int64_t)i * s]);
     else if (i == j) up[at(i, i)] = M[i + (int64_t)i * s];
   }
-  if (tid == 0) bad = 0;
+  if (tid == 0) {
+    bad = 0;
+    double mx = 0.0;
+    for (int j = 0; j < s; ++j) mx = fmax(mx, fabs(up[at(j, j)]));
+    thresh = rel_tol * mx;
+  }
   __syncthreads();
   for (int j = 0; j < s; ++j) {
     if (tid == 0) {
       const double dj = up[at(j, j)];
-      if (!(dj > 0.0) || !isfinite(dj)) {
+      if (!(dj > 0.0) || !(dj > thresh) || !isfinite(dj)) {
         bad = j + 1;
       } else {
         up[at(j, j)] = sqrt(dj);
@@ -262,16 +274,16 @@ __global__ void __launch_bounds__(1024) chol_upper_smem_kernel(double* M, int s,
   }
 }
 
-cudaError_t chol_upper(double* M, int s, int* info, cudaStream_t st) {
+cudaError_t chol_upper(double* M, int s, int* info, cudaStream_t st, double rel_tol) {
   const size_t smem = (size_t)s * (s + 1) / 2 * sizeof(double);
   if (smem <= 200 * 1024) {
     NYS_CUDA_TRY(ensure_max_dyn_smem((const void*)chol_upper_smem_kernel, 200 * 1024));
     count_launch();
-    chol_upper_smem_kernel<<<1, 1024, smem, st>>>(M, s, info);
+    chol_upper_smem_kernel<<<1, 1024, smem, st>>>(M, s, info, rel_tol);
     return cudaGetLastError();
   }
   count_launch();
-  chol_upper_kernel<<<1, 1024, 0, st>>>(M, s, info);
+  chol_upper_kernel<<<1, 1024, 0, st>>>(M, s, info, rel_tol);
   return cudaGetLastError();
 }
 
@@ -420,8 +432,9 @@ __device__ __forceinline__ void jacobi_rot(double app, double aqq, double apq, d
 // The pair indices of a round depend only on (N, r), so every load of the round -- the
 // three entries behind each rotation, the tile's four entries, the V entries -- is issued
 // before any rotation is formed: one memory latency per round instead of three.
-// (Plain pointers: in the persistent form Ain was written by other blocks earlier in the
-// same launch, so its loads must not take the non-coherent read-only path.)
+// In the persistent form Ain and V were written by other blocks earlier in the same launch:
+// their loads go through L2 (__ldcg), never through this SM's L1, which may hold the lines
+// from an earlier round.
 constexpr int JT = 16;
 constexpr int kJacVMax = 4;   // V (row, pair) elements per thread: rows <= kJacVMax * 256 / 16
 struct JacobiRoundSmem {
@@ -441,9 +454,9 @@ __device__ __forceinline__ void jacobi_round(const double* Ain, double* Aout, do
     const int m = (side == 0 ? bx : by) * JT + t;
     if (m < H) {
       rr_pair(N, r, m, rp_, rq_);
-      app = Ain[rp_ + (int64_t)rp_ * N];
-      aqq = Ain[rq_ + (int64_t)rq_ * N];
-      apq = Ain[rp_ + (int64_t)rq_ * N];
+      app = __ldcg(Ain + rp_ + (int64_t)rp_ * N);
+      aqq = __ldcg(Ain + rq_ + (int64_t)rq_ * N);
+      apq = __ldcg(Ain + rp_ + (int64_t)rq_ * N);
       have_rot = true;
     }
   }
@@ -455,10 +468,10 @@ __device__ __forceinline__ void jacobi_round(const double* Ain, double* Aout, do
   if (in_tile) {
     rr_pair(N, r, ma, pa, qa);
     rr_pair(N, r, mb, pb, qb);
-    x_pp = Ain[pa + (int64_t)pb * N];
-    x_pq = Ain[pa + (int64_t)qb * N];
-    x_qp = Ain[qa + (int64_t)pb * N];
-    x_qq = Ain[qa + (int64_t)qb * N];
+    x_pp = __ldcg(Ain + pa + (int64_t)pb * N);
+    x_pq = __ldcg(Ain + pa + (int64_t)qb * N);
+    x_qp = __ldcg(Ain + qa + (int64_t)pb * N);
+    x_qq = __ldcg(Ain + qa + (int64_t)qb * N);
   }
   // V entries: this block's 16 pairs (those of bx) over rows [lo, hi)
   const int npair = min(JT, H - bx * JT);
@@ -479,8 +492,8 @@ __device__ __forceinline__ void jacobi_round(const double* Ain, double* Aout, do
       vrow[c] = row;
       vpi[c] = p;
       vqi[c] = q;
-      vp[c] = V[row + (int64_t)p * N];
-      vq[c] = V[row + (int64_t)q * N];
+      vp[c] = __ldcg(V + row + (int64_t)p * N);
+      vq[c] = __ldcg(V + row + (int64_t)q * N);
     }
   }
   if (threadIdx.x < 2 * JT) {
@@ -524,7 +537,7 @@ __device__ __forceinline__ void jacobi_round(const double* Ain, double* Aout, do
     const int t = e / rows, row = lo + e % rows;
     const int p = sh.rp[0][t], q = sh.rq[0][t];
     const double c = sh.rc[0][t], sn = sh.rs[0][t];
-    const double a = V[row + (int64_t)p * N], bq = V[row + (int64_t)q * N];
+    const double a = __ldcg(V + row + (int64_t)p * N), bq = __ldcg(V + row + (int64_t)q * N);
     V[row + (int64_t)p * N] = c * a - sn * bq;
     V[row + (int64_t)q * N] = sn * a + c * bq;
   }
@@ -576,7 +589,7 @@ __global__ void __launch_bounds__(JT * JT) jacobi_persistent_kernel(double* A0, 
         for (int u = 0; u < 2; ++u)
 #pragma unroll
           for (int v = 0; v < 2; ++v) {
-            const double x = cur[ia[u] + (int64_t)ib[v] * N];
+            const double x = __ldcg(cur + ia[u] + (int64_t)ib[v] * N);
             tot += x * x;
             if (ia[u] != ib[v]) off += x * x;
           }
@@ -604,8 +617,8 @@ __global__ void __launch_bounds__(JT * JT) jacobi_persistent_kernel(double* A0, 
     }
     double o = 0.0, t = 0.0;
     for (int b = 0; b < nblk; ++b) {
-      o += ((volatile double*)part)[2 * b];
-      t += ((volatile double*)part)[2 * b + 1];
+      o += __ldcg(part + 2 * b);
+      t += __ldcg(part + 2 * b + 1);
     }
     // every block has read the partials before any block overwrites them next sweep
     if (!grid_barrier(&ctl[0], &ctl[1], (unsigned)nblk)) {
@@ -621,7 +634,7 @@ __global__ void __launch_bounds__(JT * JT) jacobi_persistent_kernel(double* A0, 
   // leave the diagonalised matrix in A0
   if (cur != A0) {
     for (int64_t idx = (int64_t)bid * blockDim.x + threadIdx.x; idx < (int64_t)N * N; idx += (int64_t)nblk * blockDim.x)
-      A0[idx] = cur[idx];
+      A0[idx] = __ldcg(cur + idx);
   }
 }
 

@@ -144,7 +144,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // generation word in global memory.  The last block to arrive resets the counter and
 // advances the generation; the others wait for the generation to change, at most
 // `cycles` clock64 ticks.  Every thread of every block calls it; returns false (in every
-// thread of the block) when the wait ran out.
+// thread of the block) when the wait ran out.  Data another block wrote before the barrier
+// is read after it through L2 (__ldcg / .cg loads): this SM's L1 may still hold the line
+// from before (measured: plain loads returned stale values).
 __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks,
                                              long long cycles = kWaitCycles) {
   __syncthreads();

@@ -85,8 +85,9 @@ cudaError_t gram_xty(const double* X, const double* Y, int64_t d, int s, double*
                      cudaStream_t st);
 size_t gram_work_bytes(int64_t d, int s);
 // In-place upper Cholesky of a symmetric s x s matrix (col-major): C^T C = M. info[0] = 0 ok,
-// k+1 if the k-th pivot is not positive.  M is symmetrised as (M + M^T)/2 first.
-cudaError_t chol_upper(double* M, int s, int* info, cudaStream_t st);
+// k+1 if the k-th pivot is not positive, or not above rel_tol times the largest diagonal
+// entry of M (numerically dependent columns).  M is symmetrised as (M + M^T)/2 first.
+cudaError_t chol_upper(double* M, int s, int* info, cudaStream_t st, double rel_tol = 0.0);
 // B (d x s) = Y C^{-1} with C upper (s x s); B may alias Y.
 cudaError_t trsm_right_upper(const double* C, int s, double* Y, int64_t d, cudaStream_t st);
 // Y += nu * X  (d x s)

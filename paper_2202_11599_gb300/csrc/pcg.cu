@@ -58,6 +58,51 @@ __device__ __forceinline__ double block_fixed_sum_cg(const double* a, int n, dou
   return r;
 }
 
+// Two fixed-order sums of the same kind as block_fixed_sum_cg in one pass (same values).
+__device__ __forceinline__ void block_fixed_sum2_cg(const double* a, const double* b, int n, double* out_a,
+                                                    double* out_b, double* slot2) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x & 31;
+    double sa = 0.0, sb = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      sa += __ldcg(a + i);
+      sb += __ldcg(b + i);
+    }
+    sa = warp_sum(sa);
+    sb = warp_sum(sb);
+    if (threadIdx.x == 0) {
+      slot2[0] = sa;
+      slot2[1] = sb;
+    }
+  }
+  __syncthreads();
+  *out_a = slot2[0];
+  *out_b = slot2[1];
+  __syncthreads();
+}
+
+// Five block_sum<kVecThreads> reductions with one pair of barriers (same values as five calls).
+__device__ __forceinline__ void block_sum5(double (&v)[5]) {
+  __shared__ double sh5[5][kVecThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < 5; ++t) v[t] = warp_sum(v[t]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int t = 0; t < 5; ++t) sh5[t][w] = v[t];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 5; ++t) {
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < kVecThreads / 32; ++i) s += sh5[t][i];
+    v[t] = s;
+  }
+  __syncthreads();
+}
+
 // Last-block election for a kernel that ends with a grid-wide scalar step: every block
 // calls it after writing its partials; it returns true (to every thread) only in the block
 // that arrived last, which then sees the other blocks' writes, and resets the ticket for
@@ -778,7 +823,6 @@ __global__ void __launch_bounds__(kVecThreads) admm_zu_g_kernel(int64_t d, const
                                                                 int* pcg_it_trace, const PcgState* st,
                                                                 long long nodes_per_iter, long long nodes_per_pcg_iter,
                                                                 cudaGraphConditionalHandle cond) {
-  __shared__ double sh[kVecThreads / 32];
   double* zt = ztrace ? ztrace + (int64_t)ctl->k * d : nullptr;
   double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
   for (int64_t j = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)gridDim.x * kVecThreads) {
@@ -798,18 +842,12 @@ __global__ void __launch_bounds__(kVecThreads) admm_zu_g_kernel(int64_t d, const
     a3 += zj * zj;
     a4 += uj * uj;
   }
-  a0 = block_sum<kVecThreads>(a0, sh);
-  a1 = block_sum<kVecThreads>(a1, sh);
-  a2 = block_sum<kVecThreads>(a2, sh);
-  a3 = block_sum<kVecThreads>(a3, sh);
-  a4 = block_sum<kVecThreads>(a4, sh);
+  double a5[5] = {a0, a1, a2, a3, a4};
+  block_sum5(a5);
   if (threadIdx.x == 0) {
     double* o = part5 + (int64_t)blockIdx.x * 5;
-    o[0] = a0;
-    o[1] = a1;
-    o[2] = a2;
-    o[3] = a3;
-    o[4] = a4;
+#pragma unroll
+    for (int t = 0; t < 5; ++t) o[t] = a5[t];
   }
   // the last block to finish runs the scalar step of the iteration
   if (!last_block_done(&ctl->ticket)) return;
@@ -867,6 +905,7 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
   C* wch = reinterpret_cast<C*>(sm_raw);   // chunk of w (U^T w), then g (y = w + U g)
   __shared__ double sh[kVecThreads / 32];
   __shared__ double slot;
+  __shared__ double slot2[2];
   __shared__ int s_go;
   const int b = blockIdx.x;
   const unsigned nblk = gridDim.x;
@@ -921,29 +960,6 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
         a.part_w2[b] = tw2;
         a.part_r2[b] = tr2;
       }
-      __syncthreads();
-      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-      const int len = (int)(j1 - j0);
-      constexpr int RW = 4;
-      for (int i0 = warp * RW; i0 < s; i0 += (kVecThreads / 32) * RW) {
-        C acc[RW];
-#pragma unroll
-        for (int qq = 0; qq < RW; ++qq) acc[qq] = C(0);
-#pragma unroll 8
-        for (int jj = lane; jj < len; jj += 32) {
-          const C wv = wch[jj];
-#pragma unroll
-          for (int qq = 0; qq < RW; ++qq)
-            if (i0 + qq < s) acc[qq] = fma(U[(int64_t)(i0 + qq) * d + j0 + jj], wv, acc[qq]);
-        }
-#pragma unroll
-        for (int qq = 0; qq < RW; ++qq) acc[qq] = warp_sum(acc[qq]);
-        if (lane == 0) {
-#pragma unroll
-          for (int qq = 0; qq < RW; ++qq)
-            if (i0 + qq < s) a.part_g[(int64_t)b * s + i0 + qq] = (double)acc[qq];
-        }
-      }
     }
     if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, nblk)) return fail();
     if (first && refreshed && b == 0 && threadIdx.x == 0) {
@@ -952,14 +968,43 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
     }
     first = false;
     // ---- 2. stop decision of the warm start (every block, the order of pcg_scalar_body)
-    const double w2 = block_fixed_sum_cg(a.part_w2, a.nb3, &slot);
-    const double r2 = block_fixed_sum_cg(a.part_r2, a.nb3, &slot);
+    double w2, r2;
+    block_fixed_sum2_cg(a.part_w2, a.part_r2, a.nb3, &w2, &r2, slot2);
     const double thresh2 = tol_abs ? tolk * tolk : tolk * tolk * r2;
     const int fixed = a.fixed_dev ? a.fixed_dev[k] : -1;
     const bool nostep = fixed >= 0 ? fixed == 0 : !(w2 > thresh2);
     if (!nostep) {
-      // ---- 3b. P^{-1} w and the PCG state; the PCG WHILE node takes over
-      __syncthreads();
+      // ---- 3b. P^{-1} w and the PCG state; the PCG WHILE node takes over.  U^T w partials
+      // over the blocks' chunks of w (the mapping and order of pcg_update_kernel's init step)
+      if (b < a.nb3) {
+        const int64_t j0 = (int64_t)b * a.chunk;
+        const int64_t j1 = min(d, j0 + a.chunk);
+        for (int64_t j = j0 + threadIdx.x; j < j1; j += kVecThreads) wch[j - j0] = __ldcg(w + j);
+        __syncthreads();
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int len = (int)(j1 - j0);
+        constexpr int RW = 4;
+        for (int i0 = warp * RW; i0 < s; i0 += (kVecThreads / 32) * RW) {
+          C acc[RW];
+#pragma unroll
+          for (int qq = 0; qq < RW; ++qq) acc[qq] = C(0);
+#pragma unroll 8
+          for (int jj = lane; jj < len; jj += 32) {
+            const C wv = wch[jj];
+#pragma unroll
+            for (int qq = 0; qq < RW; ++qq)
+              if (i0 + qq < s) acc[qq] = fma(U[(int64_t)(i0 + qq) * d + j0 + jj], wv, acc[qq]);
+          }
+#pragma unroll
+          for (int qq = 0; qq < RW; ++qq) acc[qq] = warp_sum(acc[qq]);
+          if (lane == 0) {
+#pragma unroll
+            for (int qq = 0; qq < RW; ++qq)
+              if (i0 + qq < s) a.part_g[(int64_t)b * s + i0 + qq] = (double)acc[qq];
+          }
+        }
+      }
+      if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, nblk)) return fail();
       for (int i = threadIdx.x; i < s; i += kVecThreads) {
         double gsum = 0.0;
 #pragma unroll 8
@@ -1026,18 +1071,12 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
         a3 += zj * zj;
         a4 += uj * uj;
       }
-      a0 = block_sum<kVecThreads>(a0, sh);
-      a1 = block_sum<kVecThreads>(a1, sh);
-      a2 = block_sum<kVecThreads>(a2, sh);
-      a3 = block_sum<kVecThreads>(a3, sh);
-      a4 = block_sum<kVecThreads>(a4, sh);
+      double a5[5] = {a0, a1, a2, a3, a4};
+      block_sum5(a5);
       if (threadIdx.x == 0) {
         double* o = a.part5 + (int64_t)b * 5;
-        o[0] = a0;
-        o[1] = a1;
-        o[2] = a2;
-        o[3] = a3;
-        o[4] = a4;
+#pragma unroll
+        for (int t = 0; t < 5; ++t) o[t] = a5[t];
       }
     }
     if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, nblk)) return fail();
