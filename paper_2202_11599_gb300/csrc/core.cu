@@ -21,51 +21,88 @@
 namespace nys {
 
 // ------------------------------------------------------------------ generic small GEMM
-// C(m, n) = sum_k a(m, k) b(k, n), FP64, column-major operands:
+// C(m, n) = sum_k a(m, k) b(k, n), column-major operands:
 //   transA: a(m,k) = A[k + m*lda]   else a(m,k) = A[m + k*lda];   b(k,n) = B[k + n*ldb]
 // Split-K: blockIdx.z handles k in [z*kchunk, min(K,(z+1)*kchunk)); the partial goes to
-// Cp + z*M*N (column-major, ld M).  Tile 64 x 64, 256 threads, 4 x 4 per thread.
+// Cp + z*M*N (column-major, ld M).  Tile 4 TPX x 4 TPX, TPX^2 threads, 4 x 4 per thread;
+// the next GK-deep slab of both operands is loaded into registers while the current one
+// is multiplied.  With `sym` (M == N, A == B) blockIdx.x enumerates only the tiles with
+// bm <= bn; each C(m, n) sums the same products in the same k order as C(n, m) would, so
+// the mirrored lower triangle equals a full computation bit for bit.
 constexpr int GT = 64, GK = 16;
 
-template <typename T>
-__global__ void __launch_bounds__(256) gemm_t_kernel(const T* __restrict__ A, int64_t lda, bool transA,
-                                                     const T* __restrict__ B, int64_t ldb, int M, int N,
-                                                     int64_t K, int64_t kchunk, T* __restrict__ Cp) {
-  __shared__ T As[GK][GT + 1];
-  __shared__ T Bs[GK][GT + 1];
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  const int m0 = blockIdx.x * GT, n0 = blockIdx.y * GT;
+template <typename T, int TPX>
+__global__ void __launch_bounds__(TPX * TPX) gemm_tile_kernel(const T* __restrict__ A, int64_t lda, bool transA,
+                                                              const T* __restrict__ B, int64_t ldb, int M, int N,
+                                                              int64_t K, int64_t kchunk, int sym, T* __restrict__ Cp) {
+  constexpr int TT = 4 * TPX, NT = TPX * TPX;
+  constexpr int LD = (GK * TT + NT - 1) / NT;
+  __shared__ T As[GK][TT + 1];
+  __shared__ T Bs[GK][TT + 1];
+  const int tx = threadIdx.x % TPX, ty = threadIdx.x / TPX;
+  int bm = blockIdx.x, bn = blockIdx.y;
+  if (sym) {
+    int t = blockIdx.x;
+    bn = 0;
+    while (t > bn) {
+      t -= bn + 1;
+      ++bn;
+    }
+    bm = t;
+  }
+  const int m0 = bm * TT, n0 = bn * TT;
   const int64_t kb = (int64_t)blockIdx.z * kchunk;
   const int64_t ke = min(K, kb + kchunk);
-  T acc[4][4] = {};
-  for (int64_t k0 = kb; k0 < ke; k0 += GK) {
-    for (int idx = threadIdx.x; idx < GK * GT; idx += 256) {
-      int kk, mm;
-      if (transA) {
-        kk = idx % GK;
-        mm = idx / GK;
-      } else {
-        mm = idx % GT;
-        kk = idx / GT;
+  T ra[LD], rb[LD];
+  auto load = [&](int64_t k0) {
+#pragma unroll
+    for (int l = 0; l < LD; ++l) {
+      const int idx = threadIdx.x + l * NT;
+      ra[l] = T(0);
+      rb[l] = T(0);
+      if (idx < GK * TT) {
+        int kk, mm;
+        if (transA) {
+          kk = idx % GK;
+          mm = idx / GK;
+        } else {
+          mm = idx % TT;
+          kk = idx / TT;
+        }
+        const int64_t k = k0 + kk;
+        const int m = m0 + mm;
+        if (k < ke && m < M) ra[l] = transA ? A[k + (int64_t)m * lda] : A[m + k * lda];
+        const int nn = idx / GK, kk2 = idx % GK;
+        const int64_t k2 = k0 + kk2;
+        const int n = n0 + nn;
+        if (k2 < ke && n < N) rb[l] = B[k2 + (int64_t)n * ldb];
       }
-      const int64_t k = k0 + kk;
-      const int m = m0 + mm;
-      T v = T(0);
-      if (k < ke && m < M) v = transA ? A[k + (int64_t)m * lda] : A[m + k * lda];
-      As[kk][mm] = v;
-      const int nn = idx / GK, kk2 = idx % GK;
-      const int64_t k2 = k0 + kk2;
-      const int n = n0 + nn;
-      Bs[kk2][nn] = (k2 < ke && n < N) ? B[k2 + (int64_t)n * ldb] : T(0);
     }
+  };
+  auto stage = [&]() {
+#pragma unroll
+    for (int l = 0; l < LD; ++l) {
+      const int idx = threadIdx.x + l * NT;
+      if (idx < GK * TT) {
+        if (transA) As[idx % GK][idx / GK] = ra[l];
+        else As[idx / TT][idx % TT] = ra[l];
+        Bs[idx % GK][idx / GK] = rb[l];
+      }
+    }
+  };
+  T acc[4][4] = {};
+  if (kb < ke) load(kb);
+  for (int64_t k0 = kb; k0 < ke; k0 += GK) {
+    stage();
     __syncthreads();
+    if (k0 + GK < ke) load(k0 + GK);
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
       T a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + TPX * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + TPX * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -78,12 +115,10 @@ __global__ void __launch_bounds__(256) gemm_t_kernel(const T* __restrict__ A, in
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int m = m0 + tx + 16 * i, n = n0 + ty + 16 * j;
+      const int m = m0 + tx + TPX * i, n = n0 + ty + TPX * j;
       if (m < M && n < N) C[m + (int64_t)n * M] = acc[i][j];
     }
 }
-#define gemm_f64_kernel gemm_t_kernel<double>
-
 // C (M x N) = sum_z Cp[z] in a fixed order, compute type T
 template <typename T>
 __global__ void sum_partials_t_kernel(const T* __restrict__ Cp, int nz, int64_t len, T* __restrict__ C) {
@@ -101,7 +136,7 @@ cudaError_t gemm_tn(const T* X, const T* Y, int64_t K, int M, int N, T* C, T* wo
   const int nz = (int)((K + kc - 1) / kc);
   dim3 grid((M + GT - 1) / GT, (N + GT - 1) / GT, nz);
   count_launch();
-  gemm_t_kernel<T><<<grid, 256, 0, st>>>(X, K, true, Y, K, M, N, K, kc, work);
+  gemm_tile_kernel<T, 16><<<grid, 256, 0, st>>>(X, K, true, Y, K, M, N, K, kc, 0, work);
   NYS_CUDA_TRY(cudaGetLastError());
   count_launch();
   sum_partials_t_kernel<T><<<(unsigned)std::min<int64_t>(1024, ((int64_t)M * N + 255) / 256), 256, 0, st>>>(
@@ -118,7 +153,7 @@ template <typename T>
 cudaError_t gemm_nn_t(const T* B, int64_t M, int K, const T* V, int N, T* C, cudaStream_t st) {
   dim3 grid((unsigned)((M + GT - 1) / GT), (N + GT - 1) / GT, 1);
   count_launch();
-  gemm_t_kernel<T><<<grid, 256, 0, st>>>(B, M, false, V, K, (int)M, N, K, K, C);
+  gemm_tile_kernel<T, 16><<<grid, 256, 0, st>>>(B, M, false, V, K, (int)M, N, K, K, 0, C);
   return cudaGetLastError();
 }
 template cudaError_t gemm_tn<float>(const float*, const float*, int64_t, int, int, float*, float*, cudaStream_t);
@@ -128,43 +163,72 @@ template size_t gemm_tn_work_elems<double>(int64_t, int, int);
 template cudaError_t gemm_nn_t<float>(const float*, int64_t, int, const float*, int, float*, cudaStream_t);
 template cudaError_t gemm_nn_t<double>(const double*, int64_t, int, const double*, int, double*, cudaStream_t);
 
-// C = alpha * sum_z Cp[z] (fixed order)
-__global__ void sum_partials_kernel(const double* __restrict__ Cp, int nz, int64_t len, double* __restrict__ C) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int z = 0; z < nz; ++z) s += Cp[z * len + i];
-    C[i] = s;
-  }
+// Gram-type products X^T Y (d x s operands, s x s result) on 40 x 40 tiles (s = 200 and
+// 400 tile exactly; the FP64 pipe, not memory, bounds these products, so padded tiles are
+// wasted time).  The split over d is sized for about kGramCtas CTAs -- a constant, so
+// the summation order, and the result, do not depend on the device -- with chunks of at
+// least 128 rows.
+constexpr int kGramTpx = 10;
+constexpr int kGramTile = 4 * kGramTpx;
+constexpr int kGramCtas = 1216;
+static int gram_tiles(int s, bool sym) {
+  const int tb = (s + kGramTile - 1) / kGramTile;
+  return sym ? tb * (tb + 1) / 2 : tb * tb;
+}
+static int64_t gram_kchunk(int64_t K, int tiles) {
+  const int64_t nz0 = std::max<int64_t>(1, kGramCtas / tiles);
+  const int64_t kc = ((K + nz0 - 1) / nz0 + GK - 1) / GK * GK;
+  return std::max<int64_t>(128, kc);
 }
 
-static int64_t gram_kchunk(int64_t K) { return std::max<int64_t>(256, ((K + 63) / 64 + GK - 1) / GK * GK); }
-
 size_t gram_work_bytes(int64_t d, int s) {
-  const int64_t kc = gram_kchunk(d);
-  const int64_t nz = (d + kc - 1) / kc;
+  int64_t nz = 1;
+  for (int sym = 0; sym < 2; ++sym) {
+    const int64_t kc = gram_kchunk(d, gram_tiles(s, sym != 0));
+    nz = std::max<int64_t>(nz, (d + kc - 1) / kc);
+  }
   return (size_t)nz * s * s * sizeof(double);
 }
 
-// C (s x s) = X^T Y, X and Y d x s column-major (ld d)
+// C = sum_z Cp[z] (fixed order); with `sym` the entries below the diagonal tiles are read
+// from their mirror (the tiles there were not computed).
+__global__ void sum_partials_gram_kernel(const double* __restrict__ Cp, int nz, int s, int sym,
+                                         double* __restrict__ C) {
+  const int64_t len = (int64_t)s * s;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < len;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % s), j = (int)(idx / s);
+    const int64_t src = (sym && i / kGramTile > j / kGramTile) ? j + (int64_t)i * s : idx;
+    double acc = 0.0;
+    for (int z = 0; z < nz; ++z) acc += Cp[z * len + src];
+    C[idx] = acc;
+  }
+}
+
+// C (s x s) = X^T Y, X and Y d x s column-major (ld d); symmetric form when X == Y
 cudaError_t gram_xty(const double* X, const double* Y, int64_t d, int s, double* C, double* work,
                      cudaStream_t st) {
-  const int64_t kc = gram_kchunk(d);
+  const bool sym = X == Y;
+  const int tiles = gram_tiles(s, sym);
+  const int64_t kc = gram_kchunk(d, tiles);
   const int nz = (int)((d + kc - 1) / kc);
-  dim3 grid((s + GT - 1) / GT, (s + GT - 1) / GT, nz);
+  const int tb = (s + kGramTile - 1) / kGramTile;
+  const dim3 grid(sym ? tiles : tb, sym ? 1 : tb, nz);
   count_launch();
-  gemm_f64_kernel<<<grid, 256, 0, st>>>(X, d, true, Y, d, s, s, d, kc, work);
+  gemm_tile_kernel<double, kGramTpx><<<grid, kGramTpx * kGramTpx, 0, st>>>(X, d, true, Y, d, s, s, d, kc, sym ? 1 : 0,
+                                                                          work);
   NYS_CUDA_TRY(cudaGetLastError());
   count_launch();
-  sum_partials_kernel<<<std::min<int64_t>(1024, ((int64_t)s * s + 255) / 256), 256, 0, st>>>(work, nz,
-                                                                                              (int64_t)s * s, C);
+  sum_partials_gram_kernel<<<std::min<int64_t>(1024, ((int64_t)s * s + 255) / 256), 256, 0, st>>>(work, nz, s,
+                                                                                                   sym ? 1 : 0, C);
   return cudaGetLastError();
 }
 
 // C (d x s) = B (d x s) * V (s x s), all column-major
 static cudaError_t gemm_nn(const double* B, int64_t d, int s, const double* V, double* C, cudaStream_t st) {
-  dim3 grid((unsigned)((d + GT - 1) / GT), (s + GT - 1) / GT, 1);
+  dim3 grid((unsigned)((d + kGramTile - 1) / kGramTile), (s + kGramTile - 1) / kGramTile, 1);
   count_launch();
-  gemm_f64_kernel<<<grid, 256, 0, st>>>(B, d, false, V, s, (int)d, s, s, s, C);
+  gemm_tile_kernel<double, kGramTpx><<<grid, kGramTpx * kGramTpx, 0, st>>>(B, d, false, V, s, (int)d, s, s, s, 0, C);
   return cudaGetLastError();
 }
 
@@ -174,15 +238,11 @@ static cudaError_t gemm_nn(const double* B, int64_t d, int s, const double* V, d
 // the k-th pivot is not positive / not finite.
 __global__ void __launch_bounds__(1024) chol_upper_kernel(double* M, int s, int* info, double rel_tol) {
   const int tid = threadIdx.x, T = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarp = T >> 5;
   __shared__ int bad;
   __shared__ double thresh;
-  for (int64_t idx = tid; idx < (int64_t)s * s; idx += T) {
-    const int i = (int)(idx % s), j = (int)(idx / s);
-    if (i < j) {
-      const double v = 0.5 * (M[i + (int64_t)j * s] + M[j + (int64_t)i * s]);
-      M[i + (int64_t)j * s] = v;
-    }
-  }
+  for (int j = warp; j < s; j += nwarp)
+    for (int i = lane; i < j; i += 32) M[i + (int64_t)j * s] = 0.5 * (M[i + (int64_t)j * s] + M[j + (int64_t)i * s]);
   if (tid == 0) {
     bad = 0;
     double mx = 0.0;
@@ -205,21 +265,18 @@ __global__ void __launch_bounds__(1024) chol_upper_kernel(double* M, int s, int*
     for (int c = j + 1 + tid; c < s; c += T) M[j + (int64_t)c * s] /= piv;
     __syncthreads();
     // trailing update of the upper triangle: M[i][c] -= C[j][i] C[j][c], j < i <= c
-    const int w = s - j - 1;
-    for (int64_t idx = tid; idx < (int64_t)w * w; idx += T) {
-      const int i = (int)(idx % w), c = (int)(idx / w);
-      if (i > c) continue;
-      const int ii = j + 1 + i, cc = j + 1 + c;
-      M[ii + (int64_t)cc * s] -= M[j + (int64_t)ii * s] * M[j + (int64_t)cc * s];
+    // (warps over columns c, lanes over rows i: no index division in the inner loop)
+    for (int c = j + 1 + warp; c < s; c += nwarp) {
+      const double rc = M[j + (int64_t)c * s];
+      double* col = M + (int64_t)c * s;
+      for (int i = j + 1 + lane; i <= c; i += 32) col[i] -= M[j + (int64_t)i * s] * rc;
     }
     __syncthreads();
   }
   if (tid == 0) *info = bad;
   // zero the strict lower triangle
-  for (int64_t idx = tid; idx < (int64_t)s * s; idx += T) {
-    const int i = (int)(idx % s), j = (int)(idx / s);
-    if (i > j) M[idx] = 0.0;
-  }
+  for (int j = warp; j < s; j += nwarp)
+    for (int i = j + 1 + lane; i < s; i += 32) M[i + (int64_t)j * s] = 0.0;
 }
 
 // Same algorithm and operation order with the upper triangle held in shared memory
@@ -228,14 +285,13 @@ __global__ void __launch_bounds__(1024) chol_upper_kernel(double* M, int s, int*
 __global__ void __launch_bounds__(1024) chol_upper_smem_kernel(double* M, int s, int* info, double rel_tol) {
   extern __shared__ double up[];
   const int tid = threadIdx.x, T = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarp = T >> 5;
   __shared__ int bad;
   __shared__ double thresh;
   auto at = [](int i, int c) { return c * (c + 1) / 2 + i; };
-  for (int64_t idx = tid; idx < (int64_t)s * s; idx += T) {
-    const int i = (int)(idx % s), j = (int)(idx / s);
-    if (i < j) up[at(i, j)] = 0.5 * (M[i + (int64_t)j * s] + M[j + (int64_t)i * s]);
-    else if (i == j) up[at(i, i)] = M[i + (int64_t)i * s];
-  }
+  for (int j = warp; j < s; j += nwarp)
+    for (int i = lane; i <= j; i += 32)
+      up[at(i, j)] = i < j ? 0.5 * (M[i + (int64_t)j * s] + M[j + (int64_t)i * s]) : M[i + (int64_t)i * s];
   if (tid == 0) {
     bad = 0;
     double mx = 0.0;
@@ -258,20 +314,17 @@ __global__ void __launch_bounds__(1024) chol_upper_smem_kernel(double* M, int s,
     for (int c = j + 1 + tid; c < s; c += T) up[at(j, c)] /= piv;
     __syncthreads();
     // trailing update of the upper triangle: M[i][c] -= C[j][i] C[j][c], j < i <= c
-    const int w = s - j - 1;
-    for (int64_t idx = tid; idx < (int64_t)w * w; idx += T) {
-      const int i = (int)(idx % w), c = (int)(idx / w);
-      if (i > c) continue;
-      const int ii = j + 1 + i, cc = j + 1 + c;
-      up[at(ii, cc)] -= up[at(j, ii)] * up[at(j, cc)];
+    // (warps over columns c, lanes over rows i: no index division in the inner loop)
+    for (int c = j + 1 + warp; c < s; c += nwarp) {
+      const double rc = up[at(j, c)];
+      double* col = up + at(0, c);
+      for (int i = j + 1 + lane; i <= c; i += 32) col[i] -= up[at(j, i)] * rc;
     }
     __syncthreads();
   }
   if (tid == 0) *info = bad;
-  for (int64_t idx = tid; idx < (int64_t)s * s; idx += T) {
-    const int i = (int)(idx % s), j = (int)(idx / s);
-    M[idx] = i <= j ? up[at(i, j)] : 0.0;
-  }
+  for (int j = warp; j < s; j += nwarp)
+    for (int i = lane; i < s; i += 32) M[i + (int64_t)j * s] = i <= j ? up[at(i, j)] : 0.0;
 }
 
 cudaError_t chol_upper(double* M, int s, int* info, cudaStream_t st, double rel_tol) {
@@ -320,7 +373,78 @@ __global__ void __launch_bounds__(kTrsmRows) trsm_ru_smem_kernel(const double* _
   }
 }
 
+// Same recurrence and order again, blocked by columns so that most of the work runs on
+// every thread: a CTA holds R rows of Y in shared memory ([c][R]); for each block of 32
+// columns it first subtracts sum_{k < j0} b_k C[k][c] from all R x 32 entries (4 R
+// threads, each row's k in ascending order), then one thread per row finishes the block
+// (k from j0 to c - 1, then the division).  Every entry sees the same fma sequence as in
+// trsm_ru_kernel, so the result is bitwise the same.  R = ceil(d / #SMs): one wave.
+constexpr int kTrsmBlk = 32;
+__global__ void __launch_bounds__(1024) trsm_ru_blocked_kernel(const double* __restrict__ Cm, int s, double* Y,
+                                                               int64_t d, int R) {
+  extern __shared__ double bs[];  // [s][R]
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  const int nr = (int)min((int64_t)R, d - r0);
+  for (int idx = threadIdx.x; idx < s * R; idx += blockDim.x) {
+    const int c = idx / R, r = idx % R;
+    bs[idx] = r < nr ? Y[r0 + r + (int64_t)c * d] : 0.0;
+  }
+  __syncthreads();
+  const int r = threadIdx.x % R, cg = threadIdx.x / R;
+  for (int j0 = 0; j0 < s; j0 += kTrsmBlk) {
+    const int j1 = min(s, j0 + kTrsmBlk);
+    if (cg < 4 && j0 > 0) {
+      double acc[kTrsmBlk / 4];
+#pragma unroll
+      for (int q = 0; q < kTrsmBlk / 4; ++q) {
+        const int c = j0 + cg + 4 * q;
+        acc[q] = c < j1 ? bs[c * R + r] : 0.0;
+      }
+      for (int k = 0; k < j0; ++k) {
+        const double bk = bs[k * R + r];
+#pragma unroll
+        for (int q = 0; q < kTrsmBlk / 4; ++q) {
+          const int c = j0 + cg + 4 * q;
+          if (c < j1) acc[q] = fma(-bk, __ldg(Cm + k + (int64_t)c * s), acc[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kTrsmBlk / 4; ++q) {
+        const int c = j0 + cg + 4 * q;
+        if (c < j1) bs[c * R + r] = acc[q];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < R) {
+      for (int c = j0; c < j1; ++c) {
+        const double* col = Cm + (int64_t)c * s;
+        double acc = bs[c * R + r];
+        for (int k = j0; k < c; ++k) acc = fma(-bs[k * R + r], __ldg(col + k), acc);
+        bs[c * R + r] = acc / __ldg(col + c);
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < s * R; idx += blockDim.x) {
+    const int c = idx / R, rr = idx % R;
+    if (rr < nr) Y[r0 + rr + (int64_t)c * d] = bs[idx];
+  }
+}
+
 cudaError_t trsm_right_upper(const double* C, int s, double* Y, int64_t d, cudaStream_t st) {
+  {
+    int R = (int)std::min<int64_t>(128, (d + sm_count() - 1) / sm_count());
+    R = std::max(R, 1);
+    while (R > 8 && (size_t)s * R * sizeof(double) > 200 * 1024) R /= 2;
+    const size_t smem_b = (size_t)s * R * sizeof(double);
+    if (R >= 8 && smem_b <= 200 * 1024) {
+      NYS_CUDA_TRY(ensure_max_dyn_smem((const void*)trsm_ru_blocked_kernel, 200 * 1024));
+      const int threads = (4 * R + 31) / 32 * 32;
+      count_launch();
+      trsm_ru_blocked_kernel<<<(unsigned)((d + R - 1) / R), threads, smem_b, st>>>(C, s, Y, d, R);
+      return cudaGetLastError();
+    }
+  }
   const size_t smem = (size_t)s * kTrsmRows * sizeof(double);
   if (smem <= 200 * 1024) {
     NYS_CUDA_TRY(ensure_max_dyn_smem((const void*)trsm_ru_smem_kernel, 200 * 1024));
@@ -345,56 +469,76 @@ cudaError_t axpy_panel(double nu, const double* X, double* Y, int64_t n, cudaStr
 }
 
 // ------------------------------------------------------------------ power iteration (lambda_max)
-__global__ void __launch_bounds__(512) power_kernel(const double* __restrict__ G, int s, int iters,
-                                                    double* out, double* v) {
-  __shared__ double sh[16];
-  const int tid = threadIdx.x;
-  for (int i = tid; i < s; i += 512) v[i] = 1.0 + 1e-3 * (double)(i % 7);  // deterministic start
+// 30 power iterations on the symmetric s x s Gram matrix G (column-major; row i is column
+// i).  One SM's FP64 pipe (about 2 FMA per clock) would need ~10 us per s = 200 matvec, so
+// the rows are spread over kPowBlocks co-resident blocks (cooperative launch): block b
+// forms w_i for its rows (one warp per row, lanes over k, then a warp sum), writes them,
+// and after a grid barrier every block reads all of w through L2 and takes the same
+// fixed-order norms, so every block holds the same v.  lam = the Rayleigh quotient
+// v^T G v / v^T v of the last iterate.
+constexpr int kPowThreads = 256;
+__global__ void __launch_bounds__(kPowThreads) power_kernel(const double* __restrict__ G, int s, int iters,
+                                                            double* out, double* wbuf, unsigned* bar) {
+  __shared__ double sh[kPowThreads / 32];
+  extern __shared__ double vs[];   // v (s)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = kPowThreads / 32;
+  const int rows_per = (s + gridDim.x - 1) / gridDim.x;
+  const int i_lo = blockIdx.x * rows_per, i_hi = min(s, i_lo + rows_per);
+  // a barrier that runs out leaves NaN here: the shift, and with it the factorisation, fails
+  if (blockIdx.x == 0 && tid == 0) *out = __longlong_as_double(0x7ff8000000000000LL);
+  for (int i = tid; i < s; i += kPowThreads) vs[i] = 1.0 + 1e-3 * (double)(i % 7);  // deterministic start
   __syncthreads();
   double lam = 0.0;
+  unsigned target = 0;
   for (int it = 0; it < iters; ++it) {
-    // w = G v (row i: sum_k G[i + k s] v_k), normalised
-    double loc = 0.0;
-    double wi[2] = {0.0, 0.0};
-    for (int r = 0; r < 2; ++r) {
-      const int i = tid + r * 512;
-      if (i < s) {
-        double acc = 0.0;
-        for (int k = 0; k < s; ++k) acc = fma(G[i + (int64_t)k * s], v[k], acc);
-        wi[r] = acc;
-      }
+    double* w = wbuf + (size_t)(it & 1) * s;   // alternate buffers: no block overwrites a w still being read
+    for (int i = i_lo + warp; i < i_hi; i += NW) {
+      const double* col = G + (int64_t)i * s;
+      double acc = 0.0;
+      for (int k = lane; k < s; k += 32) acc = fma(__ldg(col + k), vs[k], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) w[i] = acc;
     }
-    // Rayleigh quotient numerator v^T G v and ||w||^2
-    for (int r = 0; r < 2; ++r) {
-      const int i = tid + r * 512;
-      if (i < s) loc += v[i] * wi[r];
+    target += gridDim.x;
+    if (!grid_barrier_mono(bar, target)) {
+      if (tid == 0) atomicExch(bar + 1, 1u);
+      return;
     }
-    const double num = block_sum<512>(loc, sh);
-    double l2 = 0.0;
-    for (int r = 0; r < 2; ++r) l2 += wi[r] * wi[r];
-    const double nw2 = block_sum<512>(l2, sh);
-    double vv = 0.0;
-    for (int r = 0; r < 2; ++r) {
-      const int i = tid + r * 512;
-      if (i < s) vv += v[i] * v[i];
+    double num = 0.0, l2 = 0.0, vv = 0.0;
+    for (int i = tid; i < s; i += kPowThreads) {
+      const double wi = __ldcg(w + i);
+      num += vs[i] * wi;
+      l2 += wi * wi;
+      vv += vs[i] * vs[i];
     }
-    const double nv2 = block_sum<512>(vv, sh);
+    num = block_sum<kPowThreads>(num, sh);
+    const double nw2 = block_sum<kPowThreads>(l2, sh);
+    const double nv2 = block_sum<kPowThreads>(vv, sh);
     lam = num / nv2;
-    __syncthreads();
     const double inv = nw2 > 0 ? 1.0 / sqrt(nw2) : 0.0;
-    for (int r = 0; r < 2; ++r) {
-      const int i = tid + r * 512;
-      if (i < s) v[i] = wi[r] * inv;
-    }
+    for (int i = tid; i < s; i += kPowThreads) vs[i] = __ldcg(w + i) * inv;
     __syncthreads();
   }
-  if (tid == 0) *out = lam;
+  if (blockIdx.x == 0 && tid == 0) *out = lam;
 }
 
+// work: 2 s doubles + 2 words (barrier counter, timeout flag)
 cudaError_t power_lambda_max(const double* G, int s, double* out, double* work, cudaStream_t st) {
-  if (s > 1024) return cudaErrorInvalidValue;
+  if (s > 4096) return cudaErrorInvalidValue;
+  unsigned* bar = reinterpret_cast<unsigned*>(work + 2 * (size_t)s);
+  NYS_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
+  int per_sm = 0;
+  NYS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, power_kernel, kPowThreads,
+                                                             (size_t)s * sizeof(double)));
+  const int nb = std::max(1, std::min({(s + 7) / 8, 64, per_sm * sm_count()}));
+  int iters = 30;
+  const double* g = G;
+  double* w = work;
+  void* args[] = {(void*)&g, (void*)&s, (void*)&iters, (void*)&out, (void*)&w, (void*)&bar};
   count_launch();
-  power_kernel<<<1, 512, 0, st>>>(G, s, 30, out, work);
+  NYS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)power_kernel, dim3(nb), dim3(kPowThreads), args,
+                                           (size_t)s * sizeof(double), st));
   return cudaGetLastError();
 }
 
@@ -435,22 +579,26 @@ __device__ __forceinline__ void jacobi_rot(double app, double aqq, double apq, d
 // In the persistent form Ain and V were written by other blocks earlier in the same launch:
 // their loads go through L2 (__ldcg), never through this SM's L1, which may hold the lines
 // from an earlier round.
-constexpr int JT = 16;
+// 8 x 8 pair-blocks per tile: s = 200 gives 13 x 13 = 169 tiles, so a round's FP64
+// rotations (the pipe runs about 2 FMA per clock per SM) spread over every SM.
+constexpr int JT = 8;
 constexpr int kJacVMax = 4;   // V (row, pair) elements per thread: rows <= kJacVMax * 256 / 16
 struct JacobiRoundSmem {
   double rc[2][JT], rs[2][JT];
   int rp[2][JT], rq[2][JT];
 };
-__device__ __forceinline__ void jacobi_round(const double* Ain, double* Aout, double* V, int N, int r, int bx, int by,
-                                             int gy, JacobiRoundSmem& sh) {
+// `tid` is the thread's index among the tile's JT * JT threads and `sync` their barrier.
+template <int VMAX, typename Sync>
+__device__ __forceinline__ void jacobi_round_t(const double* Ain, double* Aout, double* V, int N, int r, int bx, int by,
+                                               int gy, JacobiRoundSmem& sh, const int tid, Sync sync) {
   const int H = N / 2;
-  const int tx = threadIdx.x % JT, ty = threadIdx.x / JT;
+  const int tx = tid % JT, ty = tid / JT;
   // rotation inputs (threads < 32)
   int rp_ = 0, rq_ = 1;
   double app = 0.0, aqq = 0.0, apq = 0.0;
   bool have_rot = false;
-  if (threadIdx.x < 2 * JT) {
-    const int side = threadIdx.x / JT, t = threadIdx.x % JT;
+  if (tid < 2 * JT) {
+    const int side = tid / JT, t = tid % JT;
     const int m = (side == 0 ? bx : by) * JT + t;
     if (m < H) {
       rr_pair(N, r, m, rp_, rq_);
@@ -478,11 +626,11 @@ __device__ __forceinline__ void jacobi_round(const double* Ain, double* Aout, do
   const int lo = (int)((int64_t)N * by / gy), hi = (int)((int64_t)N * (by + 1) / gy);
   const int rows = hi - lo;
   const int nel = npair > 0 ? npair * rows : 0;
-  double vp[kJacVMax], vq[kJacVMax];
-  int vrow[kJacVMax], vpi[kJacVMax], vqi[kJacVMax], vt[kJacVMax];
+  double vp[VMAX], vq[VMAX];
+  int vrow[VMAX], vpi[VMAX], vqi[VMAX], vt[VMAX];
 #pragma unroll
-  for (int c = 0; c < kJacVMax; ++c) {
-    const int e = threadIdx.x + c * JT * JT;
+  for (int c = 0; c < VMAX; ++c) {
+    const int e = tid + c * JT * JT;
     vt[c] = -1;
     if (e < nel) {
       const int t = e / rows, row = lo + e % rows;
@@ -496,8 +644,8 @@ __device__ __forceinline__ void jacobi_round(const double* Ain, double* Aout, do
       vq[c] = __ldcg(V + row + (int64_t)q * N);
     }
   }
-  if (threadIdx.x < 2 * JT) {
-    const int side = threadIdx.x / JT, t = threadIdx.x % JT;
+  if (tid < 2 * JT) {
+    const int side = tid / JT, t = tid % JT;
     double c = 1.0, sn = 0.0;
     if (have_rot) jacobi_rot(app, aqq, apq, c, sn);
     sh.rc[side][t] = c;
@@ -505,7 +653,7 @@ __device__ __forceinline__ void jacobi_round(const double* Ain, double* Aout, do
     sh.rp[side][t] = rp_;
     sh.rq[side][t] = rq_;
   }
-  __syncthreads();
+  sync();
   if (in_tile) {
     const double ca = sh.rc[0][tx], sa = sh.rs[0][tx], cb = sh.rc[1][ty], sb = sh.rs[1][ty];
     // columns: p' = c p - s q, q' = s p + c q
@@ -525,15 +673,15 @@ __device__ __forceinline__ void jacobi_round(const double* Ain, double* Aout, do
   }
   // V <- V J (the pairs of a round are disjoint: every (row, pair) element is independent)
 #pragma unroll
-  for (int c = 0; c < kJacVMax; ++c) {
+  for (int c = 0; c < VMAX; ++c) {
     if (vt[c] >= 0) {
       const double cc = sh.rc[0][vt[c]], sn = sh.rs[0][vt[c]];
       V[vrow[c] + (int64_t)vpi[c] * N] = cc * vp[c] - sn * vq[c];
       V[vrow[c] + (int64_t)vqi[c] * N] = sn * vp[c] + cc * vq[c];
     }
   }
-  // elements beyond kJacVMax per thread (only for very tall slices): the plain loop
-  for (int e = threadIdx.x + kJacVMax * JT * JT; e < nel; e += JT * JT) {
+  // elements beyond VMAX per thread (only for very tall slices): the plain loop
+  for (int e = tid + VMAX * JT * JT; e < nel; e += JT * JT) {
     const int t = e / rows, row = lo + e % rows;
     const int p = sh.rp[0][t], q = sh.rq[0][t];
     const double c = sh.rc[0][t], sn = sh.rs[0][t];
@@ -541,6 +689,11 @@ __device__ __forceinline__ void jacobi_round(const double* Ain, double* Aout, do
     V[row + (int64_t)p * N] = c * a - sn * bq;
     V[row + (int64_t)q * N] = sn * a + c * bq;
   }
+}
+
+__device__ __forceinline__ void jacobi_round(const double* Ain, double* Aout, double* V, int N, int r, int bx, int by,
+                                             int gy, JacobiRoundSmem& sh) {
+  jacobi_round_t<kJacVMax>(Ain, Aout, V, N, r, bx, by, gy, sh, (int)threadIdx.x, [] { __syncthreads(); });
 }
 
 __global__ void __launch_bounds__(JT * JT) jacobi_round_kernel(const double* __restrict__ Ain, double* __restrict__ Aout,
@@ -567,10 +720,12 @@ __global__ void __launch_bounds__(JT * JT) jacobi_persistent_kernel(double* A0, 
   double* cur = A0;
   double* nxt = A1;
   int sweeps = 0;
+  unsigned target = 0;
   for (; sweeps < max_sweeps; ++sweeps) {
     for (int r = 0; r < N - 1; ++r) {
       jacobi_round(cur, nxt, V, N, r, blockIdx.x, blockIdx.y, gridDim.y, sh);
-      if (!grid_barrier(&ctl[0], &ctl[1], (unsigned)nblk)) {
+      target += (unsigned)nblk;
+      if (!grid_barrier_mono(&ctl[0], target)) {
         if (threadIdx.x == 0) atomicExch(&ctl[3], 1u);
         return;
       }
@@ -611,7 +766,8 @@ __global__ void __launch_bounds__(JT * JT) jacobi_persistent_kernel(double* A0, 
       part[2 * bid] = o;
       part[2 * bid + 1] = t;
     }
-    if (!grid_barrier(&ctl[0], &ctl[1], (unsigned)nblk)) {
+    target += (unsigned)nblk;
+    if (!grid_barrier_mono(&ctl[0], target)) {
       if (threadIdx.x == 0) atomicExch(&ctl[3], 1u);
       return;
     }
@@ -621,7 +777,8 @@ __global__ void __launch_bounds__(JT * JT) jacobi_persistent_kernel(double* A0, 
       t += __ldcg(part + 2 * b + 1);
     }
     // every block has read the partials before any block overwrites them next sweep
-    if (!grid_barrier(&ctl[0], &ctl[1], (unsigned)nblk)) {
+    target += (unsigned)nblk;
+    if (!grid_barrier_mono(&ctl[0], target)) {
       if (threadIdx.x == 0) atomicExch(&ctl[3], 1u);
       return;
     }
@@ -671,7 +828,7 @@ __global__ void jacobi_setup_kernel(const double* __restrict__ G, int s, double*
 
 size_t jacobi_work_bytes(int s) {
   const int N = s + (s & 1);
-  const int HT = (N / 2 + 15) / 16;
+  const int HT = (N / 2 + JT - 1) / JT;
   // A0, A1, spare N x N, flags, per-block partials of the persistent form, its barrier words
   return (size_t)3 * N * N * sizeof(double) + 64 + (size_t)2 * HT * HT * sizeof(double) + 64;
 }
@@ -692,7 +849,8 @@ cudaError_t jacobi_eig(double* G, double* Vout, int s, double* work, int* sweeps
   const dim3 blocks(HT, HT);
   const int kMaxSweeps = 30;
   // one cooperative launch for all sweeps when the grid can be co-resident
-  const char* jp = std::getenv("NYS_JACOBI_PERSISTENT");   // "0" selects the round-per-launch form
+  // (NYS_JACOBI_PERSISTENT=0 selects the round-per-launch form)
+  const char* jp = std::getenv("NYS_JACOBI_PERSISTENT");
   if (N > 2 && (jp == nullptr || std::atoi(jp) != 0)) {
     int dev = 0, coop = 0, per_sm = 0;
     NYS_CUDA_TRY(cudaGetDevice(&dev));

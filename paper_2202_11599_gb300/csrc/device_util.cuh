@@ -173,6 +173,30 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
   return __syncthreads_and(ok) != 0;
 }
 
+// Grid barrier on one monotonic counter: every block adds 1 and waits until the counter
+// reaches `target` (= blocks x barriers passed so far, kept by the caller; the counter
+// starts at 0 and wraps harmlessly).  One atomic per block and no release write, so it
+// costs about one L2 round trip less than grid_barrier.  Same memory rules: data that
+// other blocks wrote before the barrier is read through L2 (__ldcg) after it.
+__device__ __forceinline__ bool grid_barrier_mono(unsigned* count, unsigned target, long long cycles = kWaitCycles) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    volatile unsigned* vc = count;
+    const long long t0 = clock64();
+    while ((int)(*vc - target) < 0) {
+      if (clock64() - t0 > cycles) {
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -962,10 +962,7 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
       }
     }
     if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, nblk)) return fail();
-    if (first && refreshed && b == 0 && threadIdx.x == 0) {
-      ctl->hx_pending = 0;
-      cudaGraphSetConditional(a.h_hx, 0u);
-    }
+    if (first && refreshed && b == 0 && threadIdx.x == 0) ctl->hx_pending = 0;
     first = false;
     // ---- 2. stop decision of the warm start (every block, the order of pcg_scalar_body)
     double w2, r2;
@@ -1044,6 +1041,7 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
         st->ticket[0] = 0u;
         st->ticket[1] = 0u;
         ctl->nodes += 1;
+        cudaGraphSetConditional(a.h_hx, 0u);
         cudaGraphSetConditional(a.h_pcg, 1u);
         cudaGraphSetConditional(a.h_zu, 1u);
       }
@@ -1115,6 +1113,7 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
       if (b == 0 && threadIdx.x == 0) {
         ctl->nodes += 1;
         cudaGraphSetConditional(a.h_admm, 0u);
+        cudaGraphSetConditional(a.h_hx, 0u);
         cudaGraphSetConditional(a.h_pcg, 0u);
         cudaGraphSetConditional(a.h_zu, 0u);
       }
@@ -1276,10 +1275,12 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   aa.mode = g.pb.D ? MODE_DIAG : MODE_ID;
 
   // Fast body (tracked warm start, no refined step or warm-start model, a single instance):
-  //   IF (h_hx) [ (H + rho I) x recompute ] -> admm_head_kernel (cooperative) ->
+  //   admm_head_kernel (cooperative) -> IF (h_hx) [ (H + rho I) x recompute ] ->
   //   WHILE (h_pcg) [ A-pass, reduce, update, P^{-1} tail ] -> IF (h_zu) [ prox / dual + scalars ]
   // The head kernel runs the iterations that need no PCG step itself and prepares the PCG
-  // state of the others.  NYS_ADMM_NOSTEP=0 selects the general body for every solve.
+  // state of the others; when the recompute is due it sets only h_hx and returns, and the
+  // next pass of the body continues that iteration.  It sets all three conditionals on every
+  // exit (their handles have no default value).  NYS_ADMM_NOSTEP=0 selects the general body.
   {
     const bool use_model = (g.warm || g.warm_record) && s > 0;
     const char* env = std::getenv("NYS_ADMM_NOSTEP");
@@ -1308,19 +1309,10 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
         *child = np.conditional.phGraph_out[0];
         return ce;
       };
-      // IF (h_hx): (H + rho I) x with one pass over A
-      cudaGraphNode_t n_hx;
-      cudaGraph_t hbody;
-      G_OK(add_cond(h_hx, cudaGraphCondTypeIf, {}, &n_hx, &hbody));
+      // head kernel first: it sets every conditional of the body (the handles carry no
+      // default, so no conditional node may be evaluated before the kernel has run)
       count_launch_suspend(true);
-      G_OK(cudaStreamBeginCaptureToGraph(cap, hbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-      aa.p = xc;
-      aa.skip = nullptr;
-      G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, true));
-      G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho + g.mu, hx, nullptr, 0, cap));
-      G_OK(cudaStreamEndCapture(cap, &hbody));
-      // head kernel
-      G_OK(cudaStreamBeginCaptureToGraph(cap, body, &n_hx, nullptr, 1, cudaStreamCaptureModeRelaxed));
+      G_OK(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
       HeadArgs ha;
       ha.d = d;
       ha.chunk = chunk;
@@ -1376,10 +1368,20 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
       G_OK(cudaStreamGetCaptureInfo(cap, &cst0, nullptr, nullptr, &deps0, nullptr, &ndeps0));
       std::vector<cudaGraphNode_t> leaf0(deps0, deps0 + ndeps0);
       G_OK(cudaStreamEndCapture(cap, &body));
+      // IF (h_hx): (H + rho I) x with one pass over A, when the head kernel asked for it
+      cudaGraphNode_t n_hx;
+      cudaGraph_t hbody;
+      G_OK(add_cond(h_hx, cudaGraphCondTypeIf, leaf0, &n_hx, &hbody));
+      G_OK(cudaStreamBeginCaptureToGraph(cap, hbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      aa.p = xc;
+      aa.skip = nullptr;
+      G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, true));
+      G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho + g.mu, hx, nullptr, 0, cap));
+      G_OK(cudaStreamEndCapture(cap, &hbody));
       // WHILE (h_pcg): PCG iterations
       cudaGraphNode_t n_pcg;
       cudaGraph_t pbody;
-      G_OK(add_cond(h_pcg, cudaGraphCondTypeWhile, leaf0, &n_pcg, &pbody));
+      G_OK(add_cond(h_pcg, cudaGraphCondTypeWhile, {n_hx}, &n_pcg, &pbody));
       G_OK(cudaStreamBeginCaptureToGraph(cap, pbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
       aa.p = p;
       aa.skip = &st->done;
