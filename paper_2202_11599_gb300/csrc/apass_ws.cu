@@ -69,9 +69,10 @@ __global__ void __launch_bounds__((3 * G + 2) * 32, 1) apass_ws64_kernel(const A
       const double* p = reinterpret_cast<const double*>(a.p);
       const bool p16 = (reinterpret_cast<uintptr_t>(p) & 15u) == 0;   // 16-byte loads allowed
       const int nv_dot = (nvec + TG - 1) / TG;
-      for (int k = 0; k < nsteps; ++k) {
-        const int st = k % S;
-        if (!warp_wait(&bars.full[st], (uint32_t)((k / S) & 1))) {
+      int st = 0;
+      uint32_t ph = 0;
+      for (int k = 0; k < nsteps; ++k, st = st + 1 == S ? 0 : st + 1, ph ^= st == 0 ? 1u : 0u) {
+        if (!warp_wait(&bars.full[st], ph)) {
           *abort_v = 1;
           break;
         }
@@ -119,9 +120,9 @@ __global__ void __launch_bounds__((3 * G + 2) * 32, 1) apass_ws64_kernel(const A
     const int j = tid - TG;
 #pragma unroll
     for (int kk = 0; kk < VPT; ++kk) acc[kk] = make_double2(0.0, 0.0);
-    for (int k = 0; k < nsteps; ++k) {
-      const int st = k % S;
-      const uint32_t ph = (uint32_t)((k / S) & 1);
+    int st = 0;
+    uint32_t ph = 0;
+    for (int k = 0; k < nsteps; ++k, st = st + 1 == S ? 0 : st + 1, ph ^= st == 0 ? 1u : 0u) {
       if (!warp_wait(&bars.ready[st], ph) || !warp_wait(&bars.full[st], ph)) {
         *abort_v = 1;
         break;

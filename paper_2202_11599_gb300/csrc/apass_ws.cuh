@@ -1,7 +1,7 @@
 // The warp-specialised fused A-pass as device code: y = A^T phi(A p) with one read of A
-// (Table 1's T_mv, the H-matvec of Alg. Nystrom PCG).  Used by the pass kernels of
-// apass_ws.cu (one pass per launch) and by the fused ADMM loop kernel (many passes per
-// launch: the stage ring and its barriers carry on from pass to pass).
+// (Table 1's T_mv, the H-matvec of Alg. Nystrom PCG), used by the pass kernels of
+// apass_ws.cu.  The roles take a stage offset (`kbase`) so that a kernel running several
+// passes could carry the stage ring and its barrier phases on from pass to pass.
 //
 // The step of the classic pass makes every warp of the CTA wait twice per group of R
 // rows for the cross-warp reduction of the row dots.  Here the CTA is split into roles
@@ -89,10 +89,12 @@ __device__ __forceinline__ int ws_produce(const ApassKArgs& a, WsBars& b, unsign
   const uint64_t pol = l2_evict_first_policy();  // A is streamed once per pass
   const uint32_t stage_bytes = (uint32_t)R * rowbytes;
   int issued = 0;
-  for (int k = 0; k < nsteps; ++k) {
+  // ring slot and barrier phase of stage kbase + k, advanced without a division per stage
+  int st = kbase % S;
+  uint32_t ph = (uint32_t)((kbase / S) & 1);
+  for (int k = 0; k < nsteps; ++k, st = st + 1 == S ? 0 : st + 1, ph ^= st == 0 ? 1u : 0u) {
     const int kg = kbase + k;
-    const int st = kg % S;
-    if (kg >= S && !mbar_wait_bounded(&b.empty[st], (uint32_t)(((kg / S) - 1) & 1))) {
+    if (kg >= S && !mbar_wait_bounded(&b.empty[st], ph ^ 1u)) {
       *abort_flag = 1;
       break;
     }
@@ -114,9 +116,9 @@ __device__ __forceinline__ double ws_finish(const ApassKArgs& a, WsBars& b, cons
   const int lane = threadIdx.x & 31;
   const bool nodot = a.mode == MODE_CONST;
   double loss = 0.0;
-  for (int k = 0; k < nsteps; ++k) {
-    const int st = (kbase + k) % S;
-    const uint32_t ph = (uint32_t)(((kbase + k) / S) & 1);
+  int st = kbase % S;
+  uint32_t ph = (uint32_t)((kbase / S) & 1);
+  for (int k = 0; k < nsteps; ++k, st = st + 1 == S ? 0 : st + 1, ph ^= st == 0 ? 1u : 0u) {
     const int64_t row0 = r0 + (int64_t)k * R;
     const int rows_here = (int)min((int64_t)R, r1 - row0);
     // the row's mode input (D_i or b_i) is loaded before the waits
@@ -152,23 +154,11 @@ __device__ __forceinline__ double ws_finish(const ApassKArgs& a, WsBars& b, cons
 }
 
 
-// Where the dot warps take p_j (read once per pass into registers): a vector written by
-// an earlier launch (plain loads), one written by other CTAs of the running launch (read
-// through L2), or the next PCG direction y + beta p formed on the fly from two such
-// vectors -- fmaf(beta, p_j, y_j), the value the CTA that owns j stores as the new p_j.
+// Where the dot warps take p_j (read once per pass into registers): a vector written by an
+// earlier launch.
 struct PSrcPlain {
   const float* p;
   __device__ __forceinline__ float operator()(int64_t e) const { return p[e]; }
-};
-struct PSrcL2 {
-  const float* p;
-  __device__ __forceinline__ float operator()(int64_t e) const { return __ldcg(p + e); }
-};
-struct PSrcAxpy {
-  const float* y;
-  const float* p;
-  float beta;
-  __device__ __forceinline__ float operator()(int64_t e) const { return fmaf(beta, __ldcg(p + e), __ldcg(y + e)); }
 };
 
 // Shared state of the float pass (beside the dynamic-memory stage ring).
@@ -196,14 +186,9 @@ __device__ __forceinline__ bool ws_pass_float(const ApassKArgs& a, WsFloatSmem<R
   constexpr int TG = 32 * G;
   WsBars& bars = sm.bars;
   const int ts_slot = timer_begin(a);
-  // the pass's shape values are re-derived on every call: when the pass runs in a loop
-  // (the fused ADMM kernel) the compiler must not hoist them out of it, where they would
-  // stay live next to the loop's own state and push the roles' loops into spills
-  int tid_o = threadIdx.x;
-  int64_t n_o = a.n, d_o = a.d, ld_o = a.ld;
-  int S_o = a.S;
-  asm volatile("" : "+r"(tid_o), "+l"(n_o), "+l"(d_o), "+l"(ld_o), "+r"(S_o));
-  const int tid = tid_o, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t n_o = a.n, d_o = a.d, ld_o = a.ld;
+  const int S_o = a.S;
   const int nvec = (int)((d_o + VEC - 1) / VEC);
   const uint32_t rowbytes = (uint32_t)(ld_o * ESZ);
   const int S = S_o;
@@ -236,19 +221,20 @@ __device__ __forceinline__ bool ws_pass_float(const ApassKArgs& a, WsFloatSmem<R
           const int64_t e = (int64_t)v * VEC + 2 * q;
           float x0 = 0.f, x1 = 0.f;
           if (v < nvec) {
-            if (e < a.d) x0 = psrc(e);
-            if (e + 1 < a.d) x1 = psrc(e + 1);
+            if (e < d_o) x0 = psrc(e);
+            if (e + 1 < d_o) x1 = psrc(e + 1);
             if (DT == NYS_FP8E4M3) {  // A_ij = s_j q_ij: a_i . p = q_i . (s o p)
-              if (e < a.d) x0 *= a.col_scale[e];
-              if (e + 1 < a.d) x1 *= a.col_scale[e + 1];
+              if (e < d_o) x0 *= a.col_scale[e];
+              if (e + 1 < d_o) x1 *= a.col_scale[e + 1];
             }
           }
           pr[kk][q] = make_float2(x0, x1);
         }
       }
-      for (int k = 0; k < nsteps; ++k) {
-        const int st = (kbase + k) % S;
-        if (!warp_wait(&bars.full[st], (uint32_t)(((kbase + k) / S) & 1))) {
+      int st = kbase % S;
+      uint32_t ph = (uint32_t)((kbase / S) & 1);
+      for (int k = 0; k < nsteps; ++k, st = st + 1 == S ? 0 : st + 1, ph ^= st == 0 ? 1u : 0u) {
+        if (!warp_wait(&bars.full[st], ph)) {
           *abort_v = 1;
           break;
         }
@@ -293,9 +279,9 @@ __device__ __forceinline__ bool ws_pass_float(const ApassKArgs& a, WsFloatSmem<R
     for (int kk = 0; kk < VPT; ++kk)
 #pragma unroll
       for (int q = 0; q < NP; ++q) acc[kk][q] = make_float2(0.f, 0.f);
-    for (int k = 0; k < nsteps; ++k) {
-      const int st = (kbase + k) % S;
-      const uint32_t ph = (uint32_t)(((kbase + k) / S) & 1);
+    int st = kbase % S;
+    uint32_t ph = (uint32_t)((kbase / S) & 1);
+    for (int k = 0; k < nsteps; ++k, st = st + 1 == S ? 0 : st + 1, ph ^= st == 0 ? 1u : 0u) {
       if (!warp_wait(&bars.ready[st], ph) || !warp_wait(&bars.full[st], ph)) {
         *abort_v = 1;
         break;
@@ -365,13 +351,6 @@ __device__ __forceinline__ bool ws_pass_float(const ApassKArgs& a, WsFloatSmem<R
   if (tid == 0 && a.loss_part) a.loss_part[blockIdx.x] = sm.loss;
   timer_end(a, ts_slot, DT);
   return true;
-}
-
-// Stages one pass of this CTA consumes (the `kbase` step from pass to pass).
-__device__ __forceinline__ int ws_pass_steps(int64_t n, int R) {
-  const int64_t r0 = n * (int64_t)blockIdx.x / gridDim.x;
-  const int64_t r1 = n * (int64_t)(blockIdx.x + 1) / gridDim.x;
-  return (int)((r1 - r0 + R - 1) / R);
 }
 
 }  // namespace nys

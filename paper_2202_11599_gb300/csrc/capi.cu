@@ -622,12 +622,7 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
     g.warm = reinterpret_cast<const nys_mlp_s*>(o.warm_model);
     g.warm_record = o.warm_record;
     GraphLoopResult gr;
-    // FP32-compute solves whose A-pass is warp-specialised run as one persistent kernel;
-    // the rest as a CUDA graph with conditional nodes
-    bool ran = false;
-    nys_status gs = NYS_OK;
-    if constexpr (sizeof(C) == 4) gs = admm_fused_try(g, st, &gr, &ran);
-    if (!ran) gs = admm_graph_run<C>(g, st, &gr);
+    nys_status gs = admm_graph_run<C>(g, st, &gr);
     if (gs != NYS_OK) return gs;
     const int done_k = std::min(gr.admm_iters, K);
     std::vector<int> its(std::max(1, done_k));

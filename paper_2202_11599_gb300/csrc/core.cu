@@ -374,25 +374,32 @@ __global__ void __launch_bounds__(kTrsmRows) trsm_ru_smem_kernel(const double* _
 }
 
 // Same recurrence and order again, blocked by columns so that most of the work runs on
-// every thread: a CTA holds R rows of Y in shared memory ([c][R]); for each block of 32
-// columns it first subtracts sum_{k < j0} b_k C[k][c] from all R x 32 entries (4 R
-// threads, each row's k in ascending order), then one thread per row finishes the block
-// (k from j0 to c - 1, then the division).  Every entry sees the same fma sequence as in
+// every thread: a CTA holds R rows of Y in shared memory ([c][R]) and, per block of 32
+// columns, those columns of C.  For each block it first subtracts sum_{k < j0} b_k C[k][c]
+// from all R x 32 entries (4 R threads, each row's k in ascending order), then one thread
+// per row finishes the block (k from j0 to c - 1, then the division).  Every entry sees the same fma sequence as in
 // trsm_ru_kernel, so the result is bitwise the same.  R = ceil(d / #SMs): one wave.
 constexpr int kTrsmBlk = 32;
 __global__ void __launch_bounds__(1024) trsm_ru_blocked_kernel(const double* __restrict__ Cm, int s, double* Y,
                                                                int64_t d, int R) {
-  extern __shared__ double bs[];  // [s][R]
+  extern __shared__ double bs[];  // [s][R], then the block's columns of C: cs[k][32], k < j1
+  double* cs = bs + (size_t)s * R;
   const int64_t r0 = (int64_t)blockIdx.x * R;
   const int nr = (int)min((int64_t)R, d - r0);
   for (int idx = threadIdx.x; idx < s * R; idx += blockDim.x) {
     const int c = idx / R, r = idx % R;
     bs[idx] = r < nr ? Y[r0 + r + (int64_t)c * d] : 0.0;
   }
-  __syncthreads();
   const int r = threadIdx.x % R, cg = threadIdx.x / R;
   for (int j0 = 0; j0 < s; j0 += kTrsmBlk) {
     const int j1 = min(s, j0 + kTrsmBlk);
+    const int w = j1 - j0;
+    // C[k][c] for k < j1, c in [j0, j1): read by every row of the CTA, staged once
+    for (int idx = threadIdx.x; idx < j1 * w; idx += blockDim.x) {
+      const int k = idx % j1, cc = idx / j1;
+      cs[k * kTrsmBlk + cc] = Cm[k + (int64_t)(j0 + cc) * s];
+    }
+    __syncthreads();
     if (cg < 4 && j0 > 0) {
       double acc[kTrsmBlk / 4];
 #pragma unroll
@@ -405,7 +412,7 @@ __global__ void __launch_bounds__(1024) trsm_ru_blocked_kernel(const double* __r
 #pragma unroll
         for (int q = 0; q < kTrsmBlk / 4; ++q) {
           const int c = j0 + cg + 4 * q;
-          if (c < j1) acc[q] = fma(-bk, __ldg(Cm + k + (int64_t)c * s), acc[q]);
+          if (c < j1) acc[q] = fma(-bk, cs[k * kTrsmBlk + cg + 4 * q], acc[q]);
         }
       }
 #pragma unroll
@@ -417,10 +424,10 @@ __global__ void __launch_bounds__(1024) trsm_ru_blocked_kernel(const double* __r
     __syncthreads();
     if (threadIdx.x < R) {
       for (int c = j0; c < j1; ++c) {
-        const double* col = Cm + (int64_t)c * s;
+        const double* col = cs + (c - j0);
         double acc = bs[c * R + r];
-        for (int k = j0; k < c; ++k) acc = fma(-bs[k * R + r], __ldg(col + k), acc);
-        bs[c * R + r] = acc / __ldg(col + c);
+        for (int k = j0; k < c; ++k) acc = fma(-bs[k * R + r], col[k * kTrsmBlk], acc);
+        bs[c * R + r] = acc / col[c * kTrsmBlk];
       }
     }
     __syncthreads();
@@ -435,8 +442,9 @@ cudaError_t trsm_right_upper(const double* C, int s, double* Y, int64_t d, cudaS
   {
     int R = (int)std::min<int64_t>(128, (d + sm_count() - 1) / sm_count());
     R = std::max(R, 1);
-    while (R > 8 && (size_t)s * R * sizeof(double) > 200 * 1024) R /= 2;
-    const size_t smem_b = (size_t)s * R * sizeof(double);
+    const size_t cblk = (size_t)s * kTrsmBlk * sizeof(double);   // staged columns of C
+    while (R > 8 && (size_t)s * R * sizeof(double) + cblk > 200 * 1024) R /= 2;
+    const size_t smem_b = (size_t)s * R * sizeof(double) + cblk;
     if (R >= 8 && smem_b <= 200 * 1024) {
       NYS_CUDA_TRY(ensure_max_dyn_smem((const void*)trsm_ru_blocked_kernel, 200 * 1024));
       const int threads = (4 * R + 31) / 32 * 32;

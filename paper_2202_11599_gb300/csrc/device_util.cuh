@@ -178,7 +178,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
 // starts at 0 and wraps harmlessly).  One atomic per block and no release write, so it
 // costs about one L2 round trip less than grid_barrier.  Same memory rules: data that
 // other blocks wrote before the barrier is read through L2 (__ldcg) after it.
-__device__ __forceinline__ bool grid_barrier_mono(unsigned* count, unsigned target, long long cycles = kWaitCycles) {
+// `sleep_ns` > 0 spaces the polls: blocks that arrive long before the last one (the end of an
+// A-pass) would otherwise keep one L2 line busy while the others still stream A.
+__device__ __forceinline__ bool grid_barrier_mono(unsigned* count, unsigned target, long long cycles = kWaitCycles,
+                                                  unsigned sleep_ns = 0) {
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
@@ -187,6 +190,7 @@ __device__ __forceinline__ bool grid_barrier_mono(unsigned* count, unsigned targ
     volatile unsigned* vc = count;
     const long long t0 = clock64();
     while ((int)(*vc - target) < 0) {
+      if (sleep_ns) __nanosleep(sleep_ns);
       if (clock64() - t0 > cycles) {
         ok = 0;
         break;

@@ -163,11 +163,6 @@ struct GraphInstance {
 };
 template <typename C>
 nys_status admm_graph_run(const GraphLoopArgs& g, cudaStream_t stream, GraphLoopResult* res);
-// The same loop as one persistent cooperative kernel (admm_fused.cu) when the problem
-// allows it (FP32 compute, warp-specialised A-pass with two rows per stage, no refined
-// step, warm-start model or sharding; NYS_ADMM_FUSED=0 turns it off).  *ran = false:
-// nothing was launched and the caller runs the graph-driven loop.
-nys_status admm_fused_try(const GraphLoopArgs& g, cudaStream_t stream, GraphLoopResult* res, bool* ran);
 // Several independent instances as parallel branches of ONE graph launch.
 template <typename C>
 nys_status admm_graph_run_many(const GraphLoopArgs* gs, int count, cudaStream_t stream, GraphInstance* insts,
