@@ -876,6 +876,231 @@ __global__ void __launch_bounds__(kVecThreads) admm_zu_g_kernel(int64_t d, const
 // before it) and returns; the next launch continues at k.  The arithmetic and its order are
 // those of the general body, so the iterates are bitwise those of a solve without this
 // kernel.  Grid barriers are bounded (NYS_ETIMEOUT).
+// One PCG iteration after its A-pass as ONE cooperative launch (Alg. Nystrom PCG): the
+// reduction of the per-CTA A-pass partials (apass_reduce_kernel), the update of x, w and the
+// tracked (H + rho I) x with the partials of ||w||^2 and U^T w (pcg_update_kernel), the
+// scalar step (pcg_scalar_body), y = P^{-1} w (pcg_tail_kernel) and the next direction
+// p = y + beta p, separated by grid barriers instead of kernel boundaries.  Every element and
+// every partial is formed by the same code, block mapping and order as in those kernels, so
+// the result is bitwise theirs; data written by other blocks in the same launch is read
+// through L2.  With zu set, the iteration that ends the PCG loop also runs the prox / dual
+// step and the scalars of the ADMM iteration (admm_zu_g_kernel, admm_scalar_g_body).
+template <typename C>
+struct PostArgs {
+  int64_t d;
+  int chunk, nbr, nb3, nb5, nbz;
+  const C* partial;      // [G][dpad] A-pass partials
+  int G;
+  int64_t dpad;
+  C rho;                 // rho + mu of the H-matvec
+  const float* cscale;   // FP8 column scales, or null
+  C *p, *v, *x, *w, *hx, *y;
+  const C* U;
+  int s;
+  const C* cvec;
+  C* gs;
+  double *pv_part, *wy_part, *part_w2, *part_g;
+  PcgState* st;
+  cudaGraphConditionalHandle cond;   // the PCG WHILE
+  // prox / dual step (zu != 0)
+  int zu;
+  double *xd, *z, *u, *ztrace, *part5, *rp, *rd;
+  int* pcg_it;
+  double kappa, rho_admm, eps_abs, eps_rel;
+  int K;
+  AdmmCtl* ctl;
+  cudaGraphConditionalHandle h_admm;
+  int* dstat;            // NYS_ETIMEOUT when a grid barrier wait runs out
+};
+
+template <typename C>
+__global__ void __launch_bounds__(kVecThreads) pcg_post_kernel(const PostArgs<C> a) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* wch = reinterpret_cast<C*>(sm_raw);   // chunk of w (U^T w), then g (y = w + U g)
+  __shared__ double sh[kVecThreads / 32];
+  __shared__ double slot;
+  PcgState* st = a.st;
+  const int b = blockIdx.x;
+  const unsigned nblk = gridDim.x;
+  const int64_t d = a.d;
+  const int s = a.s;
+  // every block reads the state before block 0 changes it below (after two barriers)
+  const int done0 = st->done;
+  const int iters0 = st->iters, fixed = st->fixed, maxit = st->maxit;
+  const double thresh2 = st->thresh2;
+  if (done0) {
+    if (b == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
+    return;
+  }
+  auto fail = [&]() {
+    if (b == 0 && threadIdx.x == 0) {
+      atomicExch(a.dstat, (int)NYS_ETIMEOUT);
+      st->done = 1;
+      cudaGraphSetConditional(a.cond, 0u);
+      if (a.zu) cudaGraphSetConditional(a.h_admm, 0u);
+    }
+  };
+  // ---- R: v = sum_g partial[g] + rho p, partials of p^T v (apass_reduce_kernel)
+  if (b < a.nbr) {
+    double dacc = 0.0;
+    for (int64_t j = b * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)a.nbr * kVecThreads) {
+      C sj = C(0);
+#pragma unroll 16
+      for (int g = 0; g < a.G; ++g) sj += a.partial[(int64_t)g * a.dpad + j];
+      if (a.cscale) sj *= (C)a.cscale[j];
+      const C pj = a.p[j];
+      const C yj = fma(a.rho, pj, sj);
+      a.v[j] = yj;
+      dacc += (double)pj * (double)yj;
+    }
+    const double t = block_sum<kVecThreads>(dacc, sh);
+    if (threadIdx.x == 0) a.pv_part[b] = t;
+  }
+  if (!grid_barrier(&st->bar_count, &st->bar_gen, nblk)) return fail();
+  // ---- U: alpha = w^T y / p^T v, x += alpha p, w -= alpha v, hx += alpha v (pcg_update_kernel)
+  const double pv = block_fixed_sum_cg(a.pv_part, a.nbr, &slot);
+  const double wy = block_fixed_sum_cg(a.wy_part, a.nb5, &slot);
+  const bool bad = !(pv > 0.0) || !isfinite(pv);
+  if (!bad && b < a.nb3) {
+    const C al = (C)(wy / pv);
+    const int64_t j0 = (int64_t)b * a.chunk;
+    const int64_t j1 = min(d, j0 + a.chunk);
+    double lw2 = 0.0;
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += kVecThreads) {
+      const C vj = __ldcg(a.v + j);
+      a.x[j] = fma(al, a.p[j], a.x[j]);
+      const C wj = fma(-al, vj, a.w[j]);
+      if (a.hx) a.hx[j] = fma(al, vj, a.hx[j]);
+      a.w[j] = wj;
+      wch[j - j0] = wj;
+      lw2 += (double)wj * (double)wj;
+    }
+    const double tw2 = block_sum<kVecThreads>(lw2, sh);
+    if (threadIdx.x == 0) a.part_w2[b] = tw2;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int len = (int)(j1 - j0);
+    constexpr int RW = 4;
+    for (int i0 = warp * RW; i0 < s; i0 += (kVecThreads / 32) * RW) {
+      C acc[RW];
+#pragma unroll
+      for (int q = 0; q < RW; ++q) acc[q] = C(0);
+#pragma unroll 8
+      for (int jj = lane; jj < len; jj += 32) {
+        const C wv = wch[jj];
+#pragma unroll
+        for (int q = 0; q < RW; ++q)
+          if (i0 + q < s) acc[q] = fma(a.U[(int64_t)(i0 + q) * d + j0 + jj], wv, acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < RW; ++q) acc[q] = warp_sum(acc[q]);
+      if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < RW; ++q)
+          if (i0 + q < s) a.part_g[(int64_t)b * s + i0 + q] = (double)acc[q];
+      }
+    }
+  }
+  if (!grid_barrier(&st->bar_count, &st->bar_gen, nblk)) return fail();
+  // ---- S: ||w||^2, stop test, iteration count, g = c o U^T w (pcg_scalar_body; every block
+  // takes the same decision, block 0 records it)
+  const double w2 = block_fixed_sum_cg(a.part_w2, a.nb3, &slot);
+  const bool stepped = !bad && isfinite(w2);
+  int iters = iters0, done = 0, status = 0;
+  if (!stepped) {
+    // first iteration: H + rho I not positive definite on p; later: the rounding floor
+    status = iters0 == 0 ? NYS_EBREAKDOWN : NYS_ENOCONV;
+    done = 1;
+  } else {
+    iters += 1;
+    if (fixed >= 0) {
+      if (iters >= fixed) done = 1;
+    } else if (!(w2 > thresh2)) {
+      done = 1;
+    } else if (iters >= maxit) {
+      done = 1;
+      status = NYS_ENOCONV;
+    }
+  }
+  if (b == 0 && threadIdx.x == 0) {
+    if (stepped) {
+      st->wy = wy;
+      st->iters = iters;
+      st->w2 = w2;
+    }
+    if (status) st->status = status;
+    st->done = done;
+    cudaGraphSetConditional(a.cond, done ? 0u : 1u);
+  }
+  if (!done) {
+    for (int i = threadIdx.x; i < s; i += kVecThreads) {
+      double g = 0.0;
+#pragma unroll 8
+      for (int bb = 0; bb < a.nb3; ++bb) g += __ldcg(a.part_g + (int64_t)bb * s + i);
+      const C gi = (C)((double)a.cvec[i] * g);
+      wch[i] = gi;
+      if (b == 0) a.gs[i] = gi;
+    }
+    __syncthreads();
+    // ---- T: y = w + U g, partials of w^T y (pcg_tail_kernel)
+    if (b < a.nb5) {
+      double lwy = 0.0;
+      for (int64_t j = b * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)a.nb5 * kVecThreads) {
+        const C wj = __ldcg(a.w + j);
+        C acc = wj;
+#pragma unroll 16
+        for (int i = 0; i < s; ++i) acc = fma(a.U[(int64_t)i * d + j], wch[i], acc);
+        a.y[j] = acc;
+        lwy += (double)wj * (double)acc;
+      }
+      const double t = block_sum<kVecThreads>(lwy, sh);
+      if (threadIdx.x == 0) a.wy_part[b] = t;
+    }
+    if (!grid_barrier(&st->bar_count, &st->bar_gen, nblk)) return fail();
+    // ---- B: beta = (w^T y)_new / (w^T y)_old, p = y + beta p
+    const double beta = block_fixed_sum_cg(a.wy_part, a.nb5, &slot) / wy;
+    const C bc = (C)beta;
+    for (int64_t j = b * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)nblk * kVecThreads)
+      a.p[j] = fma(bc, a.p[j], __ldcg(a.y + j));
+    return;
+  }
+  if (!a.zu) return;
+  // ---- Z: prox / dual step with the final x and the scalars of the ADMM iteration
+  // (admm_zu_g_kernel; x was written by other blocks above: read through L2)
+  if (b < a.nbz) {
+    double* zt = a.ztrace ? a.ztrace + (int64_t)a.ctl->k * d : nullptr;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+    for (int64_t j = b * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)a.nbz * kVecThreads) {
+      const double xj = (double)__ldcg(a.x + j);
+      const double zo = a.z[j];
+      const double vj = xj + a.u[j];
+      const double mag = fabs(vj) - a.kappa;
+      const double zj = mag > 0.0 ? copysign(mag, vj) : 0.0;
+      const double uj = a.u[j] + xj - zj;
+      a.xd[j] = xj;
+      a.z[j] = zj;
+      a.u[j] = uj;
+      if (zt) zt[j] = zj;
+      a0 += (xj - zj) * (xj - zj);
+      a1 += (zj - zo) * (zj - zo);
+      a2 += xj * xj;
+      a3 += zj * zj;
+      a4 += uj * uj;
+    }
+    double a5[5] = {a0, a1, a2, a3, a4};
+    block_sum5(a5);
+    if (threadIdx.x == 0) {
+      double* o = a.part5 + (int64_t)b * 5;
+#pragma unroll
+      for (int t = 0; t < 5; ++t) o[t] = a5[t];
+    }
+  }
+  if (!grid_barrier(&st->bar_count, &st->bar_gen, nblk)) return fail();
+  if (b == 0 && threadIdx.x < 32)
+    admm_scalar_g_body(a.nbz, a.part5, a.rho_admm, a.K, a.eps_abs, a.eps_rel, a.rp, a.rd, a.pcg_it, st, a.ctl, 0, 2,
+                       a.h_admm);
+}
+
 struct HeadArgs {
   int64_t d;
   int chunk, nb3, nbz, nb5, s;
@@ -893,6 +1118,7 @@ struct HeadArgs {
   int* pcg_it_trace;
   int* dstat;
   cudaGraphConditionalHandle h_admm, h_pcg, h_zu, h_hx;
+  int has_zu;   // 0: the PCG post kernel runs the prox / dual step, there is no IF (h_zu) node
 };
 
 template <typename C>
@@ -920,7 +1146,7 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
       atomicExch(a.dstat, (int)NYS_ETIMEOUT);
       cudaGraphSetConditional(a.h_admm, 0u);
       cudaGraphSetConditional(a.h_pcg, 0u);
-      cudaGraphSetConditional(a.h_zu, 0u);
+      if (a.has_zu) cudaGraphSetConditional(a.h_zu, 0u);
       cudaGraphSetConditional(a.h_hx, 0u);
     }
   };
@@ -933,7 +1159,7 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
         ctl->nodes += 1;
         cudaGraphSetConditional(a.h_hx, 1u);
         cudaGraphSetConditional(a.h_pcg, 0u);
-        cudaGraphSetConditional(a.h_zu, 0u);
+        if (a.has_zu) cudaGraphSetConditional(a.h_zu, 0u);
       }
       return;
     }
@@ -1043,7 +1269,7 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
         ctl->nodes += 1;
         cudaGraphSetConditional(a.h_hx, 0u);
         cudaGraphSetConditional(a.h_pcg, 1u);
-        cudaGraphSetConditional(a.h_zu, 1u);
+        if (a.has_zu) cudaGraphSetConditional(a.h_zu, 1u);
       }
       return;
     }
@@ -1115,7 +1341,7 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
         cudaGraphSetConditional(a.h_admm, 0u);
         cudaGraphSetConditional(a.h_hx, 0u);
         cudaGraphSetConditional(a.h_pcg, 0u);
-        cudaGraphSetConditional(a.h_zu, 0u);
+        if (a.has_zu) cudaGraphSetConditional(a.h_zu, 0u);
       }
       return;
     }
@@ -1235,12 +1461,18 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   C* rc = reinterpret_cast<C*>(g.rc);
   C* hx = reinterpret_cast<C*>(g.hx);
   cudaError_t e = cudaSuccess;
-#define G_OK(x)                                  \
-  do {                                           \
-    e = (x);                                     \
-    if (e != cudaSuccess) return NYS_ECUDA;      \
+#define G_OK(x)                                                                              \
+  do {                                                                                       \
+    e = (x);                                                                                 \
+    if (e != cudaSuccess) {                                                                  \
+      if (std::getenv("NYS_TRACE"))                                                          \
+        std::fprintf(stderr, "[nys] graph build: %s at pcg.cu:%d\n", cudaGetErrorString(e), __LINE__); \
+      (void)cudaGetLastError(); /* a failed build leaves no error behind for later launches */ \
+      return NYS_ECUDA;                                                                      \
+    }                                                                                        \
   } while (0)
   G_OK(cudaMemsetAsync(ctl, 0, sizeof(AdmmCtl), stream));
+  G_OK(cudaMemsetAsync(st, 0, sizeof(PcgState), stream));   // the post kernel's barrier words start at 0
   G_OK(cudaMemsetAsync(dstat, 0, sizeof(int), stream));
   G_OK(cudaMemsetAsync(hx, 0, d * sizeof(C), stream));
   if (fixed_dev) G_OK(cudaMemcpyAsync(fixed_dev, g.fixed_host, K * sizeof(int), cudaMemcpyHostToDevice, stream));
@@ -1274,6 +1506,83 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   aa.t_out = nullptr;
   aa.mode = g.pb.D ? MODE_DIAG : MODE_ID;
 
+  // One PCG iteration after its A-pass as one cooperative launch (pcg_post_kernel) instead of
+  // the reduce, update and tail kernels, for a single instance (its grid barriers want the
+  // grid co-resident; concurrent graph branches keep the separate kernels).  NYS_PCG_POST=0
+  // selects the separate kernels.
+  const int nbp = std::max(std::max(nbr, nb3), std::max(nb5, nbz));
+  const size_t sm_post = (size_t)std::max(chunk, std::max(1, s)) * sizeof(C);
+  bool use_post = g.allow_nostep && nbz <= kPart5Max;
+  {
+    const char* pe = std::getenv("NYS_PCG_POST");
+    if (pe && std::atoi(pe) == 0) use_post = false;
+    if (use_post) {
+      int per_sm = 0, coop = 0;
+      G_OK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, current_device()));
+      G_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_post_kernel<C>, kVecThreads, sm_post));
+      use_post = coop && (int64_t)per_sm * sm_count() >= nbp;
+    }
+  }
+  PostArgs<C> pa = {};
+  pa.d = d;
+  pa.chunk = chunk;
+  pa.nbr = nbr;
+  pa.nb3 = nb3;
+  pa.nb5 = nb5;
+  pa.nbz = nbz;
+  pa.partial = reinterpret_cast<const C*>(apart);
+  pa.G = g.pb.plan.grid;
+  pa.dpad = g.pb.plan.dpad;
+  pa.rho = (C)(g.rho + g.mu);
+  pa.cscale = g.pb.A->dtype == NYS_FP8E4M3 ? g.pb.A->col_scale : nullptr;
+  pa.p = p;
+  pa.v = v;
+  pa.x = xc;
+  pa.w = w;
+  pa.hx = hx;
+  pa.y = y;
+  pa.U = U;
+  pa.s = s;
+  pa.cvec = cvec;
+  pa.gs = gs;
+  pa.pv_part = pv_part;
+  pa.wy_part = wy_part;
+  pa.part_w2 = part_w2;
+  pa.part_g = part_g;
+  pa.st = st;
+  pa.xd = g.x;
+  pa.z = g.z;
+  pa.u = g.u;
+  pa.ztrace = g.ztrace;
+  pa.part5 = part5;
+  pa.rp = g.rp;
+  pa.rd = g.rd;
+  pa.pcg_it = g.pcg_it;
+  pa.kappa = g.gamma / g.rho;
+  pa.rho_admm = g.rho;
+  pa.eps_abs = g.eps_abs;
+  pa.eps_rel = g.eps_rel;
+  pa.K = K;
+  pa.ctl = ctl;
+  pa.dstat = dstat;
+  auto launch_post = [&](cudaGraphConditionalHandle hc, int zu, cudaGraphConditionalHandle ha) {
+    PostArgs<C> q = pa;
+    q.cond = hc;
+    q.zu = zu;
+    q.h_admm = ha;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nbp);
+    cfg.blockDim = dim3(kVecThreads);
+    cfg.dynamicSmemBytes = sm_post;
+    cfg.stream = cap;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, pcg_post_kernel<C>, q);
+  };
+
   // Fast body (tracked warm start, no refined step or warm-start model, a single instance):
   //   admm_head_kernel (cooperative) -> IF (h_hx) [ (H + rho I) x recompute ] ->
   //   WHILE (h_pcg) [ A-pass, reduce, update, P^{-1} tail ] -> IF (h_zu) [ prox / dual + scalars ]
@@ -1294,10 +1603,11 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
       fast = coop && (int64_t)per_sm * sm_count() >= nbf && nbz <= kPart5Max;
     }
     if (fast) {
-      cudaGraphConditionalHandle h_hx, h_zu;
+      cudaGraphConditionalHandle h_hx, h_zu = 0;
       G_OK(cudaGraphConditionalHandleCreate(&h_hx, body, 0u, 0u));
       G_OK(cudaGraphConditionalHandleCreate(&h_pcg, body, 0u, 0u));
-      G_OK(cudaGraphConditionalHandleCreate(&h_zu, body, 0u, 0u));
+      // a handle must belong to a conditional node: h_zu only with the IF (h_zu) node
+      if (!use_post) G_OK(cudaGraphConditionalHandleCreate(&h_zu, body, 0u, 0u));
       auto add_cond = [&](cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
                           const std::vector<cudaGraphNode_t>& deps, cudaGraphNode_t* node, cudaGraph_t* child) {
         cudaGraphNodeParams np = {};
@@ -1350,6 +1660,7 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
       ha.h_admm = h_admm;
       ha.h_pcg = h_pcg;
       ha.h_zu = h_zu;
+      ha.has_zu = use_post ? 0 : 1;
       ha.h_hx = h_hx;
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3((unsigned)nbf);
@@ -1386,22 +1697,28 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
       aa.p = p;
       aa.skip = &st->done;
       G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, true));
-      G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho + g.mu, v, pv_part, nbr, cap));
-      pcg_update_kernel<C><<<nb3, kVecThreads, (size_t)chunk * sizeof(C), cap>>>(
-          0, d, chunk, xc, w, rc, v, p, U, s, pv_part, nbr, wy_part, nb5, part_w2, part_r2, part_g, st, hx, cvec, gs,
-          h_pcg, 1, nullptr, nullptr, nullptr, 0.0, (C*)nullptr);
-      pcg_tail_kernel<C><<<nb5, kVecThreads, (size_t)std::max(1, s) * sizeof(C), cap>>>(d, w, y, U, s, gs, wy_part, st,
-                                                                                       0, p);
-      G_OK(cudaStreamEndCapture(cap, &pbody));
-      // IF (h_zu): prox / dual step of an iteration that took PCG steps
-      cudaGraphNode_t n_zu;
-      cudaGraph_t zbody;
-      G_OK(add_cond(h_zu, cudaGraphCondTypeIf, {n_pcg}, &n_zu, &zbody));
-      G_OK(cudaStreamBeginCaptureToGraph(cap, zbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-      admm_zu_g_kernel<C><<<nbz, kVecThreads, 0, cap>>>(d, xc, 0, g.x, g.z, g.u, g.gamma / g.rho, g.ztrace, ctl,
-                                                        part5, g.rho, K, g.eps_abs, g.eps_rel, g.rp, g.rd, g.pcg_it,
-                                                        st, 1, 4, h_admm);
-      G_OK(cudaStreamEndCapture(cap, &zbody));
+      if (use_post) {
+        // the iteration that ends the PCG loop runs the prox / dual step itself: no IF (h_zu)
+        G_OK(launch_post(h_pcg, 1, h_admm));
+        G_OK(cudaStreamEndCapture(cap, &pbody));
+      } else {
+        G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho + g.mu, v, pv_part, nbr, cap));
+        pcg_update_kernel<C><<<nb3, kVecThreads, (size_t)chunk * sizeof(C), cap>>>(
+            0, d, chunk, xc, w, rc, v, p, U, s, pv_part, nbr, wy_part, nb5, part_w2, part_r2, part_g, st, hx, cvec, gs,
+            h_pcg, 1, nullptr, nullptr, nullptr, 0.0, (C*)nullptr);
+        pcg_tail_kernel<C><<<nb5, kVecThreads, (size_t)std::max(1, s) * sizeof(C), cap>>>(d, w, y, U, s, gs, wy_part,
+                                                                                         st, 0, p);
+        G_OK(cudaStreamEndCapture(cap, &pbody));
+        // IF (h_zu): prox / dual step of an iteration that took PCG steps
+        cudaGraphNode_t n_zu;
+        cudaGraph_t zbody;
+        G_OK(add_cond(h_zu, cudaGraphCondTypeIf, {n_pcg}, &n_zu, &zbody));
+        G_OK(cudaStreamBeginCaptureToGraph(cap, zbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        admm_zu_g_kernel<C><<<nbz, kVecThreads, 0, cap>>>(d, xc, 0, g.x, g.z, g.u, g.gamma / g.rho, g.ztrace, ctl,
+                                                          part5, g.rho, K, g.eps_abs, g.eps_rel, g.rp, g.rd, g.pcg_it,
+                                                          st, 1, 4, h_admm);
+        G_OK(cudaStreamEndCapture(cap, &zbody));
+      }
       count_launch_suspend(false);
       G_OK(cudaGetLastError());
       inst->ctl = ctl;
@@ -1534,12 +1851,17 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   aa.p = p;
   aa.skip = &st->done;
   G_OK(apass_run(aa, g.pb.plan, apart, nullptr, dstat, cap, true));
-  G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho + g.mu, v, pv_part, nbr, cap));
-  pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, cap>>>(0, d, chunk, xc, w, rc, v, p, U, s, pv_part, nbr, wy_part,
-                                                          nb5, part_w2, part_r2, part_g, st, hx, cvec, gs, h_pcg, 1,
-                                                          nullptr, nullptr, nullptr, 0.0, (C*)nullptr);
-  pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, cap>>>(d, w, y, U, s, gs, wy_part, st, 0, p);
-  body_nodes = 4;
+  if (use_post) {
+    G_OK(launch_post(h_pcg, 0, h_admm));
+    body_nodes = 2;
+  } else {
+    G_OK(apass_reduce(aa, g.pb.plan, apart, g.rho + g.mu, v, pv_part, nbr, cap));
+    pcg_update_kernel<C><<<nb3, kVecThreads, sm_upd, cap>>>(0, d, chunk, xc, w, rc, v, p, U, s, pv_part, nbr, wy_part,
+                                                            nb5, part_w2, part_r2, part_g, st, hx, cvec, gs, h_pcg, 1,
+                                                            nullptr, nullptr, nullptr, 0.0, (C*)nullptr);
+    pcg_tail_kernel<C><<<nb5, kVecThreads, sm_tail, cap>>>(d, w, y, U, s, gs, wy_part, st, 0, p);
+    body_nodes = 4;
+  }
   G_OK(cudaStreamEndCapture(cap, &pbody));
 
   // ---- segment 2: prox / dual step, residuals, loop condition
@@ -1598,9 +1920,22 @@ nys_status admm_graph_run_many(const GraphLoopArgs* gs, int count, cudaStream_t 
     if (s != NYS_OK) return s;
   }
   auto t1 = now();
-  if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) return NYS_ECUDA;
+  {
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    if (ie != cudaSuccess) {
+      if (trace) std::fprintf(stderr, "[nys] graph instantiate: %s\n", cudaGetErrorString(ie));
+      (void)cudaGetLastError();
+      return NYS_ECUDA;
+    }
+  }
   auto t2 = now();
-  if (cudaGraphLaunch(exec, stream) != cudaSuccess) return NYS_ECUDA;
+  {
+    const cudaError_t le = cudaGraphLaunch(exec, stream);
+    if (le != cudaSuccess) {
+      if (trace) std::fprintf(stderr, "[nys] graph launch: %s\n", cudaGetErrorString(le));
+      return NYS_ECUDA;
+    }
+  }
   if (trace) {
     auto t3 = now();
     auto ms = [](auto a, auto b) { return std::chrono::duration<double, std::milli>(b - a).count(); };
@@ -1611,10 +1946,13 @@ nys_status admm_graph_run_many(const GraphLoopArgs* gs, int count, cudaStream_t 
   for (int i = 0; i < count; ++i) {
     AdmmCtl ctl_h;
     int dstat_h = 0;
-    if (cudaMemcpyAsync(&ctl_h, insts[i].ctl, sizeof(AdmmCtl), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-        cudaMemcpyAsync(&dstat_h, insts[i].dstat, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-        cudaStreamSynchronize(stream) != cudaSuccess)
+    cudaError_t re = cudaMemcpyAsync(&ctl_h, insts[i].ctl, sizeof(AdmmCtl), cudaMemcpyDeviceToHost, stream);
+    if (re == cudaSuccess) re = cudaMemcpyAsync(&dstat_h, insts[i].dstat, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    if (re == cudaSuccess) re = cudaStreamSynchronize(stream);
+    if (re != cudaSuccess) {
+      if (trace) std::fprintf(stderr, "[nys] graph run: %s\n", cudaGetErrorString(re));
       return NYS_ECUDA;
+    }
     count_launch_add(ctl_h.nodes);
     res[i].admm_iters = ctl_h.k;
     res[i].breakdown = ctl_h.stop == 2;

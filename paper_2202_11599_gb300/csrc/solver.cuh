@@ -19,6 +19,7 @@ struct PcgState {
   int maxit;
   int fixed;       // >= 0: run exactly this many iterations
   unsigned int ticket[2];  // last-block election of the fused update / tail kernels (zero between launches)
+  unsigned int bar_count, bar_gen;  // grid barrier of pcg_post_kernel (zeroed once per solve)
 };
 
 // Stream-ordered device allocations freed when the pool goes out of scope.

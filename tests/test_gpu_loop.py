@@ -73,3 +73,27 @@ def test_nostep_kernel_residual_stop_and_fixed_counts(monkeypatch):
                            pcg_fixed=fixed, hx_refresh=4)
     assert torch.equal(fx[True]["z_trace"], fx[False]["z_trace"])
     assert fx[True]["info"]["pcg_iters_total"] == sum(fixed)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.bfloat16])
+@pytest.mark.parametrize("mode,tol,refresh,nostep", [("rel", 1e-3, 5, "1"), ("rnorm_pow", 1.5, 7, "1"),
+                                                     ("rel", 1e-3, 5, "0"), ("rnorm_pow", 1.75, 100, "0")])
+def test_post_kernel_is_bitwise_the_separate_kernels(monkeypatch, dtype, mode, tol, refresh, nostep):
+    """One PCG iteration's reduce, update, scalar step, P^{-1} apply and direction update as
+    one cooperative launch (and, in the fast body, the prox / dual step with it) against the
+    four separate kernels (NYS_PCG_POST=0), in both graph bodies."""
+    p = gen.lasso_problem(3000, 700, nnz=30, gamma_frac=0.05, seed=73)
+    M = nx.Matrix.padded(torch.from_numpy(p.A).cuda())
+    Mi = None if dtype == torch.float64 else nx.Matrix.padded(torch.from_numpy(p.A).cuda(), dtype)
+    Om = torch.from_numpy(gen.gaussian_test_matrix(700, 40, 73)).cuda()
+    monkeypatch.setenv("NYS_ADMM_NOSTEP", nostep)
+    out = {}
+    for post in ("1", "0"):
+        monkeypatch.setenv("NYS_PCG_POST", post)
+        out[post] = nx.nysadmm_solve("lasso", M, torch.from_numpy(p.b).cuda(), p.gamma, 20.0, 40, tol, Om, A_inner=Mi,
+                                     refine=False, z_trace=True, admm_iters=200, tol_mode=mode, hx_refresh=refresh,
+                                     pcg_trace=True)
+    a, b = out["1"], out["0"]
+    assert a["pcg_trace"] == b["pcg_trace"] and a["info"]["pcg_iters_total"] > 50
+    assert torch.equal(a["z_trace"], b["z_trace"]) and torch.equal(a["x"], b["x"])
+    assert a["info"]["r_p"] == b["info"]["r_p"] and a["info"]["r_d"] == b["info"]["r_d"]
