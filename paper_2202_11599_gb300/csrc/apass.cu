@@ -465,10 +465,8 @@ __global__ void __launch_bounds__(kVecThreads) apass_reduce_kernel(const C* __re
   __shared__ double sh[kVecThreads / 32];
   double dacc = 0.0;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x) {
-    C s = C(0);
-    // fixed order over the CTAs' partials; the unroll keeps 16 loads in flight
-#pragma unroll 16
-    for (int g = 0; g < G; ++g) s += partial[(int64_t)g * dpad + j];
+    // fixed order over the CTAs' partials (increasing g)
+    C s = sum_strided_fixed<false>(partial, G, dpad, j, C(0));
     if (cscale) s *= (C)cscale[j];  // FP8: sum_i q_ij u_i -> sum_i A_ij u_i
     const C pj = p ? p[j] : C(0);
     const C yj = fma(rho, pj, s);

@@ -222,4 +222,40 @@ __device__ __forceinline__ double block_sum(double v, double* sh /* >= NT/32 */)
   return s;
 }
 
+// sum_{g < n} a[g * stride + j] added in increasing g (the order of a plain loop), the loads
+// issued 32 at a time so that a thread keeps 32 reads in flight.  CG: read through L2, for
+// data written by other blocks of the running kernel.
+template <bool CG, typename T>
+__device__ __forceinline__ T sum_strided_fixed(const T* a, int n, int64_t stride, int64_t j, T s) {
+  for (int g = 0; g < n; g += 32) {
+    T v[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+      if (g + q < n) {
+        const T* ptr = a + (int64_t)(g + q) * stride + j;
+        v[q] = CG ? __ldcg(ptr) : *ptr;
+      }
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+      if (g + q < n) s += v[q];
+  }
+  return s;
+}
+
+// acc + sum_{i < s} U[i * d + j] g[i] as one fma chain in increasing i (the row of U g, for
+// y = w + U g), the loads of U issued 32 at a time.
+template <typename C>
+__device__ __forceinline__ C urow_dot(const C* __restrict__ U, int64_t d, int64_t j, int s, const C* g, C acc) {
+  for (int i = 0; i < s; i += 32) {
+    C u[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+      if (i + q < s) u[q] = U[(int64_t)(i + q) * d + j];
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+      if (i + q < s) acc = fma(u[q], g[i + q], acc);
+  }
+  return acc;
+}
+
 }  // namespace nys

@@ -137,6 +137,35 @@ __global__ void pcg_reset_kernel(PcgState* st, double tol, int tol_abs, int maxi
 }
 
 // K4 body (run by the last block of K3): ||w||^2, stop test, iteration count,
+// Partials of U^T w over one block's chunk of w (in shared memory, len elements from j0):
+// out[i] = sum over the chunk of U[i, j] w_j, each lane adding its lane-strided elements in
+// increasing j, then a warp sum.  Eight rows of U per warp pass keep 64 loads in flight.
+template <typename C>
+__device__ __forceinline__ void utw_partials(const C* wch, int len, const C* __restrict__ U, int64_t d, int64_t j0,
+                                             int s, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int RW = 8;
+  for (int i0 = warp * RW; i0 < s; i0 += (kVecThreads / 32) * RW) {
+    C acc[RW];
+#pragma unroll
+    for (int q = 0; q < RW; ++q) acc[q] = C(0);
+#pragma unroll 8
+    for (int jj = lane; jj < len; jj += 32) {
+      const C wv = wch[jj];
+#pragma unroll
+      for (int q = 0; q < RW; ++q)
+        if (i0 + q < s) acc[q] = fma(U[(int64_t)(i0 + q) * d + j0 + jj], wv, acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < RW; ++q) acc[q] = warp_sum(acc[q]);
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < RW; ++q)
+        if (i0 + q < s) out[i0 + q] = (double)acc[q];
+    }
+  }
+}
+
 // g_i = c_i (U^T w)_i.
 template <typename C>
 __device__ void pcg_scalar_body(int init, int nb3, const double* part_w2, const double* part_r2,
@@ -182,9 +211,7 @@ __device__ void pcg_scalar_body(int init, int nb3, const double* part_w2, const 
     }
   }
   for (int i = threadIdx.x; i < s; i += kVecThreads) {
-    double g = 0.0;
-#pragma unroll 8
-    for (int b = 0; b < nb3; ++b) g += __ldcg(part_g + (int64_t)b * s + i);
+    const double g = sum_strided_fixed<true>(part_g, nb3, s, i, 0.0);
     gs[i] = (C)((double)cvec[i] * g);
   }
   __syncthreads();
@@ -261,30 +288,7 @@ __global__ void __launch_bounds__(kVecThreads) pcg_update_kernel(int init, int64
       if (init) part_r2[blockIdx.x] = tr2;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int len = (int)(j1 - j0);
-    // four rows of U per warp pass: independent accumulators keep four loads and four
-    // reductions in flight (each dot keeps its lane-strided order, then a warp sum)
-    constexpr int RW = 4;
-    for (int i0 = warp * RW; i0 < s; i0 += (kVecThreads / 32) * RW) {
-      C acc[RW];
-#pragma unroll
-      for (int q = 0; q < RW; ++q) acc[q] = C(0);
-#pragma unroll 8
-      for (int jj = lane; jj < len; jj += 32) {
-        const C wv = wch[jj];
-#pragma unroll
-        for (int q = 0; q < RW; ++q)
-          if (i0 + q < s) acc[q] = fma(U[(int64_t)(i0 + q) * d + j0 + jj], wv, acc[q]);
-      }
-#pragma unroll
-      for (int q = 0; q < RW; ++q) acc[q] = warp_sum(acc[q]);
-      if (lane == 0) {
-#pragma unroll
-        for (int q = 0; q < RW; ++q)
-          if (i0 + q < s) part_g[(int64_t)blockIdx.x * s + i0 + q] = (double)acc[q];
-      }
-    }
+    utw_partials<C>(wch, (int)(j1 - j0), U, d, j0, s, part_g + (int64_t)blockIdx.x * s);
   }
   if (!last_block_done(&st->ticket[0])) return;
   pcg_scalar_body<C>(init, (int)gridDim.x, part_w2, part_r2, part_g, s, cvec, gs, pv_part, npv, wy_part, nwy, st,
@@ -309,10 +313,7 @@ __global__ void __launch_bounds__(kVecThreads) pcg_tail_kernel(int64_t d, const 
   double lwy = 0.0;
   for (int64_t j = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)gridDim.x * kVecThreads) {
     const C wj = w[j];
-    C acc = wj;
-    // same sequential order; the unroll keeps 16 independent loads of U in flight
-#pragma unroll 16
-    for (int i = 0; i < s; ++i) acc = fma(U[(int64_t)i * d + j], g[i], acc);
+    const C acc = urow_dot(U, d, j, s, g, wj);
     y[j] = acc;
     lwy += (double)wj * (double)acc;
   }
@@ -602,8 +603,9 @@ __global__ void __launch_bounds__(kVecThreads) admm_zu_kernel(int64_t d, const C
 }
 
 // Sum of the per-block partials part5[b * 5 + t] over b = 0 .. nb-1 in increasing b (the
-// same order as a sequential loop): the warp stages them in shared memory with coalesced
-// loads first, so lane 0 adds from shared memory instead of waiting on each global load.
+// same order as a sequential loop), called by one full warp; every lane gets the five sums.
+// The warp stages the partials in shared memory with coalesced loads, then lane t adds
+// column t: five chains side by side (one FP64 add per warp instruction instead of five).
 constexpr int kPart5Max = 256;
 __device__ __forceinline__ void sum_part5(int nb, const double* part5, double (&a)[5]) {
   __shared__ double sp[kPart5Max * 5];
@@ -613,11 +615,11 @@ __device__ __forceinline__ void sum_part5(int nb, const double* part5, double (&
     for (int i = lane; i < nb * 5; i += 32) sp[i] = __ldcg(part5 + i);
     __syncwarp();
   }
-  for (int t = 0; t < 5; ++t) a[t] = 0.0;
-  if (lane == 0) {
-    for (int b = 0; b < nb; ++b)
-      for (int t = 0; t < 5; ++t) a[t] += staged ? sp[b * 5 + t] : __ldcg(part5 + (int64_t)b * 5 + t);
-  }
+  double acc = 0.0;
+  if (lane < 5)
+    for (int b = 0; b < nb; ++b) acc += staged ? sp[b * 5 + lane] : __ldcg(part5 + (int64_t)b * 5 + lane);
+#pragma unroll
+  for (int t = 0; t < 5; ++t) a[t] = __shfl_sync(0xffffffffu, acc, t);
 }
 
 // r_p, r_d (Sec. 2.1), the next PCG tolerance sqrt(r_p r_d) (Sec. 5) and the
@@ -944,9 +946,7 @@ __global__ void __launch_bounds__(kVecThreads) pcg_post_kernel(const PostArgs<C>
   if (b < a.nbr) {
     double dacc = 0.0;
     for (int64_t j = b * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)a.nbr * kVecThreads) {
-      C sj = C(0);
-#pragma unroll 16
-      for (int g = 0; g < a.G; ++g) sj += a.partial[(int64_t)g * a.dpad + j];
+      C sj = sum_strided_fixed<false>(a.partial, a.G, a.dpad, j, C(0));
       if (a.cscale) sj *= (C)a.cscale[j];
       const C pj = a.p[j];
       const C yj = fma(a.rho, pj, sj);
@@ -961,8 +961,11 @@ __global__ void __launch_bounds__(kVecThreads) pcg_post_kernel(const PostArgs<C>
   const double pv = block_fixed_sum_cg(a.pv_part, a.nbr, &slot);
   const double wy = block_fixed_sum_cg(a.wy_part, a.nb5, &slot);
   const bool bad = !(pv > 0.0) || !isfinite(pv);
+  if (threadIdx.x == 0) slot = wy / pv;   // one division (the FP64 pipe is narrow), shared
+  __syncthreads();
+  const double alpha = slot;
   if (!bad && b < a.nb3) {
-    const C al = (C)(wy / pv);
+    const C al = (C)alpha;
     const int64_t j0 = (int64_t)b * a.chunk;
     const int64_t j1 = min(d, j0 + a.chunk);
     double lw2 = 0.0;
@@ -978,28 +981,7 @@ __global__ void __launch_bounds__(kVecThreads) pcg_post_kernel(const PostArgs<C>
     const double tw2 = block_sum<kVecThreads>(lw2, sh);
     if (threadIdx.x == 0) a.part_w2[b] = tw2;
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int len = (int)(j1 - j0);
-    constexpr int RW = 4;
-    for (int i0 = warp * RW; i0 < s; i0 += (kVecThreads / 32) * RW) {
-      C acc[RW];
-#pragma unroll
-      for (int q = 0; q < RW; ++q) acc[q] = C(0);
-#pragma unroll 8
-      for (int jj = lane; jj < len; jj += 32) {
-        const C wv = wch[jj];
-#pragma unroll
-        for (int q = 0; q < RW; ++q)
-          if (i0 + q < s) acc[q] = fma(a.U[(int64_t)(i0 + q) * d + j0 + jj], wv, acc[q]);
-      }
-#pragma unroll
-      for (int q = 0; q < RW; ++q) acc[q] = warp_sum(acc[q]);
-      if (lane == 0) {
-#pragma unroll
-        for (int q = 0; q < RW; ++q)
-          if (i0 + q < s) a.part_g[(int64_t)b * s + i0 + q] = (double)acc[q];
-      }
-    }
+    utw_partials<C>(wch, (int)(j1 - j0), a.U, d, j0, s, a.part_g + (int64_t)b * s);
   }
   if (!grid_barrier(&st->bar_count, &st->bar_gen, nblk)) return fail();
   // ---- S: ||w||^2, stop test, iteration count, g = c o U^T w (pcg_scalar_body; every block
@@ -1034,9 +1016,7 @@ __global__ void __launch_bounds__(kVecThreads) pcg_post_kernel(const PostArgs<C>
   }
   if (!done) {
     for (int i = threadIdx.x; i < s; i += kVecThreads) {
-      double g = 0.0;
-#pragma unroll 8
-      for (int bb = 0; bb < a.nb3; ++bb) g += __ldcg(a.part_g + (int64_t)bb * s + i);
+      const double g = sum_strided_fixed<true>(a.part_g, a.nb3, s, i, 0.0);
       const C gi = (C)((double)a.cvec[i] * g);
       wch[i] = gi;
       if (b == 0) a.gs[i] = gi;
@@ -1047,9 +1027,7 @@ __global__ void __launch_bounds__(kVecThreads) pcg_post_kernel(const PostArgs<C>
       double lwy = 0.0;
       for (int64_t j = b * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)a.nb5 * kVecThreads) {
         const C wj = __ldcg(a.w + j);
-        C acc = wj;
-#pragma unroll 16
-        for (int i = 0; i < s; ++i) acc = fma(a.U[(int64_t)i * d + j], wch[i], acc);
+        const C acc = urow_dot(a.U, d, j, s, wch, wj);
         a.y[j] = acc;
         lwy += (double)wj * (double)acc;
       }
@@ -1058,8 +1036,10 @@ __global__ void __launch_bounds__(kVecThreads) pcg_post_kernel(const PostArgs<C>
     }
     if (!grid_barrier(&st->bar_count, &st->bar_gen, nblk)) return fail();
     // ---- B: beta = (w^T y)_new / (w^T y)_old, p = y + beta p
-    const double beta = block_fixed_sum_cg(a.wy_part, a.nb5, &slot) / wy;
-    const C bc = (C)beta;
+    const double wy_new = block_fixed_sum_cg(a.wy_part, a.nb5, &slot);
+    if (threadIdx.x == 0) slot = wy_new / wy;
+    __syncthreads();
+    const C bc = (C)slot;
     for (int64_t j = b * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)nblk * kVecThreads)
       a.p[j] = fma(bc, a.p[j], __ldcg(a.y + j));
     return;
@@ -1133,6 +1113,8 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
   __shared__ double slot;
   __shared__ double slot2[2];
   __shared__ int s_go;
+  __shared__ double s_tolk;
+  __shared__ int s_tabs;
   const int b = blockIdx.x;
   const unsigned nblk = gridDim.x;
   const int64_t d = a.d;
@@ -1163,9 +1145,17 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
       }
       return;
     }
-    double tolk;
-    int tol_abs;
-    iter_tol(a.tol_mode, a.tol, a.tol_floor, k, eps_next, &tolk, &tol_abs);
+    // one thread evaluates the schedule (a pow on the narrow FP64 pipe), the block shares it
+    if (threadIdx.x == 0) {
+      double t;
+      int ab;
+      iter_tol(a.tol_mode, a.tol, a.tol_floor, k, eps_next, &t, &ab);
+      s_tolk = t;
+      s_tabs = ab;
+    }
+    __syncthreads();
+    const double tolk = s_tolk;
+    const int tol_abs = s_tabs;
     // ---- 1. right-hand side, warm-start residual, ||w||^2, ||r||^2, U^T w partials
     if (b < a.nb3) {
       const int64_t j0 = (int64_t)b * a.chunk;
@@ -1204,34 +1194,11 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
         const int64_t j1 = min(d, j0 + a.chunk);
         for (int64_t j = j0 + threadIdx.x; j < j1; j += kVecThreads) wch[j - j0] = __ldcg(w + j);
         __syncthreads();
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const int len = (int)(j1 - j0);
-        constexpr int RW = 4;
-        for (int i0 = warp * RW; i0 < s; i0 += (kVecThreads / 32) * RW) {
-          C acc[RW];
-#pragma unroll
-          for (int qq = 0; qq < RW; ++qq) acc[qq] = C(0);
-#pragma unroll 8
-          for (int jj = lane; jj < len; jj += 32) {
-            const C wv = wch[jj];
-#pragma unroll
-            for (int qq = 0; qq < RW; ++qq)
-              if (i0 + qq < s) acc[qq] = fma(U[(int64_t)(i0 + qq) * d + j0 + jj], wv, acc[qq]);
-          }
-#pragma unroll
-          for (int qq = 0; qq < RW; ++qq) acc[qq] = warp_sum(acc[qq]);
-          if (lane == 0) {
-#pragma unroll
-            for (int qq = 0; qq < RW; ++qq)
-              if (i0 + qq < s) a.part_g[(int64_t)b * s + i0 + qq] = (double)acc[qq];
-          }
-        }
+        utw_partials<C>(wch, (int)(j1 - j0), U, d, j0, s, a.part_g + (int64_t)b * s);
       }
       if (!grid_barrier(&ctl->bar_count, &ctl->bar_gen, nblk)) return fail();
       for (int i = threadIdx.x; i < s; i += kVecThreads) {
-        double gsum = 0.0;
-#pragma unroll 8
-        for (int bb = 0; bb < a.nb3; ++bb) gsum += __ldcg(a.part_g + (int64_t)bb * s + i);
+        const double gsum = sum_strided_fixed<true>(a.part_g, a.nb3, s, i, 0.0);
         const C gi = (C)((double)cvec[i] * gsum);
         wch[i] = gi;
         if (b == 0) gs[i] = gi;
@@ -1241,9 +1208,7 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
         double lwy = 0.0;
         for (int64_t j = b * (int64_t)kVecThreads + threadIdx.x; j < d; j += (int64_t)a.nb5 * kVecThreads) {
           const C wj = __ldcg(w + j);
-          C acc = wj;
-#pragma unroll 16
-          for (int i = 0; i < s; ++i) acc = fma(U[(int64_t)i * d + j], wch[i], acc);
+          const C acc = urow_dot(U, d, j, s, wch, wj);
           y[j] = acc;
           p[j] = acc;
           lwy += (double)wj * (double)acc;
