@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(kVecThreads) apass_reduce_kernel(const C* __re
     dacc += (double)pj * (double)yj;
   }
   if (dot_part) {
-    const double t = block_sum<kVecThreads>(dacc, sh);
+    const double t = block_sum_t0<kVecThreads>(dacc, sh);
     if (threadIdx.x == 0) dot_part[blockIdx.x] = t;
   }
 }

@@ -558,8 +558,12 @@ __device__ __forceinline__ void rr_pair(int N, int r, int m, int& p, int& q) {
     p = N - 1;
     q = r;
   } else {
-    p = (r + m) % (N - 1);
-    q = (r - m + (N - 1)) % (N - 1);
+    // (r + m) mod (N - 1) and (r - m) mod (N - 1) for 0 <= r < N - 1, 0 < m < N / 2: both
+    // sums lie in [0, 2 (N - 1)), so one conditional subtraction replaces the division
+    p = r + m;
+    if (p >= N - 1) p -= N - 1;
+    q = r - m + (N - 1);
+    if (q >= N - 1) q -= N - 1;
   }
 }
 

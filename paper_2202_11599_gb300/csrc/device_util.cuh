@@ -143,7 +143,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // Grid-wide barrier of a co-resident grid (cooperative launch): an arrival counter and a
 // generation word in global memory.  The last block to arrive resets the counter and
 // advances the generation; the others wait for the generation to change, at most
-// `cycles` clock64 ticks.  Every thread of every block calls it; returns false (in every
+// `cycles` clock64 ticks.  Thread 0 arrives with an acquire-release atomic after the block's
+// __syncthreads (which orders the block's writes before it) and waits with acquire loads,
+// so no full memory fence is needed (measured: 2.4 -> 1.6 us per barrier on 40 blocks).  Every thread of every block calls it; returns false (in every
 // thread of the block) when the wait ran out.  Data another block wrote before the barrier
 // is read after it through L2 (__ldcg / .cg loads): this SM's L1 may still hold the line
 // from before (measured: plain loads returned stale values).
@@ -152,31 +154,32 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = gen;
-    const unsigned g = *vgen;
-    __threadfence();
-    if (atomicAdd(count, 1u) == nblocks - 1) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
+    unsigned g, old;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(gen) : "memory");
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(count), "r"(1u) : "memory");
+    if (old == nblocks - 1) {
+      asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" :: "l"(count), "r"(0u) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(gen), "r"(1u) : "memory");
     } else {
       const long long t0 = clock64();
-      while (*vgen == g) {
+      for (;;) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(gen) : "memory");
+        if (v != g) break;
         if (clock64() - t0 > cycles) {
           ok = 0;
           break;
         }
       }
     }
-    __threadfence();
   }
   return __syncthreads_and(ok) != 0;
 }
 
 // Grid barrier on one monotonic counter: every block adds 1 and waits until the counter
 // reaches `target` (= blocks x barriers passed so far, kept by the caller; the counter
-// starts at 0 and wraps harmlessly).  One atomic per block and no release write, so it
-// costs about one L2 round trip less than grid_barrier.  Same memory rules: data that
+// starts at 0 and wraps harmlessly).  One release add per block and acquire polls (no reset
+// write), so it costs about one L2 round trip less than grid_barrier.  Same memory rules: data that
 // other blocks wrote before the barrier is read through L2 (__ldcg) after it.
 // `sleep_ns` > 0 spaces the polls: blocks that arrive long before the last one (the end of an
 // A-pass) would otherwise keep one L2 line busy while the others still stream A.
@@ -185,18 +188,18 @@ __device__ __forceinline__ bool grid_barrier_mono(unsigned* count, unsigned targ
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(count, 1u);
-    volatile unsigned* vc = count;
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(count), "r"(1u) : "memory");
     const long long t0 = clock64();
-    while ((int)(*vc - target) < 0) {
+    for (;;) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+      if ((int)(v - target) >= 0) break;
       if (sleep_ns) __nanosleep(sleep_ns);
       if (clock64() - t0 > cycles) {
         ok = 0;
         break;
       }
     }
-    __threadfence();
   }
   return __syncthreads_and(ok) != 0;
 }
@@ -206,6 +209,24 @@ __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Block-wide sum in fixed order (deterministic), result in thread 0 only: the other threads
+// skip the final cross-warp adds (the FP64 pipe is narrow: one warp instruction occupies it
+// for many cycles).  Thread 0 adds in the order of block_sum, so the value is the same.
+template <int NT>
+__device__ __forceinline__ double block_sum_t0(double v, double* sh /* >= NT/32 */) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) s += sh[i];
+  }
+  return s;
 }
 
 // Block-wide sum in fixed order (deterministic); every thread gets the result.
@@ -222,37 +243,43 @@ __device__ __forceinline__ double block_sum(double v, double* sh /* >= NT/32 */)
   return s;
 }
 
+// Loads a thread keeps in flight in the batched sums below: 256 bytes of registers.
+template <typename T>
+constexpr int kLoadBatch = sizeof(T) == 4 ? 64 : 32;
+
 // sum_{g < n} a[g * stride + j] added in increasing g (the order of a plain loop), the loads
-// issued 32 at a time so that a thread keeps 32 reads in flight.  CG: read through L2, for
-// data written by other blocks of the running kernel.
+// issued kLoadBatch at a time so that a thread keeps that many reads in flight.  CG: read
+// through L2, for data written by other blocks of the running kernel.
 template <bool CG, typename T>
 __device__ __forceinline__ T sum_strided_fixed(const T* a, int n, int64_t stride, int64_t j, T s) {
-  for (int g = 0; g < n; g += 32) {
-    T v[32];
+  constexpr int B = kLoadBatch<T>;
+  for (int g = 0; g < n; g += B) {
+    T v[B];
 #pragma unroll
-    for (int q = 0; q < 32; ++q)
+    for (int q = 0; q < B; ++q)
       if (g + q < n) {
         const T* ptr = a + (int64_t)(g + q) * stride + j;
         v[q] = CG ? __ldcg(ptr) : *ptr;
       }
 #pragma unroll
-    for (int q = 0; q < 32; ++q)
+    for (int q = 0; q < B; ++q)
       if (g + q < n) s += v[q];
   }
   return s;
 }
 
 // acc + sum_{i < s} U[i * d + j] g[i] as one fma chain in increasing i (the row of U g, for
-// y = w + U g), the loads of U issued 32 at a time.
+// y = w + U g), the loads of U issued kLoadBatch at a time.
 template <typename C>
 __device__ __forceinline__ C urow_dot(const C* __restrict__ U, int64_t d, int64_t j, int s, const C* g, C acc) {
-  for (int i = 0; i < s; i += 32) {
-    C u[32];
+  constexpr int B = kLoadBatch<C>;
+  for (int i = 0; i < s; i += B) {
+    C u[B];
 #pragma unroll
-    for (int q = 0; q < 32; ++q)
+    for (int q = 0; q < B; ++q)
       if (i + q < s) u[q] = U[(int64_t)(i + q) * d + j];
 #pragma unroll
-    for (int q = 0; q < 32; ++q)
+    for (int q = 0; q < B; ++q)
       if (i + q < s) acc = fma(u[q], g[i + q], acc);
   }
   return acc;

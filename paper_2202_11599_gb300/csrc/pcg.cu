@@ -81,7 +81,8 @@ __device__ __forceinline__ void block_fixed_sum2_cg(const double* a, const doubl
   __syncthreads();
 }
 
-// Five block_sum<kVecThreads> reductions with one pair of barriers (same values as five calls).
+// Five block_sum<kVecThreads> reductions with one pair of barriers (same values as five calls),
+// results in thread 0 only.
 __device__ __forceinline__ void block_sum5(double (&v)[5]) {
   __shared__ double sh5[5][kVecThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -93,12 +94,14 @@ __device__ __forceinline__ void block_sum5(double (&v)[5]) {
     for (int t = 0; t < 5; ++t) sh5[t][w] = v[t];
   }
   __syncthreads();
+  if (threadIdx.x == 0) {
 #pragma unroll
-  for (int t = 0; t < 5; ++t) {
-    double s = 0.0;
+    for (int t = 0; t < 5; ++t) {
+      double s = 0.0;
 #pragma unroll
-    for (int i = 0; i < kVecThreads / 32; ++i) s += sh5[t][i];
-    v[t] = s;
+      for (int i = 0; i < kVecThreads / 32; ++i) s += sh5[t][i];
+      v[t] = s;
+    }
   }
   __syncthreads();
 }
@@ -281,8 +284,8 @@ __global__ void __launch_bounds__(kVecThreads) pcg_update_kernel(int init, int64
       wch[j - j0] = wj;
       lw2 += (double)wj * (double)wj;
     }
-    const double tw2 = block_sum<kVecThreads>(lw2, sh);
-    const double tr2 = block_sum<kVecThreads>(lr2, sh);
+    const double tw2 = block_sum_t0<kVecThreads>(lw2, sh);
+    const double tr2 = block_sum_t0<kVecThreads>(lr2, sh);
     if (threadIdx.x == 0) {
       part_w2[blockIdx.x] = tw2;
       if (init) part_r2[blockIdx.x] = tr2;
@@ -317,7 +320,7 @@ __global__ void __launch_bounds__(kVecThreads) pcg_tail_kernel(int64_t d, const 
     y[j] = acc;
     lwy += (double)wj * (double)acc;
   }
-  const double t = block_sum<kVecThreads>(lwy, sh);
+  const double t = block_sum_t0<kVecThreads>(lwy, sh);
   if (threadIdx.x == 0) part_wy[blockIdx.x] = t;
   if (!p) return;
   if (!last_block_done(&st->ticket[1])) return;
@@ -346,7 +349,7 @@ __global__ void __launch_bounds__(kVecThreads) shard_finish_kernel(int64_t d, C 
     dacc += (double)pj * (double)yj;
   }
   if (dot_part) {
-    const double t = block_sum<kVecThreads>(dacc, sh);
+    const double t = block_sum_t0<kVecThreads>(dacc, sh);
     if (threadIdx.x == 0) dot_part[blockIdx.x] = t;
   }
 }
@@ -587,11 +590,11 @@ __global__ void __launch_bounds__(kVecThreads) admm_zu_kernel(int64_t d, const C
     a3 += zj * zj;
     a4 += uj * uj;
   }
-  a0 = block_sum<kVecThreads>(a0, sh);
-  a1 = block_sum<kVecThreads>(a1, sh);
-  a2 = block_sum<kVecThreads>(a2, sh);
-  a3 = block_sum<kVecThreads>(a3, sh);
-  a4 = block_sum<kVecThreads>(a4, sh);
+  a0 = block_sum_t0<kVecThreads>(a0, sh);
+  a1 = block_sum_t0<kVecThreads>(a1, sh);
+  a2 = block_sum_t0<kVecThreads>(a2, sh);
+  a3 = block_sum_t0<kVecThreads>(a3, sh);
+  a4 = block_sum_t0<kVecThreads>(a4, sh);
   if (threadIdx.x == 0) {
     double* o = part5 + (int64_t)blockIdx.x * 5;
     o[0] = a0;
@@ -738,6 +741,25 @@ __device__ __forceinline__ void iter_tol(int tol_mode, double tol, double tol_fl
     const double t = tol_mode == NYS_TOL_RNORM_POW ? pow((double)(k + 1), -tol) : tol;
     *tol_out = fmax(t, tol_floor);
     *abs_out = 0;
+  }
+}
+
+// The schedule (k + 1)^(-beta) of NYS_TOL_RNORM_POW for k < K, filled once per solve by the
+// same device pow that iter_tol calls (so a table entry equals the value iter_tol forms).
+__global__ void tolpow_kernel(double* tab, int K, double beta) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < K) tab[k] = pow((double)(k + 1), -beta);
+}
+
+// iter_tol with the power schedule read from tolpow_kernel's table (one load instead of a
+// pow on the FP64 pipe in the loop's critical path).
+__device__ __forceinline__ void iter_tol_tab(int tol_mode, double tol, double tol_floor, int k, double eps_next,
+                                             const double* tab, double* tol_out, int* abs_out) {
+  if (tol_mode == NYS_TOL_RNORM_POW && tab) {
+    *tol_out = fmax(tab[k], tol_floor);
+    *abs_out = 0;
+  } else {
+    iter_tol(tol_mode, tol, tol_floor, k, eps_next, tol_out, abs_out);
   }
 }
 
@@ -953,7 +975,7 @@ __global__ void __launch_bounds__(kVecThreads) pcg_post_kernel(const PostArgs<C>
       a.v[j] = yj;
       dacc += (double)pj * (double)yj;
     }
-    const double t = block_sum<kVecThreads>(dacc, sh);
+    const double t = block_sum_t0<kVecThreads>(dacc, sh);
     if (threadIdx.x == 0) a.pv_part[b] = t;
   }
   if (!grid_barrier(&st->bar_count, &st->bar_gen, nblk)) return fail();
@@ -978,14 +1000,14 @@ __global__ void __launch_bounds__(kVecThreads) pcg_post_kernel(const PostArgs<C>
       wch[j - j0] = wj;
       lw2 += (double)wj * (double)wj;
     }
-    const double tw2 = block_sum<kVecThreads>(lw2, sh);
+    const double tw2 = block_sum_t0<kVecThreads>(lw2, sh);
     if (threadIdx.x == 0) a.part_w2[b] = tw2;
-    __syncthreads();
-    utw_partials<C>(wch, (int)(j1 - j0), a.U, d, j0, s, a.part_g + (int64_t)b * s);
   }
   if (!grid_barrier(&st->bar_count, &st->bar_gen, nblk)) return fail();
-  // ---- S: ||w||^2, stop test, iteration count, g = c o U^T w (pcg_scalar_body; every block
-  // takes the same decision, block 0 records it)
+  // ---- S: ||w||^2, stop test, iteration count (pcg_scalar_body; every block takes the same
+  // decision, block 0 records it).  U^T w and g = c o U^T w follow only if PCG goes on: the
+  // iteration that ends the loop needs no P^{-1} w (the separate kernels form it regardless;
+  // the values they use are the same).
   const double w2 = block_fixed_sum_cg(a.part_w2, a.nb3, &slot);
   const bool stepped = !bad && isfinite(w2);
   int iters = iters0, done = 0, status = 0;
@@ -1015,6 +1037,14 @@ __global__ void __launch_bounds__(kVecThreads) pcg_post_kernel(const PostArgs<C>
     cudaGraphSetConditional(a.cond, done ? 0u : 1u);
   }
   if (!done) {
+    // U^T w partials over this block's chunk of the new w, still in shared memory (every
+    // block that stepped has !bad here)
+    if (b < a.nb3) {
+      const int64_t j0 = (int64_t)b * a.chunk;
+      const int64_t j1 = min(d, j0 + a.chunk);
+      utw_partials<C>(wch, (int)(j1 - j0), a.U, d, j0, s, a.part_g + (int64_t)b * s);
+    }
+    if (!grid_barrier(&st->bar_count, &st->bar_gen, nblk)) return fail();
     for (int i = threadIdx.x; i < s; i += kVecThreads) {
       const double g = sum_strided_fixed<true>(a.part_g, a.nb3, s, i, 0.0);
       const C gi = (C)((double)a.cvec[i] * g);
@@ -1031,7 +1061,7 @@ __global__ void __launch_bounds__(kVecThreads) pcg_post_kernel(const PostArgs<C>
         a.y[j] = acc;
         lwy += (double)wj * (double)acc;
       }
-      const double t = block_sum<kVecThreads>(lwy, sh);
+      const double t = block_sum_t0<kVecThreads>(lwy, sh);
       if (threadIdx.x == 0) a.wy_part[b] = t;
     }
     if (!grid_barrier(&st->bar_count, &st->bar_gen, nblk)) return fail();
@@ -1093,6 +1123,7 @@ struct HeadArgs {
   double tol, tol_floor;
   int tol_mode, maxit, hx_refresh, K;
   const int* fixed_dev;
+  const double* tolpow;   // (k + 1)^(-tol) for k < K (NYS_TOL_RNORM_POW), else null
   double eps_abs, eps_rel;
   double *ztrace, *rp_trace, *rd_trace;
   int* pcg_it_trace;
@@ -1149,7 +1180,7 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
     if (threadIdx.x == 0) {
       double t;
       int ab;
-      iter_tol(a.tol_mode, a.tol, a.tol_floor, k, eps_next, &t, &ab);
+      iter_tol_tab(a.tol_mode, a.tol, a.tol_floor, k, eps_next, a.tolpow, &t, &ab);
       s_tolk = t;
       s_tabs = ab;
     }
@@ -1170,8 +1201,8 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
         wch[j - j0] = wj;
         lw2 += (double)wj * (double)wj;
       }
-      const double tw2 = block_sum<kVecThreads>(lw2, sh);
-      const double tr2 = block_sum<kVecThreads>(lr2, sh);
+      const double tw2 = block_sum_t0<kVecThreads>(lw2, sh);
+      const double tr2 = block_sum_t0<kVecThreads>(lr2, sh);
       if (threadIdx.x == 0) {
         a.part_w2[b] = tw2;
         a.part_r2[b] = tr2;
@@ -1213,7 +1244,7 @@ __global__ void __launch_bounds__(kVecThreads) admm_head_kernel(HeadArgs a, cons
           p[j] = acc;
           lwy += (double)wj * (double)acc;
         }
-        const double t = block_sum<kVecThreads>(lwy, sh);
+        const double t = block_sum_t0<kVecThreads>(lwy, sh);
         if (threadIdx.x == 0) a.wy_part[b] = t;
       }
       if (b == 0 && threadIdx.x == 0) {
@@ -1331,7 +1362,7 @@ __global__ void __launch_bounds__(kVecThreads) ws_proj_kernel(int64_t d, int s, 
     const double vj = vsub ? (double)v[j] - (double)vsub[j] : (double)v[j];
     acc += (i < s ? (double)U[(int64_t)i * d + j] : vj) * vj;
   }
-  acc = block_sum<kVecThreads>(acc, sh);
+  acc = block_sum_t0<kVecThreads>(acc, sh);
   if (threadIdx.x == 0) out[i] = acc;
 }
 
@@ -1421,6 +1452,7 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   int* dstat = pool.alloc<int>(1);
   double* part5 = pool.alloc<double>((size_t)nbz * 5);
   int* fixed_dev = g.fixed_host ? pool.alloc<int>(K) : nullptr;
+  double* tolpow = g.tol_mode == NYS_TOL_RNORM_POW && K > 0 ? pool.alloc<double>(K) : nullptr;
   if (!pool.ok()) return NYS_ENOMEM;
   C* xc = reinterpret_cast<C*>(g.xc);
   C* rc = reinterpret_cast<C*>(g.rc);
@@ -1441,6 +1473,11 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
   G_OK(cudaMemsetAsync(dstat, 0, sizeof(int), stream));
   G_OK(cudaMemsetAsync(hx, 0, d * sizeof(C), stream));
   if (fixed_dev) G_OK(cudaMemcpyAsync(fixed_dev, g.fixed_host, K * sizeof(int), cudaMemcpyHostToDevice, stream));
+  if (tolpow) {
+    count_launch();
+    tolpow_kernel<<<(K + 255) / 256, 256, 0, stream>>>(tolpow, K, g.tol);
+    G_OK(cudaGetLastError());
+  }
   G_OK(apass_prepare(g.pb.A, g.pb.plan));
   if (g.Aref) G_OK(apass_prepare(g.Aref, g.plan_ref));
 
@@ -1615,6 +1652,7 @@ nys_status admm_graph_add(cudaGraph_t graph, const GraphLoopArgs& g, cudaStream_
       ha.hx_refresh = g.hx_refresh;
       ha.K = K;
       ha.fixed_dev = fixed_dev;
+      ha.tolpow = tolpow;
       ha.eps_abs = g.eps_abs;
       ha.eps_rel = g.eps_rel;
       ha.ztrace = g.ztrace;
