@@ -225,8 +225,10 @@ nys_status nystrom_core(const double* Om, const double* Y, int64_t d, int s, dou
   }
   int sweeps = 0;
   {
+    // B^T B carries the sketch's rounding (unit roundoff 2^-(mant_bits + 1), relative): the
+    // sweeps stop at that level, and at off(B^T B) <= 1e-12 ||B^T B||_F for an FP64 sketch
     PhaseTimer pt("core: jacobi", st);
-    NYS_CU(jacobi_eig(G, V, s, jw, &sweeps, st));
+    NYS_CU(jacobi_eig(G, V, s, jw, &sweeps, st, std::max(1e-12, std::ldexp(1.0, -mant_bits - 1))));
   }
   {
     PhaseTimer pt("core: finish (U = BV)", st);

@@ -847,9 +847,11 @@ size_t jacobi_work_bytes(int s) {
 
 // Eigendecomposition of the symmetric s x s matrix G.  Results: eigenvalues on the
 // diagonal of `evals_mat` (N x N, in work), eigenvectors in the columns of Vout (N x N).
-// work layout: A0 (N*N), A1 (N*N), V (N*N), flags.
-cudaError_t jacobi_eig(double* G, double* Vout, int s, double* work, int* sweeps_out, cudaStream_t st) {
+// work layout: A0 (N*N), A1 (N*N), V (N*N), flags.  Sweeps stop once the off-diagonal
+// Frobenius norm is at most tol times the whole matrix's.
+cudaError_t jacobi_eig(double* G, double* Vout, int s, double* work, int* sweeps_out, cudaStream_t st, double tol) {
   const int N = s + (s & 1);
+  const double tol_sq = tol * tol;
   double* A0 = work;
   double* A1 = work + (size_t)N * N;
   int* done = reinterpret_cast<int*>(work + (size_t)3 * N * N);
@@ -876,7 +878,7 @@ cudaError_t jacobi_eig(double* G, double* Vout, int s, double* work, int* sweeps
       double* a1 = A1;
       double* vv = Vout;
       int n = N, ms = kMaxSweeps;
-      double tol2 = 1e-24;
+      double tol2 = tol_sq;
       void* args[] = {&a0, &a1, &vv, &n, &ms, &tol2, &part, &ctl};
       count_launch();
       NYS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_persistent_kernel, blocks, dim3(JT * JT), args, 0, st));
@@ -942,7 +944,7 @@ cudaError_t jacobi_eig(double* G, double* Vout, int s, double* work, int* sweeps
     }
     NYS_CUDA_TRY(cudaGetLastError());
     count_launch();
-    jacobi_offnorm_kernel<<<1, 256, 0, st>>>(cur, N, 1e-24, done, offv);
+    jacobi_offnorm_kernel<<<1, 256, 0, st>>>(cur, N, tol_sq, done, offv);
     NYS_CUDA_TRY(cudaMemcpyAsync(&done_h, done, sizeof(int), cudaMemcpyDeviceToHost, st));
     NYS_CUDA_TRY(cudaStreamSynchronize(st));
     if (trace)

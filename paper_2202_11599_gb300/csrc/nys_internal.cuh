@@ -95,8 +95,9 @@ cudaError_t axpy_panel(double nu, const double* X, double* Y, int64_t n, cudaStr
 // lambda_max of a symmetric s x s matrix by power iteration (device scalar out)
 cudaError_t power_lambda_max(const double* G, int s, double* out, double* work, cudaStream_t st);
 // Symmetric eigendecomposition by parallel cyclic Jacobi: G (s x s, overwritten) -> V (s x s),
-// eigenvalues in the diagonal.  Returns sweeps used in *sweeps (host).
-cudaError_t jacobi_eig(double* G, double* V, int s, double* work, int* sweeps, cudaStream_t st);
+// eigenvalues in the diagonal.  Sweeps stop once off(A) <= tol ||A||_F.  Returns sweeps used
+// in *sweeps (host).
+cudaError_t jacobi_eig(double* G, double* V, int s, double* work, int* sweeps, cudaStream_t st, double tol = 1e-12);
 size_t jacobi_work_bytes(int s);
 // After Jacobi: sort eigenpairs descending, U = B V Sigma^{-1}, lam = max(0, sigma^2 - nu).
 cudaError_t nystrom_finish(const double* B, int64_t d, int s, const double* G, const double* V,
