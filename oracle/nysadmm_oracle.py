@@ -34,6 +34,12 @@ Readings where the paper is silent or ambiguous (the same readings as the CUDA p
     while A^T b comes from the problem matrix A, so the iteration solves the perturbed
     problem 1/2 x^T A_inner^T A_inner x - (A^T b)^T x + gamma ||x||_1; the sketch shift
     then uses the FP32 eps (mantissa_bits = 23).
+  * Test matrix of an FP32-class sketch (mantissa_bits = 23): the orthonormal factor of
+    qr(Omega, 0) rounded to BF16 values (FP64 -> FP32 -> BF16, each to nearest, ties to
+    even), and that rounded matrix is the Omega of every later step (Y = H Omega, the
+    shift, Omega^T Y_nu).  The Nystrom approximation depends on Omega only through its
+    range and holds for any full-rank test matrix; the rounded one is orthonormal to
+    about 2^-8.
 
 Functions with no independent pin: none (every function here is pinned by a
 test in tests/test_oracle_pins.py against closed forms, library solvers,
@@ -142,6 +148,23 @@ def thin_qr(Omega: np.ndarray) -> np.ndarray:
     return Q
 
 
+def round_to_bf16(X: np.ndarray) -> np.ndarray:
+    """Each entry rounded to the nearest BF16 value through FP32: FP64 -> FP32 to nearest,
+    then the FP32 bit pattern rounded to its top 16 bits, to nearest with ties to even
+    (returned as FP64).  Used for the test matrix of an FP32-class sketch."""
+    f = np.asarray(X, dtype=np.float64).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def sketch_test_matrix(Omega: np.ndarray, mantissa_bits: int = 52) -> np.ndarray:
+    """The test matrix the sketch uses: qr(Omega, 0) (Alg. Randomized Nystrom
+    Approximation), rounded to BF16 values for an FP32-class sketch (mantissa_bits = 23)."""
+    Q = thin_qr(Omega)
+    return round_to_bf16(Q) if mantissa_bits == 23 else Q
+
+
 def nystrom_from_sketch(Y: np.ndarray, Omega: np.ndarray, shift_scale: float = 1.0,
                         mantissa_bits: int = 52, max_retries: int = 3):
     """Steps after Y = H Omega of the randomized Nystrom approximation:
@@ -180,8 +203,9 @@ def nystrom_from_sketch(Y: np.ndarray, Omega: np.ndarray, shift_scale: float = 1
 def nystrom(H_apply, Omega: np.ndarray, shift_scale: float = 1.0, mantissa_bits: int = 52):
     """Alg. Randomized Nystrom Approximation: H_apply(X) returns H X.
 
-    Omega is the Gaussian test matrix (d x s); it is orthonormalised here."""
-    Q = thin_qr(Omega)
+    Omega is the Gaussian test matrix (d x s); it is orthonormalised here (and rounded
+    to BF16 values for an FP32-class sketch, mantissa_bits = 23)."""
+    Q = sketch_test_matrix(Omega, mantissa_bits)
     Y = H_apply(Q)
     U, lam, nu = nystrom_from_sketch(Y, Q, shift_scale, mantissa_bits)
     return U, lam, nu, Q, Y
@@ -469,7 +493,7 @@ def adaptive_nystrom(H_apply, Omega_pool: np.ndarray, s0: int, s_max: int, rho: 
     used = 0
     ranks = []
     while True:
-        Om0 = thin_qr(Omega_pool[:, used:used + m])
+        Om0 = sketch_test_matrix(Omega_pool[:, used:used + m], mantissa_bits)
         used += m
         Y0 = H_apply(Om0)
         Om = np.hstack([Om, Om0])
@@ -484,7 +508,7 @@ def adaptive_nystrom(H_apply, Omega_pool: np.ndarray, s0: int, s_max: int, rho: 
             s0 = s0 - m
             m = s_max - s0
             if m > 0:
-                Om0 = thin_qr(Omega_pool[:, used:used + m])
+                Om0 = sketch_test_matrix(Omega_pool[:, used:used + m], mantissa_bits)
                 used += m
                 Y0 = H_apply(Om0)
                 Om = np.hstack([Om, Om0])

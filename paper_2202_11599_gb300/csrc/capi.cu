@@ -126,12 +126,14 @@ nys_status cholqr2(double* Om, int64_t d, int m, cudaStream_t st) {
 
 // Y (d x m, FP64) = (A^T diag(D) A + shift I) Om for an FP64 orthonormal panel Om.
 // prep: tensor-core operands of A prepared once by the caller (repeated sketches of the
-// same matrix), or NULL.
-nys_status sketch_panel(const nys_matrix* A, const double* D, double shift, const double* Om, int m, double* Y,
+// same matrix), or NULL.  For a low-precision matrix (an FP32-class sketch) Om is first
+// rounded in place to BF16 values; the caller's later steps use that rounded Om.
+nys_status sketch_panel(const nys_matrix* A, const double* D, double shift, double* Om, int m, double* Y,
                         cudaStream_t st, const TcPrepared* prep = nullptr) {
   PhaseTimer pt("sketch Y = H Omega", st);
   Pool pool(st);
   const int64_t n = A->n, d = A->d;
+  if (A->dtype != NYS_F64 && A->dtype != NYS_FP8E4M3) NYS_CU(round_panel_bf16(Om, d * m, st));
   if (A->dtype == NYS_FP8E4M3) {
     // FP8: sketch the dequantised matrix (s_j q_ij in FP32, exact products of the 4-bit
     // codes and the scales up to FP32 rounding) through the FP32 path

@@ -125,9 +125,13 @@ bool sketch_tc_supported(const nys_matrix* A);
 size_t tc_prepare_bytes(const nys_matrix* A);
 cudaError_t tc_prepare(const nys_matrix* A, void* scratch, TcPrepared* prep, cudaStream_t st);
 // Y (d x m, col-major FP64) = A^T diag(D) A Om (the sketch of App. B) on the tensor cores.
+// Om must hold BF16 values (round_panel_bf16): the first product takes it as one term.
 cudaError_t sketch_tc(const nys_matrix* A, const double* D, const double* Om, int m, double* Y, cudaStream_t st);
 cudaError_t sketch_tc_with(const nys_matrix* A, const TcPrepared& prep, const double* D, const double* Om, int m,
                            double* Y, cudaStream_t st);
+// X (n values, FP64) <- each entry rounded to the nearest BF16 value through FP32 (to nearest,
+// ties to even): the test matrix of an FP32-class sketch.
+cudaError_t round_panel_bf16(double* X, int64_t n, cudaStream_t st);
 // Y (d x k) = A^T diag(D) A X + rho X, FP32 X and Y column-major (multi-RHS H-matvec).
 cudaError_t tc_hmm(const nys_matrix* A, const TcPrepared& prep, const double* D, const float* X, int k, double rho,
                    float* Y, cudaStream_t st);

@@ -4,13 +4,15 @@
 //   W  = diag(D) A Omega        (n x s)   GEMM 1: M = n (rows of A), N = s, K = d
 //   Y  = A^T W                  (d x s)   GEMM 2: M = d, N = s, K = n (split over K)
 //
-// The FP32 operand of each product (Omega, then W) is written as the sum of three BF16
-// terms (x = t1 + t2 + t3 holds exactly for every float x: each term takes the next 8
-// significant bits), and A is BF16 already, so every product a * t_k is exact and the
-// tensor core accumulates them in FP32: the result is an FP32-class GEMM at tensor-core
-// rates (3 MMAs per K step instead of 1).
+// The test matrix Omega of an FP32-class sketch holds BF16 values (the orthonormal factor
+// rounded once; the rest of the Nystrom core uses that same Omega), so GEMM 1 is a plain
+// BF16 x BF16 product.  W is FP32 and is written as the sum of three BF16 terms (x = t1 +
+// t2 + t3 holds exactly for every float x: each term takes the next 8 significant bits),
+// and A is BF16 already, so every product a * t_k is exact and the tensor core accumulates
+// them in FP32: GEMM 2 is an FP32-class GEMM at tensor-core rates (3 MMAs per K step).
 //
-// Kernel design (one CTA = one 128-row tile of the output, the full N = s <= 256 in TMEM):
+// Kernel design (one CTA = two 128-row tiles of the output sharing each staged B tile, the
+// full N = s <= 256 of each in TMEM):
 //   * both operands are K-major: GEMM 1 reads the rows of A directly, GEMM 2 reads a
 //     transposed copy of A made once per sketch (2 GB of the 280 GB HBM for the paper's
 //     largest single-GPU problem); W is written by GEMM 1 already in the K-major layout
@@ -139,39 +141,53 @@ __device__ __forceinline__ void split3(float x, uint16_t (&t)[3]) {
   t[2] = bf16_bits(r2);
 }
 
-// AT = number of BF16 terms of the A operand: 1 (BF16 storage) or 3 (FP32 storage split
-// exactly into three BF16 terms).  With AT = 3 a K step issues the six MMAs a_i x b_j with
-// i + j <= 2 (0-based): the three dropped products are below 2^-24 of the result.
-template <int AT> constexpr int tc_npairs() { return AT == 1 ? 3 : 6; }
-// pair pr -> (A term, B term): AT = 1: (0,0) (0,1) (0,2); AT = 3: (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
-template <int AT> __host__ __device__ constexpr int tc_pair_a(int pr) {
-  return AT == 1 ? 0 : (pr == 2 || pr == 4 ? 1 : (pr == 5 ? 2 : 0));
+// AT, BT = number of BF16 terms of the A and B operands: 1 (BF16 values) or 3 (FP32 values
+// split exactly into three BF16 terms).  A K step issues the MMAs a_i x b_j with i + j <= 2
+// (0-based): with AT = BT = 3 the three dropped products are below 2^-24 of the result.
+template <int AT, int BT> constexpr int tc_npairs() { return AT == 3 && BT == 3 ? 6 : (AT == 1 && BT == 1 ? 1 : 3); }
+// pair pr -> (A term, B term):
+//   AT = 1: (0,0) (0,1) (0,2);  BT = 1: (0,0) (1,0) (2,0);
+//   AT = BT = 3: (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+template <int AT, int BT> __host__ __device__ constexpr int tc_pair_a(int pr) {
+  return AT == 1 ? 0 : (BT == 1 ? pr : (pr == 2 || pr == 4 ? 1 : (pr == 5 ? 2 : 0)));
 }
-template <int AT> __host__ __device__ constexpr int tc_pair_b(int pr) {
-  return AT == 1 ? pr : (pr == 1 || pr == 4 ? 1 : (pr == 3 ? 2 : 0));
+template <int AT, int BT> __host__ __device__ constexpr int tc_pair_b(int pr) {
+  return BT == 1 ? 0 : (AT == 1 ? pr : (pr == 1 || pr == 4 ? 1 : (pr == 3 ? 2 : 0)));
 }
-template <int AT> constexpr int tc_stages() { return AT == 1 ? TC_STAGES : 3; }
+// Bytes of one pipeline stage at the largest N: BM2 accumulators of 128 rows x AT terms of
+// A, and BT terms of B.  Stages fill about 224 KB of shared memory, at most 6.
+template <int AT, int BT, int BM2> constexpr int tc_stage_max_bytes() {
+  return BM2 * AT * TC_BM * TC_BK * 2 + BT * TC_NMAX * TC_BK * 2;
+}
+template <int AT, int BT, int BM2> constexpr int tc_stages() {
+  return (224 * 1024) / tc_stage_max_bytes<AT, BT, BM2>() < 6 ? (224 * 1024) / tc_stage_max_bytes<AT, BT, BM2>() : 6;
+}
 
-template <int EPI, int AT>
+// BM2 accumulators per CTA (1 or 2): a CTA computes BM2 x 128 output rows, every staged
+// tile of B serving both (half the B traffic from L2 per output row); accumulator h sits
+// at TMEM columns [256 h, 256 h + N).
+template <int EPI, int AT, int BT, int BM2>
 __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const TcArgs a) {
-  constexpr int TC_STAGES = tc_stages<AT>();
+  constexpr int TC_STAGES = tc_stages<AT, BT, BM2>();
+  constexpr uint32_t kTmemCols = BM2 == 2 ? 2 * TC_NMAX : TC_NMAX;
+  static_assert(TC_STAGES >= 2, "shared memory holds fewer than two stages");
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mma_bar[TC_STAGES];
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * TC_BM;
+  const int64_t m0 = (int64_t)blockIdx.x * (TC_BM * BM2);
   const int64_t kt0 = (int64_t)blockIdx.y * a.kslice;
   const int64_t kt1 = min(a.ktiles, kt0 + a.kslice);
   const int nkt = (int)max((int64_t)0, kt1 - kt0);
   const uint32_t a_bytes = TC_BM * TC_BK * 2;
   const uint32_t b_bytes = (uint32_t)a.NP * TC_BK * 2;
-  const uint32_t stage_bytes = AT * a_bytes + TC_TERMS * b_bytes;
+  const uint32_t stage_bytes = BM2 * AT * a_bytes + BT * b_bytes;
   const uint32_t sbase = smem_u32(smem);
   const uint32_t lbo = a.desc_swap ? TC_SBO : TC_LBO, sbo = a.desc_swap ? TC_LBO : TC_SBO;
   const uint32_t idesc = mma_idesc_bf16(TC_BM, a.NP);
 
   if (warp == 0) {
-    tmem_alloc(&tmem_slot, TC_NMAX);
+    tmem_alloc(&tmem_slot, kTmemCols);
     tmem_relinquish();
   }
   if (tid == 0) {
@@ -189,24 +205,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const TcArgs a
   auto load_stage = [&](int ktl, int stage) {
     const int64_t k0 = (kt0 + ktl) * TC_BK;
     const uint32_t st = sbase + (uint32_t)stage * stage_bytes;
-    for (int q = tid; q < AT * TC_BM * 4; q += TC_THREADS) {
-      const int ta = q / (TC_BM * 4), qa = q - ta * (TC_BM * 4);
+    for (int q = tid; q < BM2 * AT * TC_BM * 4; q += TC_THREADS) {
+      const int ht = q / (TC_BM * 4), qa = q - ht * (TC_BM * 4);   // ht = h * AT + ta
+      const int h = ht / AT, ta = ht - h * AT;
       const int r8 = qa & 7, c = (qa >> 3) & 3, g = qa >> 5;
-      const int64_t row = m0 + g * 8 + r8, k = k0 + c * 8;
+      const int64_t row = m0 + h * TC_BM + g * 8 + r8, k = k0 + c * 8;
       uint32_t bytes = 0;
       const uint16_t* src = a.A;
       if (row < a.Mrows && k < a.Kvalid) {
         bytes = (uint32_t)min((int64_t)16, (a.Kvalid - k) * 2);
         src = a.A + ta * a.aterm + row * a.lda + k;
       }
-      cp_async16(st + (uint32_t)ta * a_bytes + (uint32_t)qa * 16u, src, bytes);
+      cp_async16(st + (uint32_t)ht * a_bytes + (uint32_t)qa * 16u, src, bytes);
     }
     const int per_term = a.NP * 4;
-    for (int q = tid; q < TC_TERMS * per_term; q += TC_THREADS) {
+    for (int q = tid; q < BT * per_term; q += TC_THREADS) {
       const int t = q / per_term, qq = q - t * per_term;
       const int r8 = qq & 7, c = (qq >> 3) & 3, g = qq >> 5;
       const uint16_t* src = a.B + t * a.bterm + (int64_t)(g * 8 + r8) * a.ldb + k0 + c * 8;
-      cp_async16(st + AT * a_bytes + (uint32_t)t * b_bytes + (uint32_t)qq * 16u, src, 16u);
+      cp_async16(st + BM2 * AT * a_bytes + (uint32_t)t * b_bytes + (uint32_t)qq * 16u, src, 16u);
     }
   };
 
@@ -226,11 +243,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const TcArgs a
 #pragma unroll
       for (int kk = 0; kk < TC_BK / 16; ++kk) {
 #pragma unroll
-        for (int pr = 0; pr < tc_npairs<AT>(); ++pr) {
-          const uint64_t ad = smem_desc(st + (uint32_t)tc_pair_a<AT>(pr) * a_bytes + kk * 256u, lbo, sbo);
-          const uint64_t bd =
-              smem_desc(st + AT * a_bytes + (uint32_t)tc_pair_b<AT>(pr) * b_bytes + kk * 256u, lbo, sbo);
-          mma_bf16(tmem, ad, bd, idesc, (kt | kk | pr) != 0 ? 1u : 0u);
+        for (int h = 0; h < BM2; ++h) {
+#pragma unroll
+          for (int pr = 0; pr < tc_npairs<AT, BT>(); ++pr) {
+            const uint64_t ad =
+                smem_desc(st + (uint32_t)(h * AT + tc_pair_a<AT, BT>(pr)) * a_bytes + kk * 256u, lbo, sbo);
+            const uint64_t bd =
+                smem_desc(st + BM2 * AT * a_bytes + (uint32_t)tc_pair_b<AT, BT>(pr) * b_bytes + kk * 256u, lbo, sbo);
+            mma_bf16(tmem + (uint32_t)(h * TC_NMAX), ad, bd, idesc, (kt | kk | pr) != 0 ? 1u : 0u);
+          }
         }
       }
       mma_commit(&mma_bar[stage]);
@@ -256,36 +277,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const TcArgs a
 
   if (ok) {
     const int quad = warp & 3;
-    const int64_t row = m0 + 32 * quad + lane;
     const int half = a.NP / 2;
     const int cb = (warp >> 2) * half;
-    const uint32_t trow = tmem + ((uint32_t)(32 * quad) << 16);
-    double dr = 1.0;
-    if (EPI == 0 && a.D && row < a.Mrows) dr = a.D[row];
-    for (int c0 = cb; c0 < cb + half; c0 += 8) {
-      uint32_t v[8];
-      tmem_ld8(trow + (uint32_t)c0, v);
-      tmem_ld_wait(v);
-      if (nkt == 0) {
+    for (int h = 0; h < BM2; ++h) {
+      const int64_t row = m0 + h * TC_BM + 32 * quad + lane;
+      const uint32_t trow = tmem + (uint32_t)(h * TC_NMAX) + ((uint32_t)(32 * quad) << 16);
+      double dr = 1.0;
+      if (EPI == 0 && a.D && row < a.Mrows) dr = a.D[row];
+      for (int c0 = cb; c0 < cb + half; c0 += 8) {
+        uint32_t v[8];
+        tmem_ld8(trow + (uint32_t)c0, v);
+        tmem_ld_wait(v);
+        if (nkt == 0) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = 0u;
-      }
-      if (EPI == 0) {
-        if (row < a.wrows) {
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const float x = row < a.Mrows ? (float)(dr * (double)__uint_as_float(v[e])) : 0.f;
-            uint16_t t3[3];
-            split3(x, t3);
-#pragma unroll
-            for (int t = 0; t < TC_TERMS; ++t) a.Wt[t * a.wterm + (int64_t)(c0 + e) * a.ldw + row] = t3[t];
-          }
+          for (int e = 0; e < 8; ++e) v[e] = 0u;
         }
-      } else {
-        if (row < a.Mrows) {
-          float* P = a.P + (int64_t)blockIdx.y * a.NP * a.ldp;
+        if (EPI == 0) {
+          if (row < a.wrows) {
 #pragma unroll
-          for (int e = 0; e < 8; ++e) P[(int64_t)(c0 + e) * a.ldp + row] = __uint_as_float(v[e]);
+            for (int e = 0; e < 8; ++e) {
+              const float x = row < a.Mrows ? (float)(dr * (double)__uint_as_float(v[e])) : 0.f;
+              uint16_t t3[3];
+              split3(x, t3);
+#pragma unroll
+              for (int t = 0; t < TC_TERMS; ++t) a.Wt[t * a.wterm + (int64_t)(c0 + e) * a.ldw + row] = t3[t];
+            }
+          }
+        } else {
+          if (row < a.Mrows) {
+            float* P = a.P + (int64_t)blockIdx.y * a.NP * a.ldp;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) P[(int64_t)(c0 + e) * a.ldp + row] = __uint_as_float(v[e]);
+          }
         }
       }
     }
@@ -296,12 +319,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const TcArgs a
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, TC_NMAX);
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
 // Operand terms: Ot[t][c][k] (c < NP, k < KP) = t-th BF16 term of float(X[k + (c0 + c) d]),
 // zero outside c < mp, k < d.  X is d x m column-major (FP64 or FP32).
-template <typename T>
+// NT = 1: X holds BF16 values (the rounded test matrix of the sketch), its one term is exact.
+template <typename T, int NT>
 __global__ void split_operand_kernel(const T* __restrict__ X, int64_t d, int c0, int mp, int NP, int64_t KP,
                                      uint16_t* __restrict__ Ot) {
   const int64_t total = (int64_t)NP * KP;
@@ -314,7 +338,7 @@ __global__ void split_operand_kernel(const T* __restrict__ X, int64_t d, int c0,
     uint16_t t3[3];
     split3(x, t3);
 #pragma unroll
-    for (int t = 0; t < TC_TERMS; ++t) Ot[t * total + idx] = t3[t];
+    for (int t = 0; t < NT; ++t) Ot[t * total + idx] = t3[t];
   }
 }
 
@@ -400,22 +424,29 @@ int pick_slices(int64_t mtiles, int64_t ktiles, int sms) {
   return best;
 }
 
-template <int EPI, int AT>
+template <int EPI, int AT, int BT, int BM2>
 cudaError_t launch_tc(const TcArgs& a, dim3 grid, cudaStream_t st) {
-  constexpr int ST = tc_stages<AT>();
-  const size_t smem = (size_t)ST * (AT * TC_BM * TC_BK * 2 + (size_t)TC_TERMS * a.NP * TC_BK * 2);
-  {
-    const size_t max_smem = (size_t)ST * (AT * TC_BM * TC_BK * 2 + (size_t)TC_TERMS * TC_NMAX * TC_BK * 2);
-    NYS_CUDA_TRY(ensure_max_dyn_smem((const void*)sketch_tc_kernel<EPI, AT>, (int)max_smem));
-  }
+  constexpr int ST = tc_stages<AT, BT, BM2>();
+  const size_t smem = (size_t)ST * (BM2 * AT * TC_BM * TC_BK * 2 + (size_t)BT * a.NP * TC_BK * 2);
+  NYS_CUDA_TRY(ensure_max_dyn_smem((const void*)sketch_tc_kernel<EPI, AT, BT, BM2>,
+                                   ST * tc_stage_max_bytes<AT, BT, BM2>()));
   count_launch();
-  sketch_tc_kernel<EPI, AT><<<grid, TC_THREADS, smem, st>>>(a);
+  sketch_tc_kernel<EPI, AT, BT, BM2><<<grid, TC_THREADS, smem, st>>>(a);
   return cudaGetLastError();
 }
 
+// Output rows per CTA: two 128-row accumulators, except for FP32 x FP32 (six MMA pairs),
+// whose stages leave room for one.
+int tc_cta_rows(int at, int bt) { return TC_BM * (at == 3 && bt == 3 ? 1 : 2); }
+
 template <int EPI>
-cudaError_t launch_tc_at(int at, const TcArgs& a, dim3 grid, cudaStream_t st) {
-  return at == 3 ? launch_tc<EPI, 3>(a, grid, st) : launch_tc<EPI, 1>(a, grid, st);
+cudaError_t launch_tc_at(int at, int bt, const TcArgs& a, dim3 grid, cudaStream_t st) {
+  if constexpr (EPI == 1) {   // the second product's B is W, always three terms
+    return at == 3 ? launch_tc<EPI, 3, 3, 1>(a, grid, st) : launch_tc<EPI, 1, 3, 2>(a, grid, st);
+  } else {
+    if (at == 3) return bt == 3 ? launch_tc<EPI, 3, 3, 1>(a, grid, st) : launch_tc<EPI, 3, 1, 2>(a, grid, st);
+    return bt == 3 ? launch_tc<EPI, 1, 3, 2>(a, grid, st) : launch_tc<EPI, 1, 1, 2>(a, grid, st);
+  }
 }
 
 // FP32 storage: A (n x lda, row-major) -> three BF16 terms As[t][i][j] (row stride ldS,
@@ -440,16 +471,19 @@ __global__ void split_matrix_kernel(const float* __restrict__ A, int64_t n, int6
 namespace {
 // Y (d x m, column-major) = A^T diag(D) A X (+ rho X) on the tensor cores, given the
 // transposed copy At (d x nP) of A.  X and Y are FP64 (sketch) or FP32 (batched PCG).
+// xterms = 1: X holds BF16 values (the sketch's rounded test matrix), so the first product
+// takes one MMA term of X instead of three.
 template <typename TX, typename TY>
 cudaError_t tc_product(const nys_matrix* A, const TcPrepared& prep, const double* D, const TX* X, int m,
-                       double rho, TY* Y, cudaStream_t st, bool trace) {
+                       double rho, TY* Y, cudaStream_t st, bool trace, int xterms) {
   const int64_t n = A->n, d = A->d;
   const int64_t nP = prep.nP;
   const int64_t dP = (d + TC_BK - 1) / TC_BK * TC_BK;
   const int NPmax = std::min(TC_NMAX, (m + 15) / 16 * 16);
   const uint32_t swap = std::getenv("NYS_TC_DESC_SWAP") ? (uint32_t)std::atoi(std::getenv("NYS_TC_DESC_SWAP")) : 0u;
   const int sms = sm_count_tc();
-  const int64_t mt2 = (d + TC_BM - 1) / TC_BM;
+  const int rows1 = tc_cta_rows(prep.at, xterms), rows2 = tc_cta_rows(prep.at, TC_TERMS);
+  const int64_t mt2 = (d + rows2 - 1) / rows2;
   const int64_t kt2 = nP / TC_BK;
   const int Z = pick_slices(mt2, kt2, sms);
   const int64_t kslice2 = (kt2 + Z - 1) / Z;
@@ -464,7 +498,7 @@ cudaError_t tc_product(const nys_matrix* A, const TcPrepared& prep, const double
   };
   mark();
   Pool pool(st);
-  uint16_t* Ot = pool.alloc<uint16_t>((size_t)TC_TERMS * NPmax * dP);
+  uint16_t* Ot = pool.alloc<uint16_t>((size_t)xterms * NPmax * dP);
   uint16_t* Wt = pool.alloc<uint16_t>((size_t)TC_TERMS * NPmax * nP);
   float* P = pool.alloc<float>((size_t)Zeff * NPmax * d);
   int* status = pool.alloc<int>(1);
@@ -475,8 +509,11 @@ cudaError_t tc_product(const nys_matrix* A, const TcPrepared& prep, const double
     const int mp = std::min(TC_NMAX, m - c0);
     const int NP = (mp + 15) / 16 * 16;
     count_launch();
-    split_operand_kernel<TX><<<(unsigned)std::min<int64_t>(4096, ((int64_t)NP * dP + 255) / 256), 256, 0, st>>>(
-        X, d, c0, mp, NP, dP, Ot);
+    const unsigned sgrid = (unsigned)std::min<int64_t>(4096, ((int64_t)NP * dP + 255) / 256);
+    if (xterms == 1)
+      split_operand_kernel<TX, 1><<<sgrid, 256, 0, st>>>(X, d, c0, mp, NP, dP, Ot);
+    else
+      split_operand_kernel<TX, TC_TERMS><<<sgrid, 256, 0, st>>>(X, d, c0, mp, NP, dP, Ot);
     NYS_CUDA_TRY(cudaGetLastError());
     if (c0 == 0) mark();
 
@@ -499,7 +536,7 @@ cudaError_t tc_product(const nys_matrix* A, const TcPrepared& prep, const double
     g1.wrows = nP;
     g1.desc_swap = swap;
     g1.status = status;
-    NYS_CUDA_TRY(launch_tc_at<0>(prep.at, g1, dim3((unsigned)((n + TC_BM - 1) / TC_BM), 1), st));
+    NYS_CUDA_TRY(launch_tc_at<0>(prep.at, xterms, g1, dim3((unsigned)((n + rows1 - 1) / rows1), 1), st));
     if (c0 == 0) mark();
 
     TcArgs g2 = {};
@@ -518,7 +555,7 @@ cudaError_t tc_product(const nys_matrix* A, const TcPrepared& prep, const double
     g2.ldp = d;
     g2.desc_swap = swap;
     g2.status = status;
-    NYS_CUDA_TRY(launch_tc_at<1>(prep.at, g2, dim3((unsigned)mt2, (unsigned)Zeff), st));
+    NYS_CUDA_TRY(launch_tc_at<1>(prep.at, TC_TERMS, g2, dim3((unsigned)mt2, (unsigned)Zeff), st));
     if (c0 == 0) mark();
 
     count_launch();
@@ -544,6 +581,20 @@ cudaError_t tc_product(const nys_matrix* A, const TcPrepared& prep, const double
   return status_h ? cudaErrorLaunchTimeout : cudaSuccess;
 }
 }  // namespace
+
+namespace {
+__global__ void round_bf16_kernel(double* __restrict__ X, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    X[i] = (double)bf16_val(bf16_bits((float)X[i]));
+}
+}  // namespace
+
+cudaError_t round_panel_bf16(double* X, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  count_launch();
+  round_bf16_kernel<<<(unsigned)std::min<int64_t>(4096, (n + 255) / 256), 256, 0, st>>>(X, n);
+  return cudaGetLastError();
+}
 
 bool sketch_tc_supported(const nys_matrix* A) {
   if (A->dtype != NYS_BF16 && A->dtype != NYS_F32) return false;
@@ -623,19 +674,19 @@ cudaError_t sketch_tc(const nys_matrix* A, const double* D, const double* Om, in
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
-  return tc_product<double, double>(A, prep, D, Om, m, 0.0, Y, st, trace);
+  return tc_product<double, double>(A, prep, D, Om, m, 0.0, Y, st, trace, 1);
 }
 
 cudaError_t sketch_tc_with(const nys_matrix* A, const TcPrepared& prep, const double* D, const double* Om, int m,
                            double* Y, cudaStream_t st) {
   if (m <= 0) return cudaErrorInvalidValue;
-  return tc_product<double, double>(A, prep, D, Om, m, 0.0, Y, st, std::getenv("NYS_TRACE") != nullptr);
+  return tc_product<double, double>(A, prep, D, Om, m, 0.0, Y, st, std::getenv("NYS_TRACE") != nullptr, 1);
 }
 
 cudaError_t tc_hmm(const nys_matrix* A, const TcPrepared& prep, const double* D, const float* X, int k, double rho,
                    float* Y, cudaStream_t st) {
   if (k <= 0) return cudaErrorInvalidValue;
-  return tc_product<float, float>(A, prep, D, X, k, rho, Y, st, false);
+  return tc_product<float, float>(A, prep, D, X, k, rho, Y, st, false, TC_TERMS);
 }
 
 }  // namespace nys

@@ -119,6 +119,38 @@ def test_nystrom_exact_when_rank_exceeds_H():
     check_nystrom_exact_low_rank()
 
 
+def test_round_to_bf16_matches_torch_cast():
+    """The BF16 rounding of the FP32-class test matrix against torch's float32 -> bfloat16
+    cast (round to nearest, ties to even), on random values and on exact ties."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    x = np.concatenate([rng.standard_normal(4000), rng.standard_normal(1000) * 1e-30, [0.0, -0.0, 1.0, -3.5]])
+    f = x.astype(np.float32)
+    # exact ties: low 16 bits 0x8000, upper halves even and odd
+    hi = rng.integers(0x3000, 0x4800, size=200).astype(np.uint32)
+    ties = ((hi << 16) | 0x8000).view(np.float32)
+    f = np.concatenate([f, ties, -ties])
+    ref = torch.from_numpy(f).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+    got = o.round_to_bf16(f.astype(np.float64))
+    assert np.array_equal(got, ref)
+
+
+def test_nystrom_fp32_class_test_matrix():
+    """mantissa_bits = 23: the test matrix is qr(Omega, 0) rounded to BF16 values (within
+    2^-8 of each entry, orthonormal to ~2^-7), and the approximation still reproduces an H of rank
+    below s (any full-rank test matrix does), up to the FP32-eps shift."""
+    A, H = _spd_decay(40, 2, r=6)
+    Om = gen.gaussian_test_matrix(40, 10, 2)
+    U, lam, nu, Q, _ = o.nystrom(lambda X: H @ X, Om, shift_scale=1.0, mantissa_bits=23)
+    Q0 = o.thin_qr(Om)
+    bits = Q.astype(np.float32).view(np.uint32)
+    assert np.all((bits & 0xFFFF) == 0) and np.array_equal(Q.astype(np.float32).astype(np.float64), Q)
+    assert np.all(np.abs(Q - Q0) <= 2.0 ** -8 * np.abs(Q0) * (1 + 1e-6))   # half a BF16 ulp
+    assert 0 < np.linalg.norm(Q.T @ Q - np.eye(10), 2) <= 2.0 ** -6
+    evH = np.sort(np.linalg.eigvalsh(H))[::-1]
+    assert np.linalg.norm((U * lam) @ U.T - H, 2) <= 1e-5 * evH[0]
+
+
 # ---------------------------------------------------------------- preconditioner
 
 def check_precond_inverse(seed=3, d=45, s=9, rho=0.3):
