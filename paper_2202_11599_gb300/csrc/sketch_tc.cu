@@ -26,6 +26,7 @@
 //   * the epilogue reads TMEM with tcgen05.ld (warp w reads lanes 32 (w % 4) .. + 31):
 //     GEMM 1 scales row i by D_i and writes the three BF16 terms of W; GEMM 2 writes its
 //     K-slice's FP32 partial, and a final kernel sums the slices in a fixed order in FP64.
+#include <cuda.h>   // CUtensorMap (the encode entry point is taken from the driver at run time)
 #include <cuda_bf16.h>
 
 #include "device_util.cuh"
@@ -41,7 +42,6 @@ namespace {
 
 constexpr int TC_BM = 128;      // output rows per CTA = TMEM lanes
 constexpr int TC_BK = 32;       // K per stage (two MMA K-steps of 16)
-constexpr int TC_STAGES = 4;
 constexpr int TC_THREADS = 256;
 constexpr int TC_TERMS = 3;     // FP32 operand = t1 + t2 + t3 (BF16)
 constexpr int TC_NMAX = 256;    // MMA N limit; TMEM columns allocated
@@ -163,6 +163,49 @@ template <int AT, int BT, int BM2> constexpr int tc_stages() {
   return (224 * 1024) / tc_stage_max_bytes<AT, BT, BM2>() < 6 ? (224 * 1024) / tc_stage_max_bytes<AT, BT, BM2>() : 6;
 }
 
+// Epilogue of both staging forms: TMEM -> registers (tcgen05.ld; warp w reads lanes
+// 32 (w % 4) .. + 31 and half the columns), then W's three BF16 terms (EPI 0, rows scaled
+// by D) or the split-K slice's FP32 partial (EPI 1).
+template <int EPI, int BM2>
+__device__ __forceinline__ void tc_epilogue(const TcArgs& a, uint32_t tmem, int64_t m0, int nkt, int warp, int lane) {
+  const int quad = warp & 3;
+  const int half = a.NP / 2;
+  const int cb = (warp >> 2) * half;
+  for (int h = 0; h < BM2; ++h) {
+    const int64_t row = m0 + h * TC_BM + 32 * quad + lane;
+    const uint32_t trow = tmem + (uint32_t)(h * TC_NMAX) + ((uint32_t)(32 * quad) << 16);
+    double dr = 1.0;
+    if (EPI == 0 && a.D && row < a.Mrows) dr = a.D[row];
+    for (int c0 = cb; c0 < cb + half; c0 += 8) {
+      uint32_t v[8];
+      tmem_ld8(trow + (uint32_t)c0, v);
+      tmem_ld_wait(v);
+      if (nkt == 0) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = 0u;
+      }
+      if (EPI == 0) {
+        if (row < a.wrows) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const float x = row < a.Mrows ? (float)(dr * (double)__uint_as_float(v[e])) : 0.f;
+            uint16_t t3[3];
+            split3(x, t3);
+#pragma unroll
+            for (int t = 0; t < TC_TERMS; ++t) a.Wt[t * a.wterm + (int64_t)(c0 + e) * a.ldw + row] = t3[t];
+          }
+        }
+      } else {
+        if (row < a.Mrows) {
+          float* P = a.P + (int64_t)blockIdx.y * a.NP * a.ldp;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) P[(int64_t)(c0 + e) * a.ldp + row] = __uint_as_float(v[e]);
+        }
+      }
+    }
+  }
+}
+
 // BM2 accumulators per CTA (1 or 2): a CTA computes BM2 x 128 output rows, every staged
 // tile of B serving both (half the B traffic from L2 per output row); accumulator h sits
 // at TMEM columns [256 h, 256 h + N).
@@ -276,46 +319,135 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const TcArgs a
   tc_fence_after();
 
   if (ok) {
-    const int quad = warp & 3;
-    const int half = a.NP / 2;
-    const int cb = (warp >> 2) * half;
-    for (int h = 0; h < BM2; ++h) {
-      const int64_t row = m0 + h * TC_BM + 32 * quad + lane;
-      const uint32_t trow = tmem + (uint32_t)(h * TC_NMAX) + ((uint32_t)(32 * quad) << 16);
-      double dr = 1.0;
-      if (EPI == 0 && a.D && row < a.Mrows) dr = a.D[row];
-      for (int c0 = cb; c0 < cb + half; c0 += 8) {
-        uint32_t v[8];
-        tmem_ld8(trow + (uint32_t)c0, v);
-        tmem_ld_wait(v);
-        if (nkt == 0) {
-#pragma unroll
-          for (int e = 0; e < 8; ++e) v[e] = 0u;
-        }
-        if (EPI == 0) {
-          if (row < a.wrows) {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const float x = row < a.Mrows ? (float)(dr * (double)__uint_as_float(v[e])) : 0.f;
-              uint16_t t3[3];
-              split3(x, t3);
-#pragma unroll
-              for (int t = 0; t < TC_TERMS; ++t) a.Wt[t * a.wterm + (int64_t)(c0 + e) * a.ldw + row] = t3[t];
-            }
-          }
-        } else {
-          if (row < a.Mrows) {
-            float* P = a.P + (int64_t)blockIdx.y * a.NP * a.ldp;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) P[(int64_t)(c0 + e) * a.ldp + row] = __uint_as_float(v[e]);
-          }
-        }
-      }
-    }
+    tc_epilogue<EPI, BM2>(a, tmem, m0, nkt, warp, lane);
   } else if (tid == 0) {
     // a wait gave up: report, give the tensor core a bounded last chance to finish
     atomicExch(a.status, (int)NYS_ETIMEOUT);
     if (nkt > 0) (void)mbar_wait_bounded(&mma_bar[(nkt - 1) % TC_STAGES], (uint32_t)(((nkt - 1) / TC_STAGES) & 1));
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---- TMA staging.  One thread (warp 0, lane 0) issues, per stage and per K chunk of 8
+// elements, one tiled copy of the A box {8, BM2 x 128 rows, AT terms} and one of the B box
+// {8, N, BT terms} (cp.async.bulk.tensor.3d; rows and K outside the matrices arrive as
+// zeros) onto the stage's full barrier; one thread (warp 1, lane 0) waits for it, issues
+// the MMAs and commits them to the stage's empty barrier, which the issuing thread waits on
+// before it refills the stage.  A stage holds [chunk][term][row][8 elements]: core matrices
+// 128 B apart along the rows and (terms x rows x 16) B apart along K.  The MMAs and their
+// order are those of sketch_tc_kernel, so both forms give the same bits.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <int EPI, int AT, int BT, int BM2>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    sketch_tc_tma_kernel(const __grid_constant__ TcArgs a, const __grid_constant__ CUtensorMap tmA,
+                         const __grid_constant__ CUtensorMap tmB) {
+  constexpr int ST = tc_stages<AT, BT, BM2>();
+  constexpr uint32_t kTmemCols = BM2 == 2 ? 2 * TC_NMAX : TC_NMAX;
+  constexpr int R = TC_BM * BM2;
+  static_assert(ST >= 2, "shared memory holds fewer than two stages");
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full_bar[ST];
+  __shared__ __align__(8) uint64_t empty_bar[ST];
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * R;
+  const int64_t kt0 = (int64_t)blockIdx.y * a.kslice;
+  const int64_t kt1 = min(a.ktiles, kt0 + a.kslice);
+  const int nkt = (int)max((int64_t)0, kt1 - kt0);
+  const uint32_t a_chunk = (uint32_t)(AT * R * 16);   // one K chunk (8 elements) of the A box
+  const uint32_t b_chunk = (uint32_t)(BT * a.NP * 16);
+  const uint32_t a_bytes = 4 * a_chunk, b_bytes = 4 * b_chunk;
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t idesc = mma_idesc_bf16(TC_BM, a.NP);
+
+  if (warp == 0) {
+    tmem_alloc(&tmem_slot, kTmemCols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    s_fail = 0;
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    int kt = 0;
+    for (; kt < nkt && !s_fail; ++kt) {
+      const int s = kt % ST;
+      // the MMAs of this stage's previous use must be done reading it
+      if (kt >= ST && !mbar_wait_bounded(&empty_bar[s], (uint32_t)((kt / ST - 1) & 1))) {
+        s_fail = 1;
+        break;
+      }
+      const uint32_t st = sbase + (uint32_t)s * stage_bytes;
+      const int k0 = (int)((kt0 + kt) * TC_BK);
+      mbar_arrive_expect_tx(&full_bar[s], stage_bytes);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        tma_load_3d(st + (uint32_t)c * a_chunk, &tmA, k0 + 8 * c, (int)m0, 0, &full_bar[s]);
+        tma_load_3d(st + a_bytes + (uint32_t)c * b_chunk, &tmB, k0 + 8 * c, 0, 0, &full_bar[s]);
+      }
+    }
+    // copies issued but not consumed (a wait gave up): let them land before the CTA leaves
+    for (int j = max(0, kt - ST); j < kt; ++j) (void)mbar_wait_bounded(&full_bar[j % ST], (uint32_t)((j / ST) & 1));
+  } else if (warp == 1 && lane == 0) {
+    for (int kt = 0; kt < nkt && !s_fail; ++kt) {
+      const int s = kt % ST;
+      if (!mbar_wait_bounded(&full_bar[s], (uint32_t)((kt / ST) & 1))) {
+        s_fail = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t st = sbase + (uint32_t)s * stage_bytes;
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 16; ++kk) {
+#pragma unroll
+        for (int h = 0; h < BM2; ++h) {
+#pragma unroll
+          for (int pr = 0; pr < tc_npairs<AT, BT>(); ++pr) {
+            const uint64_t ad = smem_desc(st + (uint32_t)(2 * kk) * a_chunk +
+                                              (uint32_t)(tc_pair_a<AT, BT>(pr) * R * 16 + h * TC_BM * 16),
+                                          a_chunk, 128u);
+            const uint64_t bd = smem_desc(st + a_bytes + (uint32_t)(2 * kk) * b_chunk +
+                                              (uint32_t)(tc_pair_b<AT, BT>(pr) * a.NP * 16),
+                                          b_chunk, 128u);
+            mma_bf16(tmem + (uint32_t)(h * TC_NMAX), ad, bd, idesc, (kt | kk | pr) != 0 ? 1u : 0u);
+          }
+        }
+      }
+      mma_commit(&empty_bar[s]);
+    }
+  }
+  __syncthreads();
+  bool ok = s_fail == 0;
+  // the last commit tracks every MMA this CTA issued
+  if (ok && nkt > 0) ok = mbar_wait_bounded(&empty_bar[(nkt - 1) % ST], (uint32_t)(((nkt - 1) / ST) & 1));
+  ok = __syncthreads_and(ok);
+  tc_fence_after();
+  if (ok) {
+    tc_epilogue<EPI, BM2>(a, tmem, m0, nkt, warp, lane);
+  } else if (tid == 0) {
+    atomicExch(a.status, (int)NYS_ETIMEOUT);
+    if (nkt > 0) (void)mbar_wait_bounded(&empty_bar[(nkt - 1) % ST], (uint32_t)(((nkt - 1) / ST) & 1));
   }
   tc_fence_before();
   __syncthreads();
@@ -424,10 +556,61 @@ int pick_slices(int64_t mtiles, int64_t ktiles, int sms) {
   return best;
 }
 
+// cuTensorMapEncodeTiled from the driver (the library links only the runtime).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    (void)cudaGetLastError();
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// 3-D map of `terms` BF16 matrices (rows x K, K contiguous, row stride ld elements, term
+// stride tstride elements) with the box {8, box_rows, terms}: one K chunk of every row and
+// term per copy; rows >= rows and K >= K arrive as zeros.
+cudaError_t make_tile_map(CUtensorMap* m, const uint16_t* base, int64_t K, int64_t rows, int64_t ld, int terms,
+                          int64_t tstride, int box_rows) {
+  EncodeTiledFn enc = encode_tiled_fn();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)terms};
+  // a single term: any stride past the matrix will do
+  const cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)(terms > 1 ? tstride : ld * rows) * 2};
+  const cuuint32_t box[3] = {8u, (cuuint32_t)box_rows, (cuuint32_t)terms};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// TMA staging unless NYS_TC_TMA=0 (the cp.async form: the same MMAs, the same bits).
+bool tc_use_tma() {
+  const char* e = std::getenv("NYS_TC_TMA");
+  return !(e && std::atoi(e) == 0);
+}
+
 template <int EPI, int AT, int BT, int BM2>
 cudaError_t launch_tc(const TcArgs& a, dim3 grid, cudaStream_t st) {
   constexpr int ST = tc_stages<AT, BT, BM2>();
   const size_t smem = (size_t)ST * (BM2 * AT * TC_BM * TC_BK * 2 + (size_t)BT * a.NP * TC_BK * 2);
+  if (tc_use_tma()) {
+    CUtensorMap tmA, tmB;
+    NYS_CUDA_TRY(make_tile_map(&tmA, a.A, a.Kvalid, a.Mrows, a.lda, AT, a.aterm, TC_BM * BM2));
+    NYS_CUDA_TRY(make_tile_map(&tmB, a.B, a.ktiles * TC_BK, a.NP, a.ldb, BT, a.bterm, a.NP));
+    NYS_CUDA_TRY(ensure_max_dyn_smem((const void*)sketch_tc_tma_kernel<EPI, AT, BT, BM2>,
+                                     ST * tc_stage_max_bytes<AT, BT, BM2>()));
+    count_launch();
+    sketch_tc_tma_kernel<EPI, AT, BT, BM2><<<grid, TC_THREADS, smem, st>>>(a, tmA, tmB);
+    return cudaGetLastError();
+  }
   NYS_CUDA_TRY(ensure_max_dyn_smem((const void*)sketch_tc_kernel<EPI, AT, BT, BM2>,
                                    ST * tc_stage_max_bytes<AT, BT, BM2>()));
   count_launch();
