@@ -85,13 +85,19 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Shared-memory matrix descriptor, no swizzle: start address, leading (K) and stride
-// (M/N) byte offsets, all in 16-byte units; bits 46-48 hold the fixed value 1.
+// (M/N) byte offsets, all in 16-byte units; bits 46-48 hold the fixed value 1.  The
+// swizzled form below sets the layout field (bits 61-63; 4 = 64-byte swizzle) and takes
+// only the 8-row-group stride (the leading offset is unused there, encoded as 1).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 // Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9 and
 // 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) |
+         (4ull << 61);
+}
 __host__ __device__ constexpr uint32_t mma_idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
@@ -330,14 +336,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const TcArgs a
   if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-// ---- TMA staging.  One thread (warp 0, lane 0) issues, per stage and per K chunk of 8
-// elements, one tiled copy of the A box {8, BM2 x 128 rows, AT terms} and one of the B box
-// {8, N, BT terms} (cp.async.bulk.tensor.3d; rows and K outside the matrices arrive as
-// zeros) onto the stage's full barrier; one thread (warp 1, lane 0) waits for it, issues
+// ---- TMA staging.  One thread (warp 0, lane 0) issues, per stage, one tiled copy of the
+// A box {32 K, BM2 x 128 rows, AT terms} and one of the B box {32 K, N, BT terms}
+// (cp.async.bulk.tensor.3d with the 64-byte swizzle; rows and K outside the matrices arrive
+// as zeros) onto the stage's full barrier; one thread (warp 1, lane 0) waits for it, issues
 // the MMAs and commits them to the stage's empty barrier, which the issuing thread waits on
-// before it refills the stage.  A stage holds [chunk][term][row][8 elements]: core matrices
-// 128 B apart along the rows and (terms x rows x 16) B apart along K.  The MMAs and their
-// order are those of sketch_tc_kernel, so both forms give the same bits.
+// before it refills the stage.  A stage holds [term][row][64 bytes] in the canonical K-major
+// 64-byte-swizzle layout (8-row groups 512 B apart; the K step of 16 elements moves the
+// start address 32 B).  The MMAs and their order are those of sketch_tc_kernel, so both
+// forms give the same bits.
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
                                             uint64_t* bar) {
   asm volatile(
@@ -365,9 +372,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int64_t kt0 = (int64_t)blockIdx.y * a.kslice;
   const int64_t kt1 = min(a.ktiles, kt0 + a.kslice);
   const int nkt = (int)max((int64_t)0, kt1 - kt0);
-  const uint32_t a_chunk = (uint32_t)(AT * R * 16);   // one K chunk (8 elements) of the A box
-  const uint32_t b_chunk = (uint32_t)(BT * a.NP * 16);
-  const uint32_t a_bytes = 4 * a_chunk, b_bytes = 4 * b_chunk;
+  const uint32_t a_term = (uint32_t)(R * 64), b_term = (uint32_t)(a.NP * 64);   // [row][64 B] per term
+  const uint32_t a_bytes = AT * a_term, b_bytes = BT * b_term;
   const uint32_t stage_bytes = a_bytes + b_bytes;
   const uint32_t sbase = smem_u32(smem);
   const uint32_t idesc = mma_idesc_bf16(TC_BM, a.NP);
@@ -401,11 +407,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const uint32_t st = sbase + (uint32_t)s * stage_bytes;
       const int k0 = (int)((kt0 + kt) * TC_BK);
       mbar_arrive_expect_tx(&full_bar[s], stage_bytes);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        tma_load_3d(st + (uint32_t)c * a_chunk, &tmA, k0 + 8 * c, (int)m0, 0, &full_bar[s]);
-        tma_load_3d(st + a_bytes + (uint32_t)c * b_chunk, &tmB, k0 + 8 * c, 0, 0, &full_bar[s]);
-      }
+      tma_load_3d(st, &tmA, k0, (int)m0, 0, &full_bar[s]);
+      tma_load_3d(st + a_bytes, &tmB, k0, 0, 0, &full_bar[s]);
     }
     // copies issued but not consumed (a wait gave up): let them land before the CTA leaves
     for (int j = max(0, kt - ST); j < kt; ++j) (void)mbar_wait_bounded(&full_bar[j % ST], (uint32_t)((j / ST) & 1));
@@ -424,12 +427,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int h = 0; h < BM2; ++h) {
 #pragma unroll
           for (int pr = 0; pr < tc_npairs<AT, BT>(); ++pr) {
-            const uint64_t ad = smem_desc(st + (uint32_t)(2 * kk) * a_chunk +
-                                              (uint32_t)(tc_pair_a<AT, BT>(pr) * R * 16 + h * TC_BM * 16),
-                                          a_chunk, 128u);
-            const uint64_t bd = smem_desc(st + a_bytes + (uint32_t)(2 * kk) * b_chunk +
-                                              (uint32_t)(tc_pair_b<AT, BT>(pr) * a.NP * 16),
-                                          b_chunk, 128u);
+            const uint64_t ad = smem_desc_sw64(
+                st + (uint32_t)tc_pair_a<AT, BT>(pr) * a_term + (uint32_t)(h * TC_BM * 64 + kk * 32), 512u);
+            const uint64_t bd =
+                smem_desc_sw64(st + a_bytes + (uint32_t)tc_pair_b<AT, BT>(pr) * b_term + (uint32_t)(kk * 32), 512u);
             mma_bf16(tmem + (uint32_t)(h * TC_NMAX), ad, bd, idesc, (kt | kk | pr) != 0 ? 1u : 0u);
           }
         }
@@ -574,8 +575,8 @@ EncodeTiledFn encode_tiled_fn() {
 }
 
 // 3-D map of `terms` BF16 matrices (rows x K, K contiguous, row stride ld elements, term
-// stride tstride elements) with the box {8, box_rows, terms}: one K chunk of every row and
-// term per copy; rows >= rows and K >= K arrive as zeros.
+// stride tstride elements) with the box {32, box_rows, terms} and the 64-byte swizzle: one
+// K tile of every row and term per copy; rows >= rows and K >= K arrive as zeros.
 cudaError_t make_tile_map(CUtensorMap* m, const uint16_t* base, int64_t K, int64_t rows, int64_t ld, int terms,
                           int64_t tstride, int box_rows) {
   EncodeTiledFn enc = encode_tiled_fn();
@@ -583,10 +584,10 @@ cudaError_t make_tile_map(CUtensorMap* m, const uint16_t* base, int64_t K, int64
   const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)terms};
   // a single term: any stride past the matrix will do
   const cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)(terms > 1 ? tstride : ld * rows) * 2};
-  const cuuint32_t box[3] = {8u, (cuuint32_t)box_rows, (cuuint32_t)terms};
+  const cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, (cuuint32_t)terms};
   const cuuint32_t estr[3] = {1u, 1u, 1u};
   const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(base), dims, strides, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
