@@ -103,15 +103,27 @@ double eps_host(double t, int mant_bits) {
 }
 
 // Thin QR of Omega (d x m, in place) by CholQR2: twice G = Om^T Om, C = chol(G), Om <- Om C^{-1}.
-nys_status cholqr2(double* Om, int64_t d, int m, cudaStream_t st) {
+// fp32_class: the panel is rounded to BF16 values right after (the test matrix of an
+// FP32-class sketch), so the second pass stops after its Gram when the first pass already
+// left Om orthonormal to 2^-20 (max |Om^T Om - I|), far below that rounding's 2^-8 -- one
+// CholQR pass does so for any well-conditioned panel (loss of orthogonality ~ cond^2 2^-53).
+nys_status cholqr2(double* Om, int64_t d, int m, cudaStream_t st, bool fp32_class = false) {
   PhaseTimer pt("cholqr2", st);
   Pool pool(st);
   double* G = pool.alloc<double>((size_t)m * m);
   double* work = pool.alloc<double>(gram_work_bytes(d, m) / sizeof(double) + 1);
   int* info = pool.alloc<int>(1);
+  double* gap = pool.alloc<double>(1);
   if (!pool.ok()) return NYS_ENOMEM;
   for (int pass = 0; pass < 2; ++pass) {
     NYS_CU(gram_xty(Om, Om, d, m, G, work, st));
+    if (pass == 1 && fp32_class) {
+      NYS_CU(identity_gap(G, m, gap, st));
+      double gap_h = 1.0;
+      NYS_CU(cudaMemcpyAsync(&gap_h, gap, sizeof(double), cudaMemcpyDeviceToHost, st));
+      NYS_CU(cudaStreamSynchronize(st));
+      if (gap_h <= 0x1p-20) break;
+    }
     // a pivot below 1e-10 of the largest column norm^2: columns dependent to ~1e-5, which
     // CholQR cannot orthonormalise -- refused as a bad test matrix
     NYS_CU(chol_upper(G, m, info, st, 1e-10));
@@ -413,7 +425,7 @@ nys_status adaptive_sketch(const nys_matrix* Ain, const double* D, double shift,
                            nys_precond_s* P, int* used_out, cudaStream_t st) {
   int s0 = rank, m = rank, used = 0;
   auto add_block = [&](int cols) -> nys_status {
-    NYS_TRY(cholqr2(Om + (int64_t)used * d, d, cols, st));
+    NYS_TRY(cholqr2(Om + (int64_t)used * d, d, cols, st, Ain->dtype != NYS_F64));
     NYS_TRY(sketch_panel(Ain, D, shift, Om + (int64_t)used * d, cols, Y + (int64_t)used * d, st, tcpp));
     used += cols;
     return precond_from_panels(Om, Y, d, used, shs, mant_bits_of(Ain), P, st);
@@ -539,7 +551,7 @@ nys_status lasso_admm(const nys_matrix* A, const nys_matrix* Ain, const double* 
     NYS_TRY(adaptive_sketch(Ain, nullptr, mu, Om, Y, d, rank, smax, o.ada_tol > 0 ? o.ada_tol : 2.0, rho, shs,
                             nullptr, &P, &rank, st));
   } else {
-    NYS_TRY(cholqr2(Om, d, rank, st));
+    NYS_TRY(cholqr2(Om, d, rank, st, Ain->dtype != NYS_F64));
     NYS_TRY(sketch_panel(Ain, nullptr, mu, Om, rank, Y, st));
     NYS_TRY(precond_from_panels(Om, Y, d, rank, shs, mant_bits_of(Ain), &P, st));
   }
@@ -747,7 +759,7 @@ nys_status lasso_path(const nys_matrix* A, const nys_matrix* Ain, const double* 
   double* Y = pool.alloc<double>((size_t)d * rank);
   if (!pool.ok()) return NYS_ENOMEM;
   NYS_TRY(omega_panel(Omega, o.seed, d, rank, Om, st));
-  NYS_TRY(cholqr2(Om, d, rank, st));
+  NYS_TRY(cholqr2(Om, d, rank, st, Ain->dtype != NYS_F64));
   NYS_TRY(sketch_panel(Ain, nullptr, 0.0, Om, rank, Y, st));
   const double shs = o.shift_scale > 0 ? o.shift_scale : std::sqrt((double)d);
   NYS_TRY(precond_from_panels(Om, Y, d, rank, shs, mant_bits_of(Ain), &P, st));
@@ -871,7 +883,7 @@ nys_status lasso_batch(int count, const nys_lasso_instance* in, double rho, doub
     int* pit = pool.alloc<int>(K);
     if (!pool.ok()) return NYS_ENOMEM;
     NYS_CU(cudaMemcpyAsync(Om, in[i].Omega, (size_t)d * rank * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    NYS_TRY(cholqr2(Om, d, rank, st));
+    NYS_TRY(cholqr2(Om, d, rank, st, A->dtype != NYS_F64));
     NYS_TRY(sketch_panel(A, nullptr, 0.0, Om, rank, Y, st));
     const double shs = o.shift_scale > 0 ? o.shift_scale : std::sqrt((double)d);
     NYS_TRY(precond_from_panels(Om, Y, d, rank, shs, mant_bits_of(A), &Ps[i], st));
@@ -1209,7 +1221,7 @@ nys_status nys_sketch(const nys_matrix* A, const double* D, double diag_shift, i
       return NYS_ENOMEM;
     }
     r = omega_panel(Omega, opts ? opts->seed : 0, d, s, Om, st);
-    if (r == NYS_OK) r = cholqr2(Om, d, s, st);
+    if (r == NYS_OK) r = cholqr2(Om, d, s, st, A->dtype != NYS_F64);
     if (r == NYS_OK) r = sketch_panel(A, D, diag_shift, Om, s, Y, st);
     const double shs = (opts && opts->shift_scale > 0) ? opts->shift_scale : std::sqrt((double)d);
     if (r == NYS_OK) r = precond_from_panels(Om, Y, d, s, shs, mant_bits_of(A), P, st);

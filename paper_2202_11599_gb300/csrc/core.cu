@@ -838,6 +838,30 @@ __global__ void jacobi_setup_kernel(const double* __restrict__ G, int s, double*
   if (blockIdx.x == 0 && threadIdx.x == 0) *done = 0;
 }
 
+// max_ij |G_ij - delta_ij| of an m x m matrix (one block, fixed-order max: exact)
+__global__ void __launch_bounds__(256) identity_gap_kernel(const double* __restrict__ G, int m, double* out) {
+  __shared__ double sh[8];
+  double g = 0.0;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)m * m; idx += 256) {
+    const int i = (int)(idx % m), j = (int)(idx / m);
+    g = fmax(g, fabs(G[idx] - (i == j ? 1.0 : 0.0)));
+  }
+  for (int o = 16; o > 0; o >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = g;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < 8; ++w) r = fmax(r, sh[w]);
+    *out = r;
+  }
+}
+
+cudaError_t identity_gap(const double* G, int m, double* out, cudaStream_t st) {
+  count_launch();
+  identity_gap_kernel<<<1, 256, 0, st>>>(G, m, out);
+  return cudaGetLastError();
+}
+
 size_t jacobi_work_bytes(int s) {
   const int N = s + (s & 1);
   const int HT = (N / 2 + JT - 1) / JT;

@@ -99,6 +99,8 @@ cudaError_t power_lambda_max(const double* G, int s, double* out, double* work, 
 // in *sweeps (host).
 cudaError_t jacobi_eig(double* G, double* V, int s, double* work, int* sweeps, cudaStream_t st, double tol = 1e-12);
 size_t jacobi_work_bytes(int s);
+// *out (device) = max_ij |G_ij - delta_ij| of the m x m matrix G.
+cudaError_t identity_gap(const double* G, int m, double* out, cudaStream_t st);
 // After Jacobi: sort eigenpairs descending, U = B V Sigma^{-1}, lam = max(0, sigma^2 - nu).
 cudaError_t nystrom_finish(const double* B, int64_t d, int s, const double* G, const double* V,
                            double nu, double* U, double* lam, double* work, cudaStream_t st);
