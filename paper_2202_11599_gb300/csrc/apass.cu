@@ -26,6 +26,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 namespace nys {
 
@@ -510,6 +511,41 @@ void apass_set_tuned_rows(const nys_matrix* A, int rows) {
   else g_tuned_rows[{dev, A->dtype, vpt, A->ld * esz}] = rows;
 }
 
+// Calibrated row splits of the warp-specialised float pass, keyed by (device, dtype, row
+// bytes, rows, grid, rows per stage); device arrays of grid + 1 boundaries, owned here.
+static std::map<std::tuple<int, int, int64_t, int64_t, int, int>, int64_t*> g_row_split;
+static unsigned long long* g_cta_time = nullptr;   // set only while a calibration runs
+
+static const int64_t* row_split_lookup(int dtype, int64_t rowbytes, int64_t n, int grid, int R) {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_row_split.find({dev, dtype, rowbytes, n, grid, R});
+  return it == g_row_split.end() ? nullptr : it->second;
+}
+
+static cudaError_t row_split_store(int dtype, int64_t rowbytes, int64_t n, int grid, int R, const int64_t* host,
+                                   cudaStream_t st) {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const auto key = std::make_tuple(dev, dtype, rowbytes, n, grid, R);
+  auto it = g_row_split.find(key);
+  if (!host) {
+    if (it != g_row_split.end()) {
+      NYS_CUDA_TRY(cudaStreamSynchronize(st));
+      NYS_CUDA_TRY(cudaFree(it->second));
+      g_row_split.erase(it);
+    }
+    return cudaSuccess;
+  }
+  int64_t* buf = it == g_row_split.end() ? nullptr : it->second;
+  if (!buf) {
+    NYS_CUDA_TRY(cudaMalloc(&buf, (size_t)(grid + 1) * sizeof(int64_t)));
+    g_row_split[key] = buf;
+  }
+  NYS_CUDA_TRY(cudaMemcpyAsync(buf, host, (size_t)(grid + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  return cudaStreamSynchronize(st);
+}
+
 static int tuned_rows(int dtype, int vpt, int64_t rowbytes) {
   const int dev = current_device();
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -774,6 +810,12 @@ cudaError_t apass_run(const ApassArgs& a, const ApassPlan& plan, void* partial, 
   k.skip = a.skip;
   k.executed = nullptr;
   k.col_scale = a.col_scale;
+  k.row_split = nullptr;
+  k.cta_time = nullptr;
+  if (plan.ws && !compute_is_f64(a.dtype)) {
+    k.row_split = row_split_lookup(a.dtype, a.ld * (int64_t)dtype_size(a.dtype), a.n, plan.grid, plan.rows_per_step);
+    k.cta_time = g_cta_time;
+  }
   {
     const double esz = (double)dtype_size(a.dtype), csz = compute_is_f64(a.dtype) ? 8.0 : 4.0;
     double bytes = (double)a.n * (double)a.d * esz + (double)a.d * csz + (double)plan.grid * a.d * csz;
@@ -806,6 +848,126 @@ cudaError_t apass_run(const ApassArgs& a, const ApassPlan& plan, void* partial, 
     // algorithmic bytes: A read once, p read, partials written, per-row vectors touched
     stats_record_apass(e0, e1, k.bytes_alg, a.dtype, flag);
   }
+  return err;
+}
+
+// Balance the row slabs of the warp-specialised float pass over its CTAs (one read of A
+// split over the SMs, Table 1's T_mv).  With equal slabs the CTAs on a few SMs finish ~3 %
+// later on every pass (a group of SMs streams slower), and the pass waits for them.  Each
+// CTA's time is measured, the rows are re-split in proportion to the measured speeds
+// (boundaries on whole stages), up to three times, and a split is kept only while the pass
+// gets faster.  The split fixes which rows each CTA sums, so for a given split the results
+// stay bitwise repeatable.  ms_equal / ms_split: mean pass time before and after.
+cudaError_t apass_balance_rows(const nys_matrix* A, const void* p, void* part, int* dstat, cudaStream_t st,
+                               double* ms_equal, double* ms_split) {
+  ApassPlan plan;
+  if (ms_equal) *ms_equal = 0.0;
+  if (ms_split) *ms_split = 0.0;
+  if (compute_is_f64(A->dtype) || !apass_plan(A, &plan) || !plan.ws) return cudaSuccess;
+  const int G = plan.grid, R = plan.rows_per_step;
+  const int64_t n = A->n, rowbytes = A->ld * (int64_t)dtype_size(A->dtype);
+  if (G < 2 || n < (int64_t)G * R * 8) return cudaSuccess;   // too few rows per CTA to matter
+  ApassArgs a;
+  a.A = A->data;
+  a.n = A->n;
+  a.d = A->d;
+  a.ld = A->ld;
+  a.dtype = A->dtype;
+  a.col_scale = A->col_scale;
+  a.p = p;
+  a.D = nullptr;
+  a.b = nullptr;
+  a.D_out = nullptr;
+  a.t_out = nullptr;
+  a.mode = MODE_ID;
+  NYS_CUDA_TRY(row_split_store(A->dtype, rowbytes, n, G, R, nullptr, st));   // start from the equal split
+  unsigned long long* tbuf = nullptr;
+  NYS_CUDA_TRY(cudaMalloc(&tbuf, (size_t)2 * G * sizeof(unsigned long long)));
+  std::vector<unsigned long long> th((size_t)2 * G);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  auto time_passes = [&](double* ms) -> cudaError_t {
+    NYS_CUDA_TRY(apass_run(a, plan, part, nullptr, dstat, st, false));   // warm-up
+    NYS_CUDA_TRY(cudaEventRecord(e0, st));
+    for (int r = 0; r < 5; ++r) NYS_CUDA_TRY(apass_run(a, plan, part, nullptr, dstat, st, false));
+    NYS_CUDA_TRY(cudaEventRecord(e1, st));
+    NYS_CUDA_TRY(cudaEventSynchronize(e1));
+    float f = 0.f;
+    NYS_CUDA_TRY(cudaEventElapsedTime(&f, e0, e1));
+    *ms = f / 5.0;
+    return cudaSuccess;
+  };
+  // per-CTA time (ns) from the pass's first start to the CTA's end, median of 5 passes
+  auto cta_times = [&](std::vector<double>& T) -> cudaError_t {
+    std::vector<std::vector<double>> rep((size_t)G);
+    g_cta_time = tbuf;
+    for (int r = 0; r < 5; ++r) {
+      NYS_CUDA_TRY(cudaMemsetAsync(tbuf, 0, (size_t)2 * G * sizeof(unsigned long long), st));
+      const cudaError_t e = apass_run(a, plan, part, nullptr, dstat, st, false);
+      if (e != cudaSuccess) {
+        g_cta_time = nullptr;
+        return e;
+      }
+      NYS_CUDA_TRY(cudaMemcpyAsync(th.data(), tbuf, th.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+      NYS_CUDA_TRY(cudaStreamSynchronize(st));
+      unsigned long long t0 = ~0ull;
+      for (int c = 0; c < G; ++c) t0 = std::min(t0, th[2 * c]);
+      for (int c = 0; c < G; ++c) rep[c].push_back((double)(th[2 * c + 1] - t0));
+    }
+    g_cta_time = nullptr;
+    T.resize(G);
+    for (int c = 0; c < G; ++c) {
+      std::sort(rep[c].begin(), rep[c].end());
+      T[c] = rep[c][rep[c].size() / 2];
+    }
+    return cudaSuccess;
+  };
+  std::vector<int64_t> cur((size_t)G + 1), best_split;
+  for (int c = 0; c <= G; ++c) cur[c] = n * c / G;
+  double ms0 = 0.0, best = 0.0;
+  if (err == cudaSuccess) err = time_passes(&ms0);
+  best = ms0;
+  for (int it = 0; it < 3 && err == cudaSuccess; ++it) {
+    std::vector<double> T;
+    err = cta_times(T);
+    if (err != cudaSuccess) break;
+    std::vector<double> speed((size_t)G);
+    double tot = 0.0;
+    for (int c = 0; c < G; ++c) {
+      speed[c] = (double)(cur[c + 1] - cur[c]) / std::max(T[c], 1.0);
+      tot += speed[c];
+    }
+    std::vector<int64_t> nxt((size_t)G + 1);
+    nxt[0] = 0;
+    double cum = 0.0;
+    for (int c = 0; c + 1 < G; ++c) {
+      cum += (double)n * speed[c] / tot;
+      int64_t b = (int64_t)std::llround(cum / R) * R;
+      b = std::max(b, nxt[c] + R);
+      b = std::min(b, n - (int64_t)(G - 1 - c) * R);
+      nxt[c + 1] = b;
+    }
+    nxt[G] = n;
+    err = row_split_store(A->dtype, rowbytes, n, G, R, nxt.data(), st);
+    double ms = 0.0;
+    if (err == cudaSuccess) err = time_passes(&ms);
+    if (err != cudaSuccess) break;
+    if (ms < best * 0.998) {
+      best = ms;
+      best_split = nxt;
+      cur = nxt;
+    } else {
+      break;
+    }
+  }
+  if (err == cudaSuccess)
+    err = row_split_store(A->dtype, rowbytes, n, G, R, best_split.empty() ? nullptr : best_split.data(), st);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(tbuf);
+  if (ms_equal) *ms_equal = ms0;
+  if (ms_split) *ms_split = best;
   return err;
 }
 

@@ -35,6 +35,11 @@ struct ApassKArgs {
   DevTimer tm;    // instrumentation: in-kernel launch timing (null pointers when off)
   double bytes_alg;
   const float* col_scale;  // FP8: p is read as col_scale o p (the reduce scales the sums)
+  // warp-specialised float pass: CTA c takes rows [row_split[c], row_split[c + 1]) (null: the
+  // equal split n c / grid); cta_time (null when off): start and end %globaltimer of CTA c
+  // at [2 c] and [2 c + 1], for the row-split calibration
+  const int64_t* row_split;
+  unsigned long long* cta_time;
 };
 
 __device__ __forceinline__ unsigned long long gtimer() {

@@ -193,8 +193,9 @@ __device__ __forceinline__ bool ws_pass_float(const ApassKArgs& a, WsFloatSmem<R
   const uint32_t rowbytes = (uint32_t)(ld_o * ESZ);
   const int S = S_o;
   const uint32_t stage_bytes = (uint32_t)R * rowbytes;
-  const int64_t r0 = n_o * (int64_t)blockIdx.x / gridDim.x;
-  const int64_t r1 = n_o * (int64_t)(blockIdx.x + 1) / gridDim.x;
+  const int64_t r0 = a.row_split ? a.row_split[blockIdx.x] : n_o * (int64_t)blockIdx.x / gridDim.x;
+  const int64_t r1 = a.row_split ? a.row_split[blockIdx.x + 1] : n_o * (int64_t)(blockIdx.x + 1) / gridDim.x;
+  if (a.cta_time && tid == 0) a.cta_time[2 * blockIdx.x] = gtimer();
   const int nsteps = (int)((r1 - r0 + R - 1) / R);
   const int tail_n = (int)(d_o % VEC);
   const bool nodot = a.mode == MODE_CONST;
@@ -350,6 +351,10 @@ __device__ __forceinline__ bool ws_pass_float(const ApassKArgs& a, WsFloatSmem<R
   }
   if (tid == 0 && a.loss_part) a.loss_part[blockIdx.x] = sm.loss;
   timer_end(a, ts_slot, DT);
+  if (a.cta_time) {
+    __syncthreads();
+    if (tid == 0) a.cta_time[2 * blockIdx.x + 1] = gtimer();
+  }
   return true;
 }
 

@@ -1519,6 +1519,13 @@ nys_status nys_autotune_apass(const nys_matrix* A, int32_t* rows_out, double* ms
   cudaEventDestroy(e1);
   (void)f64;
   apass_set_tuned_rows(A, best);
+  // then the row slabs of the warp-specialised float pass, balanced over the CTAs
+  double ms_eq = 0.0, ms_split = 0.0;
+  NYS_CU(apass_balance_rows(A, p, part, dstat, st, &ms_eq, &ms_split));
+  if (ms_split > 0.0 && ms_split < best_ms) best_ms = ms_split;
+  if (std::getenv("NYS_TRACE"))
+    std::fprintf(stderr, "[nys] autotune: rows %d, pass %.4f ms (equal slabs %.4f ms, balanced %.4f ms)\n", best, best_ms,
+                 ms_eq, ms_split);
   if (rows_out) *rows_out = best;
   if (ms_out) *ms_out = best_ms;
   return NYS_OK;

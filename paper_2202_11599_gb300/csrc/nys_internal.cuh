@@ -69,6 +69,11 @@ nys_status check_hmatvec_args(const nys_matrix* A, double rho, const void* p, co
 void apass_set_tuned_rows(const nys_matrix* A, int rows);   // rows <= 0 clears
 int apass_row_candidates(const nys_matrix* A, int* out);      // out: up to 3 values
 size_t apass_partial_bytes(const nys_matrix* A, const ApassPlan& plan);
+// Calibrate unequal row slabs for the warp-specialised float pass of A (kept per device,
+// dtype, row bytes, rows, grid and stage depth; used by every later pass of that shape).
+// p: a device vector of A's compute type (d entries), part: partial scratch of the plan.
+cudaError_t apass_balance_rows(const nys_matrix* A, const void* p, void* part, int* dstat, cudaStream_t st,
+                               double* ms_equal, double* ms_split);
 
 // y = sum of partials + rho * p (+ beta * y_prev?) -- y in compute type.
 // dot_part (optional): per-block partials of p^T y (double), count returned via nblk.
