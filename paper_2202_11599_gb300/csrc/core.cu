@@ -568,17 +568,27 @@ __device__ __forceinline__ void rr_pair(int N, int r, int m, int& p, int& q) {
 }
 
 // Rotation (c, sn) that zeroes a_pq of the 2x2 block [[app, apq], [apq, aqq]] under
-// J^T A J with J_pp = J_qq = c, J_pq = sn, J_qp = -sn (Golub & Van Loan, Alg. 8.4.1).
+// J^T A J with J_pp = J_qq = c, J_pq = sn, J_qp = -sn (Golub & Van Loan, Alg. 8.4.1: the
+// smaller root t of t^2 + 2 tau t - 1 = 0, tau = (aqq - app) / (2 apq), c = 1/sqrt(1 + t^2),
+// sn = t c).  With h = aqq - app, g = 2 apq and r = sqrt(h^2 + g^2) that root is
+// t = sign(tau) |g| / (|h| + r), and 1 + t^2 = 2 r (r + |h|) / (|h| + r)^2, so
+//   c = (|h| + r) / sqrt(2 r (r + |h|)),   sn = sign(tau) |g| / sqrt(2 r (r + |h|)):
+// one square root and one reciprocal square root instead of two of each and three
+// divisions (the FP64 divide / square-root chain bounded each Jacobi round).
 __device__ __forceinline__ void jacobi_rot(double app, double aqq, double apq, double& c, double& sn) {
-  if (apq == 0.0 || fabs(apq) <= 1e-300 || fabs(apq) < 1e-17 * sqrt(fabs(app * aqq))) {
+  if (apq == 0.0 || fabs(apq) <= 1e-300 || apq * apq < 1e-34 * fabs(app * aqq)) {
     c = 1.0;
     sn = 0.0;
     return;
   }
-  const double tau = (aqq - app) / (2.0 * apq);
-  const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-  c = 1.0 / sqrt(1.0 + t * t);
-  sn = t * c;
+  const double h = aqq - app, g = 2.0 * apq;
+  const double ah = fabs(h);
+  const double r = sqrt(fma(h, h, g * g));
+  const double inv = rsqrt(2.0 * r * (r + ah));
+  // sign(tau) = sign(h) sign(g), and +1 for h = 0
+  const double gs = h > 0.0 ? g : (h < 0.0 ? -g : fabs(g));
+  c = (ah + r) * inv;
+  sn = gs * inv;
 }
 
 // One round: Aout = J^T Ain J and V <- V J for the round's N/2 disjoint rotations.
