@@ -969,7 +969,7 @@ def main():
     # DRAM bytes (read + write) per launch of the BF16 A-pass on this workload, from the ncu
     # capture of the warp-specialised kernel on 50,000 x 10,000 (profiles/): reads scale with
     # the rows (2 x 1.000266 GB), the per-CTA partial writes do not (3.0 MB).
-    ap.add_argument("--traffic", type=lambda v: None if v == "none" else float(v), default=2.0035e9,
+    ap.add_argument("--traffic", type=lambda v: None if v == "none" else float(v), default=2.0033e9,
                     help="ncu dram bytes per A-pass launch (from a committed profile), if current")
     ap.add_argument("--pcg-tol", type=float, default=None,
                     help="PCG tolerance of the mixed solve (beta for rnorm_pow, default 1.75; rel-tol otherwise, "
