@@ -514,7 +514,7 @@ void apass_set_tuned_rows(const nys_matrix* A, int rows) {
 // Calibrated row splits of the warp-specialised float pass, keyed by (device, dtype, row
 // bytes, rows, grid, rows per stage); device arrays of grid + 1 boundaries, owned here.
 static std::map<std::tuple<int, int, int64_t, int64_t, int, int>, int64_t*> g_row_split;
-static unsigned long long* g_cta_time = nullptr;   // set only while a calibration runs
+static thread_local unsigned long long* g_cta_time = nullptr;   // set only while this thread calibrates
 
 static const int64_t* row_split_lookup(int dtype, int64_t rowbytes, int64_t n, int grid, int R) {
   const int dev = current_device();
