@@ -605,24 +605,24 @@ __global__ void __launch_bounds__(kVecThreads) admm_zu_kernel(int64_t d, const C
   }
 }
 
-// Sum of the per-block partials part5[b * 5 + t] over b = 0 .. nb-1 in increasing b (the
-// same order as a sequential loop), called by one full warp; every lane gets the five sums.
-// The warp stages the partials in shared memory with coalesced loads, then lane t adds
-// column t: five chains side by side (one FP64 add per warp instruction instead of five).
+// Sum of the per-block partials part5[b * 5 + t] over b = 0 .. nb-1 in a fixed order, called
+// by one full warp; every lane gets the five sums.  Lane l adds the partials b = l, l + 32,
+// ... in increasing b, then a warp tree adds the lanes: a dependent chain of about
+// nb / 32 + 5 FP64 adds instead of nb (dependent FP64 adds are slow on this GPU).  Every
+// caller -- the host-driven loop, both graph bodies and the cooperative kernels -- uses this
+// function, so they agree bit for bit.
 constexpr int kPart5Max = 256;
 __device__ __forceinline__ void sum_part5(int nb, const double* part5, double (&a)[5]) {
-  __shared__ double sp[kPart5Max * 5];
   const int lane = threadIdx.x & 31;
-  const bool staged = nb <= kPart5Max;
-  if (staged) {
-    for (int i = lane; i < nb * 5; i += 32) sp[i] = __ldcg(part5 + i);
-    __syncwarp();
-  }
-  double acc = 0.0;
-  if (lane < 5)
-    for (int b = 0; b < nb; ++b) acc += staged ? sp[b * 5 + lane] : __ldcg(part5 + (int64_t)b * 5 + lane);
 #pragma unroll
-  for (int t = 0; t < 5; ++t) a[t] = __shfl_sync(0xffffffffu, acc, t);
+  for (int t = 0; t < 5; ++t) a[t] = 0.0;
+  for (int b = lane; b < nb; b += 32) {
+    const double* o = part5 + (int64_t)b * 5;
+#pragma unroll
+    for (int t = 0; t < 5; ++t) a[t] += __ldcg(o + t);
+  }
+#pragma unroll
+  for (int t = 0; t < 5; ++t) a[t] = warp_sum(a[t]);
 }
 
 // r_p, r_d (Sec. 2.1), the next PCG tolerance sqrt(r_p r_d) (Sec. 5) and the
