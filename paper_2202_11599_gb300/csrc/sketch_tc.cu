@@ -592,10 +592,12 @@ cudaError_t make_tile_map(CUtensorMap* m, const uint16_t* base, int64_t K, int64
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// TMA staging unless NYS_TC_TMA=0 (the cp.async form: the same MMAs, the same bits).
+// TMA staging unless NYS_TC_TMA=0 or the driver offers no tensor-map encoder (then the
+// cp.async form: the same MMAs, the same bits).
 bool tc_use_tma() {
   const char* e = std::getenv("NYS_TC_TMA");
-  return !(e && std::atoi(e) == 0);
+  if (e && std::atoi(e) == 0) return false;
+  return encode_tiled_fn() != nullptr;
 }
 
 template <int EPI, int AT, int BT, int BM2>
